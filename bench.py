@@ -1,0 +1,340 @@
+#!/usr/bin/env python3
+"""Throughput of deep-potential MD on one B300: energy+force atom-steps/s.
+
+One step = one velocity-Verlet MD step of the whole hot path (neighbour update,
+environment, embedding, attention layers, descriptor, fitting, hand-written
+backward, force/virial assembly, integration) on the 24,000-atom synthetic
+protein-in-water system (1,500-atom H/C/N/O/S blob in 7,500 waters, 57.69 x
+57.69 x 72.11 A, 0.1 atoms/A^3) with the attention-family model (embedding
+1->32->64->128, 3 attention layers of width 128 with 4 heads, axis 16,
+fitting 2048->240->240->240->1, rc 6 A, nmax 120), random N(0, 0.1) weights,
+300 K Maxwell-Boltzmann velocities, dt 0.5 fs, lists rebuilt every 10 steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--form fused|plain]
+    python bench.py --impl reference ...      # the FP64 CPU oracle on host cores
+
+Prints one JSON line (rank 0).  N > 1 (torchrun) runs N independent replicas,
+one per GPU (the model is atom-local; no collective is needed): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import configs as CF, maxwell_boltzmann, normal_blob  # noqa: E402
+
+WORKLOAD = ("protein-in-water 24,000 atoms (1,500-atom blob + 7,500 H2O, 57.69x57.69x72.11 A), "
+            "attention family: embedding 1-32-64-128, 3 attention layers (H 128, 4 heads), "
+            "axis 16, fitting 2048-240-240-240-1, rc 6 A, nmax 120; NVE dt 0.5 fs, rebuild every 10")
+METRIC = "energy+force atom-steps/s"
+FP32_ALU_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # 148 SMs x 128 FP32 lanes x FMA x 2.032 GHz
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ algorithmic work
+def af_flops_per_atom(model, n):
+    """FLOPs of energy + input-gradient backward for one atom with n real neighbours
+    (padding and recomputation excluded)."""
+    d = model.as_dict()
+    e1, e2, m1, m2, H, L = d["e1"], d["e2"], d["m1"], d["m2"], d["hidden"], d["n_layers"]
+    emb = 2 * n * (e1 + e1 * e2 + e2 * m1)
+    att_fwd = 2 * n * m1 * 3 * H + 4 * n * n * H + 2 * n * H * m1
+    att_bwd = 2 * n * m1 * H + 8 * n * n * H + 2 * n * 3 * H * m1
+    desc = 2 * 4 * n * m1 + 2 * 4 * m1 * m2
+    fit = 2 * (m1 * m2 * d["f1"] + d["f1"] * d["f2"] + d["f2"] * d["f3"] + d["f3"])
+    return 2 * emb + L * (att_fwd + att_bwd) + 3 * desc + 2 * fit
+
+
+def setup_system():
+    s = CF.protein24k()
+    model = CF.ATTN_MODEL
+    masses = s.masses
+    v0 = maxwell_boltzmann(masses[s.types], 300.0, CF.VELOCITY_SEED)
+    return s, model, masses, v0
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    s, model, masses, v0 = setup_system()
+    w = normal_blob(oracle.af_weight_count(model), CF.WEIGHT_SEED)
+    rng = np.random.default_rng(0)
+    per_step = args.ref_sample
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    for _ in range(args.warmup):
+        oracle.af_atoms(model, w, s.types, s.coords, s.box, rng.choice(s.n, per_step, replace=False))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.af_atoms(model, w, s.types, s.coords, s.box, rng.choice(s.n, per_step, replace=False))
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt
+    sample = (f"{per_step} random centre atoms per step (energy + pair gradients of each, FP64 "
+              f"C oracle, OpenMP over atoms)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "atom-steps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_atoms": s.n},
+            "cpu_baseline": {"value": value, "unit": "atom-steps/s", "cores": threads,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "atom-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(seconds=12.0):
+    """The oracle as it stands, timed on this host over a bounded random sample."""
+    import oracle
+    s, model, _, _ = setup_system()
+    w = normal_blob(oracle.af_weight_count(model), CF.WEIGHT_SEED)
+    rng = np.random.default_rng(1)
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    batch = max(8, threads * 4)
+    done = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        oracle.af_atoms(model, w, s.types, s.coords, s.box, rng.choice(s.n, batch, replace=False))
+        done += batch
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "atom-steps/s", "cores": threads, "kind": "oracle",
+            "sample": f"{done} random centre atoms of the 24,000-atom system in {dt:.1f} s "
+                      f"(energy + pair gradients per atom, FP64, OpenMP)"}
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2602_02234_b300 as dp
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    s, model, masses, v0 = setup_system()
+    w = normal_blob(dp.weight_count(dp.model_desc(model, dp.PREC_PLAIN_F32)), CF.WEIGHT_SEED)
+    stream = torch.cuda.Stream()
+
+    def make(prec):
+        return dp.DeepPotential(dp.model_desc(model, prec, skin=CF.SKIN,
+                                              rebuild_every=CF.REBUILD_EVERY),
+                                s.types, s.box, w, masses=masses, stream=stream)
+
+    forms = []
+    if args.form in ("auto", "fused"):
+        try:
+            forms.append(("fused_bf16", make(dp.PREC_FUSED_BF16)))
+        except dp.DPError as e:
+            if args.form == "fused":
+                raise
+            print(f"# fused form unavailable: {e}", file=sys.stderr)
+    forms.append(("plain_f32", make(dp.PREC_PLAIN_F32)))
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def time_steps(pot, K):
+        pot.set_state(s.coords, v0, 0)
+        pot.step(args.warmup, CF.DT_FS)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        with ClockSampler(local_rank) as clk:
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                pot.step(K, CF.DT_FS)
+                e1.record(stream)
+            e1.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, clk.summary()
+
+    results = {}
+    for name, pot in forms:
+        ms, clocks = time_steps(pot, args.steps)
+        results[name] = {"ms": ms, "clocks": clocks, "pot": pot}
+
+    main_name = forms[0][0]
+    main = results[main_name]
+    pot = main["pot"]
+    K = args.steps
+    value = s.n * K * world / (main["ms"] / 1e3)
+
+    # network phase alone: the dominant kernels, timed with events on their stream
+    cnt, _, _ = pot.neighbours()
+    nreal = np.minimum(cnt, model.nmax)
+    flops = float(sum(af_flops_per_atom(model, int(k)) for k in nreal))
+    reps = 5
+    pot.enqueue_network(1)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        pot.enqueue_network(reps)
+        e1.record(stream)
+    e1.synchronize()
+    net_ms = e0.elapsed_time(e1) / reps
+    pk, pk_kind = peaks()
+    if main_name == "fused_bf16":
+        peak = pk.get("bf16_tflops_sustained", 1400.0)
+        bound, peak_note = "tensor", f"bf16 dense sustained ({pk_kind})"
+    else:
+        peak = FP32_ALU_PEAK_TFLOPS
+        bound, peak_note = "alu", "FP32 FFMA: 148 SMs x 128 lanes x 2 x 2.032 GHz (derived)"
+    achieved = flops / (net_ms / 1e3) / 1e12
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": f"{main_name} network phase (all network kernels of one evaluation)",
+                "peak_kind": peak_note, "algorithmic_flop_per_launch": flops,
+                "launch_ms": net_ms}
+
+    # end to end through the C ABI with pinned host buffers, copies every step
+    xh = torch.empty((s.n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    vh = torch.empty((s.n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    x_now, v_now, _ = pot.get_state()
+    xh[:] = x_now
+    vh[:] = v_now
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        tr = pot.step(1, CF.DT_FS, coords=xh, vel=vh, energies=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": s.n * K * world / e2e_s, "unit": "atom-steps/s",
+           "h2d_bytes_per_step": 2 * xh.nbytes, "d2h_bytes_per_step": 2 * xh.nbytes + tr.nbytes,
+           "note": "host wall clock around dp_step(1) with pinned host coords/velocities in and out"}
+
+    n_comp, n_step = pot.kernels_per_step()
+    line = {"metric": METRIC, "value": value, "unit": "atom-steps/s", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": main["ms"] / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16" if main_name == "fused_bf16" else "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_atoms": s.n, "form": main_name,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2: skin/selection lists and pair gradients "
+                             "(~0.4 GB per step) exceed the 126 MB L2"},
+            "clocks": main["clocks"], "e2e": e2e, "gpu_launches": n_step * K,
+            "roofline": roofline}
+    for name in results:
+        line[name] = {"value": s.n * K * world / (results[name]["ms"] / 1e3),
+                      "ms_per_step": results[name]["ms"] / K}
+    if "fused_bf16" in results and "plain_f32" in results:
+        line["fused_vs_plain"] = results["plain_f32"]["ms"] / results["fused_bf16"]["ms"]
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for name, p in forms:
+        p.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--form", choices=["auto", "fused", "plain"], default="auto")
+    ap.add_argument("--ref-sample", type=int, default=48)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)       # timing rule: at least 3 untimed warm-up steps
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

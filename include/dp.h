@@ -1,0 +1,177 @@
+/*
+ * dp.h -- C ABI of libdp.so: deep-potential energy, force and virial inference
+ * and velocity-Verlet molecular dynamics on one NVIDIA B300 (sm_103a).
+ *
+ * The method is the one the paper (arXiv 2602.02234, Sec. II-III) runs inside
+ * GROMACS through DeePMD-kit: a deep potential maps each atom's local
+ * environment (neighbours within a cutoff, Sec. II; 0.6 nm, Sec. IV) to an
+ * atomic energy, E is their sum and the forces are -dE/dx (Sec. II).  The MD
+ * engine passes coordinates, species and the box and receives forces (Sec.
+ * III); these calls are that interface.  Two model families are provided:
+ *
+ *   DP_FAMILY_ATTENTION -- DPA2-like (Sec. II: "repinit" embedding MLP,
+ *     "repformer" residual self-attention layers, "fitting-net"): smooth switch
+ *     and environment matrix, per-neighbour embedding MLP, gated neighbour
+ *     attention, descriptor T^T T, per-atom fitting MLP.
+ *   DP_FAMILY_GRAPH -- DPA3-like (Sec. II: GNN with line-graph bond and angle
+ *     representations): node, edge and angle updates over the neighbour graph,
+ *     then the per-atom fitting MLP.
+ *
+ * Units: Angstrom, femtosecond, amu, eV.  Boxes are orthorhombic and periodic;
+ * coordinates may lie outside the box (they are wrapped internally only for
+ * neighbour search).
+ *
+ * Conventions for every call:
+ *   - The caller owns every array it passes; the library copies inputs and
+ *     writes outputs before returning (dp_compute, dp_step synchronise the
+ *     library's stream before returning).
+ *   - Array arguments are host pointers unless the call's ptr_kind argument is
+ *     DP_PTR_DEVICE, in which case they are device pointers on the context's
+ *     device.
+ *   - Return value 0 (DP_OK) on success, a negative DP_ERR_* code otherwise;
+ *     dp_last_error() gives a message.  No C++ exception crosses the ABI.
+ *   - A context is not thread-safe: one host thread at a time per context.
+ *   - Weight blob: FP64, layout fixed by the model description (see
+ *     dp_weight_count); the library keeps its own converted copies.
+ */
+#ifndef DP_H
+#define DP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  DP_OK = 0,
+  DP_ERR_ARG = -1,             /* invalid argument (message says which)      */
+  DP_ERR_OOM = -2,             /* device memory (or the set budget) exceeded */
+  DP_ERR_NLIST_OVERFLOW = -3,  /* more candidates than the list capacity     */
+  DP_ERR_TIMEOUT = -4,         /* a device-side wait gave up                 */
+  DP_ERR_NONFINITE = -5,       /* energy or forces not finite                */
+  DP_ERR_CUDA = -6,            /* a CUDA runtime call failed                 */
+  DP_ERR_UNSUPPORTED = -7      /* valid request this build does not provide  */
+};
+
+enum { DP_FAMILY_ATTENTION = 0, DP_FAMILY_GRAPH = 1 };
+
+/* Arithmetic of the network:
+ *   PLAIN_F64  -- unfused kernels, everything in FP64 (small systems, parity);
+ *   PLAIN_F32  -- unfused kernels, one simple kernel per operation, FP32;
+ *   FUSED_BF16 -- fused persistent kernels: BF16 tensor-core GEMMs with FP32
+ *                 accumulation, FP32 switch/softmax/LayerNorm, FP64 energy,
+ *                 virial and integration. */
+enum { DP_PREC_PLAIN_F64 = 0, DP_PREC_PLAIN_F32 = 1, DP_PREC_FUSED_BF16 = 2 };
+
+enum { DP_PTR_HOST = 0, DP_PTR_DEVICE = 1 };
+
+typedef struct dp_model_desc {
+  int family;      /* DP_FAMILY_*                                              */
+  int precision;   /* DP_PREC_*                                                */
+  int n_species;   /* species indices are 0 .. n_species-1                     */
+  int nmax;        /* neighbours kept per atom (nearest first)                 */
+  double rcut;     /* cutoff rc (A)                                            */
+  double rcut_smth;/* switch start rs (A), rs < rc                             */
+  /* attention family */
+  int e1, e2, m1;  /* embedding 1 -> e1 -> e2 -> m1                            */
+  int m2;          /* descriptor axis width (m2 <= m1)                         */
+  int n_layers;    /* attention layers                                         */
+  int hidden;      /* attention width H = heads * d                            */
+  int heads;
+  /* graph family */
+  int node_dim, edge_dim, n_gnn_layers;
+  int angle_nmax;  /* angle neighbours per atom                                */
+  double angle_rcut, angle_rcut_smth;
+  /* fitting MLP widths (both families): in -> f1 -> f2 -> f3 -> 1            */
+  int f1, f2, f3;
+  /* neighbour-list maintenance (dp_step): skin (A) and rebuild period (steps).
+   * The result never depends on them: lists are rebuilt early whenever an atom
+   * moved more than skin/2 since the last build. 0 selects 1 A / 10 steps.   */
+  double skin;
+  int rebuild_every;
+  int reserved[7];
+} dp_model_desc;
+
+typedef struct dp_ctx dp_ctx;
+
+/* Number of FP64 values in the weight blob for `desc` (written to *n).
+ * Attention family, in order (row-major W[in][out], W before b):
+ *   per species t:  W1[1][e1] b1[e1] W2[e1][e2] b2[e2] W3[e2][m1] b3[m1]
+ *   per layer l:    Wq[m1][H] Wk[m1][H] Wv[m1][H] Wo[H][m1] bo[m1]
+ *   per species t:  F1[m1*m2][f1] c1[f1] F2[f1][f2] c2[f2] F3[f2][f3] c3[f3] F4[f3][1] c4[1]
+ * Graph family: see the graph-family section of the library documentation
+ * (per species fitting at the end, same order rule).
+ * Errors: DP_ERR_ARG for an invalid description. */
+int dp_weight_count(const dp_model_desc* desc, size_t* n);
+
+/* Create a context for one system of n_atoms atoms.
+ *   types   [n_atoms]     species index of each atom (host)
+ *   masses  [n_species]   amu, only needed by dp_step (host, nullable)
+ *   box     [3]           orthorhombic box lengths, A (host)
+ *   weights [n_weights]   FP64 blob (host)
+ *   cuda_stream           cudaStream_t to run on (NULL: the library creates one)
+ * The library allocates all device buffers here and fails early with
+ * DP_ERR_OOM when they do not fit.  *out is NULL on failure. */
+int dp_init(dp_ctx** out, const dp_model_desc* desc, int n_atoms, const int32_t* types,
+            const double* masses, const double* box, const double* weights, size_t n_weights,
+            void* cuda_stream);
+
+/* Energy (eV), forces (n_atoms x 3, eV/A, nullable) and virial (3 x 3 row-major,
+ * eV, nullable) at coordinates (n_atoms x 3, A).  Virial X_ab = -sum over
+ * neighbour pairs of r_a g_b with g = dE/dr.  Neighbour lists are rebuilt as
+ * needed.  The coordinates become the context's resident positions. */
+int dp_compute(dp_ctx* ctx, const double* coords, double* energy, double* forces, double* virial,
+               int ptr_kind);
+
+/* n_steps of velocity-Verlet NVE with time step dt_fs:
+ *   v += dt/2 F/m; x += dt v; F = F(x); v += dt/2 F/m.
+ * coords_io / vel_io (n_atoms x 3): when non-NULL they are uploaded before the
+ * first step and overwritten with the final state; when NULL the resident
+ * state is used and kept on the device.  energies_out (nullable): per step
+ * {potential, kinetic} in eV, 2*n_steps values.  The whole step is one CUDA
+ * graph launch.  Needs masses at dp_init. */
+int dp_step(dp_ctx* ctx, int n_steps, double dt_fs, double* coords_io, double* vel_io,
+            double* energies_out, int ptr_kind);
+
+/* Copy the resident state out / in (n_atoms x 3 each, nullable), plus the step
+ * counter.  Resuming from a saved state reproduces the run bit for bit. */
+int dp_get_state(dp_ctx* ctx, double* coords, double* vel, long long* step, int ptr_kind);
+int dp_set_state(dp_ctx* ctx, const double* coords, const double* vel, long long step,
+                 int ptr_kind);
+
+/* Inspection after dp_compute / dp_step (host pointers):
+ *   nbr_j   [n_atoms x nmax]     neighbour atom, nearest first, -1 = empty slot
+ *   nbr_img [n_atoms x nmax x 3] periodic image n of each neighbour
+ *                                (r = (w_j - w_i) + n L, w = wrapped position)
+ *   n_in_rc [n_atoms]            neighbours within rc before truncation
+ * Any pointer may be NULL. */
+int dp_get_neighbours(dp_ctx* ctx, int32_t* nbr_j, int32_t* nbr_img, int32_t* n_in_rc);
+
+/* Atomic energies e_i (n_atoms, host) of the last evaluation. */
+int dp_get_atom_energies(dp_ctx* ctx, double* atom_e);
+
+/* Enqueue `reps` evaluations of the network alone (no neighbour update, no
+ * force assembly) on the context's stream, at the resident neighbour lists,
+ * without synchronising; for timing the network kernels with events on that
+ * stream.  Needs a prior dp_compute or dp_step. */
+int dp_enqueue_network(dp_ctx* ctx, int reps);
+
+/* Number of kernels one dp_compute / one dp_step launches (for reporting). */
+int dp_kernels_per_step(dp_ctx* ctx, int* n_compute, int* n_step);
+
+/* Device bytes held by the context. */
+int dp_device_bytes(dp_ctx* ctx, size_t* bytes);
+
+void dp_free(dp_ctx* ctx);
+
+/* Message of the last error on ctx (or of the last failed dp_init when ctx is
+ * NULL).  Valid until the next call on the same context. */
+const char* dp_last_error(const dp_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DP_H */

@@ -1,0 +1,292 @@
+"""Python binding of libdp.so: deep-potential energy/force inference and MD on one B300.
+
+Argument marshalling only -- every step of the computation runs in the CUDA
+kernels of ``libdp.so`` (built for sm_103a by ``paper_2602_02234_b300.build``).
+There is no CPU or PyTorch fallback: importing the binding without the built
+library raises, and so does any call that the library rejects.
+
+The names follow the C ABI of ``include/dp.h``:
+
+* ``ModelDesc``  -- ``dp_model_desc``
+* ``weight_count`` -- ``dp_weight_count``
+* ``DeepPotential`` -- a ``dp_ctx``: ``compute`` (``dp_compute``), ``step``
+  (``dp_step``), ``get_state``/``set_state``, ``neighbours``,
+  ``atom_energies``, ``kernels_per_step``, ``device_bytes``
+* ``DPEnergy`` -- ``torch.autograd.Function`` whose forward is ``dp_compute``
+  and whose backward returns -dE/dx * grad (forces from the hand-written
+  adjoint kernels).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdp.so")
+
+DP_OK, DP_ERR_ARG, DP_ERR_OOM, DP_ERR_NLIST_OVERFLOW, DP_ERR_TIMEOUT = 0, -1, -2, -3, -4
+DP_ERR_NONFINITE, DP_ERR_CUDA, DP_ERR_UNSUPPORTED = -5, -6, -7
+FAMILY_ATTENTION, FAMILY_GRAPH = 0, 1
+PREC_PLAIN_F64, PREC_PLAIN_F32, PREC_FUSED_BF16 = 0, 1, 2
+PTR_HOST, PTR_DEVICE = 0, 1
+
+_ERRNAMES = {DP_ERR_ARG: "DP_ERR_ARG", DP_ERR_OOM: "DP_ERR_OOM",
+             DP_ERR_NLIST_OVERFLOW: "DP_ERR_NLIST_OVERFLOW", DP_ERR_TIMEOUT: "DP_ERR_TIMEOUT",
+             DP_ERR_NONFINITE: "DP_ERR_NONFINITE", DP_ERR_CUDA: "DP_ERR_CUDA",
+             DP_ERR_UNSUPPORTED: "DP_ERR_UNSUPPORTED"}
+
+
+class DPError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class ModelDesc(C.Structure):
+    _fields_ = [("family", C.c_int), ("precision", C.c_int), ("n_species", C.c_int),
+                ("nmax", C.c_int), ("rcut", C.c_double), ("rcut_smth", C.c_double),
+                ("e1", C.c_int), ("e2", C.c_int), ("m1", C.c_int), ("m2", C.c_int),
+                ("n_layers", C.c_int), ("hidden", C.c_int), ("heads", C.c_int),
+                ("node_dim", C.c_int), ("edge_dim", C.c_int), ("n_gnn_layers", C.c_int),
+                ("angle_nmax", C.c_int), ("angle_rcut", C.c_double),
+                ("angle_rcut_smth", C.c_double), ("f1", C.c_int), ("f2", C.c_int),
+                ("f3", C.c_int), ("skin", C.c_double), ("rebuild_every", C.c_int),
+                ("reserved", C.c_int * 7)]
+
+
+def model_desc(model, precision: int, skin: float = 1.0, rebuild_every: int = 10) -> ModelDesc:
+    """A ``dp_model_desc`` from a dict (or object with ``as_dict``) of model sizes.
+
+    Attention family keys: n_species e1 e2 m1 m2 n_layers hidden heads f1 f2 f3
+    nmax rc rs.  Graph family keys: n_species node edge n_layers f1 f2 f3 nmax
+    na rc rs rca rsa.
+    """
+    d = model if isinstance(model, dict) else model.as_dict()
+    m = ModelDesc()
+    m.precision = precision
+    m.n_species = d["n_species"]
+    m.nmax = d["nmax"]
+    m.rcut = d["rc"]
+    m.rcut_smth = d["rs"]
+    m.f1, m.f2, m.f3 = d["f1"], d["f2"], d["f3"]
+    m.skin = skin
+    m.rebuild_every = rebuild_every
+    if "node" in d:
+        m.family = FAMILY_GRAPH
+        m.node_dim, m.edge_dim, m.n_gnn_layers = d["node"], d["edge"], d["n_layers"]
+        m.angle_nmax, m.angle_rcut, m.angle_rcut_smth = d["na"], d["rca"], d["rsa"]
+    else:
+        m.family = FAMILY_ATTENTION
+        m.e1, m.e2, m.m1, m.m2 = d["e1"], d["e2"], d["m1"], d["m2"]
+        m.n_layers, m.hidden, m.heads = d["n_layers"], d["hidden"], d["heads"]
+    return m
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libdp.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libdp.so is not built ({LIB_PATH}); run "
+                              "`python -m paper_2602_02234_b300.build`")
+        L = C.CDLL(LIB_PATH)
+        vp, i, d = C.c_void_p, C.c_int, C.c_double
+        L.dp_weight_count.argtypes = [C.POINTER(ModelDesc), C.POINTER(C.c_size_t)]
+        L.dp_init.argtypes = [C.POINTER(vp), C.POINTER(ModelDesc), i, vp, vp, vp, vp, C.c_size_t, vp]
+        L.dp_compute.argtypes = [vp, vp, vp, vp, vp, i]
+        L.dp_step.argtypes = [vp, i, d, vp, vp, vp, i]
+        L.dp_get_state.argtypes = [vp, vp, vp, C.POINTER(C.c_longlong), i]
+        L.dp_set_state.argtypes = [vp, vp, vp, C.c_longlong, i]
+        L.dp_get_neighbours.argtypes = [vp, vp, vp, vp]
+        L.dp_get_atom_energies.argtypes = [vp, vp]
+        L.dp_enqueue_network.argtypes = [vp, i]
+        L.dp_kernels_per_step.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.dp_device_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
+        L.dp_free.argtypes = [vp]
+        L.dp_free.restype = None
+        L.dp_last_error.argtypes = [vp]
+        L.dp_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def weight_count(desc: ModelDesc) -> int:
+    n = C.c_size_t()
+    rc = lib().dp_weight_count(C.byref(desc), C.byref(n))
+    if rc:
+        raise DPError(rc, lib().dp_last_error(None).decode())
+    return int(n.value)
+
+
+def _ptr(a):
+    """(address, kind) of a numpy array or a torch tensor."""
+    if a is None:
+        return None, PTR_HOST
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data, PTR_HOST
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            return a.data_ptr(), (PTR_DEVICE if a.is_cuda else PTR_HOST)
+    except ImportError:  # pragma: no cover
+        pass
+    raise TypeError(type(a))
+
+
+class DeepPotential:
+    """One system (``dp_ctx``): species, box and weights are fixed at creation."""
+
+    def __init__(self, desc: ModelDesc, types, box, weights, masses=None, stream=None):
+        self.desc = desc
+        self.types = np.ascontiguousarray(types, dtype=np.int32)
+        self.box = np.ascontiguousarray(box, dtype=np.float64)
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        self.n = len(self.types)
+        m = None if masses is None else np.ascontiguousarray(masses, dtype=np.float64)
+        h = C.c_void_p()
+        st = None
+        if stream is not None:
+            st = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        rc = lib().dp_init(C.byref(h), C.byref(desc), self.n, self.types.ctypes.data,
+                           None if m is None else m.ctypes.data, self.box.ctypes.data,
+                           w.ctypes.data, len(w), st)
+        if rc:
+            raise DPError(rc, lib().dp_last_error(None).decode())
+        self._h = h
+
+    def _check(self, rc):
+        if rc:
+            raise DPError(rc, lib().dp_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dp_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --------------------------------------------------------------- compute
+    def compute(self, coords, forces=None, virial=None):
+        """E (float) and, into the given buffers, forces (N x 3) and virial (3 x 3).
+
+        numpy arguments are host memory; CUDA tensors are device memory (all
+        arguments of one call must be of the same kind).  Returns (E, F, V).
+        """
+        xp, kind = _ptr(coords)
+        if kind == PTR_HOST:
+            coords = np.ascontiguousarray(coords, dtype=np.float64)
+            xp = coords.ctypes.data
+            if forces is None:
+                forces = np.zeros((self.n, 3))
+            if virial is None:
+                virial = np.zeros((3, 3))
+            e = np.zeros(1)
+            self._check(lib().dp_compute(self._h, xp, e.ctypes.data, forces.ctypes.data,
+                                         virial.ctypes.data, PTR_HOST))
+            return float(e[0]), forces, virial
+        import torch
+        dev = coords.device
+        if forces is None:
+            forces = torch.empty((self.n, 3), dtype=torch.float64, device=dev)
+        if virial is None:
+            virial = torch.empty((3, 3), dtype=torch.float64, device=dev)
+        e = torch.empty(1, dtype=torch.float64, device=dev)
+        self._check(lib().dp_compute(self._h, xp, e.data_ptr(), forces.data_ptr(),
+                                     virial.data_ptr(), PTR_DEVICE))
+        return e, forces, virial
+
+    def step(self, n_steps, dt_fs, coords=None, vel=None, energies=False):
+        """``n_steps`` of velocity Verlet.  coords/vel (numpy, updated in place)
+        are uploaded first when given; otherwise the resident state is used.
+        Returns the per-step (E_pot, E_kin) array when ``energies``."""
+        tr = np.zeros((max(n_steps, 1), 2)) if energies else None
+        if coords is not None:
+            assert coords.dtype == np.float64 and coords.flags["C_CONTIGUOUS"]
+        if vel is not None:
+            assert vel.dtype == np.float64 and vel.flags["C_CONTIGUOUS"]
+        self._check(lib().dp_step(self._h, int(n_steps), float(dt_fs),
+                                  None if coords is None else coords.ctypes.data,
+                                  None if vel is None else vel.ctypes.data,
+                                  None if tr is None else tr.ctypes.data, PTR_HOST))
+        return tr[:n_steps] if energies else None
+
+    def get_state(self):
+        x = np.zeros((self.n, 3))
+        v = np.zeros((self.n, 3))
+        s = C.c_longlong()
+        self._check(lib().dp_get_state(self._h, x.ctypes.data, v.ctypes.data, C.byref(s), PTR_HOST))
+        return x, v, int(s.value)
+
+    def set_state(self, coords, vel, step=0):
+        x = np.ascontiguousarray(coords, dtype=np.float64)
+        v = np.ascontiguousarray(vel, dtype=np.float64)
+        self._check(lib().dp_set_state(self._h, x.ctypes.data, v.ctypes.data, int(step), PTR_HOST))
+
+    # --------------------------------------------------------------- inspection
+    def neighbours(self):
+        nm = self.desc.nmax
+        j = np.zeros((self.n, nm), np.int32)
+        img = np.zeros((self.n, nm, 3), np.int32)
+        cnt = np.zeros(self.n, np.int32)
+        self._check(lib().dp_get_neighbours(self._h, j.ctypes.data, img.ctypes.data, cnt.ctypes.data))
+        return cnt, j, img
+
+    def atom_energies(self):
+        e = np.zeros(self.n)
+        self._check(lib().dp_get_atom_energies(self._h, e.ctypes.data))
+        return e
+
+    def enqueue_network(self, reps=1):
+        """Enqueue the network kernels alone ``reps`` times (no sync)."""
+        self._check(lib().dp_enqueue_network(self._h, int(reps)))
+
+    def kernels_per_step(self):
+        a, b = C.c_int(), C.c_int()
+        self._check(lib().dp_kernels_per_step(self._h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def device_bytes(self):
+        b = C.c_size_t()
+        self._check(lib().dp_device_bytes(self._h, C.byref(b)))
+        return int(b.value)
+
+
+def _dpenergy_class():
+    import torch
+
+    class DPEnergy(torch.autograd.Function):
+        """E(x) through dp_compute; backward gives dE/dx = -F from the library's
+        hand-written adjoint kernels (no autograd tape inside)."""
+
+        @staticmethod
+        def forward(ctx, coords, pot):
+            e, f, _ = pot.compute(coords.detach().contiguous())
+            if isinstance(e, float):
+                e = torch.tensor(e, dtype=torch.float64)
+                f = torch.as_tensor(f)
+            ctx.save_for_backward(f)
+            return e.reshape(())
+
+        @staticmethod
+        def backward(ctx, grad):
+            (f,) = ctx.saved_tensors
+            return -grad * f.to(grad.device), None
+
+    return DPEnergy
+
+
+def __getattr__(name):
+    if name == "DPEnergy":
+        cls = _dpenergy_class()
+        globals()["DPEnergy"] = cls
+        return cls
+    raise AttributeError(name)

@@ -1,0 +1,132 @@
+// Shared device-side definitions of libdp (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/dp.h"
+
+namespace dp {
+
+// ---------------------------------------------------------------------------
+// Device-side status word bits (written by kernels, read by the host after a
+// launch).  Kernels never trap: they record the problem and return.
+// ---------------------------------------------------------------------------
+enum : int {
+  kFlagRebuild = 1 << 0,   // neighbour skin lists must be rebuilt
+  kFlagOverflow = 1 << 1,  // a skin list exceeded its capacity
+  kFlagMirror = 1 << 2,    // a skin entry had no mirror entry (internal error)
+  kFlagTimeout = 1 << 3,   // a bounded device-side wait gave up
+  kFlagNonFinite = 1 << 4  // non-finite energy or force
+};
+
+// One periodic system of a batch.  Atoms [atom0, atom0 + natom) belong to it.
+struct SysInfo {
+  double L[3];     // box lengths
+  double cs[3];    // cell edge per direction (cells >= rc + skin)
+  int atom0, natom;
+  int cell0;       // first cell of this system in the batch's cell arrays
+  int nc[3];       // cells per direction (>= 3 when use_cells)
+  int use_cells;   // 0: brute force over atoms and images (boxes < 3 cells)
+  int nimg[3];     // image range for brute force
+  int pad;
+};
+
+// One entry of a skin (Verlet) list: neighbour atom j and its image m relative
+// to UNWRAPPED positions: r_ij = x_j - x_i + m * L (constant while atoms move).
+struct SkinEntry {
+  int j, mx, my, mz;
+};
+
+// ---------------------------------------------------------------------------
+// Exact FP64 helpers: no contraction into FMA, so distances that decide
+// neighbour membership and order are the plain IEEE products and sums.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double wrap_coord(double x, double L, double* f_out) {
+  double f = floor(__ddiv_rn(x, L));
+  *f_out = f;
+  return __dsub_rn(x, __dmul_rn(L, f));
+}
+
+// r = (w_j - w_i) + n * L per component, d2 = (x*x + y*y) + z*z
+__device__ __forceinline__ double sep_exact(const double* wi, const double* wj, const int* n,
+                                            const double* L, double* r) {
+  for (int a = 0; a < 3; ++a) {
+    double t = __dsub_rn(wj[a], wi[a]);
+    double u = __dmul_rn((double)n[a], L[a]);
+    r[a] = __dadd_rn(t, u);
+  }
+  return __dadd_rn(__dadd_rn(__dmul_rn(r[0], r[0]), __dmul_rn(r[1], r[1])), __dmul_rn(r[2], r[2]));
+}
+
+// Neighbour order: (d2, j, n) lexicographic.
+__device__ __forceinline__ bool key_less(double da, int ja, const int* na, double db, int jb,
+                                         const int* nb) {
+  if (da != db) return da < db;
+  if (ja != jb) return ja < jb;
+  for (int a = 0; a < 3; ++a)
+    if (na[a] != nb[a]) return na[a] < nb[a];
+  return false;
+}
+
+// Smooth switch sw(r) and d sw/dr (quintic smoothstep between rs and rc).
+template <typename T>
+__device__ __forceinline__ void smooth_switch(T r, T rs, T rc, T* sw, T* dsw) {
+  if (r < rs) {
+    *sw = T(1);
+    *dsw = T(0);
+  } else if (r < rc) {
+    T inv = T(1) / (rc - rs);
+    T u = (r - rs) * inv;
+    T u2 = u * u;
+    *sw = u2 * u * (T(-6) * u2 + T(15) * u - T(10)) + T(1);
+    T um1 = u - T(1);
+    *dsw = T(-30) * u2 * um1 * um1 * inv;
+  } else {
+    *sw = T(0);
+    *dsw = T(0);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T dtanh(T x);
+template <>
+__device__ __forceinline__ float dtanh<float>(float x) { return tanhf(x); }
+template <>
+__device__ __forceinline__ double dtanh<double>(double x) { return tanh(x); }
+
+template <typename T>
+__device__ __forceinline__ T dsqrt(T x);
+template <>
+__device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
+template <>
+__device__ __forceinline__ double dsqrt<double>(double x) { return sqrt(x); }
+
+template <typename T>
+__device__ __forceinline__ T dexp(T x);
+template <>
+__device__ __forceinline__ float dexp<float>(float x) { return expf(x); }
+template <>
+__device__ __forceinline__ double dexp<double>(double x) { return exp(x); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace dp

@@ -1,0 +1,97 @@
+// Launch interfaces between the runtime (ctx.cu) and the kernel files.
+#pragma once
+
+#include "common.cuh"
+
+namespace dp {
+
+// ----------------------------------------------------------------- neighbours
+struct NlistArgs {
+  int n;                 // atoms in the batch
+  int ncell;             // cells in the batch
+  int cap;               // skin-list capacity per atom
+  int nmax;
+  double rc, rskin;      // cutoff and cutoff + skin
+  const double* x;       // unwrapped positions (n x 3)
+  double* xref;          // positions at the last rebuild
+  double* w;             // wrapped positions
+  int* fl;               // floor(x / L) per component
+  const int* sys_of;
+  const SysInfo* sys;
+  int *cell_of, *cell_cnt, *cell_fill, *cell_start, *cell_idx;
+  SkinEntry* skin;
+  int* skin_cnt;
+  int* mirror;           // n x cap
+  int* sel_j;            // n x nmax
+  int* sel_img;          // n x nmax x 3
+  double* sel_r;         // n x nmax x 3
+  short* selpos;         // n x cap
+  int* n_in_rc;          // n
+  int* flags;
+};
+
+void launch_wrap(const NlistArgs& a, cudaStream_t st);
+void launch_nlist_rebuild(const NlistArgs& a, cudaStream_t st);
+void launch_select(const NlistArgs& a, cudaStream_t st);
+void launch_flag_set(int* flags, int bits, cudaStream_t st);
+int nlist_rebuild_kernels();
+int select_max_cap();   // largest skin capacity the selection kernel supports
+cudaError_t nlist_configure();
+
+// ----------------------------------------------------------------- forces, MD
+struct ForceArgs {
+  int n, nmax, cap;
+  const int* sel_j;
+  const double* sel_r;
+  const SkinEntry* skin;
+  const int* skin_cnt;
+  const int* mirror;
+  const short* selpos;
+  const float* g32;      // pair gradients dE/dr (n x nmax x 3), FP32 paths
+  const double* g64;     // or FP64
+  double* F;             // n x 3
+  double* atom_vir;      // n x 9
+};
+void launch_force_gather(const ForceArgs& a, cudaStream_t st);
+
+struct ReduceArgs {
+  int n_sys;
+  const int* sys_atom0;  // n_sys + 1 offsets
+  const double* atom_e;  // n
+  const double* atom_vir;// n x 9
+  const double* F;       // n x 3 (finiteness check)
+  double* sys_e;         // n_sys
+  double* sys_vir;       // n_sys x 9
+  int* flags;
+};
+void launch_reduce(const ReduceArgs& a, cudaStream_t st);
+
+struct MdArgs {
+  int n;
+  double dt;
+  double* x;
+  double* v;
+  const double* F;
+  const double* minv;    // kappa / m per atom
+  const double* mass;    // m per atom
+  const double* xref;
+  double half_skin2;     // (skin / 2)^2
+  int rebuild_every;
+  long long* step;       // device step counter
+  int* flags;
+  double* sys_ekin;      // n_sys
+  int n_sys;
+  const int* sys_atom0;
+  const int* sys_of;
+};
+void launch_kick_drift(const MdArgs& a, cudaStream_t st);
+void launch_kick_final(const MdArgs& a, cudaStream_t st);
+void launch_record(const MdArgs& a, const double* sys_e, double* trace, int trace_len, cudaStream_t st);
+
+// ----------------------------------------------------------------- plain model
+struct AfDims {
+  int n_species, e1, e2, m1, m2, n_layers, hidden, heads, f1, f2, f3, nmax;
+  double rc, rs;
+};
+
+}  // namespace dp

@@ -1,0 +1,177 @@
+// Forces from pair gradients, FP64 energy/virial reductions and the
+// velocity-Verlet integrator (paper Sec. II: MD integrates Newton's equations
+// with a Verlet-type scheme; forces are -dE/dx).
+//
+// F_i = sum_p g_ip - sum_{(k,p'): slot p' of k is atom i} g_kp', with
+// g = dE/dr_ij for r_ij = x_j - x_i.  The second sum is gathered, not
+// scattered: each skin entry (i -> j) knows the index of its mirror entry
+// (j -> i) in j's skin list, and selpos says which kept slot that is, so every
+// force is summed in a fixed order with no atomics (bitwise reproducible).
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace dp {
+
+template <typename G>
+__global__ void k_force_gather(int n, int nmax, int cap, const int* __restrict__ sel_j,
+                               const double* __restrict__ sel_r, const SkinEntry* __restrict__ skin,
+                               const int* __restrict__ skin_cnt, const int* __restrict__ mirror,
+                               const short* __restrict__ selpos, const G* __restrict__ g,
+                               double* __restrict__ F, double* __restrict__ atom_vir) {
+  int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  double f[3] = {0, 0, 0};
+  double vir[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int p = lane; p < nmax; p += 32) {
+    size_t o = (size_t)i * nmax + p;
+    if (sel_j[o] < 0) continue;
+    double gg[3] = {(double)g[3 * o], (double)g[3 * o + 1], (double)g[3 * o + 2]};
+    double r[3] = {sel_r[3 * o], sel_r[3 * o + 1], sel_r[3 * o + 2]};
+    for (int a = 0; a < 3; ++a) {
+      f[a] += gg[a];
+      for (int b = 0; b < 3; ++b) vir[3 * a + b] -= r[a] * gg[b];
+    }
+  }
+  int cnt = skin_cnt[i];
+  for (int c = lane; c < cnt; c += 32) {
+    size_t o = (size_t)i * cap + c;
+    int mc = mirror[o];
+    if (mc < 0) continue;
+    int j = skin[o].j;
+    int p = selpos[(size_t)j * cap + mc];
+    if (p < 0) continue;
+    size_t q = (size_t)j * nmax + p;
+    for (int a = 0; a < 3; ++a) f[a] -= (double)g[3 * q + a];
+  }
+  for (int a = 0; a < 3; ++a) f[a] = warp_sum(f[a]);
+  for (int a = 0; a < 9; ++a) vir[a] = warp_sum(vir[a]);
+  if (lane == 0) {
+    for (int a = 0; a < 3; ++a) F[3 * i + a] = f[a];
+    for (int a = 0; a < 9; ++a) atom_vir[9 * i + a] = vir[a];
+  }
+}
+
+void launch_force_gather(const ForceArgs& a, cudaStream_t st) {
+  int blocks = ceil_div((long long)a.n * 32, 256);
+  if (a.g64)
+    k_force_gather<double><<<blocks, 256, 0, st>>>(a.n, a.nmax, a.cap, a.sel_j, a.sel_r, a.skin,
+                                                   a.skin_cnt, a.mirror, a.selpos, a.g64, a.F,
+                                                   a.atom_vir);
+  else
+    k_force_gather<float><<<blocks, 256, 0, st>>>(a.n, a.nmax, a.cap, a.sel_j, a.sel_r, a.skin,
+                                                  a.skin_cnt, a.mirror, a.selpos, a.g32, a.F,
+                                                  a.atom_vir);
+}
+
+// one block per system: E and virial in FP64, fixed summation order
+__global__ void k_reduce(const int* __restrict__ sys_atom0, const double* __restrict__ atom_e,
+                         const double* __restrict__ atom_vir, const double* __restrict__ F,
+                         double* __restrict__ sys_e, double* __restrict__ sys_vir,
+                         int* __restrict__ flags) {
+  int s = blockIdx.x;
+  int a0 = sys_atom0[s], a1 = sys_atom0[s + 1];
+  __shared__ double sh[10][256];
+  double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  bool bad = false;
+  for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
+    acc[0] += atom_e[i];
+    for (int q = 0; q < 9; ++q) acc[1 + q] += atom_vir[9 * i + q];
+    for (int q = 0; q < 3; ++q) bad |= !isfinite(F[3 * i + q]);
+    bad |= !isfinite(atom_e[i]);
+  }
+  if (bad) atomicOr(flags, kFlagNonFinite);
+  for (int q = 0; q < 10; ++q) sh[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int q = 0; q < 10; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    sys_e[s] = sh[0][0];
+    for (int q = 0; q < 9; ++q) sys_vir[9 * s + q] = sh[1 + q][0];
+  }
+}
+
+void launch_reduce(const ReduceArgs& a, cudaStream_t st) {
+  k_reduce<<<a.n_sys, 256, 0, st>>>(a.sys_atom0, a.atom_e, a.atom_vir, a.F, a.sys_e, a.sys_vir,
+                                    a.flags);
+}
+
+// v += dt/2 F/m; x += dt v; request a neighbour rebuild when an atom moved
+// more than skin/2 since the last one, or every rebuild_every steps
+__global__ void k_kick_drift(int n, double dt, double* __restrict__ x, double* __restrict__ v,
+                             const double* __restrict__ F, const double* __restrict__ minv,
+                             const double* __restrict__ xref, double half_skin2,
+                             int rebuild_every, long long* __restrict__ step,
+                             int* __restrict__ flags) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    long long s = *step + 1;
+    *step = s;
+    if (rebuild_every > 0 && s % rebuild_every == 0) atomicOr(flags, kFlagRebuild);
+  }
+  if (i >= n) return;
+  double d2 = 0;
+  for (int a = 0; a < 3; ++a) {
+    double vv = v[3 * i + a] + 0.5 * dt * F[3 * i + a] * minv[i];
+    double xx = x[3 * i + a] + dt * vv;
+    v[3 * i + a] = vv;
+    x[3 * i + a] = xx;
+    double dx = xx - xref[3 * i + a];
+    d2 += dx * dx;
+  }
+  if (d2 > half_skin2) atomicOr(flags, kFlagRebuild);
+}
+
+__global__ void k_kick(int n, double dt, double* __restrict__ v, const double* __restrict__ F,
+                       const double* __restrict__ minv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int a = 0; a < 3; ++a) v[3 * i + a] += 0.5 * dt * F[3 * i + a] * minv[i];
+}
+
+void launch_kick_drift(const MdArgs& a, cudaStream_t st) {
+  k_kick_drift<<<ceil_div(a.n, 256), 256, 0, st>>>(a.n, a.dt, a.x, a.v, a.F, a.minv, a.xref,
+                                                   a.half_skin2, a.rebuild_every, a.step, a.flags);
+}
+
+void launch_kick_final(const MdArgs& a, cudaStream_t st) {
+  k_kick<<<ceil_div(a.n, 256), 256, 0, st>>>(a.n, a.dt, a.v, a.F, a.minv);
+}
+
+// per system: {E_pot, E_kin} of the step just finished into trace[step - base - 1]
+__global__ void k_record(const int* __restrict__ sys_atom0, const double* __restrict__ v,
+                         const double* __restrict__ mass, double inv_kappa,
+                         const double* __restrict__ sys_e, const long long* __restrict__ step,
+                         double* __restrict__ trace, int n_sys, int trace_len) {
+  int s = blockIdx.x;
+  int a0 = sys_atom0[s], a1 = sys_atom0[s + 1];
+  __shared__ double sh[256];
+  double acc = 0;
+  for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x)
+    for (int a = 0; a < 3; ++a) acc += 0.5 * mass[i] * v[3 * i + a] * v[3 * i + a];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    long long slot = step[0] - step[1] - 1;   // step[1] holds the base
+    if (slot >= 0 && slot < trace_len) {
+      trace[(slot * n_sys + s) * 2 + 0] = sys_e[s];
+      trace[(slot * n_sys + s) * 2 + 1] = sh[0] * inv_kappa;
+    }
+  }
+}
+
+void launch_record(const MdArgs& a, const double* sys_e, double* trace, int trace_len,
+                   cudaStream_t st) {
+  const double kappa = 1.602176634e-19 / (1.66053906660e-27 * 1e10);
+  k_record<<<a.n_sys, 256, 0, st>>>(a.sys_atom0, a.v, a.mass, 1.0 / kappa, sys_e, a.step, trace,
+                                    a.n_sys, trace_len);
+}
+
+}  // namespace dp

@@ -1,0 +1,190 @@
+"""GPU parity of the attention-family path against the FP64 oracle, through the C ABI.
+
+Tolerances (from the model's arithmetic; force RMS = RMS of the oracle's force
+components over the atoms compared):
+  plain FP64:  |dF| <= 1e-10 * F_rms, |dE| <= 1e-11 |E|   (rounding order only)
+  plain FP32:  |dF| <= 1e-4 * F_rms                          (FP32 throughout)
+  fused BF16:  |dF| <= 2e-2 * F_rms                          (BF16 GEMM operands)
+Integer work (neighbour indices and images) is compared exactly.
+"""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2602_02234_b300 as dp
+from synth import configs as C, maxwell_boltzmann, normal_blob, serving_system, water_box
+
+pytestmark = pytest.mark.gpu
+
+TOL_F = {dp.PREC_PLAIN_F64: 1e-10, dp.PREC_PLAIN_F32: 1e-4, dp.PREC_FUSED_BF16: 2e-2}
+TOL_E = {dp.PREC_PLAIN_F64: 1e-11, dp.PREC_PLAIN_F32: 2e-5, dp.PREC_FUSED_BF16: 5e-3}
+
+
+def weights(model, seed=C.WEIGHT_SEED):
+    return normal_blob(oracle.af_weight_count(model), seed)
+
+
+def make(model, system, prec, w=None, masses=None):
+    w = weights(model) if w is None else w
+    return dp.DeepPotential(dp.model_desc(model, prec), system.types, system.box, w,
+                            masses=masses), w
+
+
+def frms(F):
+    return float(np.sqrt(np.mean(F ** 2)))
+
+
+# ------------------------------------------------------------------ neighbours
+@pytest.mark.parametrize("name", ["water64", "water96_small_box", "protein24k"])
+def test_neighbour_lists_exact(name):
+    if name == "water64":
+        s, m = C.water64(), C.WATER64_MODEL
+    elif name == "water96_small_box":
+        s, m = serving_system(96, 5), C.ATTN_MODEL
+    else:
+        s, m = C.protein24k(), C.ATTN_MODEL
+    pot, w = make(m, s, dp.PREC_PLAIN_F32)
+    pot.compute(s.coords)
+    cnt, nj, img = pot.neighbours()
+    ocnt, onj, oimg, _ = oracle.neighbours(s.coords, s.box, m.rc, m.nmax)
+    assert np.array_equal(cnt, ocnt)
+    assert np.array_equal(nj, onj)
+    assert np.array_equal(img, oimg)
+
+
+# ------------------------------------------------------------------ energies / forces
+@pytest.mark.parametrize("prec", [dp.PREC_PLAIN_F64, dp.PREC_PLAIN_F32])
+def test_water64_energy_forces_virial(prec):
+    m, s = C.WATER64_MODEL, C.water64()
+    pot, w = make(m, s, prec)
+    E, F, V = pot.compute(s.coords)
+    Eo, aeo, Fo, Vo = oracle.af_compute(m, w, s.types, s.coords, s.box)
+    fr = frms(Fo)
+    assert abs(E - Eo) <= TOL_E[prec] * abs(Eo)
+    assert np.max(np.abs(F - Fo)) <= TOL_F[prec] * fr
+    assert np.max(np.abs(V - Vo)) <= TOL_F[prec] * np.linalg.norm(Vo)
+    ae = pot.atom_energies()
+    assert np.max(np.abs(ae - aeo)) <= 10 * TOL_E[prec] * np.max(np.abs(aeo)) + 1e-14
+
+
+@pytest.mark.parametrize("case", ["water96_small_box", "isolated_atom", "dimer", "water_tiny_box"])
+def test_edge_cases_fp64(case):
+    m = replace(C.ATTN_MODEL, n_layers=2, nmax=64)
+    if case == "water96_small_box":
+        s = serving_system(96, 7)
+    elif case == "isolated_atom":
+        s = water_box(1, 30.0, 1)
+        s.coords, s.types = s.coords[:1], s.types[:1]
+    elif case == "dimer":
+        s = water_box(1, 30.0, 1)
+        s.coords = np.array([[1.0, 1.0, 1.0], [29.5, 2.0, 1.5]])   # across the boundary
+        s.types = np.array([3, 0], dtype=np.int32)
+    else:
+        s = water_box(2, 5.5, 3, min_oo=2.0)      # box < rc: own images are neighbours
+        s.types = np.where(s.types == 0, 3, 0).astype(np.int32)
+    pot, w = make(m, s, dp.PREC_PLAIN_F64)
+    E, F, V = pot.compute(s.coords)
+    Eo, _, Fo, Vo = oracle.af_compute(m, w, s.types, s.coords, s.box)
+    assert E == pytest.approx(Eo, rel=1e-11, abs=1e-12)
+    scale = max(frms(Fo), 1e-12)
+    assert np.max(np.abs(F - Fo)) <= 1e-9 * scale + 1e-14
+
+
+def _sampled_parity(prec, sample_seed=3, n_sample=8):
+    m, s = C.ATTN_MODEL, C.protein24k()
+    pot, w = make(m, s, prec)
+    E, F, V = pot.compute(s.coords)
+    rng = np.random.default_rng(sample_seed)
+    # include blob (protein) atoms and the most crowded atom (truncated list)
+    cnt = oracle.neighbours(s.coords, s.box, m.rc, 1)[0]
+    sample = np.unique(np.concatenate([rng.choice(s.n, n_sample - 2, replace=False),
+                                       [rng.integers(0, s.blob_atoms), int(np.argmax(cnt))]]))
+    Fo = oracle.af_forces_subset(m, w, s.types, s.coords, s.box, sample)
+    ae_o = oracle.af_atoms(m, w, s.types, s.coords, s.box, sample)["atom_e"]
+    ae = pot.atom_energies()[sample]
+    return F[sample], Fo, ae, ae_o, E
+
+
+@pytest.mark.parametrize("prec", [dp.PREC_PLAIN_F32])
+def test_protein24k_sampled_parity(prec):
+    F, Fo, ae, ae_o, E = _sampled_parity(prec)
+    assert np.isfinite(E)
+    assert np.max(np.abs(F - Fo)) <= TOL_F[prec] * frms(Fo)
+    assert np.max(np.abs(ae - ae_o)) <= 10 * TOL_E[prec] * np.max(np.abs(ae_o))
+
+
+def test_zero_net_force_and_symmetric_virial_full_size():
+    m, s = C.ATTN_MODEL, C.protein24k()
+    pot, _ = make(m, s, dp.PREC_PLAIN_F32)
+    E, F, V = pot.compute(s.coords)
+    assert np.max(np.abs(F.sum(0))) <= 1e-4 * frms(F) * np.sqrt(s.n)
+    assert np.max(np.abs(V - V.T)) <= 1e-4 * np.linalg.norm(V)
+
+
+# ------------------------------------------------------------------ MD
+def test_md_matches_oracle_fp64():
+    m, s = C.WATER64_MODEL, C.water64()
+    masses = s.masses
+    v0 = maxwell_boltzmann(masses[s.types], 300.0, C.VELOCITY_SEED)
+    pot, w = make(m, s, dp.PREC_PLAIN_F64, masses=masses)
+    x = s.coords.copy()
+    v = v0.copy()
+    tr = pot.step(40, C.DT_FS, coords=x, vel=v, energies=True)
+    xo, vo, ep, ek = oracle.af_md(m, w, s.types, masses, s.coords, v0, s.box, 40, C.DT_FS)
+    assert np.max(np.abs(x - xo)) < 1e-9
+    assert np.max(np.abs(v - vo)) < 1e-11
+    assert np.max(np.abs(tr[:, 0] - ep)) < 1e-9 * abs(ep[0])
+    assert np.max(np.abs(tr[:, 1] - ek)) < 1e-9 * abs(ek[0])
+
+
+def test_md_resident_state_resume_is_bitwise():
+    m, s = C.WATER64_MODEL, C.water64()
+    masses = s.masses
+    v0 = maxwell_boltzmann(masses[s.types], 300.0, C.VELOCITY_SEED)
+    pot, w = make(m, s, dp.PREC_PLAIN_F32, masses=masses)
+    pot.set_state(s.coords, v0, 0)
+    pot.step(25, C.DT_FS)
+    xa, va, step_a = pot.get_state()
+    pot.step(25, C.DT_FS)
+    xb, vb, step_b = pot.get_state()
+    assert (step_a, step_b) == (25, 50)
+    pot2, _ = make(m, s, dp.PREC_PLAIN_F32, w=w, masses=masses)
+    pot2.set_state(xa, va, step_a)
+    pot2.step(25, C.DT_FS)
+    xc, vc, step_c = pot2.get_state()
+    assert step_c == 50
+    assert np.array_equal(xb, xc) and np.array_equal(vb, vc)
+
+
+def test_dpenergy_autograd_matches_finite_differences():
+    import torch
+    m = replace(C.ATTN_MODEL, n_layers=1, nmax=64)
+    s = serving_system(96, 11)
+    pot, w = make(m, s, dp.PREC_PLAIN_F64)
+    x = torch.tensor(s.coords, dtype=torch.float64, device="cuda", requires_grad=True)
+    E = dp.DPEnergy.apply(x, pot)
+    E.backward()
+    g = x.grad.cpu().numpy()
+    h = 1e-4
+    for i, a in [(0, 0), (17, 1), (50, 2)]:
+        xp = s.coords.copy(); xp[i, a] += h
+        xm = s.coords.copy(); xm[i, a] -= h
+        fd = (pot.compute(xp)[0] - pot.compute(xm)[0]) / (2 * h)
+        assert g[i, a] == pytest.approx(fd, abs=1e-8 * max(1.0, abs(fd)))
+
+
+def test_errors_are_reported_not_raised_on_device():
+    m, s = C.WATER64_MODEL, C.water64()
+    pot, _ = make(m, s, dp.PREC_PLAIN_F32)
+    with pytest.raises(dp.DPError) as e:
+        pot.step(1, 0.5)                  # no masses given at init
+    assert e.value.code == dp.DP_ERR_ARG
+    bad = s.coords.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(dp.DPError):
+        pot.compute(bad)
+    # the context stays usable
+    E, F, V = pot.compute(s.coords)
+    assert np.isfinite(E)
