@@ -166,6 +166,31 @@ int dp_device_bytes(dp_ctx* ctx, size_t* bytes);
 
 void dp_free(dp_ctx* ctx);
 
+/* Neighbour lists of one small periodic system without any device allocation.
+ * The paper has no counterpart: it is for callers that cannot allocate device
+ * memory (an MD engine that owns the allocator or has spent its memory budget,
+ * or a plugin that only receives pointers to the engine's buffers).  The
+ * lists are the ones dp_get_neighbours reports after dp_compute: every image
+ * (j, n) with 0 < |r| < rcut, nearest first by (|r|^2, j, n), the first nmax.
+ *   coords  [n_atoms x 3]        device pointer, A
+ *   box     [3]                  host pointer, A (orthorhombic)
+ *   nbr_j   [n_atoms x nmax]     device pointer, -1 = empty slot
+ *   nbr_img [n_atoms x nmax x 3] device pointer
+ *   n_in_rc [n_atoms]            device pointer, neighbours within rcut
+ *   cuda_stream                  stream to run on (NULL: legacy default stream)
+ * Limits: n_atoms <= 1024 and at most 384 neighbours within rcut per atom
+ * (DP_ERR_ARG / DP_ERR_NLIST_OVERFLOW beyond).  Its scratch memory is a static
+ * array of the library (about 6.3 MB on every GPU that loads it, held until
+ * the process exits), shared by all calls: calls that overlap on the GPU race
+ * and must be serialised by the caller.  The first call on a device looks up
+ * the array's device address; make that first call before any stream capture.
+ * The call synchronises the stream to read its status.  Errors: message from
+ * dp_noalloc_last_error(). */
+int dp_neighbour_list_noalloc(const double* coords, int n_atoms, const double* box, double rcut,
+                              int nmax, int32_t* nbr_j, int32_t* nbr_img, int32_t* n_in_rc,
+                              void* cuda_stream);
+const char* dp_noalloc_last_error(void);
+
 /* Message of the last error on ctx (or of the last failed dp_init when ctx is
  * NULL).  Valid until the next call on the same context. */
 const char* dp_last_error(const dp_ctx* ctx);

@@ -107,6 +107,9 @@ def lib():
         L.dp_enqueue_network.argtypes = [vp, i]
         L.dp_kernels_per_step.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.dp_device_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
+        L.dp_neighbour_list_noalloc.argtypes = [vp, i, vp, d, i, vp, vp, vp, vp]
+        L.dp_noalloc_last_error.argtypes = []
+        L.dp_noalloc_last_error.restype = C.c_char_p
         L.dp_free.argtypes = [vp]
         L.dp_free.restype = None
         L.dp_last_error.argtypes = [vp]
@@ -258,6 +261,27 @@ class DeepPotential:
         b = C.c_size_t()
         self._check(lib().dp_device_bytes(self._h, C.byref(b)))
         return int(b.value)
+
+
+def neighbour_list_noalloc(coords, box, rcut, nmax, stream=None):
+    """``dp_neighbour_list_noalloc``: neighbour lists of one small system
+    (<= 1024 atoms) with no device allocation by the library.  ``coords`` is a
+    CUDA float64 tensor (N x 3); the output tensors are allocated here by torch
+    (the caller's side).  Returns (n_in_rc, nbr_j, nbr_img) as CUDA tensors."""
+    import torch
+    assert coords.is_cuda and coords.dtype == torch.float64 and coords.is_contiguous()
+    n = coords.shape[0]
+    dev = coords.device
+    j = torch.empty((n, nmax), dtype=torch.int32, device=dev)
+    img = torch.empty((n, nmax, 3), dtype=torch.int32, device=dev)
+    cnt = torch.empty((n,), dtype=torch.int32, device=dev)
+    b = np.ascontiguousarray(box, dtype=np.float64)
+    st = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    rc = lib().dp_neighbour_list_noalloc(coords.data_ptr(), n, b.ctypes.data, float(rcut),
+                                         int(nmax), j.data_ptr(), img.data_ptr(), cnt.data_ptr(), st)
+    if rc:
+        raise DPError(rc, lib().dp_noalloc_last_error().decode())
+    return cnt, j, img
 
 
 def _dpenergy_class():
