@@ -166,6 +166,18 @@ int dp_device_bytes(dp_ctx* ctx, size_t* bytes);
 
 void dp_free(dp_ctx* ctx);
 
+/* Diagnostics (no paper counterpart): one 128 x n x k BF16 tensor-core product
+ * D = A B^T on the device (tcgen05.mma, FP32 accumulation in tensor memory),
+ * with A (128 x k) and B (n x k) staged in shared memory in K-major (a_mn /
+ * b_mn = 0) or MN-major (1) core-matrix layout; swap = 0 uses the descriptor
+ * stride convention of the library's fused kernels, 1 the other assignment.
+ * Host pointers, row-major FP32 (rounded to BF16 on the device).  16 <= n <=
+ * 256 and 16 <= k <= 128, multiples of 16.  Allocates its own buffers.
+ * Returns DP_ERR_ARG for sizes it cannot stage safely, DP_ERR_TIMEOUT if the
+ * product never completed (bounded wait). */
+int dp_selftest_mma(int n, int k, int a_mn, int b_mn, int swap, const float* A, const float* B,
+                    float* D);
+
 /* Neighbour lists of one small periodic system without any device allocation.
  * The paper has no counterpart: it is for callers that cannot allocate device
  * memory (an MD engine that owns the allocator or has spent its memory budget,

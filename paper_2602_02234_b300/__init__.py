@@ -110,6 +110,7 @@ def lib():
         L.dp_neighbour_list_noalloc.argtypes = [vp, i, vp, d, i, vp, vp, vp, vp]
         L.dp_noalloc_last_error.argtypes = []
         L.dp_noalloc_last_error.restype = C.c_char_p
+        L.dp_selftest_mma.argtypes = [i, i, i, i, i, vp, vp, vp]
         L.dp_free.argtypes = [vp]
         L.dp_free.restype = None
         L.dp_last_error.argtypes = [vp]
@@ -282,6 +283,19 @@ def neighbour_list_noalloc(coords, box, rcut, nmax, stream=None):
     if rc:
         raise DPError(rc, lib().dp_noalloc_last_error().decode())
     return cnt, j, img
+
+
+def selftest_mma(A, B, a_mn=0, b_mn=0, swap=0):
+    """``dp_selftest_mma``: D = A B^T (A 128 x k, B n x k) on the tensor cores."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    B = np.ascontiguousarray(B, dtype=np.float32)
+    n, k = B.shape
+    assert A.shape == (128, k)
+    D = np.zeros((128, n), np.float32)
+    rc = lib().dp_selftest_mma(n, k, a_mn, b_mn, swap, A.ctypes.data, B.ctypes.data, D.ctypes.data)
+    if rc:
+        raise DPError(rc, "selftest_mma")
+    return D
 
 
 def _dpenergy_class():
