@@ -239,4 +239,54 @@ def af_md(model, weights, types, masses, coords, vel, box, n_steps, dt, nthreads
     return x, v, ep[:n_steps], ek[:n_steps]
 
 
+# --------------------------------------------------------------------------
+# graph family
+# --------------------------------------------------------------------------
+GF_KINDS = {"Wt": 0, "we": 1, "be0": 2, "Wm": 10, "Wn": 11, "bn": 12, "Wa": 13, "Wb": 14,
+            "Wc": 15, "be": 16, "Wp": 17, "Wphi": 18, "Wq": 19, "bq": 20, "F1": 30, "c1": 31,
+            "F2": 32, "c2": 33, "F3": 34, "c3": 35, "F4": 36, "c4": 37}
+
+
+def gf_weight_count(model) -> int:
+    i, f = _gf_dims(model)
+    n = lib().oracle_gf_weight_count(_p(i, _I), _p(f, _D))
+    if n < 0:
+        raise ValueError("invalid graph-family model")
+    return int(n)
+
+
+def gf_weight_slice(model, kind: str, a: int = 0) -> slice:
+    i, f = _gf_dims(model)
+    off = lib().oracle_gf_weight_offset(_p(i, _I), _p(f, _D), GF_KINDS[kind], a)
+    if off < 0:
+        raise ValueError((kind, a))
+    d = model if isinstance(model, dict) else model.as_dict()
+    Nd, Ed = d["node"], d["edge"]
+    sizes = {"Wt": d["n_species"] * Nd, "we": Ed, "be0": Ed, "Wm": Nd * Ed, "Wn": (Nd + Ed) * Nd,
+             "bn": Nd, "Wa": Nd * Ed, "Wb": Nd * Ed, "Wc": Ed * Ed, "be": Ed, "Wp": Ed * Ed,
+             "Wphi": 4 * Ed, "Wq": Ed * Ed, "bq": Ed, "F1": Nd * d["f1"], "c1": d["f1"],
+             "F2": d["f1"] * d["f2"], "c2": d["f2"], "F3": d["f2"] * d["f3"], "c3": d["f3"],
+             "F4": d["f3"], "c4": 1}
+    return slice(int(off), int(off) + sizes[kind])
+
+
+def gf_compute(model, weights, types, coords, box, nthreads=0):
+    """(E, atomic energies, forces N x 3, virial 3 x 3) of the graph family, FP64."""
+    i, f = _gf_dims(model)
+    w, t, x, b = _c64(weights), _c32(types), _c64(coords), _c64(box)
+    if len(w) != gf_weight_count(model):
+        raise ValueError("weight blob has the wrong length")
+    n = len(t)
+    E = np.zeros(1)
+    ae = np.zeros(n)
+    F = np.zeros((n, 3))
+    V = np.zeros((3, 3))
+    rc = lib().oracle_gf_compute(_p(i, _I), _p(f, _D), _p(w, _D), n, _p(t, _I), _p(x, _D),
+                                 _p(b, _D), int(nthreads), _p(E, _D), _p(ae, _D), _p(F, _D),
+                                 _p(V, _D))
+    if rc:
+        raise RuntimeError("oracle_gf_compute failed")
+    return float(E[0]), ae, F, V
+
+
 KAPPA = 1.602176634e-19 / (1.66053906660e-27 * 1e10)
