@@ -103,8 +103,9 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ algorithmic work
 def af_flops_per_atom(model, n):
-    """FLOPs of energy + input-gradient backward for one atom with n real neighbours
-    (padding and recomputation excluded)."""
+    """Algorithmic FLOPs for one atom with n real neighbours, split as
+    (forward network, fitting forward + input gradient, backward network);
+    padding to 128 rows and the backward's recomputation are excluded."""
     d = model.as_dict()
     e1, e2, m1, m2, H, L = d["e1"], d["e2"], d["m1"], d["m2"], d["hidden"], d["n_layers"]
     emb = 2 * n * (e1 + e1 * e2 + e2 * m1)
@@ -112,11 +113,15 @@ def af_flops_per_atom(model, n):
     att_bwd = 2 * n * m1 * H + 8 * n * n * H + 2 * n * 3 * H * m1
     desc = 2 * 4 * n * m1 + 2 * 4 * m1 * m2
     fit = 2 * (m1 * m2 * d["f1"] + d["f1"] * d["f2"] + d["f2"] * d["f3"] + d["f3"])
-    return 2 * emb + L * (att_fwd + att_bwd) + 3 * desc + 2 * fit
+    return (emb + L * att_fwd + desc, 2 * fit, emb + L * att_bwd + 2 * desc)
 
 
-def setup_system():
-    s = CF.protein24k()
+def setup_system(which="protein24k"):
+    if which == "small":   # profiling case: same recipe, 4,800 atoms (300-atom blob)
+        from synth import cached, protein_in_water
+        s = cached(protein_in_water, 4800, 300, (33.74, 33.74, 42.17), CF.SYSTEM_SEED + 1)
+    else:
+        s = CF.protein24k()
     model = CF.ATTN_MODEL
     masses = s.masses
     v0 = maxwell_boltzmann(masses[s.types], 300.0, CF.VELOCITY_SEED)
@@ -185,7 +190,7 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
 
-    s, model, masses, v0 = setup_system()
+    s, model, masses, v0 = setup_system(args.system)
     w = normal_blob(dp.weight_count(dp.model_desc(model, dp.PREC_PLAIN_F32)), CF.WEIGHT_SEED)
     stream = torch.cuda.Stream()
 
@@ -197,12 +202,13 @@ def run_ours(args, rank, world, local_rank):
     forms = []
     if args.form in ("auto", "fused"):
         try:
-            forms.append(("fused_bf16", make(dp.PREC_FUSED_BF16)))
+            forms.append(("fused_f16", make(dp.PREC_FUSED)))
         except dp.DPError as e:
             if args.form == "fused":
                 raise
             print(f"# fused form unavailable: {e}", file=sys.stderr)
-    forms.append(("plain_f32", make(dp.PREC_PLAIN_F32)))
+    if args.form in ("auto", "plain"):
+        forms.append(("plain_f32", make(dp.PREC_PLAIN_F32)))
 
     def barrier():
         if dist:
@@ -240,34 +246,48 @@ def run_ours(args, rank, world, local_rank):
     K = args.steps
     value = s.n * K * world / (main["ms"] / 1e3)
 
-    # network phase alone: the dominant kernels, timed with events on their stream
+    # the dominant kernel alone, timed with events on the stream it runs on
     cnt, _, _ = pot.neighbours()
     nreal = np.minimum(cnt, model.nmax)
-    flops = float(sum(af_flops_per_atom(model, int(k)) for k in nreal))
+    parts = np.array([af_flops_per_atom(model, int(k)) for k in nreal]).sum(0)
     reps = 5
-    pot.enqueue_network(1)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
-        e0.record(stream)
-        pot.enqueue_network(reps)
-        e1.record(stream)
-    e1.synchronize()
-    net_ms = e0.elapsed_time(e1) / reps
+
+    def time_network(part_mask):
+        pot.enqueue_network(1, part_mask)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            pot.enqueue_network(reps, part_mask)
+            e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
     pk, pk_kind = peaks()
-    if main_name == "fused_bf16":
+    if main_name == "fused_f16":
+        kernel_ms = {name: time_network(mask) for name, mask in
+                     (("k_af_fwd", 1), ("k_fit", 2), ("k_af_bwd", 4))}
+        dominant = max(kernel_ms, key=kernel_ms.get)
+        flops = float(parts[{"k_af_fwd": 0, "k_fit": 1, "k_af_bwd": 2}[dominant]])
+        net_ms = kernel_ms[dominant]
         peak = pk.get("bf16_tflops_sustained", 1400.0)
-        bound, peak_note = "tensor", f"bf16 dense sustained ({pk_kind})"
+        bound = "tensor"
+        peak_note = (f"dense 16-bit tensor peak sustained ({pk_kind}; the FP16 rate equals the "
+                     "measured BF16 rate, nominal ratio 1)")
+        kernel_name = dominant
     else:
+        net_ms = time_network(0)
+        kernel_ms = {"network": net_ms}
+        flops = float(parts.sum())
         peak = FP32_ALU_PEAK_TFLOPS
         bound, peak_note = "alu", "FP32 FFMA: 148 SMs x 128 lanes x 2 x 2.032 GHz (derived)"
+        kernel_name = "plain network phase (all kernels of one evaluation)"
     achieved = flops / (net_ms / 1e3) / 1e12
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "kernel": f"{main_name} network phase (all network kernels of one evaluation)",
+                "frac": achieved / peak, "traffic": None, "kernel": kernel_name,
                 "peak_kind": peak_note, "algorithmic_flop_per_launch": flops,
-                "launch_ms": net_ms}
+                "launch_ms": net_ms, "kernel_ms": kernel_ms}
 
     # end to end through the C ABI with pinned host buffers, copies every step
     xh = torch.empty((s.n, 3), dtype=torch.float64, pin_memory=True).numpy()
@@ -293,8 +313,9 @@ def run_ours(args, rank, world, local_rank):
     line = {"metric": METRIC, "value": value, "unit": "atom-steps/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": main["ms"] / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16" if main_name == "fused_bf16" else "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_atoms": s.n, "form": main_name,
+            "dtype": "f16" if main_name == "fused_f16" else "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD if args.system == "protein24k" else
+                       f"small profiling case ({s.n} atoms)", "n_atoms": s.n, "form": main_name,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2: skin/selection lists and pair gradients "
                              "(~0.4 GB per step) exceed the 126 MB L2"},
@@ -303,9 +324,9 @@ def run_ours(args, rank, world, local_rank):
     for name in results:
         line[name] = {"value": s.n * K * world / (results[name]["ms"] / 1e3),
                       "ms_per_step": results[name]["ms"] / K}
-    if "fused_bf16" in results and "plain_f32" in results:
-        line["fused_vs_plain"] = results["plain_f32"]["ms"] / results["fused_bf16"]["ms"]
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if "fused_f16" in results and "plain_f32" in results:
+        line["fused_vs_plain"] = results["plain_f32"]["ms"] / results["fused_f16"]["ms"]
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.system == "protein24k":
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -326,6 +347,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=48)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--system", choices=["protein24k", "small"], default="protein24k",
+                    help="small: 4,800-atom box of the same recipe, for profiler captures")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)       # timing rule: at least 3 untimed warm-up steps
     rank = int(os.environ.get("RANK", 0))

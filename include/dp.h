@@ -58,12 +58,15 @@ enum {
 enum { DP_FAMILY_ATTENTION = 0, DP_FAMILY_GRAPH = 1 };
 
 /* Arithmetic of the network:
- *   PLAIN_F64  -- unfused kernels, everything in FP64 (small systems, parity);
- *   PLAIN_F32  -- unfused kernels, one simple kernel per operation, FP32;
- *   FUSED_BF16 -- fused persistent kernels: BF16 tensor-core GEMMs with FP32
- *                 accumulation, FP32 switch/softmax/LayerNorm, FP64 energy,
- *                 virial and integration. */
-enum { DP_PREC_PLAIN_F64 = 0, DP_PREC_PLAIN_F32 = 1, DP_PREC_FUSED_BF16 = 2 };
+ *   PLAIN_F64 -- unfused kernels, everything in FP64 (small systems, parity);
+ *   PLAIN_F32 -- unfused kernels, one simple kernel per operation, FP32;
+ *   FUSED     -- three persistent kernels per evaluation: every matrix product
+ *                on the tensor cores (tcgen05) with 16-bit operands (FP16; BF16
+ *                when the library is built with DP_FUSED_BF16) and FP32
+ *                accumulation, FP32 switch/softmax/LayerNorm, FP64 energy,
+ *                virial and integration.  Needs m1 = hidden = 128 with 4 heads, nmax <=
+ *                128 (DP_ERR_UNSUPPORTED otherwise). */
+enum { DP_PREC_PLAIN_F64 = 0, DP_PREC_PLAIN_F32 = 1, DP_PREC_FUSED = 2 };
 
 enum { DP_PTR_HOST = 0, DP_PTR_DEVICE = 1 };
 
@@ -101,8 +104,11 @@ typedef struct dp_ctx dp_ctx;
  *   per species t:  W1[1][e1] b1[e1] W2[e1][e2] b2[e2] W3[e2][m1] b3[m1]
  *   per layer l:    Wq[m1][H] Wk[m1][H] Wv[m1][H] Wo[H][m1] bo[m1]
  *   per species t:  F1[m1*m2][f1] c1[f1] F2[f1][f2] c2[f2] F3[f2][f3] c3[f3] F4[f3][1] c4[1]
- * Graph family: see the graph-family section of the library documentation
- * (per species fitting at the end, same order rule).
+ * Graph family (Nd = node_dim, Ed = edge_dim), in order:
+ *   W_type[S][Nd] w_e[1][Ed] b_e[Ed]
+ *   per layer l:    Wm[Nd][Ed] Wn[Nd+Ed][Nd] bn[Nd] Wa[Nd][Ed] Wb[Nd][Ed] Wc[Ed][Ed]
+ *                   be[Ed] Wp[Ed][Ed] Wphi[4][Ed] Wq[Ed][Ed] bq[Ed]
+ *   per species t:  F1[Nd][f1] c1 F2[f1][f2] c2 F3[f2][f3] c3 F4[f3][1] c4[1]
  * Errors: DP_ERR_ARG for an invalid description. */
 int dp_weight_count(const dp_model_desc* desc, size_t* n);
 
@@ -155,8 +161,11 @@ int dp_get_atom_energies(dp_ctx* ctx, double* atom_e);
 /* Enqueue `reps` evaluations of the network alone (no neighbour update, no
  * force assembly) on the context's stream, at the resident neighbour lists,
  * without synchronising; for timing the network kernels with events on that
- * stream.  Needs a prior dp_compute or dp_step. */
-int dp_enqueue_network(dp_ctx* ctx, int reps);
+ * stream.  parts: bit mask of the network's kernels to run (0 = all; for the
+ * fused path bit 0 = per-atom forward, bit 1 = fitting, bit 2 = per-atom
+ * backward; a part reuses the intermediate results of the last evaluation).
+ * Needs a prior dp_compute or dp_step. */
+int dp_enqueue_network(dp_ctx* ctx, int reps, int parts);
 
 /* Number of kernels one dp_compute / one dp_step launches (for reporting). */
 int dp_kernels_per_step(dp_ctx* ctx, int* n_compute, int* n_step);
@@ -165,6 +174,44 @@ int dp_kernels_per_step(dp_ctx* ctx, int* n_compute, int* n_step);
 int dp_device_bytes(dp_ctx* ctx, size_t* bytes);
 
 void dp_free(dp_ctx* ctx);
+
+/* ---------------------------------------------------------------- serving
+ * Continuous batching of many independent systems on one GPU (the memory
+ * limits the paper reports for DPA models, Sec. V-C, become the admission
+ * rule).  Requests (a system and a number of MD steps) are queued; every tick
+ * admits queued requests first-in first-out while a slot is free and their
+ * atoms fit the memory-sized capacity, then advances every resident system by
+ * one velocity-Verlet step in one CUDA-graph launch over the packed batch.
+ * A request leaves at the end of its last step.  Per-atom work does not depend
+ * on the batch, so a system's trajectory is the same alone and in any mix.
+ * Fused attention-family model only (DP_ERR_UNSUPPORTED otherwise). */
+typedef struct dp_server dp_server;
+
+/* max_slots: resident systems at most; max_atoms (0: no limit) and
+ * mem_budget_bytes (0: 80 % of free device memory) bound the packed atoms;
+ * masses [n_species] amu; dt_fs for every request. */
+int dp_server_create(dp_server** out, const dp_model_desc* desc, const double* masses,
+                     const double* weights, size_t n_weights, int max_slots, long long max_atoms,
+                     size_t mem_budget_bytes, double dt_fs, void* cuda_stream);
+/* Atoms and slots the server can hold at once. */
+int dp_server_capacity(dp_server* srv, int* max_atoms, int* max_slots);
+/* Queue a request (host arrays, copied): species [n], box [3], coords and
+ * velocities [n x 3].  DP_ERR_OOM if the system alone exceeds the capacity. */
+int dp_server_submit(dp_server* srv, int n_atoms, const int32_t* types, const double* box,
+                     const double* coords, const double* vel, int n_steps, uint64_t* req_id);
+/* Admit, repack if needed, advance every resident system one step. */
+int dp_server_tick(dp_server* srv, int* n_active, int* n_queued);
+/* state: 0 queued, 1 running, 2 done.  When done: final coords/velocities
+ * [n x 3], per-step {E_pot, E_kin} [2 x n_steps] (each nullable) and
+ * latency_ms[4] = {submit->done ms, submit->admit ms, tick admitted, tick done}. */
+int dp_server_poll(dp_server* srv, uint64_t req_id, int* state, double* coords, double* vel,
+                   double* energies, double* latency_ms);
+/* out[0..9] = ticks, p50 tick ms, p99 tick ms, atom-steps, busy ms, max resident
+ * systems, max resident atoms, ticks the queue head waited for memory, ticks it
+ * waited for a slot, atom capacity. */
+int dp_server_stats(dp_server* srv, double* out, int n_out);
+void dp_server_free(dp_server* srv);
+const char* dp_server_last_error(const dp_server* srv);
 
 /* Diagnostics (no paper counterpart): one 128 x n x k BF16 tensor-core product
  * D = A B^T on the device (tcgen05.mma, FP32 accumulation in tensor memory),

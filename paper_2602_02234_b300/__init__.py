@@ -29,7 +29,7 @@ LIB_PATH = os.path.join(HERE, "libdp.so")
 DP_OK, DP_ERR_ARG, DP_ERR_OOM, DP_ERR_NLIST_OVERFLOW, DP_ERR_TIMEOUT = 0, -1, -2, -3, -4
 DP_ERR_NONFINITE, DP_ERR_CUDA, DP_ERR_UNSUPPORTED = -5, -6, -7
 FAMILY_ATTENTION, FAMILY_GRAPH = 0, 1
-PREC_PLAIN_F64, PREC_PLAIN_F32, PREC_FUSED_BF16 = 0, 1, 2
+PREC_PLAIN_F64, PREC_PLAIN_F32, PREC_FUSED = 0, 1, 2
 PTR_HOST, PTR_DEVICE = 0, 1
 
 _ERRNAMES = {DP_ERR_ARG: "DP_ERR_ARG", DP_ERR_OOM: "DP_ERR_OOM",
@@ -104,13 +104,24 @@ def lib():
         L.dp_set_state.argtypes = [vp, vp, vp, C.c_longlong, i]
         L.dp_get_neighbours.argtypes = [vp, vp, vp, vp]
         L.dp_get_atom_energies.argtypes = [vp, vp]
-        L.dp_enqueue_network.argtypes = [vp, i]
+        L.dp_enqueue_network.argtypes = [vp, i, i]
         L.dp_kernels_per_step.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.dp_device_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
         L.dp_neighbour_list_noalloc.argtypes = [vp, i, vp, d, i, vp, vp, vp, vp]
         L.dp_noalloc_last_error.argtypes = []
         L.dp_noalloc_last_error.restype = C.c_char_p
         L.dp_selftest_mma.argtypes = [i, i, i, i, i, vp, vp, vp]
+        L.dp_server_create.argtypes = [C.POINTER(vp), C.POINTER(ModelDesc), vp, vp, C.c_size_t, i,
+                                       C.c_longlong, C.c_size_t, d, vp]
+        L.dp_server_capacity.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.dp_server_submit.argtypes = [vp, i, vp, vp, vp, vp, i, C.POINTER(C.c_uint64)]
+        L.dp_server_tick.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.dp_server_poll.argtypes = [vp, C.c_uint64, C.POINTER(C.c_int), vp, vp, vp, vp]
+        L.dp_server_stats.argtypes = [vp, vp, i]
+        L.dp_server_free.argtypes = [vp]
+        L.dp_server_free.restype = None
+        L.dp_server_last_error.argtypes = [vp]
+        L.dp_server_last_error.restype = C.c_char_p
         L.dp_free.argtypes = [vp]
         L.dp_free.restype = None
         L.dp_last_error.argtypes = [vp]
@@ -249,9 +260,10 @@ class DeepPotential:
         self._check(lib().dp_get_atom_energies(self._h, e.ctypes.data))
         return e
 
-    def enqueue_network(self, reps=1):
-        """Enqueue the network kernels alone ``reps`` times (no sync)."""
-        self._check(lib().dp_enqueue_network(self._h, int(reps)))
+    def enqueue_network(self, reps=1, parts=0):
+        """Enqueue the network kernels alone ``reps`` times (no sync); ``parts``
+        selects kernels (0 = all; fused: 1 forward, 2 fitting, 4 backward)."""
+        self._check(lib().dp_enqueue_network(self._h, int(reps), int(parts)))
 
     def kernels_per_step(self):
         a, b = C.c_int(), C.c_int()
@@ -262,6 +274,82 @@ class DeepPotential:
         b = C.c_size_t()
         self._check(lib().dp_device_bytes(self._h, C.byref(b)))
         return int(b.value)
+
+
+class Server:
+    """``dp_server``: continuous batching of independent systems (fused model)."""
+
+    STATS = ("ticks", "p50_tick_ms", "p99_tick_ms", "atom_steps", "busy_ms", "max_resident",
+             "max_resident_atoms", "waits_for_memory", "waits_for_slot", "atom_capacity")
+
+    def __init__(self, desc, weights, masses, max_slots=64, max_atoms=0, mem_budget=0,
+                 dt_fs=0.5, stream=None):
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        m = np.ascontiguousarray(masses, dtype=np.float64)
+        h = C.c_void_p()
+        st = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        rc = lib().dp_server_create(C.byref(h), C.byref(desc), m.ctypes.data, w.ctypes.data, len(w),
+                                    int(max_slots), int(max_atoms), int(mem_budget), float(dt_fs), st)
+        if rc:
+            raise DPError(rc, lib().dp_server_last_error(None).decode())
+        self._h = h
+        self.sizes = {}
+
+    def _check(self, rc):
+        if rc:
+            raise DPError(rc, lib().dp_server_last_error(self._h).decode())
+
+    def capacity(self):
+        a, s = C.c_int(), C.c_int()
+        self._check(lib().dp_server_capacity(self._h, C.byref(a), C.byref(s)))
+        return a.value, s.value
+
+    def submit(self, types, box, coords, vel, n_steps):
+        t = np.ascontiguousarray(types, dtype=np.int32)
+        b = np.ascontiguousarray(box, dtype=np.float64)
+        x = np.ascontiguousarray(coords, dtype=np.float64)
+        v = np.ascontiguousarray(vel, dtype=np.float64)
+        rid = C.c_uint64()
+        self._check(lib().dp_server_submit(self._h, len(t), t.ctypes.data, b.ctypes.data,
+                                           x.ctypes.data, v.ctypes.data, int(n_steps), C.byref(rid)))
+        self.sizes[rid.value] = (len(t), int(n_steps))
+        return rid.value
+
+    def tick(self):
+        a, q = C.c_int(), C.c_int()
+        self._check(lib().dp_server_tick(self._h, C.byref(a), C.byref(q)))
+        return a.value, q.value
+
+    def poll(self, rid):
+        """None while queued or running; else (coords, vel, energies, latency)."""
+        n, steps = self.sizes[rid]
+        st = C.c_int()
+        x = np.zeros((n, 3))
+        v = np.zeros((n, 3))
+        e = np.zeros((steps, 2))
+        lat = np.zeros(4)
+        self._check(lib().dp_server_poll(self._h, C.c_uint64(rid), C.byref(st), x.ctypes.data,
+                                         v.ctypes.data, e.ctypes.data, lat.ctypes.data))
+        if st.value != 2:
+            return None
+        return x, v, e, {"total_ms": lat[0], "queue_ms": lat[1], "tick_admitted": int(lat[2]),
+                         "tick_done": int(lat[3])}
+
+    def stats(self):
+        out = np.zeros(len(self.STATS))
+        self._check(lib().dp_server_stats(self._h, out.ctypes.data, len(out)))
+        return dict(zip(self.STATS, out.tolist()))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dp_server_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def neighbour_list_noalloc(coords, box, rcut, nmax, stream=None):

@@ -12,6 +12,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <deque>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -30,7 +34,10 @@ struct dp_ctx {
   double rskin = 0, skin = 0;
   int rebuild_every = 10;
   int cap = 0;
-  int ncell = 0;
+  int ncell = 0, ncell_cap = 0;
+  int n_cap = 0, sys_cap = 1;
+  std::vector<double> boxes;
+  std::vector<void*> cell_allocs;
   cudaStream_t st = nullptr;
   bool own_stream = false;
   std::string err;
@@ -59,6 +66,7 @@ struct dp_ctx {
   long long* step = nullptr;   // [0] step counter, [1] trace base
   double* trace = nullptr;
   int trace_len = 0;
+  size_t trace_elems = 0;
   // skin-list buffers are reallocated when the capacity grows
   std::vector<void*> skin_allocs;
   // network
@@ -72,6 +80,8 @@ struct dp_ctx {
 };
 
 static thread_local std::string g_init_error;
+struct dp_server;
+extern "C" void dp_server_free(dp_server* s);
 
 static int fail(dp_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
@@ -117,16 +127,29 @@ static int check_desc(const dp_model_desc* d, std::string* why) {
     if (d->e1 < 1 || d->e2 < 1 || d->m1 < 1 || d->m2 < 1 || d->m2 > d->m1) { *why = "embedding sizes invalid (need m2 <= m1)"; return -1; }
     if (d->n_layers < 0 || d->n_layers > 16) { *why = "n_layers must be 0..16"; return -1; }
     if (d->n_layers > 0 && (d->heads < 1 || d->hidden < 1 || d->hidden % d->heads)) { *why = "hidden must be a multiple of heads"; return -1; }
+  } else {
+    if (d->node_dim < 1 || d->edge_dim < 1) { *why = "node_dim and edge_dim must be positive"; return -1; }
+    if (d->n_gnn_layers < 0 || d->n_gnn_layers > 16) { *why = "n_gnn_layers must be 0..16"; return -1; }
+    if (d->angle_nmax < 1 || d->angle_nmax > 64) { *why = "angle_nmax must be 1..64"; return -1; }
+    if (!(d->angle_rcut_smth >= 0) || !(d->angle_rcut_smth < d->angle_rcut) || d->angle_rcut > d->rcut) { *why = "need 0 <= angle_rcut_smth < angle_rcut <= rcut"; return -1; }
   }
-  if (d->precision < DP_PREC_PLAIN_F64 || d->precision > DP_PREC_FUSED_BF16) { *why = "unknown precision"; return -1; }
+  if (d->precision < DP_PREC_PLAIN_F64 || d->precision > DP_PREC_FUSED) { *why = "unknown precision"; return -1; }
   return 0;
+}
+
+static GfDims gf_dims(const dp_model_desc* d) {
+  return GfDims{d->n_species, d->node_dim, d->edge_dim, d->n_gnn_layers, d->f1, d->f2, d->f3,
+                d->nmax, d->angle_nmax, d->rcut, d->rcut_smth, d->angle_rcut, d->angle_rcut_smth};
 }
 
 extern "C" int dp_weight_count(const dp_model_desc* d, size_t* n) {
   std::string why;
   if (!n) return fail(nullptr, DP_ERR_ARG, "n is NULL");
   if (check_desc(d, &why)) return fail(nullptr, DP_ERR_ARG, why);
-  if (d->family == DP_FAMILY_GRAPH) return fail(nullptr, DP_ERR_UNSUPPORTED, "graph family not available in this build");
+  if (d->family == DP_FAMILY_GRAPH) {
+    *n = gf_weight_count(gf_dims(d));
+    return DP_OK;
+  }
   size_t S = d->n_species, E1 = d->e1, E2 = d->e2, M1 = d->m1, M2 = d->m2, H = d->hidden;
   size_t t = S * (E1 + E1 + E1 * E2 + E2 + E2 * M1 + M1);
   t += (size_t)d->n_layers * (3 * M1 * H + H * M1 + M1);
@@ -190,6 +213,10 @@ static NlistArgs nlist_args(dp_ctx* c) {
   return a;
 }
 
+static NbrView nbr_view(dp_ctx* c) {
+  return NbrView{c->sel_j, c->sel_r, c->skin_list, c->skin_cnt, c->mirror, c->selpos, c->cap};
+}
+
 static MdArgs md_args(dp_ctx* c, double dt) {
   MdArgs m{};
   m.n = c->n; m.dt = dt; m.x = c->x; m.v = c->v; m.F = c->F; m.minv = c->minv; m.mass = c->mass;
@@ -211,7 +238,7 @@ static int enqueue_compute(dp_ctx* c) {
   fa.n = c->n; fa.nmax = c->desc.nmax; fa.cap = c->cap; fa.sel_j = c->sel_j; fa.sel_r = c->sel_r;
   fa.skin = c->skin_list; fa.skin_cnt = c->skin_cnt; fa.mirror = c->mirror; fa.selpos = c->selpos;
   fa.F = c->F; fa.atom_vir = c->atom_vir;
-  k += c->model->run(c->sel_j, c->sel_r, c->types, c->atom_e, c->st);
+  k += c->model->run(nbr_view(c), c->types, c->atom_e, c->st);
   fa.g32 = c->model->grad32();
   fa.g64 = c->model->grad64();
   launch_force_gather(fa, c->st); ++k;
@@ -255,6 +282,7 @@ static int compute_now(dp_ctx* c) {
       continue;
     }
     if (fl & kFlagMirror) return fail(c, DP_ERR_CUDA, "internal error: neighbour mirror missing");
+    if (fl & kFlagTimeout) return fail(c, DP_ERR_TIMEOUT, "a device-side wait gave up");
     if (fl & kFlagNonFinite) return fail(c, DP_ERR_NONFINITE, "coordinates, energy or forces are not finite");
     c->forces_valid = true;
     return DP_OK;
@@ -277,47 +305,49 @@ static int copy_out(dp_ctx* c, double* dst, const double* src, size_t count, int
 }
 
 // ------------------------------------------------------------------ C ABI
-extern "C" int dp_init(dp_ctx** out, const dp_model_desc* desc, int n_atoms, const int32_t* types,
-                       const double* masses, const double* box, const double* weights,
-                       size_t n_weights, void* cuda_stream) {
-  if (!out) return fail(nullptr, DP_ERR_ARG, "out is NULL");
-  *out = nullptr;
+// Weight blob and model sizes check shared by every constructor.
+static int check_model(const dp_model_desc* desc, const double* weights, size_t n_weights,
+                       const double* masses, AfDims* afd) {
   std::string why;
   if (check_desc(desc, &why)) return fail(nullptr, DP_ERR_ARG, why);
-  if (n_atoms < 1) return fail(nullptr, DP_ERR_ARG, "n_atoms must be >= 1");
-  if (!types || !box || !weights) return fail(nullptr, DP_ERR_ARG, "types, box and weights are required");
+  if (!weights) return fail(nullptr, DP_ERR_ARG, "weights are required");
   size_t want = 0;
   dp_weight_count(desc, &want);
   if (n_weights != want)
     return fail(nullptr, DP_ERR_ARG, "weight blob has " + std::to_string(n_weights) + " values, model needs " + std::to_string(want));
-  for (int a = 0; a < 3; ++a)
-    if (!(box[a] > 0) || !isfinite(box[a])) return fail(nullptr, DP_ERR_ARG, "box lengths must be positive");
-  for (int i = 0; i < n_atoms; ++i)
-    if (types[i] < 0 || types[i] >= desc->n_species) return fail(nullptr, DP_ERR_ARG, "atom " + std::to_string(i) + " has a species outside 0..n_species-1");
   for (size_t q = 0; q < n_weights; ++q)
     if (!isfinite(weights[q])) return fail(nullptr, DP_ERR_ARG, "weights contain a non-finite value");
-  AfDims afd{desc->n_species, desc->e1, desc->e2, desc->m1, desc->m2, desc->n_layers,
-             desc->hidden, desc->heads, desc->f1, desc->f2, desc->f3, desc->nmax,
-             desc->rcut, desc->rcut_smth};
-  if (desc->family == DP_FAMILY_GRAPH)
-    return fail(nullptr, DP_ERR_UNSUPPORTED, "graph family not available in this build");
-  if (desc->precision == DP_PREC_FUSED_BF16 && !fused_af_supported(afd, &why))
+  if (masses)
+    for (int t = 0; t < desc->n_species; ++t)
+      if (!(masses[t] > 0)) return fail(nullptr, DP_ERR_ARG, "masses must be positive");
+  *afd = AfDims{desc->n_species, desc->e1, desc->e2, desc->m1, desc->m2, desc->n_layers,
+                desc->hidden, desc->heads, desc->f1, desc->f2, desc->f3, desc->nmax,
+                desc->rcut, desc->rcut_smth};
+  if (desc->family == DP_FAMILY_GRAPH && desc->precision == DP_PREC_FUSED)
+    return fail(nullptr, DP_ERR_UNSUPPORTED, "the graph family runs on the plain FP32/FP64 kernels only");
+  if (desc->family == DP_FAMILY_ATTENTION && desc->precision == DP_PREC_FUSED &&
+      !fused_af_supported(*afd, &why))
     return fail(nullptr, DP_ERR_UNSUPPORTED, why);
+  return DP_OK;
+}
 
+// A context with room for n_cap atoms in up to sys_cap systems.  The model is
+// built for model_types (n_cap atoms); skin lists start at `cap` per atom.
+static int ctx_create(dp_ctx** out, const dp_model_desc* desc, const double* masses,
+                      const double* weights, void* cuda_stream, int n_cap, int sys_cap,
+                      const int* model_types, int cap, const AfDims& afd) {
   dp_ctx* c = new dp_ctx();
   c->desc = *desc;
-  c->n = n_atoms;
+  c->n = n_cap;
+  c->n_cap = n_cap;
+  c->sys_cap = sys_cap;
   c->skin = desc->skin > 0 ? desc->skin : 1.0;
   c->rebuild_every = desc->rebuild_every > 0 ? desc->rebuild_every : 10;
   c->rskin = desc->rcut + c->skin;
-  for (int a = 0; a < 3; ++a) c->box[a] = box[a];
-  c->types_host.assign(types, types + n_atoms);
   c->af = afd;
   if (masses) {
     c->have_masses = true;
     c->mass_species.assign(masses, masses + desc->n_species);
-    for (double m : c->mass_species)
-      if (!(m > 0)) { delete c; return fail(nullptr, DP_ERR_ARG, "masses must be positive"); }
   }
   int rc = DP_OK;
   auto bail = [&](int code) {
@@ -329,7 +359,7 @@ extern "C" int dp_init(dp_ctx** out, const dp_model_desc* desc, int n_atoms, con
     c->st = (cudaStream_t)cuda_stream;
   } else {
     cudaError_t e = cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking);
-    if (e != cudaSuccess) { cuda_fail(c, e, "stream"); return bail(c->err.find("memory") != std::string::npos ? DP_ERR_OOM : DP_ERR_CUDA); }
+    if (e != cudaSuccess) { cuda_fail(c, e, "stream"); return bail(DP_ERR_CUDA); }
     c->own_stream = true;
   }
   static bool configured = false;
@@ -337,23 +367,8 @@ extern "C" int dp_init(dp_ctx** out, const dp_model_desc* desc, int n_atoms, con
     nlist_configure();
     configured = true;
   }
-  // systems: a single system here
-  SysInfo si;
-  make_sysinfo(box, c->rskin, 0, n_atoms, 0, &si, &c->ncell);
-  double rho = n_atoms / (box[0] * box[1] * box[2]);
-  double expect = 4.0 / 3.0 * M_PI * c->rskin * c->rskin * c->rskin * rho;
-  int cap = (int)std::min<double>((double)n_atoms * 27.0 + 32.0, 2.0 * expect + 32.0);
-  cap = std::max(64, ((cap + 31) / 32) * 32);
-  std::vector<int> sys_of(n_atoms, 0), atom0 = {0, n_atoms};
-  std::vector<double> minv(n_atoms, 0.0), mass(n_atoms, 0.0);
-  const double kappa = 1.602176634e-19 / (1.66053906660e-27 * 1e10);
-  if (c->have_masses)
-    for (int i = 0; i < n_atoms; ++i) {
-      mass[i] = c->mass_species[types[i]];
-      minv[i] = kappa / mass[i];
-    }
 #define TRY(expr, where) do { cudaError_t e__ = (expr); if (e__ != cudaSuccess) { rc = cuda_fail(c, e__, where); return bail(rc); } } while (0)
-  size_t N = n_atoms;
+  size_t N = n_cap, S = sys_cap;
   TRY(dalloc(c, &c->x, 3 * N), "x");
   TRY(dalloc(c, &c->v, 3 * N), "v");
   TRY(dalloc(c, &c->F, 3 * N), "F");
@@ -364,12 +379,9 @@ extern "C" int dp_init(dp_ctx** out, const dp_model_desc* desc, int n_atoms, con
   TRY(dalloc(c, &c->mass, N), "mass");
   TRY(dalloc(c, &c->types, N), "types");
   TRY(dalloc(c, &c->sys_of, N), "sys_of");
-  TRY(dalloc(c, &c->sys_atom0, 2), "sys_atom0");
-  TRY(dalloc(c, &c->sys, 1), "sys");
+  TRY(dalloc(c, &c->sys_atom0, S + 1), "sys_atom0");
+  TRY(dalloc(c, &c->sys, S), "sys");
   TRY(dalloc(c, &c->cell_of, N), "cells");
-  TRY(dalloc(c, &c->cell_cnt, c->ncell + 1), "cells");
-  TRY(dalloc(c, &c->cell_fill, c->ncell + 1), "cells");
-  TRY(dalloc(c, &c->cell_start, c->ncell + 1), "cells");
   TRY(dalloc(c, &c->cell_idx, N), "cells");
   TRY(dalloc(c, &c->skin_cnt, N), "skin");
   TRY(dalloc(c, &c->sel_j, N * desc->nmax), "sel");
@@ -378,27 +390,121 @@ extern "C" int dp_init(dp_ctx** out, const dp_model_desc* desc, int n_atoms, con
   TRY(dalloc(c, &c->n_in_rc, N), "sel");
   TRY(dalloc(c, &c->atom_e, N), "energies");
   TRY(dalloc(c, &c->atom_vir, 9 * N), "virials");
-  TRY(dalloc(c, &c->sys_e, 1), "energies");
-  TRY(dalloc(c, &c->sys_vir, 9), "virials");
+  TRY(dalloc(c, &c->sys_e, S), "energies");
+  TRY(dalloc(c, &c->sys_vir, 9 * S), "virials");
   TRY(dalloc(c, &c->flags, 1), "flags");
   TRY(dalloc(c, &c->step, 2), "step");
-  TRY(cudaMemcpyAsync(c->types, types, sizeof(int) * N, cudaMemcpyHostToDevice, c->st), "upload");
-  TRY(cudaMemcpyAsync(c->sys_of, sys_of.data(), sizeof(int) * N, cudaMemcpyHostToDevice, c->st), "upload");
-  TRY(cudaMemcpyAsync(c->sys_atom0, atom0.data(), sizeof(int) * 2, cudaMemcpyHostToDevice, c->st), "upload");
-  TRY(cudaMemcpyAsync(c->sys, &si, sizeof si, cudaMemcpyHostToDevice, c->st), "upload");
-  TRY(cudaMemcpyAsync(c->minv, minv.data(), sizeof(double) * N, cudaMemcpyHostToDevice, c->st), "upload");
-  TRY(cudaMemcpyAsync(c->mass, mass.data(), sizeof(double) * N, cudaMemcpyHostToDevice, c->st), "upload");
-  TRY(cudaStreamSynchronize(c->st), "upload");
 #undef TRY
   rc = alloc_skin(c, cap);
   if (rc) return bail(rc);
-  if (desc->precision == DP_PREC_FUSED_BF16)
-    c->model = make_fused_af(c->af, weights, n_atoms, types, &c->err);
+  if (desc->family == DP_FAMILY_GRAPH)
+    c->model = make_plain_gf(gf_dims(desc), desc->precision == DP_PREC_PLAIN_F64, weights, n_cap,
+                             model_types, &c->err);
+  else if (desc->precision == DP_PREC_FUSED)
+    c->model = make_fused_af(c->af, weights, n_cap, model_types, &c->err);
   else
-    c->model = make_plain_af(c->af, desc->precision == DP_PREC_PLAIN_F64, weights, n_atoms, types,
-                             0, &c->err);
+    c->model = make_plain_af(c->af, desc->precision == DP_PREC_PLAIN_F64, weights, n_cap,
+                             model_types, 0, &c->err);
   if (!c->model) return bail(c->err.find("memory") != std::string::npos ? DP_ERR_OOM : DP_ERR_CUDA);
   c->bytes += c->model->bytes();
+  c->model->bind_flags(c->flags);
+  *out = c;
+  return DP_OK;
+}
+
+// Pack n_sys systems (atom counts natoms[], boxes[3*s], species types[] of all
+// atoms in order) into the context; neighbour lists and forces become stale.
+static int ctx_set_systems(dp_ctx* c, int n_sys, const int* natoms, const double* boxes,
+                           const int* types) {
+  int n = 0;
+  for (int s = 0; s < n_sys; ++s) n += natoms[s];
+  if (n_sys < 1 || n_sys > c->sys_cap || n < 1 || n > c->n_cap)
+    return fail(c, DP_ERR_ARG, "batch exceeds the context's capacity");
+  std::vector<SysInfo> si(n_sys);
+  std::vector<int> sys_of(n), atom0(n_sys + 1, 0);
+  int ncell = 0;
+  for (int s = 0, a0 = 0; s < n_sys; ++s) {
+    int nc = 0;
+    make_sysinfo(boxes + 3 * s, c->rskin, a0, natoms[s], ncell, &si[s], &nc);
+    ncell += nc;
+    for (int i = 0; i < natoms[s]; ++i) sys_of[a0 + i] = s;
+    a0 += natoms[s];
+    atom0[s + 1] = a0;
+  }
+  if (ncell + 1 > c->ncell_cap) {
+    for (void* q : c->cell_allocs) cudaFree(q);
+    c->cell_allocs.clear();
+    int cap = std::max(ncell + 1, 2 * c->ncell_cap);
+    CUDA_TRY(c, dalloc(c, &c->cell_cnt, cap, &c->cell_allocs), "cells");
+    CUDA_TRY(c, dalloc(c, &c->cell_fill, cap, &c->cell_allocs), "cells");
+    CUDA_TRY(c, dalloc(c, &c->cell_start, cap, &c->cell_allocs), "cells");
+    c->ncell_cap = cap;
+  }
+  std::vector<double> minv(n, 0.0), mass(n, 0.0);
+  const double kappa = 1.602176634e-19 / (1.66053906660e-27 * 1e10);
+  if (c->have_masses)
+    for (int i = 0; i < n; ++i) {
+      mass[i] = c->mass_species[types[i]];
+      minv[i] = kappa / mass[i];
+    }
+  CUDA_TRY(c, cudaMemcpyAsync(c->types, types, sizeof(int) * n, cudaMemcpyHostToDevice, c->st), "upload");
+  CUDA_TRY(c, cudaMemcpyAsync(c->sys_of, sys_of.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->st), "upload");
+  CUDA_TRY(c, cudaMemcpyAsync(c->sys_atom0, atom0.data(), sizeof(int) * (n_sys + 1), cudaMemcpyHostToDevice, c->st), "upload");
+  CUDA_TRY(c, cudaMemcpyAsync(c->sys, si.data(), sizeof(SysInfo) * n_sys, cudaMemcpyHostToDevice, c->st), "upload");
+  CUDA_TRY(c, cudaMemcpyAsync(c->minv, minv.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->st), "upload");
+  CUDA_TRY(c, cudaMemcpyAsync(c->mass, mass.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->st), "upload");
+  CUDA_TRY(c, cudaStreamSynchronize(c->st), "upload");
+  bool same_types = c->n == n && c->types_host.size() == (size_t)n &&
+                    std::equal(types, types + n, c->types_host.begin());
+  if (!same_types && !c->model->set_atoms(n, types))
+    return fail(c, DP_ERR_UNSUPPORTED, "this model cannot change its atom set");
+  c->types_host.assign(types, types + n);
+  c->n = n;
+  c->n_sys = n_sys;
+  c->ncell = ncell;
+  c->boxes.assign(boxes, boxes + 3 * n_sys);
+  for (int a = 0; a < 3; ++a) c->box[a] = boxes[a];
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  c->forces_valid = false;
+  return DP_OK;
+}
+
+// skin-list capacity per atom from the number density
+static int skin_capacity(double rskin, double rho, int n_atoms) {
+  double expect = 4.0 / 3.0 * M_PI * rskin * rskin * rskin * rho;
+  int cap = (int)std::min<double>((double)n_atoms * 27.0 + 32.0, 2.0 * expect + 32.0);
+  return std::max(64, ((cap + 31) / 32) * 32);
+}
+
+extern "C" int dp_init(dp_ctx** out, const dp_model_desc* desc, int n_atoms, const int32_t* types,
+                       const double* masses, const double* box, const double* weights,
+                       size_t n_weights, void* cuda_stream) {
+  if (!out) return fail(nullptr, DP_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  AfDims afd{};
+  int rc = check_model(desc, weights, n_weights, masses, &afd);
+  if (rc) return rc;
+  if (n_atoms < 1) return fail(nullptr, DP_ERR_ARG, "n_atoms must be >= 1");
+  if (!types || !box) return fail(nullptr, DP_ERR_ARG, "types and box are required");
+  for (int a = 0; a < 3; ++a)
+    if (!(box[a] > 0) || !isfinite(box[a])) return fail(nullptr, DP_ERR_ARG, "box lengths must be positive");
+  for (int i = 0; i < n_atoms; ++i)
+    if (types[i] < 0 || types[i] >= desc->n_species) return fail(nullptr, DP_ERR_ARG, "atom " + std::to_string(i) + " has a species outside 0..n_species-1");
+  const double rskin = desc->rcut + (desc->skin > 0 ? desc->skin : 1.0);
+  int cap = skin_capacity(rskin, n_atoms / (box[0] * box[1] * box[2]), n_atoms);
+  dp_ctx* c = nullptr;
+  rc = ctx_create(&c, desc, masses, weights, cuda_stream, n_atoms, 1, types, cap, afd);
+  if (rc) return rc;
+  c->types_host.assign(types, types + n_atoms);
+  rc = ctx_set_systems(c, 1, &n_atoms, box, types);
+  if (rc) {
+    g_init_error = c->err;
+    dp_free(c);
+    return rc;
+  }
   *out = c;
   return DP_OK;
 }
@@ -427,12 +533,14 @@ static int build_step_graph(dp_ctx* c, double dt, int trace_len) {
     cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
   }
-  if (trace_len > c->trace_len) {
+  const size_t need = (size_t)2 * c->n_sys * trace_len;
+  if (need > c->trace_elems) {
     if (c->trace) cudaFree(c->trace);
     c->trace = nullptr;
-    CUDA_TRY(c, cudaMalloc(&c->trace, sizeof(double) * 2 * c->n_sys * trace_len), "trace");
-    c->trace_len = trace_len;
+    CUDA_TRY(c, cudaMalloc(&c->trace, sizeof(double) * need), "trace");
+    c->trace_elems = need;
   }
+  c->trace_len = trace_len;
   MdArgs m = md_args(c, dt);
   cudaGraph_t g;
   CUDA_TRY(c, cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal), "capture");
@@ -503,6 +611,7 @@ extern "C" int dp_step(dp_ctx* c, int n_steps, double dt_fs, double* coords_io, 
       continue;
     }
     if (fl & kFlagMirror) return fail(c, DP_ERR_CUDA, "internal error: neighbour mirror missing");
+    if (fl & kFlagTimeout) return fail(c, DP_ERR_TIMEOUT, "a device-side wait gave up");
     if (fl & kFlagNonFinite) return fail(c, DP_ERR_NONFINITE, "energy or forces are not finite");
     if (energies_out) {
       if (ptr_kind == DP_PTR_DEVICE)
@@ -568,11 +677,12 @@ extern "C" int dp_get_atom_energies(dp_ctx* c, double* atom_e) {
   return DP_OK;
 }
 
-extern "C" int dp_enqueue_network(dp_ctx* c, int reps) {
+extern "C" int dp_enqueue_network(dp_ctx* c, int reps, int parts) {
   if (!c) return fail(nullptr, DP_ERR_ARG, "ctx is NULL");
   if (reps < 0) return fail(c, DP_ERR_ARG, "reps must be >= 0");
   if (!c->forces_valid) return fail(c, DP_ERR_ARG, "no resident neighbour lists: call dp_compute first");
-  for (int r = 0; r < reps; ++r) c->model->run(c->sel_j, c->sel_r, c->types, c->atom_e, c->st);
+  for (int r = 0; r < reps; ++r)
+    c->model->run_parts(nbr_view(c), c->types, c->atom_e, c->st, parts ? parts : ~0);
   CUDA_TRY(c, cudaGetLastError(), "launch");
   return DP_OK;
 }
@@ -597,6 +707,7 @@ extern "C" void dp_free(dp_ctx* c) {
   if (c->trace) cudaFree(c->trace);
   delete c->model;
   for (void* p : c->skin_allocs) cudaFree(p);
+  for (void* p : c->cell_allocs) cudaFree(p);
   for (void* p : c->allocs) cudaFree(p);
   if (c->own_stream && c->st) cudaStreamDestroy(c->st);
   delete c;
@@ -605,4 +716,335 @@ extern "C" void dp_free(dp_ctx* c) {
 extern "C" const char* dp_last_error(const dp_ctx* c) {
   if (!c) return g_init_error.c_str();
   return c->err.c_str();
+}
+
+// ===================================================================== serving
+// Continuous batching of independent systems (paper Sec. V-C finds memory the
+// limiting resource for DPA models; here requests are admitted as slots and
+// device memory free up).  All resident systems advance together: one tick =
+// one velocity-Verlet step of every system in one CUDA-graph launch over the
+// packed batch.  Requests are admitted first-in first-out when a slot is free
+// and the atoms fit the memory-sized capacity; finished ones leave at the end
+// of their last tick, and the batch is repacked before the next one.
+
+struct ServerReq {
+  uint64_t id = 0;
+  int n = 0;
+  double box[3] = {0, 0, 0};
+  std::vector<int> types;
+  std::vector<double> x, v;
+  std::vector<double> trace;  // {E_pot, E_kin} per step
+  int steps_total = 0, steps_done = 0;
+  int state = 0;              // 0 queued, 1 running, 2 done
+  long long tick_submit = 0, tick_admit = -1, tick_done = -1;
+  double t_submit = 0, t_admit = 0, t_done = 0;
+  int offset = -1;            // first atom in the current batch
+};
+
+struct dp_server {
+  dp_ctx* ctx = nullptr;
+  double dt = 0.5;
+  int max_slots = 0;
+  int n_cap = 0;
+  uint64_t next_id = 1;
+  std::map<uint64_t, ServerReq> reqs;
+  std::deque<uint64_t> queue;
+  std::vector<uint64_t> active;       // batch order
+  bool dirty = false;
+  long long ticks = 0, atom_steps = 0;
+  int atoms_in_use = 0, max_active = 0, max_atoms_seen = 0;
+  long long waits_for_memory = 0, waits_for_slot = 0;
+  std::vector<double> tick_ms;
+  double busy_ms = 0;
+  double* stage_x = nullptr;
+  double* stage_v = nullptr;
+  std::string err;
+};
+
+static thread_local std::string g_server_error;
+
+static double now_ms() {
+  return std::chrono::duration<double, std::milli>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+// bytes of device memory one atom needs in a fused context (skin capacity cap)
+static size_t bytes_per_atom(const dp_model_desc* d, int cap) {
+  size_t nm = d->nmax, L = d->n_layers;
+  size_t ctx = 120 + 12 + 16 + 24 + 4 * nm + 12 * nm + 24 * nm + 8 + 72 + (size_t)cap * 22 + 48;
+  size_t model = (L + 1) * 32768 + L * 512 + 128 * (size_t)d->m2 * 6 + 2048 + 12 * nm + 8;
+  return ctx + model;
+}
+
+extern "C" int dp_server_create(dp_server** out, const dp_model_desc* desc, const double* masses,
+                                const double* weights, size_t n_weights, int max_slots,
+                                long long max_atoms, size_t mem_budget, double dt_fs,
+                                void* cuda_stream) {
+  if (!out) { g_server_error = "out is NULL"; return DP_ERR_ARG; }
+  *out = nullptr;
+  AfDims afd{};
+  int rc = check_model(desc, weights, n_weights, masses, &afd);
+  if (rc) { g_server_error = g_init_error; return rc; }
+  if (desc->family != DP_FAMILY_ATTENTION || desc->precision != DP_PREC_FUSED) {
+    g_server_error = "the server batches the fused attention-family model";
+    return DP_ERR_UNSUPPORTED;
+  }
+  if (!masses) { g_server_error = "masses are required"; return DP_ERR_ARG; }
+  if (max_slots < 1 || !(dt_fs > 0)) { g_server_error = "need max_slots >= 1 and dt > 0"; return DP_ERR_ARG; }
+  // capacity: atoms that fit the memory budget (default: 80 % of free memory)
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    g_server_error = "cudaMemGetInfo failed";
+    return DP_ERR_CUDA;
+  }
+  size_t budget = mem_budget ? mem_budget : (size_t)(0.8 * (double)free_b);
+  const double rskin = desc->rcut + (desc->skin > 0 ? desc->skin : 1.0);
+  int cap = skin_capacity(rskin, 0.1, 1 << 20);
+  size_t fixed = (size_t)256 << 20;  // weights, tiles and per-system tables
+  if (budget <= fixed) { g_server_error = "memory budget too small"; return DP_ERR_OOM; }
+  long long n_cap = (long long)((budget - fixed) / bytes_per_atom(desc, cap));
+  if (max_atoms > 0 && max_atoms < n_cap) n_cap = max_atoms;
+  if (n_cap < 1) { g_server_error = "memory budget too small"; return DP_ERR_OOM; }
+  if (n_cap > (1 << 30)) n_cap = 1 << 30;
+  std::vector<int> types0((size_t)n_cap, 0);
+  dp_ctx* c = nullptr;
+  rc = ctx_create(&c, desc, masses, weights, cuda_stream, (int)n_cap, max_slots, types0.data(), cap,
+                  afd);
+  if (rc) { g_server_error = g_init_error; return rc; }
+  dp_server* s = new dp_server();
+  s->ctx = c;
+  s->dt = dt_fs;
+  s->max_slots = max_slots;
+  s->n_cap = (int)n_cap;
+  if (cudaMalloc(&s->stage_x, sizeof(double) * 3 * n_cap) != cudaSuccess ||
+      cudaMalloc(&s->stage_v, sizeof(double) * 3 * n_cap) != cudaSuccess) {
+    g_server_error = "out of device memory for the staging buffers";
+    dp_server_free(s);
+    return DP_ERR_OOM;
+  }
+  *out = s;
+  return DP_OK;
+}
+
+extern "C" int dp_server_capacity(dp_server* s, int* max_atoms, int* max_slots) {
+  if (!s) return DP_ERR_ARG;
+  if (max_atoms) *max_atoms = s->n_cap;
+  if (max_slots) *max_slots = s->max_slots;
+  return DP_OK;
+}
+
+extern "C" int dp_server_submit(dp_server* s, int n_atoms, const int32_t* types,
+                                const double* box, const double* coords, const double* vel,
+                                int n_steps, uint64_t* req_id) {
+  if (!s || !types || !box || !coords || !vel || !req_id || n_steps < 1 || n_atoms < 1) {
+    if (s) s->err = "invalid argument";
+    return DP_ERR_ARG;
+  }
+  if (n_atoms > s->n_cap) {
+    s->err = "system larger than the server's memory capacity";
+    return DP_ERR_OOM;
+  }
+  for (int i = 0; i < n_atoms; ++i)
+    if (types[i] < 0 || types[i] >= s->ctx->desc.n_species) {
+      s->err = "species out of range";
+      return DP_ERR_ARG;
+    }
+  ServerReq r;
+  r.id = s->next_id++;
+  r.n = n_atoms;
+  for (int a = 0; a < 3; ++a) r.box[a] = box[a];
+  r.types.assign(types, types + n_atoms);
+  r.x.assign(coords, coords + 3 * (size_t)n_atoms);
+  r.v.assign(vel, vel + 3 * (size_t)n_atoms);
+  r.steps_total = n_steps;
+  r.tick_submit = s->ticks;
+  r.t_submit = now_ms();
+  *req_id = r.id;
+  s->queue.push_back(r.id);
+  s->reqs.emplace(r.id, std::move(r));
+  return DP_OK;
+}
+
+// Rebuild the packed batch from the active requests: retained systems keep
+// their device state (copied through the staging buffers), new ones are
+// uploaded from the host.
+static int server_repack(dp_server* s) {
+  dp_ctx* c = s->ctx;
+  std::vector<int> natoms, types;
+  std::vector<double> boxes;
+  int off = 0;
+  for (uint64_t id : s->active) {
+    ServerReq& r = s->reqs[id];
+    const size_t b = sizeof(double) * 3 * r.n;
+    if (r.offset >= 0) {
+      CUDA_TRY(c, cudaMemcpyAsync(s->stage_x + 3 * off, c->x + 3 * r.offset, b, cudaMemcpyDeviceToDevice, c->st), "repack");
+      CUDA_TRY(c, cudaMemcpyAsync(s->stage_v + 3 * off, c->v + 3 * r.offset, b, cudaMemcpyDeviceToDevice, c->st), "repack");
+    } else {
+      CUDA_TRY(c, cudaMemcpyAsync(s->stage_x + 3 * off, r.x.data(), b, cudaMemcpyHostToDevice, c->st), "repack");
+      CUDA_TRY(c, cudaMemcpyAsync(s->stage_v + 3 * off, r.v.data(), b, cudaMemcpyHostToDevice, c->st), "repack");
+    }
+    natoms.push_back(r.n);
+    boxes.insert(boxes.end(), r.box, r.box + 3);
+    types.insert(types.end(), r.types.begin(), r.types.end());
+    r.offset = off;
+    off += r.n;
+  }
+  s->atoms_in_use = off;
+  if (off == 0) {
+    s->dirty = false;
+    return DP_OK;
+  }
+  CUDA_TRY(c, cudaMemcpyAsync(c->x, s->stage_x, sizeof(double) * 3 * off, cudaMemcpyDeviceToDevice, c->st), "repack");
+  CUDA_TRY(c, cudaMemcpyAsync(c->v, s->stage_v, sizeof(double) * 3 * off, cudaMemcpyDeviceToDevice, c->st), "repack");
+  int rc = ctx_set_systems(c, (int)natoms.size(), natoms.data(), boxes.data(), types.data());
+  if (rc) return rc;
+  s->dirty = false;
+  return DP_OK;
+}
+
+extern "C" int dp_server_tick(dp_server* s, int* n_active, int* n_queued) {
+  if (!s) return DP_ERR_ARG;
+  dp_ctx* c = s->ctx;
+  const double t0 = now_ms();
+  // admission, first in first out
+  while (!s->queue.empty()) {
+    ServerReq& r = s->reqs[s->queue.front()];
+    if ((int)s->active.size() >= s->max_slots) { ++s->waits_for_slot; break; }
+    int in_use = 0;
+    for (uint64_t id : s->active) in_use += s->reqs[id].n;
+    if (in_use + r.n > s->n_cap) { ++s->waits_for_memory; break; }
+    r.state = 1;
+    r.tick_admit = s->ticks;
+    r.t_admit = now_ms();
+    r.offset = -1;
+    s->active.push_back(r.id);
+    s->queue.pop_front();
+    s->dirty = true;
+  }
+  if (s->dirty) {
+    int rc = server_repack(s);
+    if (rc) { s->err = c->err; return rc; }
+  }
+  if (!s->active.empty()) {
+    int rc = DP_OK;
+    if (!c->forces_valid) rc = compute_now(c);
+    if (rc) { s->err = c->err; return rc; }
+    long long st[2];
+    for (int attempt = 0; attempt < 4; ++attempt) {
+      CUDA_TRY(c, cudaMemcpyAsync(st, c->step, sizeof st, cudaMemcpyDeviceToHost, c->st), "tick");
+      CUDA_TRY(c, cudaStreamSynchronize(c->st), "tick");
+      st[1] = st[0];
+      CUDA_TRY(c, cudaMemcpyAsync(c->step, st, sizeof st, cudaMemcpyHostToDevice, c->st), "tick");
+      CUDA_TRY(c, cudaMemcpyAsync(s->stage_x, c->x, sizeof(double) * 3 * c->n, cudaMemcpyDeviceToDevice, c->st), "tick");
+      CUDA_TRY(c, cudaMemcpyAsync(s->stage_v, c->v, sizeof(double) * 3 * c->n, cudaMemcpyDeviceToDevice, c->st), "tick");
+      if (!c->graph || c->graph_dt != s->dt || c->graph_trace_len < 1) {
+        rc = build_step_graph(c, s->dt, std::max(1, c->trace_len));
+        if (rc) { s->err = c->err; return rc; }
+      }
+      CUDA_TRY(c, cudaGraphLaunch(c->graph, c->st), "tick");
+      int fl = 0;
+      rc = read_flags(c, &fl);
+      if (rc) { s->err = c->err; return rc; }
+      if (fl & kFlagOverflow) {  // grow the skin lists and redo the step
+        rc = alloc_skin(c, c->cap * 2);
+        if (rc) { s->err = c->err; return rc; }
+        CUDA_TRY(c, cudaMemcpyAsync(c->x, s->stage_x, sizeof(double) * 3 * c->n, cudaMemcpyDeviceToDevice, c->st), "tick");
+        CUDA_TRY(c, cudaMemcpyAsync(c->v, s->stage_v, sizeof(double) * 3 * c->n, cudaMemcpyDeviceToDevice, c->st), "tick");
+        st[1] = 0;
+        CUDA_TRY(c, cudaMemcpyAsync(c->step, st, sizeof st, cudaMemcpyHostToDevice, c->st), "tick");
+        c->forces_valid = false;
+        rc = compute_now(c);
+        if (rc) { s->err = c->err; return rc; }
+        continue;
+      }
+      if (fl & kFlagTimeout) { s->err = "a device-side wait gave up"; return DP_ERR_TIMEOUT; }
+      if (fl & kFlagNonFinite) { s->err = "energy or forces are not finite"; return DP_ERR_NONFINITE; }
+      break;
+    }
+    std::vector<double> tr(2 * s->active.size());
+    CUDA_TRY(c, cudaMemcpyAsync(tr.data(), c->trace, sizeof(double) * tr.size(), cudaMemcpyDeviceToHost, c->st), "tick");
+    CUDA_TRY(c, cudaStreamSynchronize(c->st), "tick");
+    ++s->ticks;
+    s->atom_steps += c->n;
+    s->max_active = std::max(s->max_active, (int)s->active.size());
+    s->max_atoms_seen = std::max(s->max_atoms_seen, c->n);
+    std::vector<uint64_t> still;
+    for (size_t k = 0; k < s->active.size(); ++k) {
+      ServerReq& r = s->reqs[s->active[k]];
+      r.trace.push_back(tr[2 * k]);
+      r.trace.push_back(tr[2 * k + 1]);
+      if (++r.steps_done == r.steps_total) {
+        const size_t b = sizeof(double) * 3 * r.n;
+        CUDA_TRY(c, cudaMemcpyAsync(r.x.data(), c->x + 3 * r.offset, b, cudaMemcpyDeviceToHost, c->st), "results");
+        CUDA_TRY(c, cudaMemcpyAsync(r.v.data(), c->v + 3 * r.offset, b, cudaMemcpyDeviceToHost, c->st), "results");
+        r.state = 2;
+        r.tick_done = s->ticks;
+        s->dirty = true;
+      } else {
+        still.push_back(r.id);
+      }
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->st), "results");
+    const double t1 = now_ms();
+    for (size_t k = 0; k < s->active.size(); ++k) {
+      ServerReq& r = s->reqs[s->active[k]];
+      if (r.state == 2) r.t_done = t1;
+    }
+    s->active.swap(still);
+    s->tick_ms.push_back(t1 - t0);
+    s->busy_ms += t1 - t0;
+  }
+  if (n_active) *n_active = (int)s->active.size();
+  if (n_queued) *n_queued = (int)s->queue.size();
+  return DP_OK;
+}
+
+extern "C" int dp_server_poll(dp_server* s, uint64_t req_id, int* state, double* coords,
+                              double* vel, double* energies, double* latency_ms) {
+  if (!s) return DP_ERR_ARG;
+  auto it = s->reqs.find(req_id);
+  if (it == s->reqs.end()) { s->err = "unknown request"; return DP_ERR_ARG; }
+  ServerReq& r = it->second;
+  if (state) *state = r.state;
+  if (r.state != 2) return DP_OK;
+  if (coords) memcpy(coords, r.x.data(), sizeof(double) * r.x.size());
+  if (vel) memcpy(vel, r.v.data(), sizeof(double) * r.v.size());
+  if (energies) memcpy(energies, r.trace.data(), sizeof(double) * r.trace.size());
+  if (latency_ms) {
+    latency_ms[0] = r.t_done - r.t_submit;
+    latency_ms[1] = r.t_admit - r.t_submit;
+    latency_ms[2] = (double)r.tick_admit;
+    latency_ms[3] = (double)r.tick_done;
+  }
+  return DP_OK;
+}
+
+extern "C" int dp_server_stats(dp_server* s, double* out, int n_out) {
+  if (!s || !out) return DP_ERR_ARG;
+  std::vector<double> t = s->tick_ms;
+  std::sort(t.begin(), t.end());
+  auto pct = [&](double q) {
+    if (t.empty()) return 0.0;
+    size_t k = (size_t)std::min<double>((double)t.size() - 1, std::ceil(q * (double)t.size()) - 1);
+    return t[k];
+  };
+  double v[10] = {(double)s->ticks, pct(0.50), pct(0.99), (double)s->atom_steps, s->busy_ms,
+                  (double)s->max_active, (double)s->max_atoms_seen, (double)s->waits_for_memory,
+                  (double)s->waits_for_slot, (double)s->n_cap};
+  for (int k = 0; k < n_out && k < 10; ++k) out[k] = v[k];
+  return DP_OK;
+}
+
+extern "C" void dp_server_free(dp_server* s) {
+  if (!s) return;
+  if (s->ctx) cudaStreamSynchronize(s->ctx->st);
+  if (s->stage_x) cudaFree(s->stage_x);
+  if (s->stage_v) cudaFree(s->stage_v);
+  dp_free(s->ctx);
+  delete s;
+}
+
+extern "C" const char* dp_server_last_error(const dp_server* s) {
+  return s ? s->err.c_str() : g_server_error.c_str();
 }

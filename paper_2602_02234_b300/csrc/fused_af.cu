@@ -1,19 +1,1420 @@
-// Fused attention-family model (BF16 tensor cores) -- entry points.
+// Fused attention-family model on the fifth-generation tensor cores.
+//
+// Same model as the plain path (paper Sec. II: "repinit" embedding, "repformer"
+// residual self-attention, "fitting-net"; the library's reading of them), in
+// three kernels per evaluation:
+//
+//   k_af_fwd   one CTA per SM, persistent over atoms; per atom the 128
+//              neighbour slots are the 128 rows of every tile.  Environment
+//              and softmax in FP32 registers (thread = row), every matrix
+//              product a tcgen05.mma from shared-memory BF16 tiles into
+//              FP32 tensor memory.  Writes the descriptor D (BF16), T (FP32),
+//              the layer inputs G_l (BF16 tiles) and LayerNorm 1/sigma.
+//   k_fit      tiles of 128 atoms of one species: fitting MLP forward, atomic
+//              energies (FP64 sum of FP32 products) and the input-gradient
+//              chain down to dE/dD, all products on the tensor cores.
+//   k_af_bwd   per atom again: recomputes Q, K, V and the softmax of each
+//              layer from the stored G_l and runs the hand-written adjoint
+//              to g_ij = dE/dr_ij.
+//
+// Tensor memory columns of the per-atom kernels: [0,128) R0, [128,256) R1,
+// [256,384) R2 (the FP32 residual stream G, or its gradient), [384,512) R3.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
 #include "model.h"
+#include "tc.cuh"
 
 namespace dp {
+namespace fz {
+
+// Tensor-core operand type: FP16 by default (10-bit mantissa; the backward
+// seed is scaled by kGradScale to keep gradients in FP16's normal range), BF16
+// when built with -DDP_FUSED_BF16.
+#ifdef DP_FUSED_BF16
+typedef __nv_bfloat16 op_t;
+constexpr uint32_t kFmt = 1;
+__device__ __forceinline__ uint32_t pack2(float a, float b) { return tc::pack_bf16(a, b); }
+__device__ __forceinline__ float2 unpack2(uint32_t u) {
+  return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u));
+}
+__device__ __forceinline__ float op2f(op_t v) { return __bfloat162float(v); }
+__device__ __forceinline__ op_t f2op(float v) { return __float2bfloat16(v); }
+#else
+typedef __half op_t;
+constexpr uint32_t kFmt = 0;
+__device__ __forceinline__ uint32_t pack2(float a, float b) { return tc::pack_f16(a, b); }
+__device__ __forceinline__ float2 unpack2(uint32_t u) {
+  return __half22float2(*reinterpret_cast<const __half2*>(&u));
+}
+__device__ __forceinline__ float op2f(op_t v) { return __half2float(v); }
+__device__ __forceinline__ op_t f2op(float v) { return __float2half_rn(v); }
+#endif
+constexpr float kGradScale = 4096.f;
+
+constexpr int kW = 128;        // embedding / attention width and rows per atom tile
+constexpr int kThreads = 128;
+constexpr long long kPolls = 1LL << 22;
+constexpr uint32_t R0 = 0, R1 = 128, R2 = 256, R3 = 384;
+constexpr int kTile = kW * kW * 2;  // one 128 x 128 BF16 tile: 32 KB
+
+// shared-memory map of the per-atom kernels (bytes)
+constexpr int SM_G = 0, SM_Q = kTile, SM_K = 2 * kTile, SM_V = 3 * kTile, SM_P = 4 * kTile,
+              SM_W = 5 * kTile, SM_MISC = 6 * kTile;
+struct Misc {
+  uint8_t ones[16 * kW * 2];  // 16 x 128 K-major operand: row 0 ones (column sums)
+  uint8_t rhb[16 * kW * 2];   // rows 0..2: unit-vector components of each slot
+  float4 col[kW];             // per neighbour slot: {sw, rh_x, rh_y, rh_z}
+  float sw[kW], dsw[kW], s[kW], d[kW];
+  float rh[kW][3];
+  float Rt[kW][4];
+  float T[4][kW];
+  float dT[4][kW];
+  float dRt[kW][4];
+  float drc[kW][3];
+  float dswa[kW];
+  int tj[kW];
+  int mask;
+  int nvalid;
+  uint32_t tptr;
+  int pad;
+  unsigned long long bar, wbar, pbar;
+};
+constexpr int kSmemAtom = SM_MISC + (int)sizeof(Misc) + 64;
+
+struct Params {
+  int n, nmax, e1, e2, m2, n_layers, heads, dh;
+  float rs, rc, inv_nmax, inv_sqrt_d;
+  const int* sel_j;
+  const double* sel_r;
+  const int* types;
+  // BF16 weight tiles (core-matrix layout), see the host packing below
+  const uint8_t *W2T, *W3T, *W2R, *W3R;  // per species
+  const uint8_t *WqT, *WkT, *WvT, *WoT;  // per layer, 32 KB each
+  const uint8_t *WqR, *WkR, *WvR, *WoR;
+  const float *W1, *b1, *b2, *b3, *bo;   // FP32 vectors
+  uint8_t* Gst;                           // [n][L+1][32 KB]
+  float* rstd;                            // [n][L][128]
+  float2* smx;                            // [n][L][heads][128] softmax {log2 max, 1/Z}
+  op_t* D;                                // [n][128 * m2]
+  float* Tm;                              // [n][4][128]
+  const float* dD;                        // [n][128 * m2]
+  float* g;                               // [n][nmax][3]
+  int* status;
+};
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ uint64_t dK(uint32_t base, int Kx, int row0, int k0) {
+  return tc::make_desc(base + (uint32_t)(((row0 >> 3) * (Kx >> 3) + (k0 >> 3)) * 128), 128u,
+                       (uint32_t)((Kx >> 3) * 128));
+}
+// MN-major view of a K-major-stored tile: operand MN index = stored column,
+// operand K index = stored row.
+__device__ __forceinline__ uint64_t dMN(uint32_t base, int Kx, int mn0, int k0) {
+  return tc::make_desc(base + (uint32_t)(((k0 >> 3) * (Kx >> 3) + (mn0 >> 3)) * 128),
+                       (uint32_t)((Kx >> 3) * 128), 128u);
+}
+
+// An MMA operand: a K-major tile (Kx stored columns) read either directly
+// (rows = operand M/N, stored columns koff.. = operand K) or through its
+// MN-major view (stored columns mn0.. = operand M/N, stored rows koff.. = K).
+struct Opnd {
+  uint32_t base;
+  int Kx, mn, mn0, koff;
+};
+__device__ __forceinline__ uint64_t odesc(const Opnd& o, int ks) {
+  return o.mn ? dMN(o.base, o.Kx, o.mn0, o.koff + ks) : dK(o.base, o.Kx, 0, o.koff + ks);
+}
+__device__ __forceinline__ Opnd kop(const uint8_t* p, int Kx, int koff = 0) {
+  return Opnd{tc::smem_u32(p), Kx, 0, 0, koff};
+}
+__device__ __forceinline__ Opnd mnop(const uint8_t* p, int Kx, int mn0, int koff = 0) {
+  return Opnd{tc::smem_u32(p), Kx, 1, mn0, koff};
+}
+// Issue D (+)= A B over K (thread 0 only): K/16 instructions of 128 x N x 16.
+__device__ __forceinline__ void mma_issue(uint32_t d, const Opnd& A, const Opnd& B, int N, int K,
+                                          bool acc) {
+  const uint32_t id = tc::idesc_f16(128, N, A.mn, B.mn, kFmt);
+  for (int ks = 0; ks < K; ks += 16)
+    tc::mma_bf16(d, odesc(A, ks), odesc(B, ks), id, (acc || ks > 0) ? 1u : 0u);
+}
+
+__device__ __forceinline__ void zero_smem(uint8_t* dst, int bytes) {
+  int4* d = reinterpret_cast<int4*>(dst);
+  for (int i = threadIdx.x; i < bytes / 16; i += blockDim.x) d[i] = make_int4(0, 0, 0, 0);
+}
+
+// 8 consecutive values of row r, columns c..c+7 (c multiple of 8), as one
+// 16-byte store into a K-major tile with Kx columns
+__device__ __forceinline__ void store8(uint8_t* tile, int r, int c, int Kx, const float* v) {
+  uint4 u;
+  u.x = pack2(v[0], v[1]);
+  u.y = pack2(v[2], v[3]);
+  u.z = pack2(v[4], v[5]);
+  u.w = pack2(v[6], v[7]);
+  *reinterpret_cast<uint4*>(tile + tc::kmajor_off(r, c, Kx)) = u;
+}
+__device__ __forceinline__ void load8(const uint8_t* tile, int r, int c, int Kx, float* v) {
+  uint4 u = *reinterpret_cast<const uint4*>(tile + tc::kmajor_off(r, c, Kx));
+  const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float2 f = unpack2(w4[q]);
+    v[2 * q] = f.x;
+    v[2 * q + 1] = f.y;
+  }
+}
+
+// Completion tracking on one mbarrier: every thread polls (bounded) and the
+// outcome is made uniform across the CTA, so a timeout never strands part of
+// the block at a barrier.
+struct Bar {
+  unsigned long long* bar;
+  uint32_t phase;
+  __device__ bool wait(int* status) {
+    bool ok = tc::mbar_wait(reinterpret_cast<uint64_t*>(bar), phase & 1u, kPolls);
+    phase ^= 1u;
+    ok = __syncthreads_and(ok) != 0;
+    if (!ok && threadIdx.x == 0) atomicOr(status, kFlagTimeout);
+    tc::fence_after_sync();
+    return ok;
+  }
+};
+
+__device__ __forceinline__ void before_mma() {
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+}
+
+// Bulk (TMA) copy of `bytes` from global memory into a shared buffer,
+// completing on `b`.  All threads call it; thread 0 issues after a barrier
+// that orders every earlier access to the buffer before the copy.
+__device__ __forceinline__ void bulk_load(Bar& b, uint8_t* dst, const void* src, uint32_t bytes) {
+  tc::fence_async_smem();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tc::mbar_expect_tx(reinterpret_cast<uint64_t*>(b.bar), bytes);
+    tc::bulk_g2s(dst, src, bytes, reinterpret_cast<uint64_t*>(b.bar));
+  }
+}
+
+// One product group: barrier, issue by thread 0, commit to `mb`, wait.
+#define MMA_GROUP(mb, status, ...)                                   \
+  do {                                                               \
+    before_mma();                                                    \
+    if (threadIdx.x == 0) {                                          \
+      __VA_ARGS__;                                                   \
+      tc::mma_commit(reinterpret_cast<uint64_t*>((mb).bar));         \
+    }                                                                \
+    if (!(mb).wait(status)) return false;                            \
+  } while (0)
+
+// ------------------------------------------------------------------ environment
+// Thread t fills row t: switch, s = sw/r, R~, unit vector; empty slots zero.
+__device__ void env_row(const Params& p, int atom, Misc* m, int t) {
+  int j = t < p.nmax ? p.sel_j[(size_t)atom * p.nmax + t] : -1;
+  if (j < 0) {
+    m->sw[t] = 0.f; m->dsw[t] = 0.f; m->s[t] = 0.f; m->d[t] = 1.f;
+    for (int a = 0; a < 3; ++a) m->rh[t][a] = 0.f;
+    for (int a = 0; a < 4; ++a) m->Rt[t][a] = 0.f;
+    m->col[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    m->tj[t] = -1;
+    return;
+  }
+  size_t o = ((size_t)atom * p.nmax + t) * 3;
+  float r[3] = {(float)p.sel_r[o], (float)p.sel_r[o + 1], (float)p.sel_r[o + 2]};
+  float d = sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+  float sw, dsw;
+  smooth_switch(d, p.rs, p.rc, &sw, &dsw);
+  float s = sw / d;
+  m->sw[t] = sw; m->dsw[t] = dsw; m->s[t] = s; m->d[t] = d;
+  m->Rt[t][0] = s;
+  for (int a = 0; a < 3; ++a) {
+    m->rh[t][a] = r[a] / d;
+    m->Rt[t][1 + a] = s * r[a] / d;
+  }
+  m->col[t] = make_float4(sw, r[0] / d, r[1] / d, r[2] / d);
+  m->tj[t] = p.types[j];
+}
+
+__device__ void atom_setup(const Params& p, int atom, Misc* m) {
+  const int t = threadIdx.x;
+  if (t == 0) {
+    m->mask = 0;
+    m->nvalid = 0;
+  }
+  __syncthreads();
+  env_row(p, atom, m, t);
+  if (m->tj[t] >= 0) {
+    atomicOr(&m->mask, 1 << m->tj[t]);
+    atomicMax(&m->nvalid, t + 1);
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ embedding
+// Layer 1 on the SIMT cores (into the K-major tile H1, and into h1 when
+// given), layer 2 on the tensor cores species by species into H2 (BF16).
+__device__ bool embed_h2(const Params& p, uint8_t* sm, Misc* m, uint32_t tb, Bar& mb, Bar& wb,
+                         uint8_t* H1, uint8_t* H2, float* h1) {
+  const int t = threadIdx.x, warp = t >> 5;
+  const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+  const int tj = m->tj[t];
+  const float s = m->s[t];
+  uint8_t* Wt = sm + SM_W;
+  for (int c = 0; c < p.e1; c += 8) {
+    float v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      float h = 0.f;
+      if (tj >= 0) h = tanhf(s * p.W1[tj * p.e1 + c + q] + p.b1[tj * p.e1 + c + q]);
+      v[q] = h;
+      if (h1) h1[c + q] = h;
+    }
+    store8(H1, t, c, p.e1, v);
+  }
+  for (int c = 0; c < p.e2; c += 8) {
+    float z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    store8(H2, t, c, p.e2, z);
+  }
+  const int mask = m->mask;
+  for (int sp = 0; sp < 32; ++sp) {
+    if (!(mask & (1 << sp))) continue;
+    bulk_load(wb, Wt, p.W2T + (size_t)sp * p.e2 * p.e1 * 2, p.e2 * p.e1 * 2);
+    if (!wb.wait(p.status)) return false;
+    MMA_GROUP(mb, p.status, mma_issue(tb + R0, kop(H1, p.e1), kop(Wt, p.e1), p.e2, p.e1, false));
+    const bool mine = tj == sp;
+    if (__any_sync(0xffffffffu, mine)) {
+      for (int c = 0; c < p.e2; c += 32) {
+        float v[32];
+        tc::tmem_ld32(tb + lane_off + R0 + c, v);
+        if (mine) {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) v[q] = tanhf(v[q] + p.b2[sp * p.e2 + c + q]);
+#pragma unroll
+          for (int q = 0; q < 32; q += 8) store8(H2, t, c + q, p.e2, v + q);
+        }
+      }
+    }
+    tc::fence_before_sync();
+  }
+  return true;
+}
+
+// G0 into the G tile (BF16) and R2 (FP32).
+__device__ bool embed_forward(const Params& p, uint8_t* sm, Misc* m, uint32_t tb, Bar& mb, Bar& wb) {
+  const int t = threadIdx.x, warp = t >> 5;
+  const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+  uint8_t* H1 = sm + SM_Q;
+  uint8_t* H2 = sm + SM_K;
+  uint8_t* Wt = sm + SM_W;
+  uint8_t* Gt = sm + SM_G;
+  if (!embed_h2(p, sm, m, tb, mb, wb, H1, H2, nullptr)) return false;
+  const int tj = m->tj[t];
+  for (int c = 0; c < kW; c += 8) {
+    float z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    store8(Gt, t, c, kW, z);
+  }
+  {
+    float z[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) z[q] = 0.f;
+    for (int c = 0; c < kW; c += 32) tc::tmem_st32(tb + lane_off + R2 + c, z);
+  }
+  const int mask = m->mask;
+  for (int sp = 0; sp < 32; ++sp) {
+    if (!(mask & (1 << sp))) continue;
+    bulk_load(wb, Wt, p.W3T + (size_t)sp * kW * p.e2 * 2, kW * p.e2 * 2);
+    if (!wb.wait(p.status)) return false;
+    MMA_GROUP(mb, p.status, mma_issue(tb + R1, kop(H2, p.e2), kop(Wt, p.e2), kW, p.e2, false));
+    const bool mine = tj == sp;
+    if (__any_sync(0xffffffffu, mine)) {
+      for (int c = 0; c < kW; c += 32) {
+        float v[32], old[32];
+        tc::tmem_ld32(tb + lane_off + R1 + c, v);
+        tc::tmem_ld32(tb + lane_off + R2 + c, old);
+        if (mine) {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) old[q] = tanhf(v[q] + p.b3[sp * kW + c + q]);
+#pragma unroll
+          for (int q = 0; q < 32; q += 8) store8(Gt, t, c + q, kW, old + q);
+        }
+        tc::tmem_st32(tb + lane_off + R2 + c, old);
+      }
+    }
+    tc::fence_before_sync();
+  }
+  return true;
+}
+
+// Q, K, V of layer l from the G tile into tensor memory R0, R1, R3 and then
+// into BF16 tiles; weights arrive through the two staging buffers W and P.
+__device__ bool qkv(const Params& p, int l, uint8_t* sm, uint32_t tb, Bar& mb, Bar& wb, Bar& pb,
+                    bool prefetched) {
+  const int t = threadIdx.x, warp = t >> 5;
+  const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+  uint8_t *Wt = sm + SM_W, *Pt = sm + SM_P;
+  if (!prefetched) {
+    bulk_load(wb, Wt, p.WqT + (size_t)l * kTile, kTile);
+    bulk_load(pb, Pt, p.WkT + (size_t)l * kTile, kTile);
+  }
+  if (!wb.wait(p.status)) return false;
+  MMA_GROUP(mb, p.status, mma_issue(tb + R0, kop(sm + SM_G, kW), kop(Wt, kW), kW, kW, false));
+  bulk_load(wb, Wt, p.WvT + (size_t)l * kTile, kTile);
+  if (!pb.wait(p.status)) return false;
+  MMA_GROUP(mb, p.status, mma_issue(tb + R1, kop(sm + SM_G, kW), kop(Pt, kW), kW, kW, false));
+  if (!wb.wait(p.status)) return false;
+  MMA_GROUP(mb, p.status, mma_issue(tb + R3, kop(sm + SM_G, kW), kop(Wt, kW), kW, kW, false));
+  const uint32_t src[3] = {R0, R1, R3};
+  uint8_t* dst[3] = {sm + SM_Q, sm + SM_K, sm + SM_V};
+  for (int q3 = 0; q3 < 3; ++q3)
+    for (int c = 0; c < kW; c += 32) {
+      float v[32];
+      tc::tmem_ld32(tb + lane_off + src[q3] + c, v);
+#pragma unroll
+      for (int q = 0; q < 32; q += 8) store8(dst[q3], t, c + q, kW, v + q);
+    }
+  tc::fence_before_sync();
+  return true;
+}
+
+// Softmax statistics of this thread's row of the head scores in tensor memory,
+// in one pass over 32-column chunks (running maximum, rescaled sum):
+// b = max_k S_jk log2(e)/sqrt(d) over real columns, and 1/Z with
+// Z = sum_k sw_k 2^(S_jk log2(e)/sqrt(d) - b); 1/Z = 0 for an empty slot.
+__device__ float2 softmax_stats(const Params& p, const Misc* m, uint32_t taddr) {
+  const float a = p.inv_sqrt_d * 1.4426950408889634f;
+  const int nv = m->nvalid;
+  float mx = -1e30f, z = 0.f;
+  for (int c = 0; c < kW; c += 32) {
+    if (c >= nv) break;
+    float v[32];
+    tc::tmem_ld32(taddr + c, v);
+    float cm = -1e30f;
+#pragma unroll
+    for (int q = 0; q < 32; ++q)
+      if (c + q < nv) cm = fmaxf(cm, v[q] * a);
+    const float nm = fmaxf(mx, cm);
+    float zc = 0.f;
+#pragma unroll
+    for (int q = 0; q < 32; ++q)
+      if (c + q < nv) zc += m->col[c + q].x * exp2f(v[q] * a - nm);
+    z = z * exp2f(mx - nm) + zc;
+    mx = nm;
+  }
+  const float inv = (z > 0.f && threadIdx.x < nv) ? 1.f / z : 0.f;
+  return make_float2(mx, inv);
+}
+
+// attention weights w_jk of 32 columns from raw scores v (in place)
+__device__ __forceinline__ void softmax_w(const Params& p, const Misc* m, int c, float2 st,
+                                          float* v) {
+  const float a = p.inv_sqrt_d * 1.4426950408889634f;
+  const int nv = m->nvalid;
+#pragma unroll
+  for (int q = 0; q < 32; ++q)
+    v[q] = (c + q < nv) ? m->col[c + q].x * exp2f(v[q] * a - st.x) * st.y : 0.f;
+}
+
+__device__ __forceinline__ float gate(const float* rj, const float4& ck) {
+  return rj[0] * ck.y + rj[1] * ck.z + rj[2] * ck.w;
+}
+
+// ------------------------------------------------------------------ forward
+__device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32_t tb, Bar& mb,
+                         Bar& wb, Bar& pb) {
+  const int t = threadIdx.x, warp = t >> 5;
+  const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+  atom_setup(p, atom, m);
+  const int ngroups = (m->nvalid + 7) >> 3;
+  uint8_t* Gdst = p.Gst + (size_t)atom * (p.n_layers + 1) * kTile;
+  if (!embed_forward(p, sm, m, tb, mb, wb)) return false;
+  __syncthreads();
+  bool prefetched = false;
+  if (p.n_layers > 0) {
+    bulk_load(wb, sm + SM_W, p.WqT, kTile);
+    bulk_load(pb, sm + SM_P, p.WkT, kTile);
+    prefetched = true;
+  }
+  for (int i = t; i < ngroups * 2048 / 16; i += kThreads)
+    reinterpret_cast<int4*>(Gdst)[i] = reinterpret_cast<const int4*>(sm + SM_G)[i];
+  for (int l = 0; l < p.n_layers; ++l) {
+    if (!qkv(p, l, sm, tb, mb, wb, pb, prefetched)) return false;
+    prefetched = false;
+    bulk_load(wb, sm + SM_W, p.WoT + (size_t)l * kTile, kTile);  // lands during the heads
+    for (int h = 0; h < p.heads; ++h) {
+      MMA_GROUP(mb, p.status,
+                mma_issue(tb + R3, kop(sm + SM_Q, kW, h * p.dh), kop(sm + SM_K, kW, h * p.dh), kW,
+                          p.dh, false));
+      const float2 st = softmax_stats(p, m, tb + lane_off + R3);
+      p.smx[(((size_t)atom * p.n_layers + l) * p.heads + h) * kW + t] = st;
+      const float rj[3] = {m->col[t].y, m->col[t].z, m->col[t].w};
+      for (int c = 0; c < kW; c += 32) {
+        float v[32];
+        if (c < m->nvalid) {
+          tc::tmem_ld32(tb + lane_off + R3 + c, v);
+          softmax_w(p, m, c, st, v);
+#pragma unroll
+          for (int q = 0; q < 32; ++q) v[q] *= gate(rj, m->col[c + q]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) v[q] = 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 32; q += 8) store8(sm + SM_P, t, c + q, kW, v + q);
+      }
+      tc::fence_before_sync();
+      MMA_GROUP(mb, p.status,
+                mma_issue(tb + R0 + h * p.dh, kop(sm + SM_P, kW), mnop(sm + SM_V, kW, h * p.dh), p.dh,
+                          kW, false));
+    }
+    for (int c = 0; c < kW; c += 32) {
+      float v[32];
+      tc::tmem_ld32(tb + lane_off + R0 + c, v);
+#pragma unroll
+      for (int q = 0; q < 32; q += 8) store8(sm + SM_Q, t, c + q, kW, v + q);
+    }
+    tc::fence_before_sync();
+    if (!wb.wait(p.status)) return false;
+    MMA_GROUP(mb, p.status, mma_issue(tb + R1, kop(sm + SM_Q, kW), kop(sm + SM_W, kW), kW, kW, false));
+    if (l + 1 < p.n_layers) {  // next layer's first two weights land during the LayerNorm
+      bulk_load(wb, sm + SM_W, p.WqT + (size_t)(l + 1) * kTile, kTile);
+      bulk_load(pb, sm + SM_P, p.WkT + (size_t)(l + 1) * kTile, kTile);
+      prefetched = true;
+    }
+    // residual + LayerNorm, thread = row: three passes over 32-column chunks
+    const bool valid = m->tj[t] >= 0;
+    float sum = 0.f, sq = 0.f;
+    for (int c = 0; c < kW; c += 32) {
+      float g[32], y[32];
+      tc::tmem_ld32(tb + lane_off + R2 + c, g);
+      tc::tmem_ld32(tb + lane_off + R1 + c, y);
+#pragma unroll
+      for (int q = 0; q < 32; ++q) sum += g[q] + y[q] + p.bo[l * kW + c + q];
+    }
+    const float mu = sum * (1.f / kW);
+    for (int c = 0; c < kW; c += 32) {
+      float g[32], y[32];
+      tc::tmem_ld32(tb + lane_off + R2 + c, g);
+      tc::tmem_ld32(tb + lane_off + R1 + c, y);
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        float z = g[q] + y[q] + p.bo[l * kW + c + q] - mu;
+        sq += z * z;
+      }
+    }
+    const float rs = valid ? rsqrtf(sq * (1.f / kW) + 1e-5f) : 0.f;
+    for (int c = 0; c < kW; c += 32) {
+      float g[32], y[32];
+      tc::tmem_ld32(tb + lane_off + R2 + c, g);
+      tc::tmem_ld32(tb + lane_off + R1 + c, y);
+#pragma unroll
+      for (int q = 0; q < 32; ++q) g[q] = (g[q] + y[q] + p.bo[l * kW + c + q] - mu) * rs;
+      tc::tmem_st32(tb + lane_off + R2 + c, g);
+#pragma unroll
+      for (int q = 0; q < 32; q += 8) store8(sm + SM_G, t, c + q, kW, g + q);
+    }
+    p.rstd[((size_t)atom * p.n_layers + l) * kW + t] = rs;
+    tc::fence_before_sync();
+    __syncthreads();
+    uint8_t* dst = Gdst + (size_t)(l + 1) * kTile;
+    for (int i = t; i < ngroups * 2048 / 16; i += kThreads)
+      reinterpret_cast<int4*>(dst)[i] = reinterpret_cast<const int4*>(sm + SM_G)[i];
+  }
+  // descriptor: T[a][f] = (1/Nmax) sum_j R~[j][a] G[j][f]; thread = f
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  const int f = t;
+  for (int j = 0; j < m->nvalid; ++j) {
+    float gv = op2f(*reinterpret_cast<const op_t*>(sm + SM_G + tc::kmajor_off(j, f, kW)));
+#pragma unroll
+    for (int a = 0; a < 4; ++a) acc[a] += m->Rt[j][a] * gv;
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    m->T[a][f] = acc[a] * p.inv_nmax;
+    p.Tm[((size_t)atom * 4 + a) * kW + f] = acc[a] * p.inv_nmax;
+  }
+  __syncthreads();
+  op_t* Drow = p.D + (size_t)atom * kW * p.m2 + (size_t)f * p.m2;
+  for (int q = 0; q < p.m2; ++q) {
+    float v = 0.f;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) v += m->T[a][f] * m->T[a][q];
+    Drow[q] = f2op(v);
+  }
+  __syncthreads();
+  return true;
+}
+
+__device__ void kernel_prologue(Misc* m) {
+  const int t = threadIdx.x, warp = t >> 5;
+  if (t == 0) {
+    tc::mbar_init(reinterpret_cast<uint64_t*>(&m->bar), 1);
+    tc::mbar_init(reinterpret_cast<uint64_t*>(&m->wbar), 1);
+    tc::mbar_init(reinterpret_cast<uint64_t*>(&m->pbar), 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(&m->tptr, 512);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+}
+
+__device__ void kernel_epilogue(Misc* m) {
+  tc::fence_before_sync();
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(m->tptr, 512);
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_af_fwd(Params p) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  Misc* m = reinterpret_cast<Misc*>(sm + SM_MISC);
+  kernel_prologue(m);
+  Bar mb{&m->bar, 0u}, wb{&m->wbar, 0u}, pb{&m->pbar, 0u};
+  for (int atom = blockIdx.x; atom < p.n; atom += gridDim.x)
+    if (!fwd_atom(p, atom, sm, m, m->tptr, mb, wb, pb)) break;
+  kernel_epilogue(m);
+}
+
+// ------------------------------------------------------------------ backward
+// Adjoint of one atom: dE/dD (from the fitting kernel) back to g_ij.
+__device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32_t tb, Bar& mb,
+                         Bar& wb, Bar& pb) {
+  const int t = threadIdx.x, warp = t >> 5;
+  const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+  atom_setup(p, atom, m);
+  const int ngroups = (m->nvalid + 7) >> 3;
+  const int L = p.n_layers;
+  const uint8_t* Gsrc = p.Gst + (size_t)atom * (L + 1) * kTile;
+  const bool valid = m->tj[t] >= 0;
+  const int DH = p.dh;
+  // load a stored G tile: real row groups by bulk copy, the rest zero
+  auto load_G = [&](uint8_t* dst, int l, Bar& b) {
+    zero_smem(dst + ngroups * 2048, kTile - ngroups * 2048);
+    if (ngroups > 0) bulk_load(b, dst, Gsrc + (size_t)l * kTile, ngroups * 2048);
+  };
+  // ---- descriptor adjoint: dT = dD T (both orders), dR~ and dG_L
+  {
+    const int f = t;
+    float* dDs = reinterpret_cast<float*>(sm + SM_P);   // 128 x m2 FP32 staging
+    for (int i = t; i < kW * p.m2; i += kThreads) dDs[i] = p.dD[(size_t)atom * kW * p.m2 + i];
+    m->T[0][f] = p.Tm[((size_t)atom * 4 + 0) * kW + f];
+    m->T[1][f] = p.Tm[((size_t)atom * 4 + 1) * kW + f];
+    m->T[2][f] = p.Tm[((size_t)atom * 4 + 2) * kW + f];
+    m->T[3][f] = p.Tm[((size_t)atom * 4 + 3) * kW + f];
+    __syncthreads();
+    for (int a = 0; a < 4; ++a) {
+      float v = 0.f;
+      for (int q = 0; q < p.m2; ++q) v += dDs[f * p.m2 + q] * m->T[a][q];
+      if (f < p.m2)
+        for (int g = 0; g < kW; ++g) v += dDs[g * p.m2 + f] * m->T[a][g];
+      m->dT[a][f] = v;
+    }
+  }
+  {
+    load_G(sm + SM_G, L, wb);
+    if (ngroups > 0 && !wb.wait(p.status)) return false;
+    __syncthreads();
+  }
+  {
+    float dr[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int c = 0; c < kW; c += 32) {
+      float g[32];
+#pragma unroll
+      for (int q = 0; q < 32; q += 8) load8(sm + SM_G, t, c + q, kW, g + q);
+      float dg[32];
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int f = c + q;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) dr[a] += m->dT[a][f] * g[q];
+        dg[q] = valid ? kGradScale * p.inv_nmax *
+                            (m->dT[0][f] * m->Rt[t][0] + m->dT[1][f] * m->Rt[t][1] +
+                             m->dT[2][f] * m->Rt[t][2] + m->dT[3][f] * m->Rt[t][3])
+                      : 0.f;
+      }
+      tc::tmem_st32(tb + lane_off + R2 + c, dg);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) m->dRt[t][a] = dr[a] * p.inv_nmax;
+  }
+  float drow[3] = {0.f, 0.f, 0.f};  // gate adjoint, row part: sum_k dA_jk w_jk rh_k
+  m->dswa[t] = 0.f;
+  m->drc[t][0] = m->drc[t][1] = m->drc[t][2] = 0.f;
+  // gate column-sum operand: rows 0..2 = rh components of neighbour j (column j)
+  {
+    uint8_t* RHB = m->rhb;
+    for (int a = 0; a < 3; ++a)
+      *reinterpret_cast<op_t*>(RHB + tc::kmajor_off(a, t, kW)) = f2op(valid ? m->rh[t][a] : 0.f);
+  }
+  for (int l = L - 1; l >= 0; --l) {
+    // ---- stored layer input and output tiles
+    load_G(sm + SM_G, l, wb);
+    load_G(sm + SM_V, l + 1, pb);
+    if (ngroups > 0 && !(wb.wait(p.status) && pb.wait(p.status))) return false;
+    __syncthreads();
+    // ---- LayerNorm adjoint: dZ = rstd (dG - mean dG - Gout mean(dG Gout))
+    {
+      const float rs = p.rstd[((size_t)atom * L + l) * kW + t];
+      float s1 = 0.f, s2 = 0.f;
+      for (int c = 0; c < kW; c += 32) {
+        float dg[32], go[32];
+        tc::tmem_ld32(tb + lane_off + R2 + c, dg);
+#pragma unroll
+        for (int q = 0; q < 32; q += 8) load8(sm + SM_V, t, c + q, kW, go + q);
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          s1 += dg[q];
+          s2 += dg[q] * go[q];
+        }
+      }
+      s1 *= (1.f / kW);
+      s2 *= (1.f / kW);
+      for (int c = 0; c < kW; c += 32) {
+        float dg[32], go[32];
+        tc::tmem_ld32(tb + lane_off + R2 + c, dg);
+#pragma unroll
+        for (int q = 0; q < 32; q += 8) load8(sm + SM_V, t, c + q, kW, go + q);
+#pragma unroll
+        for (int q = 0; q < 32; ++q) dg[q] = valid ? rs * (dg[q] - s1 - go[q] * s2) : 0.f;
+        tc::tmem_st32(tb + lane_off + R2 + c, dg);
+#pragma unroll
+        for (int q = 0; q < 32; q += 8) store8(sm + SM_P, t, c + q, kW, dg + q);
+      }
+      tc::fence_before_sync();
+    }
+    // ---- recompute Q, K, V (weights through W; R1 and R3 are free)
+    {
+      const uint8_t* Ws[3] = {p.WqT + (size_t)l * kTile, p.WkT + (size_t)l * kTile,
+                              p.WvT + (size_t)l * kTile};
+      const uint32_t dst[3] = {R0, R1, R3};
+      for (int q3 = 0; q3 < 3; ++q3) {
+        bulk_load(wb, sm + SM_W, Ws[q3], kTile);
+        if (!wb.wait(p.status)) return false;
+        MMA_GROUP(mb, p.status,
+                  mma_issue(tb + dst[q3], kop(sm + SM_G, kW), kop(sm + SM_W, kW), kW, kW, false));
+      }
+      uint8_t* tiles[3] = {sm + SM_Q, sm + SM_K, sm + SM_V};
+      for (int q3 = 0; q3 < 3; ++q3)
+        for (int c = 0; c < kW; c += 32) {
+          float v[32];
+          tc::tmem_ld32(tb + lane_off + dst[q3] + c, v);
+#pragma unroll
+          for (int q = 0; q < 32; q += 8) store8(tiles[q3], t, c + q, kW, v + q);
+        }
+      tc::fence_before_sync();
+    }
+    // ---- dO = dZ Wo^T into R1, then the BF16 tile over G (no longer needed)
+    bulk_load(wb, sm + SM_W, p.WoR + (size_t)l * kTile, kTile);
+    if (!wb.wait(p.status)) return false;
+    MMA_GROUP(mb, p.status, mma_issue(tb + R1, kop(sm + SM_P, kW), kop(sm + SM_W, kW), kW, kW, false));
+    for (int c = 0; c < kW; c += 32) {
+      float v[32];
+      tc::tmem_ld32(tb + lane_off + R1 + c, v);
+#pragma unroll
+      for (int q = 0; q < 32; q += 8) store8(sm + SM_G, t, c + q, kW, v + q);
+    }
+    tc::fence_before_sync();
+    // ---- heads
+    for (int h = 0; h < p.heads; ++h) {
+      const int c0 = h * DH;
+      // scores
+      MMA_GROUP(mb, p.status,
+                mma_issue(tb + R3, kop(sm + SM_Q, kW, c0), kop(sm + SM_K, kW, c0), kW, DH, false));
+      const float2 st = p.smx[(((size_t)atom * L + l) * p.heads + h) * kW + t];
+      const float rj[3] = {m->col[t].y, m->col[t].z, m->col[t].w};
+      const int nv = m->nvalid;
+      // A = w * gate -> P tile
+      for (int c = 0; c < kW; c += 32) {
+        float v[32];
+        if (c < nv) {
+          tc::tmem_ld32(tb + lane_off + R3 + c, v);
+          softmax_w(p, m, c, st, v);
+#pragma unroll
+          for (int q = 0; q < 32; ++q) v[q] *= gate(rj, m->col[c + q]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) v[q] = 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 32; q += 8) store8(sm + SM_P, t, c + q, kW, v + q);
+      }
+      tc::fence_before_sync();
+      // dA = dO_h V_h^T (R1), dV_h = A^T dO_h (R0 + 2d), O_h = A V_h (R0, consumed
+      // below before dQ_h overwrites it)
+      MMA_GROUP(mb, p.status,
+                mma_issue(tb + R1, kop(sm + SM_G, kW, c0), kop(sm + SM_V, kW, c0), kW, DH, false);
+                mma_issue(tb + R0 + 2 * DH, mnop(sm + SM_P, kW, 0), mnop(sm + SM_G, kW, c0), DH, kW,
+                          false);
+                mma_issue(tb + R0, kop(sm + SM_P, kW), mnop(sm + SM_V, kW, c0), DH, kW, false));
+      // sum_k w_jk dw_jk = sum_k A_jk dA_jk = dO_j . O_j (this head's columns)
+      float wdw = 0.f;
+      {
+        float o[32];
+        tc::tmem_ld32(tb + lane_off + R0, o);
+        for (int q = 0; q < DH; q += 8) {
+          float g8[8];
+          load8(sm + SM_G, t, c0 + q, kW, g8);
+#pragma unroll
+          for (int e = 0; e < 8; ++e) wdw += g8[e] * o[q + e];
+        }
+      }
+      // softmax + gate adjoint for this row
+      for (int c = 0; c < kW; c += 32) {
+        float s[32], x[32];
+        if (c < nv) {
+          float da[32];
+          tc::tmem_ld32(tb + lane_off + R3 + c, s);
+          tc::tmem_ld32(tb + lane_off + R1 + c, da);
+          softmax_w(p, m, c, st, s);
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
+            const float4 ck = m->col[c + q];
+            const float dw = da[q] * gate(rj, ck);
+            x[q] = da[q] * s[q];                  // gate adjoint dc_jk
+            drow[0] += x[q] * ck.y;
+            drow[1] += x[q] * ck.z;
+            drow[2] += x[q] * ck.w;
+            s[q] = s[q] * (dw - wdw);             // dS_jk = w (dw - sum w dw)
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) s[q] = x[q] = 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 32; q += 8) {
+          store8(sm + SM_W, t, c + q, kW, s + q);
+          store8(sm + SM_P, t, c + q, kW, x + q);
+        }
+      }
+      tc::fence_before_sync();
+      // dQ_h = dS K_h, dK_h = dS^T Q_h (scaled at drain), column sums of dS
+      // (ones) and of the gate adjoint weighted by rh_j, accumulated over heads
+      MMA_GROUP(mb, p.status,
+                mma_issue(tb + R0, kop(sm + SM_W, kW), mnop(sm + SM_K, kW, c0), DH, kW, false);
+                mma_issue(tb + R0 + DH, mnop(sm + SM_W, kW, 0), mnop(sm + SM_Q, kW, c0), DH, kW, false);
+                mma_issue(tb + R0 + 112, mnop(sm + SM_W, kW, 0), kop(m->ones, kW), 16, kW, h > 0);
+                mma_issue(tb + R0 + 96, mnop(sm + SM_P, kW, 0), kop(m->rhb, kW), 16, kW, h > 0));
+      // write dQ_h, dK_h, dV_h (R0 columns [0,32), [32,64), [64,96)) over the
+      // head's columns of Q, K, V
+      {
+        uint8_t* tiles[3] = {sm + SM_Q, sm + SM_K, sm + SM_V};
+#pragma unroll 1
+        for (int part = 0; part < 3; ++part) {
+          float v[32];
+          tc::tmem_ld32(tb + lane_off + R0 + 32 * part, v);
+          const float sc = part < 2 ? p.inv_sqrt_d : 1.f;
+#pragma unroll
+          for (int q = 0; q < 32; ++q) v[q] *= sc;
+#pragma unroll
+          for (int q = 0; q < 32; q += 8) store8(tiles[part], t, c0 + q, kW, v + q);
+        }
+      }
+      tc::fence_before_sync();
+    }
+    // column sums of this layer: thread k owns column k
+    {
+      float v[32];
+      tc::tmem_ld32(tb + lane_off + R0 + 96, v);
+      m->drc[t][0] += v[0];
+      m->drc[t][1] += v[1];
+      m->drc[t][2] += v[2];
+      if (valid && m->sw[t] > 0.f) m->dswa[t] += v[16] / m->sw[t];
+    }
+    // ---- dG_in = dZ + dQ Wq^T + dK Wk^T + dV Wv^T, accumulated onto R2
+    {
+      const uint8_t* Ws[3] = {p.WqR + (size_t)l * kTile, p.WkR + (size_t)l * kTile,
+                              p.WvR + (size_t)l * kTile};
+      uint8_t* As[3] = {sm + SM_Q, sm + SM_K, sm + SM_V};
+      for (int q3 = 0; q3 < 3; ++q3) {
+        bulk_load(wb, sm + SM_W, Ws[q3], kTile);
+        if (!wb.wait(p.status)) return false;
+        MMA_GROUP(mb, p.status, mma_issue(tb + R2, kop(As[q3], kW), kop(sm + SM_W, kW), kW, kW, true));
+      }
+    }
+  }
+  // ---- embedding adjoint: dG0 (R2) -> ds
+  if (!embed_h2(p, sm, m, tb, mb, wb, sm + SM_Q, sm + SM_K, nullptr)) return false;
+  load_G(sm + SM_G, 0, pb);
+  if (ngroups > 0 && !pb.wait(p.status)) return false;
+  __syncthreads();
+  for (int c = 0; c < kW; c += 32) {  // da3 = dG0 (1 - G0^2) -> P tile
+    float dg[32], g0[32];
+    tc::tmem_ld32(tb + lane_off + R2 + c, dg);
+#pragma unroll
+    for (int q = 0; q < 32; q += 8) load8(sm + SM_G, t, c + q, kW, g0 + q);
+#pragma unroll
+    for (int q = 0; q < 32; ++q) dg[q] = valid ? dg[q] * (1.f - g0[q] * g0[q]) : 0.f;
+#pragma unroll
+    for (int q = 0; q < 32; q += 8) store8(sm + SM_P, t, c + q, kW, dg + q);
+  }
+  tc::fence_before_sync();
+  const int tj = m->tj[t];
+  const int mask = m->mask;
+  for (int c = 0; c < p.e2; c += 8) {
+    float z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    store8(sm + SM_V, t, c, p.e2, z);
+  }
+  for (int sp = 0; sp < 32; ++sp) {  // da2 = (da3 W3^T) (1 - h2^2) -> V tile
+    if (!(mask & (1 << sp))) continue;
+    bulk_load(wb, sm + SM_W, p.W3R + (size_t)sp * p.e2 * kW * 2, p.e2 * kW * 2);
+    if (!wb.wait(p.status)) return false;
+    MMA_GROUP(mb, p.status, mma_issue(tb + R1, kop(sm + SM_P, kW), kop(sm + SM_W, kW), p.e2, kW, false));
+    const bool mine = tj == sp;
+    if (__any_sync(0xffffffffu, mine)) {
+      for (int c = 0; c < p.e2; c += 32) {
+        float v[32], h2[32];
+        tc::tmem_ld32(tb + lane_off + R1 + c, v);
+        if (mine) {
+#pragma unroll
+          for (int q = 0; q < 32; q += 8) load8(sm + SM_K, t, c + q, p.e2, h2 + q);
+#pragma unroll
+          for (int q = 0; q < 32; ++q) v[q] *= 1.f - h2[q] * h2[q];
+#pragma unroll
+          for (int q = 0; q < 32; q += 8) store8(sm + SM_V, t, c + q, p.e2, v + q);
+        }
+      }
+    }
+    tc::fence_before_sync();
+  }
+  float ds_emb = 0.f;
+  for (int sp = 0; sp < 32; ++sp) {  // da1 = (da2 W2^T) (1 - h1^2); ds = da1 . W1
+    if (!(mask & (1 << sp))) continue;
+    bulk_load(wb, sm + SM_W, p.W2R + (size_t)sp * p.e1 * p.e2 * 2, p.e1 * p.e2 * 2);
+    if (!wb.wait(p.status)) return false;
+    MMA_GROUP(mb, p.status, mma_issue(tb + R1, kop(sm + SM_V, p.e2), kop(sm + SM_W, p.e2), p.e1, p.e2, false));
+    const bool mine = tj == sp;
+    if (__any_sync(0xffffffffu, mine)) {
+      for (int c = 0; c < p.e1; c += 32) {
+        float v[32];
+        tc::tmem_ld32(tb + lane_off + R1 + c, v);
+        if (mine)
+          for (int q = 0; q < 32 && c + q < p.e1; q += 8) {
+            float h8[8];
+            load8(sm + SM_Q, t, c + q, p.e1, h8);   // h1 (16-bit copy from the H1 tile)
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+              ds_emb += v[q + e] * (1.f - h8[e] * h8[e]) * p.W1[sp * p.e1 + c + q + e];
+          }
+      }
+    }
+    tc::fence_before_sync();
+  }
+  // ---- environment adjoint: g_j
+  __syncthreads();
+  float* gout = p.g + ((size_t)atom * p.nmax + t) * 3;
+  if (t < p.nmax) {
+    if (!valid) {
+      gout[0] = gout[1] = gout[2] = 0.f;
+    } else {
+      const float d = m->d[t], s = m->s[t], sw = m->sw[t], dswr = m->dsw[t];
+      const float* rr = m->rh[t];
+      const float un = 1.f / kGradScale;   // the layer adjoints carry the seed scale
+      float dst = m->dRt[t][0] + ds_emb * un;
+      float dr[3];
+      for (int a = 0; a < 3; ++a) {
+        dst += m->dRt[t][1 + a] * rr[a];
+        dr[a] = (drow[a] + m->drc[t][a]) * un + s * m->dRt[t][1 + a];
+      }
+      const float radial = dst * (dswr / d - sw / (d * d)) + m->dswa[t] * un * dswr;
+      const float proj = dr[0] * rr[0] + dr[1] * rr[1] + dr[2] * rr[2];
+      for (int a = 0; a < 3; ++a) gout[a] = radial * rr[a] + (dr[a] - proj * rr[a]) / d;
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_af_bwd(Params p) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  Misc* m = reinterpret_cast<Misc*>(sm + SM_MISC);
+  kernel_prologue(m);
+  // constant operand: a ones row (column sums) and zero rows 3..15 of rhb
+  zero_smem(m->ones, 16 * kW * 2);
+  zero_smem(m->rhb, 16 * kW * 2);
+  __syncthreads();
+  *reinterpret_cast<op_t*>(m->ones + tc::kmajor_off(0, threadIdx.x, kW)) = f2op(1.f);
+  __syncthreads();
+  Bar mb{&m->bar, 0u}, wb{&m->wbar, 0u}, pb{&m->pbar, 0u};
+  for (int atom = blockIdx.x; atom < p.n; atom += gridDim.x)
+    if (!bwd_atom(p, atom, sm, m, m->tptr, mb, wb, pb)) break;
+  kernel_epilogue(m);
+}
+
+// ================================================================== fitting
+struct FitParams {
+  int n_tiles, kd, f1, f2, f3, kc1, kc2;
+  const int4* tiles;      // {species, start, count, 0}
+  const int* order;       // atoms grouped by species
+  const op_t* D;          // [n][kd]
+  // per species, chunked BF16 tiles (see host packing)
+  const uint8_t *F1T, *F2T, *F3T, *F3R, *F2R, *F1R;
+  size_t sF1T, sF2T, sF3T, sF3R, sF2R, sF1R;  // bytes per species
+  const float *c1, *c2, *c3, *F4, *c4;
+  double* atom_e;
+  float* dD;              // [n][kd]
+  int* status;
+};
+
+constexpr int FT_Y1 = 0;
+constexpr int FT_TILE = 128 * 256 * 2;  // room for K up to 256
+constexpr int FT_Y2 = FT_TILE, FT_Y3 = 2 * FT_TILE, FT_CA = 3 * FT_TILE;
+constexpr int FT_CB = FT_CA + 128 * 32 * 2;
+constexpr int FT_MISC = FT_CB + 256 * 48 * 2;
+constexpr int kSmemFit = FT_MISC + 64;
+
+// acc(128 x N, tmem col0) = A(tile, Kx = K) * B(chunks of kc columns, N rows)
+__device__ bool fit_product(uint8_t* sm, const uint8_t* A, int K, const uint8_t* Bchunks, int N,
+                            int kc, uint32_t tcol, Bar& mb, Bar& wb, int* status) {
+  for (int k0 = 0; k0 < K; k0 += kc) {
+    bulk_load(wb, sm + FT_CB, Bchunks + (size_t)(k0 / kc) * N * kc * 2, N * kc * 2);
+    if (!wb.wait(status)) return false;
+    MMA_GROUP(mb, status, mma_issue(tcol, kop(A, K, k0), kop(sm + FT_CB, kc), N, kc, k0 > 0));
+  }
+  return true;
+}
+
+__device__ bool fit_layer1(uint8_t* CA, uint8_t* CB, int kc, int N, bool acc, uint32_t tb, Bar& mb,
+                           int* status) {
+  MMA_GROUP(mb, status, mma_issue(tb, kop(CA, kc), kop(CB, kc), N, kc, acc));
+  return true;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_fit(FitParams p) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(sm + FT_MISC);
+  unsigned long long* wbar = reinterpret_cast<unsigned long long*>(sm + FT_MISC + 8);
+  uint32_t* tptr = reinterpret_cast<uint32_t*>(sm + FT_MISC + 16);
+  const int t = threadIdx.x, warp = t >> 5;
+  const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+  if (t == 0) {
+    tc::mbar_init(reinterpret_cast<uint64_t*>(bar), 1);
+    tc::mbar_init(reinterpret_cast<uint64_t*>(wbar), 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tptr, 512);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tb = *tptr;
+  Bar mb{bar, 0u}, wb{wbar, 0u};
+  bool ok = true;
+  uint8_t *Y1 = sm + FT_Y1, *Y2 = sm + FT_Y2, *Y3 = sm + FT_Y3, *CA = sm + FT_CA;
+  for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
+    const int4 td = p.tiles[tile];
+    const int sp = td.x;
+    const int atom = t < td.z ? p.order[td.y + t] : -1;
+    // ---- layer 1: D (gathered rows, K = kd in chunks of kc1) x F1
+    for (int k0 = 0; k0 < p.kd && ok; k0 += p.kc1) {
+      for (int c = 0; c < p.kc1; c += 8) {
+        uint4 u = make_uint4(0, 0, 0, 0);
+        if (atom >= 0) u = *reinterpret_cast<const uint4*>(p.D + (size_t)atom * p.kd + k0 + c);
+        *reinterpret_cast<uint4*>(CA + tc::kmajor_off(t, c, p.kc1)) = u;
+      }
+      bulk_load(wb, sm + FT_CB, p.F1T + sp * p.sF1T + (size_t)(k0 / p.kc1) * p.f1 * p.kc1 * 2,
+                p.f1 * p.kc1 * 2);
+      ok = wb.wait(p.status) && fit_layer1(CA, sm + FT_CB, p.kc1, p.f1, k0 > 0, tb, mb, p.status);
+    }
+    if (!ok) break;
+    // epilogue: y = tanh(acc + c) into a K-major tile
+    auto epi_tanh = [&](int N, const float* bias, uint8_t* Y) {
+      for (int c = 0; c < N; c += 32) {
+        float v[32];
+        tc::tmem_ld32(tb + lane_off + c, v);
+        for (int q = 0; q < 32; ++q) v[q] = (c + q < N) ? tanhf(v[q] + bias[sp * N + c + q]) : 0.f;
+        for (int q = 0; q < 32 && c + q < N; q += 8) store8(Y, t, c + q, N, v + q);
+      }
+    };
+    epi_tanh(p.f1, p.c1, Y1);
+    tc::fence_before_sync();
+    ok = fit_product(sm, Y1, p.f1, p.F2T + sp * p.sF2T, p.f2, p.kc2, tb, mb, wb, p.status);
+    if (!ok) break;
+    epi_tanh(p.f2, p.c2, Y2);
+    tc::fence_before_sync();
+    ok = fit_product(sm, Y2, p.f2, p.F3T + sp * p.sF3T, p.f3, p.kc2, tb, mb, wb, p.status);
+    if (!ok) break;
+    // y3, energy (FP64 sum) and delta3 = F4 (1 - y3^2) into Y3
+    {
+      double e = 0.0;
+      for (int c = 0; c < p.f3; c += 32) {
+        float v[32];
+        tc::tmem_ld32(tb + lane_off + c, v);
+        for (int q = 0; q < 32; ++q) {
+          if (c + q >= p.f3) { v[q] = 0.f; continue; }
+          float y = tanhf(v[q] + p.c3[sp * p.f3 + c + q]);
+          float w4 = p.F4[sp * p.f3 + c + q];
+          e += (double)y * (double)w4;
+          v[q] = w4 * (1.f - y * y);
+        }
+        for (int q = 0; q < 32 && c + q < p.f3; q += 8) store8(Y3, t, c + q, p.f3, v + q);
+      }
+      if (atom >= 0) p.atom_e[atom] = e + (double)p.c4[sp];
+    }
+    // backward: delta2 = (delta3 F3^T) (1 - y2^2), delta1 = (delta2 F2^T) (1 - y1^2)
+    auto epi_dtanh = [&](int N, uint8_t* Y) {
+      for (int c = 0; c < N; c += 32) {
+        float v[32];
+        tc::tmem_ld32(tb + lane_off + c, v);
+        for (int q = 0; q < 32 && c + q < N; q += 8) {
+          float y[8];
+          load8(Y, t, c + q, N, y);
+          for (int u = 0; u < 8; ++u) y[u] = v[q + u] * (1.f - y[u] * y[u]);
+          store8(Y, t, c + q, N, y);
+        }
+      }
+    };
+    ok = fit_product(sm, Y3, p.f3, p.F3R + sp * p.sF3R, p.f2, p.kc2, tb, mb, wb, p.status);
+    if (!ok) break;
+    epi_dtanh(p.f2, Y2);
+    tc::fence_before_sync();
+    ok = fit_product(sm, Y2, p.f2, p.F2R + sp * p.sF2R, p.f1, p.kc2, tb, mb, wb, p.status);
+    if (!ok) break;
+    epi_dtanh(p.f1, Y1);
+    tc::fence_before_sync();
+    // dE/dD = delta1 F1^T, 256 columns at a time
+    for (int nb = 0; nb < p.kd / 256 && ok; ++nb) {
+      ok = fit_product(sm, Y1, p.f1, p.F1R + sp * p.sF1R + (size_t)nb * 256 * p.f1 * 2, 256, p.kc2,
+                       tb, mb, wb, p.status);
+      if (!ok) break;
+      for (int c = 0; c < 256; c += 32) {
+        float v[32];
+        tc::tmem_ld32(tb + lane_off + c, v);
+        if (atom >= 0) {
+          float4* dst = reinterpret_cast<float4*>(p.dD + (size_t)atom * p.kd + nb * 256 + c);
+          for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+      }
+      tc::fence_before_sync();
+      __syncthreads();
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tb, 512);
+}
+
+// ================================================================== host side
+static uint16_t f2bf(double x) {
+#ifdef DP_FUSED_BF16
+  float f = (float)x;
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  if ((u & 0x7fffffffu) > 0x7f800000u) return 0x7fc0;
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+#else
+  __half h = __float2half_rn((float)x);
+  uint16_t u;
+  memcpy(&u, &h, 2);
+  return u;
+#endif
+}
+
+// Append the K-major core-matrix tile of M (R x K, element (r, k) = get(r, k))
+// to `out`, K split into chunks of kc columns (each chunk its own tile).
+template <typename Get>
+static void pack(std::vector<uint16_t>& out, int R, int K, int kc, Get get) {
+  for (int k0 = 0; k0 < K; k0 += kc) {
+    size_t base = out.size();
+    out.resize(base + (size_t)R * kc, 0);
+    for (int r = 0; r < R; ++r)
+      for (int k = 0; k < kc; ++k) {
+        size_t off = (((size_t)(r >> 3) * (kc >> 3)) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);
+        out[base + off] = f2bf(get(r, k0 + k));
+      }
+  }
+}
+
+class FusedAf : public Model {
+ public:
+  ~FusedAf() override {
+    for (void* q : allocs_) cudaFree(q);
+  }
+  int run(const NbrView& nv, const int* types, double* atom_e, cudaStream_t st) override {
+    return run_parts(nv, types, atom_e, st, 7);
+  }
+  int run_parts(const NbrView& nv, const int* types, double* atom_e, cudaStream_t st,
+                int parts) override {
+    Params p = base_;
+    p.sel_j = nv.sel_j;
+    p.sel_r = nv.sel_r;
+    p.types = types;
+    int k = 0;
+    if (parts & 1) {
+      k_af_fwd<<<grid_, kThreads, kSmemAtom, st>>>(p);
+      ++k;
+    }
+    if (parts & 2) {
+      FitParams f = fit_;
+      f.atom_e = atom_e;
+      k_fit<<<std::min(fit_.n_tiles, sms_), kThreads, kSmemFit, st>>>(f);
+      ++k;
+    }
+    if (parts & 4) {
+      k_af_bwd<<<grid_, kThreads, kSmemAtom, st>>>(p);
+      ++k;
+    }
+    return k;
+  }
+  const float* grad32() const override { return g_; }
+  size_t bytes() const override { return bytes_; }
+  // atoms grouped by species for the fitting kernel, tiles of <= 128 of one species
+  bool set_atoms(int n, const int* types) override {
+    if (n < 1 || n > cap_) return false;
+    std::vector<int> order;
+    std::vector<int4> tiles;
+    for (int t = 0; t < m_.n_species; ++t) {
+      int start = (int)order.size();
+      for (int i = 0; i < n; ++i)
+        if (types[i] == t) order.push_back(i);
+      int cnt = (int)order.size() - start;
+      for (int o = 0; o < cnt; o += 128) tiles.push_back(make_int4(t, start + o, std::min(128, cnt - o), 0));
+    }
+    if (cudaMemcpy(dorder_, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dtiles_, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return false;
+    n_ = n;
+    base_.n = n;
+    fit_.n_tiles = (int)tiles.size();
+    grid_ = std::min(n, sms_);
+    return true;
+  }
+  void bind_flags(int* flags) override {
+    base_.status = flags;
+    fit_.status = flags;
+  }
+
+  bool init(const AfDims& m, const double* w, int n_atoms, const int* types, std::string* err);
+
+ private:
+  template <typename T>
+  bool dalloc(T** p, size_t count, std::string* err) {
+    size_t b = sizeof(T) * (count ? count : 1);
+    cudaError_t e = cudaMalloc((void**)p, b);
+    if (e != cudaSuccess) {
+      *err = std::string("fused model: ") + cudaGetErrorString(e);
+      cudaGetLastError();
+      return false;
+    }
+    allocs_.push_back(*p);
+    bytes_ += b;
+    return true;
+  }
+  template <typename T>
+  bool upload(T** p, const std::vector<T>& v, std::string* err) {
+    if (!dalloc(p, v.size(), err)) return false;
+    if (cudaMemcpy(*p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+      *err = "fused model: weight upload failed";
+      return false;
+    }
+    return true;
+  }
+  AfDims m_{};
+  int n_ = 0, grid_ = 0, sms_ = 0, cap_ = 0;
+  int4* dtiles_ = nullptr;
+  int* dorder_ = nullptr;
+  Params base_{};
+  FitParams fit_{};
+  float* g_ = nullptr;
+  std::vector<void*> allocs_;
+  size_t bytes_ = 0;
+};
+
+bool FusedAf::init(const AfDims& m, const double* w, int n_atoms, const int* types, std::string* err) {
+  m_ = m;
+  n_ = n_atoms;
+  const int S = m.n_species, L = m.n_layers, E1 = m.e1, E2 = m.e2, H = m.hidden;
+  const int KD = kW * m.m2;
+  // ---- walk the blob
+  size_t off = 0;
+  auto at = [&](size_t o) { return w[o]; };
+  std::vector<size_t> oW1(S), ob1(S), oW2(S), ob2(S), oW3(S), ob3(S);
+  for (int t = 0; t < S; ++t) {
+    oW1[t] = off; off += E1;
+    ob1[t] = off; off += E1;
+    oW2[t] = off; off += (size_t)E1 * E2;
+    ob2[t] = off; off += E2;
+    oW3[t] = off; off += (size_t)E2 * kW;
+    ob3[t] = off; off += kW;
+  }
+  std::vector<size_t> oq(L), ok(L), ov(L), oo(L), obo(L);
+  for (int l = 0; l < L; ++l) {
+    oq[l] = off; off += (size_t)kW * H;
+    ok[l] = off; off += (size_t)kW * H;
+    ov[l] = off; off += (size_t)kW * H;
+    oo[l] = off; off += (size_t)H * kW;
+    obo[l] = off; off += kW;
+  }
+  std::vector<size_t> oF1(S), oc1(S), oF2(S), oc2(S), oF3(S), oc3(S), oF4(S), oc4(S);
+  for (int t = 0; t < S; ++t) {
+    oF1[t] = off; off += (size_t)KD * m.f1;
+    oc1[t] = off; off += m.f1;
+    oF2[t] = off; off += (size_t)m.f1 * m.f2;
+    oc2[t] = off; off += m.f2;
+    oF3[t] = off; off += (size_t)m.f2 * m.f3;
+    oc3[t] = off; off += m.f3;
+    oF4[t] = off; off += m.f3;
+    oc4[t] = off; off += 1;
+  }
+  // ---- pack tiles
+  std::vector<uint16_t> W2T, W3T, W2R, W3R, WqT, WkT, WvT, WoT, WqR, WkR, WvR, WoR;
+  std::vector<float> W1, b1, b2, b3, bo;
+  for (int t = 0; t < S; ++t) {
+    pack(W2T, E2, E1, E1, [&](int r, int k) { return at(oW2[t] + (size_t)k * E2 + r); });
+    pack(W3T, kW, E2, E2, [&](int r, int k) { return at(oW3[t] + (size_t)k * kW + r); });
+    pack(W2R, E1, E2, E2, [&](int r, int k) { return at(oW2[t] + (size_t)r * E2 + k); });
+    pack(W3R, E2, kW, kW, [&](int r, int k) { return at(oW3[t] + (size_t)r * kW + k); });
+    for (int k = 0; k < E1; ++k) {
+      W1.push_back((float)at(oW1[t] + k));
+      b1.push_back((float)at(ob1[t] + k));
+    }
+    for (int k = 0; k < E2; ++k) b2.push_back((float)at(ob2[t] + k));
+    for (int k = 0; k < kW; ++k) b3.push_back((float)at(ob3[t] + k));
+  }
+  for (int l = 0; l < L; ++l) {
+    pack(WqT, H, kW, kW, [&](int r, int k) { return at(oq[l] + (size_t)k * H + r); });
+    pack(WkT, H, kW, kW, [&](int r, int k) { return at(ok[l] + (size_t)k * H + r); });
+    pack(WvT, H, kW, kW, [&](int r, int k) { return at(ov[l] + (size_t)k * H + r); });
+    pack(WoT, kW, H, H, [&](int r, int k) { return at(oo[l] + (size_t)k * kW + r); });
+    pack(WqR, kW, H, H, [&](int r, int k) { return at(oq[l] + (size_t)r * H + k); });
+    pack(WkR, kW, H, H, [&](int r, int k) { return at(ok[l] + (size_t)r * H + k); });
+    pack(WvR, kW, H, H, [&](int r, int k) { return at(ov[l] + (size_t)r * H + k); });
+    pack(WoR, H, kW, kW, [&](int r, int k) { return at(oo[l] + (size_t)r * kW + k); });
+    for (int k = 0; k < kW; ++k) bo.push_back((float)at(obo[l] + k));
+  }
+  // fitting: chunk widths kc1 for K = KD, kc2 for K = f
+  const int kc1 = 32;
+  const int kc2 = (m.f1 % 48 == 0 && m.f2 % 48 == 0 && m.f3 % 48 == 0) ? 48 : 16;
+  std::vector<uint16_t> F1T, F2T, F3T, F3R, F2R, F1R;
+  std::vector<float> c1, c2, c3, F4, c4;
+  for (int t = 0; t < S; ++t) {
+    pack(F1T, m.f1, KD, kc1, [&](int r, int k) { return at(oF1[t] + (size_t)k * m.f1 + r); });
+    pack(F2T, m.f2, m.f1, kc2, [&](int r, int k) { return at(oF2[t] + (size_t)k * m.f2 + r); });
+    pack(F3T, m.f3, m.f2, kc2, [&](int r, int k) { return at(oF3[t] + (size_t)k * m.f3 + r); });
+    pack(F3R, m.f2, m.f3, kc2, [&](int r, int k) { return at(oF3[t] + (size_t)r * m.f3 + k); });
+    pack(F2R, m.f1, m.f2, kc2, [&](int r, int k) { return at(oF2[t] + (size_t)r * m.f2 + k); });
+    for (int nb = 0; nb < KD / 256; ++nb)
+      pack(F1R, 256, m.f1, kc2,
+           [&](int r, int k) { return at(oF1[t] + (size_t)(nb * 256 + r) * m.f1 + k); });
+    for (int k = 0; k < m.f1; ++k) c1.push_back((float)at(oc1[t] + k));
+    for (int k = 0; k < m.f2; ++k) c2.push_back((float)at(oc2[t] + k));
+    for (int k = 0; k < m.f3; ++k) {
+      c3.push_back((float)at(oc3[t] + k));
+      F4.push_back((float)at(oF4[t] + k));
+    }
+    c4.push_back((float)at(oc4[t]));
+  }
+  Params& p = base_;
+  p.n = n_atoms; p.nmax = m.nmax; p.e1 = E1; p.e2 = E2; p.m2 = m.m2; p.n_layers = L;
+  p.heads = m.heads; p.dh = H / m.heads;
+  p.rs = (float)m.rs; p.rc = (float)m.rc; p.inv_nmax = 1.f / m.nmax;
+  p.inv_sqrt_d = 1.f / sqrtf((float)p.dh);
+  uint16_t *dW2T, *dW3T, *dW2R, *dW3R, *dWqT, *dWkT, *dWvT, *dWoT, *dWqR, *dWkR, *dWvR, *dWoR;
+  float *dW1, *db1, *db2, *db3, *dbo;
+  bool good = upload(&dW2T, W2T, err) && upload(&dW3T, W3T, err) && upload(&dW2R, W2R, err) &&
+              upload(&dW3R, W3R, err) && upload(&dW1, W1, err) && upload(&db1, b1, err) &&
+              upload(&db2, b2, err) && upload(&db3, b3, err);
+  if (good && L > 0)
+    good = upload(&dWqT, WqT, err) && upload(&dWkT, WkT, err) && upload(&dWvT, WvT, err) &&
+           upload(&dWoT, WoT, err) && upload(&dWqR, WqR, err) && upload(&dWkR, WkR, err) &&
+           upload(&dWvR, WvR, err) && upload(&dWoR, WoR, err) && upload(&dbo, bo, err);
+  if (!good) return false;
+  p.W2T = (const uint8_t*)dW2T; p.W3T = (const uint8_t*)dW3T;
+  p.W2R = (const uint8_t*)dW2R; p.W3R = (const uint8_t*)dW3R;
+  if (L > 0) {
+    p.WqT = (const uint8_t*)dWqT; p.WkT = (const uint8_t*)dWkT; p.WvT = (const uint8_t*)dWvT;
+    p.WoT = (const uint8_t*)dWoT; p.WqR = (const uint8_t*)dWqR; p.WkR = (const uint8_t*)dWkR;
+    p.WvR = (const uint8_t*)dWvR; p.WoR = (const uint8_t*)dWoR; p.bo = dbo;
+  }
+  p.W1 = dW1; p.b1 = db1; p.b2 = db2; p.b3 = db3;
+  size_t N = n_atoms;
+  if (!dalloc(&p.Gst, N * (L + 1) * kTile, err) || !dalloc(&p.rstd, N * (L > 0 ? L : 1) * kW, err) ||
+      !dalloc(&p.smx, N * (L > 0 ? L : 1) * m.heads * kW, err) ||
+      !dalloc(&p.D, N * KD, err) || !dalloc(&p.Tm, N * 4 * kW, err) ||
+      !dalloc(&g_, N * m.nmax * 3, err) || !dalloc(&p.status, 1, err))
+    return false;
+  float* ddD;
+  if (!dalloc(&ddD, N * KD, err)) return false;
+  p.dD = ddD;
+  p.g = g_;
+  cudaMemset(p.status, 0, sizeof(int));
+  // fitting tiles (capacity for any atom set up to n_atoms): see set_atoms
+  FitParams& f = fit_;
+  f.kd = KD; f.f1 = m.f1; f.f2 = m.f2; f.f3 = m.f3;
+  f.kc1 = kc1; f.kc2 = kc2;
+  cap_ = n_atoms;
+  if (!dalloc(&dtiles_, (size_t)n_atoms / 128 + S + 1, err) || !dalloc(&dorder_, (size_t)n_atoms, err))
+    return false;
+  uint16_t *dF1T, *dF2T, *dF3T, *dF3R, *dF2R, *dF1R;
+  float *dc1, *dc2, *dc3, *dF4, *dc4;
+  good = upload(&dF1T, F1T, err) &&
+         upload(&dF2T, F2T, err) && upload(&dF3T, F3T, err) && upload(&dF3R, F3R, err) &&
+         upload(&dF2R, F2R, err) && upload(&dF1R, F1R, err) && upload(&dc1, c1, err) &&
+         upload(&dc2, c2, err) && upload(&dc3, c3, err) && upload(&dF4, F4, err) && upload(&dc4, c4, err);
+  if (!good) return false;
+  f.tiles = dtiles_; f.order = dorder_; f.D = p.D;
+  f.F1T = (const uint8_t*)dF1T; f.F2T = (const uint8_t*)dF2T; f.F3T = (const uint8_t*)dF3T;
+  f.F3R = (const uint8_t*)dF3R; f.F2R = (const uint8_t*)dF2R; f.F1R = (const uint8_t*)dF1R;
+  f.sF1T = F1T.size() * 2 / S; f.sF2T = F2T.size() * 2 / S; f.sF3T = F3T.size() * 2 / S;
+  f.sF3R = F3R.size() * 2 / S; f.sF2R = F2R.size() * 2 / S; f.sF1R = F1R.size() * 2 / S;
+  f.c1 = dc1; f.c2 = dc2; f.c3 = dc3; f.F4 = dF4; f.c4 = dc4;
+  f.dD = ddD;
+  f.status = p.status;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms_, cudaDevAttrMultiProcessorCount, dev);
+  if (!set_atoms(n_atoms, types)) {
+    *err = "fused model: fitting tiles upload failed";
+    return false;
+  }
+  if (cudaFuncSetAttribute(k_af_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemAtom) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_af_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemAtom) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemFit) !=
+          cudaSuccess) {
+    *err = "fused model: shared-memory configuration failed";
+    return false;
+  }
+  return true;
+}
+
+}  // namespace fz
 
 bool fused_af_supported(const AfDims& m, std::string* why) {
-  (void)m;
-  *why = "fused BF16 path not built yet";
-  return false;
+  if (m.m1 != 128 || m.hidden != 128) { *why = "fused path needs m1 = hidden = 128"; return false; }
+  if (m.heads != 4) { *why = "fused path needs 4 heads of width 32"; return false; }
+  if (m.e1 % 16 || m.e2 % 16 || m.e1 > 64 || m.e2 > 128) { *why = "fused path needs e1 (<= 64) and e2 (<= 128) multiples of 16"; return false; }
+  if (m.nmax > 128) { *why = "fused path needs nmax <= 128"; return false; }
+  if ((128 * m.m2) % 256) { *why = "fused path needs 128 * m2 to be a multiple of 256"; return false; }
+  if (m.f1 % 16 || m.f2 % 16 || m.f3 % 16 || m.f1 > 256 || m.f2 > 256 || m.f3 > 256) { *why = "fused path needs fitting widths multiples of 16 and <= 256"; return false; }
+  if (m.n_species > 32) { *why = "fused path supports at most 32 species"; return false; }
+  return true;
 }
 
 Model* make_fused_af(const AfDims& m, const double* weights, int n_atoms, const int* types_host,
                      std::string* err) {
-  (void)m; (void)weights; (void)n_atoms; (void)types_host;
-  *err = "fused BF16 path not built yet";
-  return nullptr;
+  if (!fused_af_supported(m, err)) return nullptr;
+  auto* f = new fz::FusedAf();
+  if (!f->init(m, weights, n_atoms, types_host, err)) {
+    delete f;
+    return nullptr;
+  }
+  return f;
 }
 
 }  // namespace dp

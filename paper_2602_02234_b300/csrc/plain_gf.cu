@@ -1,0 +1,746 @@
+// Plain (unfused) graph-family potential, FP32 / FP64, one simple kernel per
+// operation.  The paper (Sec. II) describes DPA3 as a GNN whose line-graph
+// series carries bond and angle representations; the library's reading:
+//
+//   init   n_i = W_type[t_i];  e_ip = tanh(s_ip w_e + b_e),  s = sw(r)/r
+//   layer  (a) u = n Wm;  m_i = (1/nmax) sum_p sw_ip (e_ip * u_j);
+//              n_i <- n_i + tanh([n_i, m_i] Wn + bn)
+//          (b) e_ip <- e_ip + tanh(n_i Wa + n_j Wb + e_ip Wc + be)
+//          (c) q = e Wp; for the angle slots p (r < rca, at most na, nearest):
+//              a_ip = sum_l Wphi[l] * (1/na) sum_{k != p} swa_ip swa_ik P_l(c_pk) q_ik
+//              e_ip <- e_ip + swa_ip tanh(a_ip Wq + bq)
+//   energy e_i = fitting_{t_i}(n_i)
+//
+// and the hand-written adjoint.  Gradients that flow to a neighbour's node
+// (through u_j and n_j Wb) are gathered over the neighbour's incoming slots
+// in a fixed order (skin list + mirror index), so results are reproducible.
+#include <math.h>
+
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "common.cuh"
+#include "gemm.cuh"
+#include "kernels.cuh"
+#include "model.h"
+
+namespace dp {
+namespace gf {
+
+// ------------------------------------------------------------------ kernels
+// geometry of every slot: distance, switches, s = sw/r, unit vector
+template <typename T>
+__global__ void k_env(long long P, int nmax, int na, const int* __restrict__ sel_j,
+                      const double* __restrict__ sel_r, double rs, double rc, double rsa,
+                      double rca, T* __restrict__ d, T* __restrict__ sw, T* __restrict__ dsw,
+                      T* __restrict__ sa, T* __restrict__ dsa, T* __restrict__ s,
+                      T* __restrict__ rh) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= P) return;
+  int p = (int)(e % nmax);
+  if (sel_j[e] < 0) {
+    d[e] = T(1); sw[e] = dsw[e] = sa[e] = dsa[e] = s[e] = T(0);
+    rh[3 * e] = rh[3 * e + 1] = rh[3 * e + 2] = T(0);
+    return;
+  }
+  double r[3] = {sel_r[3 * e], sel_r[3 * e + 1], sel_r[3 * e + 2]};
+  double dd = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+  T a, b;
+  smooth_switch((T)dd, (T)rs, (T)rc, &a, &b);
+  d[e] = (T)dd; sw[e] = a; dsw[e] = b; s[e] = a / (T)dd;
+  for (int q = 0; q < 3; ++q) rh[3 * e + q] = (T)(r[q] / dd);
+  if (dd < rca && p < na) {
+    smooth_switch((T)dd, (T)rsa, (T)rca, &a, &b);
+    sa[e] = a; dsa[e] = b;
+  } else {
+    sa[e] = dsa[e] = T(0);
+  }
+}
+
+template <typename T>
+__global__ void k_init(int n, int nmax, int nd, int ed, const int* __restrict__ types,
+                       const int* __restrict__ sel_j, const T* __restrict__ s,
+                       const T* __restrict__ Wt, const T* __restrict__ we,
+                       const T* __restrict__ be0, T* __restrict__ node, T* __restrict__ edge) {
+  int i = blockIdx.x;
+  for (int c = threadIdx.x; c < nd; c += blockDim.x) node[(size_t)i * nd + c] = Wt[types[i] * nd + c];
+  for (int idx = threadIdx.x; idx < nmax * ed; idx += blockDim.x) {
+    int p = idx / ed, c = idx % ed;
+    size_t e = (size_t)i * nmax + p;
+    edge[e * ed + c] = sel_j[e] >= 0 ? dtanh(s[e] * we[c] + be0[c]) : T(0);
+  }
+}
+
+// m_i = (1/nmax) sum_p sw_ip e_ip * u_j(p); one block per atom
+template <typename T>
+__global__ void k_msg(int nmax, int ed, T inv_nmax, const int* __restrict__ sel_j,
+                      const T* __restrict__ sw, const T* __restrict__ edge,
+                      const T* __restrict__ u, T* __restrict__ m) {
+  int i = blockIdx.x;
+  for (int c = threadIdx.x; c < ed; c += blockDim.x) {
+    T acc = T(0);
+    for (int p = 0; p < nmax; ++p) {
+      size_t e = (size_t)i * nmax + p;
+      int j = sel_j[e];
+      if (j < 0) break;
+      acc += sw[e] * edge[e * ed + c] * u[(size_t)j * ed + c];
+    }
+    m[(size_t)i * ed + c] = acc * inv_nmax;
+  }
+}
+
+template <typename T>
+__global__ void k_add(long long n, const T* __restrict__ a, const T* __restrict__ b,
+                      T* __restrict__ out) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a[i] + b[i];
+}
+
+template <typename T>
+__global__ void k_copy(long long n, const T* __restrict__ a, T* __restrict__ out) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a[i];
+}
+
+// (b): v = tanh(A_i + B_j + C_e + be), e1 = e + v on real slots
+template <typename T>
+__global__ void k_edge(long long P, int nmax, int ed, const int* __restrict__ sel_j,
+                       const T* __restrict__ Ai, const T* __restrict__ Bj,
+                       const T* __restrict__ Ce, const T* __restrict__ be,
+                       const T* __restrict__ e_in, T* __restrict__ v, T* __restrict__ e1) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= P * ed) return;
+  long long e = idx / ed;
+  int c = (int)(idx % ed);
+  int j = sel_j[e];
+  if (j < 0) {
+    v[idx] = T(0);
+    e1[idx] = T(0);
+    return;
+  }
+  long long i = e / nmax;
+  T y = dtanh(Ai[i * ed + c] + Bj[(long long)j * ed + c] + Ce[idx] + be[c]);
+  v[idx] = y;
+  e1[idx] = e_in[idx] + y;
+}
+
+__device__ __forceinline__ void legendre4(float c, float* P, float* dP) {
+  P[0] = 1.f; P[1] = c; P[2] = 0.5f * (3.f * c * c - 1.f); P[3] = 0.5f * (5.f * c * c * c - 3.f * c);
+  dP[0] = 0.f; dP[1] = 1.f; dP[2] = 3.f * c; dP[3] = 0.5f * (15.f * c * c - 3.f);
+}
+__device__ __forceinline__ void legendre4(double c, double* P, double* dP) {
+  P[0] = 1.0; P[1] = c; P[2] = 0.5 * (3.0 * c * c - 1.0); P[3] = 0.5 * (5.0 * c * c * c - 3.0 * c);
+  dP[0] = 0.0; dP[1] = 1.0; dP[2] = 3.0 * c; dP[3] = 0.5 * (15.0 * c * c - 3.0);
+}
+
+constexpr int kMaxNa = 64;
+
+// number of angle slots of atom i (a prefix of the nearest-first list)
+template <typename T>
+__device__ int n_angle(const T* sa, long long base, int nmax, int na) {
+  int k = 0;
+  while (k < na && k < nmax && sa[base + k] > T(0)) ++k;
+  return k;
+}
+
+// (c) forward: a_ip for the angle slots of one atom (block per atom)
+template <typename T>
+__global__ void k_angle(int nmax, int na, int ed, T inv_na, const T* __restrict__ sa,
+                        const T* __restrict__ rh, const T* __restrict__ q,
+                        const T* __restrict__ Wphi, T* __restrict__ a) {
+  extern __shared__ unsigned char sm_raw[];
+  T* coef = reinterpret_cast<T*>(sm_raw);  // na x na x 4
+  int i = blockIdx.x;
+  long long base = (long long)i * nmax;
+  int nang = n_angle(sa, base, nmax, na);
+  for (int pk = threadIdx.x; pk < nang * nang; pk += blockDim.x) {
+    int p = pk / nang, k = pk % nang;
+    T P[4], dP[4];
+    const T* rp = rh + 3 * (base + p);
+    const T* rk = rh + 3 * (base + k);
+    legendre4(rp[0] * rk[0] + rp[1] * rk[1] + rp[2] * rk[2], P, dP);
+    T w = (p == k) ? T(0) : inv_na * sa[base + p] * sa[base + k];
+    for (int l = 0; l < 4; ++l) coef[(p * nang + k) * 4 + l] = w * P[l];
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < nmax * ed; idx += blockDim.x) {
+    int p = idx / ed, c = idx % ed;
+    T acc = T(0);
+    if (p < nang)
+      for (int k = 0; k < nang; ++k) {
+        T qk = q[(base + k) * ed + c];
+        const T* cf = coef + (p * nang + k) * 4;
+        acc += (Wphi[c] * cf[0] + Wphi[ed + c] * cf[1] + Wphi[2 * ed + c] * cf[2] +
+                Wphi[3 * ed + c] * cf[3]) * qk;
+      }
+    a[(base + p) * ed + c] = acc;
+  }
+}
+
+// e_out = e1 + swa * t on angle slots
+template <typename T>
+__global__ void k_angle_out(long long P, int ed, const T* __restrict__ sa, const T* __restrict__ e1,
+                            const T* __restrict__ t, T* __restrict__ out) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= P * ed) return;
+  out[idx] = e1[idx] + sa[idx / ed] * t[idx];
+}
+
+// e_i = y3 . F4 + c4 (FP64) and delta3
+template <typename T>
+__global__ void k_fit_out(int n, int f3, const int* __restrict__ types, const T* __restrict__ y3,
+                          const T* __restrict__ F4, const T* __restrict__ c4,
+                          double* __restrict__ atom_e, T* __restrict__ d3) {
+  long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (wid >= n) return;
+  int a = (int)wid, t = types[a];
+  double acc = 0.0;
+  for (int b = lane; b < f3; b += 32) {
+    T y = y3[(long long)a * f3 + b], w = F4[t * f3 + b];
+    acc += (double)y * (double)w;
+    d3[(long long)a * f3 + b] = w * (T(1) - y * y);
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) atom_e[a] = acc + (double)c4[t];
+}
+
+// ------------------------------------------------------------------ adjoint kernels
+// (c): dsa += de . t, dz = de * swa * (1 - t^2) on angle slots
+template <typename T>
+__global__ void k_angle_out_bwd(long long P, int ed, const T* __restrict__ sa,
+                                const T* __restrict__ t, const T* __restrict__ de,
+                                T* __restrict__ dz, T* __restrict__ dsa_e) {
+  long long e = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (e >= P) return;
+  T s = sa[e];
+  T acc = T(0);
+  for (int c = lane; c < ed; c += 32) {
+    T tv = t[e * ed + c], g = de[e * ed + c];
+    acc += g * tv;
+    dz[e * ed + c] = g * s * (T(1) - tv * tv);
+  }
+  acc = warp_sum(acc);
+  if (lane == 0 && s > T(0)) dsa_e[e] += acc;
+}
+
+// (c) adjoint of a_ip: dq, and the switch / unit-vector terms; block per atom
+template <typename T>
+__global__ void k_angle_bwd(int nmax, int na, int ed, T inv_na, const T* __restrict__ sa,
+                            const T* __restrict__ rh, const T* __restrict__ q,
+                            const T* __restrict__ Wphi, const T* __restrict__ da,
+                            T* __restrict__ dq, T* __restrict__ dsa_e, T* __restrict__ drh) {
+  extern __shared__ unsigned char sm_raw[];
+  T* dcoef = reinterpret_cast<T*>(sm_raw);  // na x na x 4
+  int i = blockIdx.x;
+  long long base = (long long)i * nmax;
+  int nang = n_angle(sa, base, nmax, na);
+  // dq_k[c] = sum_{p != k} sum_l Wphi[l][c] coef_pkl da_p[c]
+  for (int idx = threadIdx.x; idx < nmax * ed; idx += blockDim.x) {
+    int k = idx / ed, c = idx % ed;
+    T acc = T(0);
+    if (k < nang) {
+      const T* rk = rh + 3 * (base + k);
+      for (int p = 0; p < nang; ++p) {
+        if (p == k) continue;
+        const T* rp = rh + 3 * (base + p);
+        T P[4], dP[4];
+        legendre4(rp[0] * rk[0] + rp[1] * rk[1] + rp[2] * rk[2], P, dP);
+        T w = inv_na * sa[base + p] * sa[base + k];
+        T f = Wphi[c] * P[0] + Wphi[ed + c] * P[1] + Wphi[2 * ed + c] * P[2] + Wphi[3 * ed + c] * P[3];
+        acc += w * f * da[(base + p) * ed + c];
+      }
+    }
+    dq[(base + k) * ed + c] = acc;
+  }
+  // dcoef_pkl = sum_c da_p[c] Wphi[l][c] q_k[c]  (one warp per (p, k))
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int pk = warp; pk < nang * nang; pk += nw) {
+    int p = pk / nang, k = pk % nang;
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    if (p != k)
+      for (int c = lane; c < ed; c += 32) {
+        T x = da[(base + p) * ed + c] * q[(base + k) * ed + c];
+        for (int l = 0; l < 4; ++l) acc[l] += x * Wphi[l * ed + c];
+      }
+    for (int l = 0; l < 4; ++l) {
+      acc[l] = warp_sum(acc[l]);
+      if (lane == 0) dcoef[pk * 4 + l] = acc[l];
+    }
+  }
+  __syncthreads();
+  // switch and unit-vector terms, one thread per angle slot p (fixed order)
+  for (int p = threadIdx.x; p < nang; p += blockDim.x) {
+    const T* rp = rh + 3 * (base + p);
+    T dsp = T(0), dr[3] = {T(0), T(0), T(0)};
+    for (int k = 0; k < nang; ++k) {
+      if (k == p) continue;
+      const T* rk = rh + 3 * (base + k);
+      T P[4], dP[4];
+      legendre4(rp[0] * rk[0] + rp[1] * rk[1] + rp[2] * rk[2], P, dP);
+      // p as the first index (dcoef_pk) and as the second (dcoef_kp)
+      const T* d1 = dcoef + (p * nang + k) * 4;
+      const T* d2 = dcoef + (k * nang + p) * 4;
+      T sk = sa[base + k], sp = sa[base + p];
+      T dc = T(0);
+      for (int l = 0; l < 4; ++l) {
+        dsp += (d1[l] + d2[l]) * inv_na * sk * P[l];
+        dc += (d1[l] + d2[l]) * inv_na * sp * sk * dP[l];
+      }
+      for (int a = 0; a < 3; ++a) dr[a] += dc * rk[a];
+    }
+    dsa_e[base + p] += dsp;
+    for (int a = 0; a < 3; ++a) drh[3 * (base + p) + a] += dr[a];
+  }
+}
+
+// (b): dy = de1 (1 - v^2) on real slots
+template <typename T>
+__global__ void k_dtanh(long long n, const T* __restrict__ g, const T* __restrict__ y,
+                        T* __restrict__ out) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = g[i] * (T(1) - y[i] * y[i]);
+}
+
+// per atom: sum over its own slots (rows of dy)
+template <typename T>
+__global__ void k_rowsum(int nmax, int ed, const T* __restrict__ x, T* __restrict__ out) {
+  int i = blockIdx.x;
+  for (int c = threadIdx.x; c < ed; c += blockDim.x) {
+    T acc = T(0);
+    for (int p = 0; p < nmax; ++p) acc += x[((size_t)i * nmax + p) * ed + c];
+    out[(size_t)i * ed + c] = acc;
+  }
+}
+
+// per atom j: sum of x over every kept slot (i, p) whose neighbour is j,
+// visited in skin-list order (deterministic)
+template <typename T>
+__global__ void k_gather_in(int nmax, int ed, int cap, const SkinEntry* __restrict__ skin,
+                            const int* __restrict__ skin_cnt, const int* __restrict__ mirror,
+                            const short* __restrict__ selpos, const T* __restrict__ x,
+                            T* __restrict__ out) {
+  int j = blockIdx.x;
+  int cnt = skin_cnt[j];
+  for (int c = threadIdx.x; c < ed; c += blockDim.x) {
+    T acc = T(0);
+    for (int s = 0; s < cnt; ++s) {
+      size_t o = (size_t)j * cap + s;
+      int mc = mirror[o];
+      if (mc < 0) continue;
+      int i = skin[o].j;
+      int p = selpos[(size_t)i * cap + mc];
+      if (p < 0) continue;
+      acc += x[((size_t)i * nmax + p) * ed + c];
+    }
+    out[(size_t)j * ed + c] = acc;
+  }
+}
+
+// (a) per slot: de += (1/nmax) sw dm_i * u_j;  X = (1/nmax) sw dm_i * e (for du_j);
+// dsw += (1/nmax) sum_c dm_i e u_j
+template <typename T>
+__global__ void k_msg_bwd(long long P, int nmax, int ed, int ldm, T inv_nmax,
+                          const int* __restrict__ sel_j, const T* __restrict__ sw,
+                          const T* __restrict__ e, const T* __restrict__ u,
+                          const T* __restrict__ dm, T* __restrict__ de, T* __restrict__ X,
+                          T* __restrict__ dsw_e) {
+  long long s = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (s >= P) return;
+  int j = sel_j[s];
+  long long i = s / nmax;
+  T acc = T(0);
+  for (int c = lane; c < ed; c += 32) {
+    if (j < 0) {
+      X[s * ed + c] = T(0);
+      continue;
+    }
+    T g = dm[i * ldm + c], ev = e[s * ed + c], uv = u[(long long)j * ed + c];
+    de[s * ed + c] += inv_nmax * sw[s] * g * uv;
+    X[s * ed + c] = inv_nmax * sw[s] * g * ev;
+    acc += g * ev * uv;
+  }
+  acc = warp_sum(acc);
+  if (lane == 0 && j >= 0) dsw_e[s] += inv_nmax * acc;
+}
+
+// dn = dn1 + dnm[:, :nd]
+template <typename T>
+__global__ void k_add_strided(int n, int nd, int ld, const T* __restrict__ a, const T* __restrict__ b,
+                              T* __restrict__ out) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)n * nd) return;
+  long long i = idx / nd;
+  int c = (int)(idx % nd);
+  out[idx] = a[idx] + b[i * ld + c];
+}
+
+// edge init adjoint and the final pair gradient g = dE/dr
+template <typename T>
+__global__ void k_pair_grad(long long P, int nmax, int ed, int atom0, const int* __restrict__ sel_j,
+                            const T* __restrict__ d, const T* __restrict__ sw,
+                            const T* __restrict__ dsw, const T* __restrict__ dsa,
+                            const T* __restrict__ rh, const T* __restrict__ e0,
+                            const T* __restrict__ we, const T* __restrict__ de,
+                            const T* __restrict__ dsw_e, const T* __restrict__ dsa_e,
+                            const T* __restrict__ drh, T* __restrict__ g) {
+  long long s = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (s >= P) return;
+  if (sel_j[s] < 0) {
+    if (lane < 3) g[3 * s + lane] = T(0);
+    return;
+  }
+  T ds = T(0);
+  for (int c = lane; c < ed; c += 32) {
+    T ev = e0[s * ed + c];
+    ds += de[s * ed + c] * (T(1) - ev * ev) * we[c];
+  }
+  ds = warp_sum(ds);
+  if (lane != 0) return;
+  T dd = d[s];
+  T radial = ds * (dsw[s] / dd - sw[s] / (dd * dd)) + dsw_e[s] * dsw[s] + dsa_e[s] * dsa[s];
+  const T* r = rh + 3 * s;
+  const T* dr = drh + 3 * s;
+  T proj = dr[0] * r[0] + dr[1] * r[1] + dr[2] * r[2];
+  for (int a = 0; a < 3; ++a) g[3 * s + a] = radial * r[a] + (dr[a] - proj * r[a]) / dd;
+  (void)atom0;
+  (void)nmax;
+}
+
+template <typename T>
+__global__ void k_fill(long long n, T v, T* __restrict__ p) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+// ------------------------------------------------------------------ host side
+template <typename T>
+class PlainGf : public Model {
+ public:
+  ~PlainGf() override {
+    for (void* p : allocs_) cudaFree(p);
+  }
+  bool init(const GfDims& m, const double* w, int n_atoms, const int* types, std::string* err);
+  int run(const NbrView& nv, const int* types, double* atom_e, cudaStream_t st) override;
+  const float* grad32() const override { return grad_as<float>(); }
+  const double* grad64() const override { return grad_as<double>(); }
+  size_t bytes() const override { return bytes_; }
+
+ private:
+  template <typename U>
+  const U* grad_as() const {
+    if constexpr (std::is_same<T, U>::value) return g_;
+    else return nullptr;
+  }
+  template <typename U>
+  bool dalloc(U** p, size_t count, std::string* err) {
+    size_t b = sizeof(U) * (count ? count : 1);
+    cudaError_t e = cudaMalloc((void**)p, b);
+    if (e != cudaSuccess) {
+      *err = std::string("graph model: ") + cudaGetErrorString(e);
+      cudaGetLastError();
+      return false;
+    }
+    allocs_.push_back(*p);
+    bytes_ += b;
+    return true;
+  }
+  bool upload(T** p, const double* src, size_t count, std::string* err) {
+    if (!dalloc(p, count, err)) return false;
+    std::vector<T> h(src, src + count);
+    return cudaMemcpy(*p, h.data(), sizeof(T) * count, cudaMemcpyHostToDevice) == cudaSuccess;
+  }
+  GfDims m_{};
+  int n_ = 0;
+  long long P_ = 0;
+  // weights
+  T *Wt_, *we_, *be0_;
+  std::vector<T*> Wm_, Wn_, bn_, Wa_, Wb_, Wc_, be_, Wp_, Wphi_, Wq_, bq_;
+  std::vector<T*> F1_, c1_, F2_, c2_, F3_, c3_;
+  T *F4_, *c4_;
+  int* fit_rows_;
+  std::vector<std::pair<int, int>> fit_ranges_;
+  // geometry
+  T *d_, *sw_, *dsw_, *sa_, *dsa_, *s_, *rh_;
+  // states
+  std::vector<T*> nn_, ee_, e1_, hh_, uu_, mm_, vv_, qq_, tt_;
+  T *Ai_, *Bj_, *Ce_, *aa_;
+  T *y1_, *y2_, *y3_, *d1_, *d2_, *d3_;
+  // adjoint
+  T *dn_, *dn1_, *de_, *de1_, *dy_, *dz_, *da_, *dq_, *du_, *dx_, *dnm_, *X_, *sdy_, *gat_;
+  T *dsw_e_, *dsa_e_, *drh_, *g_;
+  std::vector<void*> allocs_;
+  size_t bytes_ = 0;
+};
+
+template <typename T>
+bool PlainGf<T>::init(const GfDims& m, const double* w, int n_atoms, const int* types,
+                      std::string* err) {
+  m_ = m;
+  n_ = n_atoms;
+  const int Nd = m.nd, Ed = m.ed, L = m.n_layers, S = m.n_species, NM = m.nmax;
+  P_ = (long long)n_atoms * NM;
+  size_t off = 0;
+  auto take = [&](T** p, size_t cnt) {
+    bool ok = upload(p, w + off, cnt, err);
+    off += cnt;
+    return ok;
+  };
+  bool ok = take(&Wt_, (size_t)S * Nd) && take(&we_, Ed) && take(&be0_, Ed);
+  Wm_.resize(L); Wn_.resize(L); bn_.resize(L); Wa_.resize(L); Wb_.resize(L); Wc_.resize(L);
+  be_.resize(L); Wp_.resize(L); Wphi_.resize(L); Wq_.resize(L); bq_.resize(L);
+  for (int l = 0; l < L && ok; ++l)
+    ok = take(&Wm_[l], (size_t)Nd * Ed) && take(&Wn_[l], (size_t)(Nd + Ed) * Nd) &&
+         take(&bn_[l], Nd) && take(&Wa_[l], (size_t)Nd * Ed) && take(&Wb_[l], (size_t)Nd * Ed) &&
+         take(&Wc_[l], (size_t)Ed * Ed) && take(&be_[l], Ed) && take(&Wp_[l], (size_t)Ed * Ed) &&
+         take(&Wphi_[l], 4 * (size_t)Ed) && take(&Wq_[l], (size_t)Ed * Ed) && take(&bq_[l], Ed);
+  F1_.resize(S); c1_.resize(S); F2_.resize(S); c2_.resize(S); F3_.resize(S); c3_.resize(S);
+  std::vector<double> F4, c4;
+  for (int t = 0; t < S && ok; ++t) {
+    ok = take(&F1_[t], (size_t)Nd * m.f1) && take(&c1_[t], m.f1) &&
+         take(&F2_[t], (size_t)m.f1 * m.f2) && take(&c2_[t], m.f2) &&
+         take(&F3_[t], (size_t)m.f2 * m.f3) && take(&c3_[t], m.f3);
+    F4.insert(F4.end(), w + off, w + off + m.f3);
+    off += m.f3;
+    c4.push_back(w[off]);
+    off += 1;
+  }
+  if (!ok || !upload(&F4_, F4.data(), F4.size(), err) || !upload(&c4_, c4.data(), c4.size(), err))
+    return false;
+  // fitting row groups
+  std::vector<int> rows;
+  fit_ranges_.assign(S, {0, 0});
+  for (int t = 0; t < S; ++t) {
+    int start = (int)rows.size();
+    for (int i = 0; i < n_atoms; ++i)
+      if (types[i] == t) rows.push_back(i);
+    fit_ranges_[t] = {start, (int)rows.size() - start};
+  }
+  if (!dalloc(&fit_rows_, rows.size(), err)) return false;
+  if (!rows.empty()) cudaMemcpy(fit_rows_, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice);
+  const size_t N = n_atoms, P = P_;
+  ok = dalloc(&d_, P, err) && dalloc(&sw_, P, err) && dalloc(&dsw_, P, err) &&
+       dalloc(&sa_, P, err) && dalloc(&dsa_, P, err) && dalloc(&s_, P, err) &&
+       dalloc(&rh_, 3 * P, err);
+  nn_.resize(L + 1); ee_.resize(L + 1);
+  e1_.resize(L); hh_.resize(L); uu_.resize(L); mm_.resize(L); vv_.resize(L); qq_.resize(L); tt_.resize(L);
+  for (int l = 0; l <= L && ok; ++l) ok = dalloc(&nn_[l], N * Nd, err) && dalloc(&ee_[l], P * Ed, err);
+  for (int l = 0; l < L && ok; ++l)
+    ok = dalloc(&e1_[l], P * Ed, err) && dalloc(&hh_[l], N * Nd, err) && dalloc(&uu_[l], N * Ed, err) &&
+         dalloc(&mm_[l], N * Ed, err) && dalloc(&vv_[l], P * Ed, err) && dalloc(&qq_[l], P * Ed, err) &&
+         dalloc(&tt_[l], P * Ed, err);
+  const int angle_smem = (int)(sizeof(T) * m.na * m.na * 4);
+  if (cudaFuncSetAttribute(k_angle<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, angle_smem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_angle_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, angle_smem) !=
+          cudaSuccess) {
+    *err = "graph model: angle kernels cannot get their shared memory";
+    return false;
+  }
+  ok = ok && dalloc(&Ai_, N * Ed, err) && dalloc(&Bj_, N * Ed, err) && dalloc(&Ce_, P * Ed, err) &&
+       dalloc(&aa_, P * Ed, err) && dalloc(&y1_, N * m.f1, err) && dalloc(&y2_, N * m.f2, err) &&
+       dalloc(&y3_, N * m.f3, err) && dalloc(&d1_, N * m.f1, err) && dalloc(&d2_, N * m.f2, err) &&
+       dalloc(&d3_, N * m.f3, err) && dalloc(&dn_, N * Nd, err) && dalloc(&dn1_, N * Nd, err) &&
+       dalloc(&de_, P * Ed, err) && dalloc(&de1_, P * Ed, err) && dalloc(&dy_, P * Ed, err) &&
+       dalloc(&dz_, P * Ed, err) && dalloc(&da_, P * Ed, err) && dalloc(&dq_, P * Ed, err) &&
+       dalloc(&du_, N * Ed, err) && dalloc(&dx_, N * Nd, err) && dalloc(&dnm_, N * (Nd + Ed), err) &&
+       dalloc(&X_, P * Ed, err) && dalloc(&sdy_, N * Ed, err) && dalloc(&gat_, N * Ed, err) &&
+       dalloc(&dsw_e_, P, err) && dalloc(&dsa_e_, P, err) && dalloc(&drh_, 3 * P, err) &&
+       dalloc(&g_, 3 * P, err);
+  return ok;
+}
+
+template <typename T>
+int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStream_t st) {
+  const GfDims& m = m_;
+  const int Nd = m.nd, Ed = m.ed, L = m.n_layers, NM = m.nmax, NA = m.na, S = m.n_species, n = n_;
+  const long long P = P_, PE = P * Ed;
+  const T inv_nmax = T(1) / T(NM), inv_na = T(1) / T(NA);
+  int k = 0;
+  auto grid = [](long long n_) { return ceil_div(n_, 256); };
+  k_env<T><<<grid(P), 256, 0, st>>>(P, NM, NA, nv.sel_j, nv.sel_r, m.rs, m.rc, m.rsa, m.rca, d_, sw_,
+                                     dsw_, sa_, dsa_, s_, rh_);
+  k_init<T><<<n, 128, 0, st>>>(n, NM, Nd, Ed, types, nv.sel_j, s_, Wt_, we_, be0_, nn_[0], ee_[0]);
+  k += 2;
+  const size_t angle_smem = sizeof(T) * NA * NA * 4;
+  for (int l = 0; l < L; ++l) {
+    // (a)
+    gemm(gemm_rowmajor<T>(n, Ed, Nd, nn_[l], Nd, Wm_[l], Ed, uu_[l], Ed), 1, st);
+    k_msg<T><<<n, 64, 0, st>>>(NM, Ed, inv_nmax, nv.sel_j, sw_, ee_[l], uu_[l], mm_[l]);
+    {
+      Gemm<T> g = gemm_rowmajor<T>(n, Nd, Nd, nn_[l], Nd, Wn_[l], Nd, hh_[l], Nd);
+      g.bias = bn_[l];
+      gemm(g, 1, st);
+      g = gemm_rowmajor<T>(n, Nd, Ed, mm_[l], Ed, Wn_[l] + (size_t)Nd * Nd, Nd, hh_[l], Nd);
+      g.beta = T(1);
+      g.epi = 1;
+      gemm(g, 1, st);
+    }
+    k_add<T><<<grid((long long)n * Nd), 256, 0, st>>>((long long)n * Nd, nn_[l], hh_[l], nn_[l + 1]);
+    // (b)
+    gemm(gemm_rowmajor<T>(n, Ed, Nd, nn_[l + 1], Nd, Wa_[l], Ed, Ai_, Ed), 1, st);
+    gemm(gemm_rowmajor<T>(n, Ed, Nd, nn_[l + 1], Nd, Wb_[l], Ed, Bj_, Ed), 1, st);
+    gemm(gemm_rowmajor<T>((int)P, Ed, Ed, ee_[l], Ed, Wc_[l], Ed, Ce_, Ed), 1, st);
+    k_edge<T><<<grid(PE), 256, 0, st>>>(P, NM, Ed, nv.sel_j, Ai_, Bj_, Ce_, be_[l], ee_[l], vv_[l],
+                                        e1_[l]);
+    // (c)
+    gemm(gemm_rowmajor<T>((int)P, Ed, Ed, e1_[l], Ed, Wp_[l], Ed, qq_[l], Ed), 1, st);
+    k_angle<T><<<n, 256, angle_smem, st>>>(NM, NA, Ed, inv_na, sa_, rh_, qq_[l], Wphi_[l], aa_);
+    {
+      Gemm<T> g = gemm_rowmajor<T>((int)P, Ed, Ed, aa_, Ed, Wq_[l], Ed, tt_[l], Ed);
+      g.bias = bq_[l];
+      g.epi = 1;
+      gemm(g, 1, st);
+    }
+    k_angle_out<T><<<grid(PE), 256, 0, st>>>(P, Ed, sa_, e1_[l], tt_[l], ee_[l + 1]);
+    k += 14;
+  }
+  // fitting
+  for (int t = 0; t < S; ++t) {
+    auto rg = fit_ranges_[t];
+    if (rg.second == 0) continue;
+    const int* rws = fit_rows_ + rg.first;
+    Gemm<T> g = gemm_rowmajor<T>(rg.second, m.f1, Nd, nn_[L], Nd, F1_[t], m.f1, y1_, m.f1);
+    g.a_rows = rws; g.c_rows = rws; g.bias = c1_[t]; g.epi = 1;
+    gemm(g, 1, st);
+    g = gemm_rowmajor<T>(rg.second, m.f2, m.f1, y1_, m.f1, F2_[t], m.f2, y2_, m.f2);
+    g.a_rows = rws; g.c_rows = rws; g.bias = c2_[t]; g.epi = 1;
+    gemm(g, 1, st);
+    g = gemm_rowmajor<T>(rg.second, m.f3, m.f2, y2_, m.f2, F3_[t], m.f3, y3_, m.f3);
+    g.a_rows = rws; g.c_rows = rws; g.bias = c3_[t]; g.epi = 1;
+    gemm(g, 1, st);
+    k += 3;
+  }
+  k_fit_out<T><<<ceil_div((long long)n * 32, 256), 256, 0, st>>>(n, m.f3, types, y3_, F4_, c4_, atom_e, d3_);
+  for (int t = 0; t < S; ++t) {
+    auto rg = fit_ranges_[t];
+    if (rg.second == 0) continue;
+    const int* rws = fit_rows_ + rg.first;
+    Gemm<T> g{};
+    g.M = rg.second; g.N = m.f2; g.K = m.f3;
+    g.A = d3_; g.a_rm = m.f3; g.a_rk = 1;
+    g.B = F3_[t]; g.b_rk = 1; g.b_rn = m.f3;
+    g.C = d2_; g.c_rm = m.f2; g.c_rn = 1; g.nb2 = 1;
+    g.a_rows = rws; g.c_rows = rws; g.alpha = T(1); g.epi = 2; g.aux = y2_;
+    gemm(g, 1, st);
+    g.N = m.f1; g.K = m.f2; g.A = d2_; g.a_rm = m.f2; g.B = F2_[t]; g.b_rn = m.f2;
+    g.C = d1_; g.c_rm = m.f1; g.aux = y1_;
+    gemm(g, 1, st);
+    g.N = Nd; g.K = m.f1; g.A = d1_; g.a_rm = m.f1; g.B = F1_[t]; g.b_rn = m.f1;
+    g.C = dn_; g.c_rm = Nd; g.epi = 0; g.aux = nullptr;
+    gemm(g, 1, st);
+    k += 3;
+  }
+  // ---- adjoint through the layers
+  k_fill<T><<<grid(PE), 256, 0, st>>>(PE, T(0), de_);
+  k_fill<T><<<grid(P), 256, 0, st>>>(P, T(0), dsw_e_);
+  k_fill<T><<<grid(P), 256, 0, st>>>(P, T(0), dsa_e_);
+  k_fill<T><<<grid(3 * P), 256, 0, st>>>(3 * P, T(0), drh_);
+  k += 5;
+  for (int l = L - 1; l >= 0; --l) {
+    // (c)
+    k_copy<T><<<grid(PE), 256, 0, st>>>(PE, de_, de1_);
+    k_angle_out_bwd<T><<<grid(P * 32), 256, 0, st>>>(P, Ed, sa_, tt_[l], de_, dz_, dsa_e_);
+    {  // da = dz Wq^T
+      Gemm<T> g{};
+      g.M = (int)P; g.N = Ed; g.K = Ed;
+      g.A = dz_; g.a_rm = Ed; g.a_rk = 1;
+      g.B = Wq_[l]; g.b_rk = 1; g.b_rn = Ed;
+      g.C = da_; g.c_rm = Ed; g.c_rn = 1; g.nb2 = 1; g.alpha = T(1);
+      gemm(g, 1, st);
+    }
+    k_angle_bwd<T><<<n, 256, angle_smem, st>>>(NM, NA, Ed, inv_na, sa_, rh_, qq_[l], Wphi_[l], da_,
+                                               dq_, dsa_e_, drh_);
+    {  // de1 += dq Wp^T
+      Gemm<T> g{};
+      g.M = (int)P; g.N = Ed; g.K = Ed;
+      g.A = dq_; g.a_rm = Ed; g.a_rk = 1;
+      g.B = Wp_[l]; g.b_rk = 1; g.b_rn = Ed;
+      g.C = de1_; g.c_rm = Ed; g.c_rn = 1; g.nb2 = 1; g.alpha = T(1); g.beta = T(1);
+      gemm(g, 1, st);
+    }
+    // (b)
+    k_dtanh<T><<<grid(PE), 256, 0, st>>>(PE, de1_, vv_[l], dy_);
+    k_copy<T><<<grid(PE), 256, 0, st>>>(PE, de1_, de_);
+    {  // de += dy Wc^T
+      Gemm<T> g{};
+      g.M = (int)P; g.N = Ed; g.K = Ed;
+      g.A = dy_; g.a_rm = Ed; g.a_rk = 1;
+      g.B = Wc_[l]; g.b_rk = 1; g.b_rn = Ed;
+      g.C = de_; g.c_rm = Ed; g.c_rn = 1; g.nb2 = 1; g.alpha = T(1); g.beta = T(1);
+      gemm(g, 1, st);
+    }
+    k_rowsum<T><<<n, 64, 0, st>>>(NM, Ed, dy_, sdy_);
+    k_gather_in<T><<<n, 64, 0, st>>>(NM, Ed, nv.cap, nv.skin, nv.skin_cnt, nv.mirror, nv.selpos, dy_, gat_);
+    k_copy<T><<<grid((long long)n * Nd), 256, 0, st>>>((long long)n * Nd, dn_, dn1_);
+    {  // dn1 += sdy Wa^T + gat Wb^T
+      Gemm<T> g{};
+      g.M = n; g.N = Nd; g.K = Ed;
+      g.A = sdy_; g.a_rm = Ed; g.a_rk = 1;
+      g.B = Wa_[l]; g.b_rk = 1; g.b_rn = Ed;
+      g.C = dn1_; g.c_rm = Nd; g.c_rn = 1; g.nb2 = 1; g.alpha = T(1); g.beta = T(1);
+      gemm(g, 1, st);
+      g.A = gat_; g.B = Wb_[l];
+      gemm(g, 1, st);
+    }
+    // (a)
+    k_dtanh<T><<<grid((long long)n * Nd), 256, 0, st>>>((long long)n * Nd, dn1_, hh_[l], dx_);
+    {  // dnm = dx Wn^T  (n x (Nd + Ed))
+      Gemm<T> g{};
+      g.M = n; g.N = Nd + Ed; g.K = Nd;
+      g.A = dx_; g.a_rm = Nd; g.a_rk = 1;
+      g.B = Wn_[l]; g.b_rk = 1; g.b_rn = Nd;
+      g.C = dnm_; g.c_rm = Nd + Ed; g.c_rn = 1; g.nb2 = 1; g.alpha = T(1);
+      gemm(g, 1, st);
+    }
+    k_add_strided<T><<<grid((long long)n * Nd), 256, 0, st>>>(n, Nd, Nd + Ed, dn1_, dnm_, dn_);
+    k_msg_bwd<T><<<grid(P * 32), 256, 0, st>>>(P, NM, Ed, Nd + Ed, inv_nmax, nv.sel_j, sw_, ee_[l],
+                                               uu_[l], dnm_ + Nd, de_, X_, dsw_e_);
+    k_gather_in<T><<<n, 64, 0, st>>>(NM, Ed, nv.cap, nv.skin, nv.skin_cnt, nv.mirror, nv.selpos, X_, du_);
+    {  // dn += du Wm^T
+      Gemm<T> g{};
+      g.M = n; g.N = Nd; g.K = Ed;
+      g.A = du_; g.a_rm = Ed; g.a_rk = 1;
+      g.B = Wm_[l]; g.b_rk = 1; g.b_rn = Ed;
+      g.C = dn_; g.c_rm = Nd; g.c_rn = 1; g.nb2 = 1; g.alpha = T(1); g.beta = T(1);
+      gemm(g, 1, st);
+    }
+    k += 18;
+  }
+  k_pair_grad<T><<<grid(P * 32), 256, 0, st>>>(P, NM, Ed, 0, nv.sel_j, d_, sw_, dsw_, dsa_, rh_, ee_[0],
+                                               we_, de_, dsw_e_, dsa_e_, drh_, g_);
+  return k + 1;
+}
+
+}  // namespace gf
+
+size_t gf_weight_count(const GfDims& m) {
+  size_t Nd = m.nd, Ed = m.ed, S = m.n_species;
+  size_t t = S * Nd + 2 * Ed;
+  t += (size_t)m.n_layers * (Nd * Ed + (Nd + Ed) * Nd + Nd + 2 * Nd * Ed + Ed * Ed + Ed + Ed * Ed +
+                             4 * Ed + Ed * Ed + Ed);
+  t += S * (Nd * m.f1 + m.f1 + (size_t)m.f1 * m.f2 + m.f2 + (size_t)m.f2 * m.f3 + m.f3 + m.f3 + 1);
+  return t;
+}
+
+Model* make_plain_gf(const GfDims& m, bool f64, const double* weights, int n_atoms,
+                     const int* types_host, std::string* err) {
+  if (m.na > gf::kMaxNa) {
+    *err = "graph model supports at most 64 angle neighbours";
+    return nullptr;
+  }
+  if (f64) {
+    auto* p = new gf::PlainGf<double>();
+    if (!p->init(m, weights, n_atoms, types_host, err)) { delete p; return nullptr; }
+    return p;
+  }
+  auto* p = new gf::PlainGf<float>();
+  if (!p->init(m, weights, n_atoms, types_host, err)) { delete p; return nullptr; }
+  return p;
+}
+
+}  // namespace dp

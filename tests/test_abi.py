@@ -62,7 +62,7 @@ int main(void) {
 
 @pytest.mark.parametrize("model", [CF.WATER64_MODEL, CF.ATTN_MODEL])
 def test_weight_count_matches_oracle(model):
-    for prec in (dp.PREC_PLAIN_F64, dp.PREC_PLAIN_F32, dp.PREC_FUSED_BF16):
+    for prec in (dp.PREC_PLAIN_F64, dp.PREC_PLAIN_F32, dp.PREC_FUSED):
         assert dp.weight_count(dp.model_desc(model, prec)) == oracle.af_weight_count(model)
 
 

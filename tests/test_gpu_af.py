@@ -4,7 +4,7 @@ Tolerances (from the model's arithmetic; force RMS = RMS of the oracle's force
 components over the atoms compared):
   plain FP64:  |dF| <= 1e-10 * F_rms, |dE| <= 1e-11 |E|   (rounding order only)
   plain FP32:  |dF| <= 1e-4 * F_rms                          (FP32 throughout)
-  fused BF16:  |dF| <= 2e-2 * F_rms                          (BF16 GEMM operands)
+  fused:       |dF| <= 2e-2 * F_rms, |dE| <= 1e-3 |E|        (16-bit tensor-core operands)
 Integer work (neighbour indices and images) is compared exactly.
 """
 from dataclasses import replace
@@ -18,8 +18,8 @@ from synth import configs as C, maxwell_boltzmann, normal_blob, serving_system, 
 
 pytestmark = pytest.mark.gpu
 
-TOL_F = {dp.PREC_PLAIN_F64: 1e-10, dp.PREC_PLAIN_F32: 1e-4, dp.PREC_FUSED_BF16: 2e-2}
-TOL_E = {dp.PREC_PLAIN_F64: 1e-11, dp.PREC_PLAIN_F32: 2e-5, dp.PREC_FUSED_BF16: 5e-3}
+TOL_F = {dp.PREC_PLAIN_F64: 1e-10, dp.PREC_PLAIN_F32: 1e-4, dp.PREC_FUSED: 2e-2}
+TOL_E = {dp.PREC_PLAIN_F64: 1e-11, dp.PREC_PLAIN_F32: 2e-5, dp.PREC_FUSED: 1e-3}
 
 
 def weights(model, seed=C.WEIGHT_SEED):
@@ -107,7 +107,7 @@ def _sampled_parity(prec, sample_seed=3, n_sample=8):
     return F[sample], Fo, ae, ae_o, E
 
 
-@pytest.mark.parametrize("prec", [dp.PREC_PLAIN_F32])
+@pytest.mark.parametrize("prec", [dp.PREC_PLAIN_F32, dp.PREC_FUSED])
 def test_protein24k_sampled_parity(prec):
     F, Fo, ae, ae_o, E = _sampled_parity(prec)
     assert np.isfinite(E)
@@ -188,3 +188,50 @@ def test_errors_are_reported_not_raised_on_device():
     # the context stays usable
     E, F, V = pot.compute(s.coords)
     assert np.isfinite(E)
+
+
+# ------------------------------------------------------------------ fused path
+def test_fused_full_system_vs_oracle():
+    """Every atom of a 700-atom protein-in-water box (configuration-2 model)."""
+    m, s = C.ATTN_MODEL, serving_system(700, 9)
+    pot, w = make(m, s, dp.PREC_FUSED)
+    E, F, V = pot.compute(s.coords)
+    Eo, aeo, Fo, Vo = oracle.af_compute(m, w, s.types, s.coords, s.box)
+    assert abs(E - Eo) <= TOL_E[dp.PREC_FUSED] * abs(Eo)
+    assert np.max(np.abs(F - Fo)) <= TOL_F[dp.PREC_FUSED] * frms(Fo)
+    assert np.max(np.abs(V - Vo)) <= TOL_F[dp.PREC_FUSED] * np.linalg.norm(Vo)
+    assert np.max(np.abs(F.sum(0))) < 1e-10
+
+
+def test_fused_vs_plain_full_size():
+    """All 24,000 atoms against the FP32 path (itself pinned to the oracle)."""
+    m, s = C.ATTN_MODEL, C.protein24k()
+    fused, w = make(m, s, dp.PREC_FUSED)
+    plain, _ = make(m, s, dp.PREC_PLAIN_F32, w=w)
+    E, F, V = fused.compute(s.coords)
+    Ep, Fp, Vp = plain.compute(s.coords)
+    assert abs(E - Ep) <= TOL_E[dp.PREC_FUSED] * abs(Ep)
+    assert np.max(np.abs(F - Fp)) <= TOL_F[dp.PREC_FUSED] * frms(Fp)
+
+
+def test_fused_unsupported_sizes_are_refused():
+    m, s = C.WATER64_MODEL, C.water64()      # m1 = 100: not a fused shape
+    with pytest.raises(dp.DPError) as e:
+        make(m, s, dp.PREC_FUSED)
+    assert e.value.code == dp.DP_ERR_UNSUPPORTED
+
+
+def test_fused_md_tracks_plain():
+    m, s = C.ATTN_MODEL, serving_system(700, 9)
+    masses = s.masses
+    v0 = maxwell_boltzmann(masses[s.types], 300.0, C.VELOCITY_SEED)
+    out = {}
+    for prec in (dp.PREC_PLAIN_F32, dp.PREC_FUSED):
+        pot, _ = make(m, s, prec, masses=masses)
+        x, v = s.coords.copy(), v0.copy()
+        tr = pot.step(20, C.DT_FS, coords=x, vel=v, energies=True)
+        out[prec] = (x, tr)
+    dx = np.max(np.abs(out[dp.PREC_FUSED][0] - out[dp.PREC_PLAIN_F32][0]))
+    assert dx < 1e-4                      # 10 fs of dynamics with ~1 % force noise
+    et = out[dp.PREC_FUSED][1].sum(1)
+    assert np.all(np.isfinite(et)) and np.max(np.abs(et - et[0])) < 1e-3 * abs(et[0])
