@@ -179,6 +179,41 @@ def cpu_baseline(seconds=12.0):
                       f"(energy + pair gradients per atom, FP64, OpenMP)"}
 
 
+# ------------------------------------------------------------------ serving
+def serving_bench(n_req, seed=7, load=0.9, n_steps=50):
+    """Continuous batching of independent systems (sizes log-uniform 96..6000,
+    50 MD steps each): capacity with every request queued at once, then a
+    Poisson-arrival run at `load` times that capacity.  Returns p50/p99 tick
+    (step) latency, request latency and aggregate atom-steps/s."""
+    import paper_2602_02234_b300 as dp
+    from paper_2602_02234_b300 import serve
+    from synth import serving_requests
+
+    model = CF.ATTN_MODEL
+    desc = dp.model_desc(model, dp.PREC_FUSED, skin=CF.SKIN, rebuild_every=CF.REBUILD_EVERY)
+    w = normal_blob(dp.weight_count(desc), CF.WEIGHT_SEED)
+    reqs = serving_requests(n_req, 0.0, seed, n_steps=n_steps)
+    masses = reqs[0].system.masses
+    vels = [maxwell_boltzmann(masses[r.system.types], 300.0, CF.VELOCITY_SEED + k)
+            for k, r in enumerate(reqs)]
+    mean_atoms = float(np.mean([r.system.n for r in reqs]))
+    srv = dp.Server(desc, w, masses, max_slots=64, dt_fs=CF.DT_FS)
+    _, st_cap = serve.run(srv, reqs, vels)
+    srv.close()
+    capacity = st_cap["atom_steps"] / st_cap["wall_s"]
+    rate = load * capacity / (mean_atoms * n_steps)
+    reqs = serving_requests(n_req, rate, seed, n_steps=n_steps)
+    srv = dp.Server(desc, w, masses, max_slots=64, dt_fs=CF.DT_FS)
+    _, st = serve.run(srv, reqs, vels)
+    srv.close()
+    return {"requests": n_req, "steps_per_request": n_steps, "offered_load": load,
+            "arrival_rate_per_s": rate, "capacity_atom_steps_per_s": capacity,
+            "p50_step_ms": st["p50_tick_ms"], "p99_step_ms": st["p99_tick_ms"],
+            "request_p50_ms": st["request_p50_ms"], "request_p99_ms": st["request_p99_ms"],
+            "atom_steps_per_s": st["atom_steps"] / st["wall_s"], "max_resident": st["max_resident"],
+            "sizes": "log-uniform 96..6000 atoms, water below 600, 6.25 % blob above"}
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -326,6 +361,8 @@ def run_ours(args, rank, world, local_rank):
                       "ms_per_step": results[name]["ms"] / K}
     if "fused_f16" in results and "plain_f32" in results:
         line["fused_vs_plain"] = results["plain_f32"]["ms"] / results["fused_f16"]["ms"]
+    if rank == 0 and args.serving > 0 and args.system == "protein24k":
+        line["serving"] = serving_bench(args.serving)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.system == "protein24k":
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if rank == 0:
@@ -347,6 +384,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=48)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving", type=int, default=48,
+                    help="requests in the continuous-batching measurement (0: skip)")
     ap.add_argument("--system", choices=["protein24k", "small"], default="protein24k",
                     help="small: 4,800-atom box of the same recipe, for profiler captures")
     args = ap.parse_args()

@@ -225,6 +225,12 @@ const char* dp_server_last_error(const dp_server* srv);
 int dp_selftest_mma(int n, int k, int a_mn, int b_mn, int swap, const float* A, const float* B,
                     float* D);
 
+/* Diagnostics (no paper counterpart): the bounded device-side wait of the
+ * fused kernels, on an mbarrier that is never completed, polled at most
+ * max_polls (1..2^20) times.  Returns DP_ERR_TIMEOUT when the wait ran out and
+ * the kernel returned normally (the expected outcome). */
+int dp_selftest_timeout(long long max_polls);
+
 /* Neighbour lists of one small periodic system without any device allocation.
  * The paper has no counterpart: it is for callers that cannot allocate device
  * memory (an MD engine that owns the allocator or has spent its memory budget,

@@ -111,6 +111,7 @@ def lib():
         L.dp_noalloc_last_error.argtypes = []
         L.dp_noalloc_last_error.restype = C.c_char_p
         L.dp_selftest_mma.argtypes = [i, i, i, i, i, vp, vp, vp]
+        L.dp_selftest_timeout.argtypes = [C.c_longlong]
         L.dp_server_create.argtypes = [C.POINTER(vp), C.POINTER(ModelDesc), vp, vp, C.c_size_t, i,
                                        C.c_longlong, C.c_size_t, d, vp]
         L.dp_server_capacity.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]

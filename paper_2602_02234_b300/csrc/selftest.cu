@@ -130,3 +130,33 @@ extern "C" int dp_selftest_mma(int n, int k, int a_mn, int b_mn, int swap, const
   cudaFree(dS);
   return rc;
 }
+
+// A bounded wait that is made to run out: an mbarrier that nothing arrives on,
+// polled max_polls times by every thread, exactly as the fused kernels wait
+// for their tensor-core products and bulk copies.  The kernel records the
+// timeout in a status word and returns normally.
+__global__ void k_selftest_timeout(long long max_polls, int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    dp::tc::mbar_init(&bar, 1);
+    dp::tc::fence_mbar_init();
+  }
+  __syncthreads();
+  bool ok = dp::tc::mbar_wait(&bar, 0, max_polls);
+  ok = __syncthreads_and(ok) != 0;
+  if (!ok && threadIdx.x == 0) atomicOr(status, dp::kFlagTimeout);
+}
+
+extern "C" int dp_selftest_timeout(long long max_polls) {
+  if (max_polls < 1 || max_polls > (1LL << 20)) return DP_ERR_ARG;
+  int* d = nullptr;
+  if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return DP_ERR_OOM;
+  cudaMemset(d, 0, sizeof(int));
+  k_selftest_timeout<<<1, 128>>>(max_polls, d);
+  int st = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&st, d, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return DP_ERR_CUDA;
+  return (st & dp::kFlagTimeout) ? DP_ERR_TIMEOUT : DP_OK;
+}

@@ -32,3 +32,12 @@ def test_tcgen05_product(n, k, a_mn, b_mn):
         assert e.code == dp.DP_ERR_ARG      # shapes the self-test cannot stage safely
         pytest.skip("shape not stageable in the self-test buffers")
     assert np.max(np.abs(D - ref)) <= 1e-5 * k
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """A wait that nothing completes gives DP_ERR_TIMEOUT (no trap, no hang);
+    the device stays usable afterwards."""
+    assert dp.lib().dp_selftest_timeout(4096) == dp.DP_ERR_TIMEOUT
+    A = bf16(np.ones((128, 16)))
+    B = bf16(np.ones((16, 16)))
+    assert np.allclose(dp.selftest_mma(A, B), 16.0)
