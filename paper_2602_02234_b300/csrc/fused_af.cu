@@ -6,7 +6,8 @@
 //
 //   k_af_fwd   one CTA per SM, persistent over atoms; per atom the 128
 //              neighbour slots are the 128 rows of every tile.  Environment
-//              and softmax in FP32 registers (thread = row), every matrix
+//              and softmax in FP32 registers (several threads per row, each
+//              owning 32-column chunks of it), every matrix
 //              product a tcgen05.mma from shared-memory BF16 tiles into
 //              FP32 tensor memory.  Writes the descriptor D (BF16), T (FP32),
 //              the layer inputs G_l (BF16 tiles) and LayerNorm 1/sigma.
@@ -58,11 +59,24 @@ __device__ __forceinline__ op_t f2op(float v) { return __float2half_rn(v); }
 #endif
 constexpr float kGradScale = 4096.f;
 
-constexpr int kW = 128;        // embedding / attention width and rows per atom tile
-constexpr int kThreads = 128;
+constexpr int kW = 128;          // embedding / attention width and rows per atom tile
+constexpr int kThreads = 256;    // per-atom kernels: two threads per neighbour row
+constexpr int kFitThreads = 128; // fitting kernel: one thread per atom row
 constexpr long long kPolls = 1LL << 22;
 constexpr uint32_t R0 = 0, R1 = 128, R2 = 256, R3 = 384;
-constexpr int kTile = kW * kW * 2;  // one 128 x 128 BF16 tile: 32 KB
+constexpr int kTile = kW * kW * 2;  // one 128 x 128 16-bit tile: 32 KB
+
+// Thread roles of the per-atom kernels.  Thread t serves neighbour row
+// r = t mod 128, which is tensor-memory lane r (warp t/32 reads lane quarter
+// (t/32) mod 4), and half h = t / 128 of that row's columns: the 32-column
+// chunks starting at 32h and 32h + 64.  Interleaving the chunks spreads the
+// empty columns past the last real neighbour over both halves.  Row sums
+// over all columns combine the two partial sums through `partner`.
+__device__ __forceinline__ int row_id() { return threadIdx.x & (kW - 1); }
+__device__ __forceinline__ int half_id() { return threadIdx.x >> 7; }
+__device__ __forceinline__ uint32_t lane_base() {
+  return (uint32_t)(32 * ((threadIdx.x >> 5) & 3)) << 16;
+}
 
 // shared-memory map of the per-atom kernels (bytes)
 constexpr int SM_G = 0, SM_Q = kTile, SM_K = 2 * kTile, SM_V = 3 * kTile, SM_P = 4 * kTile,
@@ -71,6 +85,7 @@ struct Misc {
   uint8_t ones[16 * kW * 2];  // 16 x 128 K-major operand: row 0 ones (column sums)
   uint8_t rhb[16 * kW * 2];   // rows 0..2: unit-vector components of each slot
   float4 col[kW];             // per neighbour slot: {sw, rh_x, rh_y, rh_z}
+  float4 xch[2][kW];          // row-partner exchange
   float sw[kW], dsw[kW], s[kW], d[kW];
   float rh[kW][3];
   float Rt[kW][4];
@@ -87,6 +102,7 @@ struct Misc {
   unsigned long long bar, wbar, pbar;
 };
 constexpr int kSmemAtom = SM_MISC + (int)sizeof(Misc) + 64;
+static_assert(kSmemAtom <= 227 * 1024, "per-atom shared memory");
 
 struct Params {
   int n, nmax, e1, e2, m2, n_layers, heads, dh;
@@ -94,7 +110,7 @@ struct Params {
   const int* sel_j;
   const double* sel_r;
   const int* types;
-  // BF16 weight tiles (core-matrix layout), see the host packing below
+  // 16-bit weight tiles (core-matrix layout), see the host packing below
   const uint8_t *W2T, *W3T, *W2R, *W3R;  // per species
   const uint8_t *WqT, *WkT, *WvT, *WoT;  // per layer, 32 KB each
   const uint8_t *WqR, *WkR, *WvR, *WoR;
@@ -170,6 +186,26 @@ __device__ __forceinline__ void load8(const uint8_t* tile, int r, int c, int Kx,
     v[2 * q + 1] = f.y;
   }
 }
+// store columns c..c+31 of row r, those below `ncol` only (ncol multiple of 8)
+__device__ __forceinline__ void store32(uint8_t* tile, int r, int c, int Kx, int ncol,
+                                        const float* v) {
+#pragma unroll
+  for (int q = 0; q < 32; q += 8)
+    if (c + q < ncol) store8(tile, r, c + q, Kx, v + q);
+}
+
+// The row partner's value: the two threads of a row swap a float4.  Every
+// thread of the block calls it (two barriers).  Both partners then form
+// a + b and b + a from the same two partial results, which are bitwise equal,
+// so the halves of a row never disagree on a row statistic.
+__device__ __forceinline__ float4 partner(Misc* m, float4 v) {
+  const int r = row_id(), h = half_id();
+  m->xch[h][r] = v;
+  __syncthreads();
+  const float4 o = m->xch[h ^ 1][r];
+  __syncthreads();
+  return o;
+}
 
 // Completion tracking on one mbarrier: every thread polls (bounded) and the
 // outcome is made uniform across the CTA, so a timeout never strands part of
@@ -218,7 +254,7 @@ __device__ __forceinline__ void bulk_load(Bar& b, uint8_t* dst, const void* src,
   } while (0)
 
 // ------------------------------------------------------------------ environment
-// Thread t fills row t: switch, s = sw/r, R~, unit vector; empty slots zero.
+// Row t: switch, s = sw/r, R~, unit vector; empty slots zero.
 __device__ void env_row(const Params& p, int atom, Misc* m, int t) {
   int j = t < p.nmax ? p.sel_j[(size_t)atom * p.nmax + t] : -1;
   if (j < 0) {
@@ -252,38 +288,36 @@ __device__ void atom_setup(const Params& p, int atom, Misc* m) {
     m->nvalid = 0;
   }
   __syncthreads();
-  env_row(p, atom, m, t);
-  if (m->tj[t] >= 0) {
-    atomicOr(&m->mask, 1 << m->tj[t]);
-    atomicMax(&m->nvalid, t + 1);
+  if (t < kW) {
+    env_row(p, atom, m, t);
+    if (m->tj[t] >= 0) {
+      atomicOr(&m->mask, 1 << m->tj[t]);
+      atomicMax(&m->nvalid, t + 1);
+    }
   }
   __syncthreads();
 }
 
 // ------------------------------------------------------------------ embedding
-// Layer 1 on the SIMT cores (into the K-major tile H1, and into h1 when
-// given), layer 2 on the tensor cores species by species into H2 (BF16).
+// Layer 1 on the SIMT cores into the K-major tile H1, layer 2 on the tensor
+// cores species by species into H2 (16-bit).
 __device__ bool embed_h2(const Params& p, uint8_t* sm, Misc* m, uint32_t tb, Bar& mb, Bar& wb,
-                         uint8_t* H1, uint8_t* H2, float* h1) {
-  const int t = threadIdx.x, warp = t >> 5;
-  const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
-  const int tj = m->tj[t];
-  const float s = m->s[t];
+                         uint8_t* H1, uint8_t* H2) {
+  const int r = row_id(), hf = half_id();
+  const uint32_t lo = lane_base();
+  const int tj = m->tj[r];
+  const float s = m->s[r];
   uint8_t* Wt = sm + SM_W;
-  for (int c = 0; c < p.e1; c += 8) {
+  for (int c = 8 * hf; c < p.e1; c += 16) {
     float v[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      float h = 0.f;
-      if (tj >= 0) h = tanhf(s * p.W1[tj * p.e1 + c + q] + p.b1[tj * p.e1 + c + q]);
-      v[q] = h;
-      if (h1) h1[c + q] = h;
-    }
-    store8(H1, t, c, p.e1, v);
+    for (int q = 0; q < 8; ++q)
+      v[q] = tj >= 0 ? tanhf(s * p.W1[tj * p.e1 + c + q] + p.b1[tj * p.e1 + c + q]) : 0.f;
+    store8(H1, r, c, p.e1, v);
   }
-  for (int c = 0; c < p.e2; c += 8) {
+  for (int c = 8 * hf; c < p.e2; c += 16) {
     float z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    store8(H2, t, c, p.e2, z);
+    store8(H2, r, c, p.e2, z);
   }
   const int mask = m->mask;
   for (int sp = 0; sp < 32; ++sp) {
@@ -293,14 +327,14 @@ __device__ bool embed_h2(const Params& p, uint8_t* sm, Misc* m, uint32_t tb, Bar
     MMA_GROUP(mb, p.status, mma_issue(tb + R0, kop(H1, p.e1), kop(Wt, p.e1), p.e2, p.e1, false));
     const bool mine = tj == sp;
     if (__any_sync(0xffffffffu, mine)) {
-      for (int c = 0; c < p.e2; c += 32) {
+      for (int c = 32 * hf; c < p.e2; c += 64) {
         float v[32];
-        tc::tmem_ld32(tb + lane_off + R0 + c, v);
+        tc::tmem_ld32(tb + lo + R0 + c, v);
         if (mine) {
 #pragma unroll
-          for (int q = 0; q < 32; ++q) v[q] = tanhf(v[q] + p.b2[sp * p.e2 + c + q]);
-#pragma unroll
-          for (int q = 0; q < 32; q += 8) store8(H2, t, c + q, p.e2, v + q);
+          for (int q = 0; q < 32; ++q)
+            if (c + q < p.e2) v[q] = tanhf(v[q] + p.b2[sp * p.e2 + c + q]);
+          store32(H2, r, c, p.e2, p.e2, v);
         }
       }
     }
@@ -309,25 +343,22 @@ __device__ bool embed_h2(const Params& p, uint8_t* sm, Misc* m, uint32_t tb, Bar
   return true;
 }
 
-// G0 into the G tile (BF16) and R2 (FP32).
+// G0 into the G tile (16-bit) and R2 (FP32).
 __device__ bool embed_forward(const Params& p, uint8_t* sm, Misc* m, uint32_t tb, Bar& mb, Bar& wb) {
-  const int t = threadIdx.x, warp = t >> 5;
-  const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+  const int r = row_id(), hf = half_id();
+  const uint32_t lo = lane_base();
   uint8_t* H1 = sm + SM_Q;
   uint8_t* H2 = sm + SM_K;
   uint8_t* Wt = sm + SM_W;
   uint8_t* Gt = sm + SM_G;
-  if (!embed_h2(p, sm, m, tb, mb, wb, H1, H2, nullptr)) return false;
-  const int tj = m->tj[t];
-  for (int c = 0; c < kW; c += 8) {
-    float z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    store8(Gt, t, c, kW, z);
-  }
+  if (!embed_h2(p, sm, m, tb, mb, wb, H1, H2)) return false;
+  const int tj = m->tj[r];
+  zero_smem(Gt, kTile);
   {
     float z[32];
 #pragma unroll
     for (int q = 0; q < 32; ++q) z[q] = 0.f;
-    for (int c = 0; c < kW; c += 32) tc::tmem_st32(tb + lane_off + R2 + c, z);
+    for (int c = 32 * hf; c < kW; c += 64) tc::tmem_st32(tb + lo + R2 + c, z);
   }
   const int mask = m->mask;
   for (int sp = 0; sp < 32; ++sp) {
@@ -337,17 +368,16 @@ __device__ bool embed_forward(const Params& p, uint8_t* sm, Misc* m, uint32_t tb
     MMA_GROUP(mb, p.status, mma_issue(tb + R1, kop(H2, p.e2), kop(Wt, p.e2), kW, p.e2, false));
     const bool mine = tj == sp;
     if (__any_sync(0xffffffffu, mine)) {
-      for (int c = 0; c < kW; c += 32) {
+      for (int c = 32 * hf; c < kW; c += 64) {
         float v[32], old[32];
-        tc::tmem_ld32(tb + lane_off + R1 + c, v);
-        tc::tmem_ld32(tb + lane_off + R2 + c, old);
+        tc::tmem_ld32(tb + lo + R1 + c, v);
+        tc::tmem_ld32(tb + lo + R2 + c, old);
         if (mine) {
 #pragma unroll
           for (int q = 0; q < 32; ++q) old[q] = tanhf(v[q] + p.b3[sp * kW + c + q]);
-#pragma unroll
-          for (int q = 0; q < 32; q += 8) store8(Gt, t, c + q, kW, old + q);
+          store32(Gt, r, c, kW, kW, old);
         }
-        tc::tmem_st32(tb + lane_off + R2 + c, old);
+        tc::tmem_st32(tb + lo + R2 + c, old);
       }
     }
     tc::fence_before_sync();
@@ -356,11 +386,11 @@ __device__ bool embed_forward(const Params& p, uint8_t* sm, Misc* m, uint32_t tb
 }
 
 // Q, K, V of layer l from the G tile into tensor memory R0, R1, R3 and then
-// into BF16 tiles; weights arrive through the two staging buffers W and P.
+// into 16-bit tiles; weights arrive through the two staging buffers W and P.
 __device__ bool qkv(const Params& p, int l, uint8_t* sm, uint32_t tb, Bar& mb, Bar& wb, Bar& pb,
                     bool prefetched) {
-  const int t = threadIdx.x, warp = t >> 5;
-  const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+  const int r = row_id(), hf = half_id();
+  const uint32_t lo = lane_base();
   uint8_t *Wt = sm + SM_W, *Pt = sm + SM_P;
   if (!prefetched) {
     bulk_load(wb, Wt, p.WqT + (size_t)l * kTile, kTile);
@@ -376,26 +406,25 @@ __device__ bool qkv(const Params& p, int l, uint8_t* sm, uint32_t tb, Bar& mb, B
   const uint32_t src[3] = {R0, R1, R3};
   uint8_t* dst[3] = {sm + SM_Q, sm + SM_K, sm + SM_V};
   for (int q3 = 0; q3 < 3; ++q3)
-    for (int c = 0; c < kW; c += 32) {
+    for (int c = 32 * hf; c < kW; c += 64) {
       float v[32];
-      tc::tmem_ld32(tb + lane_off + src[q3] + c, v);
-#pragma unroll
-      for (int q = 0; q < 32; q += 8) store8(dst[q3], t, c + q, kW, v + q);
+      tc::tmem_ld32(tb + lo + src[q3] + c, v);
+      store32(dst[q3], r, c, kW, kW, v);
     }
   tc::fence_before_sync();
   return true;
 }
 
-// Softmax statistics of this thread's row of the head scores in tensor memory,
-// in one pass over 32-column chunks (running maximum, rescaled sum):
-// b = max_k S_jk log2(e)/sqrt(d) over real columns, and 1/Z with
-// Z = sum_k sw_k 2^(S_jk log2(e)/sqrt(d) - b); 1/Z = 0 for an empty slot.
-__device__ float2 softmax_stats(const Params& p, const Misc* m, uint32_t taddr) {
+// Softmax statistics of row r of the head scores in tensor memory: each half
+// runs one pass over its 32-column chunks (running maximum, rescaled sum) and
+// the two partial results are merged.  b = max_k S_jk log2(e)/sqrt(d) over real
+// columns, 1/Z with Z = sum_k sw_k 2^(S_jk log2(e)/sqrt(d) - b); 1/Z = 0 for an
+// empty slot.
+__device__ float2 softmax_stats(const Params& p, Misc* m, uint32_t taddr) {
   const float a = p.inv_sqrt_d * 1.4426950408889634f;
   const int nv = m->nvalid;
   float mx = -1e30f, z = 0.f;
-  for (int c = 0; c < kW; c += 32) {
-    if (c >= nv) break;
+  for (int c = 32 * half_id(); c < nv; c += 64) {
     float v[32];
     tc::tmem_ld32(taddr + c, v);
     float cm = -1e30f;
@@ -403,15 +432,19 @@ __device__ float2 softmax_stats(const Params& p, const Misc* m, uint32_t taddr) 
     for (int q = 0; q < 32; ++q)
       if (c + q < nv) cm = fmaxf(cm, v[q] * a);
     const float nm = fmaxf(mx, cm);
-    float zc = 0.f;
+    float zc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int q = 0; q < 32; ++q)
-      if (c + q < nv) zc += m->col[c + q].x * exp2f(v[q] * a - nm);
-    z = z * exp2f(mx - nm) + zc;
+      if (c + q < nv) zc[q & 3] += m->col[c + q].x * exp2f(v[q] * a - nm);
+    z = z * exp2f(mx - nm) + ((zc[0] + zc[1]) + (zc[2] + zc[3]));
     mx = nm;
   }
-  const float inv = (z > 0.f && threadIdx.x < nv) ? 1.f / z : 0.f;
-  return make_float2(mx, inv);
+  const float4 o = partner(m, make_float4(mx, z, 0.f, 0.f));
+  const float b = fmaxf(mx, o.x);
+  // unfused products: both partners must round the same two terms
+  const float Z = __fmul_rn(z, exp2f(mx - b)) + __fmul_rn(o.y, exp2f(o.x - b));
+  const float inv = (Z > 0.f && row_id() < nv) ? 1.f / Z : 0.f;
+  return make_float2(b, inv);
 }
 
 // attention weights w_jk of 32 columns from raw scores v (in place)
@@ -431,8 +464,8 @@ __device__ __forceinline__ float gate(const float* rj, const float4& ck) {
 // ------------------------------------------------------------------ forward
 __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32_t tb, Bar& mb,
                          Bar& wb, Bar& pb) {
-  const int t = threadIdx.x, warp = t >> 5;
-  const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+  const int t = threadIdx.x, r = row_id(), hf = half_id();
+  const uint32_t lo = lane_base();
   atom_setup(p, atom, m);
   const int ngroups = (m->nvalid + 7) >> 3;
   uint8_t* Gdst = p.Gst + (size_t)atom * (p.n_layers + 1) * kTile;
@@ -446,6 +479,8 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
   }
   for (int i = t; i < ngroups * 2048 / 16; i += kThreads)
     reinterpret_cast<int4*>(Gdst)[i] = reinterpret_cast<const int4*>(sm + SM_G)[i];
+  const bool valid = m->tj[r] >= 0;
+  const float rj[3] = {m->col[r].y, m->col[r].z, m->col[r].w};
   for (int l = 0; l < p.n_layers; ++l) {
     if (!qkv(p, l, sm, tb, mb, wb, pb, prefetched)) return false;
     prefetched = false;
@@ -454,13 +489,12 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
       MMA_GROUP(mb, p.status,
                 mma_issue(tb + R3, kop(sm + SM_Q, kW, h * p.dh), kop(sm + SM_K, kW, h * p.dh), kW,
                           p.dh, false));
-      const float2 st = softmax_stats(p, m, tb + lane_off + R3);
-      p.smx[(((size_t)atom * p.n_layers + l) * p.heads + h) * kW + t] = st;
-      const float rj[3] = {m->col[t].y, m->col[t].z, m->col[t].w};
-      for (int c = 0; c < kW; c += 32) {
+      const float2 st = softmax_stats(p, m, tb + lo + R3);
+      if (hf == 0) p.smx[(((size_t)atom * p.n_layers + l) * p.heads + h) * kW + r] = st;
+      for (int c = 32 * hf; c < kW; c += 64) {
         float v[32];
         if (c < m->nvalid) {
-          tc::tmem_ld32(tb + lane_off + R3 + c, v);
+          tc::tmem_ld32(tb + lo + R3 + c, v);
           softmax_w(p, m, c, st, v);
 #pragma unroll
           for (int q = 0; q < 32; ++q) v[q] *= gate(rj, m->col[c + q]);
@@ -468,19 +502,17 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
 #pragma unroll
           for (int q = 0; q < 32; ++q) v[q] = 0.f;
         }
-#pragma unroll
-        for (int q = 0; q < 32; q += 8) store8(sm + SM_P, t, c + q, kW, v + q);
+        store32(sm + SM_P, r, c, kW, kW, v);
       }
       tc::fence_before_sync();
       MMA_GROUP(mb, p.status,
                 mma_issue(tb + R0 + h * p.dh, kop(sm + SM_P, kW), mnop(sm + SM_V, kW, h * p.dh), p.dh,
                           kW, false));
     }
-    for (int c = 0; c < kW; c += 32) {
+    for (int c = 32 * hf; c < kW; c += 64) {
       float v[32];
-      tc::tmem_ld32(tb + lane_off + R0 + c, v);
-#pragma unroll
-      for (int q = 0; q < 32; q += 8) store8(sm + SM_Q, t, c + q, kW, v + q);
+      tc::tmem_ld32(tb + lo + R0 + c, v);
+      store32(sm + SM_Q, r, c, kW, kW, v);
     }
     tc::fence_before_sync();
     if (!wb.wait(p.status)) return false;
@@ -490,61 +522,73 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
       bulk_load(pb, sm + SM_P, p.WkT + (size_t)(l + 1) * kTile, kTile);
       prefetched = true;
     }
-    // residual + LayerNorm, thread = row: three passes over 32-column chunks
-    const bool valid = m->tj[t] >= 0;
+    // residual + LayerNorm over the row's 128 columns: mean, variance, scale
+    const float* bo = p.bo + l * kW;
     float sum = 0.f, sq = 0.f;
-    for (int c = 0; c < kW; c += 32) {
+    for (int c = 32 * hf; c < kW; c += 64) {
       float g[32], y[32];
-      tc::tmem_ld32(tb + lane_off + R2 + c, g);
-      tc::tmem_ld32(tb + lane_off + R1 + c, y);
+      tc::tmem_ld32(tb + lo + R2 + c, g);
+      tc::tmem_ld32(tb + lo + R1 + c, y);
+      float s4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int q = 0; q < 32; ++q) sum += g[q] + y[q] + p.bo[l * kW + c + q];
+      for (int q = 0; q < 32; ++q) s4[q & 3] += g[q] + y[q] + bo[c + q];
+      sum += (s4[0] + s4[1]) + (s4[2] + s4[3]);
     }
+    sum += partner(m, make_float4(sum, 0.f, 0.f, 0.f)).x;
     const float mu = sum * (1.f / kW);
-    for (int c = 0; c < kW; c += 32) {
+    for (int c = 32 * hf; c < kW; c += 64) {
       float g[32], y[32];
-      tc::tmem_ld32(tb + lane_off + R2 + c, g);
-      tc::tmem_ld32(tb + lane_off + R1 + c, y);
+      tc::tmem_ld32(tb + lo + R2 + c, g);
+      tc::tmem_ld32(tb + lo + R1 + c, y);
+      float s4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
-        float z = g[q] + y[q] + p.bo[l * kW + c + q] - mu;
-        sq += z * z;
+        const float z = g[q] + y[q] + bo[c + q] - mu;
+        s4[q & 3] += z * z;
       }
+      sq += (s4[0] + s4[1]) + (s4[2] + s4[3]);
     }
+    sq += partner(m, make_float4(sq, 0.f, 0.f, 0.f)).x;
     const float rs = valid ? rsqrtf(sq * (1.f / kW) + 1e-5f) : 0.f;
-    for (int c = 0; c < kW; c += 32) {
+    for (int c = 32 * hf; c < kW; c += 64) {
       float g[32], y[32];
-      tc::tmem_ld32(tb + lane_off + R2 + c, g);
-      tc::tmem_ld32(tb + lane_off + R1 + c, y);
+      tc::tmem_ld32(tb + lo + R2 + c, g);
+      tc::tmem_ld32(tb + lo + R1 + c, y);
 #pragma unroll
-      for (int q = 0; q < 32; ++q) g[q] = (g[q] + y[q] + p.bo[l * kW + c + q] - mu) * rs;
-      tc::tmem_st32(tb + lane_off + R2 + c, g);
-#pragma unroll
-      for (int q = 0; q < 32; q += 8) store8(sm + SM_G, t, c + q, kW, g + q);
+      for (int q = 0; q < 32; ++q) g[q] = (g[q] + y[q] + bo[c + q] - mu) * rs;
+      tc::tmem_st32(tb + lo + R2 + c, g);
+      store32(sm + SM_G, r, c, kW, kW, g);
     }
-    p.rstd[((size_t)atom * p.n_layers + l) * kW + t] = rs;
+    if (hf == 0) p.rstd[((size_t)atom * p.n_layers + l) * kW + r] = rs;
     tc::fence_before_sync();
     __syncthreads();
     uint8_t* dst = Gdst + (size_t)(l + 1) * kTile;
     for (int i = t; i < ngroups * 2048 / 16; i += kThreads)
       reinterpret_cast<int4*>(dst)[i] = reinterpret_cast<const int4*>(sm + SM_G)[i];
   }
-  // descriptor: T[a][f] = (1/Nmax) sum_j R~[j][a] G[j][f]; thread = f
+  // descriptor: T[a][f] = (1/Nmax) sum_j R~[j][a] G[j][f]; feature f = row id,
+  // neighbours j split between the halves
+  const int f = r;
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  const int f = t;
-  for (int j = 0; j < m->nvalid; ++j) {
+  for (int j = hf; j < m->nvalid; j += 2) {
     float gv = op2f(*reinterpret_cast<const op_t*>(sm + SM_G + tc::kmajor_off(j, f, kW)));
 #pragma unroll
     for (int a = 0; a < 4; ++a) acc[a] += m->Rt[j][a] * gv;
   }
+  {
+    const float4 o = partner(m, make_float4(acc[0], acc[1], acc[2], acc[3]));
+    acc[0] += o.x; acc[1] += o.y; acc[2] += o.z; acc[3] += o.w;
+  }
+  if (hf == 0) {
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    m->T[a][f] = acc[a] * p.inv_nmax;
-    p.Tm[((size_t)atom * 4 + a) * kW + f] = acc[a] * p.inv_nmax;
+    for (int a = 0; a < 4; ++a) {
+      m->T[a][f] = acc[a] * p.inv_nmax;
+      p.Tm[((size_t)atom * 4 + a) * kW + f] = acc[a] * p.inv_nmax;
+    }
   }
   __syncthreads();
   op_t* Drow = p.D + (size_t)atom * kW * p.m2 + (size_t)f * p.m2;
-  for (int q = 0; q < p.m2; ++q) {
+  for (int q = hf; q < p.m2; q += 2) {
     float v = 0.f;
 #pragma unroll
     for (int a = 0; a < 4; ++a) v += m->T[a][f] * m->T[a][q];
@@ -591,48 +635,56 @@ __global__ void __launch_bounds__(kThreads, 1) k_af_fwd(Params p) {
 // Adjoint of one atom: dE/dD (from the fitting kernel) back to g_ij.
 __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32_t tb, Bar& mb,
                          Bar& wb, Bar& pb) {
-  const int t = threadIdx.x, warp = t >> 5;
-  const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+  const int t = threadIdx.x, r = row_id(), hf = half_id();
+  const uint32_t lo = lane_base();
   atom_setup(p, atom, m);
   const int ngroups = (m->nvalid + 7) >> 3;
   const int L = p.n_layers;
   const uint8_t* Gsrc = p.Gst + (size_t)atom * (L + 1) * kTile;
-  const bool valid = m->tj[t] >= 0;
+  const bool valid = m->tj[r] >= 0;
   const int DH = p.dh;
+  const int nv = m->nvalid;
   // load a stored G tile: real row groups by bulk copy, the rest zero
   auto load_G = [&](uint8_t* dst, int l, Bar& b) {
     zero_smem(dst + ngroups * 2048, kTile - ngroups * 2048);
     if (ngroups > 0) bulk_load(b, dst, Gsrc + (size_t)l * kTile, ngroups * 2048);
   };
-  // ---- descriptor adjoint: dT = dD T (both orders), dR~ and dG_L
+  // ---- descriptor adjoint: dT[a][f] = sum_q dD[f][q] T[a][q] + sum_g dD[g][f] T[a][g]
+  // (the second sum for f < m2 only); feature f = row id, the 128-term sum split
   {
-    const int f = t;
+    const int f = r;
     float* dDs = reinterpret_cast<float*>(sm + SM_P);   // 128 x m2 FP32 staging
     for (int i = t; i < kW * p.m2; i += kThreads) dDs[i] = p.dD[(size_t)atom * kW * p.m2 + i];
-    m->T[0][f] = p.Tm[((size_t)atom * 4 + 0) * kW + f];
-    m->T[1][f] = p.Tm[((size_t)atom * 4 + 1) * kW + f];
-    m->T[2][f] = p.Tm[((size_t)atom * 4 + 2) * kW + f];
-    m->T[3][f] = p.Tm[((size_t)atom * 4 + 3) * kW + f];
+    if (hf == 0)
+      for (int a = 0; a < 4; ++a) m->T[a][f] = p.Tm[((size_t)atom * 4 + a) * kW + f];
     __syncthreads();
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
     for (int a = 0; a < 4; ++a) {
-      float v = 0.f;
-      for (int q = 0; q < p.m2; ++q) v += dDs[f * p.m2 + q] * m->T[a][q];
+      if (hf == 0)
+        for (int q = 0; q < p.m2; ++q) v[a] += dDs[f * p.m2 + q] * m->T[a][q];
       if (f < p.m2)
-        for (int g = 0; g < kW; ++g) v += dDs[g * p.m2 + f] * m->T[a][g];
-      m->dT[a][f] = v;
+        for (int g = 64 * hf; g < 64 * hf + 64; ++g) v[a] += dDs[g * p.m2 + f] * m->T[a][g];
+    }
+    const float4 o = partner(m, make_float4(v[0], v[1], v[2], v[3]));
+    if (hf == 0) {
+      m->dT[0][f] = v[0] + o.x;
+      m->dT[1][f] = v[1] + o.y;
+      m->dT[2][f] = v[2] + o.z;
+      m->dT[3][f] = v[3] + o.w;
     }
   }
-  {
-    load_G(sm + SM_G, L, wb);
-    if (ngroups > 0 && !wb.wait(p.status)) return false;
-    __syncthreads();
-  }
+  load_G(sm + SM_G, L, wb);
+  if (ngroups > 0 && !wb.wait(p.status)) return false;
+  __syncthreads();
   {
     float dr[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int c = 0; c < kW; c += 32) {
+    float rt[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) rt[a] = m->Rt[r][a];
+    for (int c = 32 * hf; c < kW; c += 64) {
       float g[32];
 #pragma unroll
-      for (int q = 0; q < 32; q += 8) load8(sm + SM_G, t, c + q, kW, g + q);
+      for (int q = 0; q < 32; q += 8) load8(sm + SM_G, r, c + q, kW, g + q);
       float dg[32];
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
@@ -640,24 +692,28 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
 #pragma unroll
         for (int a = 0; a < 4; ++a) dr[a] += m->dT[a][f] * g[q];
         dg[q] = valid ? kGradScale * p.inv_nmax *
-                            (m->dT[0][f] * m->Rt[t][0] + m->dT[1][f] * m->Rt[t][1] +
-                             m->dT[2][f] * m->Rt[t][2] + m->dT[3][f] * m->Rt[t][3])
+                            (m->dT[0][f] * rt[0] + m->dT[1][f] * rt[1] + m->dT[2][f] * rt[2] +
+                             m->dT[3][f] * rt[3])
                       : 0.f;
       }
-      tc::tmem_st32(tb + lane_off + R2 + c, dg);
+      tc::tmem_st32(tb + lo + R2 + c, dg);
     }
-#pragma unroll
-    for (int a = 0; a < 4; ++a) m->dRt[t][a] = dr[a] * p.inv_nmax;
+    const float4 o = partner(m, make_float4(dr[0], dr[1], dr[2], dr[3]));
+    if (hf == 0) {
+      m->dRt[r][0] = (dr[0] + o.x) * p.inv_nmax;
+      m->dRt[r][1] = (dr[1] + o.y) * p.inv_nmax;
+      m->dRt[r][2] = (dr[2] + o.z) * p.inv_nmax;
+      m->dRt[r][3] = (dr[3] + o.w) * p.inv_nmax;
+      m->dswa[r] = 0.f;
+      m->drc[r][0] = m->drc[r][1] = m->drc[r][2] = 0.f;
+      // gate column-sum operand: rows 0..2 = rh components of neighbour r (column r)
+      for (int a = 0; a < 3; ++a)
+        *reinterpret_cast<op_t*>(m->rhb + tc::kmajor_off(a, r, kW)) =
+            f2op(valid ? m->rh[r][a] : 0.f);
+    }
   }
   float drow[3] = {0.f, 0.f, 0.f};  // gate adjoint, row part: sum_k dA_jk w_jk rh_k
-  m->dswa[t] = 0.f;
-  m->drc[t][0] = m->drc[t][1] = m->drc[t][2] = 0.f;
-  // gate column-sum operand: rows 0..2 = rh components of neighbour j (column j)
-  {
-    uint8_t* RHB = m->rhb;
-    for (int a = 0; a < 3; ++a)
-      *reinterpret_cast<op_t*>(RHB + tc::kmajor_off(a, t, kW)) = f2op(valid ? m->rh[t][a] : 0.f);
-  }
+  const float rj[3] = {m->col[r].y, m->col[r].z, m->col[r].w};
   for (int l = L - 1; l >= 0; --l) {
     // ---- stored layer input and output tiles
     load_G(sm + SM_G, l, wb);
@@ -666,31 +722,34 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
     __syncthreads();
     // ---- LayerNorm adjoint: dZ = rstd (dG - mean dG - Gout mean(dG Gout))
     {
-      const float rs = p.rstd[((size_t)atom * L + l) * kW + t];
+      const float rs = p.rstd[((size_t)atom * L + l) * kW + r];
       float s1 = 0.f, s2 = 0.f;
-      for (int c = 0; c < kW; c += 32) {
+      for (int c = 32 * hf; c < kW; c += 64) {
         float dg[32], go[32];
-        tc::tmem_ld32(tb + lane_off + R2 + c, dg);
+        tc::tmem_ld32(tb + lo + R2 + c, dg);
 #pragma unroll
-        for (int q = 0; q < 32; q += 8) load8(sm + SM_V, t, c + q, kW, go + q);
+        for (int q = 0; q < 32; q += 8) load8(sm + SM_V, r, c + q, kW, go + q);
+        float a4[4] = {0.f, 0.f, 0.f, 0.f}, b4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
-          s1 += dg[q];
-          s2 += dg[q] * go[q];
+          a4[q & 3] += dg[q];
+          b4[q & 3] += dg[q] * go[q];
         }
+        s1 += (a4[0] + a4[1]) + (a4[2] + a4[3]);
+        s2 += (b4[0] + b4[1]) + (b4[2] + b4[3]);
       }
-      s1 *= (1.f / kW);
-      s2 *= (1.f / kW);
-      for (int c = 0; c < kW; c += 32) {
+      const float4 o = partner(m, make_float4(s1, s2, 0.f, 0.f));
+      s1 = (s1 + o.x) * (1.f / kW);
+      s2 = (s2 + o.y) * (1.f / kW);
+      for (int c = 32 * hf; c < kW; c += 64) {
         float dg[32], go[32];
-        tc::tmem_ld32(tb + lane_off + R2 + c, dg);
+        tc::tmem_ld32(tb + lo + R2 + c, dg);
 #pragma unroll
-        for (int q = 0; q < 32; q += 8) load8(sm + SM_V, t, c + q, kW, go + q);
+        for (int q = 0; q < 32; q += 8) load8(sm + SM_V, r, c + q, kW, go + q);
 #pragma unroll
         for (int q = 0; q < 32; ++q) dg[q] = valid ? rs * (dg[q] - s1 - go[q] * s2) : 0.f;
-        tc::tmem_st32(tb + lane_off + R2 + c, dg);
-#pragma unroll
-        for (int q = 0; q < 32; q += 8) store8(sm + SM_P, t, c + q, kW, dg + q);
+        tc::tmem_st32(tb + lo + R2 + c, dg);
+        store32(sm + SM_P, r, c, kW, kW, dg);
       }
       tc::fence_before_sync();
     }
@@ -707,23 +766,21 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
       }
       uint8_t* tiles[3] = {sm + SM_Q, sm + SM_K, sm + SM_V};
       for (int q3 = 0; q3 < 3; ++q3)
-        for (int c = 0; c < kW; c += 32) {
+        for (int c = 32 * hf; c < kW; c += 64) {
           float v[32];
-          tc::tmem_ld32(tb + lane_off + dst[q3] + c, v);
-#pragma unroll
-          for (int q = 0; q < 32; q += 8) store8(tiles[q3], t, c + q, kW, v + q);
+          tc::tmem_ld32(tb + lo + dst[q3] + c, v);
+          store32(tiles[q3], r, c, kW, kW, v);
         }
       tc::fence_before_sync();
     }
-    // ---- dO = dZ Wo^T into R1, then the BF16 tile over G (no longer needed)
+    // ---- dO = dZ Wo^T into R1, then the 16-bit tile over G (no longer needed)
     bulk_load(wb, sm + SM_W, p.WoR + (size_t)l * kTile, kTile);
     if (!wb.wait(p.status)) return false;
     MMA_GROUP(mb, p.status, mma_issue(tb + R1, kop(sm + SM_P, kW), kop(sm + SM_W, kW), kW, kW, false));
-    for (int c = 0; c < kW; c += 32) {
+    for (int c = 32 * hf; c < kW; c += 64) {
       float v[32];
-      tc::tmem_ld32(tb + lane_off + R1 + c, v);
-#pragma unroll
-      for (int q = 0; q < 32; q += 8) store8(sm + SM_G, t, c + q, kW, v + q);
+      tc::tmem_ld32(tb + lo + R1 + c, v);
+      store32(sm + SM_G, r, c, kW, kW, v);
     }
     tc::fence_before_sync();
     // ---- heads
@@ -732,23 +789,21 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
       // scores
       MMA_GROUP(mb, p.status,
                 mma_issue(tb + R3, kop(sm + SM_Q, kW, c0), kop(sm + SM_K, kW, c0), kW, DH, false));
-      const float2 st = p.smx[(((size_t)atom * L + l) * p.heads + h) * kW + t];
-      const float rj[3] = {m->col[t].y, m->col[t].z, m->col[t].w};
-      const int nv = m->nvalid;
-      // A = w * gate -> P tile
-      for (int c = 0; c < kW; c += 32) {
+      const float2 st = p.smx[(((size_t)atom * L + l) * p.heads + h) * kW + r];
+      // w (kept in R3 for the adjoint below) and A = w * gate -> P tile
+      for (int c = 32 * hf; c < kW; c += 64) {
         float v[32];
         if (c < nv) {
-          tc::tmem_ld32(tb + lane_off + R3 + c, v);
+          tc::tmem_ld32(tb + lo + R3 + c, v);
           softmax_w(p, m, c, st, v);
+          tc::tmem_st32(tb + lo + R3 + c, v);
 #pragma unroll
           for (int q = 0; q < 32; ++q) v[q] *= gate(rj, m->col[c + q]);
         } else {
 #pragma unroll
           for (int q = 0; q < 32; ++q) v[q] = 0.f;
         }
-#pragma unroll
-        for (int q = 0; q < 32; q += 8) store8(sm + SM_P, t, c + q, kW, v + q);
+        store32(sm + SM_P, r, c, kW, kW, v);
       }
       tc::fence_before_sync();
       // dA = dO_h V_h^T (R1), dV_h = A^T dO_h (R0 + 2d), O_h = A V_h (R0, consumed
@@ -758,26 +813,28 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
                 mma_issue(tb + R0 + 2 * DH, mnop(sm + SM_P, kW, 0), mnop(sm + SM_G, kW, c0), DH, kW,
                           false);
                 mma_issue(tb + R0, kop(sm + SM_P, kW), mnop(sm + SM_V, kW, c0), DH, kW, false));
-      // sum_k w_jk dw_jk = sum_k A_jk dA_jk = dO_j . O_j (this head's columns)
+      // sum_k w_jk dw_jk = sum_k A_jk dA_jk = dO_j . O_j over this head's
+      // columns; both halves form it whole (same order, same value)
       float wdw = 0.f;
       {
         float o[32];
-        tc::tmem_ld32(tb + lane_off + R0, o);
+        tc::tmem_ld32(tb + lo + R0, o);
+        float a4[4] = {0.f, 0.f, 0.f, 0.f};
         for (int q = 0; q < DH; q += 8) {
           float g8[8];
-          load8(sm + SM_G, t, c0 + q, kW, g8);
+          load8(sm + SM_G, r, c0 + q, kW, g8);
 #pragma unroll
-          for (int e = 0; e < 8; ++e) wdw += g8[e] * o[q + e];
+          for (int e = 0; e < 8; ++e) a4[e & 3] += g8[e] * o[q + e];
         }
+        wdw = (a4[0] + a4[1]) + (a4[2] + a4[3]);
       }
       // softmax + gate adjoint for this row
-      for (int c = 0; c < kW; c += 32) {
+      for (int c = 32 * hf; c < kW; c += 64) {
         float s[32], x[32];
         if (c < nv) {
           float da[32];
-          tc::tmem_ld32(tb + lane_off + R3 + c, s);
-          tc::tmem_ld32(tb + lane_off + R1 + c, da);
-          softmax_w(p, m, c, st, s);
+          tc::tmem_ld32(tb + lo + R3 + c, s);
+          tc::tmem_ld32(tb + lo + R1 + c, da);
 #pragma unroll
           for (int q = 0; q < 32; ++q) {
             const float4 ck = m->col[c + q];
@@ -792,11 +849,8 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
 #pragma unroll
           for (int q = 0; q < 32; ++q) s[q] = x[q] = 0.f;
         }
-#pragma unroll
-        for (int q = 0; q < 32; q += 8) {
-          store8(sm + SM_W, t, c + q, kW, s + q);
-          store8(sm + SM_P, t, c + q, kW, x + q);
-        }
+        store32(sm + SM_W, r, c, kW, kW, s);
+        store32(sm + SM_P, r, c, kW, kW, x);
       }
       tc::fence_before_sync();
       // dQ_h = dS K_h, dK_h = dS^T Q_h (scaled at drain), column sums of dS
@@ -807,30 +861,30 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
                 mma_issue(tb + R0 + 112, mnop(sm + SM_W, kW, 0), kop(m->ones, kW), 16, kW, h > 0);
                 mma_issue(tb + R0 + 96, mnop(sm + SM_P, kW, 0), kop(m->rhb, kW), 16, kW, h > 0));
       // write dQ_h, dK_h, dV_h (R0 columns [0,32), [32,64), [64,96)) over the
-      // head's columns of Q, K, V
+      // head's columns of Q, K, V; each half takes 16 of the 32 columns
       {
         uint8_t* tiles[3] = {sm + SM_Q, sm + SM_K, sm + SM_V};
 #pragma unroll 1
         for (int part = 0; part < 3; ++part) {
-          float v[32];
-          tc::tmem_ld32(tb + lane_off + R0 + 32 * part, v);
+          float v[16];
+          tc::tmem_ld16(tb + lo + R0 + 32 * part + 16 * hf, v);
           const float sc = part < 2 ? p.inv_sqrt_d : 1.f;
 #pragma unroll
-          for (int q = 0; q < 32; ++q) v[q] *= sc;
-#pragma unroll
-          for (int q = 0; q < 32; q += 8) store8(tiles[part], t, c0 + q, kW, v + q);
+          for (int q = 0; q < 16; ++q) v[q] *= sc;
+          store8(tiles[part], r, c0 + 16 * hf, kW, v);
+          store8(tiles[part], r, c0 + 16 * hf + 8, kW, v + 8);
         }
       }
       tc::fence_before_sync();
     }
-    // column sums of this layer: thread k owns column k
-    {
+    // column sums of this layer: row id k owns column k (warps of half 0)
+    if (hf == 0) {
       float v[32];
-      tc::tmem_ld32(tb + lane_off + R0 + 96, v);
-      m->drc[t][0] += v[0];
-      m->drc[t][1] += v[1];
-      m->drc[t][2] += v[2];
-      if (valid && m->sw[t] > 0.f) m->dswa[t] += v[16] / m->sw[t];
+      tc::tmem_ld32(tb + lo + R0 + 96, v);
+      m->drc[r][0] += v[0];
+      m->drc[r][1] += v[1];
+      m->drc[r][2] += v[2];
+      if (valid && m->sw[r] > 0.f) m->dswa[r] += v[16] / m->sw[r];
     }
     // ---- dG_in = dZ + dQ Wq^T + dK Wk^T + dV Wv^T, accumulated onto R2
     {
@@ -845,26 +899,25 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
     }
   }
   // ---- embedding adjoint: dG0 (R2) -> ds
-  if (!embed_h2(p, sm, m, tb, mb, wb, sm + SM_Q, sm + SM_K, nullptr)) return false;
+  if (!embed_h2(p, sm, m, tb, mb, wb, sm + SM_Q, sm + SM_K)) return false;
   load_G(sm + SM_G, 0, pb);
   if (ngroups > 0 && !pb.wait(p.status)) return false;
   __syncthreads();
-  for (int c = 0; c < kW; c += 32) {  // da3 = dG0 (1 - G0^2) -> P tile
+  for (int c = 32 * hf; c < kW; c += 64) {  // da3 = dG0 (1 - G0^2) -> P tile
     float dg[32], g0[32];
-    tc::tmem_ld32(tb + lane_off + R2 + c, dg);
+    tc::tmem_ld32(tb + lo + R2 + c, dg);
 #pragma unroll
-    for (int q = 0; q < 32; q += 8) load8(sm + SM_G, t, c + q, kW, g0 + q);
+    for (int q = 0; q < 32; q += 8) load8(sm + SM_G, r, c + q, kW, g0 + q);
 #pragma unroll
     for (int q = 0; q < 32; ++q) dg[q] = valid ? dg[q] * (1.f - g0[q] * g0[q]) : 0.f;
-#pragma unroll
-    for (int q = 0; q < 32; q += 8) store8(sm + SM_P, t, c + q, kW, dg + q);
+    store32(sm + SM_P, r, c, kW, kW, dg);
   }
   tc::fence_before_sync();
-  const int tj = m->tj[t];
+  const int tj = m->tj[r];
   const int mask = m->mask;
-  for (int c = 0; c < p.e2; c += 8) {
+  for (int c = 8 * hf; c < p.e2; c += 16) {
     float z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    store8(sm + SM_V, t, c, p.e2, z);
+    store8(sm + SM_V, r, c, p.e2, z);
   }
   for (int sp = 0; sp < 32; ++sp) {  // da2 = (da3 W3^T) (1 - h2^2) -> V tile
     if (!(mask & (1 << sp))) continue;
@@ -873,16 +926,16 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
     MMA_GROUP(mb, p.status, mma_issue(tb + R1, kop(sm + SM_P, kW), kop(sm + SM_W, kW), p.e2, kW, false));
     const bool mine = tj == sp;
     if (__any_sync(0xffffffffu, mine)) {
-      for (int c = 0; c < p.e2; c += 32) {
-        float v[32], h2[32];
-        tc::tmem_ld32(tb + lane_off + R1 + c, v);
+      for (int c = 32 * hf; c < p.e2; c += 64) {
+        float v[32], h2[32] = {};
+        tc::tmem_ld32(tb + lo + R1 + c, v);
         if (mine) {
 #pragma unroll
-          for (int q = 0; q < 32; q += 8) load8(sm + SM_K, t, c + q, p.e2, h2 + q);
+          for (int q = 0; q < 32; q += 8)
+            if (c + q < p.e2) load8(sm + SM_K, r, c + q, p.e2, h2 + q);
 #pragma unroll
-          for (int q = 0; q < 32; ++q) v[q] *= 1.f - h2[q] * h2[q];
-#pragma unroll
-          for (int q = 0; q < 32; q += 8) store8(sm + SM_V, t, c + q, p.e2, v + q);
+          for (int q = 0; q < 32; ++q) v[q] *= c + q < p.e2 ? 1.f - h2[q] * h2[q] : 0.f;
+          store32(sm + SM_V, r, c, p.e2, p.e2, v);
         }
       }
     }
@@ -896,13 +949,13 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
     MMA_GROUP(mb, p.status, mma_issue(tb + R1, kop(sm + SM_V, p.e2), kop(sm + SM_W, p.e2), p.e1, p.e2, false));
     const bool mine = tj == sp;
     if (__any_sync(0xffffffffu, mine)) {
-      for (int c = 0; c < p.e1; c += 32) {
+      for (int c = 32 * hf; c < p.e1; c += 64) {
         float v[32];
-        tc::tmem_ld32(tb + lane_off + R1 + c, v);
+        tc::tmem_ld32(tb + lo + R1 + c, v);
         if (mine)
           for (int q = 0; q < 32 && c + q < p.e1; q += 8) {
             float h8[8];
-            load8(sm + SM_Q, t, c + q, p.e1, h8);   // h1 (16-bit copy from the H1 tile)
+            load8(sm + SM_Q, r, c + q, p.e1, h8);   // h1 (16-bit copy from the H1 tile)
 #pragma unroll
             for (int e = 0; e < 8; ++e)
               ds_emb += v[q + e] * (1.f - h8[e] * h8[e]) * p.W1[sp * p.e1 + c + q + e];
@@ -913,21 +966,28 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
   }
   // ---- environment adjoint: g_j
   __syncthreads();
-  float* gout = p.g + ((size_t)atom * p.nmax + t) * 3;
-  if (t < p.nmax) {
+  {
+    const float4 o = partner(m, make_float4(drow[0], drow[1], drow[2], ds_emb));
+    drow[0] += o.x;
+    drow[1] += o.y;
+    drow[2] += o.z;
+    ds_emb += o.w;
+  }
+  if (hf == 0 && r < p.nmax) {
+    float* gout = p.g + ((size_t)atom * p.nmax + r) * 3;
     if (!valid) {
       gout[0] = gout[1] = gout[2] = 0.f;
     } else {
-      const float d = m->d[t], s = m->s[t], sw = m->sw[t], dswr = m->dsw[t];
-      const float* rr = m->rh[t];
+      const float d = m->d[r], s = m->s[r], sw = m->sw[r], dswr = m->dsw[r];
+      const float* rr = m->rh[r];
       const float un = 1.f / kGradScale;   // the layer adjoints carry the seed scale
-      float dst = m->dRt[t][0] + ds_emb * un;
+      float dst = m->dRt[r][0] + ds_emb * un;
       float dr[3];
       for (int a = 0; a < 3; ++a) {
-        dst += m->dRt[t][1 + a] * rr[a];
-        dr[a] = (drow[a] + m->drc[t][a]) * un + s * m->dRt[t][1 + a];
+        dst += m->dRt[r][1 + a] * rr[a];
+        dr[a] = (drow[a] + m->drc[r][a]) * un + s * m->dRt[r][1 + a];
       }
-      const float radial = dst * (dswr / d - sw / (d * d)) + m->dswa[t] * un * dswr;
+      const float radial = dst * (dswr / d - sw / (d * d)) + m->dswa[r] * un * dswr;
       const float proj = dr[0] * rr[0] + dr[1] * rr[1] + dr[2] * rr[2];
       for (int a = 0; a < 3; ++a) gout[a] = radial * rr[a] + (dr[a] - proj * rr[a]) / d;
     }
@@ -944,7 +1004,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_af_bwd(Params p) {
   zero_smem(m->ones, 16 * kW * 2);
   zero_smem(m->rhb, 16 * kW * 2);
   __syncthreads();
-  *reinterpret_cast<op_t*>(m->ones + tc::kmajor_off(0, threadIdx.x, kW)) = f2op(1.f);
+  if (threadIdx.x < kW)
+    *reinterpret_cast<op_t*>(m->ones + tc::kmajor_off(0, threadIdx.x, kW)) = f2op(1.f);
   __syncthreads();
   Bar mb{&m->bar, 0u}, wb{&m->wbar, 0u}, pb{&m->pbar, 0u};
   for (int atom = blockIdx.x; atom < p.n; atom += gridDim.x)
@@ -991,7 +1052,7 @@ __device__ bool fit_layer1(uint8_t* CA, uint8_t* CB, int kc, int N, bool acc, ui
   return true;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) k_fit(FitParams p) {
+__global__ void __launch_bounds__(kFitThreads, 1) k_fit(FitParams p) {
   extern __shared__ __align__(1024) uint8_t sm[];
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(sm + FT_MISC);
   unsigned long long* wbar = reinterpret_cast<unsigned long long*>(sm + FT_MISC + 8);
@@ -1161,7 +1222,7 @@ class FusedAf : public Model {
     if (parts & 2) {
       FitParams f = fit_;
       f.atom_e = atom_e;
-      k_fit<<<std::min(fit_.n_tiles, sms_), kThreads, kSmemFit, st>>>(f);
+      k_fit<<<std::min(fit_.n_tiles, sms_), kFitThreads, kSmemFit, st>>>(f);
       ++k;
     }
     if (parts & 4) {

@@ -203,6 +203,23 @@ def test_fused_full_system_vs_oracle():
     assert np.max(np.abs(F.sum(0))) < 1e-10
 
 
+@pytest.mark.parametrize("shape", [
+    dict(e1=16, e2=48, m2=8, n_layers=1, f1=64, f2=32, f3=16, nmax=100),
+    dict(e1=64, e2=128, m2=16, n_layers=2, f1=256, f2=128, f3=48, nmax=128),
+    dict(e1=48, e2=80, m2=4, n_layers=0, f1=32, f2=32, f3=32, nmax=90),
+])
+def test_fused_other_supported_shapes_vs_oracle(shape):
+    """Embedding widths that are not multiples of 32, no attention layer, the
+    widest fitting layer and the largest neighbour limit the fused path takes."""
+    m, s = replace(C.ATTN_MODEL, **shape), serving_system(300, 4)
+    pot, w = make(m, s, dp.PREC_FUSED)
+    E, F, V = pot.compute(s.coords)
+    Eo, aeo, Fo, Vo = oracle.af_compute(m, w, s.types, s.coords, s.box)
+    assert abs(E - Eo) <= TOL_E[dp.PREC_FUSED] * abs(Eo)
+    assert np.max(np.abs(F - Fo)) <= TOL_F[dp.PREC_FUSED] * frms(Fo)
+    assert np.max(np.abs(V - Vo)) <= TOL_F[dp.PREC_FUSED] * np.linalg.norm(Vo)
+
+
 def test_fused_vs_plain_full_size():
     """All 24,000 atoms against the FP32 path (itself pinned to the oracle)."""
     m, s = C.ATTN_MODEL, C.protein24k()
