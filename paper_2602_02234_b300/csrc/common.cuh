@@ -110,6 +110,46 @@ __device__ __forceinline__ float dexp<float>(float x) { return expf(x); }
 template <>
 __device__ __forceinline__ double dexp<double>(double x) { return exp(x); }
 
+// ------------------------------------------------------------------ exact sums
+// Sums whose order depends on the skin list (and so on when it was last
+// rebuilt) are accumulated in 128-bit fixed point at 2^-80 resolution: integer
+// addition is associative, so the result is the same for any order.
+constexpr double kFix = 0x1p80, kUnfix = 0x1p-80;
+
+// v * 2^80 as a 128-bit integer, truncated toward zero; `bad` is set for a
+// value that is not finite or too large (|v| >= 2^46) to be represented.
+__device__ __forceinline__ __int128 to_fixed(double v, bool* bad) {
+  const double a = fabs(v);
+  if (!(a < 0x1p46)) {
+    *bad = true;
+    return 0;
+  }
+  const double s = a * kFix;                // exact: power-of-two scaling
+  const double hi = floor(s * 0x1p-64);     // exact, < 2^62
+  const double lo = s - hi * 0x1p64;        // exact, 0 <= lo < 2^64
+  const unsigned __int128 u =
+      ((unsigned __int128)(unsigned long long)hi << 64) | (unsigned long long)lo;
+  return v < 0 ? -(__int128)u : (__int128)u;
+}
+
+__device__ __forceinline__ __int128 warp_sum_fixed(__int128 v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)v, o);
+    const long long hi = __shfl_xor_sync(0xffffffffu, (long long)(v >> 64), o);
+    v += (__int128)(((unsigned __int128)(unsigned long long)hi << 64) | lo);
+  }
+  return v;
+}
+
+// the 128-bit sum as a double (deterministic; two roundings at most)
+__device__ __forceinline__ double from_fixed(__int128 v) {
+  const long long hi = (long long)(v >> 64);
+  const unsigned long long lo = (unsigned long long)v;
+  return ((double)hi * 0x1p64 + (double)lo) * kUnfix;
+}
+
+__device__ __forceinline__ double quiet_nan() { return __longlong_as_double(0x7ff8000000000000LL); }
+
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;

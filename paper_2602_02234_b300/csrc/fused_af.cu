@@ -60,7 +60,9 @@ __device__ __forceinline__ op_t f2op(float v) { return __float2half_rn(v); }
 constexpr float kGradScale = 4096.f;
 
 constexpr int kW = 128;          // embedding / attention width and rows per atom tile
-constexpr int kThreads = 256;    // per-atom kernels: two threads per neighbour row
+constexpr int kSplit = 4;                 // per-atom kernels: threads per neighbour row
+constexpr int kThreads = kW * kSplit;     // 512 threads, 16 warps
+constexpr int kStride = 32 * kSplit;      // column step between a thread's 32-column chunks
 constexpr int kFitThreads = 128; // fitting kernel: one thread per atom row
 constexpr long long kPolls = 1LL << 22;
 constexpr uint32_t R0 = 0, R1 = 128, R2 = 256, R3 = 384;
@@ -68,12 +70,11 @@ constexpr int kTile = kW * kW * 2;  // one 128 x 128 16-bit tile: 32 KB
 
 // Thread roles of the per-atom kernels.  Thread t serves neighbour row
 // r = t mod 128, which is tensor-memory lane r (warp t/32 reads lane quarter
-// (t/32) mod 4), and half h = t / 128 of that row's columns: the 32-column
-// chunks starting at 32h and 32h + 64.  Interleaving the chunks spreads the
-// empty columns past the last real neighbour over both halves.  Row sums
-// over all columns combine the two partial sums through `partner`.
+// (t/32) mod 4), and part p = t / 128 of that row's columns: the 32-column
+// chunks starting at 32p, 32p + 32 kSplit, ...  Row sums over all columns
+// combine the kSplit partial sums through `row_all` / `row_sum`.
 __device__ __forceinline__ int row_id() { return threadIdx.x & (kW - 1); }
-__device__ __forceinline__ int half_id() { return threadIdx.x >> 7; }
+__device__ __forceinline__ int part_id() { return threadIdx.x >> 7; }
 __device__ __forceinline__ uint32_t lane_base() {
   return (uint32_t)(32 * ((threadIdx.x >> 5) & 3)) << 16;
 }
@@ -85,7 +86,7 @@ struct Misc {
   uint8_t ones[16 * kW * 2];  // 16 x 128 K-major operand: row 0 ones (column sums)
   uint8_t rhb[16 * kW * 2];   // rows 0..2: unit-vector components of each slot
   float4 col[kW];             // per neighbour slot: {sw, rh_x, rh_y, rh_z}
-  float4 xch[2][kW];          // row-partner exchange
+  float4 xch[kSplit][kW];     // exchange of per-row partial results
   float sw[kW], dsw[kW], s[kW], d[kW];
   float rh[kW][3];
   float Rt[kW][4];
@@ -194,17 +195,30 @@ __device__ __forceinline__ void store32(uint8_t* tile, int r, int c, int Kx, int
     if (c + q < ncol) store8(tile, r, c + q, Kx, v + q);
 }
 
-// The row partner's value: the two threads of a row swap a float4.  Every
-// thread of the block calls it (two barriers).  Both partners then form
-// a + b and b + a from the same two partial results, which are bitwise equal,
-// so the halves of a row never disagree on a row statistic.
-__device__ __forceinline__ float4 partner(Misc* m, float4 v) {
-  const int r = row_id(), h = half_id();
-  m->xch[h][r] = v;
+// The kSplit partial results of this thread's row, in part order.  Every
+// thread of the block calls it (two barriers).  All threads of a row then
+// combine the same values in the same order, so they never disagree on a row
+// statistic.
+__device__ __forceinline__ void row_all(Misc* m, float4 v, float4* all) {
+  const int r = row_id();
+  m->xch[part_id()][r] = v;
   __syncthreads();
-  const float4 o = m->xch[h ^ 1][r];
+#pragma unroll
+  for (int i = 0; i < kSplit; ++i) all[i] = m->xch[i][r];
   __syncthreads();
-  return o;
+}
+__device__ __forceinline__ float4 row_sum(Misc* m, float4 v) {
+  float4 all[kSplit];
+  row_all(m, v, all);
+  float4 s = all[0];
+#pragma unroll
+  for (int i = 1; i < kSplit; ++i) {
+    s.x += all[i].x;
+    s.y += all[i].y;
+    s.z += all[i].z;
+    s.w += all[i].w;
+  }
+  return s;
 }
 
 // Completion tracking on one mbarrier: every thread polls (bounded) and the
@@ -303,19 +317,19 @@ __device__ void atom_setup(const Params& p, int atom, Misc* m) {
 // cores species by species into H2 (16-bit).
 __device__ bool embed_h2(const Params& p, uint8_t* sm, Misc* m, uint32_t tb, Bar& mb, Bar& wb,
                          uint8_t* H1, uint8_t* H2) {
-  const int r = row_id(), hf = half_id();
+  const int r = row_id(), pt = part_id();
   const uint32_t lo = lane_base();
   const int tj = m->tj[r];
   const float s = m->s[r];
   uint8_t* Wt = sm + SM_W;
-  for (int c = 8 * hf; c < p.e1; c += 16) {
+  for (int c = 8 * pt; c < p.e1; c += 8 * kSplit) {
     float v[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q)
       v[q] = tj >= 0 ? tanhf(s * p.W1[tj * p.e1 + c + q] + p.b1[tj * p.e1 + c + q]) : 0.f;
     store8(H1, r, c, p.e1, v);
   }
-  for (int c = 8 * hf; c < p.e2; c += 16) {
+  for (int c = 8 * pt; c < p.e2; c += 8 * kSplit) {
     float z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     store8(H2, r, c, p.e2, z);
   }
@@ -327,7 +341,7 @@ __device__ bool embed_h2(const Params& p, uint8_t* sm, Misc* m, uint32_t tb, Bar
     MMA_GROUP(mb, p.status, mma_issue(tb + R0, kop(H1, p.e1), kop(Wt, p.e1), p.e2, p.e1, false));
     const bool mine = tj == sp;
     if (__any_sync(0xffffffffu, mine)) {
-      for (int c = 32 * hf; c < p.e2; c += 64) {
+      for (int c = 32 * pt; c < p.e2; c += kStride) {
         float v[32];
         tc::tmem_ld32(tb + lo + R0 + c, v);
         if (mine) {
@@ -345,7 +359,7 @@ __device__ bool embed_h2(const Params& p, uint8_t* sm, Misc* m, uint32_t tb, Bar
 
 // G0 into the G tile (16-bit) and R2 (FP32).
 __device__ bool embed_forward(const Params& p, uint8_t* sm, Misc* m, uint32_t tb, Bar& mb, Bar& wb) {
-  const int r = row_id(), hf = half_id();
+  const int r = row_id(), pt = part_id();
   const uint32_t lo = lane_base();
   uint8_t* H1 = sm + SM_Q;
   uint8_t* H2 = sm + SM_K;
@@ -358,7 +372,7 @@ __device__ bool embed_forward(const Params& p, uint8_t* sm, Misc* m, uint32_t tb
     float z[32];
 #pragma unroll
     for (int q = 0; q < 32; ++q) z[q] = 0.f;
-    for (int c = 32 * hf; c < kW; c += 64) tc::tmem_st32(tb + lo + R2 + c, z);
+    for (int c = 32 * pt; c < kW; c += kStride) tc::tmem_st32(tb + lo + R2 + c, z);
   }
   const int mask = m->mask;
   for (int sp = 0; sp < 32; ++sp) {
@@ -368,7 +382,7 @@ __device__ bool embed_forward(const Params& p, uint8_t* sm, Misc* m, uint32_t tb
     MMA_GROUP(mb, p.status, mma_issue(tb + R1, kop(H2, p.e2), kop(Wt, p.e2), kW, p.e2, false));
     const bool mine = tj == sp;
     if (__any_sync(0xffffffffu, mine)) {
-      for (int c = 32 * hf; c < kW; c += 64) {
+      for (int c = 32 * pt; c < kW; c += kStride) {
         float v[32], old[32];
         tc::tmem_ld32(tb + lo + R1 + c, v);
         tc::tmem_ld32(tb + lo + R2 + c, old);
@@ -389,7 +403,7 @@ __device__ bool embed_forward(const Params& p, uint8_t* sm, Misc* m, uint32_t tb
 // into 16-bit tiles; weights arrive through the two staging buffers W and P.
 __device__ bool qkv(const Params& p, int l, uint8_t* sm, uint32_t tb, Bar& mb, Bar& wb, Bar& pb,
                     bool prefetched) {
-  const int r = row_id(), hf = half_id();
+  const int r = row_id(), pt = part_id();
   const uint32_t lo = lane_base();
   uint8_t *Wt = sm + SM_W, *Pt = sm + SM_P;
   if (!prefetched) {
@@ -406,7 +420,7 @@ __device__ bool qkv(const Params& p, int l, uint8_t* sm, uint32_t tb, Bar& mb, B
   const uint32_t src[3] = {R0, R1, R3};
   uint8_t* dst[3] = {sm + SM_Q, sm + SM_K, sm + SM_V};
   for (int q3 = 0; q3 < 3; ++q3)
-    for (int c = 32 * hf; c < kW; c += 64) {
+    for (int c = 32 * pt; c < kW; c += kStride) {
       float v[32];
       tc::tmem_ld32(tb + lo + src[q3] + c, v);
       store32(dst[q3], r, c, kW, kW, v);
@@ -415,16 +429,16 @@ __device__ bool qkv(const Params& p, int l, uint8_t* sm, uint32_t tb, Bar& mb, B
   return true;
 }
 
-// Softmax statistics of row r of the head scores in tensor memory: each half
+// Softmax statistics of row r of the head scores in tensor memory: each part
 // runs one pass over its 32-column chunks (running maximum, rescaled sum) and
-// the two partial results are merged.  b = max_k S_jk log2(e)/sqrt(d) over real
+// the partial results of the row are merged.  b = max_k S_jk log2(e)/sqrt(d) over real
 // columns, 1/Z with Z = sum_k sw_k 2^(S_jk log2(e)/sqrt(d) - b); 1/Z = 0 for an
 // empty slot.
 __device__ float2 softmax_stats(const Params& p, Misc* m, uint32_t taddr) {
   const float a = p.inv_sqrt_d * 1.4426950408889634f;
   const int nv = m->nvalid;
   float mx = -1e30f, z = 0.f;
-  for (int c = 32 * half_id(); c < nv; c += 64) {
+  for (int c = 32 * part_id(); c < nv; c += kStride) {
     float v[32];
     tc::tmem_ld32(taddr + c, v);
     float cm = -1e30f;
@@ -439,10 +453,14 @@ __device__ float2 softmax_stats(const Params& p, Misc* m, uint32_t taddr) {
     z = z * exp2f(mx - nm) + ((zc[0] + zc[1]) + (zc[2] + zc[3]));
     mx = nm;
   }
-  const float4 o = partner(m, make_float4(mx, z, 0.f, 0.f));
-  const float b = fmaxf(mx, o.x);
-  // unfused products: both partners must round the same two terms
-  const float Z = __fmul_rn(z, exp2f(mx - b)) + __fmul_rn(o.y, exp2f(o.x - b));
+  float4 all[kSplit];
+  row_all(m, make_float4(mx, z, 0.f, 0.f), all);
+  float b = all[0].x;
+#pragma unroll
+  for (int i = 1; i < kSplit; ++i) b = fmaxf(b, all[i].x);
+  float Z = 0.f;
+#pragma unroll
+  for (int i = 0; i < kSplit; ++i) Z += __fmul_rn(all[i].y, exp2f(all[i].x - b));
   const float inv = (Z > 0.f && row_id() < nv) ? 1.f / Z : 0.f;
   return make_float2(b, inv);
 }
@@ -464,7 +482,7 @@ __device__ __forceinline__ float gate(const float* rj, const float4& ck) {
 // ------------------------------------------------------------------ forward
 __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32_t tb, Bar& mb,
                          Bar& wb, Bar& pb) {
-  const int t = threadIdx.x, r = row_id(), hf = half_id();
+  const int t = threadIdx.x, r = row_id(), pt = part_id();
   const uint32_t lo = lane_base();
   atom_setup(p, atom, m);
   const int ngroups = (m->nvalid + 7) >> 3;
@@ -490,8 +508,8 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
                 mma_issue(tb + R3, kop(sm + SM_Q, kW, h * p.dh), kop(sm + SM_K, kW, h * p.dh), kW,
                           p.dh, false));
       const float2 st = softmax_stats(p, m, tb + lo + R3);
-      if (hf == 0) p.smx[(((size_t)atom * p.n_layers + l) * p.heads + h) * kW + r] = st;
-      for (int c = 32 * hf; c < kW; c += 64) {
+      if (pt == 0) p.smx[(((size_t)atom * p.n_layers + l) * p.heads + h) * kW + r] = st;
+      for (int c = 32 * pt; c < kW; c += kStride) {
         float v[32];
         if (c < m->nvalid) {
           tc::tmem_ld32(tb + lo + R3 + c, v);
@@ -509,7 +527,7 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
                 mma_issue(tb + R0 + h * p.dh, kop(sm + SM_P, kW), mnop(sm + SM_V, kW, h * p.dh), p.dh,
                           kW, false));
     }
-    for (int c = 32 * hf; c < kW; c += 64) {
+    for (int c = 32 * pt; c < kW; c += kStride) {
       float v[32];
       tc::tmem_ld32(tb + lo + R0 + c, v);
       store32(sm + SM_Q, r, c, kW, kW, v);
@@ -525,7 +543,7 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
     // residual + LayerNorm over the row's 128 columns: mean, variance, scale
     const float* bo = p.bo + l * kW;
     float sum = 0.f, sq = 0.f;
-    for (int c = 32 * hf; c < kW; c += 64) {
+    for (int c = 32 * pt; c < kW; c += kStride) {
       float g[32], y[32];
       tc::tmem_ld32(tb + lo + R2 + c, g);
       tc::tmem_ld32(tb + lo + R1 + c, y);
@@ -534,9 +552,9 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
       for (int q = 0; q < 32; ++q) s4[q & 3] += g[q] + y[q] + bo[c + q];
       sum += (s4[0] + s4[1]) + (s4[2] + s4[3]);
     }
-    sum += partner(m, make_float4(sum, 0.f, 0.f, 0.f)).x;
+    sum = row_sum(m, make_float4(sum, 0.f, 0.f, 0.f)).x;
     const float mu = sum * (1.f / kW);
-    for (int c = 32 * hf; c < kW; c += 64) {
+    for (int c = 32 * pt; c < kW; c += kStride) {
       float g[32], y[32];
       tc::tmem_ld32(tb + lo + R2 + c, g);
       tc::tmem_ld32(tb + lo + R1 + c, y);
@@ -548,9 +566,9 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
       }
       sq += (s4[0] + s4[1]) + (s4[2] + s4[3]);
     }
-    sq += partner(m, make_float4(sq, 0.f, 0.f, 0.f)).x;
+    sq = row_sum(m, make_float4(sq, 0.f, 0.f, 0.f)).x;
     const float rs = valid ? rsqrtf(sq * (1.f / kW) + 1e-5f) : 0.f;
-    for (int c = 32 * hf; c < kW; c += 64) {
+    for (int c = 32 * pt; c < kW; c += kStride) {
       float g[32], y[32];
       tc::tmem_ld32(tb + lo + R2 + c, g);
       tc::tmem_ld32(tb + lo + R1 + c, y);
@@ -559,7 +577,7 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
       tc::tmem_st32(tb + lo + R2 + c, g);
       store32(sm + SM_G, r, c, kW, kW, g);
     }
-    if (hf == 0) p.rstd[((size_t)atom * p.n_layers + l) * kW + r] = rs;
+    if (pt == 0) p.rstd[((size_t)atom * p.n_layers + l) * kW + r] = rs;
     tc::fence_before_sync();
     __syncthreads();
     uint8_t* dst = Gdst + (size_t)(l + 1) * kTile;
@@ -567,19 +585,19 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
       reinterpret_cast<int4*>(dst)[i] = reinterpret_cast<const int4*>(sm + SM_G)[i];
   }
   // descriptor: T[a][f] = (1/Nmax) sum_j R~[j][a] G[j][f]; feature f = row id,
-  // neighbours j split between the halves
+  // neighbours j split between the parts of a row
   const int f = r;
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int j = hf; j < m->nvalid; j += 2) {
+  for (int j = pt; j < m->nvalid; j += kSplit) {
     float gv = op2f(*reinterpret_cast<const op_t*>(sm + SM_G + tc::kmajor_off(j, f, kW)));
 #pragma unroll
     for (int a = 0; a < 4; ++a) acc[a] += m->Rt[j][a] * gv;
   }
   {
-    const float4 o = partner(m, make_float4(acc[0], acc[1], acc[2], acc[3]));
-    acc[0] += o.x; acc[1] += o.y; acc[2] += o.z; acc[3] += o.w;
+    const float4 o = row_sum(m, make_float4(acc[0], acc[1], acc[2], acc[3]));
+    acc[0] = o.x; acc[1] = o.y; acc[2] = o.z; acc[3] = o.w;
   }
-  if (hf == 0) {
+  if (pt == 0) {
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       m->T[a][f] = acc[a] * p.inv_nmax;
@@ -588,7 +606,7 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
   }
   __syncthreads();
   op_t* Drow = p.D + (size_t)atom * kW * p.m2 + (size_t)f * p.m2;
-  for (int q = hf; q < p.m2; q += 2) {
+  for (int q = pt; q < p.m2; q += kSplit) {
     float v = 0.f;
 #pragma unroll
     for (int a = 0; a < 4; ++a) v += m->T[a][f] * m->T[a][q];
@@ -635,7 +653,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_af_fwd(Params p) {
 // Adjoint of one atom: dE/dD (from the fitting kernel) back to g_ij.
 __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32_t tb, Bar& mb,
                          Bar& wb, Bar& pb) {
-  const int t = threadIdx.x, r = row_id(), hf = half_id();
+  const int t = threadIdx.x, r = row_id(), pt = part_id();
   const uint32_t lo = lane_base();
   atom_setup(p, atom, m);
   const int ngroups = (m->nvalid + 7) >> 3;
@@ -655,22 +673,23 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
     const int f = r;
     float* dDs = reinterpret_cast<float*>(sm + SM_P);   // 128 x m2 FP32 staging
     for (int i = t; i < kW * p.m2; i += kThreads) dDs[i] = p.dD[(size_t)atom * kW * p.m2 + i];
-    if (hf == 0)
+    if (pt == 0)
       for (int a = 0; a < 4; ++a) m->T[a][f] = p.Tm[((size_t)atom * 4 + a) * kW + f];
     __syncthreads();
     float v[4] = {0.f, 0.f, 0.f, 0.f};
     for (int a = 0; a < 4; ++a) {
-      if (hf == 0)
+      if (pt == 0)
         for (int q = 0; q < p.m2; ++q) v[a] += dDs[f * p.m2 + q] * m->T[a][q];
       if (f < p.m2)
-        for (int g = 64 * hf; g < 64 * hf + 64; ++g) v[a] += dDs[g * p.m2 + f] * m->T[a][g];
+        for (int g = (kW / kSplit) * pt; g < (kW / kSplit) * (pt + 1); ++g)
+          v[a] += dDs[g * p.m2 + f] * m->T[a][g];
     }
-    const float4 o = partner(m, make_float4(v[0], v[1], v[2], v[3]));
-    if (hf == 0) {
-      m->dT[0][f] = v[0] + o.x;
-      m->dT[1][f] = v[1] + o.y;
-      m->dT[2][f] = v[2] + o.z;
-      m->dT[3][f] = v[3] + o.w;
+    const float4 o = row_sum(m, make_float4(v[0], v[1], v[2], v[3]));
+    if (pt == 0) {
+      m->dT[0][f] = o.x;
+      m->dT[1][f] = o.y;
+      m->dT[2][f] = o.z;
+      m->dT[3][f] = o.w;
     }
   }
   load_G(sm + SM_G, L, wb);
@@ -681,7 +700,7 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
     float rt[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) rt[a] = m->Rt[r][a];
-    for (int c = 32 * hf; c < kW; c += 64) {
+    for (int c = 32 * pt; c < kW; c += kStride) {
       float g[32];
 #pragma unroll
       for (int q = 0; q < 32; q += 8) load8(sm + SM_G, r, c + q, kW, g + q);
@@ -698,12 +717,12 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
       }
       tc::tmem_st32(tb + lo + R2 + c, dg);
     }
-    const float4 o = partner(m, make_float4(dr[0], dr[1], dr[2], dr[3]));
-    if (hf == 0) {
-      m->dRt[r][0] = (dr[0] + o.x) * p.inv_nmax;
-      m->dRt[r][1] = (dr[1] + o.y) * p.inv_nmax;
-      m->dRt[r][2] = (dr[2] + o.z) * p.inv_nmax;
-      m->dRt[r][3] = (dr[3] + o.w) * p.inv_nmax;
+    const float4 o = row_sum(m, make_float4(dr[0], dr[1], dr[2], dr[3]));
+    if (pt == 0) {
+      m->dRt[r][0] = o.x * p.inv_nmax;
+      m->dRt[r][1] = o.y * p.inv_nmax;
+      m->dRt[r][2] = o.z * p.inv_nmax;
+      m->dRt[r][3] = o.w * p.inv_nmax;
       m->dswa[r] = 0.f;
       m->drc[r][0] = m->drc[r][1] = m->drc[r][2] = 0.f;
       // gate column-sum operand: rows 0..2 = rh components of neighbour r (column r)
@@ -724,7 +743,7 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
     {
       const float rs = p.rstd[((size_t)atom * L + l) * kW + r];
       float s1 = 0.f, s2 = 0.f;
-      for (int c = 32 * hf; c < kW; c += 64) {
+      for (int c = 32 * pt; c < kW; c += kStride) {
         float dg[32], go[32];
         tc::tmem_ld32(tb + lo + R2 + c, dg);
 #pragma unroll
@@ -738,10 +757,10 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
         s1 += (a4[0] + a4[1]) + (a4[2] + a4[3]);
         s2 += (b4[0] + b4[1]) + (b4[2] + b4[3]);
       }
-      const float4 o = partner(m, make_float4(s1, s2, 0.f, 0.f));
-      s1 = (s1 + o.x) * (1.f / kW);
-      s2 = (s2 + o.y) * (1.f / kW);
-      for (int c = 32 * hf; c < kW; c += 64) {
+      const float4 o = row_sum(m, make_float4(s1, s2, 0.f, 0.f));
+      s1 = o.x * (1.f / kW);
+      s2 = o.y * (1.f / kW);
+      for (int c = 32 * pt; c < kW; c += kStride) {
         float dg[32], go[32];
         tc::tmem_ld32(tb + lo + R2 + c, dg);
 #pragma unroll
@@ -766,7 +785,7 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
       }
       uint8_t* tiles[3] = {sm + SM_Q, sm + SM_K, sm + SM_V};
       for (int q3 = 0; q3 < 3; ++q3)
-        for (int c = 32 * hf; c < kW; c += 64) {
+        for (int c = 32 * pt; c < kW; c += kStride) {
           float v[32];
           tc::tmem_ld32(tb + lo + dst[q3] + c, v);
           store32(tiles[q3], r, c, kW, kW, v);
@@ -777,7 +796,7 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
     bulk_load(wb, sm + SM_W, p.WoR + (size_t)l * kTile, kTile);
     if (!wb.wait(p.status)) return false;
     MMA_GROUP(mb, p.status, mma_issue(tb + R1, kop(sm + SM_P, kW), kop(sm + SM_W, kW), kW, kW, false));
-    for (int c = 32 * hf; c < kW; c += 64) {
+    for (int c = 32 * pt; c < kW; c += kStride) {
       float v[32];
       tc::tmem_ld32(tb + lo + R1 + c, v);
       store32(sm + SM_G, r, c, kW, kW, v);
@@ -791,7 +810,7 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
                 mma_issue(tb + R3, kop(sm + SM_Q, kW, c0), kop(sm + SM_K, kW, c0), kW, DH, false));
       const float2 st = p.smx[(((size_t)atom * L + l) * p.heads + h) * kW + r];
       // w (kept in R3 for the adjoint below) and A = w * gate -> P tile
-      for (int c = 32 * hf; c < kW; c += 64) {
+      for (int c = 32 * pt; c < kW; c += kStride) {
         float v[32];
         if (c < nv) {
           tc::tmem_ld32(tb + lo + R3 + c, v);
@@ -814,7 +833,7 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
                           false);
                 mma_issue(tb + R0, kop(sm + SM_P, kW), mnop(sm + SM_V, kW, c0), DH, kW, false));
       // sum_k w_jk dw_jk = sum_k A_jk dA_jk = dO_j . O_j over this head's
-      // columns; both halves form it whole (same order, same value)
+      // columns; every part forms it whole (same order, same value)
       float wdw = 0.f;
       {
         float o[32];
@@ -829,28 +848,35 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
         wdw = (a4[0] + a4[1]) + (a4[2] + a4[3]);
       }
       // softmax + gate adjoint for this row
-      for (int c = 32 * hf; c < kW; c += 64) {
-        float s[32], x[32];
+      for (int c = 32 * pt; c < kW; c += kStride) {
         if (c < nv) {
-          float da[32];
+          float s[32], da[32];
           tc::tmem_ld32(tb + lo + R3 + c, s);
           tc::tmem_ld32(tb + lo + R1 + c, da);
 #pragma unroll
-          for (int q = 0; q < 32; ++q) {
-            const float4 ck = m->col[c + q];
-            const float dw = da[q] * gate(rj, ck);
-            x[q] = da[q] * s[q];                  // gate adjoint dc_jk
-            drow[0] += x[q] * ck.y;
-            drow[1] += x[q] * ck.z;
-            drow[2] += x[q] * ck.w;
-            s[q] = s[q] * (dw - wdw);             // dS_jk = w (dw - sum w dw)
+          for (int q8 = 0; q8 < 32; q8 += 8) {
+            float ds[8], x[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const int q = q8 + e;
+              const float4 ck = m->col[c + q];
+              const float dw = da[q] * gate(rj, ck);
+              x[e] = da[q] * s[q];                  // gate adjoint dc_jk
+              drow[0] += x[e] * ck.y;
+              drow[1] += x[e] * ck.z;
+              drow[2] += x[e] * ck.w;
+              ds[e] = s[q] * (dw - wdw);            // dS_jk = w (dw - sum w dw)
+            }
+            store8(sm + SM_W, r, c + q8, kW, ds);
+            store8(sm + SM_P, r, c + q8, kW, x);
           }
         } else {
+          float z[32];
 #pragma unroll
-          for (int q = 0; q < 32; ++q) s[q] = x[q] = 0.f;
+          for (int q = 0; q < 32; ++q) z[q] = 0.f;
+          store32(sm + SM_W, r, c, kW, kW, z);
+          store32(sm + SM_P, r, c, kW, kW, z);
         }
-        store32(sm + SM_W, r, c, kW, kW, s);
-        store32(sm + SM_P, r, c, kW, kW, x);
       }
       tc::fence_before_sync();
       // dQ_h = dS K_h, dK_h = dS^T Q_h (scaled at drain), column sums of dS
@@ -861,24 +887,26 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
                 mma_issue(tb + R0 + 112, mnop(sm + SM_W, kW, 0), kop(m->ones, kW), 16, kW, h > 0);
                 mma_issue(tb + R0 + 96, mnop(sm + SM_P, kW, 0), kop(m->rhb, kW), 16, kW, h > 0));
       // write dQ_h, dK_h, dV_h (R0 columns [0,32), [32,64), [64,96)) over the
-      // head's columns of Q, K, V; each half takes 16 of the 32 columns
+      // head's columns of Q, K, V; each part of a row takes 32 / kSplit columns
       {
+        constexpr int kCw = 32 / kSplit;
         uint8_t* tiles[3] = {sm + SM_Q, sm + SM_K, sm + SM_V};
-#pragma unroll 1
+#pragma unroll
         for (int part = 0; part < 3; ++part) {
-          float v[16];
-          tc::tmem_ld16(tb + lo + R0 + 32 * part + 16 * hf, v);
+          float v[kCw];
+          if constexpr (kCw == 16) tc::tmem_ld16(tb + lo + R0 + 32 * part + kCw * pt, v);
+          else tc::tmem_ld8(tb + lo + R0 + 32 * part + kCw * pt, v);
           const float sc = part < 2 ? p.inv_sqrt_d : 1.f;
 #pragma unroll
-          for (int q = 0; q < 16; ++q) v[q] *= sc;
-          store8(tiles[part], r, c0 + 16 * hf, kW, v);
-          store8(tiles[part], r, c0 + 16 * hf + 8, kW, v + 8);
+          for (int q = 0; q < kCw; ++q) v[q] *= sc;
+#pragma unroll
+          for (int q = 0; q < kCw; q += 8) store8(tiles[part], r, c0 + kCw * pt + q, kW, v + q);
         }
       }
       tc::fence_before_sync();
     }
-    // column sums of this layer: row id k owns column k (warps of half 0)
-    if (hf == 0) {
+    // column sums of this layer: row id k owns column k (warps of part 0)
+    if (pt == 0) {
       float v[32];
       tc::tmem_ld32(tb + lo + R0 + 96, v);
       m->drc[r][0] += v[0];
@@ -903,7 +931,7 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
   load_G(sm + SM_G, 0, pb);
   if (ngroups > 0 && !pb.wait(p.status)) return false;
   __syncthreads();
-  for (int c = 32 * hf; c < kW; c += 64) {  // da3 = dG0 (1 - G0^2) -> P tile
+  for (int c = 32 * pt; c < kW; c += kStride) {  // da3 = dG0 (1 - G0^2) -> P tile
     float dg[32], g0[32];
     tc::tmem_ld32(tb + lo + R2 + c, dg);
 #pragma unroll
@@ -915,7 +943,7 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
   tc::fence_before_sync();
   const int tj = m->tj[r];
   const int mask = m->mask;
-  for (int c = 8 * hf; c < p.e2; c += 16) {
+  for (int c = 8 * pt; c < p.e2; c += 8 * kSplit) {
     float z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     store8(sm + SM_V, r, c, p.e2, z);
   }
@@ -926,7 +954,7 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
     MMA_GROUP(mb, p.status, mma_issue(tb + R1, kop(sm + SM_P, kW), kop(sm + SM_W, kW), p.e2, kW, false));
     const bool mine = tj == sp;
     if (__any_sync(0xffffffffu, mine)) {
-      for (int c = 32 * hf; c < p.e2; c += 64) {
+      for (int c = 32 * pt; c < p.e2; c += kStride) {
         float v[32], h2[32] = {};
         tc::tmem_ld32(tb + lo + R1 + c, v);
         if (mine) {
@@ -949,7 +977,7 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
     MMA_GROUP(mb, p.status, mma_issue(tb + R1, kop(sm + SM_V, p.e2), kop(sm + SM_W, p.e2), p.e1, p.e2, false));
     const bool mine = tj == sp;
     if (__any_sync(0xffffffffu, mine)) {
-      for (int c = 32 * hf; c < p.e1; c += 64) {
+      for (int c = 32 * pt; c < p.e1; c += kStride) {
         float v[32];
         tc::tmem_ld32(tb + lo + R1 + c, v);
         if (mine)
@@ -967,13 +995,13 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
   // ---- environment adjoint: g_j
   __syncthreads();
   {
-    const float4 o = partner(m, make_float4(drow[0], drow[1], drow[2], ds_emb));
-    drow[0] += o.x;
-    drow[1] += o.y;
-    drow[2] += o.z;
-    ds_emb += o.w;
+    const float4 o = row_sum(m, make_float4(drow[0], drow[1], drow[2], ds_emb));
+    drow[0] = o.x;
+    drow[1] = o.y;
+    drow[2] = o.z;
+    ds_emb = o.w;
   }
-  if (hf == 0 && r < p.nmax) {
+  if (pt == 0 && r < p.nmax) {
     float* gout = p.g + ((size_t)atom * p.nmax + r) * 3;
     if (!valid) {
       gout[0] = gout[1] = gout[2] = 0.f;

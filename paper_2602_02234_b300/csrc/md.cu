@@ -5,12 +5,17 @@
 // F_i = sum_p g_ip - sum_{(k,p'): slot p' of k is atom i} g_kp', with
 // g = dE/dr_ij for r_ij = x_j - x_i.  The second sum is gathered, not
 // scattered: each skin entry (i -> j) knows the index of its mirror entry
-// (j -> i) in j's skin list, and selpos says which kept slot that is, so every
-// force is summed in a fixed order with no atomics (bitwise reproducible).
+// (j -> i) in j's skin list, and selpos says which kept slot that is.  The
+// first sum runs over the kept slots in their (canonical) order.  The second
+// runs in skin-list order, which depends on when the list was last rebuilt,
+// so it is accumulated exactly in 128-bit fixed point (2^-80 resolution) and
+// rounded once: no atomics, and the force does not depend on the rebuild
+// schedule or on which other systems share the batch (bitwise reproducible).
 #include "common.cuh"
 #include "kernels.cuh"
 
 namespace dp {
+
 
 template <typename G>
 __global__ void k_force_gather(int n, int nmax, int cap, const int* __restrict__ sel_j,
@@ -33,6 +38,8 @@ __global__ void k_force_gather(int n, int nmax, int cap, const int* __restrict__
       for (int b = 0; b < 3; ++b) vir[3 * a + b] -= r[a] * gg[b];
     }
   }
+  __int128 fm[3] = {0, 0, 0};
+  bool bad = false;
   int cnt = skin_cnt[i];
   for (int c = lane; c < cnt; c += 32) {
     size_t o = (size_t)i * cap + c;
@@ -42,12 +49,14 @@ __global__ void k_force_gather(int n, int nmax, int cap, const int* __restrict__
     int p = selpos[(size_t)j * cap + mc];
     if (p < 0) continue;
     size_t q = (size_t)j * nmax + p;
-    for (int a = 0; a < 3; ++a) f[a] -= (double)g[3 * q + a];
+    for (int a = 0; a < 3; ++a) fm[a] += to_fixed((double)g[3 * q + a], &bad);
   }
   for (int a = 0; a < 3; ++a) f[a] = warp_sum(f[a]);
+  for (int a = 0; a < 3; ++a) fm[a] = warp_sum_fixed(fm[a]);
   for (int a = 0; a < 9; ++a) vir[a] = warp_sum(vir[a]);
+  bad = __any_sync(0xffffffffu, bad);
   if (lane == 0) {
-    for (int a = 0; a < 3; ++a) F[3 * i + a] = f[a];
+    for (int a = 0; a < 3; ++a) F[3 * i + a] = bad ? quiet_nan() : f[a] - from_fixed(fm[a]);
     for (int a = 0; a < 9; ++a) atom_vir[9 * i + a] = vir[a];
   }
 }

@@ -325,7 +325,8 @@ __global__ void k_gather_in(int nmax, int ed, int cap, const SkinEntry* __restri
   int j = blockIdx.x;
   int cnt = skin_cnt[j];
   for (int c = threadIdx.x; c < ed; c += blockDim.x) {
-    T acc = T(0);
+    __int128 acc = 0;   // skin-list order: summed exactly, see to_fixed
+    bool bad = false;
     for (int s = 0; s < cnt; ++s) {
       size_t o = (size_t)j * cap + s;
       int mc = mirror[o];
@@ -333,9 +334,9 @@ __global__ void k_gather_in(int nmax, int ed, int cap, const SkinEntry* __restri
       int i = skin[o].j;
       int p = selpos[(size_t)i * cap + mc];
       if (p < 0) continue;
-      acc += x[((size_t)i * nmax + p) * ed + c];
+      acc += to_fixed((double)x[((size_t)i * nmax + p) * ed + c], &bad);
     }
-    out[(size_t)j * ed + c] = acc;
+    out[(size_t)j * ed + c] = bad ? (T)quiet_nan() : (T)from_fixed(acc);
   }
 }
 

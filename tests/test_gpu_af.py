@@ -158,6 +158,25 @@ def test_md_resident_state_resume_is_bitwise():
     assert np.array_equal(xb, xc) and np.array_equal(vb, vc)
 
 
+@pytest.mark.parametrize("prec", [dp.PREC_PLAIN_F32, dp.PREC_FUSED])
+def test_trajectory_does_not_depend_on_rebuild_schedule(prec):
+    """Shifting the step counter moves the neighbour-list rebuilds (every 10
+    steps) to other points of the same trajectory; the skin lists then hold
+    their entries in another order, and the forces must not notice (bitwise)."""
+    m, s = C.ATTN_MODEL, serving_system(700, 9)
+    masses = s.masses
+    v0 = maxwell_boltzmann(masses[s.types], 300.0, C.VELOCITY_SEED)
+    out = []
+    for step0 in (0, 5, 7):
+        pot, _ = make(m, s, prec, masses=masses)
+        pot.set_state(s.coords, v0, step=step0)
+        pot.step(23, C.DT_FS)
+        out.append(pot.get_state()[:2])
+        pot.close()
+    for x, v in out[1:]:
+        assert np.array_equal(x, out[0][0]) and np.array_equal(v, out[0][1])
+
+
 def test_dpenergy_autograd_matches_finite_differences():
     import torch
     m = replace(C.ATTN_MODEL, n_layers=1, nmax=64)

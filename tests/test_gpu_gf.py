@@ -89,3 +89,20 @@ def test_gf_md_step_matches_compute():
     assert tr[-1, 0] == pytest.approx(E, rel=1e-12)
     et = tr.sum(1)
     assert np.max(np.abs(et - et[0])) < 1e-6 * abs(et[0])
+
+
+def test_gf_trajectory_does_not_depend_on_rebuild_schedule():
+    """As for the attention family: the incoming-message gather and the force
+    gather run over skin lists whose order depends on when they were built."""
+    m, s = C.GRAPH_MODEL, serving_system(700, 9)
+    w = weights(m)
+    masses = s.masses
+    v0 = maxwell_boltzmann(masses[s.types], 300.0, C.VELOCITY_SEED)
+    out = []
+    for step0 in (0, 6):
+        pot = make(m, s, dp.PREC_PLAIN_F32, w, masses=masses)
+        pot.set_state(s.coords, v0, step=step0)
+        pot.step(17, C.DT_FS)
+        out.append(pot.get_state()[:2])
+        pot.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
