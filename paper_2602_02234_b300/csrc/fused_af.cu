@@ -100,7 +100,7 @@ struct Misc {
   int nvalid;
   uint32_t tptr;
   int pad;
-  unsigned long long bar, wbar, pbar;
+  unsigned long long bar, wbar, pbar, xbar;
 };
 constexpr int kSmemAtom = SM_MISC + (int)sizeof(Misc) + 64;
 static_assert(kSmemAtom <= 227 * 1024, "per-atom shared memory");
@@ -256,6 +256,15 @@ __device__ __forceinline__ void bulk_load(Bar& b, uint8_t* dst, const void* src,
   }
 }
 
+// Thread 0 only, after a barrier that ordered every earlier access to `dst`:
+// arm `b` for `arm` bytes when arm > 0 (one arrival: the first copy of a group
+// carries the group's total), then start the copy.
+__device__ __forceinline__ void issue_copy(Bar& b, uint8_t* dst, const void* src, uint32_t bytes,
+                                           uint32_t arm) {
+  if (arm) tc::mbar_expect_tx(reinterpret_cast<uint64_t*>(b.bar), arm);
+  tc::bulk_g2s(dst, src, bytes, reinterpret_cast<uint64_t*>(b.bar));
+}
+
 // One product group: barrier, issue by thread 0, commit to `mb`, wait.
 #define MMA_GROUP(mb, status, ...)                                   \
   do {                                                               \
@@ -399,26 +408,31 @@ __device__ bool embed_forward(const Params& p, uint8_t* sm, Misc* m, uint32_t tb
   return true;
 }
 
-// Q, K, V of layer l from the G tile into tensor memory R0, R1, R3 and then
-// into 16-bit tiles; weights arrive through the two staging buffers W and P.
-__device__ bool qkv(const Params& p, int l, uint8_t* sm, uint32_t tb, Bar& mb, Bar& wb, Bar& pb,
-                    bool prefetched) {
+// The three input projections of layer l arrive (on xb) in the Q, K and V
+// tiles themselves.
+__device__ void load_qkv_weights(const Params& p, int l, uint8_t* sm, Bar& xb) {
+  tc::fence_async_smem();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    issue_copy(xb, sm + SM_Q, p.WqT + (size_t)l * kTile, kTile, 3 * kTile);
+    issue_copy(xb, sm + SM_K, p.WkT + (size_t)l * kTile, kTile, 0);
+    issue_copy(xb, sm + SM_V, p.WvT + (size_t)l * kTile, kTile, 0);
+  }
+}
+
+// Q, K, V of one layer from the G tile in one product group (R0, R1, R3),
+// then drained as 16-bit tiles over their weights.
+__device__ bool qkv(const Params& p, uint8_t* sm, uint32_t tb, Bar& mb, Bar& xb) {
   const int r = row_id(), pt = part_id();
   const uint32_t lo = lane_base();
-  uint8_t *Wt = sm + SM_W, *Pt = sm + SM_P;
-  if (!prefetched) {
-    bulk_load(wb, Wt, p.WqT + (size_t)l * kTile, kTile);
-    bulk_load(pb, Pt, p.WkT + (size_t)l * kTile, kTile);
-  }
-  if (!wb.wait(p.status)) return false;
-  MMA_GROUP(mb, p.status, mma_issue(tb + R0, kop(sm + SM_G, kW), kop(Wt, kW), kW, kW, false));
-  bulk_load(wb, Wt, p.WvT + (size_t)l * kTile, kTile);
-  if (!pb.wait(p.status)) return false;
-  MMA_GROUP(mb, p.status, mma_issue(tb + R1, kop(sm + SM_G, kW), kop(Pt, kW), kW, kW, false));
-  if (!wb.wait(p.status)) return false;
-  MMA_GROUP(mb, p.status, mma_issue(tb + R3, kop(sm + SM_G, kW), kop(Wt, kW), kW, kW, false));
+  if (!xb.wait(p.status)) return false;
+  MMA_GROUP(mb, p.status,
+            mma_issue(tb + R0, kop(sm + SM_G, kW), kop(sm + SM_Q, kW), kW, kW, false);
+            mma_issue(tb + R1, kop(sm + SM_G, kW), kop(sm + SM_K, kW), kW, kW, false);
+            mma_issue(tb + R3, kop(sm + SM_G, kW), kop(sm + SM_V, kW), kW, kW, false));
   const uint32_t src[3] = {R0, R1, R3};
   uint8_t* dst[3] = {sm + SM_Q, sm + SM_K, sm + SM_V};
+#pragma unroll
   for (int q3 = 0; q3 < 3; ++q3)
     for (int c = 32 * pt; c < kW; c += kStride) {
       float v[32];
@@ -480,28 +494,24 @@ __device__ __forceinline__ float gate(const float* rj, const float4& ck) {
 }
 
 // ------------------------------------------------------------------ forward
+// Barriers: mb tensor-core products, wb the W tile (embedding weights, Wo),
+// xb the projection weights.
 __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32_t tb, Bar& mb,
-                         Bar& wb, Bar& pb) {
+                         Bar& wb, Bar& xb) {
   const int t = threadIdx.x, r = row_id(), pt = part_id();
   const uint32_t lo = lane_base();
   atom_setup(p, atom, m);
   const int ngroups = (m->nvalid + 7) >> 3;
   uint8_t* Gdst = p.Gst + (size_t)atom * (p.n_layers + 1) * kTile;
   if (!embed_forward(p, sm, m, tb, mb, wb)) return false;
+  if (p.n_layers > 0) load_qkv_weights(p, 0, sm, xb);   // H1, H2 tiles are free again
   __syncthreads();
-  bool prefetched = false;
-  if (p.n_layers > 0) {
-    bulk_load(wb, sm + SM_W, p.WqT, kTile);
-    bulk_load(pb, sm + SM_P, p.WkT, kTile);
-    prefetched = true;
-  }
   for (int i = t; i < ngroups * 2048 / 16; i += kThreads)
     reinterpret_cast<int4*>(Gdst)[i] = reinterpret_cast<const int4*>(sm + SM_G)[i];
   const bool valid = m->tj[r] >= 0;
   const float rj[3] = {m->col[r].y, m->col[r].z, m->col[r].w};
   for (int l = 0; l < p.n_layers; ++l) {
-    if (!qkv(p, l, sm, tb, mb, wb, pb, prefetched)) return false;
-    prefetched = false;
+    if (!qkv(p, sm, tb, mb, xb)) return false;
     bulk_load(wb, sm + SM_W, p.WoT + (size_t)l * kTile, kTile);  // lands during the heads
     for (int h = 0; h < p.heads; ++h) {
       MMA_GROUP(mb, p.status,
@@ -535,11 +545,8 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
     tc::fence_before_sync();
     if (!wb.wait(p.status)) return false;
     MMA_GROUP(mb, p.status, mma_issue(tb + R1, kop(sm + SM_Q, kW), kop(sm + SM_W, kW), kW, kW, false));
-    if (l + 1 < p.n_layers) {  // next layer's first two weights land during the LayerNorm
-      bulk_load(wb, sm + SM_W, p.WqT + (size_t)(l + 1) * kTile, kTile);
-      bulk_load(pb, sm + SM_P, p.WkT + (size_t)(l + 1) * kTile, kTile);
-      prefetched = true;
-    }
+    // next layer's projections land in the free Q, K, V tiles during the LayerNorm
+    if (l + 1 < p.n_layers) load_qkv_weights(p, l + 1, sm, xb);
     // residual + LayerNorm over the row's 128 columns: mean, variance, scale
     const float* bo = p.bo + l * kW;
     float sum = 0.f, sq = 0.f;
@@ -622,6 +629,7 @@ __device__ void kernel_prologue(Misc* m) {
     tc::mbar_init(reinterpret_cast<uint64_t*>(&m->bar), 1);
     tc::mbar_init(reinterpret_cast<uint64_t*>(&m->wbar), 1);
     tc::mbar_init(reinterpret_cast<uint64_t*>(&m->pbar), 1);
+    tc::mbar_init(reinterpret_cast<uint64_t*>(&m->xbar), 1);
     tc::fence_mbar_init();
   }
   if (warp == 0) {
@@ -643,16 +651,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_af_fwd(Params p) {
   extern __shared__ __align__(1024) uint8_t sm[];
   Misc* m = reinterpret_cast<Misc*>(sm + SM_MISC);
   kernel_prologue(m);
-  Bar mb{&m->bar, 0u}, wb{&m->wbar, 0u}, pb{&m->pbar, 0u};
+  Bar mb{&m->bar, 0u}, wb{&m->wbar, 0u}, xb{&m->xbar, 0u};
   for (int atom = blockIdx.x; atom < p.n; atom += gridDim.x)
-    if (!fwd_atom(p, atom, sm, m, m->tptr, mb, wb, pb)) break;
+    if (!fwd_atom(p, atom, sm, m, m->tptr, mb, wb, xb)) break;
   kernel_epilogue(m);
 }
 
 // ------------------------------------------------------------------ backward
 // Adjoint of one atom: dE/dD (from the fitting kernel) back to g_ij.
+// Barriers: mb tensor-core products, gb stored activation tiles, wb and xb
+// weight tiles.
 __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32_t tb, Bar& mb,
-                         Bar& wb, Bar& pb) {
+                         Bar& wb, Bar& gb, Bar& xb) {
   const int t = threadIdx.x, r = row_id(), pt = part_id();
   const uint32_t lo = lane_base();
   atom_setup(p, atom, m);
@@ -677,6 +687,7 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
       for (int a = 0; a < 4; ++a) m->T[a][f] = p.Tm[((size_t)atom * 4 + a) * kW + f];
     __syncthreads();
     float v[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
     for (int a = 0; a < 4; ++a) {
       if (pt == 0)
         for (int q = 0; q < p.m2; ++q) v[a] += dDs[f * p.m2 + q] * m->T[a][q];
@@ -692,8 +703,8 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
       m->dT[3][f] = o.w;
     }
   }
-  load_G(sm + SM_G, L, wb);
-  if (ngroups > 0 && !wb.wait(p.status)) return false;
+  load_G(sm + SM_G, L, gb);
+  if (ngroups > 0 && !gb.wait(p.status)) return false;
   __syncthreads();
   {
     float dr[4] = {0.f, 0.f, 0.f, 0.f};
@@ -734,11 +745,23 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
   float drow[3] = {0.f, 0.f, 0.f};  // gate adjoint, row part: sum_k dA_jk w_jk rh_k
   const float rj[3] = {m->col[r].y, m->col[r].z, m->col[r].w};
   for (int l = L - 1; l >= 0; --l) {
-    // ---- stored layer input and output tiles
-    load_G(sm + SM_G, l, wb);
-    load_G(sm + SM_V, l + 1, pb);
-    if (ngroups > 0 && !(wb.wait(p.status) && pb.wait(p.status))) return false;
+    // ---- loads of this layer, all in flight at once: the stored layer input
+    // (G tile) and output (V tile) on gb, Wo^T (W tile) on wb, and the Q and
+    // K weights (Q and K tiles, overwritten by the recomputed Q and K) on xb
+    zero_smem(sm + SM_G + ngroups * 2048, kTile - ngroups * 2048);
+    zero_smem(sm + SM_V + ngroups * 2048, kTile - ngroups * 2048);
+    tc::fence_async_smem();
     __syncthreads();
+    if (t == 0) {
+      if (ngroups > 0) {
+        issue_copy(gb, sm + SM_G, Gsrc + (size_t)l * kTile, ngroups * 2048, 2 * ngroups * 2048);
+        issue_copy(gb, sm + SM_V, Gsrc + (size_t)(l + 1) * kTile, ngroups * 2048, 0);
+      }
+      issue_copy(wb, sm + SM_W, p.WoR + (size_t)l * kTile, kTile, kTile);
+      issue_copy(xb, sm + SM_Q, p.WqT + (size_t)l * kTile, kTile, 2 * kTile);
+      issue_copy(xb, sm + SM_K, p.WkT + (size_t)l * kTile, kTile, 0);
+    }
+    if (ngroups > 0 && !gb.wait(p.status)) return false;
     // ---- LayerNorm adjoint: dZ = rstd (dG - mean dG - Gout mean(dG Gout))
     {
       const float rs = p.rstd[((size_t)atom * L + l) * kW + r];
@@ -772,44 +795,47 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
       }
       tc::fence_before_sync();
     }
-    // ---- recompute Q, K, V (weights through W; R1 and R3 are free)
+    // ---- dO = dZ Wo^T into R1; then Wv into the free W tile and dO (16-bit)
+    // into the free P tile
+    if (!wb.wait(p.status)) return false;
+    MMA_GROUP(mb, p.status, mma_issue(tb + R1, kop(sm + SM_P, kW), kop(sm + SM_W, kW), kW, kW, false));
+    bulk_load(wb, sm + SM_W, p.WvT + (size_t)l * kTile, kTile);
+    for (int c = 32 * pt; c < kW; c += kStride) {
+      float v[32];
+      tc::tmem_ld32(tb + lo + R1 + c, v);
+      store32(sm + SM_P, r, c, kW, kW, v);
+    }
+    tc::fence_before_sync();
+    // ---- recompute Q, K, V in one product group, drained over their weights
     {
-      const uint8_t* Ws[3] = {p.WqT + (size_t)l * kTile, p.WkT + (size_t)l * kTile,
-                              p.WvT + (size_t)l * kTile};
-      const uint32_t dst[3] = {R0, R1, R3};
-      for (int q3 = 0; q3 < 3; ++q3) {
-        bulk_load(wb, sm + SM_W, Ws[q3], kTile);
-        if (!wb.wait(p.status)) return false;
-        MMA_GROUP(mb, p.status,
-                  mma_issue(tb + dst[q3], kop(sm + SM_G, kW), kop(sm + SM_W, kW), kW, kW, false));
-      }
+      const bool ok = xb.wait(p.status);
+      if (!(wb.wait(p.status) && ok)) return false;
+    }
+    MMA_GROUP(mb, p.status,
+              mma_issue(tb + R0, kop(sm + SM_G, kW), kop(sm + SM_Q, kW), kW, kW, false);
+              mma_issue(tb + R1, kop(sm + SM_G, kW), kop(sm + SM_K, kW), kW, kW, false);
+              mma_issue(tb + R3, kop(sm + SM_G, kW), kop(sm + SM_W, kW), kW, kW, false));
+    {
+      const uint32_t src[3] = {R0, R1, R3};
       uint8_t* tiles[3] = {sm + SM_Q, sm + SM_K, sm + SM_V};
+#pragma unroll
       for (int q3 = 0; q3 < 3; ++q3)
         for (int c = 32 * pt; c < kW; c += kStride) {
           float v[32];
-          tc::tmem_ld32(tb + lo + dst[q3] + c, v);
+          tc::tmem_ld32(tb + lo + src[q3] + c, v);
           store32(tiles[q3], r, c, kW, kW, v);
         }
       tc::fence_before_sync();
     }
-    // ---- dO = dZ Wo^T into R1, then the 16-bit tile over G (no longer needed)
-    bulk_load(wb, sm + SM_W, p.WoR + (size_t)l * kTile, kTile);
-    if (!wb.wait(p.status)) return false;
-    MMA_GROUP(mb, p.status, mma_issue(tb + R1, kop(sm + SM_P, kW), kop(sm + SM_W, kW), kW, kW, false));
-    for (int c = 32 * pt; c < kW; c += kStride) {
-      float v[32];
-      tc::tmem_ld32(tb + lo + R1 + c, v);
-      store32(sm + SM_G, r, c, kW, kW, v);
-    }
-    tc::fence_before_sync();
-    // ---- heads
+    // ---- heads.  Tiles: Q, K, V; dO in P; A, then the gate adjoint, in G;
+    // dS in W
     for (int h = 0; h < p.heads; ++h) {
       const int c0 = h * DH;
       // scores
       MMA_GROUP(mb, p.status,
                 mma_issue(tb + R3, kop(sm + SM_Q, kW, c0), kop(sm + SM_K, kW, c0), kW, DH, false));
       const float2 st = p.smx[(((size_t)atom * L + l) * p.heads + h) * kW + r];
-      // w (kept in R3 for the adjoint below) and A = w * gate -> P tile
+      // w (kept in R3 for the adjoint below) and A = w * gate -> G tile
       for (int c = 32 * pt; c < kW; c += kStride) {
         float v[32];
         if (c < nv) {
@@ -822,16 +848,16 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
 #pragma unroll
           for (int q = 0; q < 32; ++q) v[q] = 0.f;
         }
-        store32(sm + SM_P, r, c, kW, kW, v);
+        store32(sm + SM_G, r, c, kW, kW, v);
       }
       tc::fence_before_sync();
       // dA = dO_h V_h^T (R1), dV_h = A^T dO_h (R0 + 2d), O_h = A V_h (R0, consumed
       // below before dQ_h overwrites it)
       MMA_GROUP(mb, p.status,
-                mma_issue(tb + R1, kop(sm + SM_G, kW, c0), kop(sm + SM_V, kW, c0), kW, DH, false);
-                mma_issue(tb + R0 + 2 * DH, mnop(sm + SM_P, kW, 0), mnop(sm + SM_G, kW, c0), DH, kW,
+                mma_issue(tb + R1, kop(sm + SM_P, kW, c0), kop(sm + SM_V, kW, c0), kW, DH, false);
+                mma_issue(tb + R0 + 2 * DH, mnop(sm + SM_G, kW, 0), mnop(sm + SM_P, kW, c0), DH, kW,
                           false);
-                mma_issue(tb + R0, kop(sm + SM_P, kW), mnop(sm + SM_V, kW, c0), DH, kW, false));
+                mma_issue(tb + R0, kop(sm + SM_G, kW), mnop(sm + SM_V, kW, c0), DH, kW, false));
       // sum_k w_jk dw_jk = sum_k A_jk dA_jk = dO_j . O_j over this head's
       // columns; every part forms it whole (same order, same value)
       float wdw = 0.f;
@@ -841,41 +867,43 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
         float a4[4] = {0.f, 0.f, 0.f, 0.f};
         for (int q = 0; q < DH; q += 8) {
           float g8[8];
-          load8(sm + SM_G, r, c0 + q, kW, g8);
+          load8(sm + SM_P, r, c0 + q, kW, g8);
 #pragma unroll
           for (int e = 0; e < 8; ++e) a4[e & 3] += g8[e] * o[q + e];
         }
         wdw = (a4[0] + a4[1]) + (a4[2] + a4[3]);
       }
-      // softmax + gate adjoint for this row
+      // softmax + gate adjoint for this row, 16 columns at a time
       for (int c = 32 * pt; c < kW; c += kStride) {
         if (c < nv) {
-          float s[32], da[32];
-          tc::tmem_ld32(tb + lo + R3 + c, s);
-          tc::tmem_ld32(tb + lo + R1 + c, da);
 #pragma unroll
-          for (int q8 = 0; q8 < 32; q8 += 8) {
-            float ds[8], x[8];
+          for (int c16 = 0; c16 < 32; c16 += 16) {
+            float s[16], da[16];
+            tc::tmem_ld16x2(tb + lo + R3 + c + c16, s, tb + lo + R1 + c + c16, da);
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-              const int q = q8 + e;
-              const float4 ck = m->col[c + q];
-              const float dw = da[q] * gate(rj, ck);
-              x[e] = da[q] * s[q];                  // gate adjoint dc_jk
-              drow[0] += x[e] * ck.y;
-              drow[1] += x[e] * ck.z;
-              drow[2] += x[e] * ck.w;
-              ds[e] = s[q] * (dw - wdw);            // dS_jk = w (dw - sum w dw)
+            for (int q8 = 0; q8 < 16; q8 += 8) {
+              float ds[8], x[8];
+#pragma unroll
+              for (int e = 0; e < 8; ++e) {
+                const int q = q8 + e;
+                const float4 ck = m->col[c + c16 + q];
+                const float dw = da[q] * gate(rj, ck);
+                x[e] = da[q] * s[q];                  // gate adjoint dc_jk
+                drow[0] += x[e] * ck.y;
+                drow[1] += x[e] * ck.z;
+                drow[2] += x[e] * ck.w;
+                ds[e] = s[q] * (dw - wdw);            // dS_jk = w (dw - sum w dw)
+              }
+              store8(sm + SM_W, r, c + c16 + q8, kW, ds);
+              store8(sm + SM_G, r, c + c16 + q8, kW, x);
             }
-            store8(sm + SM_W, r, c + q8, kW, ds);
-            store8(sm + SM_P, r, c + q8, kW, x);
           }
         } else {
           float z[32];
 #pragma unroll
           for (int q = 0; q < 32; ++q) z[q] = 0.f;
           store32(sm + SM_W, r, c, kW, kW, z);
-          store32(sm + SM_P, r, c, kW, kW, z);
+          store32(sm + SM_G, r, c, kW, kW, z);
         }
       }
       tc::fence_before_sync();
@@ -885,7 +913,7 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
                 mma_issue(tb + R0, kop(sm + SM_W, kW), mnop(sm + SM_K, kW, c0), DH, kW, false);
                 mma_issue(tb + R0 + DH, mnop(sm + SM_W, kW, 0), mnop(sm + SM_Q, kW, c0), DH, kW, false);
                 mma_issue(tb + R0 + 112, mnop(sm + SM_W, kW, 0), kop(m->ones, kW), 16, kW, h > 0);
-                mma_issue(tb + R0 + 96, mnop(sm + SM_P, kW, 0), kop(m->rhb, kW), 16, kW, h > 0));
+                mma_issue(tb + R0 + 96, mnop(sm + SM_G, kW, 0), kop(m->rhb, kW), 16, kW, h > 0));
       // write dQ_h, dK_h, dV_h (R0 columns [0,32), [32,64), [64,96)) over the
       // head's columns of Q, K, V; each part of a row takes 32 / kSplit columns
       {
@@ -914,22 +942,28 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
       m->drc[r][2] += v[2];
       if (valid && m->sw[r] > 0.f) m->dswa[r] += v[16] / m->sw[r];
     }
-    // ---- dG_in = dZ + dQ Wq^T + dK Wk^T + dV Wv^T, accumulated onto R2
-    {
-      const uint8_t* Ws[3] = {p.WqR + (size_t)l * kTile, p.WkR + (size_t)l * kTile,
-                              p.WvR + (size_t)l * kTile};
-      uint8_t* As[3] = {sm + SM_Q, sm + SM_K, sm + SM_V};
-      for (int q3 = 0; q3 < 3; ++q3) {
-        bulk_load(wb, sm + SM_W, Ws[q3], kTile);
-        if (!wb.wait(p.status)) return false;
-        MMA_GROUP(mb, p.status, mma_issue(tb + R2, kop(As[q3], kW), kop(sm + SM_W, kW), kW, kW, true));
-      }
+    // ---- dG_in = dZ + dQ Wq^T + dK Wk^T + dV Wv^T, accumulated onto R2; the
+    // three weights arrive together in the free W, G and P tiles
+    tc::fence_async_smem();
+    __syncthreads();
+    if (t == 0) {
+      issue_copy(wb, sm + SM_W, p.WqR + (size_t)l * kTile, kTile, kTile);
+      issue_copy(xb, sm + SM_G, p.WkR + (size_t)l * kTile, kTile, 2 * kTile);
+      issue_copy(xb, sm + SM_P, p.WvR + (size_t)l * kTile, kTile, 0);
     }
+    {
+      const bool ok = wb.wait(p.status);
+      if (!(xb.wait(p.status) && ok)) return false;
+    }
+    MMA_GROUP(mb, p.status,
+              mma_issue(tb + R2, kop(sm + SM_Q, kW), kop(sm + SM_W, kW), kW, kW, true);
+              mma_issue(tb + R2, kop(sm + SM_K, kW), kop(sm + SM_G, kW), kW, kW, true);
+              mma_issue(tb + R2, kop(sm + SM_V, kW), kop(sm + SM_P, kW), kW, kW, true));
   }
   // ---- embedding adjoint: dG0 (R2) -> ds
   if (!embed_h2(p, sm, m, tb, mb, wb, sm + SM_Q, sm + SM_K)) return false;
-  load_G(sm + SM_G, 0, pb);
-  if (ngroups > 0 && !pb.wait(p.status)) return false;
+  load_G(sm + SM_G, 0, gb);
+  if (ngroups > 0 && !gb.wait(p.status)) return false;
   __syncthreads();
   for (int c = 32 * pt; c < kW; c += kStride) {  // da3 = dG0 (1 - G0^2) -> P tile
     float dg[32], g0[32];
@@ -1035,9 +1069,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_af_bwd(Params p) {
   if (threadIdx.x < kW)
     *reinterpret_cast<op_t*>(m->ones + tc::kmajor_off(0, threadIdx.x, kW)) = f2op(1.f);
   __syncthreads();
-  Bar mb{&m->bar, 0u}, wb{&m->wbar, 0u}, pb{&m->pbar, 0u};
+  Bar mb{&m->bar, 0u}, wb{&m->wbar, 0u}, gb{&m->pbar, 0u}, xb{&m->xbar, 0u};
   for (int atom = blockIdx.x; atom < p.n; atom += gridDim.x)
-    if (!bwd_atom(p, atom, sm, m, m->tptr, mb, wb, pb)) break;
+    if (!bwd_atom(p, atom, sm, m, m->tptr, mb, wb, gb, xb)) break;
   kernel_epilogue(m);
 }
 
