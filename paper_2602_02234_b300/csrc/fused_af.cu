@@ -67,6 +67,7 @@ constexpr int kFitThreads = 128; // fitting kernel: one thread per atom row
 constexpr long long kPolls = 1LL << 22;
 constexpr uint32_t R0 = 0, R1 = 128, R2 = 256, R3 = 384;
 constexpr int kTile = kW * kW * 2;  // one 128 x 128 16-bit tile: 32 KB
+constexpr int kDH = 32;             // head width (4 heads over the 128 attention columns)
 
 // Thread roles of the per-atom kernels.  Thread t serves neighbour row
 // r = t mod 128, which is tensor-memory lane r (warp t/32 reads lane quarter
@@ -670,7 +671,7 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
   const int L = p.n_layers;
   const uint8_t* Gsrc = p.Gst + (size_t)atom * (L + 1) * kTile;
   const bool valid = m->tj[r] >= 0;
-  const int DH = p.dh;
+  constexpr int DH = kDH;
   const int nv = m->nvalid;
   // load a stored G tile: real row groups by bulk copy, the rest zero
   auto load_G = [&](uint8_t* dst, int l, Bar& b) {
@@ -742,7 +743,6 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
             f2op(valid ? m->rh[r][a] : 0.f);
     }
   }
-  float drow[3] = {0.f, 0.f, 0.f};  // gate adjoint, row part: sum_k dA_jk w_jk rh_k
   const float rj[3] = {m->col[r].y, m->col[r].z, m->col[r].w};
   for (int l = L - 1; l >= 0; --l) {
     // ---- loads of this layer, all in flight at once: the stored layer input
@@ -865,6 +865,7 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
         float o[32];
         tc::tmem_ld32(tb + lo + R0, o);
         float a4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
         for (int q = 0; q < DH; q += 8) {
           float g8[8];
           load8(sm + SM_P, r, c0 + q, kW, g8);
@@ -889,9 +890,6 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
                 const float4 ck = m->col[c + c16 + q];
                 const float dw = da[q] * gate(rj, ck);
                 x[e] = da[q] * s[q];                  // gate adjoint dc_jk
-                drow[0] += x[e] * ck.y;
-                drow[1] += x[e] * ck.z;
-                drow[2] += x[e] * ck.w;
                 ds[e] = s[q] * (dw - wdw);            // dS_jk = w (dw - sum w dw)
               }
               store8(sm + SM_W, r, c + c16 + q8, kW, ds);
@@ -907,13 +905,23 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
         }
       }
       tc::fence_before_sync();
-      // dQ_h = dS K_h, dK_h = dS^T Q_h (scaled at drain), column sums of dS
-      // (ones) and of the gate adjoint weighted by rh_j, accumulated over heads
+      // dQ_h = dS K_h, dK_h = dS^T Q_h (scaled at drain); column sums of dS
+      // (ones) and of the gate adjoint weighted by rh_j (accumulated over
+      // heads); row sums of the gate adjoint weighted by rh_k (R3, this head)
       MMA_GROUP(mb, p.status,
                 mma_issue(tb + R0, kop(sm + SM_W, kW), mnop(sm + SM_K, kW, c0), DH, kW, false);
                 mma_issue(tb + R0 + DH, mnop(sm + SM_W, kW, 0), mnop(sm + SM_Q, kW, c0), DH, kW, false);
                 mma_issue(tb + R0 + 112, mnop(sm + SM_W, kW, 0), kop(m->ones, kW), 16, kW, h > 0);
-                mma_issue(tb + R0 + 96, mnop(sm + SM_G, kW, 0), kop(m->rhb, kW), 16, kW, h > 0));
+                mma_issue(tb + R0 + 96, mnop(sm + SM_G, kW, 0), kop(m->rhb, kW), 16, kW, h > 0);
+                mma_issue(tb + R3, kop(sm + SM_G, kW), kop(m->rhb, kW), 16, kW, false));
+      // the gate adjoint's row part, sum_k dc_jk rh_k, joins the column part in drc
+      if (pt == 0) {
+        float v[8];
+        tc::tmem_ld8(tb + lo + R3, v);
+        m->drc[r][0] += v[0];
+        m->drc[r][1] += v[1];
+        m->drc[r][2] += v[2];
+      }
       // write dQ_h, dK_h, dV_h (R0 columns [0,32), [32,64), [64,96)) over the
       // head's columns of Q, K, V; each part of a row takes 32 / kSplit columns
       {
@@ -1014,14 +1022,17 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
       for (int c = 32 * pt; c < p.e1; c += kStride) {
         float v[32];
         tc::tmem_ld32(tb + lo + R1 + c, v);
-        if (mine)
-          for (int q = 0; q < 32 && c + q < p.e1; q += 8) {
+        if (mine) {
+#pragma unroll
+          for (int q = 0; q < 32; q += 8) {
+            if (c + q >= p.e1) break;
             float h8[8];
             load8(sm + SM_Q, r, c + q, p.e1, h8);   // h1 (16-bit copy from the H1 tile)
 #pragma unroll
             for (int e = 0; e < 8; ++e)
               ds_emb += v[q + e] * (1.f - h8[e] * h8[e]) * p.W1[sp * p.e1 + c + q + e];
           }
+        }
       }
     }
     tc::fence_before_sync();
@@ -1029,11 +1040,7 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
   // ---- environment adjoint: g_j
   __syncthreads();
   {
-    const float4 o = row_sum(m, make_float4(drow[0], drow[1], drow[2], ds_emb));
-    drow[0] = o.x;
-    drow[1] = o.y;
-    drow[2] = o.z;
-    ds_emb = o.w;
+    ds_emb = row_sum(m, make_float4(0.f, 0.f, 0.f, ds_emb)).w;
   }
   if (pt == 0 && r < p.nmax) {
     float* gout = p.g + ((size_t)atom * p.nmax + r) * 3;
@@ -1047,7 +1054,7 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
       float dr[3];
       for (int a = 0; a < 3; ++a) {
         dst += m->dRt[r][1 + a] * rr[a];
-        dr[a] = (drow[a] + m->drc[r][a]) * un + s * m->dRt[r][1 + a];
+        dr[a] = m->drc[r][a] * un + s * m->dRt[r][1 + a];
       }
       const float radial = dst * (dswr / d - sw / (d * d)) + m->dswa[r] * un * dswr;
       const float proj = dr[0] * rr[0] + dr[1] * rr[1] + dr[2] * rr[2];
