@@ -323,15 +323,37 @@ __device__ void atom_setup(const Params& p, int atom, Misc* m) {
 }
 
 // ------------------------------------------------------------------ embedding
+// Species loop over the set bits of `mask` in increasing order: the weight
+// block of species sp (bytes at base + sp * stride) arrives in one of two free
+// tiles, the next species' block is already on its way into the other one
+// while body(sp, tile) runs.  Barriers k0, k1 belong to the two tiles.
+template <typename F>
+__device__ bool species_loop(unsigned mask, const uint8_t* base, size_t stride, uint32_t bytes,
+                             uint8_t* t0, uint8_t* t1, Bar& k0, Bar& k1, int* status, F&& body) {
+  if (!mask) return true;
+  int sp = __ffs(mask) - 1;
+  int slot = 0;
+  bulk_load(k0, t0, base + (size_t)sp * stride, bytes);
+  while (sp >= 0) {
+    const unsigned rest = sp < 31 ? mask & ~((2u << sp) - 1u) : 0u;
+    const int nx = rest ? __ffs(rest) - 1 : -1;
+    if (nx >= 0) bulk_load(slot ? k0 : k1, slot ? t0 : t1, base + (size_t)nx * stride, bytes);
+    if (!(slot ? k1 : k0).wait(status)) return false;
+    if (!body(sp, slot ? t1 : t0)) return false;
+    sp = nx;
+    slot ^= 1;
+  }
+  return true;
+}
+
 // Layer 1 on the SIMT cores into the K-major tile H1, layer 2 on the tensor
-// cores species by species into H2 (16-bit).
-__device__ bool embed_h2(const Params& p, uint8_t* sm, Misc* m, uint32_t tb, Bar& mb, Bar& wb,
-                         uint8_t* H1, uint8_t* H2) {
+// cores species by species into H2 (16-bit); weights through tiles w0, w1.
+__device__ bool embed_h2(const Params& p, uint8_t* sm, Misc* m, uint32_t tb, Bar& mb, Bar& k0,
+                         Bar& k1, uint8_t* H1, uint8_t* H2, uint8_t* w0, uint8_t* w1) {
   const int r = row_id(), pt = part_id();
   const uint32_t lo = lane_base();
   const int tj = m->tj[r];
   const float s = m->s[r];
-  uint8_t* Wt = sm + SM_W;
   for (int c = 8 * pt; c < p.e1; c += 8 * kSplit) {
     float v[8];
 #pragma unroll
@@ -343,39 +365,37 @@ __device__ bool embed_h2(const Params& p, uint8_t* sm, Misc* m, uint32_t tb, Bar
     float z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     store8(H2, r, c, p.e2, z);
   }
-  const int mask = m->mask;
-  for (int sp = 0; sp < 32; ++sp) {
-    if (!(mask & (1 << sp))) continue;
-    bulk_load(wb, Wt, p.W2T + (size_t)sp * p.e2 * p.e1 * 2, p.e2 * p.e1 * 2);
-    if (!wb.wait(p.status)) return false;
+  const uint32_t bytes = p.e2 * p.e1 * 2;
+  return species_loop((unsigned)m->mask, p.W2T, bytes, bytes, w0, w1, k0, k1, p.status,
+                      [&](int sp, uint8_t* Wt) -> bool {
     MMA_GROUP(mb, p.status, mma_issue(tb + R0, kop(H1, p.e1), kop(Wt, p.e1), p.e2, p.e1, false));
     const bool mine = tj == sp;
     if (__any_sync(0xffffffffu, mine)) {
-      for (int c = 32 * pt; c < p.e2; c += kStride) {
-        float v[32];
-        tc::tmem_ld32(tb + lo + R0 + c, v);
+      for (int c = 16 * pt; c < p.e2; c += 16 * kSplit) {
+        float v[16];
+        tc::tmem_ld16(tb + lo + R0 + c, v);
         if (mine) {
 #pragma unroll
-          for (int q = 0; q < 32; ++q)
-            if (c + q < p.e2) v[q] = tanhf(v[q] + p.b2[sp * p.e2 + c + q]);
-          store32(H2, r, c, p.e2, p.e2, v);
+          for (int q = 0; q < 16; ++q) v[q] = tanhf(v[q] + p.b2[sp * p.e2 + c + q]);
+          store8(H2, r, c, p.e2, v);
+          store8(H2, r, c + 8, p.e2, v + 8);
         }
       }
     }
     tc::fence_before_sync();
-  }
-  return true;
+    return true;
+  });
 }
 
-// G0 into the G tile (16-bit) and R2 (FP32).
-__device__ bool embed_forward(const Params& p, uint8_t* sm, Misc* m, uint32_t tb, Bar& mb, Bar& wb) {
+// G0 into the G tile (16-bit) and R2 (FP32).  Tiles: H1 in Q, H2 in K,
+// weights through W and P.
+__device__ bool embed_forward(const Params& p, uint8_t* sm, Misc* m, uint32_t tb, Bar& mb, Bar& wb,
+                              Bar& xb) {
   const int r = row_id(), pt = part_id();
   const uint32_t lo = lane_base();
-  uint8_t* H1 = sm + SM_Q;
   uint8_t* H2 = sm + SM_K;
-  uint8_t* Wt = sm + SM_W;
   uint8_t* Gt = sm + SM_G;
-  if (!embed_h2(p, sm, m, tb, mb, wb, H1, H2)) return false;
+  if (!embed_h2(p, sm, m, tb, mb, wb, xb, sm + SM_Q, H2, sm + SM_W, sm + SM_P)) return false;
   const int tj = m->tj[r];
   zero_smem(Gt, kTile);
   {
@@ -384,29 +404,30 @@ __device__ bool embed_forward(const Params& p, uint8_t* sm, Misc* m, uint32_t tb
     for (int q = 0; q < 32; ++q) z[q] = 0.f;
     for (int c = 32 * pt; c < kW; c += kStride) tc::tmem_st32(tb + lo + R2 + c, z);
   }
-  const int mask = m->mask;
-  for (int sp = 0; sp < 32; ++sp) {
-    if (!(mask & (1 << sp))) continue;
-    bulk_load(wb, Wt, p.W3T + (size_t)sp * kW * p.e2 * 2, kW * p.e2 * 2);
-    if (!wb.wait(p.status)) return false;
+  const uint32_t bytes = kW * p.e2 * 2;
+  return species_loop((unsigned)m->mask, p.W3T, bytes, bytes, sm + SM_W, sm + SM_P, wb, xb,
+                      p.status, [&](int sp, uint8_t* Wt) -> bool {
     MMA_GROUP(mb, p.status, mma_issue(tb + R1, kop(H2, p.e2), kop(Wt, p.e2), kW, p.e2, false));
     const bool mine = tj == sp;
     if (__any_sync(0xffffffffu, mine)) {
       for (int c = 32 * pt; c < kW; c += kStride) {
-        float v[32], old[32];
-        tc::tmem_ld32(tb + lo + R1 + c, v);
-        tc::tmem_ld32(tb + lo + R2 + c, old);
-        if (mine) {
 #pragma unroll
-          for (int q = 0; q < 32; ++q) old[q] = tanhf(v[q] + p.b3[sp * kW + c + q]);
-          store32(Gt, r, c, kW, kW, old);
+        for (int c16 = 0; c16 < 32; c16 += 16) {
+          float v[16], g[16];
+          tc::tmem_ld16x2(tb + lo + R1 + c + c16, v, tb + lo + R2 + c + c16, g);
+          if (mine) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) g[q] = tanhf(v[q] + p.b3[sp * kW + c + c16 + q]);
+            store8(Gt, r, c + c16, kW, g);
+            store8(Gt, r, c + c16 + 8, kW, g + 8);
+          }
+          tc::tmem_st16(tb + lo + R2 + c + c16, g);
         }
-        tc::tmem_st32(tb + lo + R2 + c, old);
       }
     }
     tc::fence_before_sync();
-  }
-  return true;
+    return true;
+  });
 }
 
 // The three input projections of layer l arrive (on xb) in the Q, K and V
@@ -504,7 +525,7 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
   atom_setup(p, atom, m);
   const int ngroups = (m->nvalid + 7) >> 3;
   uint8_t* Gdst = p.Gst + (size_t)atom * (p.n_layers + 1) * kTile;
-  if (!embed_forward(p, sm, m, tb, mb, wb)) return false;
+  if (!embed_forward(p, sm, m, tb, mb, wb, xb)) return false;
   if (p.n_layers > 0) load_qkv_weights(p, 0, sm, xb);   // H1, H2 tiles are free again
   __syncthreads();
   for (int i = t; i < ngroups * 2048 / 16; i += kThreads)
@@ -968,9 +989,11 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
               mma_issue(tb + R2, kop(sm + SM_K, kW), kop(sm + SM_G, kW), kW, kW, true);
               mma_issue(tb + R2, kop(sm + SM_V, kW), kop(sm + SM_P, kW), kW, kW, true));
   }
-  // ---- embedding adjoint: dG0 (R2) -> ds
-  if (!embed_h2(p, sm, m, tb, mb, wb, sm + SM_Q, sm + SM_K)) return false;
+  // ---- embedding adjoint: dG0 (R2) -> ds.  G0 lands in the G tile while H1
+  // (Q tile) and H2 (K tile) are recomputed with weights through W and P.
   load_G(sm + SM_G, 0, gb);
+  if (!embed_h2(p, sm, m, tb, mb, wb, xb, sm + SM_Q, sm + SM_K, sm + SM_W, sm + SM_P))
+    return false;
   if (ngroups > 0 && !gb.wait(p.status)) return false;
   __syncthreads();
   for (int c = 32 * pt; c < kW; c += kStride) {  // da3 = dG0 (1 - G0^2) -> P tile
@@ -984,58 +1007,66 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
   }
   tc::fence_before_sync();
   const int tj = m->tj[r];
-  const int mask = m->mask;
   for (int c = 8 * pt; c < p.e2; c += 8 * kSplit) {
     float z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     store8(sm + SM_V, r, c, p.e2, z);
   }
-  for (int sp = 0; sp < 32; ++sp) {  // da2 = (da3 W3^T) (1 - h2^2) -> V tile
-    if (!(mask & (1 << sp))) continue;
-    bulk_load(wb, sm + SM_W, p.W3R + (size_t)sp * p.e2 * kW * 2, p.e2 * kW * 2);
-    if (!wb.wait(p.status)) return false;
-    MMA_GROUP(mb, p.status, mma_issue(tb + R1, kop(sm + SM_P, kW), kop(sm + SM_W, kW), p.e2, kW, false));
-    const bool mine = tj == sp;
-    if (__any_sync(0xffffffffu, mine)) {
-      for (int c = 32 * pt; c < p.e2; c += kStride) {
-        float v[32], h2[32] = {};
-        tc::tmem_ld32(tb + lo + R1 + c, v);
-        if (mine) {
+  // da2 = (da3 W3^T) (1 - h2^2) -> V tile; weights through W and G
+  {
+    const uint32_t bytes = p.e2 * kW * 2;
+    const bool ok = species_loop((unsigned)m->mask, p.W3R, bytes, bytes, sm + SM_W, sm + SM_G, wb,
+                                 xb, p.status, [&](int sp, uint8_t* Wt) -> bool {
+      MMA_GROUP(mb, p.status, mma_issue(tb + R1, kop(sm + SM_P, kW), kop(Wt, kW), p.e2, kW, false));
+      const bool mine = tj == sp;
+      if (__any_sync(0xffffffffu, mine)) {
+        for (int c = 32 * pt; c < p.e2; c += kStride) {
+          float v[32], h2[32] = {};
+          tc::tmem_ld32(tb + lo + R1 + c, v);
+          if (mine) {
 #pragma unroll
-          for (int q = 0; q < 32; q += 8)
-            if (c + q < p.e2) load8(sm + SM_K, r, c + q, p.e2, h2 + q);
+            for (int q = 0; q < 32; q += 8)
+              if (c + q < p.e2) load8(sm + SM_K, r, c + q, p.e2, h2 + q);
 #pragma unroll
-          for (int q = 0; q < 32; ++q) v[q] *= c + q < p.e2 ? 1.f - h2[q] * h2[q] : 0.f;
-          store32(sm + SM_V, r, c, p.e2, p.e2, v);
-        }
-      }
-    }
-    tc::fence_before_sync();
-  }
-  float ds_emb = 0.f;
-  for (int sp = 0; sp < 32; ++sp) {  // da1 = (da2 W2^T) (1 - h1^2); ds = da1 . W1
-    if (!(mask & (1 << sp))) continue;
-    bulk_load(wb, sm + SM_W, p.W2R + (size_t)sp * p.e1 * p.e2 * 2, p.e1 * p.e2 * 2);
-    if (!wb.wait(p.status)) return false;
-    MMA_GROUP(mb, p.status, mma_issue(tb + R1, kop(sm + SM_V, p.e2), kop(sm + SM_W, p.e2), p.e1, p.e2, false));
-    const bool mine = tj == sp;
-    if (__any_sync(0xffffffffu, mine)) {
-      for (int c = 32 * pt; c < p.e1; c += kStride) {
-        float v[32];
-        tc::tmem_ld32(tb + lo + R1 + c, v);
-        if (mine) {
-#pragma unroll
-          for (int q = 0; q < 32; q += 8) {
-            if (c + q >= p.e1) break;
-            float h8[8];
-            load8(sm + SM_Q, r, c + q, p.e1, h8);   // h1 (16-bit copy from the H1 tile)
-#pragma unroll
-            for (int e = 0; e < 8; ++e)
-              ds_emb += v[q + e] * (1.f - h8[e] * h8[e]) * p.W1[sp * p.e1 + c + q + e];
+            for (int q = 0; q < 32; ++q) v[q] *= c + q < p.e2 ? 1.f - h2[q] * h2[q] : 0.f;
+            store32(sm + SM_V, r, c, p.e2, p.e2, v);
           }
         }
       }
-    }
-    tc::fence_before_sync();
+      tc::fence_before_sync();
+      return true;
+    });
+    if (!ok) return false;
+  }
+  // da1 = (da2 W2^T) (1 - h1^2); ds = da1 . W1
+  float ds_emb = 0.f;
+  {
+    const uint32_t bytes = p.e1 * p.e2 * 2;
+    const bool ok = species_loop((unsigned)m->mask, p.W2R, bytes, bytes, sm + SM_W, sm + SM_G, wb,
+                                 xb, p.status, [&](int sp, uint8_t* Wt) -> bool {
+      MMA_GROUP(mb, p.status,
+                mma_issue(tb + R1, kop(sm + SM_V, p.e2), kop(Wt, p.e2), p.e1, p.e2, false));
+      const bool mine = tj == sp;
+      if (__any_sync(0xffffffffu, mine)) {
+        for (int c = 32 * pt; c < p.e1; c += kStride) {
+          float v[32];
+          tc::tmem_ld32(tb + lo + R1 + c, v);
+          if (mine) {
+#pragma unroll
+            for (int q = 0; q < 32; q += 8) {
+              if (c + q >= p.e1) break;
+              float h8[8];
+              load8(sm + SM_Q, r, c + q, p.e1, h8);   // h1 (16-bit copy from the H1 tile)
+#pragma unroll
+              for (int e = 0; e < 8; ++e)
+                ds_emb += v[q + e] * (1.f - h8[e] * h8[e]) * p.W1[sp * p.e1 + c + q + e];
+            }
+          }
+        }
+      }
+      tc::fence_before_sync();
+      return true;
+    });
+    if (!ok) return false;
   }
   // ---- environment adjoint: g_j
   __syncthreads();

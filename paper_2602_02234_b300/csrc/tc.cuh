@@ -188,6 +188,21 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
 #undef DP_R4
 #undef DP_O4
 
+// Warp-collective store of 16 consecutive FP32 columns (same lane mapping).
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
+  uint32_t r[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) r[q] = __float_as_uint(v[q]);
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+      "r"(r[15])
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 // Warp-collective store of 32 consecutive FP32 columns (same lane mapping).
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
   uint32_t r[32];
