@@ -86,7 +86,7 @@ constexpr int SM_G = 0, SM_Q = kTile, SM_K = 2 * kTile, SM_V = 3 * kTile, SM_P =
 struct Misc {
   uint8_t ones[16 * kW * 2];  // 16 x 128 K-major operand: row 0 ones (column sums)
   uint8_t rhb[16 * kW * 2];   // rows 0..2: unit-vector components of each slot
-  float4 col[kW];             // per neighbour slot: {sw, rh_x, rh_y, rh_z}
+  float4 col[kW];             // per neighbour slot: {log2 sw (-inf if empty), rh_x, rh_y, rh_z}
   float4 xch[kSplit][kW];     // exchange of per-row partial results
   float sw[kW], dsw[kW], s[kW], d[kW];
   float rh[kW][3];
@@ -119,7 +119,7 @@ struct Params {
   const float *W1, *b1, *b2, *b3, *bo;   // FP32 vectors
   uint8_t* Gst;                           // [n][L+1][32 KB]
   float* rstd;                            // [n][L][128]
-  float2* smx;                            // [n][L][heads][128] softmax {log2 max, 1/Z}
+  float* smx;                             // [n][L][heads][128] softmax log2-normaliser beta
   op_t* D;                                // [n][128 * m2]
   float* Tm;                              // [n][4][128]
   const float* dD;                        // [n][128 * m2]
@@ -156,11 +156,17 @@ __device__ __forceinline__ Opnd mnop(const uint8_t* p, int Kx, int mn0, int koff
   return Opnd{tc::smem_u32(p), Kx, 1, mn0, koff};
 }
 // Issue D (+)= A B over K (thread 0 only): K/16 instructions of 128 x N x 16.
+// The descriptors are formed once: a K step of 16 moves a K-major operand by
+// two core matrices (256 bytes) and an MN-major one by two row groups
+// (32 Kx bytes); the start-address field counts 16-byte units and stays below
+// 2^14 for any shared-memory address.
 __device__ __forceinline__ void mma_issue(uint32_t d, const Opnd& A, const Opnd& B, int N, int K,
                                           bool acc) {
   const uint32_t id = tc::idesc_f16(128, N, A.mn, B.mn, kFmt);
-  for (int ks = 0; ks < K; ks += 16)
-    tc::mma_bf16(d, odesc(A, ks), odesc(B, ks), id, (acc || ks > 0) ? 1u : 0u);
+  uint64_t da = odesc(A, 0), db = odesc(B, 0);
+  const uint64_t ia = A.mn ? (uint64_t)(2 * A.Kx) : 16u, ib = B.mn ? (uint64_t)(2 * B.Kx) : 16u;
+  for (int ks = 0; ks < K; ks += 16, da += ia, db += ib)
+    tc::mma_bf16(d, da, db, id, (acc || ks > 0) ? 1u : 0u);
 }
 
 __device__ __forceinline__ void zero_smem(uint8_t* dst, int bytes) {
@@ -285,7 +291,7 @@ __device__ void env_row(const Params& p, int atom, Misc* m, int t) {
     m->sw[t] = 0.f; m->dsw[t] = 0.f; m->s[t] = 0.f; m->d[t] = 1.f;
     for (int a = 0; a < 3; ++a) m->rh[t][a] = 0.f;
     for (int a = 0; a < 4; ++a) m->Rt[t][a] = 0.f;
-    m->col[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    m->col[t] = make_float4(-INFINITY, 0.f, 0.f, 0.f);
     m->tj[t] = -1;
     return;
   }
@@ -301,7 +307,7 @@ __device__ void env_row(const Params& p, int atom, Misc* m, int t) {
     m->rh[t][a] = r[a] / d;
     m->Rt[t][1 + a] = s * r[a] / d;
   }
-  m->col[t] = make_float4(sw, r[0] / d, r[1] / d, r[2] / d);
+  m->col[t] = make_float4(sw > 0.f ? log2f(sw) : -INFINITY, r[0] / d, r[1] / d, r[2] / d);
   m->tj[t] = p.types[j];
 }
 
@@ -465,28 +471,31 @@ __device__ bool qkv(const Params& p, uint8_t* sm, uint32_t tb, Bar& mb, Bar& xb)
   return true;
 }
 
-// Softmax statistics of row r of the head scores in tensor memory: each part
-// runs one pass over its 32-column chunks (running maximum, rescaled sum) and
-// the partial results of the row are merged.  b = max_k S_jk log2(e)/sqrt(d) over real
-// columns, 1/Z with Z = sum_k sw_k 2^(S_jk log2(e)/sqrt(d) - b); 1/Z = 0 for an
-// empty slot.
-__device__ float2 softmax_stats(const Params& p, Misc* m, uint32_t taddr) {
+// Softmax normaliser of row r of the head scores in tensor memory.  With
+// u_jk = S_jk log2(e)/sqrt(d) + log2 sw_k (-inf for an empty column) the
+// weights are w_jk = 2^(u_jk - beta_j), beta_j = log2 sum_k 2^u_jk.  Each part
+// takes one pass over its 32-column chunks (running maximum, rescaled sum) and
+// the partial results of the row are merged.  beta = +inf for an empty row, so
+// that all its weights vanish.
+__device__ float softmax_beta(const Params& p, Misc* m, uint32_t taddr) {
   const float a = p.inv_sqrt_d * 1.4426950408889634f;
   const int nv = m->nvalid;
-  float mx = -1e30f, z = 0.f;
+  float mx = -INFINITY, z = 0.f;
   for (int c = 32 * part_id(); c < nv; c += kStride) {
     float v[32];
     tc::tmem_ld32(taddr + c, v);
-    float cm = -1e30f;
+    float cm = -INFINITY;
 #pragma unroll
-    for (int q = 0; q < 32; ++q)
-      if (c + q < nv) cm = fmaxf(cm, v[q] * a);
+    for (int q = 0; q < 32; ++q) {
+      v[q] = fmaf(v[q], a, m->col[c + q].x);
+      cm = fmaxf(cm, v[q]);
+    }
     const float nm = fmaxf(mx, cm);
+    const float ref = nm == -INFINITY ? 0.f : nm;
     float zc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int q = 0; q < 32; ++q)
-      if (c + q < nv) zc[q & 3] += m->col[c + q].x * exp2f(v[q] * a - nm);
-    z = z * exp2f(mx - nm) + ((zc[0] + zc[1]) + (zc[2] + zc[3]));
+    for (int q = 0; q < 32; ++q) zc[q & 3] += exp2f(v[q] - ref);
+    z = z * exp2f(mx - ref) + ((zc[0] + zc[1]) + (zc[2] + zc[3]));
     mx = nm;
   }
   float4 all[kSplit];
@@ -494,21 +503,20 @@ __device__ float2 softmax_stats(const Params& p, Misc* m, uint32_t taddr) {
   float b = all[0].x;
 #pragma unroll
   for (int i = 1; i < kSplit; ++i) b = fmaxf(b, all[i].x);
+  const float bref = b == -INFINITY ? 0.f : b;
   float Z = 0.f;
 #pragma unroll
-  for (int i = 0; i < kSplit; ++i) Z += __fmul_rn(all[i].y, exp2f(all[i].x - b));
-  const float inv = (Z > 0.f && row_id() < nv) ? 1.f / Z : 0.f;
-  return make_float2(b, inv);
+  for (int i = 0; i < kSplit; ++i) Z += __fmul_rn(all[i].y, exp2f(all[i].x - bref));
+  return (Z > 0.f && row_id() < nv) ? bref + log2f(Z) : INFINITY;
 }
 
-// attention weights w_jk of 32 columns from raw scores v (in place)
-__device__ __forceinline__ void softmax_w(const Params& p, const Misc* m, int c, float2 st,
+// attention weights w_jk = 2^(u_jk - beta_j) of 32 columns from raw scores v
+// (in place); empty columns and empty rows give 0
+__device__ __forceinline__ void softmax_w(const Params& p, const Misc* m, int c, float beta,
                                           float* v) {
   const float a = p.inv_sqrt_d * 1.4426950408889634f;
-  const int nv = m->nvalid;
 #pragma unroll
-  for (int q = 0; q < 32; ++q)
-    v[q] = (c + q < nv) ? m->col[c + q].x * exp2f(v[q] * a - st.x) * st.y : 0.f;
+  for (int q = 0; q < 32; ++q) v[q] = exp2f(fmaf(v[q], a, m->col[c + q].x) - beta);
 }
 
 __device__ __forceinline__ float gate(const float* rj, const float4& ck) {
@@ -539,7 +547,7 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
       MMA_GROUP(mb, p.status,
                 mma_issue(tb + R3, kop(sm + SM_Q, kW, h * p.dh), kop(sm + SM_K, kW, h * p.dh), kW,
                           p.dh, false));
-      const float2 st = softmax_stats(p, m, tb + lo + R3);
+      const float st = softmax_beta(p, m, tb + lo + R3);
       if (pt == 0) p.smx[(((size_t)atom * p.n_layers + l) * p.heads + h) * kW + r] = st;
       for (int c = 32 * pt; c < kW; c += kStride) {
         float v[32];
@@ -782,6 +790,10 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
       issue_copy(xb, sm + SM_Q, p.WqT + (size_t)l * kTile, kTile, 2 * kTile);
       issue_copy(xb, sm + SM_K, p.WkT + (size_t)l * kTile, kTile, 0);
     }
+    // the layer's softmax normalisers (one per head), needed by the heads below
+    float beta4[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) beta4[h] = p.smx[(((size_t)atom * L + l) * 4 + h) * kW + r];
     if (ngroups > 0 && !gb.wait(p.status)) return false;
     // ---- LayerNorm adjoint: dZ = rstd (dG - mean dG - Gout mean(dG Gout))
     {
@@ -855,7 +867,7 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
       // scores
       MMA_GROUP(mb, p.status,
                 mma_issue(tb + R3, kop(sm + SM_Q, kW, c0), kop(sm + SM_K, kW, c0), kW, DH, false));
-      const float2 st = p.smx[(((size_t)atom * L + l) * p.heads + h) * kW + r];
+      const float st = h == 0 ? beta4[0] : h == 1 ? beta4[1] : h == 2 ? beta4[2] : beta4[3];
       // w (kept in R3 for the adjoint below) and A = w * gate -> G tile
       for (int c = 32 * pt; c < kW; c += kStride) {
         float v[32];
