@@ -242,6 +242,17 @@ struct Bar {
     tc::fence_after_sync();
     return ok;
   }
+  // Completion of tensor-core products: thread 0 polls, the block barrier
+  // passes its outcome on (and orders the later tensor-memory loads).
+  __device__ bool wait_mma(int* status) {
+    bool ok = true;
+    if (threadIdx.x == 0) ok = tc::mbar_wait(reinterpret_cast<uint64_t*>(bar), phase & 1u, kPolls);
+    phase ^= 1u;
+    ok = __syncthreads_and(ok) != 0;
+    if (!ok && threadIdx.x == 0) atomicOr(status, kFlagTimeout);
+    tc::fence_after_sync();
+    return ok;
+  }
 };
 
 __device__ __forceinline__ void before_mma() {
@@ -280,7 +291,7 @@ __device__ __forceinline__ void issue_copy(Bar& b, uint8_t* dst, const void* src
       __VA_ARGS__;                                                   \
       tc::mma_commit(reinterpret_cast<uint64_t*>((mb).bar));         \
     }                                                                \
-    if (!(mb).wait(status)) return false;                            \
+    if (!(mb).wait_mma(status)) return false;                        \
   } while (0)
 
 // ------------------------------------------------------------------ environment
@@ -543,10 +554,9 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
   for (int l = 0; l < p.n_layers; ++l) {
     if (!qkv(p, sm, tb, mb, xb)) return false;
     bulk_load(wb, sm + SM_W, p.WoT + (size_t)l * kTile, kTile);  // lands during the heads
+    MMA_GROUP(mb, p.status,
+              mma_issue(tb + R3, kop(sm + SM_Q, kW), kop(sm + SM_K, kW), kW, kDH, false));
     for (int h = 0; h < p.heads; ++h) {
-      MMA_GROUP(mb, p.status,
-                mma_issue(tb + R3, kop(sm + SM_Q, kW, h * p.dh), kop(sm + SM_K, kW, h * p.dh), kW,
-                          p.dh, false));
       const float st = softmax_beta(p, m, tb + lo + R3);
       if (pt == 0) p.smx[(((size_t)atom * p.n_layers + l) * p.heads + h) * kW + r] = st;
       for (int c = 32 * pt; c < kW; c += kStride) {
@@ -563,9 +573,13 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
         store32(sm + SM_P, r, c, kW, kW, v);
       }
       tc::fence_before_sync();
+      // O_h = A V_h, and the next head's scores (R3 has been read)
       MMA_GROUP(mb, p.status,
-                mma_issue(tb + R0 + h * p.dh, kop(sm + SM_P, kW), mnop(sm + SM_V, kW, h * p.dh), p.dh,
-                          kW, false));
+                mma_issue(tb + R0 + h * kDH, kop(sm + SM_P, kW), mnop(sm + SM_V, kW, h * kDH), kDH,
+                          kW, false);
+                if (h + 1 < p.heads)
+                  mma_issue(tb + R3, kop(sm + SM_Q, kW, (h + 1) * kDH),
+                            kop(sm + SM_K, kW, (h + 1) * kDH), kW, kDH, false));
     }
     for (int c = 32 * pt; c < kW; c += kStride) {
       float v[32];
@@ -862,11 +876,10 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
     }
     // ---- heads.  Tiles: Q, K, V; dO in P; A, then the gate adjoint, in G;
     // dS in W
+    MMA_GROUP(mb, p.status,   // scores of head 0; later heads' ride with the previous head
+              mma_issue(tb + R3, kop(sm + SM_Q, kW), kop(sm + SM_K, kW), kW, DH, false));
     for (int h = 0; h < p.heads; ++h) {
       const int c0 = h * DH;
-      // scores
-      MMA_GROUP(mb, p.status,
-                mma_issue(tb + R3, kop(sm + SM_Q, kW, c0), kop(sm + SM_K, kW, c0), kW, DH, false));
       const float st = h == 0 ? beta4[0] : h == 1 ? beta4[1] : h == 2 ? beta4[2] : beta4[3];
       // w (kept in R3 for the adjoint below) and A = w * gate -> G tile
       for (int c = 32 * pt; c < kW; c += kStride) {
@@ -940,17 +953,21 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
       tc::fence_before_sync();
       // dQ_h = dS K_h, dK_h = dS^T Q_h (scaled at drain); column sums of dS
       // (ones) and of the gate adjoint weighted by rh_j (accumulated over
-      // heads); row sums of the gate adjoint weighted by rh_k (R3, this head)
+      // heads); row sums of the gate adjoint weighted by rh_k (R1, free once
+      // dA has been read); the next head's scores (R3, w has been read)
       MMA_GROUP(mb, p.status,
                 mma_issue(tb + R0, kop(sm + SM_W, kW), mnop(sm + SM_K, kW, c0), DH, kW, false);
                 mma_issue(tb + R0 + DH, mnop(sm + SM_W, kW, 0), mnop(sm + SM_Q, kW, c0), DH, kW, false);
                 mma_issue(tb + R0 + 112, mnop(sm + SM_W, kW, 0), kop(m->ones, kW), 16, kW, h > 0);
                 mma_issue(tb + R0 + 96, mnop(sm + SM_G, kW, 0), kop(m->rhb, kW), 16, kW, h > 0);
-                mma_issue(tb + R3, kop(sm + SM_G, kW), kop(m->rhb, kW), 16, kW, false));
+                mma_issue(tb + R1, kop(sm + SM_G, kW), kop(m->rhb, kW), 16, kW, false);
+                if (h + 1 < p.heads)
+                  mma_issue(tb + R3, kop(sm + SM_Q, kW, c0 + DH), kop(sm + SM_K, kW, c0 + DH), kW, DH,
+                            false));
       // the gate adjoint's row part, sum_k dc_jk rh_k, joins the column part in drc
       if (pt == 0) {
         float v[8];
-        tc::tmem_ld8(tb + lo + R3, v);
+        tc::tmem_ld8(tb + lo + R1, v);
         m->drc[r][0] += v[0];
         m->drc[r][1] += v[1];
         m->drc[r][2] += v[2];
