@@ -12,6 +12,7 @@ fitting 2048->240->240->240->1, rc 6 A, nmax 120), random N(0, 0.1) weights,
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--form fused|plain]
     python bench.py --impl reference ...      # the FP64 CPU oracle on host cores
+    python bench.py --report 1,2,3,4,5        # per-configuration accuracy/drift/latency reports
 
 Prints one JSON line (rank 0).  N > 1 (torchrun) runs N independent replicas,
 one per GPU (the model is atom-local; no collective is needed): weak scaling.
@@ -180,11 +181,12 @@ def cpu_baseline(seconds=12.0):
 
 
 # ------------------------------------------------------------------ serving
-def serving_bench(n_req, seed=7, load=0.9, n_steps=50):
+def serving_bench(n_req, seed=7, load=0.9, n_steps=50, capacity=None, mem_budget=0):
     """Continuous batching of independent systems (sizes log-uniform 96..6000,
-    50 MD steps each): capacity with every request queued at once, then a
-    Poisson-arrival run at `load` times that capacity.  Returns p50/p99 tick
-    (step) latency, request latency and aggregate atom-steps/s."""
+    50 MD steps each): capacity with every request queued at once (unless
+    given), then a Poisson-arrival run at `load` times that capacity.  Returns
+    p50/p99 tick (step) latency, request latency and aggregate atom-steps/s.
+    mem_budget > 0 caps the device memory of the resident batch (bytes)."""
     import paper_2602_02234_b300 as dp
     from paper_2602_02234_b300 import serve
     from synth import serving_requests
@@ -197,13 +199,15 @@ def serving_bench(n_req, seed=7, load=0.9, n_steps=50):
     vels = [maxwell_boltzmann(masses[r.system.types], 300.0, CF.VELOCITY_SEED + k)
             for k, r in enumerate(reqs)]
     mean_atoms = float(np.mean([r.system.n for r in reqs]))
-    srv = dp.Server(desc, w, masses, max_slots=64, dt_fs=CF.DT_FS)
-    _, st_cap = serve.run(srv, reqs, vels)
-    srv.close()
-    capacity = st_cap["atom_steps"] / st_cap["wall_s"]
+    kw = {"mem_budget": mem_budget} if mem_budget else {}
+    if capacity is None:
+        srv = dp.Server(desc, w, masses, max_slots=64, dt_fs=CF.DT_FS, **kw)
+        _, st_cap = serve.run(srv, reqs, vels)
+        srv.close()
+        capacity = st_cap["atom_steps"] / st_cap["wall_s"]
     rate = load * capacity / (mean_atoms * n_steps)
     reqs = serving_requests(n_req, rate, seed, n_steps=n_steps)
-    srv = dp.Server(desc, w, masses, max_slots=64, dt_fs=CF.DT_FS)
+    srv = dp.Server(desc, w, masses, max_slots=64, dt_fs=CF.DT_FS, **kw)
     _, st = serve.run(srv, reqs, vels)
     srv.close()
     return {"requests": n_req, "steps_per_request": n_steps, "offered_load": load,
@@ -211,6 +215,7 @@ def serving_bench(n_req, seed=7, load=0.9, n_steps=50):
             "p50_step_ms": st["p50_tick_ms"], "p99_step_ms": st["p99_tick_ms"],
             "request_p50_ms": st["request_p50_ms"], "request_p99_ms": st["request_p99_ms"],
             "atom_steps_per_s": st["atom_steps"] / st["wall_s"], "max_resident": st["max_resident"],
+            "mem_budget_bytes": mem_budget or None,
             "sizes": "log-uniform 96..6000 atoms, water below 600, 6.25 % blob above"}
 
 
@@ -374,6 +379,175 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
+# ------------------------------------------------------------------ per-configuration reports
+def _drift(tr, n_atoms, dt_fs):
+    """Total-energy drift of an NVE trace: least-squares slope per atom per ns,
+    and the largest excursion from the first value per atom."""
+    et = tr.sum(1)
+    t_ns = np.arange(len(et)) * dt_fs * 1e-6
+    slope = float(np.polyfit(t_ns, et, 1)[0]) if len(et) > 2 else 0.0
+    return {"steps": len(et), "slope_eV_per_atom_per_ns": slope / n_atoms,
+            "max_excursion_eV_per_atom": float(np.max(np.abs(et - et[0]))) / n_atoms}
+
+
+def _err(F, Fo, E=None, Eo=None):
+    rms = float(np.sqrt(np.mean(Fo ** 2)))
+    out = {"max_abs_dF_over_F_rms": float(np.max(np.abs(F - Fo))) / rms,
+           "rms_dF_over_F_rms": float(np.sqrt(np.mean((F - Fo) ** 2))) / rms, "F_rms": rms}
+    if E is not None:
+        out["rel_dE"] = abs(E - Eo) / abs(Eo)
+    return out
+
+
+def _timed_steps(pot, K, stream):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        pot.step(K, CF.DT_FS)
+        e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / K
+
+
+def report_config(which):
+    """One JSON object for configuration `which` (1..5) of the benchmark set."""
+    import torch
+    import oracle
+    import paper_2602_02234_b300 as dp
+    stream = torch.cuda.Stream()
+    out = {"config": which}
+    if which == 1:      # 64 waters, plain FP64 / FP32 against the oracle, 100 NVE steps
+        m, s = CF.WATER64_MODEL, CF.water64()
+        w = normal_blob(oracle.af_weight_count(m), CF.WEIGHT_SEED)
+        masses = s.masses
+        v0 = maxwell_boltzmann(masses[s.types], 300.0, CF.VELOCITY_SEED)
+        Eo, _, Fo, _ = oracle.af_compute(m, w, s.types, s.coords, s.box)
+        t0 = time.perf_counter()
+        xo, vo, epo, eko = oracle.af_md(m, w, s.types, masses, s.coords, v0, s.box, 100, CF.DT_FS)
+        out["oracle_md_atom_steps_per_s"] = s.n * 100 / (time.perf_counter() - t0)
+        out["oracle_drift"] = _drift(np.stack([epo, eko], 1), s.n, CF.DT_FS)
+        for name, prec in (("plain_f64", dp.PREC_PLAIN_F64), ("plain_f32", dp.PREC_PLAIN_F32)):
+            pot = dp.DeepPotential(dp.model_desc(m, prec), s.types, s.box, w, masses=masses,
+                                   stream=stream)
+            E, F, V = pot.compute(s.coords)
+            x, v = s.coords.copy(), v0.copy()
+            tr = pot.step(100, CF.DT_FS, coords=x, vel=v, energies=True)
+            pot.set_state(s.coords, v0, 0)
+            pot.step(5, CF.DT_FS)
+            ms = _timed_steps(pot, 100, stream)
+            out[name] = {"vs_oracle": _err(F, Fo, E, Eo), "drift": _drift(tr, s.n, CF.DT_FS),
+                         "x_after_100_vs_oracle_max_A": float(np.max(np.abs(x - xo))),
+                         "ms_per_step": ms, "atom_steps_per_s": s.n / (ms / 1e3)}
+            pot.close()
+    elif which == 2:    # 24,000 atoms: NVE drift of the fused and plain forms, force agreement
+        s, m, masses, v0 = setup_system()
+        w = normal_blob(oracle.af_weight_count(m), CF.WEIGHT_SEED)
+        pots = {}
+        # 100 steps (50 fs): with random-init weights the system leaves equilibrium
+        # within ~100 fs (the potential energy falls by thousands of eV and the
+        # integration breaks down for every form), so drift is measured before that
+        for name, prec, n_steps in (("fused_f16", dp.PREC_FUSED, 100),
+                                    ("plain_f32", dp.PREC_PLAIN_F32, 100)):
+            pot = dp.DeepPotential(dp.model_desc(m, prec, skin=CF.SKIN, rebuild_every=CF.REBUILD_EVERY),
+                                   s.types, s.box, w, masses=masses, stream=stream)
+            E, F, V = pot.compute(s.coords)
+            pot.set_state(s.coords, v0, 0)
+            t0 = time.perf_counter()
+            tr = pot.step(n_steps, CF.DT_FS, energies=True)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            out[name] = {"drift": _drift(tr, s.n, CF.DT_FS),
+                         "atom_steps_per_s_over_run": s.n * n_steps / wall}
+            pots[name] = (E, F, pot)
+        Ef, Ff, _ = pots["fused_f16"]
+        Ep, Fp, _ = pots["plain_f32"]
+        out["fused_vs_plain_f32"] = _err(Ff, Fp, Ef, Ep)
+        rng = np.random.default_rng(3)
+        sample = np.sort(rng.choice(s.n, 48, replace=False))
+        Fo = oracle.af_forces_subset(m, w, s.types, s.coords, s.box, sample)
+        out["fused_vs_oracle_48_atoms"] = _err(Ff[sample], Fo)
+        out["plain_f32_vs_oracle_48_atoms"] = _err(Fp[sample], Fo)
+        for _, _, pot in pots.values():
+            pot.close()
+    elif which == 3:    # graph family at 24,000 atoms
+        s, _, masses, v0 = setup_system()
+        m = CF.GRAPH_MODEL
+        w = normal_blob(oracle.gf_weight_count(m), CF.WEIGHT_SEED)
+        res = {}
+        for name, prec, K in (("plain_f32", dp.PREC_PLAIN_F32, 5), ("plain_f64", dp.PREC_PLAIN_F64, 2),
+                              ("mixed_tc_f16", dp.PREC_FUSED, 5)):
+            pot = dp.DeepPotential(dp.model_desc(m, prec, skin=CF.SKIN, rebuild_every=CF.REBUILD_EVERY),
+                                   s.types, s.box, w, masses=masses, stream=stream)
+            E, F, V = pot.compute(s.coords)
+            pot.set_state(s.coords, v0, 0)
+            pot.step(2, CF.DT_FS)
+            ms = _timed_steps(pot, K, stream)
+            res[name] = (E, F, pot)
+            out[name] = {"ms_per_step": ms, "atom_steps_per_s": s.n / (ms / 1e3)}
+        E32, F32, _ = res["plain_f32"]
+        E64, F64, p64 = res["plain_f64"]
+        out["f32_vs_f64"] = _err(F32, F64, E32, E64)
+        out["mixed_tc_f16_vs_f64"] = _err(res["mixed_tc_f16"][1], F64, res["mixed_tc_f16"][0], E64)
+        rng = np.random.default_rng(11)
+        atoms = rng.choice(s.n, 6, replace=False)
+        h, worst = 1e-4, 0.0
+        for i in atoms:
+            for a in range(3):
+                xp = s.coords.copy(); xp[i, a] += h
+                xm = s.coords.copy(); xm[i, a] -= h
+                fd = -(p64.compute(xp)[0] - p64.compute(xm)[0]) / (2 * h)
+                worst = max(worst, abs(fd - F64[i, a]))
+        out["fd_check"] = {"atoms": len(atoms), "h_A": h, "max_abs_dF_over_F_rms":
+                           worst / float(np.sqrt(np.mean(F64 ** 2)))}
+        for _, _, pot in res.values():
+            pot.close()
+        # the attention family on the same system and precision, for the AF/GF ratio
+        sa, ma, _, _ = setup_system()
+        wa = normal_blob(oracle.af_weight_count(ma), CF.WEIGHT_SEED)
+        for name, prec, K in (("af_plain_f32", dp.PREC_PLAIN_F32, 5), ("af_fused_f16", dp.PREC_FUSED, 20)):
+            pot = dp.DeepPotential(dp.model_desc(ma, prec, skin=CF.SKIN, rebuild_every=CF.REBUILD_EVERY),
+                                   sa.types, sa.box, wa, masses=masses, stream=stream)
+            pot.set_state(sa.coords, v0, 0)
+            pot.step(3, CF.DT_FS)
+            out[name] = {"ms_per_step": _timed_steps(pot, K, stream)}
+            pot.close()
+        out["af_over_gf_throughput_f32"] = out["plain_f32"]["ms_per_step"] / out["af_plain_f32"]["ms_per_step"]
+    elif which == 4:    # serving: offered-load sweep and a memory-capped run
+        first = serving_bench(256, load=0.25)
+        cap = first["capacity_atom_steps_per_s"]
+        out["sweep"] = [first] + [serving_bench(256, load=ld, capacity=cap)
+                                  for ld in (0.5, 0.75, 0.9, 1.0, 1.2)]
+        out["memory_capped_1GB"] = serving_bench(256, load=0.9, capacity=cap, mem_budget=1 << 30)
+    elif which == 5:    # 100,000 atoms: fused vs plain FP32
+        s = CF.protein100k()
+        m = CF.ATTN_MODEL
+        masses = s.masses
+        v0 = maxwell_boltzmann(masses[s.types], 300.0, CF.VELOCITY_SEED)
+        w = normal_blob(oracle.af_weight_count(m), CF.WEIGHT_SEED)
+        res = {}
+        for name, prec, K in (("fused_f16", dp.PREC_FUSED, 50), ("plain_f32", dp.PREC_PLAIN_F32, 3)):
+            pot = dp.DeepPotential(dp.model_desc(m, prec, skin=CF.SKIN, rebuild_every=CF.REBUILD_EVERY),
+                                   s.types, s.box, w, masses=masses, stream=stream)
+            E, F, V = pot.compute(s.coords)
+            pot.set_state(s.coords, v0, 0)
+            pot.step(3, CF.DT_FS)
+            ms = _timed_steps(pot, K, stream)
+            out[name] = {"ms_per_step": ms, "atom_steps_per_s": s.n / (ms / 1e3), "steps": K}
+            res[name] = (E, F)
+            pot.close()
+        out["fused_vs_plain"] = out["plain_f32"]["ms_per_step"] / out["fused_f16"]["ms_per_step"]
+        out["fused_vs_plain_f32"] = _err(res["fused_f16"][1], res["plain_f32"][1],
+                                         res["fused_f16"][0], res["plain_f32"][0])
+        rng = np.random.default_rng(5)
+        sample = np.sort(rng.choice(s.n, 32, replace=False))
+        Fo = oracle.af_forces_subset(m, w, s.types, s.coords, s.box, sample)
+        out["fused_vs_oracle_32_atoms"] = _err(res["fused_f16"][1][sample], Fo)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -388,7 +562,14 @@ def main():
                     help="requests in the continuous-batching measurement (0: skip)")
     ap.add_argument("--system", choices=["protein24k", "small"], default="protein24k",
                     help="small: 4,800-atom box of the same recipe, for profiler captures")
+    ap.add_argument("--report", default="",
+                    help="comma-separated configurations (1-5): accuracy, drift, latency, graph "
+                         "family, serving sweep, 100k atoms; one JSON line each, no timing contract")
     args = ap.parse_args()
+    if args.report:
+        for c in args.report.split(","):
+            print(json.dumps(report_config(int(c))), flush=True)
+        return 0
     args.warmup = max(3, args.warmup)       # timing rule: at least 3 untimed warm-up steps
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

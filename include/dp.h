@@ -60,12 +60,18 @@ enum { DP_FAMILY_ATTENTION = 0, DP_FAMILY_GRAPH = 1 };
 /* Arithmetic of the network:
  *   PLAIN_F64 -- unfused kernels, everything in FP64 (small systems, parity);
  *   PLAIN_F32 -- unfused kernels, one simple kernel per operation, FP32;
- *   FUSED     -- three persistent kernels per evaluation: every matrix product
- *                on the tensor cores (tcgen05) with 16-bit operands (FP16; BF16
- *                when the library is built with DP_FUSED_BF16) and FP32
- *                accumulation, FP32 switch/softmax/LayerNorm, FP64 energy,
- *                virial and integration.  Needs m1 = hidden = 128 with 4 heads, nmax <=
- *                128 (DP_ERR_UNSUPPORTED otherwise). */
+ *   FUSED     -- attention family: three persistent kernels per evaluation:
+ *                every matrix product on the tensor cores (tcgen05) with 16-bit
+ *                operands (FP16; BF16 when the library is built with
+ *                DP_FUSED_BF16) and FP32 accumulation, FP32 switch/softmax/
+ *                LayerNorm, FP64 energy, virial and integration.  Needs m1 =
+ *                hidden = 128 with 4 heads, nmax <= 128.
+ *                Graph family ("mixed"): the unfused FP32 kernels with every
+ *                matrix product on the tensor cores (16-bit operands: FP16, or
+ *                BF16 when built with DP_GF_BF16; FP32 accumulation).  Needs
+ *                node, edge, node + edge and fitting widths that are multiples
+ *                of 16, at most 256.
+ *                DP_ERR_UNSUPPORTED for other sizes. */
 enum { DP_PREC_PLAIN_F64 = 0, DP_PREC_PLAIN_F32 = 1, DP_PREC_FUSED = 2 };
 
 enum { DP_PTR_HOST = 0, DP_PTR_DEVICE = 1 };

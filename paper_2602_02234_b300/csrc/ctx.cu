@@ -323,10 +323,11 @@ static int check_model(const dp_model_desc* desc, const double* weights, size_t 
   *afd = AfDims{desc->n_species, desc->e1, desc->e2, desc->m1, desc->m2, desc->n_layers,
                 desc->hidden, desc->heads, desc->f1, desc->f2, desc->f3, desc->nmax,
                 desc->rcut, desc->rcut_smth};
-  if (desc->family == DP_FAMILY_GRAPH && desc->precision == DP_PREC_FUSED)
-    return fail(nullptr, DP_ERR_UNSUPPORTED, "the graph family runs on the plain FP32/FP64 kernels only");
   if (desc->family == DP_FAMILY_ATTENTION && desc->precision == DP_PREC_FUSED &&
       !fused_af_supported(*afd, &why))
+    return fail(nullptr, DP_ERR_UNSUPPORTED, why);
+  if (desc->family == DP_FAMILY_GRAPH && desc->precision == DP_PREC_FUSED &&
+      !gf_mixed_supported(gf_dims(desc), &why))
     return fail(nullptr, DP_ERR_UNSUPPORTED, why);
   return DP_OK;
 }
@@ -398,8 +399,8 @@ static int ctx_create(dp_ctx** out, const dp_model_desc* desc, const double* mas
   rc = alloc_skin(c, cap);
   if (rc) return bail(rc);
   if (desc->family == DP_FAMILY_GRAPH)
-    c->model = make_plain_gf(gf_dims(desc), desc->precision == DP_PREC_PLAIN_F64, weights, n_cap,
-                             model_types, &c->err);
+    c->model = make_plain_gf(gf_dims(desc), desc->precision == DP_PREC_PLAIN_F64,
+                             desc->precision == DP_PREC_FUSED, weights, n_cap, model_types, &c->err);
   else if (desc->precision == DP_PREC_FUSED)
     c->model = make_fused_af(c->af, weights, n_cap, model_types, &c->err);
   else

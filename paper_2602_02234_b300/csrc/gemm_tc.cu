@@ -1,0 +1,190 @@
+// Tensor-core GEMM for FP32-stored operands: C = A B [+ bias] [+ beta C], then
+// an optional epilogue (tanh, or times 1 - aux^2), with 16-bit operands (FP16,
+// or BF16) and FP32 accumulation on tcgen05.  It serves the graph family's mixed form,
+// whose matrix products are all of the shape (rows x K) (K x N) with K, N
+// multiples of 16 up to 256 and rows = atoms or atom-slot pairs (millions).
+//
+// One CTA of 128 threads owns tiles of 128 rows (persistent over tiles): B is
+// converted into shared memory once, each A tile is loaded with coalesced
+// float4 reads, converted and stored in the core-matrix layout, multiplied
+// into tensor memory (K/16 instructions of 128 x N x 16) and drained by
+// thread = row through the epilogue.
+#include <algorithm>
+
+#include "common.cuh"
+#include "gemm_tc.cuh"
+#include "tc.cuh"
+
+namespace dp {
+namespace {
+
+constexpr int kRows = 128;
+constexpr long long kPollsTc = 1LL << 22;
+
+__device__ __forceinline__ uint64_t desc_k(uint32_t base, int Kx, int k0) {
+  return tc::make_desc(base + (uint32_t)((k0 >> 3) * 128), 128u, (uint32_t)((Kx >> 3) * 128));
+}
+__device__ __forceinline__ uint64_t desc_mn(uint32_t base, int Kx, int k0) {
+  return tc::make_desc(base + (uint32_t)((k0 >> 3) * (Kx >> 3) * 128), (uint32_t)((Kx >> 3) * 128),
+                       128u);
+}
+
+__global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  const int t = threadIdx.x, warp = t >> 5;
+  const int brows = g.b_nk ? g.N : g.K, bcols = g.b_nk ? g.K : g.N;
+  uint8_t* Bs = sm;
+  uint8_t* As = sm + (((size_t)brows * bcols * 2 + 1023) & ~(size_t)1023);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(As + (size_t)kRows * g.K * 2);
+  __shared__ uint32_t tptr;
+  if (t == 0) {
+    tc::mbar_init(bar, 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(&tptr, (uint32_t)tmem_cols);
+    tc::tmem_relinquish();
+  }
+  // B once: stored rows x cols (K x N, or N x K when b_nk), row-major in global
+  for (int i = t; i < brows * bcols; i += kRows) {
+    const int r = i / bcols, c = i - r * bcols;
+    const float x = g.B[(long long)r * g.ldb + c];
+    uint16_t h;
+    if (g.fp16) {
+      __half v = __float2half_rn(x);
+      h = *reinterpret_cast<uint16_t*>(&v);
+    } else {
+      __nv_bfloat16 v = __float2bfloat16(x);
+      h = *reinterpret_cast<uint16_t*>(&v);
+    }
+    *reinterpret_cast<uint16_t*>(Bs + tc::kmajor_off(r, c, bcols)) = h;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tb = tptr;
+  const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+  const uint32_t idesc = tc::idesc_f16(kRows, g.N, 0, g.b_nk ? 0 : 1, g.fp16 ? 0u : 1u);
+  const uint32_t a_base = tc::smem_u32(As), b_base = tc::smem_u32(Bs);
+  const int tiles = (g.M + kRows - 1) / kRows;
+  const int k4 = g.K >> 2;
+  uint32_t phase = 0;
+  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const long long m0 = (long long)tile * kRows;
+    // A tile: 128 rows x K, coalesced float4 reads -> 16-bit core-matrix layout
+    for (int i = t; i < kRows * k4; i += kRows) {
+      const int r = i / k4, c = (i - r * k4) << 2;
+      const long long m = m0 + r;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (m < g.M) {
+        const long long row = g.a_rows ? (long long)g.a_rows[m] : m;
+        v = *reinterpret_cast<const float4*>(g.A + row * g.lda + c);
+      }
+      uint2 u;
+      if (g.fp16) {
+        u.x = tc::pack_f16(v.x, v.y);
+        u.y = tc::pack_f16(v.z, v.w);
+      } else {
+        u.x = tc::pack_bf16(v.x, v.y);
+        u.y = tc::pack_bf16(v.z, v.w);
+      }
+      *reinterpret_cast<uint2*>(As + tc::kmajor_off(r, c, g.K)) = u;
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (t == 0) {
+      for (int ks = 0; ks < g.K; ks += 16)
+        tc::mma_bf16(tb, desc_k(a_base, g.K, ks),
+                     g.b_nk ? desc_k(b_base, g.K, ks) : desc_mn(b_base, g.N, ks), idesc,
+                     ks > 0 ? 1u : 0u);
+      tc::mma_commit(bar);
+    }
+    bool ok = true;
+    if (t == 0) ok = tc::mbar_wait(bar, phase & 1u, kPollsTc);
+    phase ^= 1u;
+    ok = __syncthreads_and(ok) != 0;
+    tc::fence_after_sync();
+    if (!ok) {
+      if (t == 0) atomicOr(g.status, kFlagTimeout);
+      break;
+    }
+    // epilogue: thread t owns row m0 + t
+    const long long m = m0 + t;
+    const bool live = m < g.M;
+    const long long row = live ? (g.c_rows ? (long long)g.c_rows[m] : m) : 0;
+    for (int c = 0; c < g.N; c += 16) {
+      float v[16];
+      tc::tmem_ld16(tb + lane_off + (uint32_t)c, v);
+      if (!live) continue;
+      float* Crow = g.C + row * g.ldc + c;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        float x = v[q];
+        if (g.bias) x += g.bias[c + q];
+        if (g.beta != 0.f) x += g.beta * Crow[q];
+        if (g.epi == 1) {
+          x = tanhf(x);
+        } else if (g.epi == 2) {
+          const float y = g.aux[row * g.ldc + c + q];
+          x *= 1.f - y * y;
+        }
+        Crow[q] = x;
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();          // tensor memory and the A tile are reused by the next tile
+    tc::fence_after_sync();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tb, (uint32_t)tmem_cols);
+}
+
+int g_sms = 0;
+
+}  // namespace
+
+bool gemm_tc_shape_ok(int N, int K) {
+  return N >= 16 && N <= 256 && N % 16 == 0 && K >= 16 && K <= 256 && K % 16 == 0;
+}
+
+static size_t smem_of(const GemmTc& g) {
+  const size_t b = ((size_t)g.N * g.K * 2 + 1023) & ~(size_t)1023;
+  return b + (size_t)kRows * g.K * 2 + 64;
+}
+
+bool gemm_tc_prepare(std::string* err) {
+  if (g_sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      *err = "cannot query the device";
+      return false;
+    }
+  }
+  // the largest request: B 256 x 256 plus a 128 x 256 A tile
+  if (cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           256 * 256 * 2 + kRows * 256 * 2 + 64) != cudaSuccess) {
+    *err = "tensor-core GEMM cannot get its shared memory";
+    return false;
+  }
+  return true;
+}
+
+void gemm_tc(const GemmTc& g, cudaStream_t st) {
+  if (g.M <= 0) return;
+  int cols = 32;
+  while (cols < g.N) cols <<= 1;
+  // at most 512 / cols CTAs may share an SM's tensor memory: pad the shared
+  // memory request so that no more than that many fit on one SM
+  const int per_sm = 512 / cols;
+  const size_t floor_smem = 233472 / (size_t)(per_sm + 1) + 1;
+  const size_t smem = std::max(smem_of(g), floor_smem);
+  const int tiles = (g.M + kRows - 1) / kRows;
+  const int grid = std::min(tiles, std::max(1, g_sms) * per_sm);
+  k_gemm_tc<<<grid, kRows, smem, st>>>(g, cols);
+}
+
+}  // namespace dp

@@ -1,0 +1,43 @@
+// Tensor-core GEMM over FP32-stored operands (16-bit products, FP16 or BF16,
+// FP32 accumulation), used by the graph family's mixed-precision form.
+#pragma once
+
+#include <string>
+
+#include <cuda_runtime.h>
+
+namespace dp {
+
+// C(m, n) = sum_k A(m, k) B(k, n) [+ bias(n)] [+ beta C(m, n)], then epi:
+// 0 none, 1 tanh, 2 times (1 - aux(m, n)^2) with aux laid out like C.
+//   A(m, k) = A[row(m) * lda + k], row(m) = a_rows ? a_rows[m] : m; A 16-byte
+//             aligned, lda a multiple of 4
+//   B(k, n) = B[k * ldb + n]  (b_nk = 0)  or  B[n * ldb + k]  (b_nk = 1)
+//   C(m, n) = C[row'(m) * ldc + n], row'(m) = c_rows ? c_rows[m] : m
+// N and K multiples of 16, at most 256.  A timed-out wait sets kFlagTimeout
+// in *status.
+struct GemmTc {
+  int M, N, K;
+  const float* A;
+  long long lda;
+  const int* a_rows;
+  const float* B;
+  long long ldb;
+  int b_nk;
+  float* C;
+  long long ldc;
+  const int* c_rows;
+  const float* bias;
+  float beta;
+  int epi;
+  const float* aux;
+  int fp16;        // operands rounded to FP16 (1) or BF16 (0)
+  int* status;
+};
+
+bool gemm_tc_shape_ok(int N, int K);
+// once per process (device attributes, shared-memory limit)
+bool gemm_tc_prepare(std::string* err);
+void gemm_tc(const GemmTc& g, cudaStream_t st);
+
+}  // namespace dp

@@ -66,8 +66,11 @@ struct GfDims {
   double rc, rs, rca, rsa;
 };
 size_t gf_weight_count(const GfDims& m);
-// Plain graph family (FP32 or FP64), unfused.
-Model* make_plain_gf(const GfDims& m, bool f64, const double* weights, int n_atoms,
-                     const int* types_host, std::string* err);
+// Whether the mixed graph form can tile these widths (reason when not).
+bool gf_mixed_supported(const GfDims& m, std::string* why);
+// Graph family, unfused: FP32 or FP64, or (tensor_cores) FP32 storage with
+// every matrix product on the tensor cores with BF16 operands.
+Model* make_plain_gf(const GfDims& m, bool f64, bool tensor_cores, const double* weights,
+                     int n_atoms, const int* types_host, std::string* err);
 
 }  // namespace dp

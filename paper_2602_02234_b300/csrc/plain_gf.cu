@@ -22,6 +22,7 @@
 
 #include "common.cuh"
 #include "gemm.cuh"
+#include "gemm_tc.cuh"
 #include "kernels.cuh"
 #include "model.h"
 
@@ -427,11 +428,41 @@ class PlainGf : public Model {
   }
   bool init(const GfDims& m, const double* w, int n_atoms, const int* types, std::string* err);
   int run(const NbrView& nv, const int* types, double* atom_e, cudaStream_t st) override;
+  void bind_flags(int* flags) override { flags_ = flags; }
+  // FP32 storage with every matrix product on the tensor cores (BF16 operands)
+  void use_tensor_cores() { tc_ = true; }
   const float* grad32() const override { return grad_as<float>(); }
   const double* grad64() const override { return grad_as<double>(); }
   size_t bytes() const override { return bytes_; }
 
  private:
+  // one matrix product: the tensor-core GEMM in the mixed form, else SIMT
+  void mm(const Gemm<T>& g, cudaStream_t st) {
+    if constexpr (std::is_same<T, float>::value) {
+      if (tc_ && g.alpha == 1.f && g.a_rk == 1 && g.c_rn == 1 && (g.b_rn == 1 || g.b_rk == 1) &&
+          gemm_tc_shape_ok(g.N, g.K) && g.a_rm % 4 == 0 &&
+          (reinterpret_cast<uintptr_t>(g.A) & 15) == 0) {
+        GemmTc t{};
+        t.M = g.M; t.N = g.N; t.K = g.K;
+        t.A = g.A; t.lda = g.a_rm; t.a_rows = g.a_rows;
+        t.B = g.B; t.b_nk = g.b_rn == 1 ? 0 : 1; t.ldb = g.b_rn == 1 ? g.b_rk : g.b_rn;
+        t.C = g.C; t.ldc = g.c_rm; t.c_rows = g.c_rows;
+        t.bias = g.bias; t.beta = g.beta; t.epi = g.epi; t.aux = g.aux;
+        t.status = flags_;
+#ifdef DP_GF_BF16
+        t.fp16 = 0;
+#else
+        t.fp16 = 1;
+#endif
+        gemm_tc(t, st);
+        return;
+      }
+    }
+    gemm(g, 1, st);
+  }
+  bool tc_ = false;
+  int* flags_ = nullptr;
+
   template <typename U>
   const U* grad_as() const {
     if constexpr (std::is_same<T, U>::value) return g_;
@@ -570,32 +601,32 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
   const size_t angle_smem = sizeof(T) * NA * NA * 4;
   for (int l = 0; l < L; ++l) {
     // (a)
-    gemm(gemm_rowmajor<T>(n, Ed, Nd, nn_[l], Nd, Wm_[l], Ed, uu_[l], Ed), 1, st);
+    mm(gemm_rowmajor<T>(n, Ed, Nd, nn_[l], Nd, Wm_[l], Ed, uu_[l], Ed), st);
     k_msg<T><<<n, 64, 0, st>>>(NM, Ed, inv_nmax, nv.sel_j, sw_, ee_[l], uu_[l], mm_[l]);
     {
       Gemm<T> g = gemm_rowmajor<T>(n, Nd, Nd, nn_[l], Nd, Wn_[l], Nd, hh_[l], Nd);
       g.bias = bn_[l];
-      gemm(g, 1, st);
+      mm(g, st);
       g = gemm_rowmajor<T>(n, Nd, Ed, mm_[l], Ed, Wn_[l] + (size_t)Nd * Nd, Nd, hh_[l], Nd);
       g.beta = T(1);
       g.epi = 1;
-      gemm(g, 1, st);
+      mm(g, st);
     }
     k_add<T><<<grid((long long)n * Nd), 256, 0, st>>>((long long)n * Nd, nn_[l], hh_[l], nn_[l + 1]);
     // (b)
-    gemm(gemm_rowmajor<T>(n, Ed, Nd, nn_[l + 1], Nd, Wa_[l], Ed, Ai_, Ed), 1, st);
-    gemm(gemm_rowmajor<T>(n, Ed, Nd, nn_[l + 1], Nd, Wb_[l], Ed, Bj_, Ed), 1, st);
-    gemm(gemm_rowmajor<T>((int)P, Ed, Ed, ee_[l], Ed, Wc_[l], Ed, Ce_, Ed), 1, st);
+    mm(gemm_rowmajor<T>(n, Ed, Nd, nn_[l + 1], Nd, Wa_[l], Ed, Ai_, Ed), st);
+    mm(gemm_rowmajor<T>(n, Ed, Nd, nn_[l + 1], Nd, Wb_[l], Ed, Bj_, Ed), st);
+    mm(gemm_rowmajor<T>((int)P, Ed, Ed, ee_[l], Ed, Wc_[l], Ed, Ce_, Ed), st);
     k_edge<T><<<grid(PE), 256, 0, st>>>(P, NM, Ed, nv.sel_j, Ai_, Bj_, Ce_, be_[l], ee_[l], vv_[l],
                                         e1_[l]);
     // (c)
-    gemm(gemm_rowmajor<T>((int)P, Ed, Ed, e1_[l], Ed, Wp_[l], Ed, qq_[l], Ed), 1, st);
+    mm(gemm_rowmajor<T>((int)P, Ed, Ed, e1_[l], Ed, Wp_[l], Ed, qq_[l], Ed), st);
     k_angle<T><<<n, 256, angle_smem, st>>>(NM, NA, Ed, inv_na, sa_, rh_, qq_[l], Wphi_[l], aa_);
     {
       Gemm<T> g = gemm_rowmajor<T>((int)P, Ed, Ed, aa_, Ed, Wq_[l], Ed, tt_[l], Ed);
       g.bias = bq_[l];
       g.epi = 1;
-      gemm(g, 1, st);
+      mm(g, st);
     }
     k_angle_out<T><<<grid(PE), 256, 0, st>>>(P, Ed, sa_, e1_[l], tt_[l], ee_[l + 1]);
     k += 14;
@@ -607,13 +638,13 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
     const int* rws = fit_rows_ + rg.first;
     Gemm<T> g = gemm_rowmajor<T>(rg.second, m.f1, Nd, nn_[L], Nd, F1_[t], m.f1, y1_, m.f1);
     g.a_rows = rws; g.c_rows = rws; g.bias = c1_[t]; g.epi = 1;
-    gemm(g, 1, st);
+    mm(g, st);
     g = gemm_rowmajor<T>(rg.second, m.f2, m.f1, y1_, m.f1, F2_[t], m.f2, y2_, m.f2);
     g.a_rows = rws; g.c_rows = rws; g.bias = c2_[t]; g.epi = 1;
-    gemm(g, 1, st);
+    mm(g, st);
     g = gemm_rowmajor<T>(rg.second, m.f3, m.f2, y2_, m.f2, F3_[t], m.f3, y3_, m.f3);
     g.a_rows = rws; g.c_rows = rws; g.bias = c3_[t]; g.epi = 1;
-    gemm(g, 1, st);
+    mm(g, st);
     k += 3;
   }
   k_fit_out<T><<<ceil_div((long long)n * 32, 256), 256, 0, st>>>(n, m.f3, types, y3_, F4_, c4_, atom_e, d3_);
@@ -627,13 +658,13 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
     g.B = F3_[t]; g.b_rk = 1; g.b_rn = m.f3;
     g.C = d2_; g.c_rm = m.f2; g.c_rn = 1; g.nb2 = 1;
     g.a_rows = rws; g.c_rows = rws; g.alpha = T(1); g.epi = 2; g.aux = y2_;
-    gemm(g, 1, st);
+    mm(g, st);
     g.N = m.f1; g.K = m.f2; g.A = d2_; g.a_rm = m.f2; g.B = F2_[t]; g.b_rn = m.f2;
     g.C = d1_; g.c_rm = m.f1; g.aux = y1_;
-    gemm(g, 1, st);
+    mm(g, st);
     g.N = Nd; g.K = m.f1; g.A = d1_; g.a_rm = m.f1; g.B = F1_[t]; g.b_rn = m.f1;
     g.C = dn_; g.c_rm = Nd; g.epi = 0; g.aux = nullptr;
-    gemm(g, 1, st);
+    mm(g, st);
     k += 3;
   }
   // ---- adjoint through the layers
@@ -652,7 +683,7 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
       g.A = dz_; g.a_rm = Ed; g.a_rk = 1;
       g.B = Wq_[l]; g.b_rk = 1; g.b_rn = Ed;
       g.C = da_; g.c_rm = Ed; g.c_rn = 1; g.nb2 = 1; g.alpha = T(1);
-      gemm(g, 1, st);
+      mm(g, st);
     }
     k_angle_bwd<T><<<n, 256, angle_smem, st>>>(NM, NA, Ed, inv_na, sa_, rh_, qq_[l], Wphi_[l], da_,
                                                dq_, dsa_e_, drh_);
@@ -662,7 +693,7 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
       g.A = dq_; g.a_rm = Ed; g.a_rk = 1;
       g.B = Wp_[l]; g.b_rk = 1; g.b_rn = Ed;
       g.C = de1_; g.c_rm = Ed; g.c_rn = 1; g.nb2 = 1; g.alpha = T(1); g.beta = T(1);
-      gemm(g, 1, st);
+      mm(g, st);
     }
     // (b)
     k_dtanh<T><<<grid(PE), 256, 0, st>>>(PE, de1_, vv_[l], dy_);
@@ -673,7 +704,7 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
       g.A = dy_; g.a_rm = Ed; g.a_rk = 1;
       g.B = Wc_[l]; g.b_rk = 1; g.b_rn = Ed;
       g.C = de_; g.c_rm = Ed; g.c_rn = 1; g.nb2 = 1; g.alpha = T(1); g.beta = T(1);
-      gemm(g, 1, st);
+      mm(g, st);
     }
     k_rowsum<T><<<n, 64, 0, st>>>(NM, Ed, dy_, sdy_);
     k_gather_in<T><<<n, 64, 0, st>>>(NM, Ed, nv.cap, nv.skin, nv.skin_cnt, nv.mirror, nv.selpos, dy_, gat_);
@@ -684,9 +715,9 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
       g.A = sdy_; g.a_rm = Ed; g.a_rk = 1;
       g.B = Wa_[l]; g.b_rk = 1; g.b_rn = Ed;
       g.C = dn1_; g.c_rm = Nd; g.c_rn = 1; g.nb2 = 1; g.alpha = T(1); g.beta = T(1);
-      gemm(g, 1, st);
+      mm(g, st);
       g.A = gat_; g.B = Wb_[l];
-      gemm(g, 1, st);
+      mm(g, st);
     }
     // (a)
     k_dtanh<T><<<grid((long long)n * Nd), 256, 0, st>>>((long long)n * Nd, dn1_, hh_[l], dx_);
@@ -696,7 +727,7 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
       g.A = dx_; g.a_rm = Nd; g.a_rk = 1;
       g.B = Wn_[l]; g.b_rk = 1; g.b_rn = Nd;
       g.C = dnm_; g.c_rm = Nd + Ed; g.c_rn = 1; g.nb2 = 1; g.alpha = T(1);
-      gemm(g, 1, st);
+      mm(g, st);
     }
     k_add_strided<T><<<grid((long long)n * Nd), 256, 0, st>>>(n, Nd, Nd + Ed, dn1_, dnm_, dn_);
     k_msg_bwd<T><<<grid(P * 32), 256, 0, st>>>(P, NM, Ed, Nd + Ed, inv_nmax, nv.sel_j, sw_, ee_[l],
@@ -708,7 +739,7 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
       g.A = du_; g.a_rm = Ed; g.a_rk = 1;
       g.B = Wm_[l]; g.b_rk = 1; g.b_rn = Ed;
       g.C = dn_; g.c_rm = Nd; g.c_rn = 1; g.nb2 = 1; g.alpha = T(1); g.beta = T(1);
-      gemm(g, 1, st);
+      mm(g, st);
     }
     k += 18;
   }
@@ -728,11 +759,29 @@ size_t gf_weight_count(const GfDims& m) {
   return t;
 }
 
-Model* make_plain_gf(const GfDims& m, bool f64, const double* weights, int n_atoms,
-                     const int* types_host, std::string* err) {
+bool gf_mixed_supported(const GfDims& m, std::string* why) {
+  const int dims[6] = {m.nd, m.ed, m.nd + m.ed, m.f1, m.f2, m.f3};
+  for (int d : dims)
+    if (!gemm_tc_shape_ok(d, 16)) {
+      *why = "the mixed graph form needs node, edge and fitting widths (and node + edge) that "
+             "are multiples of 16, at most 256";
+      return false;
+    }
+  return true;
+}
+
+Model* make_plain_gf(const GfDims& m, bool f64, bool tensor_cores, const double* weights,
+                     int n_atoms, const int* types_host, std::string* err) {
   if (m.na > gf::kMaxNa) {
     *err = "graph model supports at most 64 angle neighbours";
     return nullptr;
+  }
+  if (tensor_cores) {
+    if (!gf_mixed_supported(m, err) || !gemm_tc_prepare(err)) return nullptr;
+    auto* p = new gf::PlainGf<float>();
+    p->use_tensor_cores();
+    if (!p->init(m, weights, n_atoms, types_host, err)) { delete p; return nullptr; }
+    return p;
   }
   if (f64) {
     auto* p = new gf::PlainGf<double>();

@@ -1,7 +1,8 @@
 """GPU parity of the graph-family path against the FP64 oracle, through the C ABI.
 
 Small systems are compared whole (FP64 GPU: 1e-10 of the force RMS, rounding
-order only; FP32 GPU: 1e-4).  At the full 24,000-atom size the oracle is too
+order only; FP32 GPU: 1e-4; the mixed form, FP32 with every matrix product on
+the tensor cores with 16-bit operands: 2e-2).  At the full 24,000-atom size the oracle is too
 slow to evaluate whole (the six message-passing layers reach 36 A), so there the
 FP32 forces are compared with the FP64 GPU forces -- the FP64 path being the
 one pinned to the oracle above -- and the FP64 forces of sampled atoms with
@@ -32,7 +33,8 @@ def frms(F):
 
 
 @pytest.mark.parametrize("case", ["tiny_water8", "config3_water96_small_box", "config3_protein700"])
-@pytest.mark.parametrize("prec,tol", [(dp.PREC_PLAIN_F64, 1e-10), (dp.PREC_PLAIN_F32, 1e-4)])
+@pytest.mark.parametrize("prec,tol", [(dp.PREC_PLAIN_F64, 1e-10), (dp.PREC_PLAIN_F32, 1e-4),
+                                      (dp.PREC_FUSED, 2e-2)])
 def test_gf_vs_oracle(case, prec, tol):
     if case == "tiny_water8":
         m = replace(C.GRAPH_MODEL, node=16, edge=8, n_layers=2, f1=12, f2=10, f3=8, nmax=40, na=10)
@@ -47,10 +49,13 @@ def test_gf_vs_oracle(case, prec, tol):
             pytest.skip("FP64 is covered by the two smaller cases")
         m, s = C.GRAPH_MODEL, serving_system(700, 9)
         w = weights(m)
+    if prec == dp.PREC_FUSED and case == "tiny_water8":
+        pytest.skip("the mixed form needs widths that are multiples of 16")
     pot = make(m, s, prec, w)
     E, F, V = pot.compute(s.coords)
     Eo, aeo, Fo, Vo = oracle.gf_compute(m, w, s.types, s.coords, s.box)
-    assert abs(E - Eo) <= 10 * tol * abs(Eo)
+    etol = 1e-2 if prec == dp.PREC_FUSED else 10 * tol     # 16-bit products: ~0.2 % seen
+    assert abs(E - Eo) <= etol * abs(Eo)
     assert np.max(np.abs(F - Fo)) <= tol * frms(Fo)
     assert np.max(np.abs(V - Vo)) <= tol * np.linalg.norm(Vo)
 
@@ -106,3 +111,27 @@ def test_gf_trajectory_does_not_depend_on_rebuild_schedule():
         out.append(pot.get_state()[:2])
         pot.close()
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_gf_mixed_refuses_widths_it_cannot_tile():
+    m, s = replace(C.GRAPH_MODEL, edge=40), serving_system(96, 5)
+    with pytest.raises(dp.DPError) as e:
+        make(m, s, dp.PREC_FUSED, weights(m))
+    assert e.value.code == dp.DP_ERR_UNSUPPORTED
+
+
+def test_gf_mixed_md_tracks_fp32():
+    m, s = C.GRAPH_MODEL, serving_system(700, 9)
+    w = weights(m)
+    masses = s.masses
+    v0 = maxwell_boltzmann(masses[s.types], 300.0, C.VELOCITY_SEED)
+    out = {}
+    for prec in (dp.PREC_PLAIN_F32, dp.PREC_FUSED):
+        pot = make(m, s, prec, w, masses=masses)
+        x, v = s.coords.copy(), v0.copy()
+        tr = pot.step(20, C.DT_FS, coords=x, vel=v, energies=True)
+        out[prec] = (x, tr)
+        pot.close()
+    assert np.max(np.abs(out[dp.PREC_FUSED][0] - out[dp.PREC_PLAIN_F32][0])) < 1e-4
+    et = out[dp.PREC_FUSED][1].sum(1)
+    assert np.all(np.isfinite(et)) and np.max(np.abs(et - et[0])) < 1e-3 * abs(et[0])
