@@ -520,7 +520,7 @@ def report_config(which):
         cap = first["capacity_atom_steps_per_s"]
         out["sweep"] = [first] + [serving_bench(256, load=ld, capacity=cap)
                                   for ld in (0.5, 0.75, 0.9, 1.0, 1.2)]
-        out["memory_capped_1GB"] = serving_bench(256, load=0.9, capacity=cap, mem_budget=1 << 30)
+        out["memory_capped_2GB"] = serving_bench(256, load=0.9, capacity=cap, mem_budget=2 << 30)
     elif which == 5:    # 100,000 atoms: fused vs plain FP32
         s = CF.protein100k()
         m = CF.ATTN_MODEL
