@@ -76,6 +76,11 @@ struct dp_ctx {
   double graph_dt = 0;
   int graph_trace_len = 0;
   bool forces_valid = false;
+  // atoms [0, valid_below) already hold forces for their current positions
+  // (systems carried over by a serving repack); the next compute evaluates
+  // only the rest
+  int valid_below = 0;
+  bool graph_stale = false;   // batch changed: recapture, update the executable
   int kernels_compute = 0, kernels_step = 0;
 };
 
@@ -227,8 +232,10 @@ static MdArgs md_args(dp_ctx* c, double dt) {
 }
 
 // One evaluation on the stream: neighbours (rebuild if flagged), model, forces,
-// reductions.  Returns the number of kernels it launched.
-static int enqueue_compute(dp_ctx* c) {
+// reductions.  With atom0 > 0 only atoms [atom0, n) get energies and forces
+// (their systems must not reach below atom0) and the per-system reduction is
+// skipped.  Returns the number of kernels it launched.
+static int enqueue_compute(dp_ctx* c, int atom0 = 0) {
   NlistArgs na = nlist_args(c);
   int k = 0;
   launch_wrap(na, c->st); ++k;
@@ -238,10 +245,13 @@ static int enqueue_compute(dp_ctx* c) {
   fa.n = c->n; fa.nmax = c->desc.nmax; fa.cap = c->cap; fa.sel_j = c->sel_j; fa.sel_r = c->sel_r;
   fa.skin = c->skin_list; fa.skin_cnt = c->skin_cnt; fa.mirror = c->mirror; fa.selpos = c->selpos;
   fa.F = c->F; fa.atom_vir = c->atom_vir;
-  k += c->model->run(nbr_view(c), c->types, c->atom_e, c->st);
+  fa.atom0 = atom0;
+  if (atom0 > 0) k += c->model->run_range(nbr_view(c), c->types, c->atom_e, c->st, atom0);
+  else k += c->model->run(nbr_view(c), c->types, c->atom_e, c->st);
   fa.g32 = c->model->grad32();
   fa.g64 = c->model->grad64();
   launch_force_gather(fa, c->st); ++k;
+  if (atom0 > 0) return k;
   ReduceArgs ra{};
   ra.n_sys = c->n_sys; ra.sys_atom0 = c->sys_atom0; ra.atom_e = c->atom_e; ra.atom_vir = c->atom_vir;
   ra.F = c->F; ra.sys_e = c->sys_e; ra.sys_vir = c->sys_vir; ra.flags = c->flags;
@@ -267,11 +277,12 @@ static int clear_flags(dp_ctx* c, int bits) {
 // Evaluate at the resident positions with a fresh neighbour build; grows the
 // skin capacity and retries on overflow.
 static int compute_now(dp_ctx* c) {
+  const int atom0 = c->valid_below < c->n ? c->valid_below : 0;
   for (int attempt = 0; attempt < 4; ++attempt) {
     int rc = clear_flags(c, ~0);
     if (rc) return rc;
     launch_flag_set(c->flags, kFlagRebuild, c->st);
-    c->kernels_compute = enqueue_compute(c) + 1;
+    c->kernels_compute = enqueue_compute(c, atom0) + 1;
     CUDA_TRY(c, cudaGetLastError(), "launch");
     int fl = 0;
     rc = read_flags(c, &fl);
@@ -285,6 +296,7 @@ static int compute_now(dp_ctx* c) {
     if (fl & kFlagTimeout) return fail(c, DP_ERR_TIMEOUT, "a device-side wait gave up");
     if (fl & kFlagNonFinite) return fail(c, DP_ERR_NONFINITE, "coordinates, energy or forces are not finite");
     c->forces_valid = true;
+    c->valid_below = 0;
     return DP_OK;
   }
   return fail(c, DP_ERR_NLIST_OVERFLOW, "neighbour skin list kept overflowing");
@@ -465,11 +477,9 @@ static int ctx_set_systems(dp_ctx* c, int n_sys, const int* natoms, const double
   c->ncell = ncell;
   c->boxes.assign(boxes, boxes + 3 * n_sys);
   for (int a = 0; a < 3; ++a) c->box[a] = boxes[a];
-  if (c->graph) {
-    cudaGraphExecDestroy(c->graph);
-    c->graph = nullptr;
-  }
+  c->graph_stale = true;
   c->forces_valid = false;
+  c->valid_below = 0;
   return DP_OK;
 }
 
@@ -529,11 +539,9 @@ extern "C" int dp_compute(dp_ctx* c, const double* coords, double* energy, doubl
   return DP_OK;
 }
 
+// Capture one MD step; an existing executable graph of the same shape is
+// updated in place (cheaper than a new instantiation after a batch change).
 static int build_step_graph(dp_ctx* c, double dt, int trace_len) {
-  if (c->graph) {
-    cudaGraphExecDestroy(c->graph);
-    c->graph = nullptr;
-  }
   const size_t need = (size_t)2 * c->n_sys * trace_len;
   if (need > c->trace_elems) {
     if (c->trace) cudaFree(c->trace);
@@ -552,9 +560,20 @@ static int build_step_graph(dp_ctx* c, double dt, int trace_len) {
   k += 2;
   cudaError_t e = cudaStreamEndCapture(c->st, &g);
   if (e != cudaSuccess) return cuda_fail(c, e, "capture");
-  e = cudaGraphInstantiate(&c->graph, g, 0);
+  bool updated = false;
+  if (c->graph) {
+    cudaGraphExecUpdateResultInfo info{};
+    updated = cudaGraphExecUpdate(c->graph, g, &info) == cudaSuccess;
+    if (!updated) {
+      cudaGetLastError();
+      cudaGraphExecDestroy(c->graph);
+      c->graph = nullptr;
+    }
+  }
+  if (!updated) e = cudaGraphInstantiate(&c->graph, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+  c->graph_stale = false;
   c->graph_dt = dt;
   c->graph_trace_len = c->trace_len;
   c->kernels_step = k;
@@ -593,7 +612,7 @@ extern "C" int dp_step(dp_ctx* c, int n_steps, double dt_fs, double* coords_io, 
     step0[1] = step0[0];
     CUDA_TRY(c, cudaMemcpyAsync(c->step, step0, sizeof step0, cudaMemcpyHostToDevice, c->st), "step base");
     int tl = energies_out ? n_steps : 1;
-    if (!c->graph || c->graph_dt != dt_fs || c->graph_trace_len < tl) {
+    if (!c->graph || c->graph_stale || c->graph_dt != dt_fs || c->graph_trace_len < tl) {
       rc = build_step_graph(c, dt_fs, std::max(tl, c->trace_len));
       if (rc) return rc;
     }
@@ -759,6 +778,7 @@ struct dp_server {
   double busy_ms = 0;
   double* stage_x = nullptr;
   double* stage_v = nullptr;
+  double* stage_f = nullptr;
   std::string err;
 };
 
@@ -819,7 +839,8 @@ extern "C" int dp_server_create(dp_server** out, const dp_model_desc* desc, cons
   s->max_slots = max_slots;
   s->n_cap = (int)n_cap;
   if (cudaMalloc(&s->stage_x, sizeof(double) * 3 * n_cap) != cudaSuccess ||
-      cudaMalloc(&s->stage_v, sizeof(double) * 3 * n_cap) != cudaSuccess) {
+      cudaMalloc(&s->stage_v, sizeof(double) * 3 * n_cap) != cudaSuccess ||
+      cudaMalloc(&s->stage_f, sizeof(double) * 3 * n_cap) != cudaSuccess) {
     g_server_error = "out of device memory for the staging buffers";
     dp_server_free(s);
     return DP_ERR_OOM;
@@ -870,17 +891,29 @@ extern "C" int dp_server_submit(dp_server* s, int n_atoms, const int32_t* types,
 // Rebuild the packed batch from the active requests: retained systems keep
 // their device state (copied through the staging buffers), new ones are
 // uploaded from the host.
+// Pack the active systems contiguously: the ones already running first, in
+// their order, carrying positions, velocities and forces (still valid: a
+// system's forces depend on its own atoms only), then the newly admitted ones.
+// Only the new systems need a force evaluation before the next step.
 static int server_repack(dp_server* s) {
   dp_ctx* c = s->ctx;
   std::vector<int> natoms, types;
   std::vector<double> boxes;
-  int off = 0;
+  std::vector<uint64_t> order;
+  for (int pass = 0; pass < 2; ++pass)
+    for (uint64_t id : s->active)
+      if ((s->reqs[id].offset >= 0) == (pass == 0)) order.push_back(id);
+  s->active.swap(order);
+  int off = 0, carried = 0;
   for (uint64_t id : s->active) {
     ServerReq& r = s->reqs[id];
     const size_t b = sizeof(double) * 3 * r.n;
     if (r.offset >= 0) {
       CUDA_TRY(c, cudaMemcpyAsync(s->stage_x + 3 * off, c->x + 3 * r.offset, b, cudaMemcpyDeviceToDevice, c->st), "repack");
       CUDA_TRY(c, cudaMemcpyAsync(s->stage_v + 3 * off, c->v + 3 * r.offset, b, cudaMemcpyDeviceToDevice, c->st), "repack");
+      if (c->forces_valid)
+        CUDA_TRY(c, cudaMemcpyAsync(s->stage_f + 3 * off, c->F + 3 * r.offset, b, cudaMemcpyDeviceToDevice, c->st), "repack");
+      carried = off + r.n;
     } else {
       CUDA_TRY(c, cudaMemcpyAsync(s->stage_x + 3 * off, r.x.data(), b, cudaMemcpyHostToDevice, c->st), "repack");
       CUDA_TRY(c, cudaMemcpyAsync(s->stage_v + 3 * off, r.v.data(), b, cudaMemcpyHostToDevice, c->st), "repack");
@@ -896,10 +929,21 @@ static int server_repack(dp_server* s) {
     s->dirty = false;
     return DP_OK;
   }
+  const bool keep_forces = c->forces_valid && carried > 0;
   CUDA_TRY(c, cudaMemcpyAsync(c->x, s->stage_x, sizeof(double) * 3 * off, cudaMemcpyDeviceToDevice, c->st), "repack");
   CUDA_TRY(c, cudaMemcpyAsync(c->v, s->stage_v, sizeof(double) * 3 * off, cudaMemcpyDeviceToDevice, c->st), "repack");
+  if (keep_forces)
+    CUDA_TRY(c, cudaMemcpyAsync(c->F, s->stage_f, sizeof(double) * 3 * carried, cudaMemcpyDeviceToDevice, c->st), "repack");
   int rc = ctx_set_systems(c, (int)natoms.size(), natoms.data(), boxes.data(), types.data());
   if (rc) return rc;
+  if (keep_forces) {
+    if (carried == off) {      // departures only: no evaluation, rebuild the lists next step
+      launch_flag_set(c->flags, kFlagRebuild, c->st);
+      c->forces_valid = true;
+    } else {
+      c->valid_below = carried;
+    }
+  }
   s->dirty = false;
   return DP_OK;
 }
@@ -939,7 +983,7 @@ extern "C" int dp_server_tick(dp_server* s, int* n_active, int* n_queued) {
       CUDA_TRY(c, cudaMemcpyAsync(c->step, st, sizeof st, cudaMemcpyHostToDevice, c->st), "tick");
       CUDA_TRY(c, cudaMemcpyAsync(s->stage_x, c->x, sizeof(double) * 3 * c->n, cudaMemcpyDeviceToDevice, c->st), "tick");
       CUDA_TRY(c, cudaMemcpyAsync(s->stage_v, c->v, sizeof(double) * 3 * c->n, cudaMemcpyDeviceToDevice, c->st), "tick");
-      if (!c->graph || c->graph_dt != s->dt || c->graph_trace_len < 1) {
+      if (!c->graph || c->graph_stale || c->graph_dt != s->dt || c->graph_trace_len < 1) {
         rc = build_step_graph(c, s->dt, std::max(1, c->trace_len));
         if (rc) { s->err = c->err; return rc; }
       }
@@ -1042,6 +1086,7 @@ extern "C" void dp_server_free(dp_server* s) {
   if (s->ctx) cudaStreamSynchronize(s->ctx->st);
   if (s->stage_x) cudaFree(s->stage_x);
   if (s->stage_v) cudaFree(s->stage_v);
+  if (s->stage_f) cudaFree(s->stage_f);
   dp_free(s->ctx);
   delete s;
 }

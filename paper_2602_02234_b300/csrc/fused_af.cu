@@ -108,6 +108,7 @@ static_assert(kSmemAtom <= 227 * 1024, "per-atom shared memory");
 
 struct Params {
   int n, nmax, e1, e2, m2, n_layers, heads, dh;
+  int atom0;                              // atoms [atom0, n) are evaluated
   float rs, rc, inv_nmax, inv_sqrt_d;
   const int* sel_j;
   const double* sel_r;
@@ -696,7 +697,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_af_fwd(Params p) {
   Misc* m = reinterpret_cast<Misc*>(sm + SM_MISC);
   kernel_prologue(m);
   Bar mb{&m->bar, 0u}, wb{&m->wbar, 0u}, xb{&m->xbar, 0u};
-  for (int atom = blockIdx.x; atom < p.n; atom += gridDim.x)
+  for (int atom = p.atom0 + blockIdx.x; atom < p.n; atom += gridDim.x)
     if (!fwd_atom(p, atom, sm, m, m->tptr, mb, wb, xb)) break;
   kernel_epilogue(m);
 }
@@ -1137,7 +1138,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_af_bwd(Params p) {
     *reinterpret_cast<op_t*>(m->ones + tc::kmajor_off(0, threadIdx.x, kW)) = f2op(1.f);
   __syncthreads();
   Bar mb{&m->bar, 0u}, wb{&m->wbar, 0u}, gb{&m->pbar, 0u}, xb{&m->xbar, 0u};
-  for (int atom = blockIdx.x; atom < p.n; atom += gridDim.x)
+  for (int atom = p.atom0 + blockIdx.x; atom < p.n; atom += gridDim.x)
     if (!bwd_atom(p, atom, sm, m, m->tptr, mb, wb, gb, xb)) break;
   kernel_epilogue(m);
 }
@@ -1339,13 +1340,26 @@ class FusedAf : public Model {
   }
   int run_parts(const NbrView& nv, const int* types, double* atom_e, cudaStream_t st,
                 int parts) override {
+    return launch(nv, types, atom_e, st, parts, 0);
+  }
+  // The fitting kernel still runs over every atom (its species tiles span the
+  // batch); outside [atom0, n) it reads stale descriptors and writes energies
+  // and dE/dD that nothing reads before the next full evaluation.
+  int run_range(const NbrView& nv, const int* types, double* atom_e, cudaStream_t st,
+                int atom0) override {
+    return launch(nv, types, atom_e, st, 7, atom0);
+  }
+  int launch(const NbrView& nv, const int* types, double* atom_e, cudaStream_t st, int parts,
+             int atom0) {
     Params p = base_;
     p.sel_j = nv.sel_j;
     p.sel_r = nv.sel_r;
     p.types = types;
+    p.atom0 = atom0;
+    const int grid = std::max(1, std::min(n_ - atom0, sms_));
     int k = 0;
     if (parts & 1) {
-      k_af_fwd<<<grid_, kThreads, kSmemAtom, st>>>(p);
+      k_af_fwd<<<grid, kThreads, kSmemAtom, st>>>(p);
       ++k;
     }
     if (parts & 2) {
@@ -1355,7 +1369,7 @@ class FusedAf : public Model {
       ++k;
     }
     if (parts & 4) {
-      k_af_bwd<<<grid_, kThreads, kSmemAtom, st>>>(p);
+      k_af_bwd<<<grid, kThreads, kSmemAtom, st>>>(p);
       ++k;
     }
     return k;

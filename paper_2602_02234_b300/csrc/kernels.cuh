@@ -41,6 +41,7 @@ cudaError_t nlist_configure();
 // ----------------------------------------------------------------- forces, MD
 struct ForceArgs {
   int n, nmax, cap;
+  int atom0;             // forces of atoms [atom0, n) only
   const int* sel_j;
   const double* sel_r;
   const SkinEntry* skin;

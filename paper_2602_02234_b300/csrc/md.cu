@@ -18,12 +18,12 @@ namespace dp {
 
 
 template <typename G>
-__global__ void k_force_gather(int n, int nmax, int cap, const int* __restrict__ sel_j,
+__global__ void k_force_gather(int atom0, int n, int nmax, int cap, const int* __restrict__ sel_j,
                                const double* __restrict__ sel_r, const SkinEntry* __restrict__ skin,
                                const int* __restrict__ skin_cnt, const int* __restrict__ mirror,
                                const short* __restrict__ selpos, const G* __restrict__ g,
                                double* __restrict__ F, double* __restrict__ atom_vir) {
-  int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int i = atom0 + (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   int lane = threadIdx.x & 31;
   if (i >= n) return;
   double f[3] = {0, 0, 0};
@@ -62,13 +62,14 @@ __global__ void k_force_gather(int n, int nmax, int cap, const int* __restrict__
 }
 
 void launch_force_gather(const ForceArgs& a, cudaStream_t st) {
-  int blocks = ceil_div((long long)a.n * 32, 256);
+  int blocks = ceil_div((long long)(a.n - a.atom0) * 32, 256);
+  if (blocks <= 0) return;
   if (a.g64)
-    k_force_gather<double><<<blocks, 256, 0, st>>>(a.n, a.nmax, a.cap, a.sel_j, a.sel_r, a.skin,
+    k_force_gather<double><<<blocks, 256, 0, st>>>(a.atom0, a.n, a.nmax, a.cap, a.sel_j, a.sel_r, a.skin,
                                                    a.skin_cnt, a.mirror, a.selpos, a.g64, a.F,
                                                    a.atom_vir);
   else
-    k_force_gather<float><<<blocks, 256, 0, st>>>(a.n, a.nmax, a.cap, a.sel_j, a.sel_r, a.skin,
+    k_force_gather<float><<<blocks, 256, 0, st>>>(a.atom0, a.n, a.nmax, a.cap, a.sel_j, a.sel_r, a.skin,
                                                   a.skin_cnt, a.mirror, a.selpos, a.g32, a.F,
                                                   a.atom_vir);
 }

@@ -36,6 +36,14 @@ class Model {
     (void)parts;
     return run(nv, types, atom_e, st);
   }
+  // Only atoms [atom0, n): their atomic energies and pair gradients (the
+  // rest of both arrays is left as it was; implementations that cannot
+  // restrict the range evaluate everything).
+  virtual int run_range(const NbrView& nv, const int* types, double* atom_e, cudaStream_t st,
+                        int atom0) {
+    (void)atom0;
+    return run(nv, types, atom_e, st);
+  }
   // Pair gradients (n_atoms x nmax x 3): exactly one of the two is non-null.
   virtual const float* grad32() const { return nullptr; }
   virtual const double* grad64() const { return nullptr; }
