@@ -87,6 +87,9 @@ struct MdArgs {
 };
 void launch_kick_drift(const MdArgs& a, cudaStream_t st);
 void launch_kick_final(const MdArgs& a, cudaStream_t st);
+// *differs |= 1 when the two arrays of `count` doubles differ in any bit
+void launch_compare(long long count, const double* a, const double* b, int* differs,
+                    cudaStream_t st);
 void launch_record(const MdArgs& a, const double* sys_e, double* trace, int trace_len, cudaStream_t st);
 
 // ----------------------------------------------------------------- plain model

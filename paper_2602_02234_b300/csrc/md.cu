@@ -184,4 +184,19 @@ void launch_record(const MdArgs& a, const double* sys_e, double* trace, int trac
                                     a.n_sys, trace_len);
 }
 
+__global__ void k_compare(long long count, const double* __restrict__ a,
+                          const double* __restrict__ b, int* __restrict__ differs) {
+  bool d = false;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    d |= __double_as_longlong(a[i]) != __double_as_longlong(b[i]);
+  if (__any_sync(0xffffffffu, d) && (threadIdx.x & 31) == 0) atomicOr(differs, 1);
+}
+
+void launch_compare(long long count, const double* a, const double* b, int* differs,
+                    cudaStream_t st) {
+  const long long blocks = std::min<long long>(ceil_div(count, 256), 1184);
+  if (blocks > 0) k_compare<<<(int)blocks, 256, 0, st>>>(count, a, b, differs);
+}
+
 }  // namespace dp

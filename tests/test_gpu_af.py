@@ -177,6 +177,34 @@ def test_trajectory_does_not_depend_on_rebuild_schedule(prec):
         assert np.array_equal(x, out[0][0]) and np.array_equal(v, out[0][1])
 
 
+@pytest.mark.parametrize("prec", [dp.PREC_PLAIN_F64, dp.PREC_FUSED])
+def test_host_round_trip_each_step_matches_resident_stepping(prec):
+    """dp_step(1) fed back its own host output each step (the resident forces
+    are kept when the coordinates come back unchanged) equals resident
+    stepping bit for bit; a changed coordinate is picked up."""
+    m, s = replace(C.ATTN_MODEL, n_layers=2) if prec == dp.PREC_PLAIN_F64 else C.ATTN_MODEL, \
+        serving_system(300, 4)
+    masses = s.masses
+    v0 = maxwell_boltzmann(masses[s.types], 300.0, C.VELOCITY_SEED)
+    a, _ = make(m, s, prec, masses=masses)
+    xa, va = s.coords.copy(), v0.copy()
+    ta = a.step(6, C.DT_FS, coords=xa, vel=va, energies=True)
+    b, _ = make(m, s, prec, masses=masses)
+    xb, vb = s.coords.copy(), v0.copy()
+    tb = np.concatenate([b.step(1, C.DT_FS, coords=xb, vel=vb, energies=True) for _ in range(6)])
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(ta, tb)
+    # a moved atom must not reuse the old forces
+    xc = xb.copy()
+    xc[7, 0] += 0.05
+    xe, ve = xc.copy(), vb.copy()
+    b.step(1, C.DT_FS, coords=xe, vel=ve)
+    c, _ = make(m, s, prec, masses=masses)
+    c.set_state(xc, vb, 0)
+    c.step(1, C.DT_FS)
+    xf, vf, _ = c.get_state()
+    assert np.array_equal(xe, xf) and np.array_equal(ve, vf)
+
+
 def test_dpenergy_autograd_matches_finite_differences():
     import torch
     m = replace(C.ATTN_MODEL, n_layers=1, nmax=64)
