@@ -39,6 +39,11 @@ WORKLOAD = ("protein-in-water 24,000 atoms (1,500-atom blob + 7,500 H2O, 57.69x5
             "axis 16, fitting 2048-240-240-240-1, rc 6 A, nmax 120; NVE dt 0.5 fs, rebuild every 10")
 METRIC = "energy+force atom-steps/s"
 FP32_ALU_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # 148 SMs x 128 FP32 lanes x FMA x 2.032 GHz
+# DRAM bytes (read + write) per atom of one launch, from the ncu captures of the
+# 4,800-atom case (profiles/k_af_*_small_ncu.md); traffic grows with the atoms
+# processed (per-atom tiles, lists, gradients), so a launch over N atoms moves N x this
+NCU_TRAFFIC_PER_ATOM = {"k_af_bwd": (545.597952e6 + 9.505792e6) / 4800,
+                        "k_af_fwd": (13.464320e6 + 452.977152e6) / 4800}
 
 
 def peaks():
@@ -324,8 +329,12 @@ def run_ours(args, rank, world, local_rank):
         bound, peak_note = "alu", "FP32 FFMA: 148 SMs x 128 lanes x 2 x 2.032 GHz (derived)"
         kernel_name = "plain network phase (all kernels of one evaluation)"
     achieved = flops / (net_ms / 1e3) / 1e12
+    traffic = NCU_TRAFFIC_PER_ATOM.get(kernel_name)
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": kernel_name,
+                "frac": achieved / peak,
+                "traffic": traffic * s.n if traffic and args.system == "protein24k" else None,
+                "traffic_note": "DRAM bytes per launch, scaled from the 4,800-atom ncu capture",
+                "kernel": kernel_name,
                 "peak_kind": peak_note, "algorithmic_flop_per_launch": flops,
                 "launch_ms": net_ms, "kernel_ms": kernel_ms}
 
