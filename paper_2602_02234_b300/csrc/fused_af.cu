@@ -91,7 +91,7 @@ struct Misc {
   float sw[kW], dsw[kW], s[kW], d[kW];
   float rh[kW][3];
   float Rt[kW][4];
-  float T[4][kW];
+  __align__(16) float T[4][kW];   // also a bulk-copy destination
   float dT[4][kW];
   float dRt[kW][4];
   float drc[kW][3];
@@ -705,11 +705,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_af_fwd(Params p) {
 // ------------------------------------------------------------------ backward
 // Adjoint of one atom: dE/dD (from the fitting kernel) back to g_ij.
 // Barriers: mb tensor-core products, gb stored activation tiles, wb and xb
-// weight tiles.
+// weight tiles (xb also dE/dD and T at the start of an atom).
 __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32_t tb, Bar& mb,
                          Bar& wb, Bar& gb, Bar& xb) {
   const int t = threadIdx.x, r = row_id(), pt = part_id();
   const uint32_t lo = lane_base();
+  // dE/dD (into the P tile, FP32) and T arrive by bulk copy during the setup
+  tc::fence_async_smem();
+  __syncthreads();
+  if (t == 0) {
+    const uint32_t bd = kW * p.m2 * 4, bt = 4 * kW * 4;
+    issue_copy(xb, sm + SM_P, p.dD + (size_t)atom * kW * p.m2, bd, bd + bt);
+    issue_copy(xb, reinterpret_cast<uint8_t*>(&m->T[0][0]), p.Tm + (size_t)atom * 4 * kW, bt, 0);
+  }
   atom_setup(p, atom, m);
   const int ngroups = (m->nvalid + 7) >> 3;
   const int L = p.n_layers;
@@ -724,13 +732,11 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
   };
   // ---- descriptor adjoint: dT[a][f] = sum_q dD[f][q] T[a][q] + sum_g dD[g][f] T[a][g]
   // (the second sum for f < m2 only); feature f = row id, the 128-term sum split
+  load_G(sm + SM_G, L, gb);   // the last layer's output, for dG_L below
+  if (!xb.wait(p.status)) return false;
   {
     const int f = r;
-    float* dDs = reinterpret_cast<float*>(sm + SM_P);   // 128 x m2 FP32 staging
-    for (int i = t; i < kW * p.m2; i += kThreads) dDs[i] = p.dD[(size_t)atom * kW * p.m2 + i];
-    if (pt == 0)
-      for (int a = 0; a < 4; ++a) m->T[a][f] = p.Tm[((size_t)atom * 4 + a) * kW + f];
-    __syncthreads();
+    const float* dDs = reinterpret_cast<const float*>(sm + SM_P);   // 128 x m2 FP32
     float v[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
@@ -748,7 +754,6 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
       m->dT[3][f] = o.w;
     }
   }
-  load_G(sm + SM_G, L, gb);
   if (ngroups > 0 && !gb.wait(p.status)) return false;
   __syncthreads();
   {
