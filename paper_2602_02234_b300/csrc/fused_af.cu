@@ -485,30 +485,36 @@ __device__ bool qkv(const Params& p, uint8_t* sm, uint32_t tb, Bar& mb, Bar& xb)
 
 // Softmax normaliser of row r of the head scores in tensor memory.  With
 // u_jk = S_jk log2(e)/sqrt(d) + log2 sw_k (-inf for an empty column) the
-// weights are w_jk = 2^(u_jk - beta_j), beta_j = log2 sum_k 2^u_jk.  Each part
-// takes one pass over its 32-column chunks (running maximum, rescaled sum) and
-// the partial results of the row are merged.  beta = +inf for an empty row, so
-// that all its weights vanish.
-__device__ float softmax_beta(const Params& p, Misc* m, uint32_t taddr) {
+// weights are w_jk = 2^(u_jk - beta_j), beta_j = log2 sum_k 2^u_jk; the parts of
+// a row merge their partial (maximum, sum) pairs.  beta = +inf for an empty
+// row, so that all its weights vanish.
+// Each thread's part is one 32-column chunk, whose
+// e_k = 2^(u_k - m) (m = the chunk's maximum) it leaves in tensor memory in
+// place of the scores, so that the weights need no second exponential:
+// w_k = e_k 2^(m - beta).  Returns {beta, 2^(m - beta)}.
+static_assert(kStride == kW, "one 32-column chunk per thread");
+__device__ float2 softmax_beta_keep(const Params& p, Misc* m, uint32_t taddr) {
   const float a = p.inv_sqrt_d * 1.4426950408889634f;
   const int nv = m->nvalid;
+  const int c = 32 * part_id();
   float mx = -INFINITY, z = 0.f;
-  for (int c = 32 * part_id(); c < nv; c += kStride) {
+  if (c < nv) {
     float v[32];
     tc::tmem_ld32(taddr + c, v);
-    float cm = -INFINITY;
 #pragma unroll
     for (int q = 0; q < 32; ++q) {
       v[q] = fmaf(v[q], a, m->col[c + q].x);
-      cm = fmaxf(cm, v[q]);
+      mx = fmaxf(mx, v[q]);
     }
-    const float nm = fmaxf(mx, cm);
-    const float ref = nm == -INFINITY ? 0.f : nm;
+    const float ref = mx == -INFINITY ? 0.f : mx;
     float zc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int q = 0; q < 32; ++q) zc[q & 3] += exp2f(v[q] - ref);
-    z = z * exp2f(mx - ref) + ((zc[0] + zc[1]) + (zc[2] + zc[3]));
-    mx = nm;
+    for (int q = 0; q < 32; ++q) {
+      v[q] = exp2f(v[q] - ref);
+      zc[q & 3] += v[q];
+    }
+    z = (zc[0] + zc[1]) + (zc[2] + zc[3]);
+    tc::tmem_st32(taddr + c, v);
   }
   float4 all[kSplit];
   row_all(m, make_float4(mx, z, 0.f, 0.f), all);
@@ -519,7 +525,9 @@ __device__ float softmax_beta(const Params& p, Misc* m, uint32_t taddr) {
   float Z = 0.f;
 #pragma unroll
   for (int i = 0; i < kSplit; ++i) Z += __fmul_rn(all[i].y, exp2f(all[i].x - bref));
-  return (Z > 0.f && row_id() < nv) ? bref + log2f(Z) : INFINITY;
+  const float beta = (Z > 0.f && row_id() < nv) ? bref + log2f(Z) : INFINITY;
+  const float mref = mx == -INFINITY ? 0.f : mx;
+  return make_float2(beta, exp2f(mref - beta));
 }
 
 // attention weights w_jk = 2^(u_jk - beta_j) of 32 columns from raw scores v
@@ -558,15 +566,14 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
     MMA_GROUP(mb, p.status,
               mma_issue(tb + R3, kop(sm + SM_Q, kW), kop(sm + SM_K, kW), kW, kDH, false));
     for (int h = 0; h < p.heads; ++h) {
-      const float st = softmax_beta(p, m, tb + lo + R3);
-      if (pt == 0) p.smx[(((size_t)atom * p.n_layers + l) * p.heads + h) * kW + r] = st;
+      const float2 st = softmax_beta_keep(p, m, tb + lo + R3);
+      if (pt == 0) p.smx[(((size_t)atom * p.n_layers + l) * p.heads + h) * kW + r] = st.x;
       for (int c = 32 * pt; c < kW; c += kStride) {
         float v[32];
         if (c < m->nvalid) {
-          tc::tmem_ld32(tb + lo + R3 + c, v);
-          softmax_w(p, m, c, st, v);
+          tc::tmem_ld32(tb + lo + R3 + c, v);   // e_k = 2^(u_k - m)
 #pragma unroll
-          for (int q = 0; q < 32; ++q) v[q] *= gate(rj, m->col[c + q]);
+          for (int q = 0; q < 32; ++q) v[q] *= st.y * gate(rj, m->col[c + q]);
         } else {
 #pragma unroll
           for (int q = 0; q < 32; ++q) v[q] = 0.f;
