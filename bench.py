@@ -107,6 +107,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ------------------------------------------------------------------ replicas
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest of every rank's x: a job is as slow as its slowest replica."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, seconds):
+    """Whole-job rate: the units every rank processed over the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 # ------------------------------------------------------------------ algorithmic work
 def af_flops_per_atom(model, n):
     """Algorithmic FLOPs for one atom with n real neighbours, split as
@@ -273,11 +289,7 @@ def run_ours(args, rank, world, local_rank):
                 e1.record(stream)
             e1.synchronize()
         barrier()
-        ms = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
         return ms, clk.summary()
 
     results = {}
@@ -289,7 +301,7 @@ def run_ours(args, rank, world, local_rank):
     main = results[main_name]
     pot = main["pot"]
     K = args.steps
-    value = s.n * K * world / (main["ms"] / 1e3)
+    value = job_throughput(s.n * K, world, main["ms"] / 1e3)
 
     # the dominant kernel alone, timed with events on the stream it runs on
     cnt, _, _ = pot.neighbours()
@@ -349,12 +361,8 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(K):
         tr = pot.step(1, CF.DT_FS, coords=xh, vel=vh, energies=True)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": s.n * K * world / e2e_s, "unit": "atom-steps/s",
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    e2e = {"value": job_throughput(s.n * K, world, e2e_s), "unit": "atom-steps/s",
            "h2d_bytes_per_step": 2 * xh.nbytes, "d2h_bytes_per_step": 2 * xh.nbytes + tr.nbytes,
            "note": "host wall clock around dp_step(1) with pinned host coords/velocities in and out"}
 
@@ -371,7 +379,7 @@ def run_ours(args, rank, world, local_rank):
             "clocks": main["clocks"], "e2e": e2e, "gpu_launches": n_step * K,
             "roofline": roofline}
     for name in results:
-        line[name] = {"value": s.n * K * world / (results[name]["ms"] / 1e3),
+        line[name] = {"value": job_throughput(s.n * K, world, results[name]["ms"] / 1e3),
                       "ms_per_step": results[name]["ms"] / K}
     if "fused_f16" in results and "plain_f32" in results:
         line["fused_vs_plain"] = results["plain_f32"]["ms"] / results["fused_f16"]["ms"]

@@ -19,6 +19,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "kernels.cuh"
 #include "model.h"
@@ -89,6 +91,13 @@ struct dp_ctx {
 static thread_local std::string g_init_error;
 struct dp_server;
 extern "C" void dp_server_free(dp_server* s);
+
+// NVTX range around an ABI call or an MD step (visible in Nsight timelines;
+// no cost without a profiler attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 static int fail(dp_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
@@ -526,6 +535,7 @@ extern "C" int dp_init(dp_ctx** out, const dp_model_desc* desc, int n_atoms, con
 
 extern "C" int dp_compute(dp_ctx* c, const double* coords, double* energy, double* forces,
                           double* virial, int ptr_kind) {
+  NvtxRange nvtx("dp_compute");
   if (!c) return fail(nullptr, DP_ERR_ARG, "ctx is NULL");
   if (!coords) return fail(c, DP_ERR_ARG, "coords is NULL");
   int rc = copy_in(c, c->x, coords, 3 * (size_t)c->n, ptr_kind);
@@ -586,6 +596,7 @@ static int build_step_graph(dp_ctx* c, double dt, int trace_len) {
 
 extern "C" int dp_step(dp_ctx* c, int n_steps, double dt_fs, double* coords_io, double* vel_io,
                        double* energies_out, int ptr_kind) {
+  NvtxRange nvtx("dp_step");
   if (!c) return fail(nullptr, DP_ERR_ARG, "ctx is NULL");
   if (n_steps < 0) return fail(c, DP_ERR_ARG, "n_steps must be >= 0");
   if (!(dt_fs > 0) || !isfinite(dt_fs)) return fail(c, DP_ERR_ARG, "dt must be positive");
@@ -636,7 +647,10 @@ extern "C" int dp_step(dp_ctx* c, int n_steps, double dt_fs, double* coords_io, 
       rc = build_step_graph(c, dt_fs, std::max(tl, c->trace_len));
       if (rc) return rc;
     }
-    for (int s = 0; s < n_steps; ++s) CUDA_TRY(c, cudaGraphLaunch(c->graph, c->st), "graph launch");
+    for (int s = 0; s < n_steps; ++s) {
+      NvtxRange step("md step");
+      CUDA_TRY(c, cudaGraphLaunch(c->graph, c->st), "graph launch");
+    }
     int fl = 0;
     rc = read_flags(c, &fl);
     if (rc) return rc;
@@ -969,6 +983,7 @@ static int server_repack(dp_server* s) {
 }
 
 extern "C" int dp_server_tick(dp_server* s, int* n_active, int* n_queued) {
+  NvtxRange nvtx("dp_server_tick");
   if (!s) return DP_ERR_ARG;
   dp_ctx* c = s->ctx;
   const double t0 = now_ms();
