@@ -86,7 +86,8 @@ constexpr int SM_G = 0, SM_Q = kTile, SM_K = 2 * kTile, SM_V = 3 * kTile, SM_P =
 struct Misc {
   uint8_t ones[16 * kW * 2];  // 16 x 128 K-major operand: row 0 ones (column sums)
   uint8_t rhb[16 * kW * 2];   // rows 0..2: unit-vector components of each slot
-  float4 col[kW];             // per neighbour slot: {log2 sw (-inf if empty), rh_x, rh_y, rh_z}
+  // per neighbour slot k: cl[0][k] = log2 sw (-inf if empty), cl[1..3][k] = unit vector
+  __align__(16) float cl[4][kW];
   float4 xch[kSplit][kW];     // exchange of per-row partial results
   float sw[kW], dsw[kW], s[kW], d[kW];
   float rh[kW][3];
@@ -303,7 +304,8 @@ __device__ void env_row(const Params& p, int atom, Misc* m, int t) {
     m->sw[t] = 0.f; m->dsw[t] = 0.f; m->s[t] = 0.f; m->d[t] = 1.f;
     for (int a = 0; a < 3; ++a) m->rh[t][a] = 0.f;
     for (int a = 0; a < 4; ++a) m->Rt[t][a] = 0.f;
-    m->col[t] = make_float4(-INFINITY, 0.f, 0.f, 0.f);
+    m->cl[0][t] = -INFINITY;
+    m->cl[1][t] = m->cl[2][t] = m->cl[3][t] = 0.f;
     m->tj[t] = -1;
     return;
   }
@@ -319,7 +321,8 @@ __device__ void env_row(const Params& p, int atom, Misc* m, int t) {
     m->rh[t][a] = r[a] / d;
     m->Rt[t][1 + a] = s * r[a] / d;
   }
-  m->col[t] = make_float4(sw > 0.f ? log2f(sw) : -INFINITY, r[0] / d, r[1] / d, r[2] / d);
+  m->cl[0][t] = sw > 0.f ? log2f(sw) : -INFINITY;
+  for (int a = 0; a < 3; ++a) m->cl[1 + a][t] = r[a] / d;
   m->tj[t] = p.types[j];
 }
 
@@ -483,6 +486,42 @@ __device__ bool qkv(const Params& p, uint8_t* sm, uint32_t tb, Bar& mb, Bar& xb)
   return true;
 }
 
+// Packed FP32 pairs: two neighbour columns per instruction.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+__device__ __forceinline__ float2 bc2(float x) { return make_float2(x, x); }
+
+// gate r^_j . r^_k for the column pair (k, k+1); rj holds row j's components twice
+__device__ __forceinline__ float2 gate2(const float2* rj, const Misc* m, int k) {
+  return ffma2(rj[0], ld2(&m->cl[1][k]), ffma2(rj[1], ld2(&m->cl[2][k]), fmul2(rj[2], ld2(&m->cl[3][k]))));
+}
+
 // Softmax normaliser of row r of the head scores in tensor memory.  With
 // u_jk = S_jk log2(e)/sqrt(d) + log2 sw_k (-inf for an empty column) the
 // weights are w_jk = 2^(u_jk - beta_j), beta_j = log2 sum_k 2^u_jk; the parts of
@@ -502,18 +541,22 @@ __device__ float2 softmax_beta_keep(const Params& p, Misc* m, uint32_t taddr) {
     float v[32];
     tc::tmem_ld32(taddr + c, v);
 #pragma unroll
-    for (int q = 0; q < 32; ++q) {
-      v[q] = fmaf(v[q], a, m->col[c + q].x);
-      mx = fmaxf(mx, v[q]);
+    for (int q = 0; q < 32; q += 2) {
+      const float2 u = ffma2(make_float2(v[q], v[q + 1]), bc2(a), ld2(&m->cl[0][c + q]));
+      v[q] = u.x;
+      v[q + 1] = u.y;
+      mx = fmaxf(mx, fmaxf(u.x, u.y));
     }
-    const float ref = mx == -INFINITY ? 0.f : mx;
-    float zc[4] = {0.f, 0.f, 0.f, 0.f};
+    const float2 nref = bc2(mx == -INFINITY ? 0.f : -mx);
+    float2 zc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll
-    for (int q = 0; q < 32; ++q) {
-      v[q] = exp2f(v[q] - ref);
-      zc[q & 3] += v[q];
+    for (int q = 0; q < 32; q += 2) {
+      const float2 u = fadd2(make_float2(v[q], v[q + 1]), nref);
+      v[q] = exp2f(u.x);
+      v[q + 1] = exp2f(u.y);
+      zc[(q >> 1) & 1] = fadd2(zc[(q >> 1) & 1], make_float2(v[q], v[q + 1]));
     }
-    z = (zc[0] + zc[1]) + (zc[2] + zc[3]);
+    z = (zc[0].x + zc[1].x) + (zc[0].y + zc[1].y);
     tc::tmem_st32(taddr + c, v);
   }
   float4 all[kSplit];
@@ -536,11 +579,12 @@ __device__ __forceinline__ void softmax_w(const Params& p, const Misc* m, int c,
                                           float* v) {
   const float a = p.inv_sqrt_d * 1.4426950408889634f;
 #pragma unroll
-  for (int q = 0; q < 32; ++q) v[q] = exp2f(fmaf(v[q], a, m->col[c + q].x) - beta);
-}
-
-__device__ __forceinline__ float gate(const float* rj, const float4& ck) {
-  return rj[0] * ck.y + rj[1] * ck.z + rj[2] * ck.w;
+  for (int q = 0; q < 32; q += 2) {
+    const float2 u = fadd2(ffma2(make_float2(v[q], v[q + 1]), bc2(a), ld2(&m->cl[0][c + q])),
+                           bc2(-beta));
+    v[q] = exp2f(u.x);
+    v[q + 1] = exp2f(u.y);
+  }
 }
 
 // ------------------------------------------------------------------ forward
@@ -559,7 +603,8 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
   for (int i = t; i < ngroups * 2048 / 16; i += kThreads)
     reinterpret_cast<int4*>(Gdst)[i] = reinterpret_cast<const int4*>(sm + SM_G)[i];
   const bool valid = m->tj[r] >= 0;
-  const float rj[3] = {m->col[r].y, m->col[r].z, m->col[r].w};
+  const float2 rj[3] = {make_float2(m->cl[1][r], m->cl[1][r]), make_float2(m->cl[2][r], m->cl[2][r]),
+                        make_float2(m->cl[3][r], m->cl[3][r])};
   for (int l = 0; l < p.n_layers; ++l) {
     if (!qkv(p, sm, tb, mb, xb)) return false;
     bulk_load(wb, sm + SM_W, p.WoT + (size_t)l * kTile, kTile);  // lands during the heads
@@ -573,7 +618,11 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
         if (c < m->nvalid) {
           tc::tmem_ld32(tb + lo + R3 + c, v);   // e_k = 2^(u_k - m)
 #pragma unroll
-          for (int q = 0; q < 32; ++q) v[q] *= st.y * gate(rj, m->col[c + q]);
+          for (int q = 0; q < 32; q += 2) {
+            const float2 w = fmul2(fmul2(make_float2(v[q], v[q + 1]), bc2(st.y)), gate2(rj, m, c + q));
+            v[q] = w.x;
+            v[q + 1] = w.y;
+          }
         } else {
 #pragma unroll
           for (int q = 0; q < 32; ++q) v[q] = 0.f;
@@ -799,7 +848,8 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
             f2op(valid ? m->rh[r][a] : 0.f);
     }
   }
-  const float rj[3] = {m->col[r].y, m->col[r].z, m->col[r].w};
+  const float2 rj[3] = {make_float2(m->cl[1][r], m->cl[1][r]), make_float2(m->cl[2][r], m->cl[2][r]),
+                        make_float2(m->cl[3][r], m->cl[3][r])};
   for (int l = L - 1; l >= 0; --l) {
     // ---- loads of this layer, all in flight at once: the stored layer input
     // (G tile) and output (V tile) on gb, Wo^T (W tile) on wb, and the Q and
@@ -902,7 +952,11 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
           softmax_w(p, m, c, st, v);
           tc::tmem_st32(tb + lo + R3 + c, v);
 #pragma unroll
-          for (int q = 0; q < 32; ++q) v[q] *= gate(rj, m->col[c + q]);
+          for (int q = 0; q < 32; q += 2) {
+            const float2 w = fmul2(make_float2(v[q], v[q + 1]), gate2(rj, m, c + q));
+            v[q] = w.x;
+            v[q + 1] = w.y;
+          }
         } else {
 #pragma unroll
           for (int q = 0; q < 32; ++q) v[q] = 0.f;
@@ -944,12 +998,16 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
             for (int q8 = 0; q8 < 16; q8 += 8) {
               float ds[8], x[8];
 #pragma unroll
-              for (int e = 0; e < 8; ++e) {
+              for (int e = 0; e < 8; e += 2) {
                 const int q = q8 + e;
-                const float4 ck = m->col[c + c16 + q];
-                const float dw = da[q] * gate(rj, ck);
-                x[e] = da[q] * s[q];                  // gate adjoint dc_jk
-                ds[e] = s[q] * (dw - wdw);            // dS_jk = w (dw - sum w dw)
+                const float2 s2 = make_float2(s[q], s[q + 1]), da2 = make_float2(da[q], da[q + 1]);
+                const float2 dw = fmul2(da2, gate2(rj, m, c + c16 + q));
+                const float2 xx = fmul2(da2, s2);                       // gate adjoint dc_jk
+                const float2 dd = fmul2(s2, fadd2(dw, bc2(-wdw)));      // dS = w (dw - sum w dw)
+                x[e] = xx.x;
+                x[e + 1] = xx.y;
+                ds[e] = dd.x;
+                ds[e + 1] = dd.y;
               }
               store8(sm + SM_W, r, c + c16 + q8, kW, ds);
               store8(sm + SM_G, r, c + c16 + q8, kW, x);
