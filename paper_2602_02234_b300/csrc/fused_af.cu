@@ -204,6 +204,15 @@ __device__ __forceinline__ void store32(uint8_t* tile, int r, int c, int Kx, int
     if (c + q < ncol) store8(tile, r, c + q, Kx, v + q);
 }
 
+// tanh by the hardware approximation (one instruction, relative error about
+// 2^-11): every tanh output of the fused path is rounded to a 16-bit operand
+// tile, whose rounding is of the same size.
+__device__ __forceinline__ float tanh_hw(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // The kSplit partial results of this thread's row, in part order.  Every
 // thread of the block calls it (two barriers).  All threads of a row then
 // combine the same values in the same order, so they never disagree on a row
@@ -379,7 +388,7 @@ __device__ bool embed_h2(const Params& p, uint8_t* sm, Misc* m, uint32_t tb, Bar
     float v[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q)
-      v[q] = tj >= 0 ? tanhf(s * p.W1[tj * p.e1 + c + q] + p.b1[tj * p.e1 + c + q]) : 0.f;
+      v[q] = tj >= 0 ? tanh_hw(s * p.W1[tj * p.e1 + c + q] + p.b1[tj * p.e1 + c + q]) : 0.f;
     store8(H1, r, c, p.e1, v);
   }
   for (int c = 8 * pt; c < p.e2; c += 8 * kSplit) {
@@ -397,7 +406,7 @@ __device__ bool embed_h2(const Params& p, uint8_t* sm, Misc* m, uint32_t tb, Bar
         tc::tmem_ld16(tb + lo + R0 + c, v);
         if (mine) {
 #pragma unroll
-          for (int q = 0; q < 16; ++q) v[q] = tanhf(v[q] + p.b2[sp * p.e2 + c + q]);
+          for (int q = 0; q < 16; ++q) v[q] = tanh_hw(v[q] + p.b2[sp * p.e2 + c + q]);
           store8(H2, r, c, p.e2, v);
           store8(H2, r, c + 8, p.e2, v + 8);
         }
@@ -438,7 +447,7 @@ __device__ bool embed_forward(const Params& p, uint8_t* sm, Misc* m, uint32_t tb
           tc::tmem_ld16x2(tb + lo + R1 + c + c16, v, tb + lo + R2 + c + c16, g);
           if (mine) {
 #pragma unroll
-            for (int q = 0; q < 16; ++q) g[q] = tanhf(v[q] + p.b3[sp * kW + c + c16 + q]);
+            for (int q = 0; q < 16; ++q) g[q] = tanh_hw(v[q] + p.b3[sp * kW + c + c16 + q]);
             store8(Gt, r, c + c16, kW, g);
             store8(Gt, r, c + c16 + 8, kW, g + 8);
           }
@@ -515,6 +524,7 @@ __device__ __forceinline__ float2 fadd2(float2 a, float2 b) {
   return d;
 }
 __device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+
 __device__ __forceinline__ float2 bc2(float x) { return make_float2(x, x); }
 
 // gate r^_j . r^_k for the column pair (k, k+1); rj holds row j's components twice
@@ -1296,7 +1306,7 @@ __global__ void __launch_bounds__(kFitThreads, 1) k_fit(FitParams p) {
       for (int c = 0; c < N; c += 32) {
         float v[32];
         tc::tmem_ld32(tb + lane_off + c, v);
-        for (int q = 0; q < 32; ++q) v[q] = (c + q < N) ? tanhf(v[q] + bias[sp * N + c + q]) : 0.f;
+        for (int q = 0; q < 32; ++q) v[q] = (c + q < N) ? tanh_hw(v[q] + bias[sp * N + c + q]) : 0.f;
         for (int q = 0; q < 32 && c + q < N; q += 8) store8(Y, t, c + q, N, v + q);
       }
     };
@@ -1316,7 +1326,7 @@ __global__ void __launch_bounds__(kFitThreads, 1) k_fit(FitParams p) {
         tc::tmem_ld32(tb + lane_off + c, v);
         for (int q = 0; q < 32; ++q) {
           if (c + q >= p.f3) { v[q] = 0.f; continue; }
-          float y = tanhf(v[q] + p.c3[sp * p.f3 + c + q]);
+          float y = tanh_hw(v[q] + p.c3[sp * p.f3 + c + q]);
           float w4 = p.F4[sp * p.f3 + c + q];
           e += (double)y * (double)w4;
           v[q] = w4 * (1.f - y * y);
