@@ -164,6 +164,16 @@ int dp_get_neighbours(dp_ctx* ctx, int32_t* nbr_j, int32_t* nbr_img, int32_t* n_
 /* Atomic energies e_i (n_atoms, host) of the last evaluation. */
 int dp_get_atom_energies(dp_ctx* ctx, double* atom_e);
 
+/* DP group (paper Sec. III: the deep potential covers a selected group of
+ * atoms, the protein, and the rest is left to a classical force field).
+ * mask: n_atoms bytes in host memory, nonzero = member; NULL = every atom
+ * (the default).  With a group, only pairs of members are neighbours and only
+ * members carry energy: the result equals evaluating the members alone in the
+ * same box, and non-members get zero energy and zero force.  The next
+ * evaluation rebuilds the neighbour lists.  DP_ERR_ARG for a NULL ctx,
+ * DP_ERR_UNSUPPORTED for a multi-system (serving) context. */
+int dp_set_group(dp_ctx* ctx, const unsigned char* mask);
+
 /* Enqueue `reps` evaluations of the network alone (no neighbour update, no
  * force assembly) on the context's stream, at the resident neighbour lists,
  * without synchronising; for timing the network kernels with events on that

@@ -173,6 +173,25 @@ def af_compute(model, weights, types, coords, box, nthreads=0):
     return float(E[0]), ae, F, V
 
 
+def af_compute_group(model, weights, types, coords, box, mask, nthreads=0):
+    """The potential over a DP group (paper Sec. III: the deep potential covers
+    a selected atom group): by definition the members evaluated alone in the
+    same box, so only members see each other and carry energy; non-members get
+    zero energy and force.  Returns (E, atomic energies, forces, virial)."""
+    mask = np.asarray(mask, dtype=bool)
+    idx = np.nonzero(mask)[0]
+    n = len(mask)
+    ae = np.zeros(n)
+    F = np.zeros((n, 3))
+    if len(idx) == 0:
+        return 0.0, ae, F, np.zeros((3, 3))
+    E, ae_g, F_g, V = af_compute(model, weights, np.asarray(types)[idx], np.asarray(coords)[idx],
+                                 box, nthreads)
+    ae[idx] = ae_g
+    F[idx] = F_g
+    return E, ae, F, V
+
+
 def af_atoms(model, weights, types, coords, box, centres, nthreads=0, want_desc=False):
     """Per centre: atomic energy, pair gradients g (nmax x 3), neighbour j and image."""
     i, f = _af_dims(model)

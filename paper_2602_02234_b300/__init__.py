@@ -104,6 +104,7 @@ def lib():
         L.dp_set_state.argtypes = [vp, vp, vp, C.c_longlong, i]
         L.dp_get_neighbours.argtypes = [vp, vp, vp, vp]
         L.dp_get_atom_energies.argtypes = [vp, vp]
+        L.dp_set_group.argtypes = [vp, vp]
         L.dp_enqueue_network.argtypes = [vp, i, i]
         L.dp_kernels_per_step.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.dp_device_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
@@ -255,6 +256,18 @@ class DeepPotential:
         cnt = np.zeros(self.n, np.int32)
         self._check(lib().dp_get_neighbours(self._h, j.ctypes.data, img.ctypes.data, cnt.ctypes.data))
         return cnt, j, img
+
+    def set_group(self, mask=None):
+        """DP group: a boolean array over the atoms (None: every atom).  Only
+        pairs of members interact through the potential; non-members get zero
+        energy and force (dp_set_group)."""
+        if mask is None:
+            self._check(lib().dp_set_group(self._h, None))
+            return
+        m = np.ascontiguousarray(np.asarray(mask, dtype=bool), dtype=np.uint8)
+        if m.shape != (self.n,):
+            raise ValueError("mask must have one entry per atom")
+        self._check(lib().dp_set_group(self._h, m.ctypes.data))
 
     def atom_energies(self):
         e = np.zeros(self.n)

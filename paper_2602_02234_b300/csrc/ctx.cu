@@ -51,6 +51,8 @@ struct dp_ctx {
   // device state
   double *x = nullptr, *v = nullptr, *F = nullptr, *xref = nullptr, *w = nullptr;
   double* xin = nullptr;      // staging for uploaded coordinates
+  unsigned char* grp = nullptr;  // DP group (1 = member), used when use_grp
+  bool use_grp = false;
   int* differs = nullptr;     // compare result
   double *minv = nullptr, *mass = nullptr;
   int* fl = nullptr;
@@ -220,6 +222,7 @@ static NlistArgs nlist_args(dp_ctx* c) {
   a.n = c->n; a.ncell = c->ncell; a.cap = c->cap; a.nmax = c->desc.nmax;
   a.rc = c->desc.rcut; a.rskin = c->rskin;
   a.x = c->x; a.xref = c->xref; a.w = c->w; a.fl = c->fl;
+  a.grp = c->use_grp ? c->grp : nullptr;
   a.sys_of = c->sys_of; a.sys = c->sys;
   a.cell_of = c->cell_of; a.cell_cnt = c->cell_cnt; a.cell_fill = c->cell_fill;
   a.cell_start = c->cell_start; a.cell_idx = c->cell_idx;
@@ -266,6 +269,8 @@ static int enqueue_compute(dp_ctx* c, int atom0 = 0) {
   ReduceArgs ra{};
   ra.n_sys = c->n_sys; ra.sys_atom0 = c->sys_atom0; ra.atom_e = c->atom_e; ra.atom_vir = c->atom_vir;
   ra.F = c->F; ra.sys_e = c->sys_e; ra.sys_vir = c->sys_vir; ra.flags = c->flags;
+  ra.atom_e_out = c->atom_e;
+  ra.grp = c->use_grp ? c->grp : nullptr;
   launch_reduce(ra, c->st); ++k;
   return k;
 }
@@ -591,6 +596,25 @@ static int build_step_graph(dp_ctx* c, double dt, int trace_len) {
   c->graph_dt = dt;
   c->graph_trace_len = c->trace_len;
   c->kernels_step = k;
+  return DP_OK;
+}
+
+// DP group (the paper's NNPot atom group): only pairs of members are
+// neighbours and only members carry energy; NULL restores every atom.
+extern "C" int dp_set_group(dp_ctx* c, const unsigned char* mask) {
+  if (!c) return fail(nullptr, DP_ERR_ARG, "ctx is NULL");
+  if (c->n_sys != 1) return fail(c, DP_ERR_UNSUPPORTED, "a DP group needs a single-system context");
+  if (mask) {
+    if (!c->grp) CUDA_TRY(c, dalloc(c, &c->grp, (size_t)c->n_cap), "group");
+    std::vector<unsigned char> g(c->n);
+    for (int i = 0; i < c->n; ++i) g[i] = mask[i] ? 1 : 0;
+    CUDA_TRY(c, cudaMemcpyAsync(c->grp, g.data(), c->n, cudaMemcpyHostToDevice, c->st), "group");
+    CUDA_TRY(c, cudaStreamSynchronize(c->st), "group");
+  }
+  c->use_grp = mask != nullptr;
+  c->forces_valid = false;
+  c->valid_below = 0;
+  c->graph_stale = true;
   return DP_OK;
 }
 

@@ -606,6 +606,13 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
   const uint32_t lo = lane_base();
   atom_setup(p, atom, m);
   const int ngroups = (m->nvalid + 7) >> 3;
+  if (ngroups == 0) {   // no neighbours: R~ = 0, so T = 0 and D = 0 (the fitting still runs)
+    op_t* Drow = p.D + (size_t)atom * kW * p.m2;
+    for (int i = t; i < kW * p.m2; i += kThreads) Drow[i] = f2op(0.f);
+    for (int i = t; i < 4 * kW; i += kThreads) p.Tm[(size_t)atom * 4 * kW + i] = 0.f;
+    __syncthreads();
+    return true;
+  }
   uint8_t* Gdst = p.Gst + (size_t)atom * (p.n_layers + 1) * kTile;
   if (!embed_forward(p, sm, m, tb, mb, wb, xb)) return false;
   if (p.n_layers > 0) load_qkv_weights(p, 0, sm, xb);   // H1, H2 tiles are free again
@@ -800,6 +807,11 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
   // (the second sum for f < m2 only); feature f = row id, the 128-term sum split
   load_G(sm + SM_G, L, gb);   // the last layer's output, for dG_L below
   if (!xb.wait(p.status)) return false;
+  if (ngroups == 0) {   // no neighbours: no pair gradients (no copy was issued on gb)
+    for (int i = t; i < p.nmax * 3; i += kThreads) p.g[(size_t)atom * p.nmax * 3 + i] = 0.f;
+    __syncthreads();
+    return true;
+  }
   {
     const int f = r;
     const float* dDs = reinterpret_cast<const float*>(sm + SM_P);   // 128 x m2 FP32

@@ -22,6 +22,7 @@ struct NlistArgs {
   SkinEntry* skin;
   int* skin_cnt;
   int* mirror;           // n x cap
+  const unsigned char* grp;  // optional DP group: pairs only between members
   int* sel_j;            // n x nmax
   int* sel_img;          // n x nmax x 3
   double* sel_r;         // n x nmax x 3
@@ -58,12 +59,14 @@ void launch_force_gather(const ForceArgs& a, cudaStream_t st);
 struct ReduceArgs {
   int n_sys;
   const int* sys_atom0;  // n_sys + 1 offsets
-  const double* atom_e;  // n
+  const double* atom_e;  // n (unused by the kernel: atom_e_out is read and written)
   const double* atom_vir;// n x 9
   const double* F;       // n x 3 (finiteness check)
   double* sys_e;         // n_sys
   double* sys_vir;       // n_sys x 9
   int* flags;
+  double* atom_e_out;    // with grp: energies of non-members set to 0 here
+  const unsigned char* grp;
 };
 void launch_reduce(const ReduceArgs& a, cudaStream_t st);
 

@@ -75,16 +75,19 @@ void launch_force_gather(const ForceArgs& a, cudaStream_t st) {
 }
 
 // one block per system: E and virial in FP64, fixed summation order
-__global__ void k_reduce(const int* __restrict__ sys_atom0, const double* __restrict__ atom_e,
+// With a DP group, atoms outside it contribute nothing (their energy is set
+// to 0; they have no kept pairs, so no virial or force either).
+__global__ void k_reduce(const int* __restrict__ sys_atom0, double* __restrict__ atom_e,
                          const double* __restrict__ atom_vir, const double* __restrict__ F,
                          double* __restrict__ sys_e, double* __restrict__ sys_vir,
-                         int* __restrict__ flags) {
+                         int* __restrict__ flags, const unsigned char* __restrict__ grp) {
   int s = blockIdx.x;
   int a0 = sys_atom0[s], a1 = sys_atom0[s + 1];
   __shared__ double sh[10][256];
   double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   bool bad = false;
   for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
+    if (grp && !grp[i]) atom_e[i] = 0.0;
     acc[0] += atom_e[i];
     for (int q = 0; q < 9; ++q) acc[1 + q] += atom_vir[9 * i + q];
     for (int q = 0; q < 3; ++q) bad |= !isfinite(F[3 * i + q]);
@@ -105,8 +108,8 @@ __global__ void k_reduce(const int* __restrict__ sys_atom0, const double* __rest
 }
 
 void launch_reduce(const ReduceArgs& a, cudaStream_t st) {
-  k_reduce<<<a.n_sys, 256, 0, st>>>(a.sys_atom0, a.atom_e, a.atom_vir, a.F, a.sys_e, a.sys_vir,
-                                    a.flags);
+  k_reduce<<<a.n_sys, 256, 0, st>>>(a.sys_atom0, a.atom_e_out, a.atom_vir, a.F, a.sys_e,
+                                    a.sys_vir, a.flags, a.grp);
 }
 
 // v += dt/2 F/m; x += dt v; request a neighbour rebuild when an atom moved

@@ -14,7 +14,7 @@ import pytest
 
 import oracle
 import paper_2602_02234_b300 as dp
-from synth import configs as C, maxwell_boltzmann, normal_blob, serving_system, water_box
+from synth import configs as C, maxwell_boltzmann, normal_blob, protein_in_water, serving_system, water_box
 
 pytestmark = pytest.mark.gpu
 
@@ -299,3 +299,33 @@ def test_fused_md_tracks_plain():
     assert dx < 1e-4                      # 10 fs of dynamics with ~1 % force noise
     et = out[dp.PREC_FUSED][1].sum(1)
     assert np.all(np.isfinite(et)) and np.max(np.abs(et - et[0])) < 1e-3 * abs(et[0])
+
+
+# ------------------------------------------------------------------ DP group
+@pytest.mark.parametrize("prec", [dp.PREC_PLAIN_F32, dp.PREC_FUSED])
+def test_dp_group_equals_the_members_alone(prec):
+    """The protein-only deep potential of the paper (Sec. III): the 300-atom
+    blob of a 3,000-atom protein-in-water box as the group."""
+    m = C.ATTN_MODEL
+    s = protein_in_water(3000, 300, (31.07, 31.07, 31.07), 11)
+    mask = np.zeros(s.n, bool)
+    mask[: s.blob_atoms] = True
+    pot, w = make(m, s, prec)
+    pot.set_group(mask)
+    E, F, V = pot.compute(s.coords)
+    Eo, aeo, Fo, Vo = oracle.af_compute_group(m, w, s.types, s.coords, s.box, mask)
+    assert abs(E - Eo) <= TOL_E[prec] * abs(Eo)
+    assert np.max(np.abs(F[mask] - Fo[mask])) <= TOL_F[prec] * frms(Fo[mask])
+    assert np.max(np.abs(V - Vo)) <= TOL_F[prec] * np.linalg.norm(Vo)
+    assert np.all(F[~mask] == 0) and np.all(pot.atom_energies()[~mask] == 0)
+    # non-members are invisible: moving them changes nothing, bit for bit
+    x2 = s.coords.copy()
+    x2[~mask] += np.random.default_rng(2).normal(0, 0.3, (int((~mask).sum()), 3))
+    E2, F2, _ = pot.compute(x2)
+    assert E2 == E and np.array_equal(F2, F)
+    # back to every atom
+    pot.set_group(None)
+    E3, F3, _ = pot.compute(s.coords)
+    ref, _ = make(m, s, prec, w=w)
+    E4, F4, _ = ref.compute(s.coords)
+    assert E3 == E4 and np.array_equal(F3, F4)

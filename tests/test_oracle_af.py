@@ -349,3 +349,53 @@ def test_nve_second_order_and_reversible():
     x2, v2, _, _ = oracle.af_md(m, w, s.types, masses, x1, -v1, s.box, 20, 0.5)
     assert np.max(np.abs(x2 - s.coords)) < 1e-9
     assert np.max(np.abs(v2 + v0)) < 1e-11
+
+
+# ---------------------------------------------------------------- DP group
+def test_group_equals_full_model_when_the_rest_is_beyond_the_cutoff():
+    """Members in one corner of a large box, non-members more than rc away:
+    the full model's energies and forces on the members (its own neighbour
+    search over every atom) must equal the group evaluation, and the group
+    evaluation of every atom must equal the full model."""
+    m = TINY
+    w = blob(m, seed=13)
+    a = small_water(6, 8.0, 4)
+    b = small_water(6, 8.0, 9)
+    box = np.full(3, 40.0)
+    xa = a.coords % 8.0 + 1.0                   # members inside [1, 9]^3
+    xb = b.coords % 8.0 + 22.0                  # others inside [22, 30]^3: > 6 A away
+    x = np.concatenate([xa, xb])
+    t = np.concatenate([a.types, b.types]).astype(np.int32)
+    mask = np.arange(len(t)) < len(xa)
+    E, ae, F, V = oracle.af_compute(m, w, t, x, box)
+    Eg, aeg, Fg, Vg = oracle.af_compute_group(m, w, t, x, box, mask)
+    assert np.allclose(aeg[mask], ae[mask], rtol=0, atol=1e-13)
+    assert np.allclose(Fg[mask], F[mask], rtol=0, atol=1e-13)
+    assert np.all(aeg[~mask] == 0) and np.all(Fg[~mask] == 0)
+    assert Eg == pytest.approx(ae[mask].sum(), rel=1e-13)
+    E2, ae2, F2, V2 = oracle.af_compute_group(m, w, t, x, box, np.ones(len(t), bool))
+    assert E2 == E and np.array_equal(F2, F) and np.array_equal(V2, V)
+
+
+def test_group_forces_are_central_differences_of_the_group_energy():
+    """Non-members sit among the members (mixed in one box): the group energy
+    must not see them, and its forces must be its own gradient."""
+    m = TINY
+    w = blob(m, seed=17)
+    s = small_water(10, 9.5, 6)
+    mask = np.zeros(s.n, bool)
+    mask[: 3 * 6] = True                       # the first six molecules
+    E, ae, F, V = oracle.af_compute_group(m, w, s.types, s.coords, s.box, mask)
+    h = 1e-4
+    for i in (0, 4, 13):
+        for k in range(3):
+            xp = s.coords.copy(); xp[i, k] += h
+            xm = s.coords.copy(); xm[i, k] -= h
+            fd = -(oracle.af_compute_group(m, w, s.types, xp, s.box, mask)[0]
+                   - oracle.af_compute_group(m, w, s.types, xm, s.box, mask)[0]) / (2 * h)
+            assert abs(fd - F[i, k]) < 1e-7 * np.sqrt(np.mean(F[mask] ** 2)) + 1e-10
+    # moving a non-member changes nothing
+    x2 = s.coords.copy()
+    x2[~mask] += 0.37
+    E2 = oracle.af_compute_group(m, w, s.types, x2, s.box, mask)[0]
+    assert E2 == E
