@@ -60,10 +60,13 @@ __device__ __forceinline__ double sep_exact(const double* wi, const double* wj, 
   return __dadd_rn(__dadd_rn(__dmul_rn(r[0], r[0]), __dmul_rn(r[1], r[1])), __dmul_rn(r[2], r[2]));
 }
 
-// Neighbour order: (d2, j, n) lexicographic.
+// Neighbour order: (d2, j, n) lexicographic.  d2 >= 0 is never NaN, and the
+// bit patterns of non-negative doubles order like their values, so d2 is
+// compared as a 64-bit integer (integer pipe, not the FP64 one).
 __device__ __forceinline__ bool key_less(double da, int ja, const int* na, double db, int jb,
                                          const int* nb) {
-  if (da != db) return da < db;
+  const long long ia = __double_as_longlong(da), ib = __double_as_longlong(db);
+  if (ia != ib) return ia < ib;
   if (ja != jb) return ja < jb;
   for (int a = 0; a < 3; ++a)
     if (na[a] != nb[a]) return na[a] < nb[a];
