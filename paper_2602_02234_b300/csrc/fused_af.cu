@@ -205,8 +205,11 @@ __device__ __forceinline__ void store32(uint8_t* tile, int r, int c, int Kx, int
 }
 
 // tanh by the hardware approximation (one instruction, relative error about
-// 2^-11): every tanh output of the fused path is rounded to a 16-bit operand
-// tile, whose rounding is of the same size.
+// 2^-11), for the embedding layers whose outputs only ever serve as 16-bit
+// operands (rounded to the same size anyway).  G0, which also enters the FP32
+// residual stream, and the fitting layers, which give the energy, use tanhf:
+// their forward values must stay consistent with the 1 - y^2 the backward
+// uses, or the forces stop being the gradient of the energy (NVE drift).
 __device__ __forceinline__ float tanh_hw(float x) {
   float y;
   asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -447,7 +450,7 @@ __device__ bool embed_forward(const Params& p, uint8_t* sm, Misc* m, uint32_t tb
           tc::tmem_ld16x2(tb + lo + R1 + c + c16, v, tb + lo + R2 + c + c16, g);
           if (mine) {
 #pragma unroll
-            for (int q = 0; q < 16; ++q) g[q] = tanh_hw(v[q] + p.b3[sp * kW + c + c16 + q]);
+            for (int q = 0; q < 16; ++q) g[q] = tanhf(v[q] + p.b3[sp * kW + c + c16 + q]);   // G0 enters the FP32 residual stream
             store8(Gt, r, c + c16, kW, g);
             store8(Gt, r, c + c16 + 8, kW, g + 8);
           }
@@ -1318,7 +1321,7 @@ __global__ void __launch_bounds__(kFitThreads, 1) k_fit(FitParams p) {
       for (int c = 0; c < N; c += 32) {
         float v[32];
         tc::tmem_ld32(tb + lane_off + c, v);
-        for (int q = 0; q < 32; ++q) v[q] = (c + q < N) ? tanh_hw(v[q] + bias[sp * N + c + q]) : 0.f;
+        for (int q = 0; q < 32; ++q) v[q] = (c + q < N) ? tanhf(v[q] + bias[sp * N + c + q]) : 0.f;
         for (int q = 0; q < 32 && c + q < N; q += 8) store8(Y, t, c + q, N, v + q);
       }
     };
@@ -1338,7 +1341,7 @@ __global__ void __launch_bounds__(kFitThreads, 1) k_fit(FitParams p) {
         tc::tmem_ld32(tb + lane_off + c, v);
         for (int q = 0; q < 32; ++q) {
           if (c + q >= p.f3) { v[q] = 0.f; continue; }
-          float y = tanh_hw(v[q] + p.c3[sp * p.f3 + c + q]);
+          float y = tanhf(v[q] + p.c3[sp * p.f3 + c + q]);
           float w4 = p.F4[sp * p.f3 + c + q];
           e += (double)y * (double)w4;
           v[q] = w4 * (1.f - y * y);
