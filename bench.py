@@ -500,6 +500,17 @@ def report_config(which):
         pot.step(3, CF.DT_FS)
         ms = _timed_steps(pot, 20, stream)
         Ego, _, Fgo, _ = oracle.af_compute_group(m, w, s.types, s.coords, s.box, mask)
+        # four fitting heads on the shared descriptor (energies of all four per step)
+        from dataclasses import replace as _replace
+        m4 = _replace(m, fit_heads=4)
+        w4 = normal_blob(oracle.af_weight_count(m4), CF.WEIGHT_SEED)
+        pot4 = dp.DeepPotential(dp.model_desc(m4, dp.PREC_FUSED, skin=CF.SKIN, rebuild_every=CF.REBUILD_EVERY),
+                                s.types, s.box, w4, masses=masses, stream=stream)
+        pot4.set_state(s.coords, v0, 0)
+        pot4.step(3, CF.DT_FS)
+        out["fit_heads_4_fused"] = {"ms_per_step": _timed_steps(pot4, 20, stream),
+                                    "head_energies": [float(x) for x in pot4.head_energies()]}
+        pot4.close()
         out["dp_group_protein_fused"] = {
             "members": int(mask.sum()), "ms_per_step": ms,
             "member_atom_steps_per_s": int(mask.sum()) / (ms / 1e3),

@@ -100,7 +100,13 @@ typedef struct dp_model_desc {
    * moved more than skin/2 since the last build. 0 selects 1 A / 10 steps.   */
   double skin;
   int rebuild_every;
-  int reserved[7];
+  /* attention family: fitting heads sharing one descriptor (the paper's
+   * multi-task large atomic models, Sec. II: one branch per training set).
+   * 0 or 1 = one head.  Head 0 gives dp_compute's energy, the forces, the
+   * virial and the MD; every head's energy comes from dp_get_head_energies.
+   * The weight blob holds the fitting nets of head 0, 1, ... in order.     */
+  int fit_heads;
+  int reserved[6];
 } dp_model_desc;
 
 typedef struct dp_ctx dp_ctx;
@@ -163,6 +169,12 @@ int dp_get_neighbours(dp_ctx* ctx, int32_t* nbr_j, int32_t* nbr_img, int32_t* n_
 
 /* Atomic energies e_i (n_atoms, host) of the last evaluation. */
 int dp_get_atom_energies(dp_ctx* ctx, double* atom_e);
+
+/* Energies of every fitting head at the last evaluation: out[s * k + h] for
+ * system s and head h (k = fit_heads; s = 0 for a single-system context), in
+ * host memory, FP64.  Head 0 equals dp_compute's energy.  DP_ERR_ARG for NULL
+ * pointers or before the first evaluation. */
+int dp_get_head_energies(dp_ctx* ctx, double* out);
 
 /* DP group (paper Sec. III: the deep potential covers a selected group of
  * atoms, the protein, and the rest is left to a classical force field).

@@ -99,11 +99,48 @@ AF_KINDS = {"eW1": 0, "eb1": 1, "eW2": 2, "eb2": 3, "eW3": 4, "eb3": 5,
 
 
 def af_weight_count(model) -> int:
+    """Blob length; with k fitting heads the fitting nets of heads 1..k-1
+    follow head 0's, in the same layout."""
     i, f = _af_dims(model)
     n = lib().oracle_af_weight_count(_p(i, _I), _p(f, _D))
     if n < 0:
         raise ValueError("invalid attention-family model")
-    return int(n)
+    d = model if isinstance(model, dict) else model.as_dict()
+    return int(n) + (max(1, d.get("fit_heads", 1)) - 1) * _af_fit_len(d)
+
+
+def _af_fit_len(d):
+    return d["n_species"] * (d["m1"] * d["m2"] * d["f1"] + d["f1"] + d["f1"] * d["f2"] + d["f2"]
+                             + d["f2"] * d["f3"] + d["f3"] + d["f3"] + 1)
+
+
+def af_head_blob(model, weights, h):
+    """The single-head model of fitting head h: the shared embedding and
+    attention weights followed by head h's fitting nets."""
+    d = dict(model if isinstance(model, dict) else model.as_dict())
+    d["fit_heads"] = 1
+    n1 = af_weight_count(d)
+    fl = _af_fit_len(d)
+    w = np.asarray(weights, dtype=np.float64)
+    shared = n1 - fl
+    return np.concatenate([w[:shared], w[shared + h * fl: shared + (h + 1) * fl]]), d
+
+
+def af_compute_heads(model, weights, types, coords, box, nthreads=0):
+    """Multi-head fitting on one shared descriptor (paper Sec. II: a large
+    atomic model with one fitting branch per training set), by definition: head
+    h is the single-head model with head h's fitting nets.  Returns the energies
+    of all heads and (E, atomic energies, forces, virial) of head 0."""
+    d = model if isinstance(model, dict) else model.as_dict()
+    k = max(1, d.get("fit_heads", 1))
+    energies, head0 = [], None
+    for h in range(k):
+        wh, dh = af_head_blob(model, weights, h)
+        r = af_compute(dh, wh, types, coords, box, nthreads)
+        energies.append(r[0])
+        if h == 0:
+            head0 = r
+    return np.array(energies), head0
 
 
 def af_weight_slice(model, kind: str, a: int) -> slice:

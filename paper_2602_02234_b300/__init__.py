@@ -53,7 +53,7 @@ class ModelDesc(C.Structure):
                 ("angle_nmax", C.c_int), ("angle_rcut", C.c_double),
                 ("angle_rcut_smth", C.c_double), ("f1", C.c_int), ("f2", C.c_int),
                 ("f3", C.c_int), ("skin", C.c_double), ("rebuild_every", C.c_int),
-                ("reserved", C.c_int * 7)]
+                ("fit_heads", C.c_int), ("reserved", C.c_int * 6)]
 
 
 def model_desc(model, precision: int, skin: float = 1.0, rebuild_every: int = 10) -> ModelDesc:
@@ -81,6 +81,7 @@ def model_desc(model, precision: int, skin: float = 1.0, rebuild_every: int = 10
         m.family = FAMILY_ATTENTION
         m.e1, m.e2, m.m1, m.m2 = d["e1"], d["e2"], d["m1"], d["m2"]
         m.n_layers, m.hidden, m.heads = d["n_layers"], d["hidden"], d["heads"]
+        m.fit_heads = d.get("fit_heads", 1)
     return m
 
 
@@ -105,6 +106,7 @@ def lib():
         L.dp_get_neighbours.argtypes = [vp, vp, vp, vp]
         L.dp_get_atom_energies.argtypes = [vp, vp]
         L.dp_set_group.argtypes = [vp, vp]
+        L.dp_get_head_energies.argtypes = [vp, vp]
         L.dp_enqueue_network.argtypes = [vp, i, i]
         L.dp_kernels_per_step.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.dp_device_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
@@ -256,6 +258,14 @@ class DeepPotential:
         cnt = np.zeros(self.n, np.int32)
         self._check(lib().dp_get_neighbours(self._h, j.ctypes.data, img.ctypes.data, cnt.ctypes.data))
         return cnt, j, img
+
+    def head_energies(self):
+        """Energy of every fitting head at the last evaluation (head 0 first;
+        dp_get_head_energies)."""
+        k = max(1, self.desc.fit_heads) if self.desc.family == FAMILY_ATTENTION else 1
+        e = np.zeros(k)
+        self._check(lib().dp_get_head_energies(self._h, e.ctypes.data))
+        return e
 
     def set_group(self, mask=None):
         """DP group: a boolean array over the atoms (None: every atom).  Only

@@ -51,6 +51,7 @@ struct dp_ctx {
   // device state
   double *x = nullptr, *v = nullptr, *F = nullptr, *xref = nullptr, *w = nullptr;
   double* xin = nullptr;      // staging for uploaded coordinates
+  double* head_sys_e = nullptr;  // energies of fitting heads 1.. per system: [sys][head - 1]
   unsigned char* grp = nullptr;  // DP group (1 = member), used when use_grp
   bool use_grp = false;
   int* differs = nullptr;     // compare result
@@ -152,6 +153,8 @@ static int check_desc(const dp_model_desc* d, std::string* why) {
     if (!(d->angle_rcut_smth >= 0) || !(d->angle_rcut_smth < d->angle_rcut) || d->angle_rcut > d->rcut) { *why = "need 0 <= angle_rcut_smth < angle_rcut <= rcut"; return -1; }
   }
   if (d->precision < DP_PREC_PLAIN_F64 || d->precision > DP_PREC_FUSED) { *why = "unknown precision"; return -1; }
+  if (d->fit_heads < 0 || d->fit_heads > 16) { *why = "fit_heads must be 0..16"; return -1; }
+  if (d->fit_heads > 1 && d->family != DP_FAMILY_ATTENTION) { *why = "fitting heads are an attention-family option"; return -1; }
   return 0;
 }
 
@@ -171,7 +174,8 @@ extern "C" int dp_weight_count(const dp_model_desc* d, size_t* n) {
   size_t S = d->n_species, E1 = d->e1, E2 = d->e2, M1 = d->m1, M2 = d->m2, H = d->hidden;
   size_t t = S * (E1 + E1 + E1 * E2 + E2 + E2 * M1 + M1);
   t += (size_t)d->n_layers * (3 * M1 * H + H * M1 + M1);
-  t += S * (M1 * M2 * d->f1 + d->f1 + (size_t)d->f1 * d->f2 + d->f2 + (size_t)d->f2 * d->f3 + d->f3 + d->f3 + 1);
+  const size_t heads = d->fit_heads > 1 ? d->fit_heads : 1;
+  t += heads * S * (M1 * M2 * d->f1 + d->f1 + (size_t)d->f1 * d->f2 + d->f2 + (size_t)d->f2 * d->f3 + d->f3 + d->f3 + 1);
   *n = t;
   return DP_OK;
 }
@@ -266,6 +270,12 @@ static int enqueue_compute(dp_ctx* c, int atom0 = 0) {
   fa.g64 = c->model->grad64();
   launch_force_gather(fa, c->st); ++k;
   if (atom0 > 0) return k;
+  if (c->head_sys_e && c->model->head_energies()) {
+    launch_head_reduce(c->n_sys, c->af.fit_heads - 1, c->n_cap, c->sys_atom0,
+                       c->model->head_energies(), c->use_grp ? c->grp : nullptr, c->head_sys_e,
+                       c->st);
+    ++k;
+  }
   ReduceArgs ra{};
   ra.n_sys = c->n_sys; ra.sys_atom0 = c->sys_atom0; ra.atom_e = c->atom_e; ra.atom_vir = c->atom_vir;
   ra.F = c->F; ra.sys_e = c->sys_e; ra.sys_vir = c->sys_vir; ra.flags = c->flags;
@@ -350,7 +360,7 @@ static int check_model(const dp_model_desc* desc, const double* weights, size_t 
       if (!(masses[t] > 0)) return fail(nullptr, DP_ERR_ARG, "masses must be positive");
   *afd = AfDims{desc->n_species, desc->e1, desc->e2, desc->m1, desc->m2, desc->n_layers,
                 desc->hidden, desc->heads, desc->f1, desc->f2, desc->f3, desc->nmax,
-                desc->rcut, desc->rcut_smth};
+                desc->rcut, desc->rcut_smth, desc->fit_heads > 1 ? desc->fit_heads : 1};
   if (desc->family == DP_FAMILY_ATTENTION && desc->precision == DP_PREC_FUSED &&
       !fused_af_supported(*afd, &why))
     return fail(nullptr, DP_ERR_UNSUPPORTED, why);
@@ -422,6 +432,7 @@ static int ctx_create(dp_ctx** out, const dp_model_desc* desc, const double* mas
   TRY(dalloc(c, &c->atom_e, N), "energies");
   TRY(dalloc(c, &c->atom_vir, 9 * N), "virials");
   TRY(dalloc(c, &c->sys_e, S), "energies");
+  if (c->af.fit_heads > 1) TRY(dalloc(c, &c->head_sys_e, S * (c->af.fit_heads - 1)), "energies");
   TRY(dalloc(c, &c->sys_vir, 9 * S), "virials");
   TRY(dalloc(c, &c->flags, 1), "flags");
   TRY(dalloc(c, &c->step, 2), "step");
@@ -596,6 +607,23 @@ static int build_step_graph(dp_ctx* c, double dt, int trace_len) {
   c->graph_dt = dt;
   c->graph_trace_len = c->trace_len;
   c->kernels_step = k;
+  return DP_OK;
+}
+
+extern "C" int dp_get_head_energies(dp_ctx* c, double* out) {
+  if (!c) return fail(nullptr, DP_ERR_ARG, "ctx is NULL");
+  if (!out) return fail(c, DP_ERR_ARG, "out is NULL");
+  if (!c->forces_valid) return fail(c, DP_ERR_ARG, "no evaluation at the resident positions yet");
+  const int k = c->desc.family == DP_FAMILY_GRAPH ? 1 : std::max(1, c->af.fit_heads);
+  std::vector<double> e0(c->n_sys), eh((size_t)c->n_sys * (k > 1 ? k - 1 : 0));
+  CUDA_TRY(c, cudaMemcpyAsync(e0.data(), c->sys_e, sizeof(double) * c->n_sys, cudaMemcpyDeviceToHost, c->st), "energies");
+  if (k > 1)
+    CUDA_TRY(c, cudaMemcpyAsync(eh.data(), c->head_sys_e, sizeof(double) * eh.size(), cudaMemcpyDeviceToHost, c->st), "energies");
+  CUDA_TRY(c, cudaStreamSynchronize(c->st), "synchronize");
+  for (int s = 0; s < c->n_sys; ++s) {
+    out[(size_t)s * k] = e0[s];
+    for (int h = 1; h < k; ++h) out[(size_t)s * k + h] = eh[(size_t)s * (k - 1) + h - 1];
+  }
   return DP_OK;
 }
 

@@ -1251,6 +1251,7 @@ struct FitParams {
   double* atom_e;
   float* dD;              // [n][kd]
   int* status;
+  int grad;               // 1: also dE/dD (the head that drives the forces); 0: energy only
 };
 
 constexpr int FT_Y1 = 0;
@@ -1350,6 +1351,7 @@ __global__ void __launch_bounds__(kFitThreads, 1) k_fit(FitParams p) {
       }
       if (atom >= 0) p.atom_e[atom] = e + (double)p.c4[sp];
     }
+    if (!p.grad) continue;
     // backward: delta2 = (delta3 F3^T) (1 - y2^2), delta1 = (delta2 F2^T) (1 - y1^2)
     auto epi_dtanh = [&](int N, uint8_t* Y) {
       for (int c = 0; c < N; c += 32) {
@@ -1462,6 +1464,13 @@ class FusedAf : public Model {
       f.atom_e = atom_e;
       k_fit<<<std::min(fit_.n_tiles, sms_), kFitThreads, kSmemFit, st>>>(f);
       ++k;
+      for (size_t h = 0; h < heads_fit_.size(); ++h) {   // further heads: energies only
+        FitParams fh = heads_fit_[h];
+        fh.n_tiles = fit_.n_tiles;
+        fh.atom_e = head_e_ + h * (size_t)cap_;
+        k_fit<<<std::min(fit_.n_tiles, sms_), kFitThreads, kSmemFit, st>>>(fh);
+        ++k;
+      }
     }
     if (parts & 4) {
       k_af_bwd<<<grid, kThreads, kSmemAtom, st>>>(p);
@@ -1470,6 +1479,7 @@ class FusedAf : public Model {
     return k;
   }
   const float* grad32() const override { return g_; }
+  const double* head_energies() const override { return head_e_; }
   size_t bytes() const override { return bytes_; }
   // atoms grouped by species for the fitting kernel, tiles of <= 128 of one species
   bool set_atoms(int n, const int* types) override {
@@ -1526,6 +1536,8 @@ class FusedAf : public Model {
   int n_ = 0, grid_ = 0, sms_ = 0, cap_ = 0;
   int4* dtiles_ = nullptr;
   int* dorder_ = nullptr;
+  std::vector<FitParams> heads_fit_;   // fitting heads 1.. (energy only)
+  double* head_e_ = nullptr;           // their atomic energies, [head - 1][cap_]
   Params base_{};
   FitParams fit_{};
   float* g_ = nullptr;
@@ -1617,6 +1629,30 @@ bool FusedAf::init(const AfDims& m, const double* w, int n_atoms, const int* typ
     }
     c4.push_back((float)at(oc4[t]));
   }
+  // further fitting heads (same layout, one block after another): forward only
+  const int HF = m.fit_heads > 1 ? m.fit_heads : 1;
+  const size_t fit_len = off - oF1[0];
+  struct HeadTiles {
+    std::vector<uint16_t> F1T, F2T, F3T;
+    std::vector<float> c1, c2, c3, F4, c4;
+  };
+  std::vector<HeadTiles> extra(HF - 1);
+  for (int h = 1; h < HF; ++h) {
+    HeadTiles& X = extra[h - 1];
+    const size_t sh = (size_t)h * fit_len;
+    for (int t = 0; t < S; ++t) {
+      pack(X.F1T, m.f1, KD, kc1, [&](int r, int k) { return at(sh + oF1[t] + (size_t)k * m.f1 + r); });
+      pack(X.F2T, m.f2, m.f1, kc2, [&](int r, int k) { return at(sh + oF2[t] + (size_t)k * m.f2 + r); });
+      pack(X.F3T, m.f3, m.f2, kc2, [&](int r, int k) { return at(sh + oF3[t] + (size_t)k * m.f3 + r); });
+      for (int k = 0; k < m.f1; ++k) X.c1.push_back((float)at(sh + oc1[t] + k));
+      for (int k = 0; k < m.f2; ++k) X.c2.push_back((float)at(sh + oc2[t] + k));
+      for (int k = 0; k < m.f3; ++k) {
+        X.c3.push_back((float)at(sh + oc3[t] + k));
+        X.F4.push_back((float)at(sh + oF4[t] + k));
+      }
+      X.c4.push_back((float)at(sh + oc4[t]));
+    }
+  }
   Params& p = base_;
   p.n = n_atoms; p.nmax = m.nmax; p.e1 = E1; p.e2 = E2; p.m2 = m.m2; p.n_layers = L;
   p.heads = m.heads; p.dh = H / m.heads;
@@ -1673,6 +1709,23 @@ bool FusedAf::init(const AfDims& m, const double* w, int n_atoms, const int* typ
   f.c1 = dc1; f.c2 = dc2; f.c3 = dc3; f.F4 = dF4; f.c4 = dc4;
   f.dD = ddD;
   f.status = p.status;
+  f.grad = 1;
+  for (int h = 1; h < HF; ++h) {
+    HeadTiles& X = extra[h - 1];
+    FitParams fh = f;
+    uint16_t *e1, *e2, *e3;
+    float *v1, *v2, *v3, *v4, *v5;
+    if (!(upload(&e1, X.F1T, err) && upload(&e2, X.F2T, err) && upload(&e3, X.F3T, err) &&
+          upload(&v1, X.c1, err) && upload(&v2, X.c2, err) && upload(&v3, X.c3, err) &&
+          upload(&v4, X.F4, err) && upload(&v5, X.c4, err)))
+      return false;
+    fh.F1T = (const uint8_t*)e1; fh.F2T = (const uint8_t*)e2; fh.F3T = (const uint8_t*)e3;
+    fh.F3R = fh.F2R = fh.F1R = nullptr;
+    fh.c1 = v1; fh.c2 = v2; fh.c3 = v3; fh.F4 = v4; fh.c4 = v5;
+    fh.grad = 0;
+    heads_fit_.push_back(fh);
+  }
+  if (HF > 1 && !dalloc(&head_e_, (size_t)(HF - 1) * n_atoms, err)) return false;
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms_, cudaDevAttrMultiProcessorCount, dev);

@@ -99,6 +99,11 @@ void launch_record(const MdArgs& a, const double* sys_e, double* trace, int trac
 struct AfDims {
   int n_species, e1, e2, m1, m2, n_layers, hidden, heads, f1, f2, f3, nmax;
   double rc, rs;
+  int fit_heads;         // fitting heads sharing the descriptor (>= 1)
 };
+// per (system, extra head) sums of atomic energies: head_e is [heads][n],
+// out[s * heads + h]; members of a DP group only (grp optional)
+void launch_head_reduce(int n_sys, int heads, int n, const int* sys_atom0, const double* head_e,
+                        const unsigned char* grp, double* out, cudaStream_t st);
 
 }  // namespace dp

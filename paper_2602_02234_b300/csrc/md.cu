@@ -202,4 +202,29 @@ void launch_compare(long long count, const double* a, const double* b, int* diff
   if (blocks > 0) k_compare<<<(int)blocks, 256, 0, st>>>(count, a, b, differs);
 }
 
+// one block per (system, extra fitting head), fixed summation order
+__global__ void k_head_reduce(int heads, int n, const int* __restrict__ sys_atom0,
+                              const double* __restrict__ head_e, const unsigned char* __restrict__ grp,
+                              double* __restrict__ out) {
+  const int s = blockIdx.x, h = blockIdx.y;
+  const int a0 = sys_atom0[s], a1 = sys_atom0[s + 1];
+  __shared__ double sh[256];
+  double acc = 0.0;
+  for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x)
+    if (!grp || grp[i]) acc += head_e[(size_t)h * n + i];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[(size_t)s * heads + h] = sh[0];
+}
+
+void launch_head_reduce(int n_sys, int heads, int n, const int* sys_atom0, const double* head_e,
+                        const unsigned char* grp, double* out, cudaStream_t st) {
+  if (n_sys > 0 && heads > 0)
+    k_head_reduce<<<dim3(n_sys, heads), 256, 0, st>>>(heads, n, sys_atom0, head_e, grp, out);
+}
+
 }  // namespace dp

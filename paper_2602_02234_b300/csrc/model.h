@@ -44,6 +44,9 @@ class Model {
     (void)atom0;
     return run(nv, types, atom_e, st);
   }
+  // Atomic energies of fitting heads 1.. (FP64, [head - 1][capacity]; null
+  // for a single head).
+  virtual const double* head_energies() const { return nullptr; }
   // Pair gradients (n_atoms x nmax x 3): exactly one of the two is non-null.
   virtual const float* grad32() const { return nullptr; }
   virtual const double* grad64() const { return nullptr; }

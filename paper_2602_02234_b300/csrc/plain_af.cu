@@ -239,6 +239,22 @@ __global__ void k_fit_out(int na, int f3, int atom0, const int* __restrict__ typ
   if (lane == 0) atom_e[atom0 + a] = acc + (double)c4[t];
 }
 
+// energy only (further fitting heads): e_i = y3 . F4 + c4 in FP64
+template <typename T>
+__global__ void k_fit_energy(int na, int f3, int atom0, const int* __restrict__ types,
+                             const T* __restrict__ y3, const T* __restrict__ F4,
+                             const T* __restrict__ c4, double* __restrict__ atom_e) {
+  long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (wid >= na) return;
+  int a = (int)wid;
+  int t = types[atom0 + a];
+  double acc = 0.0;
+  for (int b = lane; b < f3; b += 32) acc += (double)y3[(long long)a * f3 + b] * (double)F4[t * f3 + b];
+  acc = warp_sum(acc);
+  if (lane == 0) atom_e[atom0 + a] = acc + (double)c4[t];
+}
+
 // =========================================================================
 // backward kernels
 // =========================================================================
@@ -503,8 +519,9 @@ struct PlainAf {
   // weights
   T *eW1, *eb1, *eW2, *eb2, *eW3, *eb3;  // species stacked
   std::vector<T*> Wqkv, Wo, bo;           // per layer; Wqkv is [m1][3H]
-  std::vector<T*> F1, c1, F2, c2, F3, c3; // per species
-  T *F4, *c4;                             // species stacked [S][f3], [S]
+  std::vector<T*> F1, c1, F2, c2, F3, c3; // per head and species: [h * S + t]
+  std::vector<T*> F4, c4;                 // per head, species stacked [S][f3], [S]
+  double* head_e = nullptr;               // heads 1..: atomic energies [h - 1][n_atoms]
   // per-chunk activations
   T *d, *sw, *dsw, *s, *Rt, *rh;
   int* tj;
@@ -594,19 +611,25 @@ static void* create_impl(const AfDims& m, const double* w, int n_atoms, const in
     CK(upload(P, &P->Wo[l], take((size_t)H * M1)));
     CK(upload(P, &P->bo[l], take(M1)));
   }
-  P->F1.resize(S); P->c1.resize(S); P->F2.resize(S); P->c2.resize(S); P->F3.resize(S); P->c3.resize(S);
-  std::vector<double> F4, c4;
-  for (int t = 0; t < S; ++t) {
-    CK(upload(P, &P->F1[t], take((size_t)M1 * M2 * m.f1)));
-    CK(upload(P, &P->c1[t], take(m.f1)));
-    CK(upload(P, &P->F2[t], take((size_t)m.f1 * m.f2)));
-    CK(upload(P, &P->c2[t], take(m.f2)));
-    CK(upload(P, &P->F3[t], take((size_t)m.f2 * m.f3)));
-    CK(upload(P, &P->c3[t], take(m.f3)));
-    auto a = take(m.f3); F4.insert(F4.end(), a.begin(), a.end());
-    a = take(1); c4.insert(c4.end(), a.begin(), a.end());
+  const int HF = m.fit_heads > 1 ? m.fit_heads : 1;
+  P->F1.resize(HF * S); P->c1.resize(HF * S); P->F2.resize(HF * S); P->c2.resize(HF * S);
+  P->F3.resize(HF * S); P->c3.resize(HF * S); P->F4.resize(HF); P->c4.resize(HF);
+  for (int h = 0; h < HF; ++h) {      // fitting nets of head 0, 1, ... in blob order
+    std::vector<double> F4, c4;
+    for (int t = 0; t < S; ++t) {
+      const int q = h * S + t;
+      CK(upload(P, &P->F1[q], take((size_t)M1 * M2 * m.f1)));
+      CK(upload(P, &P->c1[q], take(m.f1)));
+      CK(upload(P, &P->F2[q], take((size_t)m.f1 * m.f2)));
+      CK(upload(P, &P->c2[q], take(m.f2)));
+      CK(upload(P, &P->F3[q], take((size_t)m.f2 * m.f3)));
+      CK(upload(P, &P->c3[q], take(m.f3)));
+      auto a = take(m.f3); F4.insert(F4.end(), a.begin(), a.end());
+      a = take(1); c4.insert(c4.end(), a.begin(), a.end());
+    }
+    CK(upload(P, &P->F4[h], F4)); CK(upload(P, &P->c4[h], c4));
   }
-  CK(upload(P, &P->F4, F4)); CK(upload(P, &P->c4, c4));
+  if (HF > 1) CK(P->alloc(&P->head_e, (size_t)(HF - 1) * n_atoms));
 
   // ---- chunk size from the activation footprint per atom
   size_t per_atom = sizeof(T) * ((size_t)NM * (4 + 4 + 3 + E1 + E2) + (size_t)(L + 1) * NM * M1 +
@@ -738,7 +761,7 @@ static int run_impl(PlainAf<T>* P, const int* sel_j, const double* sel_r, const 
       launches += 3;
     }
     k_fit_out<T><<<ceil_div((long long)na * 32, 256), 256, 0, st>>>(na, m.f3, a0, types, P->y3,
-                                                                     P->F4, P->c4, atom_e, P->d3);
+                                                                     P->F4[0], P->c4[0], atom_e, P->d3);
     launches += 1;
     // ---------------- backward
     for (int t = 0; t < S; ++t) {
@@ -840,6 +863,28 @@ static int run_impl(PlainAf<T>* P, const int* sel_j, const double* sel_r, const 
         rows, NM, a0, P->d, P->sw, P->dsw, P->s, P->rh, P->tj, P->dRt, P->ds, P->dsw_att, P->dcg,
         P->g);
     launches += 2;
+    // further fitting heads on the same descriptor: energies only
+    for (int h = 1; h < (int)P->F4.size(); ++h) {
+      for (int t = 0; t < S; ++t) {
+        auto rg = P->fit_ranges[c][t];
+        if (rg.second == 0) continue;
+        const int* rws = P->fit_rows + rg.first;
+        const int q = h * S + t;
+        Gemm<T> g = gemm_rowmajor<T>(rg.second, m.f1, M1 * M2, P->D, M1 * M2, P->F1[q], m.f1, P->y1, m.f1);
+        g.a_rows = rws; g.c_rows = rws; g.bias = P->c1[q]; g.epi = 1;
+        gemm(g, 1, st);
+        g = gemm_rowmajor<T>(rg.second, m.f2, m.f1, P->y1, m.f1, P->F2[q], m.f2, P->y2, m.f2);
+        g.a_rows = rws; g.c_rows = rws; g.bias = P->c2[q]; g.epi = 1;
+        gemm(g, 1, st);
+        g = gemm_rowmajor<T>(rg.second, m.f3, m.f2, P->y2, m.f2, P->F3[q], m.f3, P->y3, m.f3);
+        g.a_rows = rws; g.c_rows = rws; g.bias = P->c3[q]; g.epi = 1;
+        gemm(g, 1, st);
+        launches += 3;
+      }
+      k_fit_energy<T><<<ceil_div((long long)na * 32, 256), 256, 0, st>>>(
+          na, m.f3, a0, types, P->y3, P->F4[h], P->c4[h], P->head_e + (size_t)(h - 1) * P->n_atoms);
+      launches += 1;
+    }
   }
   P->kernels_per_call = launches;
   return 0;
@@ -857,6 +902,7 @@ class PlainAfModel : public Model {
   }
   const float* grad32() const override { return grad_as<float>(); }
   const double* grad64() const override { return grad_as<double>(); }
+  const double* head_energies() const override { return p_->head_e; }
   size_t bytes() const override { return p_->bytes; }
 
  private:

@@ -31,6 +31,7 @@ class AttnModel:
     nmax: int
     rc: float = 6.0
     rs: float = 0.5
+    fit_heads: int = 1
 
     def as_dict(self):
         return asdict(self)

@@ -84,3 +84,19 @@ def test_argument_errors_without_gpu():
     with pytest.raises(dp.DPError) as e:
         dp.DeepPotential(d, [0, 1, 1], [10.0, -1, 10], w)
     assert e.value.code == dp.DP_ERR_ARG
+
+
+def test_weight_count_with_fitting_heads_matches_the_oracle():
+    from dataclasses import replace
+    from synth import configs as C
+    for k in (1, 2, 4):
+        m = replace(C.ATTN_MODEL, fit_heads=k)
+        assert dp.weight_count(dp.model_desc(m, dp.PREC_PLAIN_F32)) == oracle.af_weight_count(m)
+    m = replace(C.ATTN_MODEL, fit_heads=3)
+    w = np.arange(oracle.af_weight_count(m), dtype=np.float64)
+    w0, d0 = oracle.af_head_blob(m, w, 0)
+    w2, _ = oracle.af_head_blob(m, w, 2)
+    n1 = oracle.af_weight_count(d0)
+    assert len(w0) == len(w2) == n1 and d0["fit_heads"] == 1
+    fl = oracle.af_weight_count(m) - n1
+    assert np.array_equal(w0, w[:n1]) and np.array_equal(w2[n1 - fl // 2:], w[-(fl // 2):])

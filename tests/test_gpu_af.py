@@ -329,3 +329,27 @@ def test_dp_group_equals_the_members_alone(prec):
     ref, _ = make(m, s, prec, w=w)
     E4, F4, _ = ref.compute(s.coords)
     assert E3 == E4 and np.array_equal(F3, F4)
+
+
+# ------------------------------------------------------------------ fitting heads
+@pytest.mark.parametrize("prec", [dp.PREC_PLAIN_F32, dp.PREC_FUSED])
+def test_fitting_heads_share_one_descriptor(prec):
+    """Three fitting heads on the configuration-2 model: every head's energy
+    matches the single-head model with that head's fitting nets; forces,
+    virial and dp_compute's energy are head 0's."""
+    m = replace(C.ATTN_MODEL, fit_heads=3)
+    s = serving_system(700, 9)
+    w = weights(m)
+    pot = dp.DeepPotential(dp.model_desc(m, prec), s.types, s.box, w)
+    E, F, V = pot.compute(s.coords)
+    he = pot.head_energies()
+    eo, (Eo, aeo, Fo, Vo) = oracle.af_compute_heads(m, w, s.types, s.coords, s.box)
+    assert he.shape == (3,) and he[0] == E
+    for h in range(3):
+        # a head's total can be small by cancellation: scale by its atomic energies
+        wh, dh = oracle.af_head_blob(m, w, h)
+        ae_h = oracle.af_compute(dh, wh, s.types, s.coords, s.box)[1]
+        assert abs(he[h] - eo[h]) <= TOL_E[prec] * np.sum(np.abs(ae_h))
+    assert len(set(np.round(eo, 6))) == 3                  # the heads really differ
+    assert np.max(np.abs(F - Fo)) <= TOL_F[prec] * frms(Fo)
+    assert np.max(np.abs(V - Vo)) <= TOL_F[prec] * np.linalg.norm(Vo)
