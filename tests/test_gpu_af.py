@@ -353,3 +353,27 @@ def test_fitting_heads_share_one_descriptor(prec):
     assert len(set(np.round(eo, 6))) == 3                  # the heads really differ
     assert np.max(np.abs(F - Fo)) <= TOL_F[prec] * frms(Fo)
     assert np.max(np.abs(V - Vo)) <= TOL_F[prec] * np.linalg.norm(Vo)
+
+
+@pytest.mark.parametrize("prec", [dp.PREC_PLAIN_F32, dp.PREC_FUSED])
+def test_isolated_atoms_keep_their_energy(prec):
+    """Atoms with no neighbour within rc (the fused kernels skip their
+    per-atom pipeline) still carry the fitting of a zero descriptor, and no
+    force; the rest of the box is unaffected."""
+    m = C.ATTN_MODEL
+    base = serving_system(300, 4)
+    L = base.box.copy()
+    L[0] += 30.0                                 # empty slab beyond the water
+    x = np.concatenate([base.coords % base.box, [[base.box[0] + 15.0, 3.0, 4.0],
+                                                 [base.box[0] + 15.0, 9.0, 11.0]]])
+    t = np.concatenate([base.types, [1, 4]]).astype(np.int32)
+    from synth import System
+    s = System(coords=x, types=t, box=L, species=base.species, note="isolated", blob_atoms=0)
+    pot, w = make(m, s, prec)
+    E, F, V = pot.compute(s.coords)
+    Eo, aeo, Fo, Vo = oracle.af_compute(m, w, s.types, s.coords, s.box)
+    ae = pot.atom_energies()
+    assert abs(E - Eo) <= TOL_E[prec] * np.sum(np.abs(aeo))
+    assert np.all(F[-2:] == 0)
+    assert np.max(np.abs(ae[-2:] - aeo[-2:])) <= 1e-3 * np.max(np.abs(aeo[-2:])) + 1e-6
+    assert np.max(np.abs(F - Fo)) <= TOL_F[prec] * frms(Fo)
