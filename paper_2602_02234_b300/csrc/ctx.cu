@@ -181,6 +181,9 @@ extern "C" int dp_weight_count(const dp_model_desc* d, size_t* n) {
 }
 
 // ------------------------------------------------------------------ systems
+// the small-box search keeps the images -nimg..nimg of an axis in one 32-bit mask
+constexpr int kMaxImages = 15;
+
 static void make_sysinfo(const double* L, double rskin, int atom0, int natom, int cell0,
                          SysInfo* s, int* ncell) {
   memset(s, 0, sizeof *s);
@@ -468,6 +471,8 @@ static int ctx_set_systems(dp_ctx* c, int n_sys, const int* natoms, const double
   for (int s = 0, a0 = 0; s < n_sys; ++s) {
     int nc = 0;
     make_sysinfo(boxes + 3 * s, c->rskin, a0, natoms[s], ncell, &si[s], &nc);
+    if (std::max(si[s].nimg[0], std::max(si[s].nimg[1], si[s].nimg[2])) > kMaxImages)
+      return fail(c, DP_ERR_ARG, "a box edge is shorter than (rc + skin) / 14");
     ncell += nc;
     for (int i = 0; i < natoms[s]; ++i) sys_of[a0 + i] = s;
     a0 += natoms[s];

@@ -136,46 +136,87 @@ __global__ void k_cell_sort(int ncell, const int* __restrict__ cell_start,
 }
 
 // -------------------------------------------------------------- skin lists
-// One warp per atom; candidates are appended in a fixed order (cells in
-// (dx, dy, dz) order, atoms ascending inside a cell; or atoms then images for
-// small boxes) using a ballot prefix, so the list is deterministic.
-__global__ void k_skin_build(int n, const double* __restrict__ w, const int* __restrict__ fl,
-                             const int* __restrict__ sys_of, const SysInfo* __restrict__ sys,
-                             const int* __restrict__ cell_of, const int* __restrict__ cell_start,
-                             const int* __restrict__ cell_idx, double rskin, int cap,
-                             SkinEntry* __restrict__ skin, int* __restrict__ skin_cnt,
-                             int* __restrict__ flags) {
+// One warp per atom.  Candidates (j, image) first pass a conservative FP32
+// test, |r|^2 < (rskin + margin)^2 for the cell search or |r_a| < rskin +
+// margin per axis for small boxes, where the margin is orders of magnitude
+// above the FP32 rounding of coordinates of that size; the survivors go
+// through a per-warp queue and are decided by the exact FP64 distance in
+// batches of 32, so the (slow) FP64 work scales with the skin size rather
+// than with the number of candidates.  Entries are appended through ballots
+// in the order the candidates were queued, so the list is deterministic.
+constexpr int kSkinWarps = 4;
+
+// position of the k-th (from 0) set bit of m, -1 if there are fewer
+__device__ __forceinline__ int nth_bit(unsigned m, int k) {
+  for (int b = 0; b < 32; ++b)
+    if ((m >> b) & 1u) {
+      if (k == 0) return b;
+      --k;
+    }
+  return -1;
+}
+
+__global__ void __launch_bounds__(32 * kSkinWarps)
+k_skin_build(int n, const double* __restrict__ w, const int* __restrict__ fl,
+             const int* __restrict__ sys_of, const SysInfo* __restrict__ sys,
+             const int* __restrict__ cell_of, const int* __restrict__ cell_start,
+             const int* __restrict__ cell_idx, double rskin, int cap,
+             SkinEntry* __restrict__ skin, int* __restrict__ skin_cnt,
+             int* __restrict__ flags) {
   if (!(*flags & kFlagRebuild)) return;
+  __shared__ int4 queue_all[kSkinWarps][64];
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (warp >= n) return;
+  int4* queue = queue_all[threadIdx.x >> 5];
+  const unsigned lt = (1u << lane) - 1u;
   int i = warp;
   const SysInfo& S = sys[sys_of[i]];
   double wi[3] = {w[3 * i], w[3 * i + 1], w[3 * i + 2]};
   int fi[3] = {fl[3 * i], fl[3 * i + 1], fl[3 * i + 2]};
-  double r2cut = rskin * rskin;
-  int cnt = 0;
+  const double r2cut = rskin * rskin;
+  const float Lf[3] = {(float)S.L[0], (float)S.L[1], (float)S.L[2]};
+  const float wif[3] = {(float)wi[0], (float)wi[1], (float)wi[2]};
+  const float lim = (float)rskin + 1e-5f * (fmaxf(Lf[0], fmaxf(Lf[1], Lf[2])) + (float)rskin);
+  const float lim2 = lim * lim;
+  int cnt = 0, qn = 0;
   SkinEntry* out = skin + (size_t)i * cap;
 
-  auto consider = [&](int j, int nx, int ny, int nz, bool valid) {
+  // exact decision for queue[0, k), then the rest moves to the front
+  auto flush = [&](int k) {
     bool take = false;
     SkinEntry e;
-    if (valid && !(j == i && nx == 0 && ny == 0 && nz == 0)) {
-      int nn[3] = {nx, ny, nz};
+    if (lane < k) {
+      const int4 q = queue[lane];
+      int nn[3] = {q.y, q.z, q.w};
       double r[3];
-      double d2 = sep_exact(wi, w + 3 * j, nn, S.L, r);
+      double d2 = sep_exact(wi, w + 3 * q.x, nn, S.L, r);
       if (d2 < r2cut && d2 > 0.0) {
         take = true;
-        e.j = j;
-        e.mx = nx - fl[3 * j + 0] + fi[0];
-        e.my = ny - fl[3 * j + 1] + fi[1];
-        e.mz = nz - fl[3 * j + 2] + fi[2];
+        e.j = q.x;
+        e.mx = q.y - fl[3 * q.x + 0] + fi[0];
+        e.my = q.z - fl[3 * q.x + 1] + fi[1];
+        e.mz = q.w - fl[3 * q.x + 2] + fi[2];
       }
     }
     unsigned b = __ballot_sync(0xffffffffu, take);
-    int pos = cnt + __popc(b & ((1u << lane) - 1u));
+    int pos = cnt + __popc(b & lt);
     if (take && pos < cap) out[pos] = e;
     cnt += __popc(b);
+    const int rest = qn - k;
+    int4 v = make_int4(0, 0, 0, 0);
+    if (lane < rest) v = queue[k + lane];
+    __syncwarp();
+    if (lane < rest) queue[lane] = v;
+    __syncwarp();
+    qn = rest;
+  };
+  auto enqueue = [&](bool pass, int j, int nx, int ny, int nz) {
+    unsigned b = __ballot_sync(0xffffffffu, pass);
+    if (pass) queue[qn + __popc(b & lt)] = make_int4(j, nx, ny, nz);
+    qn += __popc(b);
+    __syncwarp();
+    if (qn >= 32) flush(32);
   };
 
   if (S.use_cells) {
@@ -195,30 +236,50 @@ __global__ void k_skin_build(int n, const double* __restrict__ w, const int* __r
           int lo = cell_start[cell], hi = cell_start[cell + 1];
           for (int base = lo; base < hi; base += 32) {
             int s = base + lane;
-            bool valid = s < hi;
-            int j = valid ? cell_idx[s] : 0;
-            consider(j, nn[0], nn[1], nn[2], valid);
+            bool pass = false;
+            int j = 0;
+            if (s < hi) {
+              j = cell_idx[s];
+              float d2 = 0.f;
+              for (int a = 0; a < 3; ++a) {
+                const float r = ((float)w[3 * j + a] - wif[a]) + (float)nn[a] * Lf[a];
+                d2 += r * r;
+              }
+              pass = d2 < lim2 && !(j == i && nn[0] == 0 && nn[1] == 0 && nn[2] == 0);
+            }
+            enqueue(pass, j, nn[0], nn[1], nn[2]);
           }
         }
   } else {
-    int nx = 2 * S.nimg[0] + 1, ny = 2 * S.nimg[1] + 1, nz = 2 * S.nimg[2] + 1;
-    int per_atom = nx * ny * nz;
-    long long total = (long long)S.natom * per_atom;
-    for (long long base = 0; base < total; base += 32) {
-      long long s = base + lane;
-      bool valid = s < total;
-      int j = S.atom0, ix = 0, iy = 0, iz = 0;
-      if (valid) {
-        int jj = (int)(s / per_atom);
-        int im = (int)(s % per_atom);
-        j = S.atom0 + jj;
-        ix = im / (ny * nz) - S.nimg[0];
-        iy = (im / nz) % ny - S.nimg[1];
-        iz = im % nz - S.nimg[2];
+    // per lane one atom j; per axis the images with |r_a| < lim as a bit mask
+    // (bit b: image b - nimg), then the lane's candidates in (x, y, z) order
+    for (int base = 0; base < S.natom; base += 32) {
+      const int jj = base + lane;
+      const bool valid = jj < S.natom;
+      const int j = S.atom0 + (valid ? jj : 0);
+      unsigned m[3] = {0u, 0u, 0u};
+      if (valid)
+        for (int a = 0; a < 3; ++a) {
+          const float t = (float)w[3 * j + a] - wif[a];
+          for (int b = 0; b <= 2 * S.nimg[a]; ++b)
+            if (fabsf(t + (float)(b - S.nimg[a]) * Lf[a]) < lim) m[a] |= 1u << b;
+        }
+      const int cy = __popc(m[1]), cz = __popc(m[2]);
+      const int ncand = __popc(m[0]) * cy * cz;
+      const int kmax = __reduce_max_sync(0xffffffffu, ncand);
+      for (int q = 0; q < kmax; ++q) {
+        bool pass = q < ncand;
+        int nn[3] = {0, 0, 0};
+        if (pass) {
+          const int kk[3] = {q / (cy * cz), (q / cz) % cy, q % cz};
+          for (int a = 0; a < 3; ++a) nn[a] = nth_bit(m[a], kk[a]) - S.nimg[a];
+          pass = !(j == i && nn[0] == 0 && nn[1] == 0 && nn[2] == 0);
+        }
+        enqueue(pass, j, nn[0], nn[1], nn[2]);
       }
-      consider(j, ix, iy, iz, valid);
     }
   }
+  if (qn > 0) flush(qn);
   if (lane == 0) {
     skin_cnt[i] = cnt < cap ? cnt : cap;
     if (cnt > cap) atomicOr(flags, kFlagOverflow);
@@ -369,7 +430,7 @@ void launch_nlist_rebuild(const NlistArgs& a, cudaStream_t st) {
   k_cell_fill<<<nb, 256, 0, st>>>(a.n, a.cell_of, a.cell_start, a.cell_fill, a.cell_idx, a.flags);
   k_cell_sort<<<ceil_div(a.ncell > 0 ? a.ncell : 1, 128), 128, 0, st>>>(a.ncell, a.cell_start,
                                                                       a.cell_idx, a.flags);
-  k_skin_build<<<ceil_div((long long)a.n * 32, 128), 128, 0, st>>>(
+  k_skin_build<<<ceil_div((long long)a.n, kSkinWarps), 32 * kSkinWarps, 0, st>>>(
       a.n, a.w, a.fl, a.sys_of, a.sys, a.cell_of, a.cell_start, a.cell_idx, a.rskin, a.cap, a.skin,
       a.skin_cnt, a.flags);
   k_mirror<<<ceil_div((long long)a.n * a.cap, 256), 256, 0, st>>>(a.n, a.cap, a.skin, a.skin_cnt,

@@ -37,12 +37,14 @@ def frms(F):
 
 
 # ------------------------------------------------------------------ neighbours
-@pytest.mark.parametrize("name", ["water64", "water96_small_box", "protein24k"])
+@pytest.mark.parametrize("name", ["water64", "water96_small_box", "slab900", "protein24k"])
 def test_neighbour_lists_exact(name):
     if name == "water64":
         s, m = C.water64(), C.WATER64_MODEL
     elif name == "water96_small_box":
         s, m = serving_system(96, 5), C.ATTN_MODEL
+    elif name == "slab900":       # two axes below 3 cells: the per-axis image search
+        s, m = protein_in_water(900, 90, (26.0, 19.0, 19.0), 21), C.ATTN_MODEL
     else:
         s, m = C.protein24k(), C.ATTN_MODEL
     pot, w = make(m, s, dp.PREC_PLAIN_F32)
@@ -235,6 +237,13 @@ def test_errors_are_reported_not_raised_on_device():
     # the context stays usable
     E, F, V = pot.compute(s.coords)
     assert np.isfinite(E)
+    # a box edge below (rc + skin) / 14 would need more periodic images per
+    # axis than the small-box search holds
+    tiny = water_box(1, 30.0, 1)
+    with pytest.raises(dp.DPError) as e:
+        dp.DeepPotential(dp.model_desc(m, dp.PREC_PLAIN_F32), tiny.types[:1],
+                         np.array([0.3, 30.0, 30.0]), weights(m))
+    assert e.value.code == dp.DP_ERR_ARG
 
 
 # ------------------------------------------------------------------ fused path
