@@ -5,8 +5,8 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 (``paper_2602_02234_b300``) and never imports it; the two meet only in the
 seeded generators of ``synth``.
 
-The arithmetic is plain C (``af_oracle.c``, ``gf_oracle.c``) in double
-precision; this file only marshals numpy arrays through ctypes.
+The arithmetic is plain C (``af_oracle.c``, ``afmp_oracle.c``, ``gf_oracle.c``)
+in double precision; this file only marshals numpy arrays through ctypes.
 """
 from __future__ import annotations
 
@@ -54,6 +54,13 @@ def _declare(L):
     L.oracle_af_md.restype = C.c_int
     L.oracle_af_md.argtypes = [_PI, _PD, _PD, C.c_int, _PI, _PD, _PD, _PD, _PD, C.c_int,
                                C.c_double, C.c_int, _PD, _PD]
+    L.oracle_afmp_weight_count.restype = C.c_longlong
+    L.oracle_afmp_weight_count.argtypes = [_PI, _PD]
+    L.oracle_afmp_weight_offset.restype = C.c_longlong
+    L.oracle_afmp_weight_offset.argtypes = [_PI, _PD, C.c_int, C.c_int]
+    L.oracle_afmp_compute.restype = C.c_int
+    L.oracle_afmp_compute.argtypes = [_PI, _PD, _PD, C.c_int, _PI, _PD, _PD, C.c_int, _PD, _PD,
+                                      _PD, _PD]
     L.oracle_switch.restype = None
     L.oracle_switch.argtypes = [C.c_double, C.c_double, C.c_double, _PD, _PD]
     if hasattr(L, "oracle_gf_compute"):
@@ -98,10 +105,24 @@ AF_KINDS = {"eW1": 0, "eb1": 1, "eW2": 2, "eb2": 3, "eW3": 4, "eb3": 5,
             "fW1": 20, "fb1": 21, "fW2": 22, "fb2": 23, "fW3": 24, "fb3": 25, "fW4": 26, "fb4": 27}
 
 
+def _mp(model) -> bool:
+    d = model if isinstance(model, dict) else model.as_dict()
+    return bool(d.get("message_passing", 0))
+
+
 def af_weight_count(model) -> int:
     """Blob length; with k fitting heads the fitting nets of heads 1..k-1
-    follow head 0's, in the same layout."""
+    follow head 0's, in the same layout.  With message passing the blob also
+    holds the atom-channel weights (afmp_oracle.c)."""
     i, f = _af_dims(model)
+    if _mp(model):
+        d = model if isinstance(model, dict) else model.as_dict()
+        if max(1, d.get("fit_heads", 1)) != 1:
+            raise ValueError("message passing takes one fitting head")
+        n = lib().oracle_afmp_weight_count(_p(i, _I), _p(f, _D))
+        if n < 0:
+            raise ValueError("invalid attention-family model")
+        return int(n)
     n = lib().oracle_af_weight_count(_p(i, _I), _p(f, _D))
     if n < 0:
         raise ValueError("invalid attention-family model")
@@ -143,8 +164,23 @@ def af_compute_heads(model, weights, types, coords, box, nthreads=0):
     return np.array(energies), head0
 
 
+def afmp_weight_slice(model, kind: str, a: int = 0) -> slice:
+    """Message-passing blocks: ``Wt`` (species rows of the atom channel's
+    initial value), ``Wm`` / ``bm`` of layer ``a``."""
+    i, f = _af_dims(model)
+    d = model if isinstance(model, dict) else model.as_dict()
+    k = {"Wt": 0, "Wm": 1, "bm": 2}[kind]
+    off = lib().oracle_afmp_weight_offset(_p(i, _I), _p(f, _D), k, a)
+    if off < 0:
+        raise ValueError((kind, a))
+    size = {"Wt": d["n_species"] * d["m1"], "Wm": d["m1"] * d["m1"], "bm": d["m1"]}[kind]
+    return slice(int(off), int(off) + size)
+
+
 def af_weight_slice(model, kind: str, a: int) -> slice:
     """Slice of the blob holding block ``kind`` of species/layer ``a``."""
+    if _mp(model):
+        raise ValueError("use afmp_weight_slice for message-passing blobs")
     i, f = _af_dims(model)
     off = lib().oracle_af_weight_offset(_p(i, _I), _p(f, _D), AF_KINDS[kind], a)
     if off < 0:
@@ -202,11 +238,12 @@ def af_compute(model, weights, types, coords, box, nthreads=0):
     ae = np.zeros(n)
     F = np.zeros((n, 3))
     V = np.zeros((3, 3))
-    rc = lib().oracle_af_compute(_p(i, _I), _p(f, _D), _p(w, _D), n, _p(t, _I), _p(x, _D),
+    fn = lib().oracle_afmp_compute if _mp(model) else lib().oracle_af_compute
+    rc = fn(_p(i, _I), _p(f, _D), _p(w, _D), n, _p(t, _I), _p(x, _D),
                                  _p(b, _D), int(nthreads), _p(E, _D), _p(ae, _D), _p(F, _D),
                                  _p(V, _D))
     if rc:
-        raise RuntimeError("oracle_af_compute failed")
+        raise RuntimeError("attention-family oracle failed")
     return float(E[0]), ae, F, V
 
 
@@ -231,6 +268,8 @@ def af_compute_group(model, weights, types, coords, box, mask, nthreads=0):
 
 def af_atoms(model, weights, types, coords, box, centres, nthreads=0, want_desc=False):
     """Per centre: atomic energy, pair gradients g (nmax x 3), neighbour j and image."""
+    if _mp(model):
+        raise ValueError("message passing couples every atom: use af_compute")
     i, f = _af_dims(model)
     d = model if isinstance(model, dict) else model.as_dict()
     nmax = d["nmax"]
@@ -281,6 +320,8 @@ def af_forces_subset(model, weights, types, coords, box, sample, nthreads=0):
 
 def af_md(model, weights, types, masses, coords, vel, box, n_steps, dt, nthreads=0):
     """Velocity-Verlet NVE; returns (x, v, epot[n_steps], ekin[n_steps])."""
+    if _mp(model):
+        raise ValueError("af_md covers the model without message passing")
     i, f = _af_dims(model)
     w, t, m, b = _c64(weights), _c32(types), _c64(masses), _c64(box)
     x = _c64(coords).copy()

@@ -12,7 +12,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboracle.so")
-SOURCES = ["af_oracle.c", "gf_oracle.c"]
+SOURCES = ["af_oracle.c", "afmp_oracle.c", "gf_oracle.c"]
 HEADERS = ["oracle_common.h"]
 
 

@@ -32,6 +32,7 @@ class AttnModel:
     rc: float = 6.0
     rs: float = 0.5
     fit_heads: int = 1
+    message_passing: int = 0     # 1: atom channel passed between neighbours each layer
 
     def as_dict(self):
         return asdict(self)
