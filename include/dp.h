@@ -106,7 +106,16 @@ typedef struct dp_model_desc {
    * virial and the MD; every head's energy comes from dp_get_head_energies.
    * The weight blob holds the fitting nets of head 0, 1, ... in order.     */
   int fit_heads;
-  int reserved[6];
+  /* attention family: 1 = cross-atom message passing (DPA2's repformer layers
+   * exchange information between neighbouring atoms, Sec. II; DPA2 needs the
+   * atoms within n_layers x rc, Sec. III).  An atom channel h (width m1)
+   * starts at Wt[t_i]; before attention layer l every kept pair feature G_ip
+   * gains tanh(h_j Wm_l + bm_l) of its neighbour j, and after the layer
+   * h_i += (1/nmax) sum_p sw_ip G_ip.  Atom i's energy then depends on the
+   * atoms up to n_layers neighbour hops away.  Plain precisions only, one
+   * fitting head; every atom's activations stay resident (one chunk).     */
+  int message_passing;
+  int reserved[5];
 } dp_model_desc;
 
 typedef struct dp_ctx dp_ctx;
@@ -114,7 +123,9 @@ typedef struct dp_ctx dp_ctx;
 /* Number of FP64 values in the weight blob for `desc` (written to *n).
  * Attention family, in order (row-major W[in][out], W before b):
  *   per species t:  W1[1][e1] b1[e1] W2[e1][e2] b2[e2] W3[e2][m1] b3[m1]
+ *   (message passing) Wt[n_species][m1]
  *   per layer l:    Wq[m1][H] Wk[m1][H] Wv[m1][H] Wo[H][m1] bo[m1]
+ *                   (message passing) Wm[m1][m1] bm[m1]
  *   per species t:  F1[m1*m2][f1] c1[f1] F2[f1][f2] c2[f2] F3[f2][f3] c3[f3] F4[f3][1] c4[1]
  * Graph family (Nd = node_dim, Ed = edge_dim), in order:
  *   W_type[S][Nd] w_e[1][Ed] b_e[Ed]

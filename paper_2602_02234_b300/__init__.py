@@ -53,7 +53,8 @@ class ModelDesc(C.Structure):
                 ("angle_nmax", C.c_int), ("angle_rcut", C.c_double),
                 ("angle_rcut_smth", C.c_double), ("f1", C.c_int), ("f2", C.c_int),
                 ("f3", C.c_int), ("skin", C.c_double), ("rebuild_every", C.c_int),
-                ("fit_heads", C.c_int), ("reserved", C.c_int * 6)]
+                ("fit_heads", C.c_int), ("message_passing", C.c_int),
+                ("reserved", C.c_int * 5)]
 
 
 def model_desc(model, precision: int, skin: float = 1.0, rebuild_every: int = 10) -> ModelDesc:
@@ -82,6 +83,7 @@ def model_desc(model, precision: int, skin: float = 1.0, rebuild_every: int = 10
         m.e1, m.e2, m.m1, m.m2 = d["e1"], d["e2"], d["m1"], d["m2"]
         m.n_layers, m.hidden, m.heads = d["n_layers"], d["hidden"], d["heads"]
         m.fit_heads = d.get("fit_heads", 1)
+        m.message_passing = d.get("message_passing", 0)
     return m
 
 

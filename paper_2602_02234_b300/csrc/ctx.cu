@@ -155,6 +155,9 @@ static int check_desc(const dp_model_desc* d, std::string* why) {
   if (d->precision < DP_PREC_PLAIN_F64 || d->precision > DP_PREC_FUSED) { *why = "unknown precision"; return -1; }
   if (d->fit_heads < 0 || d->fit_heads > 16) { *why = "fit_heads must be 0..16"; return -1; }
   if (d->fit_heads > 1 && d->family != DP_FAMILY_ATTENTION) { *why = "fitting heads are an attention-family option"; return -1; }
+  if (d->message_passing != 0 && d->message_passing != 1) { *why = "message_passing must be 0 or 1"; return -1; }
+  if (d->message_passing && d->family != DP_FAMILY_ATTENTION) { *why = "message passing is an attention-family option"; return -1; }
+  if (d->message_passing && d->fit_heads > 1) { *why = "message passing takes one fitting head"; return -1; }
   return 0;
 }
 
@@ -174,6 +177,7 @@ extern "C" int dp_weight_count(const dp_model_desc* d, size_t* n) {
   size_t S = d->n_species, E1 = d->e1, E2 = d->e2, M1 = d->m1, M2 = d->m2, H = d->hidden;
   size_t t = S * (E1 + E1 + E1 * E2 + E2 + E2 * M1 + M1);
   t += (size_t)d->n_layers * (3 * M1 * H + H * M1 + M1);
+  if (d->message_passing) t += S * M1 + (size_t)d->n_layers * (M1 * M1 + M1);
   const size_t heads = d->fit_heads > 1 ? d->fit_heads : 1;
   t += heads * S * (M1 * M2 * d->f1 + d->f1 + (size_t)d->f1 * d->f2 + d->f2 + (size_t)d->f2 * d->f3 + d->f3 + d->f3 + 1);
   *n = t;
@@ -363,7 +367,10 @@ static int check_model(const dp_model_desc* desc, const double* weights, size_t 
       if (!(masses[t] > 0)) return fail(nullptr, DP_ERR_ARG, "masses must be positive");
   *afd = AfDims{desc->n_species, desc->e1, desc->e2, desc->m1, desc->m2, desc->n_layers,
                 desc->hidden, desc->heads, desc->f1, desc->f2, desc->f3, desc->nmax,
-                desc->rcut, desc->rcut_smth, desc->fit_heads > 1 ? desc->fit_heads : 1};
+                desc->rcut, desc->rcut_smth, desc->fit_heads > 1 ? desc->fit_heads : 1,
+                desc->message_passing};
+  if (desc->message_passing && desc->precision == DP_PREC_FUSED)
+    return fail(nullptr, DP_ERR_UNSUPPORTED, "message passing runs in the plain FP32 / FP64 forms");
   if (desc->family == DP_FAMILY_ATTENTION && desc->precision == DP_PREC_FUSED &&
       !fused_af_supported(*afd, &why))
     return fail(nullptr, DP_ERR_UNSUPPORTED, why);

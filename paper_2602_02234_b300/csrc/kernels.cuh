@@ -100,6 +100,7 @@ struct AfDims {
   int n_species, e1, e2, m1, m2, n_layers, hidden, heads, f1, f2, f3, nmax;
   double rc, rs;
   int fit_heads;         // fitting heads sharing the descriptor (>= 1)
+  int mp;                // 1: atom channel passed between neighbours every layer
 };
 // per (system, extra head) sums of atomic energies: head_e is [heads][n],
 // out[s * heads + h]; members of a DP group only (grp optional)

@@ -510,6 +510,121 @@ __global__ void k_zero(long long n, T* __restrict__ p) {
 }
 
 // =========================================================================
+// message passing between atoms (atom channel h, width m1; one chunk holds
+// every atom so that a layer finishes for all atoms before the next starts)
+// =========================================================================
+// h_i = Wt[t_i]
+template <typename T>
+__global__ void k_mp_init(int n, int m1, const int* __restrict__ types, const T* __restrict__ Wt,
+                          T* __restrict__ h) {
+  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (long long)n * m1) return;
+  const int i = (int)(q / m1), f = (int)(q % m1);
+  h[q] = Wt[(long long)types[i] * m1 + f];
+}
+
+// G'_ip = G_ip + U_{j(p)} for kept slots; empty slots copy G
+template <typename T>
+__global__ void k_mp_add(long long rows, int m1, const int* __restrict__ sel_j,
+                         const T* __restrict__ G, const T* __restrict__ U, T* __restrict__ Gp) {
+  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= rows * m1) return;
+  const long long row = q / m1;
+  const int f = (int)(q % m1);
+  const int j = sel_j[row];
+  T v = G[q];
+  if (j >= 0) v += U[(long long)j * m1 + f];
+  Gp[q] = v;
+}
+
+// h_i += (1/Nmax) sum_p sw_ip G_ip, slots in increasing order
+template <typename T>
+__global__ void k_mp_pool(int n, int nmax, int m1, T inv_nmax, const T* __restrict__ sw,
+                          const T* __restrict__ G, T* __restrict__ h) {
+  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (long long)n * m1) return;
+  const long long i = q / m1;
+  const int f = (int)(q % m1);
+  T acc = T(0);
+  for (int p = 0; p < nmax; ++p) acc += sw[i * nmax + p] * G[(i * nmax + p) * m1 + f];
+  h[q] += acc * inv_nmax;
+}
+
+// adjoint of the pool for kept slots: dG_ip += (sw_ip / Nmax) dh_i and
+// dE/dsw_ip += (1/Nmax) G_ip . dh_i (one warp per slot, fixed reduction tree)
+template <typename T>
+__global__ void k_mp_pool_bwd(long long rows, int nmax, int m1, T inv_nmax,
+                              const int* __restrict__ sel_j, const T* __restrict__ sw,
+                              const T* __restrict__ G, const T* __restrict__ dh, T* __restrict__ dG,
+                              T* __restrict__ dsw) {
+  const long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= rows || sel_j[row] < 0) return;
+  const long long i = row / nmax;
+  const T sc = sw[row] * inv_nmax;
+  T dot = T(0);
+  for (int f = lane; f < m1; f += 32) {
+    const T d = dh[i * m1 + f];
+    dG[row * m1 + f] += sc * d;
+    dot += G[row * m1 + f] * d;
+  }
+  for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+  if (lane == 0) dsw[row] += dot * inv_nmax;
+}
+
+// dq_j = (sum over the slots (i, p) naming j of dG'_ip) * (1 - U_j^2).  The
+// slots are found through j's skin list and summed in increasing i * nmax + p,
+// so the result does not depend on the order the skin list holds them in.
+// One warp per atom; shared memory: 2 x cap ints per warp.
+template <typename T>
+__global__ void k_mp_gather(int n, int nmax, int m1, int cap, const SkinEntry* __restrict__ skin,
+                            const int* __restrict__ skin_cnt, const int* __restrict__ mirror,
+                            const short* __restrict__ selpos, const T* __restrict__ dG,
+                            const T* __restrict__ U, T* __restrict__ dq) {
+  extern __shared__ int mp_smem[];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (j >= n) return;
+  int* keys = mp_smem + (size_t)wib * 2 * cap;
+  int* ord = keys + cap;
+  const int cnt = skin_cnt[j];
+  int k = 0;
+  for (int base = 0; base < cnt; base += 32) {
+    const int c = base + lane;
+    bool take = false;
+    int key = 0;
+    if (c < cnt) {
+      const long long e = (long long)j * cap + c;
+      const int i = skin[e].j, cp = mirror[e];
+      if (cp >= 0) {
+        const int p = selpos[(long long)i * cap + cp];
+        if (p >= 0) {
+          take = true;
+          key = i * nmax + p;
+        }
+      }
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, take);
+    if (take) keys[k + __popc(b & ((1u << lane) - 1u))] = key;
+    k += __popc(b);
+  }
+  __syncwarp();
+  for (int q = lane; q < k; q += 32) {
+    const int kq = keys[q];
+    int r = 0;
+    for (int t = 0; t < k; ++t) r += keys[t] < kq ? 1 : 0;
+    ord[r] = kq;
+  }
+  __syncwarp();
+  for (int f = lane; f < m1; f += 32) {
+    T acc = T(0);
+    for (int t = 0; t < k; ++t) acc += dG[(long long)ord[t] * m1 + f];
+    const T u = U[(long long)j * m1 + f];
+    dq[(long long)j * m1 + f] = acc * (T(1) - u * u);
+  }
+}
+
+// =========================================================================
 // host side
 // =========================================================================
 template <typename T>
@@ -522,6 +637,11 @@ struct PlainAf {
   std::vector<T*> F1, c1, F2, c2, F3, c3; // per head and species: [h * S + t]
   std::vector<T*> F4, c4;                 // per head, species stacked [S][f3], [S]
   double* head_e = nullptr;               // heads 1..: atomic energies [h - 1][n_atoms]
+  // message passing: species rows of h^0, per layer Wm [m1][m1] and bm; atom
+  // channel h, its adjoint dh, dq, per layer U = tanh(h Wm + bm), G' buffer
+  T* Wt = nullptr;
+  std::vector<T*> Wm, bm, U;
+  T *hbuf = nullptr, *dh = nullptr, *dq = nullptr, *Gp = nullptr;
   // per-chunk activations
   T *d, *sw, *dsw, *s, *Rt, *rh;
   int* tj;
@@ -597,7 +717,9 @@ static void* create_impl(const AfDims& m, const double* w, int n_atoms, const in
   CK(upload(P, &P->eW1, eW1)); CK(upload(P, &P->eb1, eb1));
   CK(upload(P, &P->eW2, eW2)); CK(upload(P, &P->eb2, eb2));
   CK(upload(P, &P->eW3, eW3)); CK(upload(P, &P->eb3, eb3));
+  if (m.mp) CK(upload(P, &P->Wt, take((size_t)S * M1)));
   P->Wqkv.resize(L); P->Wo.resize(L); P->bo.resize(L);
+  if (m.mp) { P->Wm.resize(L); P->bm.resize(L); P->U.resize(L); }
   for (int l = 0; l < L; ++l) {
     auto q = take((size_t)M1 * H), k = take((size_t)M1 * H), v = take((size_t)M1 * H);
     std::vector<double> qkv((size_t)M1 * 3 * H);
@@ -610,6 +732,10 @@ static void* create_impl(const AfDims& m, const double* w, int n_atoms, const in
     CK(upload(P, &P->Wqkv[l], qkv));
     CK(upload(P, &P->Wo[l], take((size_t)H * M1)));
     CK(upload(P, &P->bo[l], take(M1)));
+    if (m.mp) {
+      CK(upload(P, &P->Wm[l], take((size_t)M1 * M1)));
+      CK(upload(P, &P->bm[l], take(M1)));
+    }
   }
   const int HF = m.fit_heads > 1 ? m.fit_heads : 1;
   P->F1.resize(HF * S); P->c1.resize(HF * S); P->F2.resize(HF * S); P->c2.resize(HF * S);
@@ -645,6 +771,7 @@ static void* create_impl(const AfDims& m, const double* w, int n_atoms, const in
   if (ch < 1) ch = 1;
   if (ch > n_atoms) ch = n_atoms;
   if (ch < 1) ch = 1;
+  if (m.mp) ch = n_atoms;       // a layer needs every atom's previous layer
   int C = (int)ch;
   P->chunk = C;
   size_t rows = (size_t)C * NM;
@@ -671,6 +798,12 @@ static void* create_impl(const AfDims& m, const double* w, int n_atoms, const in
   CK(P->alloc(&P->dQKV, rows * 3 * H)); CK(P->alloc(&P->dsw_att, rows));
   CK(P->alloc(&P->dcg, (size_t)C * NM * NM)); CK(P->alloc(&P->ds, rows));
   CK(P->alloc(&P->g, (size_t)n_atoms * NM * 3));
+  if (m.mp) {
+    const size_t na = (size_t)n_atoms * M1;
+    CK(P->alloc(&P->hbuf, na)); CK(P->alloc(&P->dh, na)); CK(P->alloc(&P->dq, na));
+    CK(P->alloc(&P->Gp, rows * M1));
+    for (int l = 0; l < L; ++l) CK(P->alloc(&P->U[l], na));
+  }
   // ---- fitting row groups (atoms of one species inside one chunk)
   int nch = (n_atoms + C - 1) / C;
   std::vector<int> rowsv;
@@ -693,8 +826,10 @@ static void* create_impl(const AfDims& m, const double* w, int n_atoms, const in
 }
 
 template <typename T>
-static int run_impl(PlainAf<T>* P, const int* sel_j, const double* sel_r, const int* types,
-                    double* atom_e, cudaStream_t st) {
+static int run_impl(PlainAf<T>* P, const NbrView& nv, const int* types, double* atom_e,
+                    cudaStream_t st) {
+  const int* sel_j = nv.sel_j;
+  const double* sel_r = nv.sel_r;
   const AfDims& m = P->m;
   const int S = m.n_species, L = m.n_layers, M1 = m.m1, M2 = m.m2, H = m.hidden;
   const int NH = m.heads, NM = m.nmax, E1 = m.e1, E2 = m.e2, DH = H / NH;
@@ -711,9 +846,26 @@ static int run_impl(PlainAf<T>* P, const int* sel_j, const double* sel_r, const 
         rows, E1, E2, M1, P->s, P->tj, P->eW1, P->eb1, P->eW2, P->eb2, P->eW3, P->eb3, P->h1,
         P->h2, P->G[0]);
     launches += 2;
+    const T inv_nm = T(1) / (T)NM;
+    const long long nm1 = (long long)na * M1;
+    if (m.mp) {
+      k_mp_init<T><<<ceil_div(nm1, 256), 256, 0, st>>>(na, M1, types, P->Wt, P->hbuf);
+      launches += 1;
+    }
     for (int l = 0; l < L; ++l) {
       T* QKV = P->QKV[l];
-      gemm(gemm_rowmajor<T>(rows, 3 * H, M1, P->G[l], M1, P->Wqkv[l], 3 * H, QKV, 3 * H), 1, st);
+      const T* gin = P->G[l];
+      if (m.mp) {   // U = tanh(h Wm + bm); G' = G + U of each slot's neighbour
+        Gemm<T> g = gemm_rowmajor<T>(na, M1, M1, P->hbuf, M1, P->Wm[l], M1, P->U[l], M1);
+        g.bias = P->bm[l];
+        g.epi = 1;
+        gemm(g, 1, st);
+        k_mp_add<T><<<ceil_div((long long)rows * M1, 256), 256, 0, st>>>(
+            rows, M1, sel_j + (long long)a0 * NM, P->G[l], P->U[l], P->Gp);
+        gin = P->Gp;
+        launches += 2;
+      }
+      gemm(gemm_rowmajor<T>(rows, 3 * H, M1, gin, M1, P->Wqkv[l], 3 * H, QKV, 3 * H), 1, st);
       {  // S = Q K^T / sqrt(d), per (atom, head)
         Gemm<T> g{};
         g.M = NM; g.N = NM; g.K = DH;
@@ -740,8 +892,13 @@ static int run_impl(PlainAf<T>* P, const int* sel_j, const double* sel_r, const 
         gemm(g, 1, st);
       }
       k_layernorm<T><<<ceil_div((long long)rows * 32, 256), 256, 0, st>>>(
-          rows, M1, P->G[l], P->Zb, P->tj, P->G[l + 1], P->rstd[l]);
+          rows, M1, gin, P->Zb, P->tj, P->G[l + 1], P->rstd[l]);
       launches += 6;
+      if (m.mp && l + 1 < L) {   // h += (1/Nmax) sum_p sw_p G^{l+1}_p
+        k_mp_pool<T><<<ceil_div(nm1, 256), 256, 0, st>>>(na, NM, M1, inv_nm, P->sw, P->G[l + 1],
+                                                         P->hbuf);
+        launches += 1;
+      }
     }
     k_descriptor<T><<<na, 128, sizeof(T) * 4 * M1, st>>>(NM, M1, M2, P->Rt, P->G[L], P->Tm, P->D);
     launches += 1;
@@ -793,8 +950,18 @@ static int run_impl(PlainAf<T>* P, const int* sel_j, const double* sel_r, const 
     k_zero<T><<<ceil_div((long long)na * NM * NM, 256), 256, 0, st>>>((long long)na * NM * NM, P->dcg);
     k_zero<T><<<ceil_div(rows, 256), 256, 0, st>>>(rows, P->dsw_att);
     launches += 3;
+    if (m.mp) {
+      k_zero<T><<<ceil_div(nm1, 256), 256, 0, st>>>(nm1, P->dh);
+      launches += 1;
+    }
     for (int l = L - 1; l >= 0; --l) {
       T* QKV = P->QKV[l];
+      if (m.mp && l + 1 < L) {   // adjoint of h^{l+1} = h^l + pool(G^{l+1})
+        k_mp_pool_bwd<T><<<ceil_div((long long)rows * 32, 256), 256, 0, st>>>(
+            rows, NM, M1, inv_nm, sel_j + (long long)a0 * NM, P->sw, P->G[l + 1], P->dh, P->dG,
+            P->dsw_att);
+        launches += 1;
+      }
       k_layernorm_bwd<T><<<ceil_div((long long)rows * 32, 256), 256, 0, st>>>(
           rows, M1, P->G[l + 1], P->rstd[l], P->tj, P->dG, P->dZ);
       {  // dO = dZ Wo^T
@@ -852,6 +1019,19 @@ static int run_impl(PlainAf<T>* P, const int* sel_j, const double* sel_r, const 
         gemm(g, 1, st);
       }
       launches += 8;
+      if (m.mp) {   // G' = G + U_{j(p)}: dh^l += ((sum of dG' naming j) (1 - U^2)) Wm^T
+        int warps = 4;
+        while (warps > 1 && sizeof(int) * 2 * nv.cap * warps > 48 * 1024) --warps;
+        k_mp_gather<T><<<ceil_div(na, warps), warps * 32, sizeof(int) * 2 * nv.cap * warps, st>>>(
+            na, NM, M1, nv.cap, nv.skin, nv.skin_cnt, nv.mirror, nv.selpos, P->dG, P->U[l], P->dq);
+        Gemm<T> g{};
+        g.M = na; g.N = M1; g.K = M1;
+        g.A = P->dq; g.a_rm = M1; g.a_rk = 1;
+        g.B = P->Wm[l]; g.b_rk = 1; g.b_rn = M1;
+        g.C = P->dh; g.c_rm = M1; g.c_rn = 1; g.nb2 = 1; g.alpha = T(1); g.beta = T(1);
+        gemm(g, 1, st);
+        launches += 2;
+      }
     }
     {
       const int warps = 4;
@@ -897,7 +1077,7 @@ class PlainAfModel : public Model {
   explicit PlainAfModel(PlainAf<T>* p) : p_(p) {}
   ~PlainAfModel() override { delete p_; }
   int run(const NbrView& nv, const int* types, double* atom_e, cudaStream_t st) override {
-    run_impl(p_, nv.sel_j, nv.sel_r, types, atom_e, st);
+    run_impl(p_, nv, types, atom_e, st);
     return p_->kernels_per_call;
   }
   const float* grad32() const override { return grad_as<float>(); }

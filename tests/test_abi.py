@@ -43,9 +43,10 @@ def test_struct_layout_matches_c():
 #include <stddef.h>
 #include "dp.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(dp_model_desc), offsetof(dp_model_desc, rcut),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(dp_model_desc), offsetof(dp_model_desc, rcut),
          offsetof(dp_model_desc, angle_rcut), offsetof(dp_model_desc, f1),
-         offsetof(dp_model_desc, skin), offsetof(dp_model_desc, rebuild_every));
+         offsetof(dp_model_desc, skin), offsetof(dp_model_desc, rebuild_every),
+         offsetof(dp_model_desc, fit_heads), offsetof(dp_model_desc, message_passing));
   return 0;
 }
 '''
@@ -57,7 +58,7 @@ int main(void) {
         vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
     M = dp.ModelDesc
     assert vals == [C.sizeof(M), M.rcut.offset, M.angle_rcut.offset, M.f1.offset, M.skin.offset,
-                    M.rebuild_every.offset]
+                    M.rebuild_every.offset, M.fit_heads.offset, M.message_passing.offset]
 
 
 @pytest.mark.parametrize("model", [CF.WATER64_MODEL, CF.ATTN_MODEL])
@@ -100,3 +101,21 @@ def test_weight_count_with_fitting_heads_matches_the_oracle():
     assert len(w0) == len(w2) == n1 and d0["fit_heads"] == 1
     fl = oracle.af_weight_count(m) - n1
     assert np.array_equal(w0, w[:n1]) and np.array_equal(w2[n1 - fl // 2:], w[-(fl // 2):])
+
+
+def test_message_passing_desc_and_weight_count():
+    from dataclasses import replace
+    from synth import configs as C
+    m = replace(C.ATTN_MODEL, message_passing=1)
+    for prec in (dp.PREC_PLAIN_F64, dp.PREC_PLAIN_F32):
+        assert dp.weight_count(dp.model_desc(m, prec)) == oracle.af_weight_count(m)
+    d = dp.model_desc(m, dp.PREC_PLAIN_F32)
+    d.fit_heads = 2
+    with pytest.raises(dp.DPError) as e:
+        dp.weight_count(d)
+    assert e.value.code == dp.DP_ERR_ARG
+    d = dp.model_desc(C.GRAPH_MODEL, dp.PREC_PLAIN_F32)
+    d.message_passing = 1
+    with pytest.raises(dp.DPError) as e:
+        dp.weight_count(d)
+    assert e.value.code == dp.DP_ERR_ARG

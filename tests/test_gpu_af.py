@@ -386,3 +386,128 @@ def test_isolated_atoms_keep_their_energy(prec):
     assert np.all(F[-2:] == 0)
     assert np.max(np.abs(ae[-2:] - aeo[-2:])) <= 1e-3 * np.max(np.abs(aeo[-2:])) + 1e-6
     assert np.max(np.abs(F - Fo)) <= TOL_F[prec] * frms(Fo)
+
+
+# ------------------------------------------------------------------ message passing
+MP_MODEL = replace(C.ATTN_MODEL, message_passing=1)
+_mp_oracle_cache = {}
+
+
+def _mp_system():
+    return protein_in_water(2400, 150, (26.8, 26.8, 33.5), 5)
+
+
+def _mp_oracle(model, s, key):
+    if key not in _mp_oracle_cache:
+        _mp_oracle_cache[key] = oracle.af_compute(model, weights(model), s.types, s.coords, s.box)
+    return _mp_oracle_cache[key]
+
+
+@pytest.mark.parametrize("prec", [dp.PREC_PLAIN_F64, dp.PREC_PLAIN_F32])
+def test_message_passing_vs_oracle(prec):
+    """2,400 atoms (protein blob in water, 19 tiles of 128 with a ragged tail):
+    energies, atomic energies, forces and virial against the FP64 oracle."""
+    s = _mp_system()
+    pot, w = make(MP_MODEL, s, prec)
+    E, F, V = pot.compute(s.coords)
+    Eo, aeo, Fo, Vo = _mp_oracle(MP_MODEL, s, "protein2400")
+    fr = frms(Fo)
+    assert abs(E - Eo) <= TOL_E[prec] * abs(Eo)
+    assert np.max(np.abs(F - Fo)) <= TOL_F[prec] * fr
+    assert np.max(np.abs(V - Vo)) <= TOL_F[prec] * np.linalg.norm(Vo)
+    ae = pot.atom_energies()
+    assert np.max(np.abs(ae - aeo)) <= 10 * TOL_E[prec] * np.max(np.abs(aeo)) + 1e-14
+
+
+def test_message_passing_edge_cases_fp64():
+    """A box smaller than rc (own images are neighbours, one atom's slots name
+    the same atom several times) and an isolated atom beside a dimer."""
+    m = replace(MP_MODEL, n_layers=2, nmax=64)
+    s = water_box(2, 5.5, 3, min_oo=2.0)
+    s.types = np.where(s.types == 0, 3, 0).astype(np.int32)
+    pot, w = make(m, s, dp.PREC_PLAIN_F64)
+    E, F, V = pot.compute(s.coords)
+    Eo, _, Fo, Vo = oracle.af_compute(m, w, s.types, s.coords, s.box)
+    assert E == pytest.approx(Eo, rel=1e-11, abs=1e-12)
+    assert np.max(np.abs(F - Fo)) <= 1e-9 * frms(Fo) + 1e-14
+    s = water_box(1, 30.0, 1)
+    s.coords = np.array([[1.0, 1.0, 1.0], [29.5, 2.0, 1.5], [15.0, 15.0, 15.0]])
+    s.types = np.array([3, 0, 1], dtype=np.int32)
+    pot, w = make(m, s, dp.PREC_PLAIN_F64)
+    E, F, V = pot.compute(s.coords)
+    Eo, aeo, Fo, Vo = oracle.af_compute(m, w, s.types, s.coords, s.box)
+    assert E == pytest.approx(Eo, rel=1e-11, abs=1e-12)
+    assert np.max(np.abs(F - Fo)) <= 1e-9 * frms(Fo) + 1e-14
+    assert np.all(F[2] == 0)
+
+
+def test_message_passing_trajectory_does_not_depend_on_rebuild_schedule():
+    """The reverse gather of the message adjoint sums the slots naming an atom
+    in (i, p) order, not in skin-list order: shifted rebuilds change nothing."""
+    m, s = replace(MP_MODEL, n_layers=2), serving_system(700, 9)
+    masses = s.masses
+    v0 = maxwell_boltzmann(masses[s.types], 300.0, C.VELOCITY_SEED)
+    out = []
+    for step0 in (0, 5, 7):
+        pot, _ = make(m, s, dp.PREC_PLAIN_F32, masses=masses)
+        pot.set_state(s.coords, v0, step=step0)
+        pot.step(23, C.DT_FS)
+        out.append(pot.get_state()[:2])
+        pot.close()
+    for x, v in out[1:]:
+        assert np.array_equal(x, out[0][0]) and np.array_equal(v, out[0][1])
+
+
+def _hops_to(k, nj, layers):
+    """Atoms i that reach atom k within `layers` links i -> j of the kept lists."""
+    n = nj.shape[0]
+    src = np.repeat(np.arange(n), nj.shape[1])
+    dst = nj.reshape(-1)
+    keep = dst >= 0
+    src, dst = src[keep], dst[keep]
+    order = np.argsort(dst, kind="stable")
+    src, dst = src[order], dst[order]
+    start = np.searchsorted(dst, np.arange(n + 1))
+    reach = np.zeros(n, bool)
+    reach[k] = True
+    frontier = np.array([k])
+    for _ in range(layers):
+        nxt = np.unique(np.concatenate([src[start[j]:start[j + 1]] for j in frontier]))
+        nxt = nxt[~reach[nxt]]
+        reach[nxt] = True
+        frontier = nxt
+    return reach
+
+
+def test_message_passing_locality_full_size():
+    """24,000 atoms, FP32: moving one atom changes the atomic energy of every
+    atom whose kept lists reach it in one link, and leaves every atom that
+    cannot reach it within L links bit for bit unchanged (the L x rc halo),
+    with the net force zero."""
+    s = C.protein24k()
+    pot, w = make(MP_MODEL, s, dp.PREC_PLAIN_F32)
+    E0, F0, _ = pot.compute(s.coords)
+    ae0 = pot.atom_energies()
+    cnt0, nj0, img0 = pot.neighbours()
+    assert np.max(np.abs(F0.sum(0))) <= 1e-3 * frms(F0) * np.sqrt(s.n)
+    k = s.blob_atoms + 1000
+    x = s.coords.copy()
+    x[k] += np.array([1e-3, -2e-3, 1.5e-3])
+    pot.compute(x)
+    ae1 = pot.atom_energies()
+    cnt1, nj1, _ = pot.neighbours()
+    # links of either evaluation (k may enter or leave a list at the cutoff)
+    both = np.concatenate([nj0, nj1], 1)
+    reach = _hops_to(k, both, MP_MODEL.n_layers)
+    one = np.array([k in set(nj0[i]) and k in set(nj1[i]) for i in range(s.n)])
+    one[k] = True
+    assert np.array_equal(ae1[~reach], ae0[~reach])
+    assert np.all(ae1[one] != ae0[one])
+    assert reach.sum() > one.sum() > 1
+
+
+def test_message_passing_refused_by_the_fused_form():
+    s = C.water64()
+    with pytest.raises(dp.DPError) as e:
+        make(replace(MP_MODEL, nmax=64), s, dp.PREC_FUSED)
+    assert e.value.code == dp.DP_ERR_UNSUPPORTED
