@@ -516,6 +516,24 @@ def report_config(which):
             "member_atom_steps_per_s": int(mask.sum()) / (ms / 1e3),
             "vs_oracle": _err(Fg[mask], Fgo[mask], Eg, Ego)}
         pot.close()
+        # cross-atom message passing (atom channel passed between neighbours
+        # each layer), plain FP32 against the same path without it
+        mm = _replace(m, message_passing=1)
+        wm = normal_blob(oracle.af_weight_count(mm), CF.WEIGHT_SEED)
+        res_mp = {}
+        for name, mdl, wts in (("plain_f32", m, w), ("message_passing_plain_f32", mm, wm)):
+            pot = dp.DeepPotential(dp.model_desc(mdl, dp.PREC_PLAIN_F32, skin=CF.SKIN,
+                                                 rebuild_every=CF.REBUILD_EVERY),
+                                   s.types, s.box, wts, masses=masses, stream=stream)
+            pot.set_state(s.coords, v0, 0)
+            pot.step(2, CF.DT_FS)
+            res_mp[name] = _timed_steps(pot, 5, stream)
+            pot.close()
+        out["message_passing_plain_f32"] = {
+            "ms_per_step": res_mp["message_passing_plain_f32"],
+            "atom_steps_per_s": s.n / (res_mp["message_passing_plain_f32"] / 1e3),
+            "plain_f32_ms_per_step": res_mp["plain_f32"],
+            "overhead": res_mp["message_passing_plain_f32"] / res_mp["plain_f32"] - 1.0}
     elif which == 3:    # graph family at 24,000 atoms
         s, _, masses, v0 = setup_system()
         m = CF.GRAPH_MODEL

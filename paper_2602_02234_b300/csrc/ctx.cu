@@ -369,8 +369,7 @@ static int check_model(const dp_model_desc* desc, const double* weights, size_t 
                 desc->hidden, desc->heads, desc->f1, desc->f2, desc->f3, desc->nmax,
                 desc->rcut, desc->rcut_smth, desc->fit_heads > 1 ? desc->fit_heads : 1,
                 desc->message_passing};
-  if (desc->message_passing && desc->precision == DP_PREC_FUSED)
-    return fail(nullptr, DP_ERR_UNSUPPORTED, "message passing runs in the plain FP32 / FP64 forms");
+
   if (desc->family == DP_FAMILY_ATTENTION && desc->precision == DP_PREC_FUSED &&
       !fused_af_supported(*afd, &why))
     return fail(nullptr, DP_ERR_UNSUPPORTED, why);

@@ -28,8 +28,10 @@
 #include <vector>
 
 #include "common.cuh"
+#include "gemm.cuh"
 #include "kernels.cuh"
 #include "model.h"
+#include "mp.cuh"
 #include "tc.cuh"
 
 namespace dp {
@@ -127,6 +129,16 @@ struct Params {
   const float* dD;                        // [n][128 * m2]
   float* g;                               // [n][nmax][3]
   int* status;
+  // cross-atom message passing: one launch per layer, this one does layers
+  // [lb, le) (without message passing lb = 0, le = n_layers)
+  int mp, lb, le, cap;
+  uint8_t* Gpst;                          // [n][L][32 KB] layer inputs after the message
+  float* Gf32;                            // [n][128][128] FP32 residual stream between launches
+  const float* U;                         // [L][cap][128] tanh(h Wm + bm) of each layer
+  float* hbuf;                            // [n][128] atom channel h
+  float* dG32;                            // [n][128][128] scaled dE/dG' of the layer just done
+  const float* hgrad;                     // [n][128] scaled dE/dh
+  float* accs;                            // [n][128][8] dR~ (4), gate (3), dE/dsw between launches
 };
 
 // ------------------------------------------------------------------ helpers
@@ -603,6 +615,7 @@ __device__ __forceinline__ void softmax_w(const Params& p, const Misc* m, int c,
 // ------------------------------------------------------------------ forward
 // Barriers: mb tensor-core products, wb the W tile (embedding weights, Wo),
 // xb the projection weights.
+template <bool MP>
 __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32_t tb, Bar& mb,
                          Bar& wb, Bar& xb) {
   const int t = threadIdx.x, r = row_id(), pt = part_id();
@@ -617,15 +630,54 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
     return true;
   }
   uint8_t* Gdst = p.Gst + (size_t)atom * (p.n_layers + 1) * kTile;
-  if (!embed_forward(p, sm, m, tb, mb, wb, xb)) return false;
-  if (p.n_layers > 0) load_qkv_weights(p, 0, sm, xb);   // H1, H2 tiles are free again
-  __syncthreads();
-  for (int i = t; i < ngroups * 2048 / 16; i += kThreads)
-    reinterpret_cast<int4*>(Gdst)[i] = reinterpret_cast<const int4*>(sm + SM_G)[i];
+  if (!MP || p.lb == 0) {
+    if (!embed_forward(p, sm, m, tb, mb, wb, xb)) return false;
+    if (p.le > 0) load_qkv_weights(p, 0, sm, xb);   // H1, H2 tiles are free again
+    __syncthreads();
+    for (int i = t; i < ngroups * 2048 / 16; i += kThreads)
+      reinterpret_cast<int4*>(Gdst)[i] = reinterpret_cast<const int4*>(sm + SM_G)[i];
+  } else {   // message passing: the residual stream left by the previous launch
+    load_qkv_weights(p, p.lb, sm, xb);
+    const float* src = p.Gf32 + ((size_t)atom * kW + r) * kW;
+    for (int c = 32 * pt; c < kW; c += kStride) {
+      float g[32];
+#pragma unroll
+      for (int q = 0; q < 32; q += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(src + c + q);
+        g[q] = v.x; g[q + 1] = v.y; g[q + 2] = v.z; g[q + 3] = v.w;
+      }
+      tc::tmem_st32(tb + lo + R2 + c, g);
+    }
+  }
   const bool valid = m->tj[r] >= 0;
   const float2 rj[3] = {make_float2(m->cl[1][r], m->cl[1][r]), make_float2(m->cl[2][r], m->cl[2][r]),
                         make_float2(m->cl[3][r], m->cl[3][r])};
-  for (int l = 0; l < p.n_layers; ++l) {
+  const int jr = MP && r < p.nmax ? p.sel_j[(size_t)atom * p.nmax + r] : -1;
+  const int l_end = MP ? p.le : p.n_layers;
+  for (int l = MP ? p.lb : 0; l < l_end; ++l) {
+    if constexpr (MP) {
+      // message: G' = G + U of the slot's neighbour, into R2 (FP32) and the G
+      // tile (16-bit, also kept for the backward's recomputation)
+      const float* u = p.U + ((size_t)l * p.cap + (jr >= 0 ? jr : 0)) * kW;
+      for (int c = 32 * pt; c < kW; c += kStride) {
+        float g[32];
+        tc::tmem_ld32(tb + lo + R2 + c, g);
+        if (jr >= 0) {
+#pragma unroll
+          for (int q = 0; q < 32; q += 4) {
+            const float4 v = *reinterpret_cast<const float4*>(u + c + q);
+            g[q] += v.x; g[q + 1] += v.y; g[q + 2] += v.z; g[q + 3] += v.w;
+          }
+        }
+        tc::tmem_st32(tb + lo + R2 + c, g);
+        store32(sm + SM_G, r, c, kW, kW, g);
+      }
+      tc::fence_before_sync();
+      __syncthreads();
+      uint8_t* gp = p.Gpst + ((size_t)atom * p.n_layers + l) * kTile;
+      for (int i = t; i < ngroups * 2048 / 16; i += kThreads)
+        reinterpret_cast<int4*>(gp)[i] = reinterpret_cast<const int4*>(sm + SM_G)[i];
+    }
     if (!qkv(p, sm, tb, mb, xb)) return false;
     bulk_load(wb, sm + SM_W, p.WoT + (size_t)l * kTile, kTile);  // lands during the heads
     MMA_GROUP(mb, p.status,
@@ -667,7 +719,7 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
     if (!wb.wait(p.status)) return false;
     MMA_GROUP(mb, p.status, mma_issue(tb + R1, kop(sm + SM_Q, kW), kop(sm + SM_W, kW), kW, kW, false));
     // next layer's projections land in the free Q, K, V tiles during the LayerNorm
-    if (l + 1 < p.n_layers) load_qkv_weights(p, l + 1, sm, xb);
+    if (l + 1 < l_end) load_qkv_weights(p, l + 1, sm, xb);
     // residual + LayerNorm over the row's 128 columns: mean, variance, scale
     const float* bo = p.bo + l * kW;
     float sum = 0.f, sq = 0.f;
@@ -711,6 +763,46 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
     uint8_t* dst = Gdst + (size_t)(l + 1) * kTile;
     for (int i = t; i < ngroups * 2048 / 16; i += kThreads)
       reinterpret_cast<int4*>(dst)[i] = reinterpret_cast<const int4*>(sm + SM_G)[i];
+    if (MP && l + 1 < p.n_layers) {
+      // atom channel: h_i += (1/Nmax) sum_r sw_r G[r][c].  Each warp sums its
+      // 32 rows of its 32 columns by a butterfly (lane q ends with column
+      // c + q), then the four row quarters are added in order.
+      float v[32];
+      tc::tmem_ld32(tb + lo + R2 + 32 * pt, v);
+      const float swr = m->sw[r];
+#pragma unroll
+      for (int q = 0; q < 32; ++q) v[q] *= swr;
+      const int lane = t & 31;
+#pragma unroll
+      for (int w = 16; w >= 1; w >>= 1) {
+        const bool up = (lane & w) != 0;
+#pragma unroll
+        for (int q = 0; q < w; ++q) {
+          const float send = up ? v[q] : v[q + w];
+          const float keep = up ? v[q + w] : v[q];
+          v[q] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+        }
+      }
+      float* xs = reinterpret_cast<float*>(&m->xch[0][0]);   // [row quarter][column]
+      xs[((t >> 5) & 3) * kW + 32 * pt + lane] = v[0];
+      __syncthreads();
+      if (pt == 0)
+        p.hbuf[(size_t)atom * kW + r] += ((xs[r] + xs[kW + r]) + (xs[2 * kW + r] + xs[3 * kW + r])) * p.inv_nmax;
+      __syncthreads();
+    }
+  }
+  if (MP && p.le < p.n_layers) {   // message passing: the next launch continues from R2
+    float* dstf = p.Gf32 + ((size_t)atom * kW + r) * kW;
+    for (int c = 32 * pt; c < kW; c += kStride) {
+      float g[32];
+      tc::tmem_ld32(tb + lo + R2 + c, g);
+#pragma unroll
+      for (int q = 0; q < 32; q += 4)
+        *reinterpret_cast<float4*>(dstf + c + q) = make_float4(g[q], g[q + 1], g[q + 2], g[q + 3]);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    return true;
   }
   // descriptor: T[a][f] = (1/Nmax) sum_j R~[j][a] G[j][f]; feature f = row id,
   // neighbours j split between the parts of a row
@@ -768,13 +860,14 @@ __device__ void kernel_epilogue(Misc* m) {
   if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(m->tptr, 512);
 }
 
+template <bool MP>
 __global__ void __launch_bounds__(kThreads, 1) k_af_fwd(Params p) {
   extern __shared__ __align__(1024) uint8_t sm[];
   Misc* m = reinterpret_cast<Misc*>(sm + SM_MISC);
   kernel_prologue(m);
   Bar mb{&m->bar, 0u}, wb{&m->wbar, 0u}, xb{&m->xbar, 0u};
   for (int atom = p.atom0 + blockIdx.x; atom < p.n; atom += gridDim.x)
-    if (!fwd_atom(p, atom, sm, m, m->tptr, mb, wb, xb)) break;
+    if (!fwd_atom<MP>(p, atom, sm, m, m->tptr, mb, wb, xb)) break;
   kernel_epilogue(m);
 }
 
@@ -782,22 +875,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_af_fwd(Params p) {
 // Adjoint of one atom: dE/dD (from the fitting kernel) back to g_ij.
 // Barriers: mb tensor-core products, gb stored activation tiles, wb and xb
 // weight tiles (xb also dE/dD and T at the start of an atom).
+template <bool MP>
 __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32_t tb, Bar& mb,
                          Bar& wb, Bar& gb, Bar& xb) {
   const int t = threadIdx.x, r = row_id(), pt = part_id();
   const uint32_t lo = lane_base();
   // dE/dD (into the P tile, FP32) and T arrive by bulk copy during the setup
+  const int L = p.n_layers;
+  const bool top = !MP || p.le == L;   // this launch starts at the descriptor
   tc::fence_async_smem();
   __syncthreads();
-  if (t == 0) {
+  if (t == 0 && top) {
     const uint32_t bd = kW * p.m2 * 4, bt = 4 * kW * 4;
     issue_copy(xb, sm + SM_P, p.dD + (size_t)atom * kW * p.m2, bd, bd + bt);
     issue_copy(xb, reinterpret_cast<uint8_t*>(&m->T[0][0]), p.Tm + (size_t)atom * 4 * kW, bt, 0);
   }
   atom_setup(p, atom, m);
   const int ngroups = (m->nvalid + 7) >> 3;
-  const int L = p.n_layers;
   const uint8_t* Gsrc = p.Gst + (size_t)atom * (L + 1) * kTile;
+  const uint8_t* Gpsrc = MP ? p.Gpst + (size_t)atom * L * kTile : Gsrc;
   const bool valid = m->tj[r] >= 0;
   constexpr int DH = kDH;
   const int nv = m->nvalid;
@@ -808,13 +904,38 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
   };
   // ---- descriptor adjoint: dT[a][f] = sum_q dD[f][q] T[a][q] + sum_g dD[g][f] T[a][g]
   // (the second sum for f < m2 only); feature f = row id, the 128-term sum split
-  load_G(sm + SM_G, L, gb);   // the last layer's output, for dG_L below
-  if (!xb.wait(p.status)) return false;
+  if (top) {
+    load_G(sm + SM_G, L, gb);   // the last layer's output, for dG_L below
+    if (!xb.wait(p.status)) return false;
+  }
   if (ngroups == 0) {   // no neighbours: no pair gradients (no copy was issued on gb)
     for (int i = t; i < p.nmax * 3; i += kThreads) p.g[(size_t)atom * p.nmax * 3 + i] = 0.f;
     __syncthreads();
     return true;
   }
+  if (!top) {
+    // message passing: dE/dG' of layer le and the accumulated sums, as the
+    // previous launch left them (the cross-atom step ran in between)
+    const float* src = p.dG32 + ((size_t)atom * kW + r) * kW;
+    for (int c = 32 * pt; c < kW; c += kStride) {
+      float g[32];
+#pragma unroll
+      for (int q = 0; q < 32; q += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(src + c + q);
+        g[q] = v.x; g[q + 1] = v.y; g[q + 2] = v.z; g[q + 3] = v.w;
+      }
+      tc::tmem_st32(tb + lo + R2 + c, g);
+    }
+    if (pt == 0) {
+      const float* a = p.accs + ((size_t)atom * kW + r) * 8;
+      for (int q = 0; q < 4; ++q) m->dRt[r][q] = a[q];
+      for (int q = 0; q < 3; ++q) m->drc[r][q] = a[4 + q];
+      m->dswa[r] = a[7];
+      for (int q = 0; q < 3; ++q)
+        *reinterpret_cast<op_t*>(m->rhb + tc::kmajor_off(q, r, kW)) = f2op(valid ? m->rh[r][q] : 0.f);
+    }
+    __syncthreads();
+  } else {   // descriptor adjoint
   {
     const int f = r;
     const float* dDs = reinterpret_cast<const float*>(sm + SM_P);   // 128 x m2 FP32
@@ -873,9 +994,10 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
             f2op(valid ? m->rh[r][a] : 0.f);
     }
   }
+  }
   const float2 rj[3] = {make_float2(m->cl[1][r], m->cl[1][r]), make_float2(m->cl[2][r], m->cl[2][r]),
                         make_float2(m->cl[3][r], m->cl[3][r])};
-  for (int l = L - 1; l >= 0; --l) {
+  for (int l = (MP ? p.le : L) - 1; l >= (MP ? p.lb : 0); --l) {
     // ---- loads of this layer, all in flight at once: the stored layer input
     // (G tile) and output (V tile) on gb, Wo^T (W tile) on wb, and the Q and
     // K weights (Q and K tiles, overwritten by the recomputed Q and K) on xb
@@ -885,7 +1007,7 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
     __syncthreads();
     if (t == 0) {
       if (ngroups > 0) {
-        issue_copy(gb, sm + SM_G, Gsrc + (size_t)l * kTile, ngroups * 2048, 2 * ngroups * 2048);
+        issue_copy(gb, sm + SM_G, Gpsrc + (size_t)l * kTile, ngroups * 2048, 2 * ngroups * 2048);
         issue_copy(gb, sm + SM_V, Gsrc + (size_t)(l + 1) * kTile, ngroups * 2048, 0);
       }
       issue_copy(wb, sm + SM_W, p.WoR + (size_t)l * kTile, kTile, kTile);
@@ -897,6 +1019,30 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
 #pragma unroll
     for (int h = 0; h < 4; ++h) beta4[h] = p.smx[(((size_t)atom * L + l) * 4 + h) * kW + r];
     if (ngroups > 0 && !gb.wait(p.status)) return false;
+    if (MP && l + 1 < L) {
+      // adjoint of h^{l+1} = h^l + (1/Nmax) sum_r sw_r G_{l+1}[r]: dG_{l+1}[r] +=
+      // (sw_r / Nmax) dh, dE/dsw_r += (1/Nmax) G_{l+1}[r] . dh (G_{l+1} in the V tile)
+      const float sc = m->sw[r] * p.inv_nmax;
+      const float* dhr = p.hgrad + (size_t)atom * kW;
+      float dot = 0.f;
+      for (int c = 32 * pt; c < kW; c += kStride) {
+        float dg[32], go[32];
+        tc::tmem_ld32(tb + lo + R2 + c, dg);
+#pragma unroll
+        for (int q = 0; q < 32; q += 8) load8(sm + SM_V, r, c + q, kW, go + q);
+        float a4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int q = 0; q < 32; q += 4) {
+          const float4 d = *reinterpret_cast<const float4*>(dhr + c + q);
+          dg[q] += sc * d.x; dg[q + 1] += sc * d.y; dg[q + 2] += sc * d.z; dg[q + 3] += sc * d.w;
+          a4[0] += go[q] * d.x; a4[1] += go[q + 1] * d.y; a4[2] += go[q + 2] * d.z; a4[3] += go[q + 3] * d.w;
+        }
+        dot += (a4[0] + a4[1]) + (a4[2] + a4[3]);
+        tc::tmem_st32(tb + lo + R2 + c, dg);
+      }
+      dot = row_sum(m, make_float4(dot, 0.f, 0.f, 0.f)).x;
+      if (pt == 0 && valid) m->dswa[r] += dot * p.inv_nmax;
+    }
     // ---- LayerNorm adjoint: dZ = rstd (dG - mean dG - Gout mean(dG Gout))
     {
       const float rs = p.rstd[((size_t)atom * L + l) * kW + r];
@@ -1114,6 +1260,27 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
               mma_issue(tb + R2, kop(sm + SM_K, kW), kop(sm + SM_G, kW), kW, kW, true);
               mma_issue(tb + R2, kop(sm + SM_V, kW), kop(sm + SM_P, kW), kW, kW, true));
   }
+  if (MP && p.lb > 0) {
+    // message passing: dE/dG' of layer lb and the sums go to the cross-atom
+    // step and the next launch
+    float* dst = p.dG32 + ((size_t)atom * kW + r) * kW;
+    for (int c = 32 * pt; c < kW; c += kStride) {
+      float g[32];
+      tc::tmem_ld32(tb + lo + R2 + c, g);
+#pragma unroll
+      for (int q = 0; q < 32; q += 4)
+        *reinterpret_cast<float4*>(dst + c + q) = make_float4(g[q], g[q + 1], g[q + 2], g[q + 3]);
+    }
+    if (pt == 0) {
+      float* a = p.accs + ((size_t)atom * kW + r) * 8;
+      for (int q = 0; q < 4; ++q) a[q] = m->dRt[r][q];
+      for (int q = 0; q < 3; ++q) a[4 + q] = m->drc[r][q];
+      a[7] = m->dswa[r];
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    return true;
+  }
   // ---- embedding adjoint: dG0 (R2) -> ds.  G0 lands in the G tile while H1
   // (Q tile) and H2 (K tile) are recomputed with weights through W and P.
   load_G(sm + SM_G, 0, gb);
@@ -1221,6 +1388,7 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
   return true;
 }
 
+template <bool MP>
 __global__ void __launch_bounds__(kThreads, 1) k_af_bwd(Params p) {
   extern __shared__ __align__(1024) uint8_t sm[];
   Misc* m = reinterpret_cast<Misc*>(sm + SM_MISC);
@@ -1234,7 +1402,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_af_bwd(Params p) {
   __syncthreads();
   Bar mb{&m->bar, 0u}, wb{&m->wbar, 0u}, gb{&m->pbar, 0u}, xb{&m->xbar, 0u};
   for (int atom = p.atom0 + blockIdx.x; atom < p.n; atom += gridDim.x)
-    if (!bwd_atom(p, atom, sm, m, m->tptr, mb, wb, gb, xb)) break;
+    if (!bwd_atom<MP>(p, atom, sm, m, m->tptr, mb, wb, gb, xb)) break;
   kernel_epilogue(m);
 }
 
@@ -1452,11 +1620,30 @@ class FusedAf : public Model {
     p.sel_j = nv.sel_j;
     p.sel_r = nv.sel_r;
     p.types = types;
+    if (m_.mp) atom0 = 0;   // every atom's previous layer feeds its neighbours
     p.atom0 = atom0;
     const int grid = std::max(1, std::min(n_ - atom0, sms_));
+    const int L = m_.n_layers;
     int k = 0;
-    if (parts & 1) {
-      k_af_fwd<<<grid, kThreads, kSmemAtom, st>>>(p);
+    if ((parts & 1) && m_.mp) {
+      // one launch per layer; U = tanh(h Wm + bm) of every atom in between
+      k_mp_init<float><<<ceil_div((long long)n_ * kW, 256), 256, 0, st>>>(n_, kW, types, mp_Wt_,
+                                                                         p.hbuf);
+      ++k;
+      for (int l = 0; l < L; ++l) {
+        Gemm<float> g = gemm_rowmajor<float>(n_, kW, kW, p.hbuf, kW, mp_Wm_[l], kW,
+                                             mp_U_ + (size_t)l * cap_ * kW, kW);
+        g.bias = mp_bm_[l];
+        g.epi = 1;
+        gemm(g, 1, st);
+        Params q = p;
+        q.lb = l;
+        q.le = l + 1;
+        k_af_fwd<true><<<grid, kThreads, kSmemAtom, st>>>(q);
+        k += 2;
+      }
+    } else if (parts & 1) {
+      k_af_fwd<false><<<grid, kThreads, kSmemAtom, st>>>(p);
       ++k;
     }
     if (parts & 2) {
@@ -1472,8 +1659,32 @@ class FusedAf : public Model {
         ++k;
       }
     }
-    if (parts & 4) {
-      k_af_bwd<<<grid, kThreads, kSmemAtom, st>>>(p);
+    if ((parts & 4) && m_.mp) {
+      // one launch per layer, from the top; between them the message adjoint
+      // dh += ((sum of dE/dG' over the slots naming j) (1 - U_j^2)) Wm^T
+      cudaMemsetAsync(mp_dh_, 0, sizeof(float) * (size_t)n_ * kW, st);
+      for (int l = L - 1; l >= 0; --l) {
+        Params q = p;
+        q.lb = l;
+        q.le = l + 1;
+        k_af_bwd<true><<<grid, kThreads, kSmemAtom, st>>>(q);
+        ++k;
+        if (l == 0) break;
+        int warps = 4;
+        while (warps > 1 && sizeof(int) * 2 * nv.cap * warps > 48 * 1024) --warps;
+        k_mp_gather<float><<<ceil_div(n_, warps), warps * 32, sizeof(int) * 2 * nv.cap * warps, st>>>(
+            n_, m_.nmax, kW, kW, nv.cap, nv.skin, nv.skin_cnt, nv.mirror, nv.selpos, p.dG32,
+            mp_U_ + (size_t)l * cap_ * kW, mp_dq_);
+        Gemm<float> g{};
+        g.M = n_; g.N = kW; g.K = kW;
+        g.A = mp_dq_; g.a_rm = kW; g.a_rk = 1;
+        g.B = mp_Wm_[l]; g.b_rk = 1; g.b_rn = kW;
+        g.C = mp_dh_; g.c_rm = kW; g.c_rn = 1; g.nb2 = 1; g.alpha = 1.f; g.beta = 1.f;
+        gemm(g, 1, st);
+        k += 2;
+      }
+    } else if (parts & 4) {
+      k_af_bwd<false><<<grid, kThreads, kSmemAtom, st>>>(p);
       ++k;
     }
     return k;
@@ -1541,6 +1752,10 @@ class FusedAf : public Model {
   Params base_{};
   FitParams fit_{};
   float* g_ = nullptr;
+  // message passing (FP32): Wt [S][128], per layer Wm [128][128] and bm, U, dh, dq
+  float* mp_Wt_ = nullptr;
+  std::vector<float*> mp_Wm_, mp_bm_;
+  float *mp_U_ = nullptr, *mp_dh_ = nullptr, *mp_dq_ = nullptr;
   std::vector<void*> allocs_;
   size_t bytes_ = 0;
 };
@@ -1562,13 +1777,19 @@ bool FusedAf::init(const AfDims& m, const double* w, int n_atoms, const int* typ
     oW3[t] = off; off += (size_t)E2 * kW;
     ob3[t] = off; off += kW;
   }
-  std::vector<size_t> oq(L), ok(L), ov(L), oo(L), obo(L);
+  size_t oWt = 0;
+  if (m.mp) { oWt = off; off += (size_t)S * kW; }
+  std::vector<size_t> oq(L), ok(L), ov(L), oo(L), obo(L), oWm(L), obm(L);
   for (int l = 0; l < L; ++l) {
     oq[l] = off; off += (size_t)kW * H;
     ok[l] = off; off += (size_t)kW * H;
     ov[l] = off; off += (size_t)kW * H;
     oo[l] = off; off += (size_t)H * kW;
     obo[l] = off; off += kW;
+    if (m.mp) {
+      oWm[l] = off; off += (size_t)kW * kW;
+      obm[l] = off; off += kW;
+    }
   }
   std::vector<size_t> oF1(S), oc1(S), oF2(S), oc2(S), oF3(S), oc3(S), oF4(S), oc4(S);
   for (int t = 0; t < S; ++t) {
@@ -1686,6 +1907,31 @@ bool FusedAf::init(const AfDims& m, const double* w, int n_atoms, const int* typ
   if (!dalloc(&ddD, N * KD, err)) return false;
   p.dD = ddD;
   p.g = g_;
+  p.lb = 0;
+  p.le = L;
+  p.cap = n_atoms;
+  p.mp = m.mp;
+  if (m.mp) {   // message passing: FP32 weights of the atom channel and the between-launch state
+    std::vector<float> Wt(w + oWt, w + oWt + (size_t)S * kW);
+    if (!upload(&mp_Wt_, Wt, err)) return false;
+    mp_Wm_.resize(L);
+    mp_bm_.resize(L);
+    for (int l = 0; l < L; ++l) {
+      std::vector<float> a(w + oWm[l], w + oWm[l] + (size_t)kW * kW), b(w + obm[l], w + obm[l] + kW);
+      if (!upload(&mp_Wm_[l], a, err) || !upload(&mp_bm_[l], b, err)) return false;
+    }
+    float* U = nullptr;
+    float* dh = nullptr;
+    if (!dalloc(&p.Gpst, N * (L > 0 ? L : 1) * kTile, err) || !dalloc(&p.Gf32, N * kW * kW, err) ||
+        !dalloc(&U, (size_t)(L > 0 ? L : 1) * N * kW, err) || !dalloc(&p.hbuf, N * kW, err) ||
+        !dalloc(&p.dG32, N * kW * kW, err) || !dalloc(&dh, N * kW, err) ||
+        !dalloc(&mp_dq_, N * kW, err) || !dalloc(&p.accs, N * kW * 8, err))
+      return false;
+    p.U = U;
+    p.hgrad = dh;
+    mp_U_ = U;
+    mp_dh_ = dh;
+  }
   cudaMemset(p.status, 0, sizeof(int));
   // fitting tiles (capacity for any atom set up to n_atoms): see set_atoms
   FitParams& f = fit_;
@@ -1733,9 +1979,13 @@ bool FusedAf::init(const AfDims& m, const double* w, int n_atoms, const int* typ
     *err = "fused model: fitting tiles upload failed";
     return false;
   }
-  if (cudaFuncSetAttribute(k_af_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemAtom) !=
+  if (cudaFuncSetAttribute(k_af_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemAtom) !=
           cudaSuccess ||
-      cudaFuncSetAttribute(k_af_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemAtom) !=
+      cudaFuncSetAttribute(k_af_bwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemAtom) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_af_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemAtom) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_af_bwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemAtom) !=
           cudaSuccess ||
       cudaFuncSetAttribute(k_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemFit) !=
           cudaSuccess) {

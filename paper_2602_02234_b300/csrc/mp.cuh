@@ -1,0 +1,74 @@
+// Kernels of the cross-atom message passing shared by the plain and fused
+// attention-family paths: the atom channel's initial value and the reverse
+// gather of the message adjoint.
+#pragma once
+
+#include "common.cuh"
+
+namespace dp {
+
+// h_i = Wt[t_i]
+template <typename T>
+__global__ void k_mp_init(int n, int m1, const int* __restrict__ types, const T* __restrict__ Wt,
+                          T* __restrict__ h) {
+  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (long long)n * m1) return;
+  const int i = (int)(q / m1), f = (int)(q % m1);
+  h[q] = Wt[(long long)types[i] * m1 + f];
+}
+
+// dq_j = (sum over the slots (i, p) naming j of dG'_ip) * (1 - U_j^2), slot
+// (i, p) being row i * row_stride + p of dG.  The slots are found through j's
+// skin list and summed in increasing i * nmax + p, so the result does not
+// depend on the order the skin list holds them in.  One warp per atom; shared
+// memory: 2 x cap ints per warp.
+template <typename T>
+__global__ void k_mp_gather(int n, int nmax, int row_stride, int m1, int cap,
+                            const SkinEntry* __restrict__ skin, const int* __restrict__ skin_cnt, const int* __restrict__ mirror,
+                            const short* __restrict__ selpos, const T* __restrict__ dG,
+                            const T* __restrict__ U, T* __restrict__ dq) {
+  extern __shared__ int mp_smem[];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (j >= n) return;
+  int* keys = mp_smem + (size_t)wib * 2 * cap;
+  int* ord = keys + cap;
+  const int cnt = skin_cnt[j];
+  int k = 0;
+  for (int base = 0; base < cnt; base += 32) {
+    const int c = base + lane;
+    bool take = false;
+    int key = 0;
+    if (c < cnt) {
+      const long long e = (long long)j * cap + c;
+      const int i = skin[e].j, cp = mirror[e];
+      if (cp >= 0) {
+        const int p = selpos[(long long)i * cap + cp];
+        if (p >= 0) {
+          take = true;
+          key = i * nmax + p;
+        }
+      }
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, take);
+    if (take) keys[k + __popc(b & ((1u << lane) - 1u))] = key;
+    k += __popc(b);
+  }
+  __syncwarp();
+  for (int q = lane; q < k; q += 32) {
+    const int kq = keys[q];
+    int r = 0;
+    for (int t = 0; t < k; ++t) r += keys[t] < kq ? 1 : 0;
+    const int i = kq / nmax;
+    ord[r] = i * row_stride + (kq - i * nmax);     // the slot's row of dG
+  }
+  __syncwarp();
+  for (int f = lane; f < m1; f += 32) {
+    T acc = T(0);
+    for (int t = 0; t < k; ++t) acc += dG[(long long)ord[t] * m1 + f];
+    const T u = U[(long long)j * m1 + f];
+    dq[(long long)j * m1 + f] = acc * (T(1) - u * u);
+  }
+}
+
+}  // namespace dp

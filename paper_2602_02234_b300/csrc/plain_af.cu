@@ -25,6 +25,7 @@
 #include "common.cuh"
 #include "kernels.cuh"
 #include "gemm.cuh"
+#include "mp.cuh"
 #include "model.h"
 
 namespace dp {
@@ -513,28 +514,22 @@ __global__ void k_zero(long long n, T* __restrict__ p) {
 // message passing between atoms (atom channel h, width m1; one chunk holds
 // every atom so that a layer finishes for all atoms before the next starts)
 // =========================================================================
-// h_i = Wt[t_i]
-template <typename T>
-__global__ void k_mp_init(int n, int m1, const int* __restrict__ types, const T* __restrict__ Wt,
-                          T* __restrict__ h) {
-  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= (long long)n * m1) return;
-  const int i = (int)(q / m1), f = (int)(q % m1);
-  h[q] = Wt[(long long)types[i] * m1 + f];
-}
-
-// G'_ip = G_ip + U_{j(p)} for kept slots; empty slots copy G
+// G'_ip = G_ip + U_{j(p)} for kept slots; empty slots copy G (one warp per slot)
 template <typename T>
 __global__ void k_mp_add(long long rows, int m1, const int* __restrict__ sel_j,
                          const T* __restrict__ G, const T* __restrict__ U, T* __restrict__ Gp) {
-  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= rows * m1) return;
-  const long long row = q / m1;
-  const int f = (int)(q % m1);
+  const long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= rows) return;
   const int j = sel_j[row];
-  T v = G[q];
-  if (j >= 0) v += U[(long long)j * m1 + f];
-  Gp[q] = v;
+  const T* g = G + row * m1;
+  T* o = Gp + row * m1;
+  if (j < 0) {
+    for (int f = lane; f < m1; f += 32) o[f] = g[f];
+  } else {
+    const T* u = U + (long long)j * m1;
+    for (int f = lane; f < m1; f += 32) o[f] = g[f] + u[f];
+  }
 }
 
 // h_i += (1/Nmax) sum_p sw_ip G_ip, slots in increasing order
@@ -570,58 +565,6 @@ __global__ void k_mp_pool_bwd(long long rows, int nmax, int m1, T inv_nmax,
   }
   for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
   if (lane == 0) dsw[row] += dot * inv_nmax;
-}
-
-// dq_j = (sum over the slots (i, p) naming j of dG'_ip) * (1 - U_j^2).  The
-// slots are found through j's skin list and summed in increasing i * nmax + p,
-// so the result does not depend on the order the skin list holds them in.
-// One warp per atom; shared memory: 2 x cap ints per warp.
-template <typename T>
-__global__ void k_mp_gather(int n, int nmax, int m1, int cap, const SkinEntry* __restrict__ skin,
-                            const int* __restrict__ skin_cnt, const int* __restrict__ mirror,
-                            const short* __restrict__ selpos, const T* __restrict__ dG,
-                            const T* __restrict__ U, T* __restrict__ dq) {
-  extern __shared__ int mp_smem[];
-  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int j = blockIdx.x * (blockDim.x >> 5) + wib;
-  if (j >= n) return;
-  int* keys = mp_smem + (size_t)wib * 2 * cap;
-  int* ord = keys + cap;
-  const int cnt = skin_cnt[j];
-  int k = 0;
-  for (int base = 0; base < cnt; base += 32) {
-    const int c = base + lane;
-    bool take = false;
-    int key = 0;
-    if (c < cnt) {
-      const long long e = (long long)j * cap + c;
-      const int i = skin[e].j, cp = mirror[e];
-      if (cp >= 0) {
-        const int p = selpos[(long long)i * cap + cp];
-        if (p >= 0) {
-          take = true;
-          key = i * nmax + p;
-        }
-      }
-    }
-    const unsigned b = __ballot_sync(0xffffffffu, take);
-    if (take) keys[k + __popc(b & ((1u << lane) - 1u))] = key;
-    k += __popc(b);
-  }
-  __syncwarp();
-  for (int q = lane; q < k; q += 32) {
-    const int kq = keys[q];
-    int r = 0;
-    for (int t = 0; t < k; ++t) r += keys[t] < kq ? 1 : 0;
-    ord[r] = kq;
-  }
-  __syncwarp();
-  for (int f = lane; f < m1; f += 32) {
-    T acc = T(0);
-    for (int t = 0; t < k; ++t) acc += dG[(long long)ord[t] * m1 + f];
-    const T u = U[(long long)j * m1 + f];
-    dq[(long long)j * m1 + f] = acc * (T(1) - u * u);
-  }
 }
 
 // =========================================================================
@@ -860,7 +803,7 @@ static int run_impl(PlainAf<T>* P, const NbrView& nv, const int* types, double* 
         g.bias = P->bm[l];
         g.epi = 1;
         gemm(g, 1, st);
-        k_mp_add<T><<<ceil_div((long long)rows * M1, 256), 256, 0, st>>>(
+        k_mp_add<T><<<ceil_div((long long)rows * 32, 256), 256, 0, st>>>(
             rows, M1, sel_j + (long long)a0 * NM, P->G[l], P->U[l], P->Gp);
         gin = P->Gp;
         launches += 2;
@@ -1023,7 +966,7 @@ static int run_impl(PlainAf<T>* P, const NbrView& nv, const int* types, double* 
         int warps = 4;
         while (warps > 1 && sizeof(int) * 2 * nv.cap * warps > 48 * 1024) --warps;
         k_mp_gather<T><<<ceil_div(na, warps), warps * 32, sizeof(int) * 2 * nv.cap * warps, st>>>(
-            na, NM, M1, nv.cap, nv.skin, nv.skin_cnt, nv.mirror, nv.selpos, P->dG, P->U[l], P->dq);
+            na, NM, NM, M1, nv.cap, nv.skin, nv.skin_cnt, nv.mirror, nv.selpos, P->dG, P->U[l], P->dq);
         Gemm<T> g{};
         g.M = na; g.N = M1; g.K = M1;
         g.A = P->dq; g.a_rm = M1; g.a_rk = 1;
