@@ -138,13 +138,16 @@ def af_flops_per_atom(model, n):
     return (emb + L * att_fwd + desc, 2 * fit, emb + L * att_bwd + 2 * desc)
 
 
-def setup_system(which="protein24k"):
+def setup_system(which="protein24k", message_passing=False):
     if which == "small":   # profiling case: same recipe, 4,800 atoms (300-atom blob)
         from synth import cached, protein_in_water
         s = cached(protein_in_water, 4800, 300, (33.74, 33.74, 42.17), CF.SYSTEM_SEED + 1)
     else:
         s = CF.protein24k()
     model = CF.ATTN_MODEL
+    if message_passing:
+        from dataclasses import replace
+        model = replace(model, message_passing=1)
     masses = s.masses
     v0 = maxwell_boltzmann(masses[s.types], 300.0, CF.VELOCITY_SEED)
     return s, model, masses, v0
@@ -251,7 +254,7 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
 
-    s, model, masses, v0 = setup_system(args.system)
+    s, model, masses, v0 = setup_system(args.system, args.message_passing)
     w = normal_blob(dp.weight_count(dp.model_desc(model, dp.PREC_PLAIN_F32)), CF.WEIGHT_SEED)
     stream = torch.cuda.Stream()
 
@@ -341,6 +344,8 @@ def run_ours(args, rank, world, local_rank):
         bound, peak_note = "alu", "FP32 FFMA: 148 SMs x 128 lanes x 2 x 2.032 GHz (derived)"
         kernel_name = "plain network phase (all kernels of one evaluation)"
     achieved = flops / (net_ms / 1e3) / 1e12
+    if args.message_passing:   # every network part is several launches plus cross-atom steps
+        kernel_name += " (message passing: one launch per layer)"
     traffic = NCU_TRAFFIC_PER_ATOM.get(kernel_name)
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
@@ -373,6 +378,7 @@ def run_ours(args, rank, world, local_rank):
             "dtype": "f16" if main_name == "fused_f16" else "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD if args.system == "protein24k" else
                        f"small profiling case ({s.n} atoms)", "n_atoms": s.n, "form": main_name,
+                       "message_passing": bool(args.message_passing),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2: skin/selection lists and pair gradients "
                              "(~0.4 GB per step) exceed the 126 MB L2"},
@@ -383,9 +389,10 @@ def run_ours(args, rank, world, local_rank):
                       "ms_per_step": results[name]["ms"] / K}
     if "fused_f16" in results and "plain_f32" in results:
         line["fused_vs_plain"] = results["plain_f32"]["ms"] / results["fused_f16"]["ms"]
-    if rank == 0 and args.serving > 0 and args.system == "protein24k":
+    plain_model = not args.message_passing
+    if rank == 0 and args.serving > 0 and args.system == "protein24k" and plain_model:
         line["serving"] = serving_bench(args.serving)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.system == "protein24k":
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.system == "protein24k" and plain_model:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -521,19 +528,27 @@ def report_config(which):
         mm = _replace(m, message_passing=1)
         wm = normal_blob(oracle.af_weight_count(mm), CF.WEIGHT_SEED)
         res_mp = {}
-        for name, mdl, wts in (("plain_f32", m, w), ("message_passing_plain_f32", mm, wm)):
-            pot = dp.DeepPotential(dp.model_desc(mdl, dp.PREC_PLAIN_F32, skin=CF.SKIN,
+        for name, mdl, wts, prec, K in (
+                ("plain_f32", m, w, dp.PREC_PLAIN_F32, 5),
+                ("message_passing_plain_f32", mm, wm, dp.PREC_PLAIN_F32, 5),
+                ("fused_f16", m, w, dp.PREC_FUSED, 20),
+                ("message_passing_fused_f16", mm, wm, dp.PREC_FUSED, 20)):
+            pot = dp.DeepPotential(dp.model_desc(mdl, prec, skin=CF.SKIN,
                                                  rebuild_every=CF.REBUILD_EVERY),
                                    s.types, s.box, wts, masses=masses, stream=stream)
             pot.set_state(s.coords, v0, 0)
-            pot.step(2, CF.DT_FS)
-            res_mp[name] = _timed_steps(pot, 5, stream)
+            pot.step(3, CF.DT_FS)
+            res_mp[name] = (_timed_steps(pot, K, stream), pot.compute(s.coords))
             pot.close()
-        out["message_passing_plain_f32"] = {
-            "ms_per_step": res_mp["message_passing_plain_f32"],
-            "atom_steps_per_s": s.n / (res_mp["message_passing_plain_f32"] / 1e3),
-            "plain_f32_ms_per_step": res_mp["plain_f32"],
-            "overhead": res_mp["message_passing_plain_f32"] / res_mp["plain_f32"] - 1.0}
+        for form, base in (("plain_f32", "plain_f32"), ("fused_f16", "fused_f16")):
+            ms = res_mp["message_passing_" + form][0]
+            out["message_passing_" + form] = {
+                "ms_per_step": ms, "atom_steps_per_s": s.n / (ms / 1e3),
+                "without_messages_ms_per_step": res_mp[base][0],
+                "overhead": ms / res_mp[base][0] - 1.0}
+        Emf, Fmf, _ = res_mp["message_passing_fused_f16"][1]
+        Emp, Fmp, _ = res_mp["message_passing_plain_f32"][1]
+        out["message_passing_fused_vs_plain_f32"] = _err(Fmf, Fmp, Emf, Emp)
     elif which == 3:    # graph family at 24,000 atoms
         s, _, masses, v0 = setup_system()
         m = CF.GRAPH_MODEL
@@ -624,6 +639,9 @@ def main():
                     help="requests in the continuous-batching measurement (0: skip)")
     ap.add_argument("--system", choices=["protein24k", "small"], default="protein24k",
                     help="small: 4,800-atom box of the same recipe, for profiler captures")
+    ap.add_argument("--message-passing", action="store_true",
+                    help="the attention family with cross-atom message passing (no serving or "
+                         "CPU-baseline legs: its oracle is a whole-system program)")
     ap.add_argument("--report", default="",
                     help="comma-separated configurations (1-5): accuracy, drift, latency, graph "
                          "family, serving sweep, 100k atoms; one JSON line each, no timing contract")
