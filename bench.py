@@ -42,8 +42,8 @@ FP32_ALU_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # 148 SMs x 128 FP32 lan
 # DRAM bytes (read + write) per atom of one launch, from the ncu captures of the
 # 4,800-atom case (profiles/k_af_*_small_ncu.md); traffic grows with the atoms
 # processed (per-atom tiles, lists, gradients), so a launch over N atoms moves N x this
-NCU_TRAFFIC_PER_ATOM = {"k_af_bwd": (545.728512e6 + 9.657344e6) / 4800,
-                        "k_af_fwd": (13.444096e6 + 452.961536e6) / 4800}
+NCU_TRAFFIC_PER_ATOM = {"k_af_bwd": (545.673728e6 + 9.578496e6) / 4800,
+                        "k_af_fwd": (13.900800e6 + 452.975104e6) / 4800}
 
 
 def peaks():
