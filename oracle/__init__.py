@@ -61,6 +61,12 @@ def _declare(L):
     L.oracle_afmp_compute.restype = C.c_int
     L.oracle_afmp_compute.argtypes = [_PI, _PD, _PD, C.c_int, _PI, _PD, _PD, C.c_int, _PD, _PD,
                                       _PD, _PD]
+    L.oracle_afmp_compute_seeded.restype = C.c_int
+    L.oracle_afmp_compute_seeded.argtypes = [_PI, _PD, _PD, C.c_int, _PI, _PD, _PD, C.c_int, _PD,
+                                             _PD, _PD, _PD, _PD]
+    L.oracle_gf_compute_seeded.restype = C.c_int
+    L.oracle_gf_compute_seeded.argtypes = [_PI, _PD, _PD, C.c_int, _PI, _PD, _PD, C.c_int, _PD,
+                                           _PD, _PD, _PD, _PD]
     L.oracle_switch.restype = None
     L.oracle_switch.argtypes = [C.c_double, C.c_double, C.c_double, _PD, _PD]
     if hasattr(L, "oracle_gf_compute"):
@@ -244,6 +250,33 @@ def af_compute(model, weights, types, coords, box, nthreads=0):
                                  _p(V, _D))
     if rc:
         raise RuntimeError("attention-family oracle failed")
+    return float(E[0]), ae, F, V
+
+
+def compute_seeded(model, weights, types, coords, box, seed, nthreads=0):
+    """E = sum_i seed_i e_i of a layer-coupled model (attention family with
+    message passing, or graph family), its forces -dE/dx on every atom, the
+    atomic energies e_i and the virial.  Atoms with seed 0 are ghosts: they
+    take part as centres and neighbours, their own energy is not counted."""
+    d = model if isinstance(model, dict) else model.as_dict()
+    graph = "node" in d
+    if not graph and not _mp(model):
+        raise ValueError("seeded evaluation covers the layer-coupled models")
+    i, f = _gf_dims(model) if graph else _af_dims(model)
+    w, t, x, b = _c64(weights), _c32(types), _c64(coords), _c64(box)
+    sd = _c64(seed)
+    n = len(t)
+    if len(sd) != n:
+        raise ValueError("one seed per atom")
+    E = np.zeros(1)
+    ae = np.zeros(n)
+    F = np.zeros((n, 3))
+    V = np.zeros((3, 3))
+    fn = lib().oracle_gf_compute_seeded if graph else lib().oracle_afmp_compute_seeded
+    rc = fn(_p(i, _I), _p(f, _D), _p(w, _D), n, _p(t, _I), _p(x, _D), _p(b, _D), int(nthreads),
+            _p(sd, _D), _p(E, _D), _p(ae, _D), _p(F, _D), _p(V, _D))
+    if rc:
+        raise RuntimeError("seeded oracle failed")
     return float(E[0]), ae, F, V
 
 

@@ -297,9 +297,9 @@ static void amp_layer_fwd(const amp_model* m, const amp_weights* W, int l, amp_a
   free(Z);
 }
 
-/* Descriptor and fitting from G^L: e_i, then dE/dG^L into a->dG and
- * dE/dR~ into a->dRt. */
-static void amp_fit(const amp_model* m, const amp_weights* W, int ti, amp_atom* a) {
+/* Descriptor and fitting from G^L: e_i, then seed * de_i/dG^L into a->dG and
+ * seed * de_i/dR~ into a->dRt. */
+static void amp_fit(const amp_model* m, const amp_weights* W, int ti, double seed, amp_atom* a) {
   const int nn = a->nn, M1 = m->m1, M2 = m->m2, L = m->n_layers;
   const int F1 = m->f1, F2 = m->f2, F3 = m->f3, ND = M1 * M2;
   const double inv_nmax = 1.0 / (double)m->nmax;
@@ -339,7 +339,7 @@ static void amp_fit(const amp_model* m, const amp_weights* W, int ti, amp_atom* 
   a->e = e;
   /* backward */
   double *l3 = z_alloc(F3), *l2 = z_alloc(F2), *l1 = z_alloc(F1), *dD = z_alloc(ND);
-  for (int b = 0; b < F3; ++b) l3[b] = W->fW4[ti][b] * (1.0 - y3[b] * y3[b]);
+  for (int b = 0; b < F3; ++b) l3[b] = seed * W->fW4[ti][b] * (1.0 - y3[b] * y3[b]);
   for (int c = 0; c < F2; ++c) {
     double acc = 0;
     for (int b = 0; b < F3; ++b) acc += W->fW3[ti][c * F3 + b] * l3[b];
@@ -503,12 +503,15 @@ static void owrap_all_mp(int n, const double* x, const double* L, double* w) {
     for (int c = 0; c < 3; ++c) w[3 * i + c] = owrap(x[3 * i + c], L[c]);
 }
 
-/* Whole-system energy, atomic energies, forces (n x 3) and virial (3 x 3,
- * row-major); every output but `energy` is nullable.  Sums run in atom order.
- * Returns -1 for an invalid model. */
-int oracle_afmp_compute(const int32_t* idims, const double* fdims, const double* weights, int n,
+/* E = sum_i seed_i e_i (seed NULL: all ones), its forces -dE/dx (n x 3) and
+ * virial (3 x 3, row-major), and the atomic energies e_i; every output but
+ * `energy` is nullable.  Sums run in atom order.  Returns -1 for an invalid
+ * model.  A seed of 0 makes an atom a ghost: it is a centre (its neighbours'
+ * features need it) but its energy is not counted. */
+static int afmp_compute(const int32_t* idims, const double* fdims, const double* weights, int n,
                         const int32_t* types, const double* x, const double* box, int nthreads,
-                        double* energy, double* atom_e, double* forces, double* virial) {
+                        const double* seed, double* energy, double* atom_e, double* forces,
+                        double* virial) {
   amp_model m;
   amp_weights W;
   amp_model_from(idims, fdims, &m);
@@ -569,7 +572,7 @@ int oracle_afmp_compute(const int32_t* idims, const double* fdims, const double*
   }
   /* energies, then the adjoint in reverse */
 #pragma omp parallel for schedule(dynamic, 1)
-  for (int i = 0; i < n; ++i) amp_fit(&m, &W, types[i], &at[i]);
+  for (int i = 0; i < n; ++i) amp_fit(&m, &W, types[i], seed ? seed[i] : 1.0, &at[i]);
   double* dh = z_alloc((size_t)n * M1);     /* dE/dh^{l+1}, then dE/dh^l */
   double* dU = z_alloc((size_t)n * M1);
   for (int l = L - 1; l >= 0; --l) {
@@ -614,7 +617,7 @@ int oracle_afmp_compute(const int32_t* idims, const double* fdims, const double*
   double E = 0, vir[9] = {0};
   if (forces) memset(forces, 0, sizeof(double) * 3 * (size_t)n);
   for (int i = 0; i < n; ++i) {
-    E += at[i].e;
+    E += seed ? seed[i] * at[i].e : at[i].e;
     if (atom_e) atom_e[i] = at[i].e;
     for (int p = 0; p < at[i].nn; ++p) {
       const double* g = pg + ((size_t)i * m.nmax + p) * 3;
@@ -635,4 +638,19 @@ int oracle_afmp_compute(const int32_t* idims, const double* fdims, const double*
   free(U); free(at); free(h); free(dh); free(dU); free(pg); free(w);
   if (have) ocells_free(&cells);
   return 0;
+}
+
+int oracle_afmp_compute(const int32_t* idims, const double* fdims, const double* weights, int n,
+                        const int32_t* types, const double* x, const double* box, int nthreads,
+                        double* energy, double* atom_e, double* forces, double* virial) {
+  return afmp_compute(idims, fdims, weights, n, types, x, box, nthreads, NULL, energy, atom_e,
+                      forces, virial);
+}
+
+int oracle_afmp_compute_seeded(const int32_t* idims, const double* fdims, const double* weights,
+                               int n, const int32_t* types, const double* x, const double* box,
+                               int nthreads, const double* seed, double* energy, double* atom_e,
+                               double* forces, double* virial) {
+  return afmp_compute(idims, fdims, weights, n, types, x, box, nthreads, seed, energy, atom_e,
+                      forces, virial);
 }

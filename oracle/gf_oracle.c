@@ -185,10 +185,13 @@ static void ovecmatT(const double* dy, const double* W, int in, int out, double*
   }
 }
 
-/* Whole-system energy, atomic energies, forces and virial. */
-int oracle_gf_compute(const int32_t* idims, const double* fdims, const double* w, int n,
+/* E = sum_i seed_i e_i (seed NULL: all ones), atomic energies e_i, forces
+ * -dE/dx and virial.  A seed of 0 makes an atom a ghost: its features are
+ * computed (its neighbours need them) but its energy is not counted. */
+static int gf_compute(const int32_t* idims, const double* fdims, const double* w, int n,
                       const int32_t* types, const double* x, const double* box, int nthreads,
-                      double* energy, double* atom_e, double* forces, double* virial) {
+                      const double* seed, double* energy, double* atom_e, double* forces,
+                      double* virial) {
   ogf_model m;
   ogf_offsets o;
   ogf_model_from(idims, fdims, &m);
@@ -375,7 +378,8 @@ int oracle_gf_compute(const int32_t* idims, const double* fdims, const double* w
     double* d3 = malloc(sizeof(double) * F3);
     double* d2 = calloc(F2, sizeof(double));
     double* d1 = calloc(F1, sizeof(double));
-    for (int b = 0; b < F3; ++b) d3[b] = w[o.F4[t] + b] * (1.0 - y3[b] * y3[b]);
+    const double sd = seed ? seed[i] : 1.0;
+    for (int b = 0; b < F3; ++b) d3[b] = sd * w[o.F4[t] + b] * (1.0 - y3[b] * y3[b]);
     ovecmatT(d3, w + o.F3[t], F2, F3, d2);
     for (int b = 0; b < F2; ++b) d2[b] *= 1.0 - y2[b] * y2[b];
     ovecmatT(d2, w + o.F2[t], F1, F2, d1);
@@ -384,7 +388,7 @@ int oracle_gf_compute(const int32_t* idims, const double* fdims, const double* w
     free(y1); free(y2); free(y3); free(d3); free(d2); free(d1);
   }
   double E = 0.0;
-  for (int i = 0; i < n; ++i) E += ae[i];
+  for (int i = 0; i < n; ++i) E += seed ? seed[i] * ae[i] : ae[i];
   if (energy) *energy = E;
   if (atom_e) memcpy(atom_e, ae, sizeof(double) * n);
 
@@ -527,4 +531,19 @@ int oracle_gf_compute(const int32_t* idims, const double* fdims, const double* w
   free(wr); free(cnt); free(nang); free(nbj); free(rv); free(dd); free(sw); free(dsw); free(sa);
   free(dsa); free(sv); free(rh);
   return 0;
+}
+
+int oracle_gf_compute(const int32_t* idims, const double* fdims, const double* w, int n,
+                      const int32_t* types, const double* x, const double* box, int nthreads,
+                      double* energy, double* atom_e, double* forces, double* virial) {
+  return gf_compute(idims, fdims, w, n, types, x, box, nthreads, NULL, energy, atom_e, forces,
+                    virial);
+}
+
+int oracle_gf_compute_seeded(const int32_t* idims, const double* fdims, const double* w, int n,
+                             const int32_t* types, const double* x, const double* box,
+                             int nthreads, const double* seed, double* energy, double* atom_e,
+                             double* forces, double* virial) {
+  return gf_compute(idims, fdims, w, n, types, x, box, nthreads, seed, energy, atom_e, forces,
+                    virial);
 }

@@ -18,8 +18,18 @@ one per rank; a rank
    communication) and sums what it receives.
 
 E is the sum over ranks of the owned energies.  One halo exchange of
-positions and one reverse exchange of forces per evaluation; the graph family
-(receptive field L x rc) would need a halo of L x rc or one exchange per layer.
+positions and one reverse exchange of forces per evaluation.
+
+Layer-coupled models (the attention family with message passing, the graph
+family) reach L neighbour hops: an owned atom's energy depends on atoms up to
+L x rc away, which is why the paper broadens the ghost area to L x rc (Sec.
+III).  With `hops = L` the halo is L x rc; every atom then evaluates as a
+centre (ghosts included, since their features feed the owned atoms') and the
+energy counted is the owned atoms' only (seed 1 for owned, 0 for ghosts), so
+the adjoint gives each local atom its partial force; the reverse exchange is
+the same.  A ghost within L - 1 hops of an owned atom keeps its whole
+neighbour list inside the halo; the outermost ghosts' lists are cut, but
+only their species reach the owned atoms.
 
 The evaluation of a subdomain is a callback (on GPUs a context over owned +
 ghost atoms with the ghosts excluded as centres; in the tests the FP64
@@ -50,14 +60,16 @@ def slab_distance(coords, box, rank, n_ranks, axis=0):
 
 
 class SlabDecomposition:
-    """Slabs along `axis`; ghost halo of width rc."""
+    """Slabs along `axis`; ghost halo of width hops x rc."""
 
-    def __init__(self, box, n_ranks, rank, rc, axis=0):
+    def __init__(self, box, n_ranks, rank, rc, axis=0, hops=1):
         box = np.asarray(box, dtype=np.float64)
-        if n_ranks > 1 and box[axis] / n_ranks < rc:
-            # a neighbour two slabs away would need a second hop of the halo
-            raise ValueError("slabs must be at least rc wide")
+        halo = hops * rc
+        if n_ranks > 1 and box[axis] / n_ranks < halo:
+            # a ghost two slabs away would need a second hop of the exchange
+            raise ValueError("slabs must be at least as wide as the halo (hops x rc)")
         self.box, self.n_ranks, self.rank, self.rc, self.axis = box, n_ranks, rank, rc, axis
+        self.halo = halo
 
     def gather_local(self, dist, ids, coords, types):
         """Owned atoms (global ids, positions, species) in; owned + ghosts out.
@@ -77,7 +89,7 @@ class SlabDecomposition:
         for r, (pi, px, pt) in enumerate(parts):
             if r == self.rank:
                 continue
-            near = slab_distance(px, self.box, self.rank, self.n_ranks, self.axis) < self.rc
+            near = slab_distance(px, self.box, self.rank, self.n_ranks, self.axis) < self.halo
             g_ids.append(pi[near])
             g_x.append(px[near])
             g_t.append(pt[near])
