@@ -133,12 +133,15 @@ struct Params {
   // [lb, le) (without message passing lb = 0, le = n_layers)
   int mp, lb, le, cap;
   uint8_t* Gpst;                          // [n][L][32 KB] layer inputs after the message
-  float* Gf32;                            // [n][128][128] FP32 residual stream between launches
+  // FP32 per-slot state between launches in a row-fastest layout: float4 group
+  // g (columns 4g..4g+3) of slot row r of atom a at float4 index (a * 32 + g) * 128 + r,
+  // so the 32 rows a warp holds move as one contiguous 512-byte access
+  float* Gf32;                            // [n][32][128] float4: residual stream
   const float* U;                         // [L][cap][128] tanh(h Wm + bm) of each layer
   float* hbuf;                            // [n][128] atom channel h
-  float* dG32;                            // [n][128][128] scaled dE/dG' of the layer just done
+  float* dG32;                            // [n][32][128] float4: scaled dE/dG' of the layer just done
   const float* hgrad;                     // [n][128] scaled dE/dh
-  float* accs;                            // [n][128][8] dR~ (4), gate (3), dE/dsw between launches
+  float* accs;                            // [n][8][128] dR~ (4), gate (3), dE/dsw between launches
 };
 
 // ------------------------------------------------------------------ helpers
@@ -638,12 +641,12 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
       reinterpret_cast<int4*>(Gdst)[i] = reinterpret_cast<const int4*>(sm + SM_G)[i];
   } else {   // message passing: the residual stream left by the previous launch
     load_qkv_weights(p, p.lb, sm, xb);
-    const float* src = p.Gf32 + ((size_t)atom * kW + r) * kW;
+    const float4* src = reinterpret_cast<const float4*>(p.Gf32) + (size_t)atom * 32 * kW + r;
     for (int c = 32 * pt; c < kW; c += kStride) {
       float g[32];
 #pragma unroll
       for (int q = 0; q < 32; q += 4) {
-        const float4 v = *reinterpret_cast<const float4*>(src + c + q);
+        const float4 v = src[(size_t)((c + q) >> 2) * kW];
         g[q] = v.x; g[q + 1] = v.y; g[q + 2] = v.z; g[q + 3] = v.w;
       }
       tc::tmem_st32(tb + lo + R2 + c, g);
@@ -792,13 +795,13 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
     }
   }
   if (MP && p.le < p.n_layers) {   // message passing: the next launch continues from R2
-    float* dstf = p.Gf32 + ((size_t)atom * kW + r) * kW;
+    float4* dstf = reinterpret_cast<float4*>(p.Gf32) + (size_t)atom * 32 * kW + r;
     for (int c = 32 * pt; c < kW; c += kStride) {
       float g[32];
       tc::tmem_ld32(tb + lo + R2 + c, g);
 #pragma unroll
       for (int q = 0; q < 32; q += 4)
-        *reinterpret_cast<float4*>(dstf + c + q) = make_float4(g[q], g[q + 1], g[q + 2], g[q + 3]);
+        dstf[(size_t)((c + q) >> 2) * kW] = make_float4(g[q], g[q + 1], g[q + 2], g[q + 3]);
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -916,21 +919,21 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
   if (!top) {
     // message passing: dE/dG' of layer le and the accumulated sums, as the
     // previous launch left them (the cross-atom step ran in between)
-    const float* src = p.dG32 + ((size_t)atom * kW + r) * kW;
+    const float4* src = reinterpret_cast<const float4*>(p.dG32) + (size_t)atom * 32 * kW + r;
     for (int c = 32 * pt; c < kW; c += kStride) {
       float g[32];
 #pragma unroll
       for (int q = 0; q < 32; q += 4) {
-        const float4 v = *reinterpret_cast<const float4*>(src + c + q);
+        const float4 v = src[(size_t)((c + q) >> 2) * kW];
         g[q] = v.x; g[q + 1] = v.y; g[q + 2] = v.z; g[q + 3] = v.w;
       }
       tc::tmem_st32(tb + lo + R2 + c, g);
     }
     if (pt == 0) {
-      const float* a = p.accs + ((size_t)atom * kW + r) * 8;
-      for (int q = 0; q < 4; ++q) m->dRt[r][q] = a[q];
-      for (int q = 0; q < 3; ++q) m->drc[r][q] = a[4 + q];
-      m->dswa[r] = a[7];
+      const float* a = p.accs + (size_t)atom * 8 * kW + r;
+      for (int q = 0; q < 4; ++q) m->dRt[r][q] = a[q * kW];
+      for (int q = 0; q < 3; ++q) m->drc[r][q] = a[(4 + q) * kW];
+      m->dswa[r] = a[7 * kW];
       for (int q = 0; q < 3; ++q)
         *reinterpret_cast<op_t*>(m->rhb + tc::kmajor_off(q, r, kW)) = f2op(valid ? m->rh[r][q] : 0.f);
     }
@@ -1026,19 +1029,22 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
       const float* dhr = p.hgrad + (size_t)atom * kW;
       float dot = 0.f;
       for (int c = 32 * pt; c < kW; c += kStride) {
-        float dg[32], go[32];
-        tc::tmem_ld32(tb + lo + R2 + c, dg);
-#pragma unroll
-        for (int q = 0; q < 32; q += 8) load8(sm + SM_V, r, c + q, kW, go + q);
         float a4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int q = 0; q < 32; q += 4) {
-          const float4 d = *reinterpret_cast<const float4*>(dhr + c + q);
-          dg[q] += sc * d.x; dg[q + 1] += sc * d.y; dg[q + 2] += sc * d.z; dg[q + 3] += sc * d.w;
-          a4[0] += go[q] * d.x; a4[1] += go[q + 1] * d.y; a4[2] += go[q + 2] * d.z; a4[3] += go[q + 3] * d.w;
+        for (int h16 = 0; h16 < 32; h16 += 16) {   // 16 columns at a time (register budget)
+          float dg[16], go[16];
+          tc::tmem_ld16(tb + lo + R2 + c + h16, dg);
+          load8(sm + SM_V, r, c + h16, kW, go);
+          load8(sm + SM_V, r, c + h16 + 8, kW, go + 8);
+#pragma unroll
+          for (int q = 0; q < 16; q += 4) {
+            const float4 d = *reinterpret_cast<const float4*>(dhr + c + h16 + q);
+            dg[q] += sc * d.x; dg[q + 1] += sc * d.y; dg[q + 2] += sc * d.z; dg[q + 3] += sc * d.w;
+            a4[0] += go[q] * d.x; a4[1] += go[q + 1] * d.y; a4[2] += go[q + 2] * d.z; a4[3] += go[q + 3] * d.w;
+          }
+          tc::tmem_st16(tb + lo + R2 + c + h16, dg);
         }
         dot += (a4[0] + a4[1]) + (a4[2] + a4[3]);
-        tc::tmem_st32(tb + lo + R2 + c, dg);
       }
       dot = row_sum(m, make_float4(dot, 0.f, 0.f, 0.f)).x;
       if (pt == 0 && valid) m->dswa[r] += dot * p.inv_nmax;
@@ -1263,19 +1269,19 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
   if (MP && p.lb > 0) {
     // message passing: dE/dG' of layer lb and the sums go to the cross-atom
     // step and the next launch
-    float* dst = p.dG32 + ((size_t)atom * kW + r) * kW;
+    float4* dst = reinterpret_cast<float4*>(p.dG32) + (size_t)atom * 32 * kW + r;
     for (int c = 32 * pt; c < kW; c += kStride) {
       float g[32];
       tc::tmem_ld32(tb + lo + R2 + c, g);
 #pragma unroll
       for (int q = 0; q < 32; q += 4)
-        *reinterpret_cast<float4*>(dst + c + q) = make_float4(g[q], g[q + 1], g[q + 2], g[q + 3]);
+        dst[(size_t)((c + q) >> 2) * kW] = make_float4(g[q], g[q + 1], g[q + 2], g[q + 3]);
     }
     if (pt == 0) {
-      float* a = p.accs + ((size_t)atom * kW + r) * 8;
-      for (int q = 0; q < 4; ++q) a[q] = m->dRt[r][q];
-      for (int q = 0; q < 3; ++q) a[4 + q] = m->drc[r][q];
-      a[7] = m->dswa[r];
+      float* a = p.accs + (size_t)atom * 8 * kW + r;
+      for (int q = 0; q < 4; ++q) a[q * kW] = m->dRt[r][q];
+      for (int q = 0; q < 3; ++q) a[(4 + q) * kW] = m->drc[r][q];
+      a[7 * kW] = m->dswa[r];
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -1672,9 +1678,9 @@ class FusedAf : public Model {
         if (l == 0) break;
         int warps = 4;
         while (warps > 1 && sizeof(int) * 2 * nv.cap * warps > 48 * 1024) --warps;
-        k_mp_gather<float><<<ceil_div(n_, warps), warps * 32, sizeof(int) * 2 * nv.cap * warps, st>>>(
-            n_, m_.nmax, kW, kW, nv.cap, nv.skin, nv.skin_cnt, nv.mirror, nv.selpos, p.dG32,
-            mp_U_ + (size_t)l * cap_ * kW, mp_dq_);
+        k_mp_gather4<<<ceil_div(n_, warps), warps * 32, sizeof(int) * 2 * nv.cap * warps, st>>>(
+            n_, m_.nmax, nv.cap, nv.skin, nv.skin_cnt, nv.mirror, nv.selpos,
+            reinterpret_cast<const float4*>(p.dG32), mp_U_ + (size_t)l * cap_ * kW, mp_dq_);
         Gemm<float> g{};
         g.M = n_; g.N = kW; g.K = kW;
         g.A = mp_dq_; g.a_rm = kW; g.a_rk = 1;
@@ -1911,6 +1917,10 @@ bool FusedAf::init(const AfDims& m, const double* w, int n_atoms, const int* typ
   p.le = L;
   p.cap = n_atoms;
   p.mp = m.mp;
+  if (m.mp && n_atoms > 500000) {   // the gather's 32-bit float4 indices of per-slot state
+    *err = "fused message passing supports at most 500,000 atoms";
+    return false;
+  }
   if (m.mp) {   // message passing: FP32 weights of the atom channel and the between-launch state
     std::vector<float> Wt(w + oWt, w + oWt + (size_t)S * kW);
     if (!upload(&mp_Wt_, Wt, err)) return false;

@@ -71,4 +71,58 @@ __global__ void k_mp_gather(int n, int nmax, int row_stride, int m1, int cap,
   }
 }
 
+// The same sum for 128-wide features stored in the fused kernels' row-fastest
+// layout: float4 group g of slot row p of atom i at (i * 32 + g) * 128 + p.
+// Lane g owns columns 4g..4g+3.  Slots are visited in increasing i * nmax + p.
+__global__ void k_mp_gather4(int n, int nmax, int cap, const SkinEntry* __restrict__ skin,
+                             const int* __restrict__ skin_cnt, const int* __restrict__ mirror,
+                             const short* __restrict__ selpos, const float4* __restrict__ dG,
+                             const float* __restrict__ U, float* __restrict__ dq) {
+  extern __shared__ int mp_smem4[];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (j >= n) return;
+  int* keys = mp_smem4 + (size_t)wib * 2 * cap;
+  int* ord = keys + cap;
+  const int cnt = skin_cnt[j];
+  int k = 0;
+  for (int base = 0; base < cnt; base += 32) {
+    const int c = base + lane;
+    bool take = false;
+    int key = 0;
+    if (c < cnt) {
+      const long long e = (long long)j * cap + c;
+      const int i = skin[e].j, cp = mirror[e];
+      if (cp >= 0) {
+        const int p = selpos[(long long)i * cap + cp];
+        if (p >= 0) {
+          take = true;
+          key = i * nmax + p;
+        }
+      }
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, take);
+    if (take) keys[k + __popc(b & ((1u << lane) - 1u))] = key;
+    k += __popc(b);
+  }
+  __syncwarp();
+  for (int q = lane; q < k; q += 32) {
+    const int kq = keys[q];
+    int r = 0;
+    for (int t = 0; t < k; ++t) r += keys[t] < kq ? 1 : 0;
+    const int i = kq / nmax;
+    ord[r] = i * 32 * 128 + (kq - i * nmax);     // float4 index of the slot's group 0
+  }
+  __syncwarp();
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int t = 0; t < k; ++t) {
+    const float4 v = dG[(long long)ord[t] + lane * 128];
+    acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+  }
+  const float4 u = reinterpret_cast<const float4*>(U + (long long)j * 128)[lane];
+  reinterpret_cast<float4*>(dq + (long long)j * 128)[lane] =
+      make_float4(acc.x * (1.f - u.x * u.x), acc.y * (1.f - u.y * u.y), acc.z * (1.f - u.z * u.z),
+                  acc.w * (1.f - u.w * u.w));
+}
+
 }  // namespace dp
