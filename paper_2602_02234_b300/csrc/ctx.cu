@@ -892,6 +892,9 @@ static size_t bytes_per_atom(const dp_model_desc* d, int cap) {
   size_t nm = d->nmax, L = d->n_layers;
   size_t ctx = 120 + 12 + 16 + 24 + 4 * nm + 12 * nm + 24 * nm + 8 + 72 + (size_t)cap * 22 + 48;
   size_t model = (L + 1) * 32768 + L * 512 + 128 * (size_t)d->m2 * 6 + 2048 + 12 * nm + 8;
+  if (d->fit_heads > 1) model += 8 * (size_t)(d->fit_heads - 1);
+  // message passing: post-message tiles, FP32 stream and dE/dG', U, h, dh, dq, sums
+  if (d->message_passing) model += L * 32768 + 2 * 65536 + L * 512 + 3 * 512 + 4096;
   return ctx + model;
 }
 
@@ -923,6 +926,7 @@ extern "C" int dp_server_create(dp_server** out, const dp_model_desc* desc, cons
   if (budget <= fixed) { g_server_error = "memory budget too small"; return DP_ERR_OOM; }
   long long n_cap = (long long)((budget - fixed) / bytes_per_atom(desc, cap));
   if (max_atoms > 0 && max_atoms < n_cap) n_cap = max_atoms;
+  if (desc->message_passing && n_cap > 500000) n_cap = 500000;   // the fused form's limit
   if (n_cap < 1) { g_server_error = "memory budget too small"; return DP_ERR_OOM; }
   if (n_cap > (1 << 30)) n_cap = 1 << 30;
   std::vector<int> types0((size_t)n_cap, 0);

@@ -74,7 +74,7 @@ __global__ void k_mp_gather(int n, int nmax, int row_stride, int m1, int cap,
 // The same sum for 128-wide features stored in the fused kernels' row-fastest
 // layout: float4 group g of slot row p of atom i at (i * 32 + g) * 128 + p.
 // Lane g owns columns 4g..4g+3.  Slots are visited in increasing i * nmax + p.
-__global__ void k_mp_gather4(int n, int nmax, int cap, const SkinEntry* __restrict__ skin,
+static __global__ void k_mp_gather4(int n, int nmax, int cap, const SkinEntry* __restrict__ skin,
                              const int* __restrict__ skin_cnt, const int* __restrict__ mirror,
                              const short* __restrict__ selpos, const float4* __restrict__ dG,
                              const float* __restrict__ U, float* __restrict__ dq) {

@@ -119,3 +119,14 @@ def test_message_passing_desc_and_weight_count():
     with pytest.raises(dp.DPError) as e:
         dp.weight_count(d)
     assert e.value.code == dp.DP_ERR_ARG
+
+
+def test_library_is_built_from_the_current_sources():
+    """libdp.so must be newer than every source and header under csrc/ (a
+    stale library would test and time old code)."""
+    import glob
+    pkg = os.path.join(ROOT, "paper_2602_02234_b300")
+    lib_path = os.path.join(pkg, "libdp.so")
+    srcs = glob.glob(os.path.join(pkg, "csrc", "*")) + [os.path.join(ROOT, "include", "dp.h")]
+    newest = max(os.path.getmtime(f) for f in srcs)
+    assert os.path.getmtime(lib_path) >= newest, "libdp.so is older than its sources: rebuild"

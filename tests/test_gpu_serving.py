@@ -2,6 +2,8 @@
 in a mix (bitwise: per-atom work and per-system reductions do not depend on the
 batch), equals the single-system dp_step path, admission respects the memory
 capacity, and requests that arrive while others run are admitted at once."""
+from dataclasses import replace
+
 import numpy as np
 import pytest
 
@@ -12,18 +14,20 @@ from synth import configs as C, maxwell_boltzmann, normal_blob, serving_system
 pytestmark = pytest.mark.gpu
 
 M = C.ATTN_MODEL
+M_MP = replace(C.ATTN_MODEL, message_passing=1)
 
 
-def weights():
-    return normal_blob(oracle.af_weight_count(M), C.WEIGHT_SEED)
+def weights(model=M):
+    return normal_blob(oracle.af_weight_count(model), C.WEIGHT_SEED)
 
 
 def masses():
     return serving_system(96, 1).masses
 
 
-def server(**kw):
-    return dp.Server(dp.model_desc(M, dp.PREC_FUSED), weights(), masses(), dt_fs=C.DT_FS, **kw)
+def server(model=M, **kw):
+    return dp.Server(dp.model_desc(model, dp.PREC_FUSED), weights(model), masses(), dt_fs=C.DT_FS,
+                     **kw)
 
 
 def vel(s, seed):
@@ -44,16 +48,20 @@ def run_to_end(srv, ids):
     raise AssertionError("requests did not finish")
 
 
-def test_alone_equals_mixed_and_single_context():
+@pytest.mark.parametrize("model", [M, M_MP], ids=["attention", "message_passing"])
+def test_alone_equals_mixed_and_single_context(model):
+    """With message passing too: an atom's messages come from its own system
+    and the adjoint's reverse sums visit slots in (i, p) order, whatever the
+    batch holds."""
     target = serving_system(320, 3)
     others = [serving_system(n, 10 + n) for n in (96, 700, 1500)]
     v_t = vel(target, 1)
     # alone
-    srv = server(max_slots=8)
+    srv = server(model, max_slots=8)
     alone = run_to_end(srv, {"t": srv.submit(target.types, target.box, target.coords, v_t, 30)})["t"]
     srv.close()
     # in a mix: others already running, one joins later, some leave early
-    srv = server(max_slots=8)
+    srv = server(model, max_slots=8)
     ids = {"o0": srv.submit(others[0].types, others[0].box, others[0].coords, vel(others[0], 2), 12),
            "o1": srv.submit(others[1].types, others[1].box, others[1].coords, vel(others[1], 3), 40)}
     for _ in range(5):
@@ -70,8 +78,8 @@ def test_alone_equals_mixed_and_single_context():
     assert np.array_equal(alone[1], mixed["t"][1])
     assert np.array_equal(alone[2], mixed["t"][2])
     # the same run through a single-system context
-    pot = dp.DeepPotential(dp.model_desc(M, dp.PREC_FUSED), target.types, target.box, weights(),
-                           masses=masses())
+    pot = dp.DeepPotential(dp.model_desc(model, dp.PREC_FUSED), target.types, target.box,
+                           weights(model), masses=masses())
     x, v = target.coords.copy(), v_t.copy()
     tr = pot.step(30, C.DT_FS, coords=x, vel=v, energies=True)
     assert np.max(np.abs(x - alone[0])) < 1e-9
