@@ -52,7 +52,7 @@ enum {
   DP_ERR_TIMEOUT = -4,         /* a device-side wait gave up                 */
   DP_ERR_NONFINITE = -5,       /* energy or forces not finite                */
   DP_ERR_CUDA = -6,            /* a CUDA runtime call failed                 */
-  DP_ERR_UNSUPPORTED = -7      /* valid request this build does not provide  */
+  DP_ERR_UNSUPPORTED = -7      /* valid request the library does not support */
 };
 
 enum { DP_FAMILY_ATTENTION = 0, DP_FAMILY_GRAPH = 1 };
