@@ -110,7 +110,8 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
       if (t == 0) atomicOr(g.status, kFlagTimeout);
       break;
     }
-    // epilogue: thread t owns row m0 + t
+    // epilogue: thread t owns row m0 + t; 16 columns at a time, moved as four
+    // 16-byte accesses (rows are 16-byte aligned: ldc is a multiple of 4 floats)
     const long long m = m0 + t;
     const bool live = m < g.M;
     const long long row = live ? (g.c_rows ? (long long)g.c_rows[m] : m) : 0;
@@ -118,20 +119,36 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
       float v[16];
       tc::tmem_ld16(tb + lane_off + (uint32_t)c, v);
       if (!live) continue;
-      float* Crow = g.C + row * g.ldc + c;
+      float4* Crow = reinterpret_cast<float4*>(g.C + row * g.ldc + c);
+      float cin[16], ax[16];
+      if (g.beta != 0.f)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 u = Crow[q];
+          cin[4 * q] = u.x; cin[4 * q + 1] = u.y; cin[4 * q + 2] = u.z; cin[4 * q + 3] = u.w;
+        }
+      if (g.epi == 2) {
+        const float4* arow = reinterpret_cast<const float4*>(g.aux + row * g.ldc + c);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 u = arow[q];
+          ax[4 * q] = u.x; ax[4 * q + 1] = u.y; ax[4 * q + 2] = u.z; ax[4 * q + 3] = u.w;
+        }
+      }
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         float x = v[q];
         if (g.bias) x += g.bias[c + q];
-        if (g.beta != 0.f) x += g.beta * Crow[q];
+        if (g.beta != 0.f) x += g.beta * cin[q];
         if (g.epi == 1) {
           x = tanhf(x);
         } else if (g.epi == 2) {
-          const float y = g.aux[row * g.ldc + c + q];
-          x *= 1.f - y * y;
+          x *= 1.f - ax[q] * ax[q];
         }
-        Crow[q] = x;
+        v[q] = x;
       }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) Crow[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
     }
     tc::fence_before_sync();
     __syncthreads();          // tensor memory and the A tile are reused by the next tile

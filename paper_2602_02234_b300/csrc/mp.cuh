@@ -1,6 +1,7 @@
-// Kernels of the cross-atom message passing shared by the plain and fused
-// attention-family paths: the atom channel's initial value and the reverse
-// gather of the message adjoint.
+// Kernels shared by the paths whose adjoint gathers per-slot values onto the
+// neighbour atom (cross-atom message passing of the attention family, the
+// graph family's messages): the atom channel's initial value and the reverse
+// gather.
 #pragma once
 
 #include "common.cuh"
@@ -18,10 +19,10 @@ __global__ void k_mp_init(int n, int m1, const int* __restrict__ types, const T*
 }
 
 // dq_j = (sum over the slots (i, p) naming j of dG'_ip) * (1 - U_j^2), slot
-// (i, p) being row i * row_stride + p of dG.  The slots are found through j's
-// skin list and summed in increasing i * nmax + p, so the result does not
-// depend on the order the skin list holds them in.  One warp per atom; shared
-// memory: 2 x cap ints per warp.
+// (i, p) being row i * row_stride + p of dG (U null: the plain sum).  The
+// slots are found through j's skin list and summed in increasing i * nmax + p,
+// so the result does not depend on the order the skin list holds them in.
+// One warp per atom; shared memory: 2 x cap ints per warp.
 template <typename T>
 __global__ void k_mp_gather(int n, int nmax, int row_stride, int m1, int cap,
                             const SkinEntry* __restrict__ skin, const int* __restrict__ skin_cnt, const int* __restrict__ mirror,
@@ -66,8 +67,11 @@ __global__ void k_mp_gather(int n, int nmax, int row_stride, int m1, int cap,
   for (int f = lane; f < m1; f += 32) {
     T acc = T(0);
     for (int t = 0; t < k; ++t) acc += dG[(long long)ord[t] * m1 + f];
-    const T u = U[(long long)j * m1 + f];
-    dq[(long long)j * m1 + f] = acc * (T(1) - u * u);
+    if (U) {
+      const T u = U[(long long)j * m1 + f];
+      acc *= T(1) - u * u;
+    }
+    dq[(long long)j * m1 + f] = acc;
   }
 }
 

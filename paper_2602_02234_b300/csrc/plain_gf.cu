@@ -22,6 +22,7 @@
 
 #include "common.cuh"
 #include "gemm.cuh"
+#include "mp.cuh"
 #include "gemm_tc.cuh"
 #include "kernels.cuh"
 #include "model.h"
@@ -316,31 +317,6 @@ __global__ void k_rowsum(int nmax, int ed, const T* __restrict__ x, T* __restric
   }
 }
 
-// per atom j: sum of x over every kept slot (i, p) whose neighbour is j,
-// visited in skin-list order (deterministic)
-template <typename T>
-__global__ void k_gather_in(int nmax, int ed, int cap, const SkinEntry* __restrict__ skin,
-                            const int* __restrict__ skin_cnt, const int* __restrict__ mirror,
-                            const short* __restrict__ selpos, const T* __restrict__ x,
-                            T* __restrict__ out) {
-  int j = blockIdx.x;
-  int cnt = skin_cnt[j];
-  for (int c = threadIdx.x; c < ed; c += blockDim.x) {
-    __int128 acc = 0;   // skin-list order: summed exactly, see to_fixed
-    bool bad = false;
-    for (int s = 0; s < cnt; ++s) {
-      size_t o = (size_t)j * cap + s;
-      int mc = mirror[o];
-      if (mc < 0) continue;
-      int i = skin[o].j;
-      int p = selpos[(size_t)i * cap + mc];
-      if (p < 0) continue;
-      acc += to_fixed((double)x[((size_t)i * nmax + p) * ed + c], &bad);
-    }
-    out[(size_t)j * ed + c] = bad ? (T)quiet_nan() : (T)from_fixed(acc);
-  }
-}
-
 // (a) per slot: de += (1/nmax) sw dm_i * u_j;  X = (1/nmax) sw dm_i * e (for du_j);
 // dsw += (1/nmax) sum_c dm_i e u_j
 template <typename T>
@@ -441,7 +417,9 @@ class PlainGf : public Model {
     if constexpr (std::is_same<T, float>::value) {
       if (tc_ && g.alpha == 1.f && g.a_rk == 1 && g.c_rn == 1 && (g.b_rn == 1 || g.b_rk == 1) &&
           gemm_tc_shape_ok(g.N, g.K) && g.a_rm % 4 == 0 &&
-          (reinterpret_cast<uintptr_t>(g.A) & 15) == 0) {
+          (reinterpret_cast<uintptr_t>(g.A) & 15) == 0 && g.c_rm % 4 == 0 &&
+          (reinterpret_cast<uintptr_t>(g.C) & 15) == 0 &&
+          (reinterpret_cast<uintptr_t>(g.aux) & 15) == 0) {   // 16-byte rows of A, C, aux
         GemmTc t{};
         t.M = g.M; t.N = g.N; t.K = g.K;
         t.A = g.A; t.lda = g.a_rm; t.a_rows = g.a_rows;
@@ -459,6 +437,15 @@ class PlainGf : public Model {
       }
     }
     gemm(g, 1, st);
+  }
+  // per atom j: the sum of x over every kept slot (i, p) whose neighbour is j,
+  // in increasing (i, p) order whatever the skin list's order
+  void gather_in(const NbrView& nv, const T* x, T* out, cudaStream_t st) {
+    int warps = 4;
+    while (warps > 1 && sizeof(int) * 2 * nv.cap * warps > 48 * 1024) --warps;
+    k_mp_gather<T><<<ceil_div(n_, warps), warps * 32, sizeof(int) * 2 * nv.cap * warps, st>>>(
+        n_, m_.nmax, m_.nmax, m_.ed, nv.cap, nv.skin, nv.skin_cnt, nv.mirror, nv.selpos, x,
+        nullptr, out);
   }
   bool tc_ = false;
   int* flags_ = nullptr;
@@ -707,7 +694,7 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
       mm(g, st);
     }
     k_rowsum<T><<<n, 64, 0, st>>>(NM, Ed, dy_, sdy_);
-    k_gather_in<T><<<n, 64, 0, st>>>(NM, Ed, nv.cap, nv.skin, nv.skin_cnt, nv.mirror, nv.selpos, dy_, gat_);
+    gather_in(nv, dy_, gat_, st);
     k_copy<T><<<grid((long long)n * Nd), 256, 0, st>>>((long long)n * Nd, dn_, dn1_);
     {  // dn1 += sdy Wa^T + gat Wb^T
       Gemm<T> g{};
@@ -732,7 +719,7 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
     k_add_strided<T><<<grid((long long)n * Nd), 256, 0, st>>>(n, Nd, Nd + Ed, dn1_, dnm_, dn_);
     k_msg_bwd<T><<<grid(P * 32), 256, 0, st>>>(P, NM, Ed, Nd + Ed, inv_nmax, nv.sel_j, sw_, ee_[l],
                                                uu_[l], dnm_ + Nd, de_, X_, dsw_e_);
-    k_gather_in<T><<<n, 64, 0, st>>>(NM, Ed, nv.cap, nv.skin, nv.skin_cnt, nv.mirror, nv.selpos, X_, du_);
+    gather_in(nv, X_, du_, st);
     {  // dn += du Wm^T
       Gemm<T> g{};
       g.M = n; g.N = Nd; g.K = Ed;
