@@ -146,16 +146,25 @@ __device__ int n_angle(const T* sa, long long base, int nmax, int na) {
   return k;
 }
 
-// (c) forward: a_ip for the angle slots of one atom (block per atom)
+// (c) forward: a_ip for the angle slots of one atom (block per atom).
+// a_p[c] = sum_l Wphi[l][c] sum_k coef_pkl q_k[c] with coef_pkl = w_pk P_l(c_pk)
+// (0 for k = p), the coefficients and the slots' q rows staged in shared memory.
+// Shared memory: na x na x 4 coefficients, then (staged) na x ed of q.
 template <typename T>
 __global__ void k_angle(int nmax, int na, int ed, T inv_na, const T* __restrict__ sa,
                         const T* __restrict__ rh, const T* __restrict__ q,
-                        const T* __restrict__ Wphi, T* __restrict__ a) {
+                        const T* __restrict__ Wphi, T* __restrict__ a, int staged) {
   extern __shared__ unsigned char sm_raw[];
   T* coef = reinterpret_cast<T*>(sm_raw);  // na x na x 4
   int i = blockIdx.x;
   long long base = (long long)i * nmax;
   int nang = n_angle(sa, base, nmax, na);
+  const T* qs = q + base * ed;
+  if (staged) {
+    T* st = coef + (size_t)na * na * 4;    // na x ed
+    for (int idx = threadIdx.x; idx < nang * ed; idx += blockDim.x) st[idx] = qs[idx];
+    qs = st;
+  }
   for (int pk = threadIdx.x; pk < nang * nang; pk += blockDim.x) {
     int p = pk / nang, k = pk % nang;
     T P[4], dP[4];
@@ -168,15 +177,17 @@ __global__ void k_angle(int nmax, int na, int ed, T inv_na, const T* __restrict_
   __syncthreads();
   for (int idx = threadIdx.x; idx < nmax * ed; idx += blockDim.x) {
     int p = idx / ed, c = idx % ed;
-    T acc = T(0);
-    if (p < nang)
+    T out = T(0);
+    if (p < nang) {
+      T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
       for (int k = 0; k < nang; ++k) {
-        T qk = q[(base + k) * ed + c];
+        const T qk = qs[k * ed + c];
         const T* cf = coef + (p * nang + k) * 4;
-        acc += (Wphi[c] * cf[0] + Wphi[ed + c] * cf[1] + Wphi[2 * ed + c] * cf[2] +
-                Wphi[3 * ed + c] * cf[3]) * qk;
+        s0 += cf[0] * qk; s1 += cf[1] * qk; s2 += cf[2] * qk; s3 += cf[3] * qk;
       }
-    a[(base + p) * ed + c] = acc;
+      out = Wphi[c] * s0 + Wphi[ed + c] * s1 + Wphi[2 * ed + c] * s2 + Wphi[3 * ed + c] * s3;
+    }
+    a[(base + p) * ed + c] = out;
   }
 }
 
@@ -228,49 +239,93 @@ __global__ void k_angle_out_bwd(long long P, int ed, const T* __restrict__ sa,
   if (lane == 0 && s > T(0)) dsa_e[e] += acc;
 }
 
-// (c) adjoint of a_ip: dq, and the switch / unit-vector terms; block per atom
+// (c) adjoint of a_ip: dq, and the switch / unit-vector terms; block per atom.
+// Shared memory: the adjoints dcoef_pkl (na x na x 4); with mode >= 1 also the
+// coefficients coef_pkl = w_pk P_l(c_pk) (0 for k = p), with mode 2 also the
+// angle slots' da and q rows (na rows of ed, stored with stride ed + 1 so that
+// threads on different rows of one column hit different banks).  Mode 0
+// recomputes the coefficients per column (the host picks the largest mode
+// that fits).
 template <typename T>
 __global__ void k_angle_bwd(int nmax, int na, int ed, T inv_na, const T* __restrict__ sa,
                             const T* __restrict__ rh, const T* __restrict__ q,
                             const T* __restrict__ Wphi, const T* __restrict__ da,
-                            T* __restrict__ dq, T* __restrict__ dsa_e, T* __restrict__ drh) {
+                            T* __restrict__ dq, T* __restrict__ dsa_e, T* __restrict__ drh,
+                            int mode) {
   extern __shared__ unsigned char sm_raw[];
   T* dcoef = reinterpret_cast<T*>(sm_raw);  // na x na x 4
+  T* coef = dcoef + (size_t)na * na * 4;    // na x na x 4 (mode >= 1)
   int i = blockIdx.x;
   long long base = (long long)i * nmax;
   int nang = n_angle(sa, base, nmax, na);
-  // dq_k[c] = sum_{p != k} sum_l Wphi[l][c] coef_pkl da_p[c]
+  const T* das = da + base * ed;
+  const T* qs = q + base * ed;
+  int ld = ed;
+  if (mode == 2) {
+    ld = ed + 1;
+    T* s_da = coef + (size_t)na * na * 4;
+    T* s_q = s_da + (size_t)na * ld;
+    for (int idx = threadIdx.x; idx < nang * ed; idx += blockDim.x) {
+      const int p = idx / ed, c = idx - p * ed;
+      s_da[p * ld + c] = das[idx];
+      s_q[p * ld + c] = qs[idx];
+    }
+    das = s_da;
+    qs = s_q;
+  }
+  if (mode >= 1) {
+    for (int pk = threadIdx.x; pk < nang * nang; pk += blockDim.x) {
+      int p = pk / nang, k = pk % nang;
+      T P[4], dP[4];
+      const T* rp = rh + 3 * (base + p);
+      const T* rk = rh + 3 * (base + k);
+      legendre4(rp[0] * rk[0] + rp[1] * rk[1] + rp[2] * rk[2], P, dP);
+      T w = (p == k) ? T(0) : inv_na * sa[base + p] * sa[base + k];
+      for (int l = 0; l < 4; ++l) coef[pk * 4 + l] = w * P[l];
+    }
+  }
+  __syncthreads();
+  // dq_k[c] = sum_l Wphi[l][c] sum_p coef_pkl da_p[c]
   for (int idx = threadIdx.x; idx < nmax * ed; idx += blockDim.x) {
     int k = idx / ed, c = idx % ed;
-    T acc = T(0);
+    T out = T(0);
     if (k < nang) {
+      T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
       const T* rk = rh + 3 * (base + k);
       for (int p = 0; p < nang; ++p) {
-        if (p == k) continue;
-        const T* rp = rh + 3 * (base + p);
-        T P[4], dP[4];
-        legendre4(rp[0] * rk[0] + rp[1] * rk[1] + rp[2] * rk[2], P, dP);
-        T w = inv_na * sa[base + p] * sa[base + k];
-        T f = Wphi[c] * P[0] + Wphi[ed + c] * P[1] + Wphi[2 * ed + c] * P[2] + Wphi[3 * ed + c] * P[3];
-        acc += w * f * da[(base + p) * ed + c];
+        const T d = das[p * ld + c];
+        T cf[4];
+        if (mode >= 1) {
+          for (int l = 0; l < 4; ++l) cf[l] = coef[(p * nang + k) * 4 + l];
+        } else {
+          const T* rp = rh + 3 * (base + p);
+          T P[4], dP[4];
+          legendre4(rp[0] * rk[0] + rp[1] * rk[1] + rp[2] * rk[2], P, dP);
+          const T w = (p == k) ? T(0) : inv_na * sa[base + p] * sa[base + k];
+          for (int l = 0; l < 4; ++l) cf[l] = w * P[l];
+        }
+        s0 += cf[0] * d; s1 += cf[1] * d; s2 += cf[2] * d; s3 += cf[3] * d;
       }
+      out = Wphi[c] * s0 + Wphi[ed + c] * s1 + Wphi[2 * ed + c] * s2 + Wphi[3 * ed + c] * s3;
     }
-    dq[(base + k) * ed + c] = acc;
+    dq[(base + k) * ed + c] = out;
   }
-  // dcoef_pkl = sum_c da_p[c] Wphi[l][c] q_k[c]  (one warp per (p, k))
-  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int pk = warp; pk < nang * nang; pk += nw) {
-    int p = pk / nang, k = pk % nang;
-    T acc[4] = {T(0), T(0), T(0), T(0)};
+  // dcoef_pkl = sum_c da_p[c] Wphi[l][c] q_k[c]  (one thread per (p, k))
+  for (int pk = threadIdx.x; pk < nang * nang; pk += blockDim.x) {
+    const int p = pk / nang, k = pk - p * nang;
+    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
     if (p != k)
-      for (int c = lane; c < ed; c += 32) {
-        T x = da[(base + p) * ed + c] * q[(base + k) * ed + c];
-        for (int l = 0; l < 4; ++l) acc[l] += x * Wphi[l * ed + c];
+      for (int c = 0; c < ed; ++c) {
+        const T x = das[p * ld + c] * qs[k * ld + c];
+        a0 += x * Wphi[c];
+        a1 += x * Wphi[ed + c];
+        a2 += x * Wphi[2 * ed + c];
+        a3 += x * Wphi[3 * ed + c];
       }
-    for (int l = 0; l < 4; ++l) {
-      acc[l] = warp_sum(acc[l]);
-      if (lane == 0) dcoef[pk * 4 + l] = acc[l];
-    }
+    dcoef[pk * 4 + 0] = a0;
+    dcoef[pk * 4 + 1] = a1;
+    dcoef[pk * 4 + 2] = a2;
+    dcoef[pk * 4 + 3] = a3;
   }
   __syncthreads();
   // switch and unit-vector terms, one thread per angle slot p (fixed order)
@@ -449,6 +504,9 @@ class PlainGf : public Model {
   }
   bool tc_ = false;
   int* flags_ = nullptr;
+  // shared-memory variants of the angle kernels (see k_angle, k_angle_bwd)
+  int angle_staged_ = 0, angle_mode_ = 0;
+  size_t angle_smem_ = 0, angle_bwd_smem_ = 0;
 
   template <typename U>
   const U* grad_as() const {
@@ -552,10 +610,17 @@ bool PlainGf<T>::init(const GfDims& m, const double* w, int n_atoms, const int* 
     ok = dalloc(&e1_[l], P * Ed, err) && dalloc(&hh_[l], N * Nd, err) && dalloc(&uu_[l], N * Ed, err) &&
          dalloc(&mm_[l], N * Ed, err) && dalloc(&vv_[l], P * Ed, err) && dalloc(&qq_[l], P * Ed, err) &&
          dalloc(&tt_[l], P * Ed, err);
-  const int angle_smem = (int)(sizeof(T) * m.na * m.na * 4);
+  // the angle kernels stage as much as fits in 227 KB of shared memory
+  const size_t kMaxSmem = 232448, na2 = (size_t)m.na * m.na * 4 * sizeof(T),
+               rowsz = (size_t)m.na * m.ed * sizeof(T), rowsz1 = (size_t)m.na * (m.ed + 1) * sizeof(T);
+  angle_staged_ = na2 + rowsz <= kMaxSmem ? 1 : 0;
+  angle_smem_ = na2 + (angle_staged_ ? rowsz : 0);
+  angle_mode_ = 2 * na2 + 2 * rowsz1 <= kMaxSmem ? 2 : (2 * na2 <= kMaxSmem ? 1 : 0);
+  angle_bwd_smem_ = na2 * (angle_mode_ >= 1 ? 2 : 1) + (angle_mode_ == 2 ? 2 * rowsz1 : 0);
+  const int angle_smem = (int)angle_smem_, angle_bwd_smem = (int)angle_bwd_smem_;
   if (cudaFuncSetAttribute(k_angle<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, angle_smem) !=
           cudaSuccess ||
-      cudaFuncSetAttribute(k_angle_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, angle_smem) !=
+      cudaFuncSetAttribute(k_angle_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, angle_bwd_smem) !=
           cudaSuccess) {
     *err = "graph model: angle kernels cannot get their shared memory";
     return false;
@@ -585,7 +650,7 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
                                      dsw_, sa_, dsa_, s_, rh_);
   k_init<T><<<n, 128, 0, st>>>(n, NM, Nd, Ed, types, nv.sel_j, s_, Wt_, we_, be0_, nn_[0], ee_[0]);
   k += 2;
-  const size_t angle_smem = sizeof(T) * NA * NA * 4;
+  const size_t angle_smem = angle_smem_, angle_bwd_smem = angle_bwd_smem_;
   for (int l = 0; l < L; ++l) {
     // (a)
     mm(gemm_rowmajor<T>(n, Ed, Nd, nn_[l], Nd, Wm_[l], Ed, uu_[l], Ed), st);
@@ -608,7 +673,8 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
                                         e1_[l]);
     // (c)
     mm(gemm_rowmajor<T>((int)P, Ed, Ed, e1_[l], Ed, Wp_[l], Ed, qq_[l], Ed), st);
-    k_angle<T><<<n, 256, angle_smem, st>>>(NM, NA, Ed, inv_na, sa_, rh_, qq_[l], Wphi_[l], aa_);
+    k_angle<T><<<n, 256, angle_smem, st>>>(NM, NA, Ed, inv_na, sa_, rh_, qq_[l], Wphi_[l], aa_,
+                                           angle_staged_);
     {
       Gemm<T> g = gemm_rowmajor<T>((int)P, Ed, Ed, aa_, Ed, Wq_[l], Ed, tt_[l], Ed);
       g.bias = bq_[l];
@@ -672,8 +738,8 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
       g.C = da_; g.c_rm = Ed; g.c_rn = 1; g.nb2 = 1; g.alpha = T(1);
       mm(g, st);
     }
-    k_angle_bwd<T><<<n, 256, angle_smem, st>>>(NM, NA, Ed, inv_na, sa_, rh_, qq_[l], Wphi_[l], da_,
-                                               dq_, dsa_e_, drh_);
+    k_angle_bwd<T><<<n, 256, angle_bwd_smem, st>>>(NM, NA, Ed, inv_na, sa_, rh_, qq_[l], Wphi_[l], da_,
+                                                   dq_, dsa_e_, drh_, angle_mode_);
     {  // de1 += dq Wp^T
       Gemm<T> g{};
       g.M = (int)P; g.N = Ed; g.K = Ed;
