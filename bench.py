@@ -37,6 +37,9 @@ from synth import configs as CF, maxwell_boltzmann, normal_blob  # noqa: E402
 WORKLOAD = ("protein-in-water 24,000 atoms (1,500-atom blob + 7,500 H2O, 57.69x57.69x72.11 A), "
             "attention family: embedding 1-32-64-128, 3 attention layers (H 128, 4 heads), "
             "axis 16, fitting 2048-240-240-240-1, rc 6 A, nmax 120; NVE dt 0.5 fs, rebuild every 10")
+GRAPH_WORKLOAD = ("protein-in-water 24,000 atoms (same system), graph family: node 128, edge 64, "
+                  "6 layers, angle channel 40 nearest within 4 A, fitting 128-240-240-240-1, "
+                  "rc 6 A, nmax 120; NVE dt 0.5 fs, rebuild every 10")
 METRIC = "energy+force atom-steps/s"
 FP32_ALU_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # 148 SMs x 128 FP32 lanes x FMA x 2.032 GHz
 # DRAM bytes (read + write) per atom of one launch, from the ncu captures of the
@@ -138,13 +141,13 @@ def af_flops_per_atom(model, n):
     return (emb + L * att_fwd + desc, 2 * fit, emb + L * att_bwd + 2 * desc)
 
 
-def setup_system(which="protein24k", message_passing=False):
+def setup_system(which="protein24k", message_passing=False, family="attention"):
     if which == "small":   # profiling case: same recipe, 4,800 atoms (300-atom blob)
         from synth import cached, protein_in_water
         s = cached(protein_in_water, 4800, 300, (33.74, 33.74, 42.17), CF.SYSTEM_SEED + 1)
     else:
         s = CF.protein24k()
-    model = CF.ATTN_MODEL
+    model = CF.GRAPH_MODEL if family == "graph" else CF.ATTN_MODEL
     if message_passing:
         from dataclasses import replace
         model = replace(model, message_passing=1)
@@ -254,7 +257,8 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
 
-    s, model, masses, v0 = setup_system(args.system, args.message_passing)
+    graph = args.family == "graph"
+    s, model, masses, v0 = setup_system(args.system, args.message_passing, args.family)
     w = normal_blob(dp.weight_count(dp.model_desc(model, dp.PREC_PLAIN_F32)), CF.WEIGHT_SEED)
     stream = torch.cuda.Stream()
 
@@ -264,9 +268,10 @@ def run_ours(args, rank, world, local_rank):
                                 s.types, s.box, w, masses=masses, stream=stream)
 
     forms = []
+    fused_name = "mixed_tc_f16" if graph else "fused_f16"
     if args.form in ("auto", "fused"):
         try:
-            forms.append(("fused_f16", make(dp.PREC_FUSED)))
+            forms.append((fused_name, make(dp.PREC_FUSED)))
         except dp.DPError as e:
             if args.form == "fused":
                 raise
@@ -309,7 +314,7 @@ def run_ours(args, rank, world, local_rank):
     # the dominant kernel alone, timed with events on the stream it runs on
     cnt, _, _ = pot.neighbours()
     nreal = np.minimum(cnt, model.nmax)
-    parts = np.array([af_flops_per_atom(model, int(k)) for k in nreal]).sum(0)
+    parts = None if graph else np.array([af_flops_per_atom(model, int(k)) for k in nreal]).sum(0)
     reps = 5
 
     def time_network(part_mask):
@@ -325,7 +330,24 @@ def run_ours(args, rank, world, local_rank):
         return e0.elapsed_time(e1) / reps
 
     pk, pk_kind = peaks()
-    if main_name == "fused_f16":
+    if graph:
+        # memory-bound: the edge features (pairs x Ed FP32) must be read and written
+        # once per layer in the forward and their adjoint once per layer in the
+        # backward, a floor under every evaluation's DRAM traffic
+        net_ms = time_network(0)
+        kernel_ms = {"network": net_ms}
+        alg_bytes = float(model.n_layers * 4 * int(nreal.sum()) * model.edge * 4)
+        achieved = alg_bytes / (net_ms / 1e3) / 1e9
+        peak = pk.get("hbm_gbs", 6400.0)
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "kernel": "graph network phase (all kernels of one evaluation)",
+                    "peak_kind": f"HBM copy bandwidth ({pk_kind})",
+                    "algorithmic_bytes_per_launch": alg_bytes,
+                    "algorithmic_bytes_note": "L x 4 x pairs x Ed x 4 B: edge features read and "
+                                              "written per layer, forward and backward",
+                    "launch_ms": net_ms, "kernel_ms": kernel_ms}
+    elif main_name == "fused_f16":
         kernel_ms = {name: time_network(mask) for name, mask in
                      (("k_af_fwd", 1), ("k_fit", 2), ("k_af_bwd", 4))}
         dominant = max(kernel_ms, key=kernel_ms.get)
@@ -343,17 +365,18 @@ def run_ours(args, rank, world, local_rank):
         peak = FP32_ALU_PEAK_TFLOPS
         bound, peak_note = "alu", "FP32 FFMA: 148 SMs x 128 lanes x 2 x 2.032 GHz (derived)"
         kernel_name = "plain network phase (all kernels of one evaluation)"
-    achieved = flops / (net_ms / 1e3) / 1e12
-    if args.message_passing:   # every network part is several launches plus cross-atom steps
-        kernel_name += " (message passing: one launch per layer)"
-    traffic = NCU_TRAFFIC_PER_ATOM.get(kernel_name)
-    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak,
-                "traffic": traffic * s.n if traffic and args.system == "protein24k" else None,
-                "traffic_note": "DRAM bytes per launch, scaled from the 4,800-atom ncu capture",
-                "kernel": kernel_name,
-                "peak_kind": peak_note, "algorithmic_flop_per_launch": flops,
-                "launch_ms": net_ms, "kernel_ms": kernel_ms}
+    if not graph:
+        achieved = flops / (net_ms / 1e3) / 1e12
+        if args.message_passing:   # every network part is several launches plus cross-atom steps
+            kernel_name += " (message passing: one launch per layer)"
+        traffic = NCU_TRAFFIC_PER_ATOM.get(kernel_name)
+        roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak,
+                    "traffic": traffic * s.n if traffic and args.system == "protein24k" else None,
+                    "traffic_note": "DRAM bytes per launch, scaled from the 4,800-atom ncu capture",
+                    "kernel": kernel_name,
+                    "peak_kind": peak_note, "algorithmic_flop_per_launch": flops,
+                    "launch_ms": net_ms, "kernel_ms": kernel_ms}
 
     # end to end through the C ABI with pinned host buffers, copies every step
     xh = torch.empty((s.n, 3), dtype=torch.float64, pin_memory=True).numpy()
@@ -375,9 +398,12 @@ def run_ours(args, rank, world, local_rank):
     line = {"metric": METRIC, "value": value, "unit": "atom-steps/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": main["ms"] / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f16" if main_name == "fused_f16" else "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD if args.system == "protein24k" else
+            "dtype": "f16" if main_name in ("fused_f16", "mixed_tc_f16") else "f32",
+            "data": "synthetic",
+            "config": {"workload": (GRAPH_WORKLOAD if graph else WORKLOAD)
+                       if args.system == "protein24k" else
                        f"small profiling case ({s.n} atoms)", "n_atoms": s.n, "form": main_name,
+                       "family": args.family,
                        "message_passing": bool(args.message_passing),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2: skin/selection lists and pair gradients "
@@ -387,9 +413,9 @@ def run_ours(args, rank, world, local_rank):
     for name in results:
         line[name] = {"value": job_throughput(s.n * K, world, results[name]["ms"] / 1e3),
                       "ms_per_step": results[name]["ms"] / K}
-    if "fused_f16" in results and "plain_f32" in results:
-        line["fused_vs_plain"] = results["plain_f32"]["ms"] / results["fused_f16"]["ms"]
-    plain_model = not args.message_passing
+    if fused_name in results and "plain_f32" in results:
+        line["fused_vs_plain"] = results["plain_f32"]["ms"] / results[fused_name]["ms"]
+    plain_model = not args.message_passing and not graph
     if rank == 0 and args.serving > 0 and args.system == "protein24k" and plain_model:
         line["serving"] = serving_bench(args.serving)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.system == "protein24k" and plain_model:
@@ -639,6 +665,9 @@ def main():
                     help="requests in the continuous-batching measurement (0: skip)")
     ap.add_argument("--system", choices=["protein24k", "small"], default="protein24k",
                     help="small: 4,800-atom box of the same recipe, for profiler captures")
+    ap.add_argument("--family", choices=["attention", "graph"], default="attention",
+                    help="graph: the graph family's step (mixed tensor-core form and plain FP32; "
+                         "no serving or CPU-baseline legs)")
     ap.add_argument("--message-passing", action="store_true",
                     help="the attention family with cross-atom message passing (no serving or "
                          "CPU-baseline legs: its oracle is a whole-system program)")

@@ -30,6 +30,13 @@
 namespace dp {
 namespace gf {
 
+// slot of element idx of a (slots x ed) array: a shift when ed is a power of
+// two (ed_shift >= 0), else a division
+__device__ __forceinline__ long long slot_of(long long idx, int ed, int ed_shift) {
+  return ed_shift >= 0 ? (idx >> ed_shift) : idx / ed;
+}
+
+
 // ------------------------------------------------------------------ kernels
 // geometry of every slot: distance, switches, s = sw/r, unit vector
 template <typename T>
@@ -107,14 +114,14 @@ __global__ void k_copy(long long n, const T* __restrict__ a, T* __restrict__ out
 
 // (b): v = tanh(A_i + B_j + C_e + be), e1 = e + v on real slots
 template <typename T>
-__global__ void k_edge(long long P, int nmax, int ed, const int* __restrict__ sel_j,
+__global__ void k_edge(long long P, int nmax, int ed, int ed_shift, const int* __restrict__ sel_j,
                        const T* __restrict__ Ai, const T* __restrict__ Bj,
                        const T* __restrict__ Ce, const T* __restrict__ be,
                        const T* __restrict__ e_in, T* __restrict__ v, T* __restrict__ e1) {
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= P * ed) return;
-  long long e = idx / ed;
-  int c = (int)(idx % ed);
+  long long e = slot_of(idx, ed, ed_shift);
+  int c = (int)(idx - e * ed);
   int j = sel_j[e];
   if (j < 0) {
     v[idx] = T(0);
@@ -193,11 +200,11 @@ __global__ void k_angle(int nmax, int na, int ed, T inv_na, const T* __restrict_
 
 // e_out = e1 + swa * t on angle slots
 template <typename T>
-__global__ void k_angle_out(long long P, int ed, const T* __restrict__ sa, const T* __restrict__ e1,
-                            const T* __restrict__ t, T* __restrict__ out) {
+__global__ void k_angle_out(long long P, int ed, int ed_shift, const T* __restrict__ sa,
+                            const T* __restrict__ e1, const T* __restrict__ t, T* __restrict__ out) {
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= P * ed) return;
-  out[idx] = e1[idx] + sa[idx / ed] * t[idx];
+  out[idx] = e1[idx] + sa[slot_of(idx, ed, ed_shift)] * t[idx];
 }
 
 // e_i = y3 . F4 + c4 (FP64) and delta3
@@ -548,7 +555,7 @@ class PlainGf : public Model {
   T *Ai_, *Bj_, *Ce_, *aa_;
   T *y1_, *y2_, *y3_, *d1_, *d2_, *d3_;
   // adjoint
-  T *dn_, *dn1_, *de_, *de1_, *dy_, *dz_, *da_, *dq_, *du_, *dx_, *dnm_, *X_, *sdy_, *gat_;
+  T *dn_, *dn1_, *de_, *dy_, *dz_, *da_, *dq_, *du_, *dx_, *dnm_, *X_, *sdy_, *gat_;
   T *dsw_e_, *dsa_e_, *drh_, *g_;
   std::vector<void*> allocs_;
   size_t bytes_ = 0;
@@ -629,7 +636,7 @@ bool PlainGf<T>::init(const GfDims& m, const double* w, int n_atoms, const int* 
        dalloc(&aa_, P * Ed, err) && dalloc(&y1_, N * m.f1, err) && dalloc(&y2_, N * m.f2, err) &&
        dalloc(&y3_, N * m.f3, err) && dalloc(&d1_, N * m.f1, err) && dalloc(&d2_, N * m.f2, err) &&
        dalloc(&d3_, N * m.f3, err) && dalloc(&dn_, N * Nd, err) && dalloc(&dn1_, N * Nd, err) &&
-       dalloc(&de_, P * Ed, err) && dalloc(&de1_, P * Ed, err) && dalloc(&dy_, P * Ed, err) &&
+       dalloc(&de_, P * Ed, err) && dalloc(&dy_, P * Ed, err) &&
        dalloc(&dz_, P * Ed, err) && dalloc(&da_, P * Ed, err) && dalloc(&dq_, P * Ed, err) &&
        dalloc(&du_, N * Ed, err) && dalloc(&dx_, N * Nd, err) && dalloc(&dnm_, N * (Nd + Ed), err) &&
        dalloc(&X_, P * Ed, err) && dalloc(&sdy_, N * Ed, err) && dalloc(&gat_, N * Ed, err) &&
@@ -651,6 +658,7 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
   k_init<T><<<n, 128, 0, st>>>(n, NM, Nd, Ed, types, nv.sel_j, s_, Wt_, we_, be0_, nn_[0], ee_[0]);
   k += 2;
   const size_t angle_smem = angle_smem_, angle_bwd_smem = angle_bwd_smem_;
+  const int ed_shift = (Ed & (Ed - 1)) == 0 ? __builtin_ctz((unsigned)Ed) : -1;
   for (int l = 0; l < L; ++l) {
     // (a)
     mm(gemm_rowmajor<T>(n, Ed, Nd, nn_[l], Nd, Wm_[l], Ed, uu_[l], Ed), st);
@@ -669,8 +677,8 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
     mm(gemm_rowmajor<T>(n, Ed, Nd, nn_[l + 1], Nd, Wa_[l], Ed, Ai_, Ed), st);
     mm(gemm_rowmajor<T>(n, Ed, Nd, nn_[l + 1], Nd, Wb_[l], Ed, Bj_, Ed), st);
     mm(gemm_rowmajor<T>((int)P, Ed, Ed, ee_[l], Ed, Wc_[l], Ed, Ce_, Ed), st);
-    k_edge<T><<<grid(PE), 256, 0, st>>>(P, NM, Ed, nv.sel_j, Ai_, Bj_, Ce_, be_[l], ee_[l], vv_[l],
-                                        e1_[l]);
+    k_edge<T><<<grid(PE), 256, 0, st>>>(P, NM, Ed, ed_shift, nv.sel_j, Ai_, Bj_, Ce_, be_[l], ee_[l],
+                                        vv_[l], e1_[l]);
     // (c)
     mm(gemm_rowmajor<T>((int)P, Ed, Ed, e1_[l], Ed, Wp_[l], Ed, qq_[l], Ed), st);
     k_angle<T><<<n, 256, angle_smem, st>>>(NM, NA, Ed, inv_na, sa_, rh_, qq_[l], Wphi_[l], aa_,
@@ -681,7 +689,7 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
       g.epi = 1;
       mm(g, st);
     }
-    k_angle_out<T><<<grid(PE), 256, 0, st>>>(P, Ed, sa_, e1_[l], tt_[l], ee_[l + 1]);
+    k_angle_out<T><<<grid(PE), 256, 0, st>>>(P, Ed, ed_shift, sa_, e1_[l], tt_[l], ee_[l + 1]);
     k += 14;
   }
   // fitting
@@ -727,8 +735,7 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
   k_fill<T><<<grid(3 * P), 256, 0, st>>>(3 * P, T(0), drh_);
   k += 5;
   for (int l = L - 1; l >= 0; --l) {
-    // (c)
-    k_copy<T><<<grid(PE), 256, 0, st>>>(PE, de_, de1_);
+    // (c): de holds dE/de_{l+1}; it becomes dE/de1 in place (e_{l+1} = e1 + swa t)
     k_angle_out_bwd<T><<<grid(P * 32), 256, 0, st>>>(P, Ed, sa_, tt_[l], de_, dz_, dsa_e_);
     {  // da = dz Wq^T
       Gemm<T> g{};
@@ -740,17 +747,16 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
     }
     k_angle_bwd<T><<<n, 256, angle_bwd_smem, st>>>(NM, NA, Ed, inv_na, sa_, rh_, qq_[l], Wphi_[l], da_,
                                                    dq_, dsa_e_, drh_, angle_mode_);
-    {  // de1 += dq Wp^T
+    {  // de1 = de + dq Wp^T, in place
       Gemm<T> g{};
       g.M = (int)P; g.N = Ed; g.K = Ed;
       g.A = dq_; g.a_rm = Ed; g.a_rk = 1;
       g.B = Wp_[l]; g.b_rk = 1; g.b_rn = Ed;
-      g.C = de1_; g.c_rm = Ed; g.c_rn = 1; g.nb2 = 1; g.alpha = T(1); g.beta = T(1);
+      g.C = de_; g.c_rm = Ed; g.c_rn = 1; g.nb2 = 1; g.alpha = T(1); g.beta = T(1);
       mm(g, st);
     }
-    // (b)
-    k_dtanh<T><<<grid(PE), 256, 0, st>>>(PE, de1_, vv_[l], dy_);
-    k_copy<T><<<grid(PE), 256, 0, st>>>(PE, de1_, de_);
+    // (b): de now holds dE/de1; it becomes dE/de_l (e1 = e_l + tanh(...))
+    k_dtanh<T><<<grid(PE), 256, 0, st>>>(PE, de_, vv_[l], dy_);
     {  // de += dy Wc^T
       Gemm<T> g{};
       g.M = (int)P; g.N = Ed; g.K = Ed;
