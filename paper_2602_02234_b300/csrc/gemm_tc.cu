@@ -71,24 +71,41 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
   uint32_t phase = 0;
   for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const long long m0 = (long long)tile * kRows;
-    // A tile: 128 rows x K, coalesced float4 reads -> 16-bit core-matrix layout
-    for (int i = t; i < kRows * k4; i += kRows) {
-      const int r = i / k4, c = (i - r * k4) << 2;
-      const long long m = m0 + r;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (m < g.M) {
-        const long long row = g.a_rows ? (long long)g.a_rows[m] : m;
-        v = *reinterpret_cast<const float4*>(g.A + row * g.lda + c);
+    // A tile: 128 rows x K, coalesced float4 reads -> 16-bit core-matrix layout;
+    // each thread issues kLoads reads before converting any, so that enough
+    // bytes are in flight to keep HBM busy
+    constexpr int kLoads = 16;
+    const int total = kRows * k4;
+    for (int base = 0; base < total; base += kRows * kLoads) {
+      float4 v[kLoads];
+#pragma unroll
+      for (int u = 0; u < kLoads; ++u) {
+        const int i = base + u * kRows + t;
+        v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < total) {
+          const int r = i / k4, c = (i - r * k4) << 2;
+          const long long m = m0 + r;
+          if (m < g.M) {
+            const long long row = g.a_rows ? (long long)g.a_rows[m] : m;
+            v[u] = *reinterpret_cast<const float4*>(g.A + row * g.lda + c);
+          }
+        }
       }
-      uint2 u;
-      if (g.fp16) {
-        u.x = tc::pack_f16(v.x, v.y);
-        u.y = tc::pack_f16(v.z, v.w);
-      } else {
-        u.x = tc::pack_bf16(v.x, v.y);
-        u.y = tc::pack_bf16(v.z, v.w);
+#pragma unroll
+      for (int u = 0; u < kLoads; ++u) {
+        const int i = base + u * kRows + t;
+        if (i >= total) break;
+        const int r = i / k4, c = (i - r * k4) << 2;
+        uint2 w;
+        if (g.fp16) {
+          w.x = tc::pack_f16(v[u].x, v[u].y);
+          w.y = tc::pack_f16(v[u].z, v[u].w);
+        } else {
+          w.x = tc::pack_bf16(v[u].x, v[u].y);
+          w.y = tc::pack_bf16(v[u].z, v[u].w);
+        }
+        *reinterpret_cast<uint2*>(As + tc::kmajor_off(r, c, g.K)) = w;
       }
-      *reinterpret_cast<uint2*>(As + tc::kmajor_off(r, c, g.K)) = u;
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
