@@ -335,11 +335,14 @@ __global__ void k_angle_bwd(int nmax, int na, int ed, T inv_na, const T* __restr
     dcoef[pk * 4 + 3] = a3;
   }
   __syncthreads();
-  // switch and unit-vector terms, one thread per angle slot p (fixed order)
-  for (int p = threadIdx.x; p < nang; p += blockDim.x) {
+  // switch and unit-vector terms: one warp per angle slot p, lanes over the
+  // partners k, then a fixed-order warp reduction
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int p = warp; p < nang; p += nw) {
     const T* rp = rh + 3 * (base + p);
+    const T sp = sa[base + p];
     T dsp = T(0), dr[3] = {T(0), T(0), T(0)};
-    for (int k = 0; k < nang; ++k) {
+    for (int k = lane; k < nang; k += 32) {
       if (k == p) continue;
       const T* rk = rh + 3 * (base + k);
       T P[4], dP[4];
@@ -347,7 +350,7 @@ __global__ void k_angle_bwd(int nmax, int na, int ed, T inv_na, const T* __restr
       // p as the first index (dcoef_pk) and as the second (dcoef_kp)
       const T* d1 = dcoef + (p * nang + k) * 4;
       const T* d2 = dcoef + (k * nang + p) * 4;
-      T sk = sa[base + k], sp = sa[base + p];
+      const T sk = sa[base + k];
       T dc = T(0);
       for (int l = 0; l < 4; ++l) {
         dsp += (d1[l] + d2[l]) * inv_na * sk * P[l];
@@ -355,8 +358,12 @@ __global__ void k_angle_bwd(int nmax, int na, int ed, T inv_na, const T* __restr
       }
       for (int a = 0; a < 3; ++a) dr[a] += dc * rk[a];
     }
-    dsa_e[base + p] += dsp;
-    for (int a = 0; a < 3; ++a) drh[3 * (base + p) + a] += dr[a];
+    dsp = warp_sum(dsp);
+    for (int a = 0; a < 3; ++a) dr[a] = warp_sum(dr[a]);
+    if (lane == 0) {
+      dsa_e[base + p] += dsp;
+      for (int a = 0; a < 3; ++a) drh[3 * (base + p) + a] += dr[a];
+    }
   }
 }
 
