@@ -135,3 +135,21 @@ def test_gf_mixed_md_tracks_fp32():
     assert np.max(np.abs(out[dp.PREC_FUSED][0] - out[dp.PREC_PLAIN_F32][0])) < 1e-4
     et = out[dp.PREC_FUSED][1].sum(1)
     assert np.all(np.isfinite(et)) and np.max(np.abs(et - et[0])) < 1e-3 * abs(et[0])
+
+
+@pytest.mark.parametrize("na,ed,mode", [(64, 16, "recompute per column"),
+                                        (56, 64, "coefficients only"),
+                                        (40, 64, "coefficients and rows staged")])
+def test_gf_angle_channel_shared_memory_variants_fp64(na, ed, mode):
+    """The angle kernels keep as much in shared memory as fits: with FP64 and a
+    large angle capacity the adjoint falls back to unstaged rows (56 slots) or
+    to recomputing the coefficients per column (64 slots).  Every variant
+    must give the oracle's result."""
+    m = replace(C.GRAPH_MODEL, node=32, edge=ed, n_layers=2, f1=32, f2=32, f3=16, nmax=96, na=na)
+    s = serving_system(96, 7)
+    w = weights(m, 5, 0.2)
+    pot = make(m, s, dp.PREC_PLAIN_F64, w)
+    E, F, V = pot.compute(s.coords)
+    Eo, _, Fo, Vo = oracle.gf_compute(m, w, s.types, s.coords, s.box)
+    assert E == pytest.approx(Eo, rel=1e-11)
+    assert np.max(np.abs(F - Fo)) <= 1e-10 * frms(Fo)
