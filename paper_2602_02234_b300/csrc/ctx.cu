@@ -71,6 +71,9 @@ struct dp_ctx {
   double *atom_e = nullptr, *atom_vir = nullptr, *sys_e = nullptr, *sys_vir = nullptr;
   int* flags = nullptr;
   long long* step = nullptr;   // [0] step counter, [1] trace base
+  // dp_step's checkpoint for a retry after a neighbour-capacity overflow
+  double *xck = nullptr, *vck = nullptr;
+  long long* stepck = nullptr;
   double* trace = nullptr;
   int trace_len = 0;
   size_t trace_elems = 0;
@@ -421,6 +424,9 @@ static int ctx_create(dp_ctx** out, const dp_model_desc* desc, const double* mas
   TRY(dalloc(c, &c->v, 3 * N), "v");
   TRY(dalloc(c, &c->F, 3 * N), "F");
   TRY(dalloc(c, &c->xin, 3 * N), "xin");
+  TRY(dalloc(c, &c->xck, 3 * N), "checkpoint");
+  TRY(dalloc(c, &c->vck, 3 * N), "checkpoint");
+  TRY(dalloc(c, &c->stepck, 1), "checkpoint");
   TRY(dalloc(c, &c->differs, 1), "differs");
   TRY(dalloc(c, &c->xref, 3 * N), "xref");
   TRY(dalloc(c, &c->w, 3 * N), "w");
@@ -691,20 +697,18 @@ extern "C" int dp_step(dp_ctx* c, int n_steps, double dt_fs, double* coords_io, 
     if (rc) return rc;
   }
   if (n_steps == 0) return DP_OK;
-  // checkpoint for a retry after a neighbour-capacity overflow
-  std::vector<double> x0(3 * (size_t)c->n), v0(3 * (size_t)c->n);
-  long long step0[2];
+  // checkpoint (on the device, no host round trip) for a retry after a
+  // neighbour-capacity overflow; the trace base is the step counter at entry
+  const size_t nb = sizeof(double) * 3 * (size_t)c->n;
   for (int attempt = 0; attempt < 4; ++attempt) {
     if (!c->forces_valid) {
       rc = compute_now(c);
       if (rc) return rc;
     }
-    CUDA_TRY(c, cudaMemcpyAsync(x0.data(), c->x, sizeof(double) * x0.size(), cudaMemcpyDeviceToHost, c->st), "checkpoint");
-    CUDA_TRY(c, cudaMemcpyAsync(v0.data(), c->v, sizeof(double) * v0.size(), cudaMemcpyDeviceToHost, c->st), "checkpoint");
-    CUDA_TRY(c, cudaMemcpyAsync(step0, c->step, sizeof step0, cudaMemcpyDeviceToHost, c->st), "checkpoint");
-    CUDA_TRY(c, cudaStreamSynchronize(c->st), "checkpoint");
-    step0[1] = step0[0];
-    CUDA_TRY(c, cudaMemcpyAsync(c->step, step0, sizeof step0, cudaMemcpyHostToDevice, c->st), "step base");
+    CUDA_TRY(c, cudaMemcpyAsync(c->xck, c->x, nb, cudaMemcpyDeviceToDevice, c->st), "checkpoint");
+    CUDA_TRY(c, cudaMemcpyAsync(c->vck, c->v, nb, cudaMemcpyDeviceToDevice, c->st), "checkpoint");
+    CUDA_TRY(c, cudaMemcpyAsync(c->stepck, c->step, sizeof(long long), cudaMemcpyDeviceToDevice, c->st), "checkpoint");
+    CUDA_TRY(c, cudaMemcpyAsync(c->step + 1, c->step, sizeof(long long), cudaMemcpyDeviceToDevice, c->st), "step base");
     int tl = energies_out ? n_steps : 1;
     if (!c->graph || c->graph_stale || c->graph_dt != dt_fs || c->graph_trace_len < tl) {
       rc = build_step_graph(c, dt_fs, std::max(tl, c->trace_len));
@@ -720,10 +724,9 @@ extern "C" int dp_step(dp_ctx* c, int n_steps, double dt_fs, double* coords_io, 
     if (fl & kFlagOverflow) {
       rc = alloc_skin(c, c->cap * 2);
       if (rc) return rc;
-      CUDA_TRY(c, cudaMemcpyAsync(c->x, x0.data(), sizeof(double) * x0.size(), cudaMemcpyHostToDevice, c->st), "restore");
-      CUDA_TRY(c, cudaMemcpyAsync(c->v, v0.data(), sizeof(double) * v0.size(), cudaMemcpyHostToDevice, c->st), "restore");
-      step0[1] = 0;
-      CUDA_TRY(c, cudaMemcpyAsync(c->step, step0, sizeof step0, cudaMemcpyHostToDevice, c->st), "restore");
+      CUDA_TRY(c, cudaMemcpyAsync(c->x, c->xck, nb, cudaMemcpyDeviceToDevice, c->st), "restore");
+      CUDA_TRY(c, cudaMemcpyAsync(c->v, c->vck, nb, cudaMemcpyDeviceToDevice, c->st), "restore");
+      CUDA_TRY(c, cudaMemcpyAsync(c->step, c->stepck, sizeof(long long), cudaMemcpyDeviceToDevice, c->st), "restore");
       c->forces_valid = false;
       continue;
     }
@@ -890,7 +893,7 @@ static double now_ms() {
 // bytes of device memory one atom needs in a fused context (skin capacity cap)
 static size_t bytes_per_atom(const dp_model_desc* d, int cap) {
   size_t nm = d->nmax, L = d->n_layers;
-  size_t ctx = 120 + 12 + 16 + 24 + 4 * nm + 12 * nm + 24 * nm + 8 + 72 + (size_t)cap * 22 + 48;
+  size_t ctx = 120 + 12 + 16 + 24 + 4 * nm + 12 * nm + 24 * nm + 8 + 72 + (size_t)cap * 22 + 48 + 48;
   size_t model = (L + 1) * 32768 + L * 512 + 128 * (size_t)d->m2 * 6 + 2048 + 12 * nm + 8;
   if (d->fit_heads > 1) model += 8 * (size_t)(d->fit_heads - 1);
   // message passing: post-message tiles, FP32 stream and dE/dG', U, h, dh, dq, sums

@@ -562,3 +562,31 @@ def test_message_passing_fused_with_inert_messages_is_the_fused_model():
     Eb, Fb, Vb = b.compute(s.coords)
     assert Ea == Eb and np.array_equal(Fa, Fb) and np.array_equal(Va, Vb)
     assert np.array_equal(a.atom_energies(), b.atom_energies())
+
+
+def test_md_retries_after_a_neighbour_capacity_overflow():
+    """300 atoms start dilute (the skin capacity is sized from the mean
+    density: 160 entries per atom) and fall towards the box centre, so the
+    lists rebuilt during dp_step outgrow it.  dp_step restores its on-device
+    checkpoint, doubles the capacity and reruns the steps; the trajectory must
+    still be the oracle's."""
+    m = replace(C.ATTN_MODEL, n_layers=1, nmax=64)
+    rng = np.random.default_rng(17)
+    L = 20.0
+    g = (np.arange(7) + 0.5) * (L / 7)
+    pts = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)[:300]
+    x0 = pts + rng.uniform(-0.3, 0.3, pts.shape)
+    types = (np.arange(300) % 2 == 0).astype(np.int32) * 3       # O-like and H
+    box = np.full(3, L)
+    masses = np.array([1.008, 12.011, 14.007, 15.999, 32.06])
+    v0 = -0.04 * (x0 - L / 2)                                    # A/fs, inwards
+    w = weights(m)
+    pot = dp.DeepPotential(dp.model_desc(m, dp.PREC_PLAIN_F64), types, box, w, masses=masses)
+    pot.set_state(x0, v0, 0)
+    pot.step(20, C.DT_FS)
+    x, v, _ = pot.get_state()
+    xo, vo, _, _ = oracle.af_md(m, w, types, masses, x0, v0, box, 20, C.DT_FS)
+    # the final configuration needs more skin entries than the first capacity
+    cnt = oracle.neighbours(xo, box, m.rc + 1.0, 1)[0]
+    assert cnt.max() > 160
+    assert np.max(np.abs(x - xo)) < 1e-9 and np.max(np.abs(v - vo)) < 1e-9
