@@ -11,7 +11,9 @@ The names follow the C ABI of ``include/dp.h``:
 * ``weight_count`` -- ``dp_weight_count``
 * ``DeepPotential`` -- a ``dp_ctx``: ``compute`` (``dp_compute``), ``step``
   (``dp_step``), ``get_state``/``set_state``, ``neighbours``,
-  ``atom_energies``, ``kernels_per_step``, ``device_bytes``
+  ``atom_energies``, ``head_energies`` (``dp_get_head_energies``),
+  ``set_group`` (``dp_set_group``), ``kernels_per_step``, ``device_bytes``
+* ``Server`` -- ``dp_server_*``: continuous batching of independent systems
 * ``DPEnergy`` -- ``torch.autograd.Function`` whose forward is ``dp_compute``
   and whose backward returns -dE/dx * grad (forces from the hand-written
   adjoint kernels).
@@ -61,8 +63,11 @@ def model_desc(model, precision: int, skin: float = 1.0, rebuild_every: int = 10
     """A ``dp_model_desc`` from a dict (or object with ``as_dict``) of model sizes.
 
     Attention family keys: n_species e1 e2 m1 m2 n_layers hidden heads f1 f2 f3
-    nmax rc rs.  Graph family keys: n_species node edge n_layers f1 f2 f3 nmax
-    na rc rs rca rsa.
+    nmax rc rs, and optionally fit_heads (fitting heads on one descriptor) and
+    message_passing (0/1: the atom channel passed between neighbours every
+    layer).  Graph family keys: n_species node edge n_layers f1 f2 f3 nmax na
+    rc rs rca rsa.  precision: PREC_PLAIN_F64, PREC_PLAIN_F32 or PREC_FUSED
+    (16-bit tensor-core operands; for the graph family the mixed form).
     """
     d = model if isinstance(model, dict) else model.as_dict()
     m = ModelDesc()
