@@ -36,6 +36,16 @@ __device__ __forceinline__ long long slot_of(long long idx, int ed, int ed_shift
   return ed_shift >= 0 ? (idx >> ed_shift) : idx / ed;
 }
 
+// four consecutive values (16- or 32-byte aligned) as vector loads
+__device__ __forceinline__ void ld4(const float* p, float* v) {
+  const float4 u = *reinterpret_cast<const float4*>(p);
+  v[0] = u.x; v[1] = u.y; v[2] = u.z; v[3] = u.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double* v) {
+  const double2 u = reinterpret_cast<const double2*>(p)[0], w = reinterpret_cast<const double2*>(p)[1];
+  v[0] = u.x; v[1] = u.y; v[2] = w.x; v[3] = w.y;
+}
+
 
 // ------------------------------------------------------------------ kernels
 // geometry of every slot: distance, switches, s = sw/r, unit vector
@@ -156,19 +166,22 @@ __device__ int n_angle(const T* sa, long long base, int nmax, int na) {
 // (c) forward: a_ip for the angle slots of one atom (block per atom).
 // a_p[c] = sum_l Wphi[l][c] sum_k coef_pkl q_k[c] with coef_pkl = w_pk P_l(c_pk)
 // (0 for k = p), the coefficients and the slots' q rows staged in shared memory.
-// Shared memory: na x na x 4 coefficients, then (staged) na x ed of q.
+// Shared memory: na x na x 4 coefficients, Wphi by column (ed x 4), then
+// (staged) na x ed of q.
 template <typename T>
 __global__ void k_angle(int nmax, int na, int ed, T inv_na, const T* __restrict__ sa,
                         const T* __restrict__ rh, const T* __restrict__ q,
                         const T* __restrict__ Wphi, T* __restrict__ a, int staged) {
   extern __shared__ unsigned char sm_raw[];
   T* coef = reinterpret_cast<T*>(sm_raw);  // na x na x 4
+  T* W4 = coef + (size_t)na * na * 4;      // ed x 4: Wphi[l][c] at W4[4 c + l]
   int i = blockIdx.x;
   long long base = (long long)i * nmax;
   int nang = n_angle(sa, base, nmax, na);
+  for (int idx = threadIdx.x; idx < 4 * ed; idx += blockDim.x) W4[idx] = Wphi[(idx & 3) * ed + (idx >> 2)];
   const T* qs = q + base * ed;
   if (staged) {
-    T* st = coef + (size_t)na * na * 4;    // na x ed
+    T* st = W4 + (size_t)ed * 4;            // na x ed
     for (int idx = threadIdx.x; idx < nang * ed; idx += blockDim.x) st[idx] = qs[idx];
     qs = st;
   }
@@ -189,10 +202,13 @@ __global__ void k_angle(int nmax, int na, int ed, T inv_na, const T* __restrict_
       T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
       for (int k = 0; k < nang; ++k) {
         const T qk = qs[k * ed + c];
-        const T* cf = coef + (p * nang + k) * 4;
+        T cf[4];
+        ld4(coef + (p * nang + k) * 4, cf);
         s0 += cf[0] * qk; s1 += cf[1] * qk; s2 += cf[2] * qk; s3 += cf[3] * qk;
       }
-      out = Wphi[c] * s0 + Wphi[ed + c] * s1 + Wphi[2 * ed + c] * s2 + Wphi[3 * ed + c] * s3;
+      T w[4];
+      ld4(W4 + 4 * c, w);
+      out = w[0] * s0 + w[1] * s1 + w[2] * s2 + w[3] * s3;
     }
     a[(base + p) * ed + c] = out;
   }
@@ -261,10 +277,12 @@ __global__ void k_angle_bwd(int nmax, int na, int ed, T inv_na, const T* __restr
                             int mode) {
   extern __shared__ unsigned char sm_raw[];
   T* dcoef = reinterpret_cast<T*>(sm_raw);  // na x na x 4
-  T* coef = dcoef + (size_t)na * na * 4;    // na x na x 4 (mode >= 1)
+  T* W4 = dcoef + (size_t)na * na * 4;      // ed x 4: Wphi[l][c] at W4[4 c + l]
+  T* coef = W4 + (size_t)ed * 4;            // na x na x 4 (mode >= 1)
   int i = blockIdx.x;
   long long base = (long long)i * nmax;
   int nang = n_angle(sa, base, nmax, na);
+  for (int idx = threadIdx.x; idx < 4 * ed; idx += blockDim.x) W4[idx] = Wphi[(idx & 3) * ed + (idx >> 2)];
   const T* das = da + base * ed;
   const T* qs = q + base * ed;
   int ld = ed;
@@ -303,7 +321,7 @@ __global__ void k_angle_bwd(int nmax, int na, int ed, T inv_na, const T* __restr
         const T d = das[p * ld + c];
         T cf[4];
         if (mode >= 1) {
-          for (int l = 0; l < 4; ++l) cf[l] = coef[(p * nang + k) * 4 + l];
+          ld4(coef + (p * nang + k) * 4, cf);
         } else {
           const T* rp = rh + 3 * (base + p);
           T P[4], dP[4];
@@ -313,7 +331,9 @@ __global__ void k_angle_bwd(int nmax, int na, int ed, T inv_na, const T* __restr
         }
         s0 += cf[0] * d; s1 += cf[1] * d; s2 += cf[2] * d; s3 += cf[3] * d;
       }
-      out = Wphi[c] * s0 + Wphi[ed + c] * s1 + Wphi[2 * ed + c] * s2 + Wphi[3 * ed + c] * s3;
+      T w[4];
+      ld4(W4 + 4 * c, w);
+      out = w[0] * s0 + w[1] * s1 + w[2] * s2 + w[3] * s3;
     }
     dq[(base + k) * ed + c] = out;
   }
@@ -324,10 +344,12 @@ __global__ void k_angle_bwd(int nmax, int na, int ed, T inv_na, const T* __restr
     if (p != k)
       for (int c = 0; c < ed; ++c) {
         const T x = das[p * ld + c] * qs[k * ld + c];
-        a0 += x * Wphi[c];
-        a1 += x * Wphi[ed + c];
-        a2 += x * Wphi[2 * ed + c];
-        a3 += x * Wphi[3 * ed + c];
+        T w[4];
+        ld4(W4 + 4 * c, w);
+        a0 += x * w[0];
+        a1 += x * w[1];
+        a2 += x * w[2];
+        a3 += x * w[3];
       }
     dcoef[pk * 4 + 0] = a0;
     dcoef[pk * 4 + 1] = a1;
@@ -626,11 +648,12 @@ bool PlainGf<T>::init(const GfDims& m, const double* w, int n_atoms, const int* 
          dalloc(&tt_[l], P * Ed, err);
   // the angle kernels stage as much as fits in 227 KB of shared memory
   const size_t kMaxSmem = 232448, na2 = (size_t)m.na * m.na * 4 * sizeof(T),
+               w4 = (size_t)m.ed * 4 * sizeof(T),
                rowsz = (size_t)m.na * m.ed * sizeof(T), rowsz1 = (size_t)m.na * (m.ed + 1) * sizeof(T);
-  angle_staged_ = na2 + rowsz <= kMaxSmem ? 1 : 0;
-  angle_smem_ = na2 + (angle_staged_ ? rowsz : 0);
-  angle_mode_ = 2 * na2 + 2 * rowsz1 <= kMaxSmem ? 2 : (2 * na2 <= kMaxSmem ? 1 : 0);
-  angle_bwd_smem_ = na2 * (angle_mode_ >= 1 ? 2 : 1) + (angle_mode_ == 2 ? 2 * rowsz1 : 0);
+  angle_staged_ = na2 + w4 + rowsz <= kMaxSmem ? 1 : 0;
+  angle_smem_ = na2 + w4 + (angle_staged_ ? rowsz : 0);
+  angle_mode_ = 2 * na2 + w4 + 2 * rowsz1 <= kMaxSmem ? 2 : (2 * na2 + w4 <= kMaxSmem ? 1 : 0);
+  angle_bwd_smem_ = na2 * (angle_mode_ >= 1 ? 2 : 1) + w4 + (angle_mode_ == 2 ? 2 * rowsz1 : 0);
   const int angle_smem = (int)angle_smem_, angle_bwd_smem = (int)angle_bwd_smem_;
   if (cudaFuncSetAttribute(k_angle<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, angle_smem) !=
           cudaSuccess ||
