@@ -132,11 +132,37 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
     const long long m = m0 + t;
     const bool live = m < g.M;
     const long long row = live ? (g.c_rows ? (long long)g.c_rows[m] : m) : 0;
+    const int jn = live && g.epi == 3 ? g.sel_j[row] : -1;
     for (int c = 0; c < g.N; c += 16) {
       float v[16];
       tc::tmem_ld16(tb + lane_off + (uint32_t)c, v);
       if (!live) continue;
       float4* Crow = reinterpret_cast<float4*>(g.C + row * g.ldc + c);
+      if (g.epi == 3) {   // edge update: v = tanh(Ai + Bj + acc + b), e1 = e_in + v
+        float4* Vrow = reinterpret_cast<float4*>(g.v_out + row * g.ldc + c);
+        if (jn < 0) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            Vrow[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            Crow[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+          continue;
+        }
+        const float4* arow = reinterpret_cast<const float4*>(g.Ai + (row / g.nmax) * g.ldc + c);
+        const float4* brow = reinterpret_cast<const float4*>(g.Bj + (long long)jn * g.ldc + c);
+        const float4* erow = reinterpret_cast<const float4*>(g.e_in + row * g.ldc + c);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 a = arow[q], b = brow[q], e = erow[q];
+          const float y0 = tanhf(a.x + b.x + v[4 * q] + g.bias[c + 4 * q]);
+          const float y1 = tanhf(a.y + b.y + v[4 * q + 1] + g.bias[c + 4 * q + 1]);
+          const float y2 = tanhf(a.z + b.z + v[4 * q + 2] + g.bias[c + 4 * q + 2]);
+          const float y3 = tanhf(a.w + b.w + v[4 * q + 3] + g.bias[c + 4 * q + 3]);
+          Vrow[q] = make_float4(y0, y1, y2, y3);
+          Crow[q] = make_float4(e.x + y0, e.y + y1, e.z + y2, e.w + y3);
+        }
+        continue;
+      }
       float cin[16], ax[16];
       if (g.beta != 0.f)
 #pragma unroll

@@ -9,7 +9,11 @@
 namespace dp {
 
 // C(m, n) = sum_k A(m, k) B(k, n) [+ bias(n)] [+ beta C(m, n)], then epi:
-// 0 none, 1 tanh, 2 times (1 - aux(m, n)^2) with aux laid out like C.
+// 0 none, 1 tanh, 2 times (1 - aux(m, n)^2) with aux laid out like C, or
+// 3 the graph family's edge update for row m = slot (i, p) of atom i = m / nmax
+// with neighbour j = sel_j[m]: v = tanh(Ai(i, n) + Bj(j, n) + acc + bias(n)),
+// v_out(m, n) = v and C(m, n) = e_in(m, n) + v (both 0 for an empty slot);
+// Ai, Bj, e_in, v_out laid out like C, c_rows and beta unused.
 //   A(m, k) = A[row(m) * lda + k], row(m) = a_rows ? a_rows[m] : m; A 16-byte
 //             aligned, lda a multiple of 4
 //   B(k, n) = B[k * ldb + n]  (b_nk = 0)  or  B[n * ldb + k]  (b_nk = 1)
@@ -34,6 +38,11 @@ struct GemmTc {
   const float* aux;
   int fp16;        // operands rounded to FP16 (1) or BF16 (0)
   int* status;
+  // epi 3 only
+  const int* sel_j;
+  int nmax;
+  const float *Ai, *Bj, *e_in;
+  float* v_out;
 };
 
 bool gemm_tc_shape_ok(int N, int K);

@@ -538,6 +538,32 @@ class PlainGf : public Model {
         n_, m_.nmax, m_.nmax, m_.ed, nv.cap, nv.skin, nv.skin_cnt, nv.mirror, nv.selpos, x,
         nullptr, out);
   }
+  // mixed form: the edge update of layer l as the epilogue of e Wc on the
+  // tensor cores (Ce never reaches memory); false when not applicable
+  bool edge_fused(int l, const NbrView& nv, cudaStream_t st) {
+    if constexpr (std::is_same<T, float>::value) {
+      const int Ed = m_.ed;
+      if (!tc_ || !gemm_tc_shape_ok(Ed, Ed) || Ed % 4 != 0) return false;
+      GemmTc t{};
+      t.M = (int)((long long)n_ * m_.nmax); t.N = Ed; t.K = Ed;
+      t.A = ee_[l]; t.lda = Ed;
+      t.B = Wc_[l]; t.ldb = Ed; t.b_nk = 0;
+      t.C = e1_[l]; t.ldc = Ed;
+      t.bias = be_[l]; t.epi = 3;
+      t.sel_j = nv.sel_j; t.nmax = m_.nmax; t.Ai = Ai_; t.Bj = Bj_; t.e_in = ee_[l]; t.v_out = vv_[l];
+      t.status = flags_;
+#ifdef DP_GF_BF16
+      t.fp16 = 0;
+#else
+      t.fp16 = 1;
+#endif
+      gemm_tc(t, st);
+      return true;
+    } else {
+      (void)l; (void)nv; (void)st;
+      return false;
+    }
+  }
   bool tc_ = false;
   int* flags_ = nullptr;
   // shared-memory variants of the angle kernels (see k_angle, k_angle_bwd)
@@ -706,9 +732,13 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
     // (b)
     mm(gemm_rowmajor<T>(n, Ed, Nd, nn_[l + 1], Nd, Wa_[l], Ed, Ai_, Ed), st);
     mm(gemm_rowmajor<T>(n, Ed, Nd, nn_[l + 1], Nd, Wb_[l], Ed, Bj_, Ed), st);
-    mm(gemm_rowmajor<T>((int)P, Ed, Ed, ee_[l], Ed, Wc_[l], Ed, Ce_, Ed), st);
-    k_edge<T><<<grid(PE), 256, 0, st>>>(P, NM, Ed, ed_shift, nv.sel_j, Ai_, Bj_, Ce_, be_[l], ee_[l],
-                                        vv_[l], e1_[l]);
+    if (edge_fused(l, nv, st)) {
+      --k;   // one launch instead of two
+    } else {
+      mm(gemm_rowmajor<T>((int)P, Ed, Ed, ee_[l], Ed, Wc_[l], Ed, Ce_, Ed), st);
+      k_edge<T><<<grid(PE), 256, 0, st>>>(P, NM, Ed, ed_shift, nv.sel_j, Ai_, Bj_, Ce_, be_[l],
+                                          ee_[l], vv_[l], e1_[l]);
+    }
     // (c)
     mm(gemm_rowmajor<T>((int)P, Ed, Ed, e1_[l], Ed, Wp_[l], Ed, qq_[l], Ed), st);
     k_angle<T><<<n, 256, angle_smem, st>>>(NM, NA, Ed, inv_na, sa_, rh_, qq_[l], Wphi_[l], aa_,
