@@ -138,6 +138,22 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
       tc::tmem_ld16(tb + lane_off + (uint32_t)c, v);
       if (!live) continue;
       float4* Crow = reinterpret_cast<float4*>(g.C + row * g.ldc + c);
+      if (g.epi == 4) {   // angle output: t = tanh(acc + b), e_out = e_in + sa t
+        float4* Orow = reinterpret_cast<float4*>(g.v_out + row * g.ldc + c);
+        const float4* erow = reinterpret_cast<const float4*>(g.e_in + row * g.ldc + c);
+        const float sw = g.sa[row];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 e = erow[q];
+          const float t0 = tanhf(v[4 * q] + g.bias[c + 4 * q]);
+          const float t1 = tanhf(v[4 * q + 1] + g.bias[c + 4 * q + 1]);
+          const float t2 = tanhf(v[4 * q + 2] + g.bias[c + 4 * q + 2]);
+          const float t3 = tanhf(v[4 * q + 3] + g.bias[c + 4 * q + 3]);
+          Crow[q] = make_float4(t0, t1, t2, t3);
+          Orow[q] = make_float4(e.x + sw * t0, e.y + sw * t1, e.z + sw * t2, e.w + sw * t3);
+        }
+        continue;
+      }
       if (g.epi == 3) {   // edge update: v = tanh(Ai + Bj + acc + b), e1 = e_in + v
         float4* Vrow = reinterpret_cast<float4*>(g.v_out + row * g.ldc + c);
         if (jn < 0) {

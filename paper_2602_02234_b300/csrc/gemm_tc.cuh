@@ -13,7 +13,9 @@ namespace dp {
 // 3 the graph family's edge update for row m = slot (i, p) of atom i = m / nmax
 // with neighbour j = sel_j[m]: v = tanh(Ai(i, n) + Bj(j, n) + acc + bias(n)),
 // v_out(m, n) = v and C(m, n) = e_in(m, n) + v (both 0 for an empty slot);
-// Ai, Bj, e_in, v_out laid out like C, c_rows and beta unused.
+// Ai, Bj, e_in, v_out laid out like C, c_rows and beta unused; or 4 the angle
+// channel's output: C(m, n) = t = tanh(acc + bias(n)) and
+// v_out(m, n) = e_in(m, n) + sa[m] t (e_in, v_out laid out like C).
 //   A(m, k) = A[row(m) * lda + k], row(m) = a_rows ? a_rows[m] : m; A 16-byte
 //             aligned, lda a multiple of 4
 //   B(k, n) = B[k * ldb + n]  (b_nk = 0)  or  B[n * ldb + k]  (b_nk = 1)
@@ -38,10 +40,10 @@ struct GemmTc {
   const float* aux;
   int fp16;        // operands rounded to FP16 (1) or BF16 (0)
   int* status;
-  // epi 3 only
+  // epi 3 and 4
   const int* sel_j;
   int nmax;
-  const float *Ai, *Bj, *e_in;
+  const float *Ai, *Bj, *e_in, *sa;
   float* v_out;
 };
 

@@ -564,6 +564,32 @@ class PlainGf : public Model {
       return false;
     }
   }
+  // mixed form: t = tanh(a Wq + bq) and e_{l+1} = e1 + swa t in one product's
+  // epilogue; false when not applicable
+  bool angle_out_fused(int l, cudaStream_t st) {
+    if constexpr (std::is_same<T, float>::value) {
+      const int Ed = m_.ed;
+      if (!tc_ || !gemm_tc_shape_ok(Ed, Ed) || Ed % 4 != 0) return false;
+      GemmTc t{};
+      t.M = (int)((long long)n_ * m_.nmax); t.N = Ed; t.K = Ed;
+      t.A = aa_; t.lda = Ed;
+      t.B = Wq_[l]; t.ldb = Ed; t.b_nk = 0;
+      t.C = tt_[l]; t.ldc = Ed;
+      t.bias = bq_[l]; t.epi = 4;
+      t.sa = sa_; t.e_in = e1_[l]; t.v_out = ee_[l + 1];
+      t.status = flags_;
+#ifdef DP_GF_BF16
+      t.fp16 = 0;
+#else
+      t.fp16 = 1;
+#endif
+      gemm_tc(t, st);
+      return true;
+    } else {
+      (void)l; (void)st;
+      return false;
+    }
+  }
   bool tc_ = false;
   int* flags_ = nullptr;
   // shared-memory variants of the angle kernels (see k_angle, k_angle_bwd)
@@ -743,13 +769,15 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
     mm(gemm_rowmajor<T>((int)P, Ed, Ed, e1_[l], Ed, Wp_[l], Ed, qq_[l], Ed), st);
     k_angle<T><<<n, 256, angle_smem, st>>>(NM, NA, Ed, inv_na, sa_, rh_, qq_[l], Wphi_[l], aa_,
                                            angle_staged_);
-    {
+    if (angle_out_fused(l, st)) {
+      --k;   // one launch instead of two
+    } else {
       Gemm<T> g = gemm_rowmajor<T>((int)P, Ed, Ed, aa_, Ed, Wq_[l], Ed, tt_[l], Ed);
       g.bias = bq_[l];
       g.epi = 1;
       mm(g, st);
+      k_angle_out<T><<<grid(PE), 256, 0, st>>>(P, Ed, ed_shift, sa_, e1_[l], tt_[l], ee_[l + 1]);
     }
-    k_angle_out<T><<<grid(PE), 256, 0, st>>>(P, Ed, ed_shift, sa_, e1_[l], tt_[l], ee_[l + 1]);
     k += 14;
   }
   // fitting
