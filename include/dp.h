@@ -197,6 +197,18 @@ int dp_get_head_energies(dp_ctx* ctx, double* out);
  * DP_ERR_UNSUPPORTED for a multi-system (serving) context. */
 int dp_set_group(dp_ctx* ctx, const unsigned char* mask);
 
+/* Centres of one subdomain of a domain decomposition (the paper names
+ * domain-decomposed inference future work, Sec. V-B, Sec. VII): the context
+ * holds the owned atoms and their ghosts (every atom within rc of the
+ * subdomain); mask (n_atoms bytes, host memory, nonzero = owned) selects the
+ * centres.  Only centres carry energy and have neighbour lists, every atom may
+ * be a neighbour, so the forces of dp_compute are the owned centres' partial
+ * forces on every local atom: the ghosts' parts belong to their owners.  NULL
+ * restores every atom.  Atom-local models only (the attention family without
+ * message passing): DP_ERR_UNSUPPORTED otherwise, and for a multi-system
+ * context; DP_ERR_ARG for a NULL ctx. */
+int dp_set_centres(dp_ctx* ctx, const unsigned char* mask);
+
 /* Enqueue `reps` evaluations of the network alone (no neighbour update, no
  * force assembly) on the context's stream, at the resident neighbour lists,
  * without synchronising; for timing the network kernels with events on that

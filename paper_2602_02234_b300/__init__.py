@@ -12,7 +12,8 @@ The names follow the C ABI of ``include/dp.h``:
 * ``DeepPotential`` -- a ``dp_ctx``: ``compute`` (``dp_compute``), ``step``
   (``dp_step``), ``get_state``/``set_state``, ``neighbours``,
   ``atom_energies``, ``head_energies`` (``dp_get_head_energies``),
-  ``set_group`` (``dp_set_group``), ``kernels_per_step``, ``device_bytes``
+  ``set_group`` (``dp_set_group``), ``set_centres`` (``dp_set_centres``),
+  ``kernels_per_step``, ``device_bytes``
 * ``Server`` -- ``dp_server_*``: continuous batching of independent systems
 * ``DPEnergy`` -- ``torch.autograd.Function`` whose forward is ``dp_compute``
   and whose backward returns -dE/dx * grad (forces from the hand-written
@@ -113,6 +114,7 @@ def lib():
         L.dp_get_neighbours.argtypes = [vp, vp, vp, vp]
         L.dp_get_atom_energies.argtypes = [vp, vp]
         L.dp_set_group.argtypes = [vp, vp]
+        L.dp_set_centres.argtypes = [vp, vp]
         L.dp_get_head_energies.argtypes = [vp, vp]
         L.dp_enqueue_network.argtypes = [vp, i, i]
         L.dp_kernels_per_step.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -285,6 +287,19 @@ class DeepPotential:
         if m.shape != (self.n,):
             raise ValueError("mask must have one entry per atom")
         self._check(lib().dp_set_group(self._h, m.ctypes.data))
+
+    def set_centres(self, mask=None):
+        """Centres of a domain-decomposed subdomain: a boolean array over the
+        local atoms (owned True, ghosts False; None: every atom).  Only centres
+        carry energy; forces are the centres' partial forces on every local
+        atom (dp_set_centres)."""
+        if mask is None:
+            self._check(lib().dp_set_centres(self._h, None))
+            return
+        m = np.ascontiguousarray(np.asarray(mask, dtype=bool), dtype=np.uint8)
+        if m.shape != (self.n,):
+            raise ValueError("mask must have one entry per atom")
+        self._check(lib().dp_set_centres(self._h, m.ctypes.data))
 
     def atom_energies(self):
         e = np.zeros(self.n)

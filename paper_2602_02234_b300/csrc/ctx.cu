@@ -54,6 +54,7 @@ struct dp_ctx {
   double* head_sys_e = nullptr;  // energies of fitting heads 1.. per system: [sys][head - 1]
   unsigned char* grp = nullptr;  // DP group (1 = member), used when use_grp
   bool use_grp = false;
+  bool grp_centres = false;      // grp marks centres only (dp_set_centres)
   int* differs = nullptr;     // compare result
   double *minv = nullptr, *mass = nullptr;
   int* fl = nullptr;
@@ -237,6 +238,7 @@ static NlistArgs nlist_args(dp_ctx* c) {
   a.rc = c->desc.rcut; a.rskin = c->rskin;
   a.x = c->x; a.xref = c->xref; a.w = c->w; a.fl = c->fl;
   a.grp = c->use_grp ? c->grp : nullptr;
+  a.grp_centres = c->grp_centres ? 1 : 0;
   a.sys_of = c->sys_of; a.sys = c->sys;
   a.cell_of = c->cell_of; a.cell_cnt = c->cell_cnt; a.cell_fill = c->cell_fill;
   a.cell_start = c->cell_start; a.cell_idx = c->cell_idx;
@@ -644,11 +646,8 @@ extern "C" int dp_get_head_energies(dp_ctx* c, double* out) {
   return DP_OK;
 }
 
-// DP group (the paper's NNPot atom group): only pairs of members are
-// neighbours and only members carry energy; NULL restores every atom.
-extern "C" int dp_set_group(dp_ctx* c, const unsigned char* mask) {
-  if (!c) return fail(nullptr, DP_ERR_ARG, "ctx is NULL");
-  if (c->n_sys != 1) return fail(c, DP_ERR_UNSUPPORTED, "a DP group needs a single-system context");
+static int set_mask(dp_ctx* c, const unsigned char* mask, bool centres) {
+  if (c->n_sys != 1) return fail(c, DP_ERR_UNSUPPORTED, "a group needs a single-system context");
   if (mask) {
     if (!c->grp) CUDA_TRY(c, dalloc(c, &c->grp, (size_t)c->n_cap), "group");
     std::vector<unsigned char> g(c->n);
@@ -657,10 +656,28 @@ extern "C" int dp_set_group(dp_ctx* c, const unsigned char* mask) {
     CUDA_TRY(c, cudaStreamSynchronize(c->st), "group");
   }
   c->use_grp = mask != nullptr;
+  c->grp_centres = mask != nullptr && centres;
   c->forces_valid = false;
   c->valid_below = 0;
   c->graph_stale = true;
   return DP_OK;
+}
+
+// DP group (the paper's NNPot atom group): only pairs of members are
+// neighbours and only members carry energy; NULL restores every atom.
+extern "C" int dp_set_group(dp_ctx* c, const unsigned char* mask) {
+  if (!c) return fail(nullptr, DP_ERR_ARG, "ctx is NULL");
+  return set_mask(c, mask, false);
+}
+
+// Centres of a domain-decomposed subdomain: only marked atoms are centres and
+// carry energy, every atom is a neighbour; NULL restores every atom.
+extern "C" int dp_set_centres(dp_ctx* c, const unsigned char* mask) {
+  if (!c) return fail(nullptr, DP_ERR_ARG, "ctx is NULL");
+  if (mask && (c->desc.family != DP_FAMILY_ATTENTION || c->desc.message_passing))
+    return fail(c, DP_ERR_UNSUPPORTED,
+                "a centres mask needs an atom-local model (ghosts of layer-coupled models evaluate as centres)");
+  return set_mask(c, mask, true);
 }
 
 extern "C" int dp_step(dp_ctx* c, int n_steps, double dt_fs, double* coords_io, double* vel_io,

@@ -23,6 +23,7 @@ struct NlistArgs {
   int* skin_cnt;
   int* mirror;           // n x cap
   const unsigned char* grp;  // optional DP group: pairs only between members
+  int grp_centres;           // 1: grp marks centres only (any atom is a neighbour)
   int* sel_j;            // n x nmax
   int* sel_img;          // n x nmax x 3
   double* sel_r;         // n x nmax x 3

@@ -327,12 +327,13 @@ __global__ void k_flag_set(int* flags, int bits) {
 
 // -------------------------------------------------------------- selection
 // One warp per atom.  sel_* hold the kept neighbours in key order; selpos maps
-// every skin entry to its slot (or -1).
+// every skin entry to its slot (or -1).  With grp: pairs of members only, or
+// (grp_centres) every pair whose centre is a member.
 __global__ void k_select(int n, int cap, int nmax, double rc, const double* __restrict__ w,
                          const int* __restrict__ fl, const int* __restrict__ sys_of,
                          const SysInfo* __restrict__ sys, const SkinEntry* __restrict__ skin,
                          const int* __restrict__ skin_cnt, const unsigned char* __restrict__ grp,
-                         int* __restrict__ sel_j,
+                         int grp_centres, int* __restrict__ sel_j,
                          int* __restrict__ sel_img, double* __restrict__ sel_r,
                          short* __restrict__ selpos, int* __restrict__ n_in_rc) {
   extern __shared__ unsigned char smem_raw[];
@@ -365,7 +366,7 @@ __global__ void k_select(int n, int cap, int nmax, double rc, const double* __re
       nn[1] = e.my + fl[3 * j + 1] - fi[1];
       nn[2] = e.mz + fl[3 * j + 2] - fi[2];
       d2 = sep_exact(wi, w + 3 * j, nn, S.L, r);
-      take = d2 < rc2 && d2 > 0.0 && (!grp || (grp[i] && grp[j]));
+      take = d2 < rc2 && d2 > 0.0 && (!grp || (grp[i] && (grp_centres || grp[j])));
       sp[c] = -1;
     }
     unsigned b = __ballot_sync(0xffffffffu, take);
@@ -455,7 +456,8 @@ void launch_select(const NlistArgs& a, cudaStream_t st) {
   size_t sm = select_smem_bytes(a.cap, warps);
   k_select<<<ceil_div(a.n, warps), warps * 32, sm, st>>>(a.n, a.cap, a.nmax, a.rc, a.w, a.fl,
                                                          a.sys_of, a.sys, a.skin, a.skin_cnt,
-                                                         a.grp, a.sel_j, a.sel_img, a.sel_r,
+                                                         a.grp, a.grp_centres, a.sel_j,
+                                                         a.sel_img, a.sel_r,
                                                          a.selpos, a.n_in_rc);
 }
 

@@ -31,9 +31,10 @@ the same.  A ghost within L - 1 hops of an owned atom keeps its whole
 neighbour list inside the halo; the outermost ghosts' lists are cut, but
 only their species reach the owned atoms.
 
-The evaluation of a subdomain is a callback (on GPUs a context over owned +
-ghost atoms with the ghosts excluded as centres; in the tests the FP64
-oracle), so this module holds the partitioning and the communication only.
+The evaluation of a subdomain is a callback (on a GPU, a context over owned +
+ghost atoms whose centres mask, dp_set_centres, marks the owned ones; in the
+CPU tests the FP64 oracle), so this module holds the partitioning and the
+communication only.
 Exchanges use torch.distributed object collectives (gloo or NCCL); the design
 sends to every rank for simplicity, where a production layout would talk to
 the two slab neighbours only.
@@ -130,6 +131,23 @@ class SlabDecomposition:
         parts = [None] * self.n_ranks
         dist.all_gather_object(parts, float(value))
         return float(sum(parts[r] for r in range(self.n_ranks)))   # fixed order
+
+
+def local_system(coords, types, box, rank, n_ranks, rc, hops=1, axis=0):
+    """Rank `rank`'s local atoms computed from the whole system in one process
+    (what gather_local returns after its exchange): (global ids, positions,
+    species, n_owned), owned atoms first by increasing id, then the ghosts
+    within hops x rc of the slab by increasing id.  Neighbours at exactly
+    equal distances are ranked by atom index; an evaluator that must rank
+    them as the whole system does numbers the local atoms by global id."""
+    coords = np.asarray(coords, dtype=np.float64)
+    types = np.asarray(types, dtype=np.int32)
+    owner = slab_owner(coords, box, n_ranks, axis)
+    own = np.nonzero(owner == rank)[0]
+    near = slab_distance(coords, box, rank, n_ranks, axis) < hops * rc
+    ghost = np.nonzero(near & (owner != rank))[0]
+    ids = np.concatenate([own, ghost])
+    return ids, coords[ids], types[ids], len(own)
 
 
 def partial_forces(n_local, centres, pair_j, pair_g):

@@ -1,0 +1,65 @@
+"""GPU subdomain evaluation of the slab decomposition: every rank's local
+system (owned atoms and their ghosts within rc) evaluated on the GPU with the
+owned atoms as the only centres (dp_set_centres); the partial forces summed
+over ranks, the owned energies and the virials must equal the whole system's
+evaluation in the same precision.  The local atoms are numbered in the order
+of their global ids, so neighbours at exactly equal distances (a water's two
+hydrogens seen from its oxygen) are ranked as in the whole system; the owned
+centres then see the same neighbour lists in the same order and give the
+same pair gradients, and only the grouping of the final sums differs
+(tolerance 1e-12 of the force RMS in every precision)."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2602_02234_b300 as dp
+from paper_2602_02234_b300 import dd
+from synth import configs as C, normal_blob, protein_in_water
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("prec", [dp.PREC_PLAIN_F64, dp.PREC_PLAIN_F32, dp.PREC_FUSED])
+@pytest.mark.parametrize("world", [2, 3])
+def test_subdomains_on_the_gpu_reproduce_the_whole_system(prec, world):
+    m = C.ATTN_MODEL
+    s = protein_in_water(900, 90, (26.0, 19.0, 19.0), 21)
+    w = normal_blob(oracle.af_weight_count(m), C.WEIGHT_SEED)
+    desc = dp.model_desc(m, prec)
+    whole = dp.DeepPotential(desc, s.types, s.box, w)
+    E, F, V = whole.compute(s.coords)
+    whole.close()
+    Fs, Es, Vs = np.zeros_like(F), 0.0, np.zeros((3, 3))
+    seen = np.zeros(s.n, bool)
+    for rank in range(world):
+        ids, x, t, n_own = dd.local_system(s.coords, s.types, s.box, rank, world, m.rc)
+        assert len(ids) > n_own                       # there are ghosts
+        seen[ids[:n_own]] = True
+        owned = np.arange(len(ids)) < n_own
+        order = np.argsort(ids, kind="stable")        # global-id order
+        ids, x, t, owned = ids[order], x[order], t[order], owned[order]
+        pot = dp.DeepPotential(desc, t, s.box, w)
+        pot.set_centres(owned)
+        El, Fl, Vl = pot.compute(x)
+        ae = pot.atom_energies()
+        assert np.all(ae[~owned] == 0.0)               # ghosts carry no energy
+        pot.close()
+        np.add.at(Fs, ids, Fl)
+        Es += El
+        Vs += Vl
+    assert seen.all()
+    rms = float(np.sqrt(np.mean(F ** 2)))
+    assert np.max(np.abs(Fs - F)) <= 1e-12 * rms
+    assert Es == pytest.approx(E, rel=1e-12)
+    assert np.max(np.abs(Vs - V)) <= 1e-12 * np.max(np.abs(V))
+
+
+def test_centres_mask_refused_for_layer_coupled_models():
+    from dataclasses import replace
+    m = replace(C.ATTN_MODEL, message_passing=1)
+    s = protein_in_water(900, 90, (26.0, 19.0, 19.0), 21)
+    w = normal_blob(oracle.af_weight_count(m), C.WEIGHT_SEED)
+    pot = dp.DeepPotential(dp.model_desc(m, dp.PREC_PLAIN_F32), s.types, s.box, w)
+    with pytest.raises(dp.DPError) as e:
+        pot.set_centres(np.arange(s.n) < 100)
+    assert e.value.code == dp.DP_ERR_UNSUPPORTED
