@@ -209,6 +209,18 @@ int dp_set_group(dp_ctx* ctx, const unsigned char* mask);
  * context; DP_ERR_ARG for a NULL ctx. */
 int dp_set_centres(dp_ctx* ctx, const unsigned char* mask);
 
+/* Energy seed of one subdomain, for every model and needed by the
+ * layer-coupled ones (attention family with message passing, graph family),
+ * whose energy reaches n_layers neighbour hops: the context holds the owned
+ * atoms and every atom within n_layers x rc of the subdomain (Sec. III: the
+ * broadened ghost area); mask (n_atoms bytes, host memory, nonzero = owned)
+ * marks the atoms whose energy counts.  Every atom evaluates as a centre (the
+ * ghosts' features feed the owned atoms'), only marked atoms carry energy, and
+ * the adjoint is seeded with the mask, so dp_compute's forces are
+ * -d(sum of owned energies)/dx on every local atom.  NULL restores every atom.
+ * DP_ERR_ARG for a NULL ctx, DP_ERR_UNSUPPORTED for a multi-system context. */
+int dp_set_energy_seed(dp_ctx* ctx, const unsigned char* mask);
+
 /* Enqueue `reps` evaluations of the network alone (no neighbour update, no
  * force assembly) on the context's stream, at the resident neighbour lists,
  * without synchronising; for timing the network kernels with events on that

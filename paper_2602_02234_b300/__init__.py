@@ -13,6 +13,7 @@ The names follow the C ABI of ``include/dp.h``:
   (``dp_step``), ``get_state``/``set_state``, ``neighbours``,
   ``atom_energies``, ``head_energies`` (``dp_get_head_energies``),
   ``set_group`` (``dp_set_group``), ``set_centres`` (``dp_set_centres``),
+  ``set_energy_seed`` (``dp_set_energy_seed``),
   ``kernels_per_step``, ``device_bytes``
 * ``Server`` -- ``dp_server_*``: continuous batching of independent systems
 * ``DPEnergy`` -- ``torch.autograd.Function`` whose forward is ``dp_compute``
@@ -115,6 +116,7 @@ def lib():
         L.dp_get_atom_energies.argtypes = [vp, vp]
         L.dp_set_group.argtypes = [vp, vp]
         L.dp_set_centres.argtypes = [vp, vp]
+        L.dp_set_energy_seed.argtypes = [vp, vp]
         L.dp_get_head_energies.argtypes = [vp, vp]
         L.dp_enqueue_network.argtypes = [vp, i, i]
         L.dp_kernels_per_step.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -300,6 +302,19 @@ class DeepPotential:
         if m.shape != (self.n,):
             raise ValueError("mask must have one entry per atom")
         self._check(lib().dp_set_centres(self._h, m.ctypes.data))
+
+    def set_energy_seed(self, mask=None):
+        """Energy seed of a subdomain (any model; needed by layer-coupled ones):
+        a boolean array over the local atoms (owned True).  Every atom is a
+        centre, only owned energies count and seed the adjoint
+        (dp_set_energy_seed)."""
+        if mask is None:
+            self._check(lib().dp_set_energy_seed(self._h, None))
+            return
+        m = np.ascontiguousarray(np.asarray(mask, dtype=bool), dtype=np.uint8)
+        if m.shape != (self.n,):
+            raise ValueError("mask must have one entry per atom")
+        self._check(lib().dp_set_energy_seed(self._h, m.ctypes.data))
 
     def atom_energies(self):
         e = np.zeros(self.n)

@@ -54,7 +54,9 @@ struct dp_ctx {
   double* head_sys_e = nullptr;  // energies of fitting heads 1.. per system: [sys][head - 1]
   unsigned char* grp = nullptr;  // DP group (1 = member), used when use_grp
   bool use_grp = false;
-  bool grp_centres = false;      // grp marks centres only (dp_set_centres)
+  // what grp marks: 0 DP group members (dp_set_group), 1 centres
+  // (dp_set_centres), 2 the atoms whose energy counts (dp_set_energy_seed)
+  int grp_mode = 0;
   int* differs = nullptr;     // compare result
   double *minv = nullptr, *mass = nullptr;
   int* fl = nullptr;
@@ -237,8 +239,8 @@ static NlistArgs nlist_args(dp_ctx* c) {
   a.n = c->n; a.ncell = c->ncell; a.cap = c->cap; a.nmax = c->desc.nmax;
   a.rc = c->desc.rcut; a.rskin = c->rskin;
   a.x = c->x; a.xref = c->xref; a.w = c->w; a.fl = c->fl;
-  a.grp = c->use_grp ? c->grp : nullptr;
-  a.grp_centres = c->grp_centres ? 1 : 0;
+  a.grp = c->use_grp && c->grp_mode != 2 ? c->grp : nullptr;   // an energy seed keeps every pair
+  a.grp_centres = c->grp_mode == 1 ? 1 : 0;
   a.sys_of = c->sys_of; a.sys = c->sys;
   a.cell_of = c->cell_of; a.cell_cnt = c->cell_cnt; a.cell_fill = c->cell_fill;
   a.cell_start = c->cell_start; a.cell_idx = c->cell_idx;
@@ -646,7 +648,7 @@ extern "C" int dp_get_head_energies(dp_ctx* c, double* out) {
   return DP_OK;
 }
 
-static int set_mask(dp_ctx* c, const unsigned char* mask, bool centres) {
+static int set_mask(dp_ctx* c, const unsigned char* mask, int mode) {
   if (c->n_sys != 1) return fail(c, DP_ERR_UNSUPPORTED, "a group needs a single-system context");
   if (mask) {
     if (!c->grp) CUDA_TRY(c, dalloc(c, &c->grp, (size_t)c->n_cap), "group");
@@ -655,8 +657,11 @@ static int set_mask(dp_ctx* c, const unsigned char* mask, bool centres) {
     CUDA_TRY(c, cudaMemcpyAsync(c->grp, g.data(), c->n, cudaMemcpyHostToDevice, c->st), "group");
     CUDA_TRY(c, cudaStreamSynchronize(c->st), "group");
   }
+  const bool seeded = mask != nullptr && mode == 2;
+  if (!c->model->set_energy_seed(seeded ? c->grp : nullptr) && seeded)
+    return fail(c, DP_ERR_UNSUPPORTED, "this model takes no energy seed");
   c->use_grp = mask != nullptr;
-  c->grp_centres = mask != nullptr && centres;
+  c->grp_mode = mask != nullptr ? mode : 0;
   c->forces_valid = false;
   c->valid_below = 0;
   c->graph_stale = true;
@@ -667,7 +672,7 @@ static int set_mask(dp_ctx* c, const unsigned char* mask, bool centres) {
 // neighbours and only members carry energy; NULL restores every atom.
 extern "C" int dp_set_group(dp_ctx* c, const unsigned char* mask) {
   if (!c) return fail(nullptr, DP_ERR_ARG, "ctx is NULL");
-  return set_mask(c, mask, false);
+  return set_mask(c, mask, 0);
 }
 
 // Centres of a domain-decomposed subdomain: only marked atoms are centres and
@@ -677,7 +682,15 @@ extern "C" int dp_set_centres(dp_ctx* c, const unsigned char* mask) {
   if (mask && (c->desc.family != DP_FAMILY_ATTENTION || c->desc.message_passing))
     return fail(c, DP_ERR_UNSUPPORTED,
                 "a centres mask needs an atom-local model (ghosts of layer-coupled models evaluate as centres)");
-  return set_mask(c, mask, true);
+  return set_mask(c, mask, 1);
+}
+
+// Energy seed of a subdomain of a layer-coupled model: every atom evaluates as
+// a centre, only marked atoms carry energy and seed the adjoint; NULL
+// restores every atom.
+extern "C" int dp_set_energy_seed(dp_ctx* c, const unsigned char* mask) {
+  if (!c) return fail(nullptr, DP_ERR_ARG, "ctx is NULL");
+  return set_mask(c, mask, 2);
 }
 
 extern "C" int dp_step(dp_ctx* c, int n_steps, double dt_fs, double* coords_io, double* vel_io,

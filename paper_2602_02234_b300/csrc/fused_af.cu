@@ -1426,6 +1426,7 @@ struct FitParams {
   float* dD;              // [n][kd]
   int* status;
   int grad;               // 1: also dE/dD (the head that drives the forces); 0: energy only
+  const unsigned char* seed;  // energy seed per atom (optional): the adjoint starts from it
 };
 
 constexpr int FT_Y1 = 0;
@@ -1508,8 +1509,9 @@ __global__ void __launch_bounds__(kFitThreads, 1) k_fit(FitParams p) {
     tc::fence_before_sync();
     ok = fit_product(sm, Y2, p.f2, p.F3T + sp * p.sF3T, p.f3, p.kc2, tb, mb, wb, p.status);
     if (!ok) break;
-    // y3, energy (FP64 sum) and delta3 = F4 (1 - y3^2) into Y3
+    // y3, energy (FP64 sum) and delta3 = seed F4 (1 - y3^2) into Y3
     {
+      const float sd = p.seed && atom >= 0 && !p.seed[atom] ? 0.f : 1.f;
       double e = 0.0;
       for (int c = 0; c < p.f3; c += 32) {
         float v[32];
@@ -1519,7 +1521,7 @@ __global__ void __launch_bounds__(kFitThreads, 1) k_fit(FitParams p) {
           float y = tanhf(v[q] + p.c3[sp * p.f3 + c + q]);
           float w4 = p.F4[sp * p.f3 + c + q];
           e += (double)y * (double)w4;
-          v[q] = w4 * (1.f - y * y);
+          v[q] = sd * w4 * (1.f - y * y);
         }
         for (int q = 0; q < 32 && c + q < p.f3; q += 8) store8(Y3, t, c + q, p.f3, v + q);
       }
@@ -1722,6 +1724,10 @@ class FusedAf : public Model {
   void bind_flags(int* flags) override {
     base_.status = flags;
     fit_.status = flags;
+  }
+  bool set_energy_seed(const unsigned char* seed) override {
+    fit_.seed = seed;
+    return true;
   }
 
   bool init(const AfDims& m, const double* w, int n_atoms, const int* types, std::string* err);

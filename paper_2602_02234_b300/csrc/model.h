@@ -60,6 +60,13 @@ class Model {
   }
   // Device status word that kernels set bits of (kFlag*) instead of trapping.
   virtual void bind_flags(int* flags) { (void)flags; }
+  // Per-atom energy seed (device bytes, 1 = the atom's energy counts; null:
+  // every atom): the fitting adjoint starts from seed_i instead of 1, so the
+  // pair gradients are those of sum_i seed_i e_i.  False when unsupported.
+  virtual bool set_energy_seed(const unsigned char* seed) {
+    (void)seed;
+    return false;
+  }
 };
 
 // Plain attention family (FP32 or FP64), unfused.  nmax <= 256.

@@ -223,18 +223,19 @@ template <typename T>
 __global__ void k_fit_out(int na, int f3, int atom0, const int* __restrict__ types,
                           const T* __restrict__ y3, const T* __restrict__ F4,
                           const T* __restrict__ c4, double* __restrict__ atom_e,
-                          T* __restrict__ d3) {
+                          T* __restrict__ d3, const unsigned char* __restrict__ seed) {
   long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (wid >= na) return;
   int a = (int)wid;
   int t = types[atom0 + a];
+  const T sd = seed && !seed[atom0 + a] ? T(0) : T(1);   // energy seed of the adjoint
   double acc = 0.0;
   for (int b = lane; b < f3; b += 32) {
     T y = y3[(long long)a * f3 + b];
     T w = F4[t * f3 + b];
     acc += (double)y * (double)w;
-    d3[(long long)a * f3 + b] = w * (T(1) - y * y);
+    d3[(long long)a * f3 + b] = sd * w * (T(1) - y * y);
   }
   acc = warp_sum(acc);
   if (lane == 0) atom_e[atom0 + a] = acc + (double)c4[t];
@@ -585,6 +586,7 @@ struct PlainAf {
   T* Wt = nullptr;
   std::vector<T*> Wm, bm, U;
   T *hbuf = nullptr, *dh = nullptr, *dq = nullptr, *Gp = nullptr;
+  const unsigned char* seed = nullptr;     // energy seed (device, optional)
   // per-chunk activations
   T *d, *sw, *dsw, *s, *Rt, *rh;
   int* tj;
@@ -861,7 +863,7 @@ static int run_impl(PlainAf<T>* P, const NbrView& nv, const int* types, double* 
       launches += 3;
     }
     k_fit_out<T><<<ceil_div((long long)na * 32, 256), 256, 0, st>>>(na, m.f3, a0, types, P->y3,
-                                                                     P->F4[0], P->c4[0], atom_e, P->d3);
+                                                                     P->F4[0], P->c4[0], atom_e, P->d3, P->seed);
     launches += 1;
     // ---------------- backward
     for (int t = 0; t < S; ++t) {
@@ -1026,6 +1028,10 @@ class PlainAfModel : public Model {
   const float* grad32() const override { return grad_as<float>(); }
   const double* grad64() const override { return grad_as<double>(); }
   const double* head_energies() const override { return p_->head_e; }
+  bool set_energy_seed(const unsigned char* seed) override {
+    p_->seed = seed;
+    return true;
+  }
   size_t bytes() const override { return p_->bytes; }
 
  private:

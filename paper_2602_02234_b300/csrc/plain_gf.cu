@@ -227,16 +227,18 @@ __global__ void k_angle_out(long long P, int ed, int ed_shift, const T* __restri
 template <typename T>
 __global__ void k_fit_out(int n, int f3, const int* __restrict__ types, const T* __restrict__ y3,
                           const T* __restrict__ F4, const T* __restrict__ c4,
-                          double* __restrict__ atom_e, T* __restrict__ d3) {
+                          double* __restrict__ atom_e, T* __restrict__ d3,
+                          const unsigned char* __restrict__ seed) {
   long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (wid >= n) return;
   int a = (int)wid, t = types[a];
+  const T sd = seed && !seed[a] ? T(0) : T(1);   // energy seed of the adjoint
   double acc = 0.0;
   for (int b = lane; b < f3; b += 32) {
     T y = y3[(long long)a * f3 + b], w = F4[t * f3 + b];
     acc += (double)y * (double)w;
-    d3[(long long)a * f3 + b] = w * (T(1) - y * y);
+    d3[(long long)a * f3 + b] = sd * w * (T(1) - y * y);
   }
   acc = warp_sum(acc);
   if (lane == 0) atom_e[a] = acc + (double)c4[t];
@@ -496,6 +498,10 @@ class PlainGf : public Model {
   bool init(const GfDims& m, const double* w, int n_atoms, const int* types, std::string* err);
   int run(const NbrView& nv, const int* types, double* atom_e, cudaStream_t st) override;
   void bind_flags(int* flags) override { flags_ = flags; }
+  bool set_energy_seed(const unsigned char* seed) override {
+    seed_ = seed;
+    return true;
+  }
   // FP32 storage with every matrix product on the tensor cores (BF16 operands)
   void use_tensor_cores() { tc_ = true; }
   const float* grad32() const override { return grad_as<float>(); }
@@ -592,6 +598,7 @@ class PlainGf : public Model {
   }
   bool tc_ = false;
   int* flags_ = nullptr;
+  const unsigned char* seed_ = nullptr;   // energy seed (device, optional)
   // shared-memory variants of the angle kernels (see k_angle, k_angle_bwd)
   int angle_staged_ = 0, angle_mode_ = 0;
   size_t angle_smem_ = 0, angle_bwd_smem_ = 0;
@@ -796,7 +803,8 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
     mm(g, st);
     k += 3;
   }
-  k_fit_out<T><<<ceil_div((long long)n * 32, 256), 256, 0, st>>>(n, m.f3, types, y3_, F4_, c4_, atom_e, d3_);
+  k_fit_out<T><<<ceil_div((long long)n * 32, 256), 256, 0, st>>>(n, m.f3, types, y3_, F4_, c4_, atom_e, d3_,
+                                                                 seed_);
   for (int t = 0; t < S; ++t) {
     auto rg = fit_ranges_[t];
     if (rg.second == 0) continue;

@@ -32,7 +32,8 @@ neighbour list inside the halo; the outermost ghosts' lists are cut, but
 only their species reach the owned atoms.
 
 The evaluation of a subdomain is a callback (on a GPU, a context over owned +
-ghost atoms whose centres mask, dp_set_centres, marks the owned ones; in the
+ghost atoms whose centres mask, dp_set_centres, marks the owned ones, or for
+a layer-coupled model whose energy seed, dp_set_energy_seed, does; in the
 CPU tests the FP64 oracle), so this module holds the partitioning and the
 communication only.
 Exchanges use torch.distributed object collectives (gloo or NCCL); the design
