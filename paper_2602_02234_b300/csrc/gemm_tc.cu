@@ -139,9 +139,10 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
       if (!live) continue;
       float4* Crow = reinterpret_cast<float4*>(g.C + row * g.ldc + c);
       if (g.epi == 4) {   // angle output: t = tanh(acc + b), e_out = e_in + sa t
-        float4* Orow = reinterpret_cast<float4*>(g.v_out + row * g.ldc + c);
-        const float4* erow = reinterpret_cast<const float4*>(g.e_in + row * g.ldc + c);
-        const float sw = g.sa[row];
+        const long long xr = g.x_rows ? (long long)g.x_rows[m] : row;
+        float4* Orow = reinterpret_cast<float4*>(g.v_out + xr * g.ldc + c);
+        const float4* erow = reinterpret_cast<const float4*>(g.e_in + xr * g.ldc + c);
+        const float sw = g.sa[xr];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const float4 e = erow[q];

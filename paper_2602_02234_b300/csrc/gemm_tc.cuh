@@ -15,7 +15,8 @@ namespace dp {
 // v_out(m, n) = v and C(m, n) = e_in(m, n) + v (both 0 for an empty slot);
 // Ai, Bj, e_in, v_out laid out like C, c_rows and beta unused; or 4 the angle
 // channel's output: C(m, n) = t = tanh(acc + bias(n)) and
-// v_out(m, n) = e_in(m, n) + sa[m] t (e_in, v_out laid out like C).
+// v_out(x, n) = e_in(x, n) + sa[x] t at row x = x_rows ? x_rows[m] : row'(m)
+// (e_in, v_out with C's ldc; e_in may equal v_out).
 //   A(m, k) = A[row(m) * lda + k], row(m) = a_rows ? a_rows[m] : m; A 16-byte
 //             aligned, lda a multiple of 4
 //   B(k, n) = B[k * ldb + n]  (b_nk = 0)  or  B[n * ldb + k]  (b_nk = 1)
@@ -45,6 +46,7 @@ struct GemmTc {
   int nmax;
   const float *Ai, *Bj, *e_in, *sa;
   float* v_out;
+  const int* x_rows;   // epi 4: row of e_in, v_out and sa for m (optional)
 };
 
 bool gemm_tc_shape_ok(int N, int K);

@@ -17,6 +17,7 @@
 #include <math.h>
 
 #include <string>
+#include <algorithm>
 #include <type_traits>
 #include <vector>
 
@@ -166,10 +167,12 @@ __device__ int n_angle(const T* sa, long long base, int nmax, int na) {
 // (c) forward: a_ip for the angle slots of one atom (block per atom).
 // a_p[c] = sum_l Wphi[l][c] sum_k coef_pkl q_k[c] with coef_pkl = w_pk P_l(c_pk)
 // (0 for k = p), the coefficients and the slots' q rows staged in shared memory.
+// q and a hold the angle rows only: slot p < ca of atom i at row i ca + p
+// (ca = min(na, nmax); rows p >= the atom's angle count get a = 0).
 // Shared memory: na x na x 4 coefficients, Wphi by column (ed x 4), then
 // (staged) na x ed of q.
 template <typename T>
-__global__ void k_angle(int nmax, int na, int ed, T inv_na, const T* __restrict__ sa,
+__global__ void k_angle(int nmax, int na, int ca, int ed, T inv_na, const T* __restrict__ sa,
                         const T* __restrict__ rh, const T* __restrict__ q,
                         const T* __restrict__ Wphi, T* __restrict__ a, int staged) {
   extern __shared__ unsigned char sm_raw[];
@@ -179,7 +182,8 @@ __global__ void k_angle(int nmax, int na, int ed, T inv_na, const T* __restrict_
   long long base = (long long)i * nmax;
   int nang = n_angle(sa, base, nmax, na);
   for (int idx = threadIdx.x; idx < 4 * ed; idx += blockDim.x) W4[idx] = Wphi[(idx & 3) * ed + (idx >> 2)];
-  const T* qs = q + base * ed;
+  const long long abase = (long long)i * ca;   // this atom's first angle row
+  const T* qs = q + abase * ed;
   if (staged) {
     T* st = W4 + (size_t)ed * 4;            // na x ed
     for (int idx = threadIdx.x; idx < nang * ed; idx += blockDim.x) st[idx] = qs[idx];
@@ -195,7 +199,7 @@ __global__ void k_angle(int nmax, int na, int ed, T inv_na, const T* __restrict_
     for (int l = 0; l < 4; ++l) coef[(p * nang + k) * 4 + l] = w * P[l];
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < nmax * ed; idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < ca * ed; idx += blockDim.x) {
     int p = idx / ed, c = idx % ed;
     T out = T(0);
     if (p < nang) {
@@ -210,17 +214,21 @@ __global__ void k_angle(int nmax, int na, int ed, T inv_na, const T* __restrict_
       ld4(W4 + 4 * c, w);
       out = w[0] * s0 + w[1] * s1 + w[2] * s2 + w[3] * s3;
     }
-    a[(base + p) * ed + c] = out;
+    a[(abase + p) * ed + c] = out;
   }
 }
 
-// e_out = e1 + swa * t on angle slots
+// e += swa * t on the angle rows (t by angle row i ca + p, e and swa by slot
+// i nmax + p; the other slots keep e_{l+1} = e1, swa being 0 there)
 template <typename T>
-__global__ void k_angle_out(long long P, int ed, int ed_shift, const T* __restrict__ sa,
-                            const T* __restrict__ e1, const T* __restrict__ t, T* __restrict__ out) {
+__global__ void k_angle_out(long long PA, int ed, int ed_shift, int nmax, int ca,
+                            const T* __restrict__ sa, const T* __restrict__ t, T* __restrict__ e) {
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= P * ed) return;
-  out[idx] = e1[idx] + sa[slot_of(idx, ed, ed_shift)] * t[idx];
+  if (idx >= PA * ed) return;
+  const long long m = slot_of(idx, ed, ed_shift), i = m / ca;
+  const long long row = i * nmax + (m - i * ca);
+  const int c = (int)(idx - m * ed);
+  e[row * ed + c] += sa[row] * t[idx];
 }
 
 // e_i = y3 . F4 + c4 (FP64) and delta3
@@ -245,20 +253,22 @@ __global__ void k_fit_out(int n, int f3, const int* __restrict__ types, const T*
 }
 
 // ------------------------------------------------------------------ adjoint kernels
-// (c): dsa += de . t, dz = de * swa * (1 - t^2) on angle slots
+// (c): dsa += de . t, dz = de * swa * (1 - t^2) on the angle rows (t, dz by
+// angle row m = i ca + p; de, swa, dsa by slot i nmax + p)
 template <typename T>
-__global__ void k_angle_out_bwd(long long P, int ed, const T* __restrict__ sa,
+__global__ void k_angle_out_bwd(long long PA, int ed, int nmax, int ca, const T* __restrict__ sa,
                                 const T* __restrict__ t, const T* __restrict__ de,
                                 T* __restrict__ dz, T* __restrict__ dsa_e) {
-  long long e = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  long long m = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
-  if (e >= P) return;
+  if (m >= PA) return;
+  const long long i = m / ca, e = i * nmax + (m - i * ca);
   T s = sa[e];
   T acc = T(0);
   for (int c = lane; c < ed; c += 32) {
-    T tv = t[e * ed + c], g = de[e * ed + c];
+    T tv = t[m * ed + c], g = de[e * ed + c];
     acc += g * tv;
-    dz[e * ed + c] = g * s * (T(1) - tv * tv);
+    dz[m * ed + c] = g * s * (T(1) - tv * tv);
   }
   acc = warp_sum(acc);
   if (lane == 0 && s > T(0)) dsa_e[e] += acc;
@@ -270,9 +280,9 @@ __global__ void k_angle_out_bwd(long long P, int ed, const T* __restrict__ sa,
 // angle slots' da and q rows (na rows of ed, stored with stride ed + 1 so that
 // threads on different rows of one column hit different banks).  Mode 0
 // recomputes the coefficients per column (the host picks the largest mode
-// that fits).
+// that fits).  q, da and dq hold the angle rows only (row i ca + p).
 template <typename T>
-__global__ void k_angle_bwd(int nmax, int na, int ed, T inv_na, const T* __restrict__ sa,
+__global__ void k_angle_bwd(int nmax, int na, int ca, int ed, T inv_na, const T* __restrict__ sa,
                             const T* __restrict__ rh, const T* __restrict__ q,
                             const T* __restrict__ Wphi, const T* __restrict__ da,
                             T* __restrict__ dq, T* __restrict__ dsa_e, T* __restrict__ drh,
@@ -285,8 +295,9 @@ __global__ void k_angle_bwd(int nmax, int na, int ed, T inv_na, const T* __restr
   long long base = (long long)i * nmax;
   int nang = n_angle(sa, base, nmax, na);
   for (int idx = threadIdx.x; idx < 4 * ed; idx += blockDim.x) W4[idx] = Wphi[(idx & 3) * ed + (idx >> 2)];
-  const T* das = da + base * ed;
-  const T* qs = q + base * ed;
+  const long long abase = (long long)i * ca;   // this atom's first angle row
+  const T* das = da + abase * ed;
+  const T* qs = q + abase * ed;
   int ld = ed;
   if (mode == 2) {
     ld = ed + 1;
@@ -313,7 +324,7 @@ __global__ void k_angle_bwd(int nmax, int na, int ed, T inv_na, const T* __restr
   }
   __syncthreads();
   // dq_k[c] = sum_l Wphi[l][c] sum_p coef_pkl da_p[c]
-  for (int idx = threadIdx.x; idx < nmax * ed; idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < ca * ed; idx += blockDim.x) {
     int k = idx / ed, c = idx % ed;
     T out = T(0);
     if (k < nang) {
@@ -337,7 +348,7 @@ __global__ void k_angle_bwd(int nmax, int na, int ed, T inv_na, const T* __restr
       ld4(W4 + 4 * c, w);
       out = w[0] * s0 + w[1] * s1 + w[2] * s2 + w[3] * s3;
     }
-    dq[(base + k) * ed + c] = out;
+    dq[(abase + k) * ed + c] = out;
   }
   // dcoef_pkl = sum_c da_p[c] Wphi[l][c] q_k[c]  (one thread per (p, k))
   for (int pk = threadIdx.x; pk < nang * nang; pk += blockDim.x) {
@@ -554,7 +565,7 @@ class PlainGf : public Model {
       t.M = (int)((long long)n_ * m_.nmax); t.N = Ed; t.K = Ed;
       t.A = ee_[l]; t.lda = Ed;
       t.B = Wc_[l]; t.ldb = Ed; t.b_nk = 0;
-      t.C = e1_[l]; t.ldc = Ed;
+      t.C = ee_[l + 1]; t.ldc = Ed;   // e1; the angle channel then updates its rows in place
       t.bias = be_[l]; t.epi = 3;
       t.sel_j = nv.sel_j; t.nmax = m_.nmax; t.Ai = Ai_; t.Bj = Bj_; t.e_in = ee_[l]; t.v_out = vv_[l];
       t.status = flags_;
@@ -571,18 +582,19 @@ class PlainGf : public Model {
     }
   }
   // mixed form: t = tanh(a Wq + bq) and e_{l+1} = e1 + swa t in one product's
-  // epilogue; false when not applicable
+  // epilogue, over the angle rows (e_{l+1} holds e1 and is updated in place);
+  // false when not applicable
   bool angle_out_fused(int l, cudaStream_t st) {
     if constexpr (std::is_same<T, float>::value) {
       const int Ed = m_.ed;
       if (!tc_ || !gemm_tc_shape_ok(Ed, Ed) || Ed % 4 != 0) return false;
       GemmTc t{};
-      t.M = (int)((long long)n_ * m_.nmax); t.N = Ed; t.K = Ed;
+      t.M = (int)((long long)n_ * nac_); t.N = Ed; t.K = Ed;
       t.A = aa_; t.lda = Ed;
       t.B = Wq_[l]; t.ldb = Ed; t.b_nk = 0;
       t.C = tt_[l]; t.ldc = Ed;
       t.bias = bq_[l]; t.epi = 4;
-      t.sa = sa_; t.e_in = e1_[l]; t.v_out = ee_[l + 1];
+      t.sa = sa_; t.e_in = ee_[l + 1]; t.v_out = ee_[l + 1]; t.x_rows = ang_rows_;
       t.status = flags_;
 #ifdef DP_GF_BF16
       t.fp16 = 0;
@@ -629,6 +641,10 @@ class PlainGf : public Model {
   GfDims m_{};
   int n_ = 0;
   long long P_ = 0;
+  // the angle channel works on angle rows only: slot p < nac_ = min(na, nmax)
+  // of atom i is angle row i nac_ + p, at slot ang_rows_[i nac_ + p] = i nmax + p
+  int nac_ = 0;
+  int* ang_rows_ = nullptr;
   // weights
   T *Wt_, *we_, *be0_;
   std::vector<T*> Wm_, Wn_, bn_, Wa_, Wb_, Wc_, be_, Wp_, Wphi_, Wq_, bq_;
@@ -639,11 +655,11 @@ class PlainGf : public Model {
   // geometry
   T *d_, *sw_, *dsw_, *sa_, *dsa_, *s_, *rh_;
   // states
-  std::vector<T*> nn_, ee_, e1_, hh_, uu_, mm_, vv_, qq_, tt_;
+  std::vector<T*> nn_, ee_, hh_, uu_, mm_, vv_, qq_, tt_;   // qq_, tt_ by angle row
   T *Ai_, *Bj_, *Ce_, *aa_;
   T *y1_, *y2_, *y3_, *d1_, *d2_, *d3_;
   // adjoint
-  T *dn_, *dn1_, *de_, *dy_, *dz_, *da_, *dq_, *du_, *dx_, *dnm_, *X_, *sdy_, *gat_;
+  T *dn_, *dn1_, *de_, *dy_, *dz_, *da_, *dq_, *du_, *dx_, *dnm_, *X_, *sdy_, *gat_;   // aa_, dz_, da_, dq_ by angle row
   T *dsw_e_, *dsa_e_, *drh_, *g_;
   std::vector<void*> allocs_;
   size_t bytes_ = 0;
@@ -695,16 +711,24 @@ bool PlainGf<T>::init(const GfDims& m, const double* w, int n_atoms, const int* 
   if (!dalloc(&fit_rows_, rows.size(), err)) return false;
   if (!rows.empty()) cudaMemcpy(fit_rows_, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice);
   const size_t N = n_atoms, P = P_;
+  nac_ = std::min(m.na, NM);
+  const size_t PA = (size_t)n_atoms * nac_;
+  {
+    std::vector<int> ar(PA);
+    for (size_t q = 0; q < PA; ++q) ar[q] = (int)((q / nac_) * NM + q % nac_);
+    if (!dalloc(&ang_rows_, PA, err)) return false;
+    if (PA) cudaMemcpy(ang_rows_, ar.data(), sizeof(int) * PA, cudaMemcpyHostToDevice);
+  }
   ok = dalloc(&d_, P, err) && dalloc(&sw_, P, err) && dalloc(&dsw_, P, err) &&
        dalloc(&sa_, P, err) && dalloc(&dsa_, P, err) && dalloc(&s_, P, err) &&
        dalloc(&rh_, 3 * P, err);
   nn_.resize(L + 1); ee_.resize(L + 1);
-  e1_.resize(L); hh_.resize(L); uu_.resize(L); mm_.resize(L); vv_.resize(L); qq_.resize(L); tt_.resize(L);
+  hh_.resize(L); uu_.resize(L); mm_.resize(L); vv_.resize(L); qq_.resize(L); tt_.resize(L);
   for (int l = 0; l <= L && ok; ++l) ok = dalloc(&nn_[l], N * Nd, err) && dalloc(&ee_[l], P * Ed, err);
   for (int l = 0; l < L && ok; ++l)
-    ok = dalloc(&e1_[l], P * Ed, err) && dalloc(&hh_[l], N * Nd, err) && dalloc(&uu_[l], N * Ed, err) &&
-         dalloc(&mm_[l], N * Ed, err) && dalloc(&vv_[l], P * Ed, err) && dalloc(&qq_[l], P * Ed, err) &&
-         dalloc(&tt_[l], P * Ed, err);
+    ok = dalloc(&hh_[l], N * Nd, err) && dalloc(&uu_[l], N * Ed, err) &&
+         dalloc(&mm_[l], N * Ed, err) && dalloc(&vv_[l], P * Ed, err) && dalloc(&qq_[l], PA * Ed, err) &&
+         dalloc(&tt_[l], PA * Ed, err);
   // the angle kernels stage as much as fits in 227 KB of shared memory
   const size_t kMaxSmem = 232448, na2 = (size_t)m.na * m.na * 4 * sizeof(T),
                w4 = (size_t)m.ed * 4 * sizeof(T),
@@ -722,11 +746,11 @@ bool PlainGf<T>::init(const GfDims& m, const double* w, int n_atoms, const int* 
     return false;
   }
   ok = ok && dalloc(&Ai_, N * Ed, err) && dalloc(&Bj_, N * Ed, err) && dalloc(&Ce_, P * Ed, err) &&
-       dalloc(&aa_, P * Ed, err) && dalloc(&y1_, N * m.f1, err) && dalloc(&y2_, N * m.f2, err) &&
+       dalloc(&aa_, PA * Ed, err) && dalloc(&y1_, N * m.f1, err) && dalloc(&y2_, N * m.f2, err) &&
        dalloc(&y3_, N * m.f3, err) && dalloc(&d1_, N * m.f1, err) && dalloc(&d2_, N * m.f2, err) &&
        dalloc(&d3_, N * m.f3, err) && dalloc(&dn_, N * Nd, err) && dalloc(&dn1_, N * Nd, err) &&
        dalloc(&de_, P * Ed, err) && dalloc(&dy_, P * Ed, err) &&
-       dalloc(&dz_, P * Ed, err) && dalloc(&da_, P * Ed, err) && dalloc(&dq_, P * Ed, err) &&
+       dalloc(&dz_, PA * Ed, err) && dalloc(&da_, PA * Ed, err) && dalloc(&dq_, PA * Ed, err) &&
        dalloc(&du_, N * Ed, err) && dalloc(&dx_, N * Nd, err) && dalloc(&dnm_, N * (Nd + Ed), err) &&
        dalloc(&X_, P * Ed, err) && dalloc(&sdy_, N * Ed, err) && dalloc(&gat_, N * Ed, err) &&
        dalloc(&dsw_e_, P, err) && dalloc(&dsa_e_, P, err) && dalloc(&drh_, 3 * P, err) &&
@@ -740,6 +764,8 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
   const int Nd = m.nd, Ed = m.ed, L = m.n_layers, NM = m.nmax, NA = m.na, S = m.n_species, n = n_;
   const long long P = P_, PE = P * Ed;
   const T inv_nmax = T(1) / T(NM), inv_na = T(1) / T(NA);
+  const int CA = nac_;
+  const long long PA = (long long)n * CA;
   int k = 0;
   auto grid = [](long long n_) { return ceil_div(n_, 256); };
   k_env<T><<<grid(P), 256, 0, st>>>(P, NM, NA, nv.sel_j, nv.sel_r, m.rs, m.rc, m.rsa, m.rca, d_, sw_,
@@ -770,20 +796,24 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
     } else {
       mm(gemm_rowmajor<T>((int)P, Ed, Ed, ee_[l], Ed, Wc_[l], Ed, Ce_, Ed), st);
       k_edge<T><<<grid(PE), 256, 0, st>>>(P, NM, Ed, ed_shift, nv.sel_j, Ai_, Bj_, Ce_, be_[l],
-                                          ee_[l], vv_[l], e1_[l]);
+                                          ee_[l], vv_[l], ee_[l + 1]);
     }
-    // (c)
-    mm(gemm_rowmajor<T>((int)P, Ed, Ed, e1_[l], Ed, Wp_[l], Ed, qq_[l], Ed), st);
-    k_angle<T><<<n, 256, angle_smem, st>>>(NM, NA, Ed, inv_na, sa_, rh_, qq_[l], Wphi_[l], aa_,
+    // (c) on the angle rows; e_{l+1} holds e1 until the angle update below
+    {
+      Gemm<T> g = gemm_rowmajor<T>((int)PA, Ed, Ed, ee_[l + 1], Ed, Wp_[l], Ed, qq_[l], Ed);
+      g.a_rows = ang_rows_;
+      mm(g, st);
+    }
+    k_angle<T><<<n, 256, angle_smem, st>>>(NM, NA, CA, Ed, inv_na, sa_, rh_, qq_[l], Wphi_[l], aa_,
                                            angle_staged_);
     if (angle_out_fused(l, st)) {
       --k;   // one launch instead of two
     } else {
-      Gemm<T> g = gemm_rowmajor<T>((int)P, Ed, Ed, aa_, Ed, Wq_[l], Ed, tt_[l], Ed);
+      Gemm<T> g = gemm_rowmajor<T>((int)PA, Ed, Ed, aa_, Ed, Wq_[l], Ed, tt_[l], Ed);
       g.bias = bq_[l];
       g.epi = 1;
       mm(g, st);
-      k_angle_out<T><<<grid(PE), 256, 0, st>>>(P, Ed, ed_shift, sa_, e1_[l], tt_[l], ee_[l + 1]);
+      k_angle_out<T><<<grid(PA * Ed), 256, 0, st>>>(PA, Ed, ed_shift, NM, CA, sa_, tt_[l], ee_[l + 1]);
     }
     k += 14;
   }
@@ -832,23 +862,24 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
   k += 5;
   for (int l = L - 1; l >= 0; --l) {
     // (c): de holds dE/de_{l+1}; it becomes dE/de1 in place (e_{l+1} = e1 + swa t)
-    k_angle_out_bwd<T><<<grid(P * 32), 256, 0, st>>>(P, Ed, sa_, tt_[l], de_, dz_, dsa_e_);
-    {  // da = dz Wq^T
+    k_angle_out_bwd<T><<<grid(PA * 32), 256, 0, st>>>(PA, Ed, NM, CA, sa_, tt_[l], de_, dz_, dsa_e_);
+    {  // da = dz Wq^T (angle rows)
       Gemm<T> g{};
-      g.M = (int)P; g.N = Ed; g.K = Ed;
+      g.M = (int)PA; g.N = Ed; g.K = Ed;
       g.A = dz_; g.a_rm = Ed; g.a_rk = 1;
       g.B = Wq_[l]; g.b_rk = 1; g.b_rn = Ed;
       g.C = da_; g.c_rm = Ed; g.c_rn = 1; g.nb2 = 1; g.alpha = T(1);
       mm(g, st);
     }
-    k_angle_bwd<T><<<n, 256, angle_bwd_smem, st>>>(NM, NA, Ed, inv_na, sa_, rh_, qq_[l], Wphi_[l], da_,
-                                                   dq_, dsa_e_, drh_, angle_mode_);
-    {  // de1 = de + dq Wp^T, in place
+    k_angle_bwd<T><<<n, 256, angle_bwd_smem, st>>>(NM, NA, CA, Ed, inv_na, sa_, rh_, qq_[l], Wphi_[l],
+                                                   da_, dq_, dsa_e_, drh_, angle_mode_);
+    {  // de1 = de + dq Wp^T, in place on the angle rows' slots (dq is 0 elsewhere)
       Gemm<T> g{};
-      g.M = (int)P; g.N = Ed; g.K = Ed;
+      g.M = (int)PA; g.N = Ed; g.K = Ed;
       g.A = dq_; g.a_rm = Ed; g.a_rk = 1;
       g.B = Wp_[l]; g.b_rk = 1; g.b_rn = Ed;
       g.C = de_; g.c_rm = Ed; g.c_rn = 1; g.nb2 = 1; g.alpha = T(1); g.beta = T(1);
+      g.c_rows = ang_rows_;
       mm(g, st);
     }
     // (b): de now holds dE/de1; it becomes dE/de_l (e1 = e_l + tanh(...))
