@@ -45,8 +45,42 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
     tc::tmem_alloc(&tptr, (uint32_t)tmem_cols);
     tc::tmem_relinquish();
   }
-  // B once: stored rows x cols (K x N, or N x K when b_nk), row-major in global
-  for (int i = t; i < brows * bcols; i += kRows) {
+  // B once: stored rows x cols (K x N, or N x K when b_nk), row-major in global;
+  // by float4 with eight reads in flight per thread when rows are 16-byte aligned
+  const bool bvec = (bcols & 3) == 0 && (g.ldb & 3) == 0 &&
+                    (reinterpret_cast<uintptr_t>(g.B) & 15) == 0;
+  if (bvec) {
+    const int cq = bcols >> 2, total4 = brows * cq;
+    constexpr int kBLoads = 8;
+    for (int base = 0; base < total4; base += kRows * kBLoads) {
+      float4 v[kBLoads];
+#pragma unroll
+      for (int u = 0; u < kBLoads; ++u) {
+        const int i = base + u * kRows + t;
+        v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < total4) {
+          const int r = i / cq, c = (i - r * cq) << 2;
+          v[u] = *reinterpret_cast<const float4*>(g.B + (long long)r * g.ldb + c);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kBLoads; ++u) {
+        const int i = base + u * kRows + t;
+        if (i >= total4) break;
+        const int r = i / cq, c = (i - r * cq) << 2;
+        uint2 w;
+        if (g.fp16) {
+          w.x = tc::pack_f16(v[u].x, v[u].y);
+          w.y = tc::pack_f16(v[u].z, v[u].w);
+        } else {
+          w.x = tc::pack_bf16(v[u].x, v[u].y);
+          w.y = tc::pack_bf16(v[u].z, v[u].w);
+        }
+        *reinterpret_cast<uint2*>(Bs + tc::kmajor_off(r, c, bcols)) = w;
+      }
+    }
+  }
+  for (int i = bvec ? brows * bcols : t; i < brows * bcols; i += kRows) {
     const int r = i / bcols, c = i - r * bcols;
     const float x = g.B[(long long)r * g.ldb + c];
     uint16_t h;

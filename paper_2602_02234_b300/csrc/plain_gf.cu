@@ -46,6 +46,13 @@ __device__ __forceinline__ void ld4(const double* p, double* v) {
   const double2 u = reinterpret_cast<const double2*>(p)[0], w = reinterpret_cast<const double2*>(p)[1];
   v[0] = u.x; v[1] = u.y; v[2] = w.x; v[3] = w.y;
 }
+__device__ __forceinline__ void st4(float* p, const float* v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double* v) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
 
 
 // ------------------------------------------------------------------ kernels
@@ -156,65 +163,188 @@ __device__ __forceinline__ void legendre4(double c, double* P, double* dP) {
 
 constexpr int kMaxNa = 64;
 
-// number of angle slots of atom i (a prefix of the nearest-first list)
+// Angle-channel blocks: kAngThreads threads per atom.  The products over the
+// angle slots are register-tiled: a thread owns a 4 x 4 block of outputs
+// (4 slot rows x the columns cg + 16 j, j < 4, of a 64-column block, cg =
+// thread mod 16) and keeps the four Legendre orders' partial sums of each in
+// registers, so one pass over the summed index reads 4 row values and 4
+// coefficient quadruples per 64 multiply-adds.  Rows beyond the atom's angle
+// count are computed from clamped (valid) rows and never stored.
+constexpr int kAngThreads = 128;
+
+// coef[(p na + k) 4 + l] = w_pk P_l(c_pk) for p, k < nang, 0 elsewhere (also
+// for p == k and for the padding rows up to ra = na rounded up to 4), from
+// the slots' switches gsa and unit vectors grh staged in shared memory
 template <typename T>
-__device__ int n_angle(const T* sa, long long base, int nmax, int na) {
-  int k = 0;
-  while (k < na && k < nmax && sa[base + k] > T(0)) ++k;
-  return k;
+__device__ void angle_coef(T* coef, int na, int ra, int nang, const T* gsa, const T* grh,
+                           T inv_na) {
+  for (int pk = threadIdx.x; pk < ra * na; pk += blockDim.x) {
+    const int p = pk / na, k = pk - p * na;
+    T P[4] = {T(0), T(0), T(0), T(0)}, dP[4];
+    T w = T(0);
+    if (p < nang && k < nang && p != k) {
+      const T* rp = grh + 3 * p;
+      const T* rk = grh + 3 * k;
+      legendre4(rp[0] * rk[0] + rp[1] * rk[1] + rp[2] * rk[2], P, dP);
+      w = inv_na * gsa[p] * gsa[k];
+    }
+#pragma unroll
+    for (int l = 0; l < 4; ++l) coef[(size_t)pk * 4 + l] = w * P[l];
+  }
 }
 
-// (c) forward: a_ip for the angle slots of one atom (block per atom).
-// a_p[c] = sum_l Wphi[l][c] sum_k coef_pkl q_k[c] with coef_pkl = w_pk P_l(c_pk)
-// (0 for k = p), the coefficients and the slots' q rows staged in shared memory.
-// q and a hold the angle rows only: slot p < ca of atom i at row i ca + p
-// (ca = min(na, nmax); rows p >= the atom's angle count get a = 0).
-// Shared memory: na x na x 4 coefficients, Wphi by column (ed x 4), then
-// (staged) na x ed of q.
+// Asynchronous element copies global -> shared (cp.async, completion per
+// thread by commit group; a block barrier then publishes them)
 template <typename T>
-__global__ void k_angle(int nmax, int na, int ca, int ed, T inv_na, const T* __restrict__ sa,
-                        const T* __restrict__ rh, const T* __restrict__ q,
-                        const T* __restrict__ Wphi, T* __restrict__ a, int staged) {
-  extern __shared__ unsigned char sm_raw[];
-  T* coef = reinterpret_cast<T*>(sm_raw);  // na x na x 4
-  T* W4 = coef + (size_t)na * na * 4;      // ed x 4: Wphi[l][c] at W4[4 c + l]
-  int i = blockIdx.x;
-  long long base = (long long)i * nmax;
-  int nang = n_angle(sa, base, nmax, na);
-  for (int idx = threadIdx.x; idx < 4 * ed; idx += blockDim.x) W4[idx] = Wphi[(idx & 3) * ed + (idx >> 2)];
-  const long long abase = (long long)i * ca;   // this atom's first angle row
-  const T* qs = q + abase * ed;
-  if (staged) {
-    T* st = W4 + (size_t)ed * 4;            // na x ed
-    for (int idx = threadIdx.x; idx < nang * ed; idx += blockDim.x) st[idx] = qs[idx];
-    qs = st;
-  }
-  for (int pk = threadIdx.x; pk < nang * nang; pk += blockDim.x) {
-    int p = pk / nang, k = pk % nang;
-    T P[4], dP[4];
-    const T* rp = rh + 3 * (base + p);
-    const T* rk = rh + 3 * (base + k);
-    legendre4(rp[0] * rk[0] + rp[1] * rk[1] + rp[2] * rk[2], P, dP);
-    T w = (p == k) ? T(0) : inv_na * sa[base + p] * sa[base + k];
-    for (int l = 0; l < 4; ++l) coef[(p * nang + k) * 4 + l] = w * P[l];
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < ca * ed; idx += blockDim.x) {
-    int p = idx / ed, c = idx % ed;
-    T out = T(0);
-    if (p < nang) {
-      T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-      for (int k = 0; k < nang; ++k) {
-        const T qk = qs[k * ed + c];
-        T cf[4];
-        ld4(coef + (p * nang + k) * 4, cf);
-        s0 += cf[0] * qk; s1 += cf[1] * qk; s2 += cf[2] * qk; s3 += cf[3] * qk;
-      }
-      T w[4];
-      ld4(W4 + 4 * c, w);
-      out = w[0] * s0 + w[1] * s1 + w[2] * s2 + w[3] * s3;
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// The angle kernels are persistent: a block loops over atoms i = blockIdx.x,
+// + gridDim.x, ... and, while it works on one atom, copies the next atom's
+// slot data into the other of two buffers.  A buffer holds the slots'
+// switches (na), unit vectors (3 na) and, when staged, rows of up to two
+// (rows x ed) arrays with stride ed + 1 (the rows of one column then fall in
+// different banks).
+template <typename T>
+struct AngleBuf {
+  T *sa, *rh, *r0, *r1;
+};
+template <typename T>
+__device__ __forceinline__ AngleBuf<T> angle_buf(T* start, int na, int ed, int nrows, int b) {
+  const size_t one = 4 * (size_t)na + (size_t)nrows * na * (ed + 1);
+  T* p = start + (size_t)b * one;
+  AngleBuf<T> u;
+  u.sa = p;
+  u.rh = p + na;
+  u.r0 = nrows > 0 ? p + 4 * (size_t)na : nullptr;
+  u.r1 = nrows > 1 ? u.r0 + (size_t)na * (ed + 1) : nullptr;
+  return u;
+}
+// start the copies of atom i's slot data into u (one commit group per thread)
+template <typename T>
+__device__ __forceinline__ void angle_fetch(const AngleBuf<T>& u, int ca, int ed, long long base,
+                                            long long abase, const T* sa, const T* rh, const T* x0,
+                                            const T* x1) {
+  if (threadIdx.x < ca) cp_async_elem(u.sa + threadIdx.x, sa + base + threadIdx.x);
+  for (int idx = threadIdx.x; idx < 3 * ca; idx += blockDim.x) cp_async_elem(u.rh + idx, rh + 3 * base + idx);
+  const int total = ca * ed;
+  if (u.r0)
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+      const int p = idx / ed;
+      cp_async_elem(u.r0 + p * (ed + 1) + (idx - p * ed), x0 + abase * ed + idx);
     }
-    a[(abase + p) * ed + c] = out;
+  if (u.r1)
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+      const int p = idx / ed;
+      cp_async_elem(u.r1 + p * (ed + 1) + (idx - p * ed), x1 + abase * ed + idx);
+    }
+  cp_async_commit();
+}
+// Next atom's copies started, this atom's awaited; returns the angle count
+// (the slots with swa > 0, a prefix of the nearest-first list), counted by
+// the block barrier that also publishes the copies.  Thread t < ca copied
+// switch t itself, so it may read it before the barrier.
+template <typename T>
+__device__ __forceinline__ int angle_next(const AngleBuf<T>& cur, const AngleBuf<T>& nxt, int i, int n,
+                                          int nmax, int ca, int ed, const T* sa, const T* rh,
+                                          const T* x0, const T* x1) {
+  const int nx = i + gridDim.x;
+  if (nx < n) {
+    angle_fetch(nxt, ca, ed, (long long)nx * nmax, (long long)nx * ca, sa, rh, x0, x1);
+    cp_async_wait<1>();
+  } else {
+    cp_async_wait<0>();
+  }
+  return __syncthreads_count(threadIdx.x < ca && cur.sa[threadIdx.x] > T(0));
+}
+
+// (c) forward: a_p[c] = sum_l Wphi[l][c] sum_k coef_pkl q_k[c] for the angle
+// slots p of each atom.  q and a hold the angle rows only: slot p < ca of atom
+// i at row i ca + p (ca = min(na, nmax)); rows from the atom's angle count up
+// to ca get a = 0.  Shared memory: the coefficients (ra x na x 4), Wphi by
+// column (ed x 4, Wphi[l][c] at W4[4 c + l]), then two slot-data buffers
+// (q rows staged when `staged`).
+template <typename T>
+__global__ void __launch_bounds__(kAngThreads) k_angle(int n, int nmax, int na, int ca, int ed, T inv_na,
+                                                       const T* __restrict__ sa,
+                                                       const T* __restrict__ rh,
+                                                       const T* __restrict__ q,
+                                                       const T* __restrict__ Wphi,
+                                                       T* __restrict__ a, int staged) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int ra = (na + 3) & ~3;
+  T* coef = reinterpret_cast<T*>(sm_raw);
+  T* W4 = coef + (size_t)ra * na * 4;
+  T* bufs = W4 + (size_t)ed * 4;
+  for (int idx = threadIdx.x; idx < 4 * ed; idx += blockDim.x) W4[idx] = Wphi[(idx & 3) * ed + (idx >> 2)];
+  const int nrows = staged ? 1 : 0;
+  int i = blockIdx.x;
+  if (i < n) angle_fetch(angle_buf(bufs, na, ed, nrows, 0), ca, ed, (long long)i * nmax, (long long)i * ca, sa, rh, q, q);
+  for (int it = 0; i < n; ++it, i += gridDim.x) {
+    const AngleBuf<T> cur = angle_buf(bufs, na, ed, nrows, it & 1);
+    const int nang = angle_next(cur, angle_buf(bufs, na, ed, nrows, (it + 1) & 1), i, n, nmax, ca, ed, sa,
+                                rh, q, q);
+    const long long abase = (long long)i * ca;
+    const T* qs = staged ? cur.r0 : q + abase * ed;
+    const int ld = staged ? ed + 1 : ed;
+    angle_coef(coef, na, ra, nang, cur.sa, cur.rh, inv_na);
+    __syncthreads();
+    const int cg = threadIdx.x & 15;
+    const int ntile = (nang + 3) >> 2;
+    for (int cb = 0; cb < ed; cb += 64)
+      for (int rt = threadIdx.x >> 4; rt < ntile; rt += kAngThreads / 16) {
+        const int p0 = 4 * rt;
+        int cc[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cc[j] = min(cb + cg + 16 * j, ed - 1);
+        T acc[4][4][4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int l = 0; l < 4; ++l) acc[x][j][l] = T(0);
+        for (int k = 0; k < nang; ++k) {
+          T qv[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) qv[j] = qs[k * ld + cc[j]];
+#pragma unroll
+          for (int x = 0; x < 4; ++x) {
+            T cf[4];
+            ld4(coef + ((size_t)(p0 + x) * na + k) * 4, cf);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+              for (int l = 0; l < 4; ++l) acc[x][j][l] += cf[l] * qv[j];
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c = cb + cg + 16 * j;
+          if (c >= ed) continue;
+          T w[4];
+          ld4(W4 + 4 * c, w);
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+            if (p0 + x < nang)
+              a[(abase + p0 + x) * ed + c] =
+                  w[0] * acc[x][j][0] + w[1] * acc[x][j][1] + w[2] * acc[x][j][2] + w[3] * acc[x][j][3];
+        }
+      }
+    for (int idx = threadIdx.x; idx < (ca - nang) * ed; idx += blockDim.x)
+      a[(abase + nang) * ed + idx] = T(0);
+    __syncthreads();   // the coefficients and this buffer are rewritten next
   }
 }
 
@@ -274,131 +404,170 @@ __global__ void k_angle_out_bwd(long long PA, int ed, int nmax, int ca, const T*
   if (lane == 0 && s > T(0)) dsa_e[e] += acc;
 }
 
-// (c) adjoint of a_ip: dq, and the switch / unit-vector terms; block per atom.
-// Shared memory: the adjoints dcoef_pkl (na x na x 4); with mode >= 1 also the
-// coefficients coef_pkl = w_pk P_l(c_pk) (0 for k = p), with mode 2 also the
-// angle slots' da and q rows (na rows of ed, stored with stride ed + 1 so that
-// threads on different rows of one column hit different banks).  Mode 0
-// recomputes the coefficients per column (the host picks the largest mode
-// that fits).  q, da and dq hold the angle rows only (row i ca + p).
+// (c) adjoint of a_p for each atom: dq, then the switch and unit-vector
+// terms through dcoef_pkl = sum_c da_p[c] Wphi[l][c] q_k[c].  q, da and dq
+// hold the angle rows only (row i ca + p).  Shared memory: the coefficients
+// (ra x na x 4; overwritten by dcoef once dq is done), Wphi by column (ed x
+// 4), then two slot-data buffers (da and q rows staged when `staged`).
 template <typename T>
-__global__ void k_angle_bwd(int nmax, int na, int ca, int ed, T inv_na, const T* __restrict__ sa,
-                            const T* __restrict__ rh, const T* __restrict__ q,
-                            const T* __restrict__ Wphi, const T* __restrict__ da,
-                            T* __restrict__ dq, T* __restrict__ dsa_e, T* __restrict__ drh,
-                            int mode) {
-  extern __shared__ unsigned char sm_raw[];
-  T* dcoef = reinterpret_cast<T*>(sm_raw);  // na x na x 4
-  T* W4 = dcoef + (size_t)na * na * 4;      // ed x 4: Wphi[l][c] at W4[4 c + l]
-  T* coef = W4 + (size_t)ed * 4;            // na x na x 4 (mode >= 1)
-  int i = blockIdx.x;
-  long long base = (long long)i * nmax;
-  int nang = n_angle(sa, base, nmax, na);
+__global__ void __launch_bounds__(kAngThreads) k_angle_bwd(int n, int nmax, int na, int ca, int ed, T inv_na,
+                                                           const T* __restrict__ sa,
+                                                           const T* __restrict__ rh,
+                                                           const T* __restrict__ q,
+                                                           const T* __restrict__ Wphi,
+                                                           const T* __restrict__ da,
+                                                           T* __restrict__ dq, T* __restrict__ dsa_e,
+                                                           T* __restrict__ drh, int staged) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int ra = (na + 3) & ~3;
+  T* coef = reinterpret_cast<T*>(sm_raw);   // later dcoef
+  T* W4 = coef + (size_t)ra * na * 4;
+  T* bufs = W4 + (size_t)ed * 4;
   for (int idx = threadIdx.x; idx < 4 * ed; idx += blockDim.x) W4[idx] = Wphi[(idx & 3) * ed + (idx >> 2)];
-  const long long abase = (long long)i * ca;   // this atom's first angle row
-  const T* das = da + abase * ed;
-  const T* qs = q + abase * ed;
-  int ld = ed;
-  if (mode == 2) {
-    ld = ed + 1;
-    T* s_da = coef + (size_t)na * na * 4;
-    T* s_q = s_da + (size_t)na * ld;
-    for (int idx = threadIdx.x; idx < nang * ed; idx += blockDim.x) {
-      const int p = idx / ed, c = idx - p * ed;
-      s_da[p * ld + c] = das[idx];
-      s_q[p * ld + c] = qs[idx];
-    }
-    das = s_da;
-    qs = s_q;
-  }
-  if (mode >= 1) {
-    for (int pk = threadIdx.x; pk < nang * nang; pk += blockDim.x) {
-      int p = pk / nang, k = pk % nang;
-      T P[4], dP[4];
-      const T* rp = rh + 3 * (base + p);
-      const T* rk = rh + 3 * (base + k);
-      legendre4(rp[0] * rk[0] + rp[1] * rk[1] + rp[2] * rk[2], P, dP);
-      T w = (p == k) ? T(0) : inv_na * sa[base + p] * sa[base + k];
-      for (int l = 0; l < 4; ++l) coef[pk * 4 + l] = w * P[l];
-    }
-  }
-  __syncthreads();
-  // dq_k[c] = sum_l Wphi[l][c] sum_p coef_pkl da_p[c]
-  for (int idx = threadIdx.x; idx < ca * ed; idx += blockDim.x) {
-    int k = idx / ed, c = idx % ed;
-    T out = T(0);
-    if (k < nang) {
-      T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-      const T* rk = rh + 3 * (base + k);
-      for (int p = 0; p < nang; ++p) {
-        const T d = das[p * ld + c];
-        T cf[4];
-        if (mode >= 1) {
-          ld4(coef + (p * nang + k) * 4, cf);
-        } else {
-          const T* rp = rh + 3 * (base + p);
-          T P[4], dP[4];
-          legendre4(rp[0] * rk[0] + rp[1] * rk[1] + rp[2] * rk[2], P, dP);
-          const T w = (p == k) ? T(0) : inv_na * sa[base + p] * sa[base + k];
-          for (int l = 0; l < 4; ++l) cf[l] = w * P[l];
+  const int nrows = staged ? 2 : 0;
+  int i = blockIdx.x;
+  if (i < n)
+    angle_fetch(angle_buf(bufs, na, ed, nrows, 0), ca, ed, (long long)i * nmax, (long long)i * ca, sa, rh,
+                da, q);
+  for (int it = 0; i < n; ++it, i += gridDim.x) {
+    const AngleBuf<T> cur = angle_buf(bufs, na, ed, nrows, it & 1);
+    const int nang = angle_next(cur, angle_buf(bufs, na, ed, nrows, (it + 1) & 1), i, n, nmax, ca, ed, sa,
+                                rh, da, q);
+    const long long base = (long long)i * nmax, abase = (long long)i * ca;
+    const T* das = staged ? cur.r0 : da + abase * ed;
+    const T* qs = staged ? cur.r1 : q + abase * ed;
+    const int ld = staged ? ed + 1 : ed;
+    const T* gsa = cur.sa;
+    const T* grh = cur.rh;
+    angle_coef(coef, na, ra, nang, gsa, grh, inv_na);
+    __syncthreads();
+    const int ntile = (nang + 3) >> 2;
+    // dq_k[c] = sum_l Wphi[l][c] sum_p coef_pkl da_p[c]: a 4 x 4 block (slots
+    // k0.., columns cg + 16 j) per thread, summed over p
+    {
+      const int cg = threadIdx.x & 15;
+      for (int cb = 0; cb < ed; cb += 64)
+        for (int rt = threadIdx.x >> 4; rt < ntile; rt += kAngThreads / 16) {
+          const int k0 = 4 * rt;
+          int cc[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) cc[j] = min(cb + cg + 16 * j, ed - 1);
+          T acc[4][4][4];
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+              for (int l = 0; l < 4; ++l) acc[x][j][l] = T(0);
+          for (int p = 0; p < nang; ++p) {
+            T dv[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) dv[j] = das[p * ld + cc[j]];
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+              T cf[4];
+              ld4(coef + ((size_t)p * na + k0 + x) * 4, cf);
+#pragma unroll
+              for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int l = 0; l < 4; ++l) acc[x][j][l] += cf[l] * dv[j];
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int c = cb + cg + 16 * j;
+            if (c >= ed) continue;
+            T w[4];
+            ld4(W4 + 4 * c, w);
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+              if (k0 + x < nang)
+                dq[(abase + k0 + x) * ed + c] =
+                    w[0] * acc[x][j][0] + w[1] * acc[x][j][1] + w[2] * acc[x][j][2] + w[3] * acc[x][j][3];
+          }
         }
-        s0 += cf[0] * d; s1 += cf[1] * d; s2 += cf[2] * d; s3 += cf[3] * d;
-      }
-      T w[4];
-      ld4(W4 + 4 * c, w);
-      out = w[0] * s0 + w[1] * s1 + w[2] * s2 + w[3] * s3;
+      for (int idx = threadIdx.x; idx < (ca - nang) * ed; idx += blockDim.x)
+        dq[(abase + nang) * ed + idx] = T(0);
     }
-    dq[(abase + k) * ed + c] = out;
-  }
-  // dcoef_pkl = sum_c da_p[c] Wphi[l][c] q_k[c]  (one thread per (p, k))
-  for (int pk = threadIdx.x; pk < nang * nang; pk += blockDim.x) {
-    const int p = pk / nang, k = pk - p * nang;
-    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-    if (p != k)
+    __syncthreads();   // the coefficients are read for the last time above
+    // dcoef_pkl = sum_c da_p[c] Wphi[l][c] q_k[c]: a 2 x 4 block of (p, k) per
+    // thread (enough blocks to occupy the whole CTA), summed over the columns
+    // in order; written over the coefficients
+    T* dcoef = coef;
+    const int nkt = ntile, npt = (nang + 1) >> 1;
+    for (int tile = threadIdx.x; tile < npt * nkt; tile += blockDim.x) {
+      const int p0 = 2 * (tile / nkt), k0 = 4 * (tile % nkt);
+      int pr[2], kr[4];
+#pragma unroll
+      for (int x = 0; x < 2; ++x) pr[x] = min(p0 + x, nang - 1) * ld;
+#pragma unroll
+      for (int y = 0; y < 4; ++y) kr[y] = min(k0 + y, nang - 1) * ld;
+      T acc[2][4][4];
+#pragma unroll
+      for (int x = 0; x < 2; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y)
+#pragma unroll
+          for (int l = 0; l < 4; ++l) acc[x][y][l] = T(0);
+#pragma unroll 2
       for (int c = 0; c < ed; ++c) {
-        const T x = das[p * ld + c] * qs[k * ld + c];
-        T w[4];
+        T dv[2], qv[4], w[4];
+#pragma unroll
+        for (int x = 0; x < 2; ++x) dv[x] = das[pr[x] + c];
+#pragma unroll
+        for (int y = 0; y < 4; ++y) qv[y] = qs[kr[y] + c];
         ld4(W4 + 4 * c, w);
-        a0 += x * w[0];
-        a1 += x * w[1];
-        a2 += x * w[2];
-        a3 += x * w[3];
+#pragma unroll
+        for (int x = 0; x < 2; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) {
+            const T xy = dv[x] * qv[y];
+#pragma unroll
+            for (int l = 0; l < 4; ++l) acc[x][y][l] += xy * w[l];
+          }
       }
-    dcoef[pk * 4 + 0] = a0;
-    dcoef[pk * 4 + 1] = a1;
-    dcoef[pk * 4 + 2] = a2;
-    dcoef[pk * 4 + 3] = a3;
-  }
-  __syncthreads();
-  // switch and unit-vector terms: one warp per angle slot p, lanes over the
-  // partners k, then a fixed-order warp reduction
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int p = warp; p < nang; p += nw) {
-    const T* rp = rh + 3 * (base + p);
-    const T sp = sa[base + p];
-    T dsp = T(0), dr[3] = {T(0), T(0), T(0)};
-    for (int k = lane; k < nang; k += 32) {
-      if (k == p) continue;
-      const T* rk = rh + 3 * (base + k);
-      T P[4], dP[4];
-      legendre4(rp[0] * rk[0] + rp[1] * rk[1] + rp[2] * rk[2], P, dP);
-      // p as the first index (dcoef_pk) and as the second (dcoef_kp)
-      const T* d1 = dcoef + (p * nang + k) * 4;
-      const T* d2 = dcoef + (k * nang + p) * 4;
-      const T sk = sa[base + k];
-      T dc = T(0);
-      for (int l = 0; l < 4; ++l) {
-        dsp += (d1[l] + d2[l]) * inv_na * sk * P[l];
-        dc += (d1[l] + d2[l]) * inv_na * sp * sk * dP[l];
+#pragma unroll
+      for (int x = 0; x < 2; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          const int p = p0 + x, k = k0 + y;
+          if (p >= nang || k >= nang) continue;
+#pragma unroll
+          for (int l = 0; l < 4; ++l) dcoef[((size_t)p * na + k) * 4 + l] = p == k ? T(0) : acc[x][y][l];
+        }
+    }
+    __syncthreads();
+    // switch and unit-vector terms: one warp per angle slot p, lanes over the
+    // partners k, then a fixed-order warp reduction
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int p = warp; p < nang; p += nw) {
+      const T* rp = grh + 3 * p;
+      const T sp = gsa[p];
+      T dsp = T(0), dr[3] = {T(0), T(0), T(0)};
+      for (int k = lane; k < nang; k += 32) {
+        if (k == p) continue;
+        const T* rk = grh + 3 * k;
+        T P[4], dP[4];
+        legendre4(rp[0] * rk[0] + rp[1] * rk[1] + rp[2] * rk[2], P, dP);
+        // p as the first index (dcoef_pk) and as the second (dcoef_kp)
+        const T* d1 = dcoef + ((size_t)p * na + k) * 4;
+        const T* d2 = dcoef + ((size_t)k * na + p) * 4;
+        const T sk = gsa[k];
+        T dc = T(0);
+        for (int l = 0; l < 4; ++l) {
+          dsp += (d1[l] + d2[l]) * inv_na * sk * P[l];
+          dc += (d1[l] + d2[l]) * inv_na * sp * sk * dP[l];
+        }
+        for (int a = 0; a < 3; ++a) dr[a] += dc * rk[a];
       }
-      for (int a = 0; a < 3; ++a) dr[a] += dc * rk[a];
+      dsp = warp_sum(dsp);
+      for (int a = 0; a < 3; ++a) dr[a] = warp_sum(dr[a]);
+      if (lane == 0) {
+        dsa_e[base + p] += dsp;
+        for (int a = 0; a < 3; ++a) drh[3 * (base + p) + a] += dr[a];
+      }
     }
-    dsp = warp_sum(dsp);
-    for (int a = 0; a < 3; ++a) dr[a] = warp_sum(dr[a]);
-    if (lane == 0) {
-      dsa_e[base + p] += dsp;
-      for (int a = 0; a < 3; ++a) drh[3 * (base + p) + a] += dr[a];
-    }
+    __syncthreads();   // dcoef and this buffer are rewritten next
   }
 }
 
@@ -408,6 +577,19 @@ __global__ void k_dtanh(long long n, const T* __restrict__ g, const T* __restric
                         T* __restrict__ out) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = g[i] * (T(1) - y[i] * y[i]);
+}
+// the same, four elements per thread (n4 = n / 4; 16-byte aligned arrays)
+template <typename T>
+__global__ void k_dtanh4(long long n4, const T* __restrict__ g, const T* __restrict__ y,
+                         T* __restrict__ out) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n4) return;
+  T gv[4], yv[4];
+  ld4(g + 4 * i, gv);
+  ld4(y + 4 * i, yv);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) gv[q] *= T(1) - yv[q] * yv[q];
+  st4(out + 4 * i, gv);
 }
 
 // per atom: sum over its own slots (rows of dy)
@@ -421,7 +603,7 @@ __global__ void k_rowsum(int nmax, int ed, const T* __restrict__ x, T* __restric
   }
 }
 
-// (a) per slot: de += (1/nmax) sw dm_i * u_j;  X = (1/nmax) sw dm_i * e (for du_j);
+// (a) per kept slot: de += (1/nmax) sw dm_i * u_j;  X = (1/nmax) sw dm_i * e (for du_j);
 // dsw += (1/nmax) sum_c dm_i e u_j
 template <typename T>
 __global__ void k_msg_bwd(long long P, int nmax, int ed, int ldm, T inv_nmax,
@@ -433,20 +615,55 @@ __global__ void k_msg_bwd(long long P, int nmax, int ed, int ldm, T inv_nmax,
   int lane = threadIdx.x & 31;
   if (s >= P) return;
   int j = sel_j[s];
+  if (j < 0) return;   // an empty slot: no message, and its X row is never gathered
   long long i = s / nmax;
   T acc = T(0);
   for (int c = lane; c < ed; c += 32) {
-    if (j < 0) {
-      X[s * ed + c] = T(0);
-      continue;
-    }
     T g = dm[i * ldm + c], ev = e[s * ed + c], uv = u[(long long)j * ed + c];
     de[s * ed + c] += inv_nmax * sw[s] * g * uv;
     X[s * ed + c] = inv_nmax * sw[s] * g * ev;
     acc += g * ev * uv;
   }
   acc = warp_sum(acc);
-  if (lane == 0 && j >= 0) dsw_e[s] += inv_nmax * acc;
+  if (lane == 0) dsw_e[s] += inv_nmax * acc;
+}
+
+// The same with 16 threads per slot, four columns each (ed, ldm multiples of
+// 4, 16-byte aligned rows); the dsw sum closes with a fixed-order reduction
+// over the 16 lanes.
+template <typename T>
+__global__ void k_msg_bwd4(long long P, int nmax, int ed, int ldm, T inv_nmax,
+                           const int* __restrict__ sel_j, const T* __restrict__ sw,
+                           const T* __restrict__ e, const T* __restrict__ u,
+                           const T* __restrict__ dm, T* __restrict__ de, T* __restrict__ X,
+                           T* __restrict__ dsw_e) {
+  const long long s = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+  const int l16 = threadIdx.x & 15;
+  if (s >= P) return;   // the whole 16-lane group leaves together
+  const int j = sel_j[s];
+  if (j < 0) return;    // likewise: an empty slot
+  const unsigned mask = 0xFFFFu << (threadIdx.x & 16);
+  const long long i = s / nmax;
+  const T f = inv_nmax * sw[s];
+  T acc = T(0);
+  for (int c = 4 * l16; c < ed; c += 64) {
+    T g[4], ev[4], uv[4], d[4], x[4];
+    ld4(dm + i * ldm + c, g);
+    ld4(e + s * ed + c, ev);
+    ld4(u + (long long)j * ed + c, uv);
+    ld4(de + s * ed + c, d);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      d[q] += f * g[q] * uv[q];
+      x[q] = f * g[q] * ev[q];
+      acc += g[q] * ev[q] * uv[q];
+    }
+    st4(de + s * ed + c, d);
+    st4(X + s * ed + c, x);
+  }
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(mask, acc, o);
+  if (l16 == 0) dsw_e[s] += inv_nmax * acc;
 }
 
 // dn = dn1 + dnm[:, :nd]
@@ -611,8 +828,9 @@ class PlainGf : public Model {
   bool tc_ = false;
   int* flags_ = nullptr;
   const unsigned char* seed_ = nullptr;   // energy seed (device, optional)
-  // shared-memory variants of the angle kernels (see k_angle, k_angle_bwd)
-  int angle_staged_ = 0, angle_mode_ = 0;
+  // shared-memory variants of the angle kernels (see k_angle, k_angle_bwd):
+  // the slots' rows staged in shared memory when they fit
+  int angle_staged_ = 0, angle_bwd_staged_ = 0, angle_grid_ = 1, angle_bwd_grid_ = 1;
   size_t angle_smem_ = 0, angle_bwd_smem_ = 0;
 
   template <typename U>
@@ -729,14 +947,20 @@ bool PlainGf<T>::init(const GfDims& m, const double* w, int n_atoms, const int* 
     ok = dalloc(&hh_[l], N * Nd, err) && dalloc(&uu_[l], N * Ed, err) &&
          dalloc(&mm_[l], N * Ed, err) && dalloc(&vv_[l], P * Ed, err) && dalloc(&qq_[l], PA * Ed, err) &&
          dalloc(&tt_[l], PA * Ed, err);
-  // the angle kernels stage as much as fits in 227 KB of shared memory
-  const size_t kMaxSmem = 232448, na2 = (size_t)m.na * m.na * 4 * sizeof(T),
-               w4 = (size_t)m.ed * 4 * sizeof(T),
-               rowsz = (size_t)m.na * m.ed * sizeof(T), rowsz1 = (size_t)m.na * (m.ed + 1) * sizeof(T);
-  angle_staged_ = na2 + w4 + rowsz <= kMaxSmem ? 1 : 0;
-  angle_smem_ = na2 + w4 + (angle_staged_ ? rowsz : 0);
-  angle_mode_ = 2 * na2 + w4 + 2 * rowsz1 <= kMaxSmem ? 2 : (2 * na2 + w4 <= kMaxSmem ? 1 : 0);
-  angle_bwd_smem_ = na2 * (angle_mode_ >= 1 ? 2 : 1) + w4 + (angle_mode_ == 2 ? 2 * rowsz1 : 0);
+  // the angle kernels hold the coefficients and Wphi in shared memory, with
+  // two slot-data buffers (switches and unit vectors, plus the slots' rows
+  // when they fit in 227 KB)
+  const size_t kMaxSmem = 232448, ra = (size_t)((m.na + 3) & ~3),
+               fixed = (ra * m.na * 4 + (size_t)m.ed * 4) * sizeof(T),
+               geo = 2 * (size_t)m.na * 4 * sizeof(T), arows = 2 * (size_t)m.na * (m.ed + 1) * sizeof(T);
+  if (fixed + geo > kMaxSmem) {
+    *err = "graph model: the angle coefficients do not fit in shared memory";
+    return false;
+  }
+  angle_staged_ = fixed + geo + arows <= kMaxSmem ? 1 : 0;
+  angle_smem_ = fixed + geo + (angle_staged_ ? arows : 0);
+  angle_bwd_staged_ = fixed + geo + 2 * arows <= kMaxSmem ? 1 : 0;
+  angle_bwd_smem_ = fixed + geo + (angle_bwd_staged_ ? 2 * arows : 0);
   const int angle_smem = (int)angle_smem_, angle_bwd_smem = (int)angle_bwd_smem_;
   if (cudaFuncSetAttribute(k_angle<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, angle_smem) !=
           cudaSuccess ||
@@ -744,6 +968,19 @@ bool PlainGf<T>::init(const GfDims& m, const double* w, int n_atoms, const int* 
           cudaSuccess) {
     *err = "graph model: angle kernels cannot get their shared memory";
     return false;
+  }
+  {  // persistent grids: the blocks that fit on the device at once
+    int dev = 0, sms = 0, bf = 0, bb = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, k_angle<T>, kAngThreads, angle_smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bb, k_angle_bwd<T>, kAngThreads, angle_bwd_smem) !=
+            cudaSuccess) {
+      *err = "graph model: cannot size the angle kernels' grids";
+      return false;
+    }
+    angle_grid_ = std::max(1, std::min(n_atoms, sms * std::max(1, bf)));
+    angle_bwd_grid_ = std::max(1, std::min(n_atoms, sms * std::max(1, bb)));
   }
   ok = ok && dalloc(&Ai_, N * Ed, err) && dalloc(&Bj_, N * Ed, err) && dalloc(&Ce_, P * Ed, err) &&
        dalloc(&aa_, PA * Ed, err) && dalloc(&y1_, N * m.f1, err) && dalloc(&y2_, N * m.f2, err) &&
@@ -804,8 +1041,8 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
       g.a_rows = ang_rows_;
       mm(g, st);
     }
-    k_angle<T><<<n, 256, angle_smem, st>>>(NM, NA, CA, Ed, inv_na, sa_, rh_, qq_[l], Wphi_[l], aa_,
-                                           angle_staged_);
+    k_angle<T><<<angle_grid_, kAngThreads, angle_smem, st>>>(n, NM, NA, CA, Ed, inv_na, sa_, rh_, qq_[l],
+                                                             Wphi_[l], aa_, angle_staged_);
     if (angle_out_fused(l, st)) {
       --k;   // one launch instead of two
     } else {
@@ -871,8 +1108,8 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
       g.C = da_; g.c_rm = Ed; g.c_rn = 1; g.nb2 = 1; g.alpha = T(1);
       mm(g, st);
     }
-    k_angle_bwd<T><<<n, 256, angle_bwd_smem, st>>>(NM, NA, CA, Ed, inv_na, sa_, rh_, qq_[l], Wphi_[l],
-                                                   da_, dq_, dsa_e_, drh_, angle_mode_);
+    k_angle_bwd<T><<<angle_bwd_grid_, kAngThreads, angle_bwd_smem, st>>>(
+        n, NM, NA, CA, Ed, inv_na, sa_, rh_, qq_[l], Wphi_[l], da_, dq_, dsa_e_, drh_, angle_bwd_staged_);
     {  // de1 = de + dq Wp^T, in place on the angle rows' slots (dq is 0 elsewhere)
       Gemm<T> g{};
       g.M = (int)PA; g.N = Ed; g.K = Ed;
@@ -883,7 +1120,10 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
       mm(g, st);
     }
     // (b): de now holds dE/de1; it becomes dE/de_l (e1 = e_l + tanh(...))
-    k_dtanh<T><<<grid(PE), 256, 0, st>>>(PE, de_, vv_[l], dy_);
+    if (PE % 4 == 0)
+      k_dtanh4<T><<<grid(PE / 4), 256, 0, st>>>(PE / 4, de_, vv_[l], dy_);
+    else
+      k_dtanh<T><<<grid(PE), 256, 0, st>>>(PE, de_, vv_[l], dy_);
     {  // de += dy Wc^T
       Gemm<T> g{};
       g.M = (int)P; g.N = Ed; g.K = Ed;
@@ -916,8 +1156,12 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
       mm(g, st);
     }
     k_add_strided<T><<<grid((long long)n * Nd), 256, 0, st>>>(n, Nd, Nd + Ed, dn1_, dnm_, dn_);
-    k_msg_bwd<T><<<grid(P * 32), 256, 0, st>>>(P, NM, Ed, Nd + Ed, inv_nmax, nv.sel_j, sw_, ee_[l],
-                                               uu_[l], dnm_ + Nd, de_, X_, dsw_e_);
+    if (Ed % 4 == 0 && Nd % 4 == 0)
+      k_msg_bwd4<T><<<grid(P * 16), 256, 0, st>>>(P, NM, Ed, Nd + Ed, inv_nmax, nv.sel_j, sw_, ee_[l],
+                                                  uu_[l], dnm_ + Nd, de_, X_, dsw_e_);
+    else
+      k_msg_bwd<T><<<grid(P * 32), 256, 0, st>>>(P, NM, Ed, Nd + Ed, inv_nmax, nv.sel_j, sw_, ee_[l],
+                                                 uu_[l], dnm_ + Nd, de_, X_, dsw_e_);
     gather_in(nv, X_, du_, st);
     {  // dn += du Wm^T
       Gemm<T> g{};

@@ -137,14 +137,15 @@ def test_gf_mixed_md_tracks_fp32():
     assert np.all(np.isfinite(et)) and np.max(np.abs(et - et[0])) < 1e-3 * abs(et[0])
 
 
-@pytest.mark.parametrize("na,ed,mode", [(64, 16, "recompute per column"),
-                                        (56, 64, "coefficients only"),
-                                        (40, 64, "coefficients and rows staged")])
+@pytest.mark.parametrize("na,ed,mode", [(40, 64, "rows staged in both kernels"),
+                                        (64, 16, "rows staged in both kernels, 64 slots"),
+                                        (64, 64, "the adjoint reads its rows from global memory"),
+                                        (64, 128, "both kernels read their rows from global memory")])
 def test_gf_angle_channel_shared_memory_variants_fp64(na, ed, mode):
-    """The angle kernels keep as much in shared memory as fits: with FP64 and a
-    large angle capacity the adjoint falls back to unstaged rows (56 slots) or
-    to recomputing the coefficients per column (64 slots).  Every variant
-    must give the oracle's result."""
+    """The angle kernels hold the coefficients in shared memory with two
+    buffers of slot data, the slots' q and da rows included when they fit:
+    with FP64 and 64 angle slots the adjoint's rows stop fitting at edge width
+    64 and the forward's at 128.  Every variant must give the oracle's result."""
     m = replace(C.GRAPH_MODEL, node=32, edge=ed, n_layers=2, f1=32, f2=32, f3=16, nmax=96, na=na)
     s = serving_system(96, 7)
     w = weights(m, 5, 0.2)
