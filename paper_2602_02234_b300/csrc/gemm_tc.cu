@@ -19,6 +19,7 @@ namespace dp {
 namespace {
 
 constexpr int kRows = 128;
+constexpr int kStageLd = 20;   // epilogue stage row stride (floats): 16-byte rows, conflict-free phases
 constexpr long long kPollsTc = 1LL << 22;
 
 __device__ __forceinline__ uint64_t desc_k(uint32_t base, int Kx, int k0) {
@@ -36,6 +37,7 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
   uint8_t* Bs = sm;
   uint8_t* As = sm + (((size_t)brows * bcols * 2 + 1023) & ~(size_t)1023);
   uint64_t* bar = reinterpret_cast<uint64_t*>(As + (size_t)kRows * g.K * 2);
+  float* stage = reinterpret_cast<float*>(As + (size_t)kRows * g.K * 2 + 64);   // kRows x kStageLd
   __shared__ uint32_t tptr;
   if (t == 0) {
     tc::mbar_init(bar, 1);
@@ -98,6 +100,7 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
   tc::fence_after_sync();
   const uint32_t tb = tptr;
   const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+  const int lane = t & 31;
   const uint32_t idesc = tc::idesc_f16(kRows, g.N, 0, g.b_nk ? 0 : 1, g.fp16 ? 0u : 1u);
   const uint32_t a_base = tc::smem_u32(As), b_base = tc::smem_u32(Bs);
   const int tiles = (g.M + kRows - 1) / kRows;
@@ -161,88 +164,87 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
       if (t == 0) atomicOr(g.status, kFlagTimeout);
       break;
     }
-    // epilogue: thread t owns row m0 + t; 16 columns at a time, moved as four
-    // 16-byte accesses (rows are 16-byte aligned: ldc is a multiple of 4 floats)
-    const long long m = m0 + t;
-    const bool live = m < g.M;
-    const long long row = live ? (g.c_rows ? (long long)g.c_rows[m] : m) : 0;
-    const int jn = live && g.epi == 3 ? g.sel_j[row] : -1;
+    // epilogue, 16 columns at a time: each warp reads its 32 accumulator rows
+    // (thread = row) and turns them around through its shared-memory stage,
+    // so that four neighbouring threads own one row's 16 columns and every
+    // global access of the warp covers 8 rows x 64 contiguous bytes
+    float* st = stage + warp * 32 * kStageLd;
     for (int c = 0; c < g.N; c += 16) {
       float v[16];
       tc::tmem_ld16(tb + lane_off + (uint32_t)c, v);
-      if (!live) continue;
-      float4* Crow = reinterpret_cast<float4*>(g.C + row * g.ldc + c);
-      if (g.epi == 4) {   // angle output: t = tanh(acc + b), e_out = e_in + sa t
-        const long long xr = g.x_rows ? (long long)g.x_rows[m] : row;
-        float4* Orow = reinterpret_cast<float4*>(g.v_out + xr * g.ldc + c);
-        const float4* erow = reinterpret_cast<const float4*>(g.e_in + xr * g.ldc + c);
-        const float sw = g.sa[xr];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float4 e = erow[q];
-          const float t0 = tanhf(v[4 * q] + g.bias[c + 4 * q]);
-          const float t1 = tanhf(v[4 * q + 1] + g.bias[c + 4 * q + 1]);
-          const float t2 = tanhf(v[4 * q + 2] + g.bias[c + 4 * q + 2]);
-          const float t3 = tanhf(v[4 * q + 3] + g.bias[c + 4 * q + 3]);
-          Crow[q] = make_float4(t0, t1, t2, t3);
-          Orow[q] = make_float4(e.x + sw * t0, e.y + sw * t1, e.z + sw * t2, e.w + sw * t3);
-        }
-        continue;
-      }
-      if (g.epi == 3) {   // edge update: v = tanh(Ai + Bj + acc + b), e1 = e_in + v
-        float4* Vrow = reinterpret_cast<float4*>(g.v_out + row * g.ldc + c);
-        if (jn < 0) {
+      for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<float4*>(st + lane * kStageLd + 4 * q) =
+            make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      __syncwarp();
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            Vrow[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-            Crow[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-          }
+      for (int u = 0; u < 4; ++u) {
+        const int f = lane + 32 * u, rl = f >> 2, c4 = (f & 3) << 2;
+        const long long m = m0 + 32 * warp + rl;
+        if (m >= g.M) continue;
+        const float4 acc = *reinterpret_cast<const float4*>(st + rl * kStageLd + c4);
+        const float x[4] = {acc.x, acc.y, acc.z, acc.w};
+        const int col = c + c4;
+        const long long row = g.c_rows ? (long long)g.c_rows[m] : m;
+        float4* Cp = reinterpret_cast<float4*>(g.C + row * g.ldc + col);
+        const float4 bv = g.bias ? *reinterpret_cast<const float4*>(g.bias + col)
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float b[4] = {bv.x, bv.y, bv.z, bv.w};
+        if (g.epi == 4) {   // angle output: t = tanh(acc + b), e_out = e_in + sa t
+          const long long xr = g.x_rows ? (long long)g.x_rows[m] : row;
+          const float4 e = *reinterpret_cast<const float4*>(g.e_in + xr * g.ldc + col);
+          const float sw = g.sa[xr];
+          float y[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) y[q] = tanhf(x[q] + b[q]);
+          *Cp = make_float4(y[0], y[1], y[2], y[3]);
+          *reinterpret_cast<float4*>(g.v_out + xr * g.ldc + col) =
+              make_float4(e.x + sw * y[0], e.y + sw * y[1], e.z + sw * y[2], e.w + sw * y[3]);
           continue;
         }
-        const float4* arow = reinterpret_cast<const float4*>(g.Ai + (row / g.nmax) * g.ldc + c);
-        const float4* brow = reinterpret_cast<const float4*>(g.Bj + (long long)jn * g.ldc + c);
-        const float4* erow = reinterpret_cast<const float4*>(g.e_in + row * g.ldc + c);
+        if (g.epi == 3) {   // edge update: v = tanh(Ai + Bj + acc + b), e1 = e_in + v
+          float4* Vp = reinterpret_cast<float4*>(g.v_out + row * g.ldc + col);
+          const int jn = g.sel_j[row];
+          if (jn < 0) {
+            *Vp = make_float4(0.f, 0.f, 0.f, 0.f);
+            *Cp = make_float4(0.f, 0.f, 0.f, 0.f);
+            continue;
+          }
+          const float4 av = *reinterpret_cast<const float4*>(g.Ai + (row / g.nmax) * g.ldc + col);
+          const float4 bj = *reinterpret_cast<const float4*>(g.Bj + (long long)jn * g.ldc + col);
+          const float4 e = *reinterpret_cast<const float4*>(g.e_in + row * g.ldc + col);
+          const float y0 = tanhf(av.x + bj.x + x[0] + b[0]);
+          const float y1 = tanhf(av.y + bj.y + x[1] + b[1]);
+          const float y2 = tanhf(av.z + bj.z + x[2] + b[2]);
+          const float y3 = tanhf(av.w + bj.w + x[3] + b[3]);
+          *Vp = make_float4(y0, y1, y2, y3);
+          *Cp = make_float4(e.x + y0, e.y + y1, e.z + y2, e.w + y3);
+          continue;
+        }
+        float cin[4] = {0.f, 0.f, 0.f, 0.f}, ax[4] = {0.f, 0.f, 0.f, 0.f};
+        if (g.beta != 0.f) {
+          const float4 w = *Cp;
+          cin[0] = w.x; cin[1] = w.y; cin[2] = w.z; cin[3] = w.w;
+        }
+        if (g.epi == 2) {
+          const float4 w = *reinterpret_cast<const float4*>(g.aux + row * g.ldc + col);
+          ax[0] = w.x; ax[1] = w.y; ax[2] = w.z; ax[3] = w.w;
+        }
+        float y[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const float4 a = arow[q], b = brow[q], e = erow[q];
-          const float y0 = tanhf(a.x + b.x + v[4 * q] + g.bias[c + 4 * q]);
-          const float y1 = tanhf(a.y + b.y + v[4 * q + 1] + g.bias[c + 4 * q + 1]);
-          const float y2 = tanhf(a.z + b.z + v[4 * q + 2] + g.bias[c + 4 * q + 2]);
-          const float y3 = tanhf(a.w + b.w + v[4 * q + 3] + g.bias[c + 4 * q + 3]);
-          Vrow[q] = make_float4(y0, y1, y2, y3);
-          Crow[q] = make_float4(e.x + y0, e.y + y1, e.z + y2, e.w + y3);
+          float z = x[q] + b[q];
+          if (g.beta != 0.f) z += g.beta * cin[q];
+          if (g.epi == 1) {
+            z = tanhf(z);
+          } else if (g.epi == 2) {
+            z *= 1.f - ax[q] * ax[q];
+          }
+          y[q] = z;
         }
-        continue;
+        *Cp = make_float4(y[0], y[1], y[2], y[3]);
       }
-      float cin[16], ax[16];
-      if (g.beta != 0.f)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float4 u = Crow[q];
-          cin[4 * q] = u.x; cin[4 * q + 1] = u.y; cin[4 * q + 2] = u.z; cin[4 * q + 3] = u.w;
-        }
-      if (g.epi == 2) {
-        const float4* arow = reinterpret_cast<const float4*>(g.aux + row * g.ldc + c);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float4 u = arow[q];
-          ax[4 * q] = u.x; ax[4 * q + 1] = u.y; ax[4 * q + 2] = u.z; ax[4 * q + 3] = u.w;
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        float x = v[q];
-        if (g.bias) x += g.bias[c + q];
-        if (g.beta != 0.f) x += g.beta * cin[q];
-        if (g.epi == 1) {
-          x = tanhf(x);
-        } else if (g.epi == 2) {
-          x *= 1.f - ax[q] * ax[q];
-        }
-        v[q] = x;
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) Crow[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      __syncwarp();   // the stage is rewritten by the next column block
     }
     tc::fence_before_sync();
     __syncthreads();          // tensor memory and the A tile are reused by the next tile
@@ -263,7 +265,7 @@ bool gemm_tc_shape_ok(int N, int K) {
 
 static size_t smem_of(const GemmTc& g) {
   const size_t b = ((size_t)g.N * g.K * 2 + 1023) & ~(size_t)1023;
-  return b + (size_t)kRows * g.K * 2 + 64;
+  return b + (size_t)kRows * g.K * 2 + 64 + (size_t)kRows * kStageLd * 4;
 }
 
 bool gemm_tc_prepare(std::string* err) {
@@ -277,7 +279,7 @@ bool gemm_tc_prepare(std::string* err) {
   }
   // the largest request: B 256 x 256 plus a 128 x 256 A tile
   if (cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           256 * 256 * 2 + kRows * 256 * 2 + 64) != cudaSuccess) {
+                           256 * 256 * 2 + kRows * 256 * 2 + 64 + kRows * kStageLd * 4) != cudaSuccess) {
     *err = "tensor-core GEMM cannot get its shared memory";
     return false;
   }

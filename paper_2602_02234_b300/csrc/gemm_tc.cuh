@@ -20,8 +20,9 @@ namespace dp {
 //   A(m, k) = A[row(m) * lda + k], row(m) = a_rows ? a_rows[m] : m; A 16-byte
 //             aligned, lda a multiple of 4
 //   B(k, n) = B[k * ldb + n]  (b_nk = 0)  or  B[n * ldb + k]  (b_nk = 1)
-//   C(m, n) = C[row'(m) * ldc + n], row'(m) = c_rows ? c_rows[m] : m; C and aux
-//             16-byte aligned, ldc a multiple of 4 (the epilogue moves float4s)
+//   C(m, n) = C[row'(m) * ldc + n], row'(m) = c_rows ? c_rows[m] : m; C, aux,
+//             bias (and Ai, Bj, e_in, v_out) 16-byte aligned, ldc a multiple of
+//             4 (the epilogue moves float4s)
 // N and K multiples of 16, at most 256.  A timed-out wait sets kFlagTimeout
 // in *status.
 struct GemmTc {

@@ -744,7 +744,8 @@ class PlainGf : public Model {
           gemm_tc_shape_ok(g.N, g.K) && g.a_rm % 4 == 0 &&
           (reinterpret_cast<uintptr_t>(g.A) & 15) == 0 && g.c_rm % 4 == 0 &&
           (reinterpret_cast<uintptr_t>(g.C) & 15) == 0 &&
-          (reinterpret_cast<uintptr_t>(g.aux) & 15) == 0) {   // 16-byte rows of A, C, aux
+          (reinterpret_cast<uintptr_t>(g.aux) & 15) == 0 &&
+          (reinterpret_cast<uintptr_t>(g.bias) & 15) == 0) {   // 16-byte rows of A, C, aux; bias
         GemmTc t{};
         t.M = g.M; t.N = g.N; t.K = g.K;
         t.A = g.A; t.lda = g.a_rm; t.a_rows = g.a_rows;
