@@ -163,6 +163,21 @@ __device__ __forceinline__ void legendre4(double c, double* P, double* dP) {
 
 constexpr int kMaxNa = 64;
 
+// acc[l] += c[l] * x for l < 4; FP32 as two packed pair instructions
+__device__ __forceinline__ void fma4(double* acc, const double* c, double x) {
+#pragma unroll
+  for (int l = 0; l < 4; ++l) acc[l] += c[l] * x;
+}
+__device__ __forceinline__ void fma4(float* acc, const float* c, float x) {
+#pragma unroll
+  for (int h = 0; h < 4; h += 2)
+    asm("{\n\t.reg .b64 ra, rb, rc;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %4};\n\tmov.b64 rc, {%0, %1};\n\t"
+        "fma.rn.f32x2 rc, ra, rb, rc;\n\tmov.b64 {%0, %1}, rc;\n\t}"
+        : "+f"(acc[h]), "+f"(acc[h + 1])
+        : "f"(c[h]), "f"(c[h + 1]), "f"(x));
+}
+
 // Angle-channel blocks: kAngThreads threads per atom.  The products over the
 // angle slots are register-tiled: a thread owns a 4 x 4 block of outputs
 // (4 slot rows x the columns cg + 16 j, j < 4, of a 64-column block, cg =
@@ -325,8 +340,7 @@ __global__ void __launch_bounds__(kAngThreads) k_angle(int n, int nmax, int na, 
             ld4(coef + ((size_t)(p0 + x) * na + k) * 4, cf);
 #pragma unroll
             for (int j = 0; j < 4; ++j)
-#pragma unroll
-              for (int l = 0; l < 4; ++l) acc[x][j][l] += cf[l] * qv[j];
+              fma4(acc[x][j], cf, qv[j]);
           }
         }
 #pragma unroll
@@ -469,8 +483,7 @@ __global__ void __launch_bounds__(kAngThreads) k_angle_bwd(int n, int nmax, int 
               ld4(coef + ((size_t)p * na + k0 + x) * 4, cf);
 #pragma unroll
               for (int j = 0; j < 4; ++j)
-#pragma unroll
-                for (int l = 0; l < 4; ++l) acc[x][j][l] += cf[l] * dv[j];
+                fma4(acc[x][j], cf, dv[j]);
             }
           }
 #pragma unroll
@@ -522,8 +535,7 @@ __global__ void __launch_bounds__(kAngThreads) k_angle_bwd(int n, int nmax, int 
 #pragma unroll
           for (int y = 0; y < 4; ++y) {
             const T xy = dv[x] * qv[y];
-#pragma unroll
-            for (int l = 0; l < 4; ++l) acc[x][y][l] += xy * w[l];
+            fma4(acc[x][y], w, xy);
           }
       }
 #pragma unroll
