@@ -117,6 +117,51 @@ __global__ void k_msg(int nmax, int ed, T inv_nmax, const int* __restrict__ sel_
   }
 }
 
+// The same, one warp per atom: lane l owns columns 2l, 2l + 1 (+ 64 k), and
+// four slots' rows are read before any is summed; the sum runs over the
+// slots in order and stops at the first empty one, as above (the kept slots
+// are a prefix of the list).  ed even.
+template <typename T>
+__global__ void k_msg_warp(int n, int nmax, int ed, T inv_nmax, const int* __restrict__ sel_j,
+                           const T* __restrict__ sw, const T* __restrict__ edge,
+                           const T* __restrict__ u, T* __restrict__ m) {
+  const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  const size_t base = (size_t)i * nmax;
+  for (int c = 2 * lane; c < ed; c += 64) {
+    T a0 = T(0), a1 = T(0);
+    bool done = false;
+    for (int p = 0; p < nmax && !done; p += 4) {
+      int jj[4];
+      T sv[4], e0[4], e1[4], u0[4], u1[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        jj[q] = p + q < nmax ? sel_j[base + p + q] : -1;
+        if (jj[q] >= 0) {
+          const size_t e = base + p + q;
+          sv[q] = sw[e];
+          e0[q] = edge[e * ed + c];
+          e1[q] = edge[e * ed + c + 1];
+          u0[q] = u[(size_t)jj[q] * ed + c];
+          u1[q] = u[(size_t)jj[q] * ed + c + 1];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (jj[q] < 0) {
+          done = true;
+          break;
+        }
+        a0 += sv[q] * e0[q] * u0[q];
+        a1 += sv[q] * e1[q] * u1[q];
+      }
+    }
+    m[(size_t)i * ed + c] = a0 * inv_nmax;
+    m[(size_t)i * ed + c + 1] = a1 * inv_nmax;
+  }
+}
+
 template <typename T>
 __global__ void k_add(long long n, const T* __restrict__ a, const T* __restrict__ b,
                       T* __restrict__ out) {
@@ -416,6 +461,34 @@ __global__ void k_angle_out_bwd(long long PA, int ed, int nmax, int ca, const T*
   }
   acc = warp_sum(acc);
   if (lane == 0 && s > T(0)) dsa_e[e] += acc;
+}
+// The same with 16 threads per angle row, four columns each (ed a multiple
+// of 4); the dsa sum closes with a fixed-order reduction over the 16 lanes.
+template <typename T>
+__global__ void k_angle_out_bwd4(long long PA, int ed, int nmax, int ca, const T* __restrict__ sa,
+                                 const T* __restrict__ t, const T* __restrict__ de,
+                                 T* __restrict__ dz, T* __restrict__ dsa_e) {
+  const long long m = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+  const int l16 = threadIdx.x & 15;
+  if (m >= PA) return;   // the whole 16-lane group leaves together
+  const unsigned mask = 0xFFFFu << (threadIdx.x & 16);
+  const long long i = m / ca, e = i * nmax + (m - i * ca);
+  const T s = sa[e];
+  T acc = T(0);
+  for (int c = 4 * l16; c < ed; c += 64) {
+    T tv[4], g[4], z[4];
+    ld4(t + m * ed + c, tv);
+    ld4(de + e * ed + c, g);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      acc += g[q] * tv[q];
+      z[q] = g[q] * s * (T(1) - tv[q] * tv[q]);
+    }
+    st4(dz + m * ed + c, z);
+  }
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(mask, acc, o);
+  if (l16 == 0 && s > T(0)) dsa_e[e] += acc;
 }
 
 // (c) adjoint of a_p for each atom: dq, then the switch and unit-vector
@@ -1027,7 +1100,11 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
   for (int l = 0; l < L; ++l) {
     // (a)
     mm(gemm_rowmajor<T>(n, Ed, Nd, nn_[l], Nd, Wm_[l], Ed, uu_[l], Ed), st);
-    k_msg<T><<<n, 64, 0, st>>>(NM, Ed, inv_nmax, nv.sel_j, sw_, ee_[l], uu_[l], mm_[l]);
+    if (Ed % 2 == 0)
+      k_msg_warp<T><<<ceil_div((long long)n * 32, 256), 256, 0, st>>>(n, NM, Ed, inv_nmax, nv.sel_j, sw_,
+                                                                       ee_[l], uu_[l], mm_[l]);
+    else
+      k_msg<T><<<n, 64, 0, st>>>(NM, Ed, inv_nmax, nv.sel_j, sw_, ee_[l], uu_[l], mm_[l]);
     {
       Gemm<T> g = gemm_rowmajor<T>(n, Nd, Nd, nn_[l], Nd, Wn_[l], Nd, hh_[l], Nd);
       g.bias = bn_[l];
@@ -1112,7 +1189,10 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
   k += 5;
   for (int l = L - 1; l >= 0; --l) {
     // (c): de holds dE/de_{l+1}; it becomes dE/de1 in place (e_{l+1} = e1 + swa t)
-    k_angle_out_bwd<T><<<grid(PA * 32), 256, 0, st>>>(PA, Ed, NM, CA, sa_, tt_[l], de_, dz_, dsa_e_);
+    if (Ed % 4 == 0)
+      k_angle_out_bwd4<T><<<grid(PA * 16), 256, 0, st>>>(PA, Ed, NM, CA, sa_, tt_[l], de_, dz_, dsa_e_);
+    else
+      k_angle_out_bwd<T><<<grid(PA * 32), 256, 0, st>>>(PA, Ed, NM, CA, sa_, tt_[l], de_, dz_, dsa_e_);
     {  // da = dz Wq^T (angle rows)
       Gemm<T> g{};
       g.M = (int)PA; g.N = Ed; g.K = Ed;
