@@ -105,6 +105,8 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
   const uint32_t a_base = tc::smem_u32(As), b_base = tc::smem_u32(Bs);
   const int tiles = (g.M + kRows - 1) / kRows;
   const int k4 = g.K >> 2;
+  // row of element i of an A tile: i / k4, a shift when k4 is a power of two
+  const int k4s = (k4 & (k4 - 1)) == 0 ? __ffs(k4) - 1 : -1;
   uint32_t phase = 0;
   for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const long long m0 = (long long)tile * kRows;
@@ -120,7 +122,7 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
         const int i = base + u * kRows + t;
         v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (i < total) {
-          const int r = i / k4, c = (i - r * k4) << 2;
+          const int r = k4s >= 0 ? i >> k4s : i / k4, c = (i - r * k4) << 2;
           const long long m = m0 + r;
           if (m < g.M) {
             const long long row = g.a_rows ? (long long)g.a_rows[m] : m;
@@ -132,7 +134,7 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
       for (int u = 0; u < kLoads; ++u) {
         const int i = base + u * kRows + t;
         if (i >= total) break;
-        const int r = i / k4, c = (i - r * k4) << 2;
+        const int r = k4s >= 0 ? i >> k4s : i / k4, c = (i - r * k4) << 2;
         uint2 w;
         if (g.fp16) {
           w.x = tc::pack_f16(v[u].x, v[u].y);
@@ -210,7 +212,7 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
             *Cp = make_float4(0.f, 0.f, 0.f, 0.f);
             continue;
           }
-          const float4 av = *reinterpret_cast<const float4*>(g.Ai + (row / g.nmax) * g.ldc + col);
+          const float4 av = *reinterpret_cast<const float4*>(g.Ai + (long long)((int)row / g.nmax) * g.ldc + col);
           const float4 bj = *reinterpret_cast<const float4*>(g.Bj + (long long)jn * g.ldc + col);
           const float4 e = *reinterpret_cast<const float4*>(g.e_in + row * g.ldc + col);
           const float y0 = tanhf(av.x + bj.x + x[0] + b[0]);

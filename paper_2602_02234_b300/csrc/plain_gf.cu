@@ -472,7 +472,8 @@ __global__ void k_angle_out_bwd4(long long PA, int ed, int nmax, int ca, const T
   const int l16 = threadIdx.x & 15;
   if (m >= PA) return;   // the whole 16-lane group leaves together
   const unsigned mask = 0xFFFFu << (threadIdx.x & 16);
-  const long long i = m / ca, e = i * nmax + (m - i * ca);
+  const int i32 = (int)m / ca;   // angle rows < 2^31
+  const long long i = i32, e = i * nmax + (m - i * ca);
   const T s = sa[e];
   T acc = T(0);
   for (int c = 4 * l16; c < ed; c += 64) {
@@ -728,7 +729,7 @@ __global__ void k_msg_bwd4(long long P, int nmax, int ed, int ldm, T inv_nmax,
   const int j = sel_j[s];
   if (j < 0) return;    // likewise: an empty slot
   const unsigned mask = 0xFFFFu << (threadIdx.x & 16);
-  const long long i = s / nmax;
+  const long long i = (int)s / nmax;   // slots < 2^31
   const T f = inv_nmax * sw[s];
   T acc = T(0);
   for (int c = 4 * l16; c < ed; c += 64) {
@@ -976,6 +977,10 @@ bool PlainGf<T>::init(const GfDims& m, const double* w, int n_atoms, const int* 
   n_ = n_atoms;
   const int Nd = m.nd, Ed = m.ed, L = m.n_layers, S = m.n_species, NM = m.nmax;
   P_ = (long long)n_atoms * NM;
+  if (P_ > 2147483647LL) {   // slot indices are 32-bit in the products and kernels
+    *err = "graph model: atoms x nmax must stay below 2^31";
+    return false;
+  }
   size_t off = 0;
   auto take = [&](T** p, size_t cnt) {
     bool ok = upload(p, w + off, cnt, err);
