@@ -64,6 +64,40 @@ __global__ void k_mp_gather(int n, int nmax, int row_stride, int m1, int cap,
     ord[r] = i * row_stride + (kq - i * nmax);     // the slot's row of dG
   }
   __syncwarp();
+  if ((m1 & 1) == 0) {
+    // lane owns column pairs 2 lane + 64 q; four rows in flight, summed in order
+    for (int f = 2 * lane; f < m1; f += 64) {
+      T a0 = T(0), a1 = T(0);
+      int t = 0;
+      for (; t + 4 <= k; t += 4) {
+        T x0[4], x1[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const T* r = dG + (long long)ord[t + q] * m1 + f;
+          x0[q] = r[0];
+          x1[q] = r[1];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          a0 += x0[q];
+          a1 += x1[q];
+        }
+      }
+      for (; t < k; ++t) {
+        const T* r = dG + (long long)ord[t] * m1 + f;
+        a0 += r[0];
+        a1 += r[1];
+      }
+      if (U) {
+        const T u0 = U[(long long)j * m1 + f], u1 = U[(long long)j * m1 + f + 1];
+        a0 *= T(1) - u0 * u0;
+        a1 *= T(1) - u1 * u1;
+      }
+      dq[(long long)j * m1 + f] = a0;
+      dq[(long long)j * m1 + f + 1] = a1;
+    }
+    return;
+  }
   for (int f = lane; f < m1; f += 32) {
     T acc = T(0);
     for (int t = 0; t < k; ++t) acc += dG[(long long)ord[t] * m1 + f];

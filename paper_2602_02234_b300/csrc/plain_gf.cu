@@ -678,6 +678,46 @@ __global__ void k_dtanh4(long long n4, const T* __restrict__ g, const T* __restr
   st4(out + 4 * i, gv);
 }
 
+// (b) fused per atom: dy = de1 (1 - v^2) on every slot row and the atom's sum
+// of those rows (block per atom; ed a multiple of 4, at most 4 x blockDim).
+// Thread t owns the column quad t mod (ed / 4) and the rows congruent to
+// t / (ed / 4); the row groups' partial sums are added in group order.
+template <typename T>
+__global__ void k_dtanh_rowsum(int nmax, int ed, const T* __restrict__ g, const T* __restrict__ y,
+                               T* __restrict__ dy, T* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T* part = reinterpret_cast<T*>(sm_raw);   // [row group][ed]
+  const int cqn = ed >> 2, nrg = blockDim.x / cqn;
+  const int cq = threadIdx.x % cqn, rg = threadIdx.x / cqn;
+  const size_t base = (size_t)blockIdx.x * nmax * ed;
+  T acc[4] = {T(0), T(0), T(0), T(0)};
+  if (rg < nrg)
+    for (int p = rg; p < nmax; p += nrg) {
+      const size_t o = base + (size_t)p * ed + 4 * cq;
+      T gv[4], yv[4];
+      ld4(g + o, gv);
+      ld4(y + o, yv);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        gv[q] *= T(1) - yv[q] * yv[q];
+        acc[q] += gv[q];
+      }
+      st4(dy + o, gv);
+    }
+  if (rg < nrg) st4(part + (size_t)rg * ed + 4 * cq, acc);
+  __syncthreads();
+  if (rg == 0) {
+    T tot[4] = {T(0), T(0), T(0), T(0)};
+    for (int r = 0; r < nrg; ++r) {
+      T v[4];
+      ld4(part + (size_t)r * ed + 4 * cq, v);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) tot[q] += v[q];
+    }
+    st4(out + (size_t)blockIdx.x * ed + 4 * cq, tot);
+  }
+}
+
 // per atom: sum over its own slots (rows of dy)
 template <typename T>
 __global__ void k_rowsum(int nmax, int ed, const T* __restrict__ x, T* __restrict__ out) {
@@ -1218,7 +1258,10 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
       mm(g, st);
     }
     // (b): de now holds dE/de1; it becomes dE/de_l (e1 = e_l + tanh(...))
-    if (PE % 4 == 0)
+    const bool fused_rowsum = Ed % 4 == 0 && Ed <= 1024;
+    if (fused_rowsum)   // dy and its per-atom row sum sdy in one pass
+      k_dtanh_rowsum<T><<<n, 256, 256 / (Ed / 4) * Ed * sizeof(T), st>>>(NM, Ed, de_, vv_[l], dy_, sdy_);
+    else if (PE % 4 == 0)
       k_dtanh4<T><<<grid(PE / 4), 256, 0, st>>>(PE / 4, de_, vv_[l], dy_);
     else
       k_dtanh<T><<<grid(PE), 256, 0, st>>>(PE, de_, vv_[l], dy_);
@@ -1230,7 +1273,7 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
       g.C = de_; g.c_rm = Ed; g.c_rn = 1; g.nb2 = 1; g.alpha = T(1); g.beta = T(1);
       mm(g, st);
     }
-    k_rowsum<T><<<n, 64, 0, st>>>(NM, Ed, dy_, sdy_);
+    if (!fused_rowsum) k_rowsum<T><<<n, 64, 0, st>>>(NM, Ed, dy_, sdy_);
     gather_in(nv, dy_, gat_, st);
     k_copy<T><<<grid((long long)n * Nd), 256, 0, st>>>((long long)n * Nd, dn_, dn1_);
     {  // dn1 += sdy Wa^T + gat Wb^T
@@ -1269,7 +1312,7 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
       g.C = dn_; g.c_rm = Nd; g.c_rn = 1; g.nb2 = 1; g.alpha = T(1); g.beta = T(1);
       mm(g, st);
     }
-    k += 18;
+    k += fused_rowsum ? 17 : 18;
   }
   k_pair_grad<T><<<grid(P * 32), 256, 0, st>>>(P, NM, Ed, 0, nv.sel_j, d_, sw_, dsw_, dsa_, rh_, ee_[0],
                                                we_, de_, dsw_e_, dsa_e_, drh_, g_);
