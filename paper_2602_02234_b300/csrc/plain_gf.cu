@@ -836,12 +836,6 @@ __global__ void k_pair_grad(long long P, int nmax, int ed, int atom0, const int*
   (void)nmax;
 }
 
-template <typename T>
-__global__ void k_fill(long long n, T v, T* __restrict__ p) {
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) p[i] = v;
-}
-
 // ------------------------------------------------------------------ host side
 template <typename T>
 class PlainGf : public Model {
@@ -1227,11 +1221,12 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
     k += 3;
   }
   // ---- adjoint through the layers
-  k_fill<T><<<grid(PE), 256, 0, st>>>(PE, T(0), de_);
-  k_fill<T><<<grid(P), 256, 0, st>>>(P, T(0), dsw_e_);
-  k_fill<T><<<grid(P), 256, 0, st>>>(P, T(0), dsa_e_);
-  k_fill<T><<<grid(3 * P), 256, 0, st>>>(3 * P, T(0), drh_);
-  k += 5;
+  // adjoint accumulators start at zero (all-zero bytes are 0.0 in FP32 and FP64)
+  cudaMemsetAsync(de_, 0, sizeof(T) * PE, st);
+  cudaMemsetAsync(dsw_e_, 0, sizeof(T) * P, st);
+  cudaMemsetAsync(dsa_e_, 0, sizeof(T) * P, st);
+  cudaMemsetAsync(drh_, 0, sizeof(T) * 3 * P, st);
+  k += 1;   // k_fit_out
   for (int l = L - 1; l >= 0; --l) {
     // (c): de holds dE/de_{l+1}; it becomes dE/de1 in place (e_{l+1} = e1 + swa t)
     if (Ed % 4 == 0)
