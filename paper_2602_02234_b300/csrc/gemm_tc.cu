@@ -19,7 +19,8 @@ namespace dp {
 namespace {
 
 constexpr int kRows = 128;
-constexpr int kStageLd = 20;   // epilogue stage row stride (floats): 16-byte rows, conflict-free phases
+constexpr int kStageLd = 20;
+constexpr size_t kMaxSmemBlock = 232448;   // opt-in shared memory per block (static + dynamic)   // epilogue stage row stride (floats): 16-byte rows, conflict-free phases
 constexpr long long kPollsTc = 1LL << 22;
 
 __device__ __forceinline__ uint64_t desc_k(uint32_t base, int Kx, int k0) {
@@ -36,8 +37,10 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
   const int brows = g.b_nk ? g.N : g.K, bcols = g.b_nk ? g.K : g.N;
   uint8_t* Bs = sm;
   uint8_t* As = sm + (((size_t)brows * bcols * 2 + 1023) & ~(size_t)1023);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(As + (size_t)kRows * g.K * 2);
-  float* stage = reinterpret_cast<float*>(As + (size_t)kRows * g.K * 2 + 64);   // kRows x kStageLd
+  uint8_t* Al = As + (size_t)kRows * g.K * 2;   // remainder tile (split only)
+  uint8_t* tail = g.split ? Al + (size_t)kRows * g.K * 2 : Al;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(tail);
+  float* stage = reinterpret_cast<float*>(tail + 64);   // kRows x kStageLd
   __shared__ uint32_t tptr;
   if (t == 0) {
     tc::mbar_init(bar, 1);
@@ -102,7 +105,7 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
   const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
   const int lane = t & 31;
   const uint32_t idesc = tc::idesc_f16(kRows, g.N, 0, g.b_nk ? 0 : 1, g.fp16 ? 0u : 1u);
-  const uint32_t a_base = tc::smem_u32(As), b_base = tc::smem_u32(Bs);
+  const uint32_t a_base = tc::smem_u32(As), al_base = tc::smem_u32(Al), b_base = tc::smem_u32(Bs);
   const int tiles = (g.M + kRows - 1) / kRows;
   const int k4 = g.K >> 2;
   // row of element i of an A tile: i / k4, a shift when k4 is a power of two
@@ -143,7 +146,23 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
           w.x = tc::pack_bf16(v[u].x, v[u].y);
           w.y = tc::pack_bf16(v[u].z, v[u].w);
         }
-        *reinterpret_cast<uint2*>(As + tc::kmajor_off(r, c, g.K)) = w;
+        const int off = tc::kmajor_off(r, c, g.K);
+        *reinterpret_cast<uint2*>(As + off) = w;
+        if (g.split) {   // remainder v - high, itself rounded to 16 bits
+          const float2 h0 = g.fp16 ? __half22float2(*reinterpret_cast<const __half2*>(&w.x))
+                                   : __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w.x));
+          const float2 h1 = g.fp16 ? __half22float2(*reinterpret_cast<const __half2*>(&w.y))
+                                   : __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w.y));
+          uint2 lo;
+          if (g.fp16) {
+            lo.x = tc::pack_f16(v[u].x - h0.x, v[u].y - h0.y);
+            lo.y = tc::pack_f16(v[u].z - h1.x, v[u].w - h1.y);
+          } else {
+            lo.x = tc::pack_bf16(v[u].x - h0.x, v[u].y - h0.y);
+            lo.y = tc::pack_bf16(v[u].z - h1.x, v[u].w - h1.y);
+          }
+          *reinterpret_cast<uint2*>(Al + off) = lo;
+        }
       }
     }
     tc::fence_async_smem();
@@ -151,10 +170,11 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
     __syncthreads();
     tc::fence_after_sync();
     if (t == 0) {
-      for (int ks = 0; ks < g.K; ks += 16)
-        tc::mma_bf16(tb, desc_k(a_base, g.K, ks),
-                     g.b_nk ? desc_k(b_base, g.K, ks) : desc_mn(b_base, g.N, ks), idesc,
-                     ks > 0 ? 1u : 0u);
+      for (int ks = 0; ks < g.K; ks += 16) {
+        const uint64_t db = g.b_nk ? desc_k(b_base, g.K, ks) : desc_mn(b_base, g.N, ks);
+        tc::mma_bf16(tb, desc_k(a_base, g.K, ks), db, idesc, ks > 0 ? 1u : 0u);
+        if (g.split) tc::mma_bf16(tb, desc_k(al_base, g.K, ks), db, idesc, 1u);
+      }
       tc::mma_commit(bar);
     }
     bool ok = true;
@@ -258,6 +278,7 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
 }
 
 int g_sms = 0;
+size_t g_max_dyn = 0;   // dynamic shared memory the kernel may request
 
 }  // namespace
 
@@ -267,7 +288,7 @@ bool gemm_tc_shape_ok(int N, int K) {
 
 static size_t smem_of(const GemmTc& g) {
   const size_t b = ((size_t)g.N * g.K * 2 + 1023) & ~(size_t)1023;
-  return b + (size_t)kRows * g.K * 2 + 64 + (size_t)kRows * kStageLd * 4;
+  return b + (size_t)kRows * g.K * 2 * (g.split ? 2 : 1) + 64 + (size_t)kRows * kStageLd * 4;
 }
 
 bool gemm_tc_prepare(std::string* err) {
@@ -279,17 +300,26 @@ bool gemm_tc_prepare(std::string* err) {
       return false;
     }
   }
-  // the largest request: B 256 x 256 plus a 128 x 256 A tile
-  if (cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           256 * 256 * 2 + kRows * 256 * 2 + 64 + kRows * kStageLd * 4) != cudaSuccess) {
+  // up to the per-block limit less the static part (a split A that would not
+  // fit falls back to one product)
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, k_gemm_tc) != cudaSuccess) {
+    *err = "tensor-core GEMM: cannot query the kernel";
+    return false;
+  }
+  g_max_dyn = kMaxSmemBlock - fa.sharedSizeBytes;
+  if (cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g_max_dyn) !=
+      cudaSuccess) {
     *err = "tensor-core GEMM cannot get its shared memory";
     return false;
   }
   return true;
 }
 
-void gemm_tc(const GemmTc& g, cudaStream_t st) {
-  if (g.M <= 0) return;
+void gemm_tc(const GemmTc& g0, cudaStream_t st) {
+  if (g0.M <= 0) return;
+  GemmTc g = g0;
+  if (g.split && smem_of(g) > g_max_dyn) g.split = 0;
   int cols = 32;
   while (cols < g.N) cols <<= 1;
   // at most 512 / cols CTAs may share an SM's tensor memory: pad the shared

@@ -41,6 +41,8 @@ struct GemmTc {
   int epi;
   const float* aux;
   int fp16;        // operands rounded to FP16 (1) or BF16 (0)
+  int split;       // 1: A as a 16-bit high part plus a 16-bit remainder, two
+                   // products per K step (A's rounding error ~2^-22 instead of 2^-11)
   int* status;
   // epi 3 and 4
   const int* sel_j;

@@ -878,6 +878,7 @@ class PlainGf : public Model {
 #else
         t.fp16 = 1;
 #endif
+        t.split = 1;   // activations as high part + remainder
         gemm_tc(t, st);
         return;
       }
@@ -912,6 +913,7 @@ class PlainGf : public Model {
 #else
       t.fp16 = 1;
 #endif
+      t.split = 1;
       gemm_tc(t, st);
       return true;
     } else {
@@ -939,6 +941,7 @@ class PlainGf : public Model {
 #else
       t.fp16 = 1;
 #endif
+      t.split = 1;
       gemm_tc(t, st);
       return true;
     } else {
