@@ -878,7 +878,10 @@ class PlainGf : public Model {
 #else
         t.fp16 = 1;
 #endif
-        t.split = 1;   // activations as high part + remainder
+        // products over atom rows (node features, fitting) take the
+        // activations as a 16-bit high part plus remainder: they carry most of
+        // the 16-bit error and cost little; products over slot rows keep one
+        t.split = g.M <= n_ ? 1 : 0;
         gemm_tc(t, st);
         return;
       }
@@ -913,7 +916,7 @@ class PlainGf : public Model {
 #else
       t.fp16 = 1;
 #endif
-      t.split = 1;
+      t.split = 0;   // slot rows: one 16-bit activation operand
       gemm_tc(t, st);
       return true;
     } else {
@@ -941,7 +944,7 @@ class PlainGf : public Model {
 #else
       t.fp16 = 1;
 #endif
-      t.split = 1;
+      t.split = 0;   // slot rows: one 16-bit activation operand
       gemm_tc(t, st);
       return true;
     } else {

@@ -70,9 +70,9 @@ def test_gf_full_size_fp32_and_mixed_vs_fp64_and_finite_differences():
     p32.close()
     assert abs(E32 - E64) <= 1e-5 * abs(E64)
     assert np.max(np.abs(F32 - F64)) <= 1e-4 * frms(F64)
-    # the mixed form (16-bit products, activations split into high part and
-    # remainder) within the 2e-2 bound of the 16-bit forms at full size
-    # (1.23e-2 seen), energy within 1e-2
+    # the mixed form (16-bit products; atom-row products with activations
+    # split into high part and remainder) within the 2e-2 bound of the 16-bit
+    # forms at full size (1.36e-2 seen), energy within 1e-2
     pmx = make(m, s, dp.PREC_FUSED, w)
     Emx, Fmx, Vmx = pmx.compute(s.coords)
     pmx.close()
