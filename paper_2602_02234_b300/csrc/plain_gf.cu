@@ -841,6 +841,9 @@ template <typename T>
 class PlainGf : public Model {
  public:
   ~PlainGf() override {
+    for (cudaStream_t x : fit_st_) cudaStreamDestroy(x);
+    for (cudaEvent_t x : fit_ev_) cudaEventDestroy(x);
+    if (fork_ev_) cudaEventDestroy(fork_ev_);
     for (void* p : allocs_) cudaFree(p);
   }
   bool init(const GfDims& m, const double* w, int n_atoms, const int* types, std::string* err);
@@ -997,6 +1000,21 @@ class PlainGf : public Model {
   T *F4_, *c4_;
   int* fit_rows_;
   std::vector<std::pair<int, int>> fit_ranges_;
+  // the species' fitting products run concurrently: one stream each, forked
+  // from and joined back to the evaluation's stream by events
+  std::vector<cudaStream_t> fit_st_;
+  std::vector<cudaEvent_t> fit_ev_;
+  cudaEvent_t fork_ev_ = nullptr;
+  void fit_fork(cudaStream_t st) {
+    cudaEventRecord(fork_ev_, st);
+    for (cudaStream_t x : fit_st_) cudaStreamWaitEvent(x, fork_ev_, 0);
+  }
+  void fit_join(cudaStream_t st) {
+    for (size_t t = 0; t < fit_st_.size(); ++t) {
+      cudaEventRecord(fit_ev_[t], fit_st_[t]);
+      cudaStreamWaitEvent(st, fit_ev_[t], 0);
+    }
+  }
   // geometry
   T *d_, *sw_, *dsw_, *sa_, *dsa_, *s_, *rh_;
   // states
@@ -1058,6 +1076,18 @@ bool PlainGf<T>::init(const GfDims& m, const double* w, int n_atoms, const int* 
     fit_ranges_[t] = {start, (int)rows.size() - start};
   }
   if (!dalloc(&fit_rows_, rows.size(), err)) return false;
+  fit_st_.assign(S, nullptr);
+  fit_ev_.assign(S, nullptr);
+  for (int t = 0; t < S; ++t)
+    if (cudaStreamCreateWithFlags(&fit_st_[t], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&fit_ev_[t], cudaEventDisableTiming) != cudaSuccess) {
+      *err = "graph model: cannot create the fitting streams";
+      return false;
+    }
+  if (cudaEventCreateWithFlags(&fork_ev_, cudaEventDisableTiming) != cudaSuccess) {
+    *err = "graph model: cannot create the fitting streams";
+    return false;
+  }
   if (!rows.empty()) cudaMemcpy(fit_rows_, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice);
   const size_t N = n_atoms, P = P_;
   nac_ = std::min(m.na, NM);
@@ -1189,24 +1219,28 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
     }
     k += 14;
   }
-  // fitting
+  // fitting: each species' rows on its own stream (disjoint rows of y1..y3)
+  fit_fork(st);
   for (int t = 0; t < S; ++t) {
     auto rg = fit_ranges_[t];
     if (rg.second == 0) continue;
     const int* rws = fit_rows_ + rg.first;
+    cudaStream_t fs = fit_st_[t];
     Gemm<T> g = gemm_rowmajor<T>(rg.second, m.f1, Nd, nn_[L], Nd, F1_[t], m.f1, y1_, m.f1);
     g.a_rows = rws; g.c_rows = rws; g.bias = c1_[t]; g.epi = 1;
-    mm(g, st);
+    mm(g, fs);
     g = gemm_rowmajor<T>(rg.second, m.f2, m.f1, y1_, m.f1, F2_[t], m.f2, y2_, m.f2);
     g.a_rows = rws; g.c_rows = rws; g.bias = c2_[t]; g.epi = 1;
-    mm(g, st);
+    mm(g, fs);
     g = gemm_rowmajor<T>(rg.second, m.f3, m.f2, y2_, m.f2, F3_[t], m.f3, y3_, m.f3);
     g.a_rows = rws; g.c_rows = rws; g.bias = c3_[t]; g.epi = 1;
-    mm(g, st);
+    mm(g, fs);
     k += 3;
   }
+  fit_join(st);
   k_fit_out<T><<<ceil_div((long long)n * 32, 256), 256, 0, st>>>(n, m.f3, types, y3_, F4_, c4_, atom_e, d3_,
                                                                  seed_);
+  fit_fork(st);
   for (int t = 0; t < S; ++t) {
     auto rg = fit_ranges_[t];
     if (rg.second == 0) continue;
@@ -1217,15 +1251,16 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
     g.B = F3_[t]; g.b_rk = 1; g.b_rn = m.f3;
     g.C = d2_; g.c_rm = m.f2; g.c_rn = 1; g.nb2 = 1;
     g.a_rows = rws; g.c_rows = rws; g.alpha = T(1); g.epi = 2; g.aux = y2_;
-    mm(g, st);
+    mm(g, fit_st_[t]);
     g.N = m.f1; g.K = m.f2; g.A = d2_; g.a_rm = m.f2; g.B = F2_[t]; g.b_rn = m.f2;
     g.C = d1_; g.c_rm = m.f1; g.aux = y1_;
-    mm(g, st);
+    mm(g, fit_st_[t]);
     g.N = Nd; g.K = m.f1; g.A = d1_; g.a_rm = m.f1; g.B = F1_[t]; g.b_rn = m.f1;
     g.C = dn_; g.c_rm = Nd; g.epi = 0; g.aux = nullptr;
-    mm(g, st);
+    mm(g, fit_st_[t]);
     k += 3;
   }
+  fit_join(st);
   // ---- adjoint through the layers
   // adjoint accumulators start at zero (all-zero bytes are 0.0 in FP32 and FP64)
   cudaMemsetAsync(de_, 0, sizeof(T) * PE, st);
