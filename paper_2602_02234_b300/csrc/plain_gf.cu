@@ -92,6 +92,21 @@ __global__ void k_init(int n, int nmax, int nd, int ed, const int* __restrict__ 
                        const T* __restrict__ be0, T* __restrict__ node, T* __restrict__ edge) {
   int i = blockIdx.x;
   for (int c = threadIdx.x; c < nd; c += blockDim.x) node[(size_t)i * nd + c] = Wt[types[i] * nd + c];
+  if ((ed & 3) == 0) {   // four columns per thread, one 16-byte store
+    const int eq = ed >> 2;
+    for (int idx = threadIdx.x; idx < nmax * eq; idx += blockDim.x) {
+      const int p = idx / eq, c = (idx - p * eq) << 2;
+      const size_t e = (size_t)i * nmax + p;
+      T v[4] = {T(0), T(0), T(0), T(0)};
+      if (sel_j[e] >= 0) {
+        const T se = s[e];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = dtanh(se * we[c + q] + be0[c + q]);
+      }
+      st4(edge + e * ed + c, v);
+    }
+    return;
+  }
   for (int idx = threadIdx.x; idx < nmax * ed; idx += blockDim.x) {
     int p = idx / ed, c = idx % ed;
     size_t e = (size_t)i * nmax + p;
@@ -835,6 +850,42 @@ __global__ void k_pair_grad(long long P, int nmax, int ed, int atom0, const int*
   (void)atom0;
   (void)nmax;
 }
+// The same with 16 threads per slot, four columns each (ed a multiple of 4);
+// the ds sum closes with a fixed-order reduction over the 16 lanes.
+template <typename T>
+__global__ void k_pair_grad4(long long P, int ed, const int* __restrict__ sel_j, const T* __restrict__ d,
+                             const T* __restrict__ sw, const T* __restrict__ dsw,
+                             const T* __restrict__ dsa, const T* __restrict__ rh,
+                             const T* __restrict__ e0, const T* __restrict__ we,
+                             const T* __restrict__ de, const T* __restrict__ dsw_e,
+                             const T* __restrict__ dsa_e, const T* __restrict__ drh, T* __restrict__ g) {
+  const long long s = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+  const int l16 = threadIdx.x & 15;
+  if (s >= P) return;   // the whole 16-lane group leaves together
+  if (sel_j[s] < 0) {   // likewise
+    if (l16 < 3) g[3 * s + l16] = T(0);
+    return;
+  }
+  const unsigned mask = 0xFFFFu << (threadIdx.x & 16);
+  T ds = T(0);
+  for (int c = 4 * l16; c < ed; c += 64) {
+    T ev[4], dv[4], wv[4];
+    ld4(e0 + s * ed + c, ev);
+    ld4(de + s * ed + c, dv);
+    ld4(we + c, wv);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ds += dv[q] * (T(1) - ev[q] * ev[q]) * wv[q];
+  }
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) ds += __shfl_xor_sync(mask, ds, o);
+  if (l16 != 0) return;
+  const T dd = d[s];
+  const T radial = ds * (dsw[s] / dd - sw[s] / (dd * dd)) + dsw_e[s] * dsw[s] + dsa_e[s] * dsa[s];
+  const T* r = rh + 3 * s;
+  const T* dr = drh + 3 * s;
+  const T proj = dr[0] * r[0] + dr[1] * r[1] + dr[2] * r[2];
+  for (int a = 0; a < 3; ++a) g[3 * s + a] = radial * r[a] + (dr[a] - proj * r[a]) / dd;
+}
 
 // ------------------------------------------------------------------ host side
 template <typename T>
@@ -1350,8 +1401,12 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
     }
     k += fused_rowsum ? 17 : 18;
   }
-  k_pair_grad<T><<<grid(P * 32), 256, 0, st>>>(P, NM, Ed, 0, nv.sel_j, d_, sw_, dsw_, dsa_, rh_, ee_[0],
-                                               we_, de_, dsw_e_, dsa_e_, drh_, g_);
+  if (Ed % 4 == 0)
+    k_pair_grad4<T><<<grid(P * 16), 256, 0, st>>>(P, Ed, nv.sel_j, d_, sw_, dsw_, dsa_, rh_, ee_[0], we_, de_,
+                                                  dsw_e_, dsa_e_, drh_, g_);
+  else
+    k_pair_grad<T><<<grid(P * 32), 256, 0, st>>>(P, NM, Ed, 0, nv.sel_j, d_, sw_, dsw_, dsa_, rh_, ee_[0],
+                                                 we_, de_, dsw_e_, dsa_e_, drh_, g_);
   return k + 1;
 }
 
