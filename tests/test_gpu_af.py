@@ -94,8 +94,8 @@ def test_edge_cases_fp64(case):
     assert np.max(np.abs(F - Fo)) <= 1e-9 * scale + 1e-14
 
 
-def _sampled_parity(prec, sample_seed=3, n_sample=8):
-    m, s = C.ATTN_MODEL, C.protein24k()
+def _sampled_parity(prec, sample_seed=3, n_sample=8, system=C.protein24k):
+    m, s = C.ATTN_MODEL, system()
     pot, w = make(m, s, prec)
     E, F, V = pot.compute(s.coords)
     rng = np.random.default_rng(sample_seed)
@@ -112,6 +112,17 @@ def _sampled_parity(prec, sample_seed=3, n_sample=8):
 @pytest.mark.parametrize("prec", [dp.PREC_PLAIN_F32, dp.PREC_FUSED])
 def test_protein24k_sampled_parity(prec):
     F, Fo, ae, ae_o, E = _sampled_parity(prec)
+    assert np.isfinite(E)
+    assert np.max(np.abs(F - Fo)) <= TOL_F[prec] * frms(Fo)
+    assert np.max(np.abs(ae - ae_o)) <= 10 * TOL_E[prec] * np.max(np.abs(ae_o))
+
+
+@pytest.mark.parametrize("prec", [dp.PREC_PLAIN_F32, dp.PREC_FUSED])
+def test_protein100k_sampled_parity(prec):
+    """The 100,000-atom configuration (6,001-atom blob + 31,333 waters) in the
+    launch configuration its benchmark times: sampled forces and atomic
+    energies against the oracle."""
+    F, Fo, ae, ae_o, E = _sampled_parity(prec, sample_seed=7, system=C.protein100k)
     assert np.isfinite(E)
     assert np.max(np.abs(F - Fo)) <= TOL_F[prec] * frms(Fo)
     assert np.max(np.abs(ae - ae_o)) <= 10 * TOL_E[prec] * np.max(np.abs(ae_o))
