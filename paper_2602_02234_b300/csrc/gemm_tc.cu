@@ -23,15 +23,6 @@ constexpr int kStageLd = 20;
 constexpr size_t kMaxSmemBlock = 232448;   // opt-in shared memory per block (static + dynamic)   // epilogue stage row stride (floats): 16-byte rows, conflict-free phases
 constexpr long long kPollsTc = 1LL << 22;
 
-// tanh from one exponential: with t = e^(-2|x|), tanh|x| = (1 - t) / (1 + t).
-// Absolute error a few 1e-8 (relative error grows only where |x| is tiny and
-// the value itself is), against a multi-instruction tanhf; the epilogues add
-// the result to FP32 features, where the absolute error is what counts.
-__device__ __forceinline__ float tanh_exp(float x) {
-  const float t = __expf(-2.f * fabsf(x));
-  return copysignf(__fdividef(1.f - t, 1.f + t), x);
-}
-
 __device__ __forceinline__ uint64_t desc_k(uint32_t base, int Kx, int k0) {
   return tc::make_desc(base + (uint32_t)((k0 >> 3) * 128), 128u, (uint32_t)((Kx >> 3) * 128));
 }
@@ -227,7 +218,7 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
           const float sw = g.sa[xr];
           float y[4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) y[q] = tanh_exp(x[q] + b[q]);
+          for (int q = 0; q < 4; ++q) y[q] = tanhf(x[q] + b[q]);
           *Cp = make_float4(y[0], y[1], y[2], y[3]);
           *reinterpret_cast<float4*>(g.v_out + xr * g.ldc + col) =
               make_float4(e.x + sw * y[0], e.y + sw * y[1], e.z + sw * y[2], e.w + sw * y[3]);
@@ -244,10 +235,10 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
           const float4 av = *reinterpret_cast<const float4*>(g.Ai + (long long)((int)row / g.nmax) * g.ldc + col);
           const float4 bj = *reinterpret_cast<const float4*>(g.Bj + (long long)jn * g.ldc + col);
           const float4 e = *reinterpret_cast<const float4*>(g.e_in + row * g.ldc + col);
-          const float y0 = tanh_exp(av.x + bj.x + x[0] + b[0]);
-          const float y1 = tanh_exp(av.y + bj.y + x[1] + b[1]);
-          const float y2 = tanh_exp(av.z + bj.z + x[2] + b[2]);
-          const float y3 = tanh_exp(av.w + bj.w + x[3] + b[3]);
+          const float y0 = tanhf(av.x + bj.x + x[0] + b[0]);
+          const float y1 = tanhf(av.y + bj.y + x[1] + b[1]);
+          const float y2 = tanhf(av.z + bj.z + x[2] + b[2]);
+          const float y3 = tanhf(av.w + bj.w + x[3] + b[3]);
           *Vp = make_float4(y0, y1, y2, y3);
           *Cp = make_float4(e.x + y0, e.y + y1, e.z + y2, e.w + y3);
           continue;
@@ -267,7 +258,7 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
           float z = x[q] + b[q];
           if (g.beta != 0.f) z += g.beta * cin[q];
           if (g.epi == 1) {
-            z = tanh_exp(z);
+            z = tanhf(z);
           } else if (g.epi == 2) {
             z *= 1.f - ax[q] * ax[q];
           }
