@@ -163,3 +163,22 @@ def test_gf_angle_channel_shared_memory_variants_fp64(na, ed, mode):
     Eo, _, Fo, Vo = oracle.gf_compute(m, w, s.types, s.coords, s.box)
     assert E == pytest.approx(Eo, rel=1e-11)
     assert np.max(np.abs(F - Fo)) <= 1e-10 * frms(Fo)
+
+
+@pytest.mark.parametrize("edge", [5, 6])
+@pytest.mark.parametrize("prec,tol", [(dp.PREC_PLAIN_F64, 1e-10), (dp.PREC_PLAIN_F32, 1e-4)])
+def test_gf_edge_widths_without_vector_paths(edge, prec, tol):
+    """Edge widths that are not multiples of 4 take the scalar kernels (message,
+    message adjoint, angle-output adjoint, tanh adjoint and row sum, pair
+    gradient, edge initialisation; width 5 also the block-per-atom message):
+    same results as the oracle."""
+    m = replace(C.GRAPH_MODEL, node=12, edge=edge, n_layers=2, f1=12, f2=10, f3=8, nmax=40, na=10)
+    s = water_box(8, 9.0, 3, min_oo=2.3)
+    s.types = np.where(s.types == 0, 3, 0).astype(np.int32)
+    w = weights(m, 4, 0.3)
+    pot = make(m, s, prec, w)
+    E, F, V = pot.compute(s.coords)
+    Eo, aeo, Fo, Vo = oracle.gf_compute(m, w, s.types, s.coords, s.box)
+    assert abs(E - Eo) <= 10 * tol * abs(Eo)
+    assert np.max(np.abs(F - Fo)) <= tol * frms(Fo)
+    assert np.max(np.abs(V - Vo)) <= tol * np.linalg.norm(Vo)
