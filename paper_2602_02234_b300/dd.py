@@ -36,9 +36,10 @@ ghost atoms whose centres mask, dp_set_centres, marks the owned ones, or for
 a layer-coupled model whose energy seed, dp_set_energy_seed, does; in the
 CPU tests the FP64 oracle), so this module holds the partitioning and the
 communication only.
-Exchanges use torch.distributed object collectives (gloo or NCCL); the design
-sends to every rank for simplicity, where a production layout would talk to
-the two slab neighbours only.
+The halo exchange and the reverse force exchange are point to point with the
+two slab neighbours (torch.distributed isend/irecv, gloo or NCCL): since the
+halo is no wider than a slab, every ghost comes from one of them.  The total
+energy is the one global reduction.
 """
 from __future__ import annotations
 
@@ -73,56 +74,66 @@ class SlabDecomposition:
         self.box, self.n_ranks, self.rank, self.rc, self.axis = box, n_ranks, rank, rc, axis
         self.halo = halo
 
+    def peers(self):
+        """The slab neighbours (rank - 1 and rank + 1, periodic): with a halo
+        no wider than a slab, every ghost lives in one of them."""
+        if self.n_ranks == 1:
+            return []
+        return sorted({(self.rank - 1) % self.n_ranks, (self.rank + 1) % self.n_ranks})
+
     def gather_local(self, dist, ids, coords, types):
         """Owned atoms (global ids, positions, species) in; owned + ghosts out.
 
-        Returns (local_ids, local_coords, local_types, n_owned): the owned atoms
-        first, in the given order, then the ghosts by increasing global id."""
+        Each rank sends its slab neighbours the owned atoms within the halo of
+        their slabs (point to point) and receives theirs.  Returns
+        (local_ids, local_coords, local_types, n_owned): the owned atoms
+        first, in the given order, then the ghosts by increasing global id;
+        `ghost_from` keeps the rank each ghost came from."""
         ids = np.asarray(ids, dtype=np.int64)
         coords = np.asarray(coords, dtype=np.float64)
         types = np.asarray(types, dtype=np.int32)
-        mine = (ids, coords, types)
-        parts = [None] * self.n_ranks
-        if dist is not None and self.n_ranks > 1:
-            dist.all_gather_object(parts, mine)
-        else:
-            parts = [mine]
-        g_ids, g_x, g_t = [], [], []
-        for r, (pi, px, pt) in enumerate(parts):
-            if r == self.rank:
-                continue
-            near = slab_distance(px, self.box, self.rank, self.n_ranks, self.axis) < self.halo
-            g_ids.append(pi[near])
-            g_x.append(px[near])
-            g_t.append(pt[near])
+        out = {}
+        for q in self.peers():
+            near = slab_distance(coords, self.box, q, self.n_ranks, self.axis) < self.halo
+            out[q] = np.concatenate([ids[near, None].astype(np.float64), coords[near],
+                                     types[near, None].astype(np.float64)], axis=1)
+        got = _exchange(dist, out, 5) if out and dist is not None else {}
+        g_ids, g_x, g_t, g_src = [], [], [], []
+        for q, rows in sorted(got.items()):
+            g_ids.append(rows[:, 0].astype(np.int64))
+            g_x.append(rows[:, 1:4])
+            g_t.append(rows[:, 4].astype(np.int32))
+            g_src.append(np.full(len(rows), q, np.int64))
         if g_ids:
             gi = np.concatenate(g_ids)
             order = np.argsort(gi, kind="stable")
-            gi, gx, gt = gi[order], np.concatenate(g_x)[order], np.concatenate(g_t)[order]
+            gi, gx = gi[order], np.concatenate(g_x)[order]
+            gt, gs = np.concatenate(g_t)[order], np.concatenate(g_src)[order]
         else:
-            gi, gx, gt = np.zeros(0, np.int64), np.zeros((0, 3)), np.zeros(0, np.int32)
+            gi, gx, gt, gs = np.zeros(0, np.int64), np.zeros((0, 3)), np.zeros(0, np.int32), np.zeros(0, np.int64)
+        self.ghost_from = gs
         return (np.concatenate([ids, gi]), np.concatenate([coords, gx]),
                 np.concatenate([types, gt]), len(ids))
 
     def reduce_forces(self, dist, local_ids, local_forces, n_owned):
         """Partial forces on owned + ghost atoms in; total forces on the owned
-        atoms out (the ghosts' partial forces go back to their owners)."""
+        atoms out: each ghost's partial force goes back to the neighbour it
+        came from (point to point), which adds it to its owned atom."""
         local_ids = np.asarray(local_ids, dtype=np.int64)
+        local_forces = np.asarray(local_forces, dtype=np.float64)
         F = np.array(local_forces[:n_owned], dtype=np.float64)
-        sent = (local_ids[n_owned:], np.asarray(local_forces[n_owned:], dtype=np.float64))
-        parts = [None] * self.n_ranks
-        if dist is not None and self.n_ranks > 1:
-            dist.all_gather_object(parts, sent)
-        else:
+        if dist is None or self.n_ranks == 1:
             return F
+        gids, gF = local_ids[n_owned:], local_forces[n_owned:]
+        out = {}
+        for q in self.peers():
+            sel = self.ghost_from == q
+            out[q] = np.concatenate([gids[sel, None].astype(np.float64), gF[sel]], axis=1)
+        got = _exchange(dist, out, 4)
         pos = {int(g): k for k, g in enumerate(local_ids[:n_owned])}
-        for r, (gi, gf) in enumerate(parts):
-            if r == self.rank:
-                continue
-            for g, f in zip(gi, gf):
-                k = pos.get(int(g))
-                if k is not None:
-                    F[k] += f
+        for q in sorted(got):                       # fixed order: by rank, then as sent
+            for row in got[q]:
+                F[pos[int(row[0])]] += row[1:4]
         return F
 
     def total(self, dist, value):
@@ -163,3 +174,25 @@ def partial_forces(n_local, centres, pair_j, pair_g):
             F[i] += pair_g[q, p]
             F[j] -= pair_g[q, p]
     return F
+
+
+def _exchange(dist, out, width):
+    """Point-to-point exchange of float64 row blocks with the peers in `out`
+    ({rank: (k, width) array}): sizes first, then the rows, with non-blocking
+    sends and receives so that no ordering between the ranks is needed.
+    Returns {rank: the rows that rank sent here}."""
+    import torch
+    peers = sorted(out)
+    n_out = {q: torch.tensor([len(out[q])], dtype=torch.int64) for q in peers}
+    n_in = {q: torch.zeros(1, dtype=torch.int64) for q in peers}
+    reqs = [dist.isend(n_out[q], q) for q in peers] + [dist.irecv(n_in[q], q) for q in peers]
+    for r in reqs:
+        r.wait()
+    t_out = {q: torch.from_numpy(np.ascontiguousarray(out[q], dtype=np.float64).reshape(-1)) for q in peers}
+    t_in = {q: torch.zeros(int(n_in[q].item()) * width, dtype=torch.float64) for q in peers}
+    reqs = [dist.isend(t_out[q], q) for q in peers if t_out[q].numel()]
+    reqs += [dist.irecv(t_in[q], q) for q in peers if t_in[q].numel()]
+    for r in reqs:
+        r.wait()
+    return {q: t_in[q].numpy().reshape(-1, width) for q in peers}
+

@@ -173,3 +173,13 @@ def test_seeded_oracle_counts_only_seeded_atoms():
         assert E2 == pytest.approx(float(np.sum(ae1[seed > 0])), rel=1e-13)
         assert np.array_equal(ae2, ae1)
         assert np.max(np.abs(F2.sum(0))) <= 1e-10 * np.max(np.abs(F2))
+
+
+def test_exchange_partners_are_the_slab_neighbours():
+    """Halo and force exchanges are point to point with the two slab
+    neighbours (one for two ranks, none for one)."""
+    box = np.array([40.0, 20.0, 20.0])
+    assert dd.SlabDecomposition(box, 4, 0, 6.0).peers() == [1, 3]
+    assert dd.SlabDecomposition(box, 4, 2, 6.0).peers() == [1, 3]
+    assert dd.SlabDecomposition(box, 2, 1, 6.0).peers() == [0]
+    assert dd.SlabDecomposition(box, 1, 0, 6.0).peers() == []
