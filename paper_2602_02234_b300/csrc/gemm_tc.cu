@@ -191,6 +191,7 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
     // so that four neighbouring threads own one row's 16 columns and every
     // global access of the warp covers 8 rows x 64 contiguous bytes
     float* st = stage + warp * 32 * kStageLd;
+    float dacc[4] = {0.f, 0.f, 0.f, 0.f};   // epi 5: this thread's part of each row's dsw sum
     for (int c = 0; c < g.N; c += 16) {
       float v[16];
       tc::tmem_ld16(tb + lane_off + (uint32_t)c, v);
@@ -222,6 +223,29 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
           *Cp = make_float4(y[0], y[1], y[2], y[3]);
           *reinterpret_cast<float4*>(g.v_out + xr * g.ldc + col) =
               make_float4(e.x + sw * y[0], e.y + sw * y[1], e.z + sw * y[2], e.w + sw * y[3]);
+          continue;
+        }
+        if (g.epi == 5) {   // edge adjoint and the message's adjoint on kept slots
+          const float4 dv = *Cp;
+          float y[4] = {dv.x + x[0], dv.y + x[1], dv.z + x[2], dv.w + x[3]};
+          const int jn = g.sel_j[row];
+          if (jn >= 0) {
+            const float f = g.inv_nmax * g.sw[row];
+            const float4 gv = *reinterpret_cast<const float4*>(g.dm + (long long)((int)row / g.nmax) * g.lddm + col);
+            const float4 uv = *reinterpret_cast<const float4*>(g.u + (long long)jn * g.ldc + col);
+            const float4 ev = *reinterpret_cast<const float4*>(g.e_in + row * g.ldc + col);
+            const float gq[4] = {gv.x, gv.y, gv.z, gv.w}, uq[4] = {uv.x, uv.y, uv.z, uv.w},
+                        eq[4] = {ev.x, ev.y, ev.z, ev.w};
+            float xo[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              y[q] += f * gq[q] * uq[q];
+              xo[q] = f * gq[q] * eq[q];
+              dacc[u] += gq[q] * eq[q] * uq[q];
+            }
+            *reinterpret_cast<float4*>(g.x_out + row * g.ldc + col) = make_float4(xo[0], xo[1], xo[2], xo[3]);
+          }
+          *Cp = make_float4(y[0], y[1], y[2], y[3]);
           continue;
         }
         if (g.epi == 3) {   // edge update: v = tanh(Ai + Bj + acc + b), e1 = e_in + v
@@ -267,6 +291,19 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
         *Cp = make_float4(y[0], y[1], y[2], y[3]);
       }
       __syncwarp();   // the stage is rewritten by the next column block
+    }
+    if (g.epi == 5) {   // each row's dsw sum over its four threads (lanes 4r .. 4r + 3), in a fixed order
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        float v = dacc[u];
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        const long long m = m0 + 32 * warp + (lane >> 2) + 8 * u;
+        if ((lane & 3) == 0 && m < g.M) {
+          const long long row = g.c_rows ? (long long)g.c_rows[m] : m;
+          if (g.sel_j[row] >= 0) g.dsw[row] += g.inv_nmax * v;
+        }
+      }
     }
     tc::fence_before_sync();
     __syncthreads();          // tensor memory and the A tile are reused by the next tile

@@ -16,7 +16,7 @@ namespace dp {
 // Ai, Bj, e_in, v_out laid out like C, c_rows and beta unused; or 4 the angle
 // channel's output: C(m, n) = t = tanh(acc + bias(n)) and
 // v_out(x, n) = e_in(x, n) + sa[x] t at row x = x_rows ? x_rows[m] : row'(m)
-// (e_in, v_out with C's ldc; e_in may equal v_out).
+// (e_in, v_out with C's ldc; e_in may equal v_out); or 5, below.
 //   A(m, k) = A[row(m) * lda + k], row(m) = a_rows ? a_rows[m] : m; A 16-byte
 //             aligned, lda a multiple of 4
 //   B(k, n) = B[k * ldb + n]  (b_nk = 0)  or  B[n * ldb + k]  (b_nk = 1)
@@ -50,6 +50,15 @@ struct GemmTc {
   const float *Ai, *Bj, *e_in, *sa;
   float* v_out;
   const int* x_rows;   // epi 4: row of e_in, v_out and sa for m (optional)
+  // epi 5 (the graph family's edge adjoint with the message's, C = de, beta 1):
+  // for row m = slot (i, p), i = m / nmax, j = sel_j[m]: C += acc, and on kept
+  // slots C += f g_i u_j, x_out = f g_i e_in, dsw[m] += inv_nmax sum_n g_i e_in
+  // u_j with f = inv_nmax sw[m] and g_i row i of dm (stride lddm); u, e_in,
+  // x_out laid out like C
+  const float *sw, *dm, *u;
+  long long lddm;
+  float *x_out, *dsw;
+  float inv_nmax;
 };
 
 bool gemm_tc_shape_ok(int N, int K);

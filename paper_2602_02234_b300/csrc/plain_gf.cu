@@ -1006,6 +1006,37 @@ class PlainGf : public Model {
       return false;
     }
   }
+  // mixed form: de += dy Wc^T with the message adjoint of layer l in the same
+  // product's epilogue (de += f dm_i u_j, X = f dm_i e, dsw on kept slots);
+  // false when not applicable (then the two run separately)
+  bool msg_fusable() const {
+    if constexpr (std::is_same<T, float>::value)
+      return tc_ && gemm_tc_shape_ok(m_.ed, m_.ed) && m_.ed % 4 == 0 && m_.nd % 4 == 0;
+    else
+      return false;
+  }
+  void msg_fused(int l, const NbrView& nv, cudaStream_t st) {
+    if constexpr (std::is_same<T, float>::value) {
+      const int Ed = m_.ed, Nd = m_.nd;
+      GemmTc t{};
+      t.M = (int)((long long)n_ * m_.nmax); t.N = Ed; t.K = Ed;
+      t.A = dy_; t.lda = Ed;
+      t.B = Wc_[l]; t.ldb = Ed; t.b_nk = 1;
+      t.C = de_; t.ldc = Ed; t.beta = 1.f; t.epi = 5;
+      t.sel_j = nv.sel_j; t.nmax = m_.nmax; t.sw = sw_; t.dm = dnm_ + Nd; t.lddm = Nd + Ed;
+      t.u = uu_[l]; t.e_in = ee_[l]; t.x_out = X_; t.dsw = dsw_e_; t.inv_nmax = 1.f / (float)m_.nmax;
+      t.status = flags_;
+#ifdef DP_GF_BF16
+      t.fp16 = 0;
+#else
+      t.fp16 = 1;
+#endif
+      t.split = 0;   // slot rows: one 16-bit activation operand
+      gemm_tc(t, st);
+    } else {
+      (void)l; (void)nv; (void)st;
+    }
+  }
   bool tc_ = false;
   int* flags_ = nullptr;
   const unsigned char* seed_ = nullptr;   // energy seed (device, optional)
@@ -1352,7 +1383,8 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
       k_dtanh4<T><<<grid(PE / 4), 256, 0, st>>>(PE / 4, de_, vv_[l], dy_);
     else
       k_dtanh<T><<<grid(PE), 256, 0, st>>>(PE, de_, vv_[l], dy_);
-    {  // de += dy Wc^T
+    const bool fused_msg = msg_fusable();
+    if (!fused_msg) {  // de += dy Wc^T (else below, with the message adjoint)
       Gemm<T> g{};
       g.M = (int)P; g.N = Ed; g.K = Ed;
       g.A = dy_; g.a_rm = Ed; g.a_rk = 1;
@@ -1384,7 +1416,9 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
       mm(g, st);
     }
     k_add_strided<T><<<grid((long long)n * Nd), 256, 0, st>>>(n, Nd, Nd + Ed, dn1_, dnm_, dn_);
-    if (Ed % 4 == 0 && Nd % 4 == 0)
+    if (fused_msg)
+      msg_fused(l, nv, st);
+    else if (Ed % 4 == 0 && Nd % 4 == 0)
       k_msg_bwd4<T><<<grid(P * 16), 256, 0, st>>>(P, NM, Ed, Nd + Ed, inv_nmax, nv.sel_j, sw_, ee_[l],
                                                   uu_[l], dnm_ + Nd, de_, X_, dsw_e_);
     else
@@ -1399,7 +1433,7 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
       g.C = dn_; g.c_rm = Nd; g.c_rn = 1; g.nb2 = 1; g.alpha = T(1); g.beta = T(1);
       mm(g, st);
     }
-    k += fused_rowsum ? 17 : 18;
+    k += 18 - (fused_rowsum ? 1 : 0) - (fused_msg ? 1 : 0);
   }
   if (Ed % 4 == 0)
     k_pair_grad4<T><<<grid(P * 16), 256, 0, st>>>(P, Ed, nv.sel_j, d_, sw_, dsw_, dsa_, rh_, ee_[0], we_, de_,
