@@ -46,6 +46,15 @@ __device__ __forceinline__ void ld4(const double* p, double* v) {
   const double2 u = reinterpret_cast<const double2*>(p)[0], w = reinterpret_cast<const double2*>(p)[1];
   v[0] = u.x; v[1] = u.y; v[2] = w.x; v[3] = w.y;
 }
+// two consecutive values (8- or 16-byte aligned) as one vector load
+__device__ __forceinline__ void ld2(const float* p, float* v) {
+  const float2 u = *reinterpret_cast<const float2*>(p);
+  v[0] = u.x; v[1] = u.y;
+}
+__device__ __forceinline__ void ld2(const double* p, double* v) {
+  const double2 u = *reinterpret_cast<const double2*>(p);
+  v[0] = u.x; v[1] = u.y;
+}
 __device__ __forceinline__ void st4(float* p, const float* v) {
   *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
@@ -155,11 +164,12 @@ __global__ void k_msg_warp(int n, int nmax, int ed, T inv_nmax, const int* __res
         jj[q] = p + q < nmax ? sel_j[base + p + q] : -1;
         if (jj[q] >= 0) {
           const size_t e = base + p + q;
+          T ev[2], uv[2];
           sv[q] = sw[e];
-          e0[q] = edge[e * ed + c];
-          e1[q] = edge[e * ed + c + 1];
-          u0[q] = u[(size_t)jj[q] * ed + c];
-          u1[q] = u[(size_t)jj[q] * ed + c + 1];
+          ld2(edge + e * ed + c, ev);
+          ld2(u + (size_t)jj[q] * ed + c, uv);
+          e0[q] = ev[0]; e1[q] = ev[1];
+          u0[q] = uv[0]; u1[q] = uv[1];
         }
       }
 #pragma unroll
