@@ -20,7 +20,7 @@ import pytest
 import torch
 
 import oracle
-from synth import configs as C, normal_blob, water_box
+from synth import configs as C, normal_blob, serving_system, water_box
 from tests import af_torch_ref
 
 TINY = C.AttnModel(n_species=2, e1=6, e2=10, m1=16, m2=4, n_layers=2, hidden=16, heads=2,
@@ -399,3 +399,41 @@ def test_group_forces_are_central_differences_of_the_group_energy():
     x2[~mask] += 0.37
     E2 = oracle.af_compute_group(m, w, s.types, x2, s.box, mask)[0]
     assert E2 == E
+
+
+# ---------------------------------------------------------------- sampled forces
+def _subset_case(name):
+    if name == "water64":              # the config-1 model: nmax 46 truncates every list
+        return C.WATER64_MODEL, C.water64()
+    if name == "water96_small_box":    # 9.86 A box < 2 rc: several images of one atom
+        return replace(C.ATTN_MODEL, n_layers=1), serving_system(96, 5)
+    # 700 atoms, nmax lowered to 80 (about 90 lie within rc): lists truncate
+    return replace(C.ATTN_MODEL, n_layers=1, nmax=80), serving_system(700, 9)
+
+
+@pytest.mark.parametrize("name", ["water64", "water96_small_box", "protein700_truncated"])
+def test_forces_subset_equals_the_whole_system_forces(name):
+    """The sampled-force assembly used at 24,000 and 100,000 atoms (pair
+    gradients of the sample and of every centre that lists a sampled atom,
+    gathered in numpy) against the whole-system forces of the C oracle, which
+    central differences pin.  The sample holds the most crowded atom, whose
+    list is truncated, and random atoms; the cases cover truncated lists and a
+    box whose atoms see several images of one neighbour."""
+    m, s = _subset_case(name)
+    w = blob(m, seed=C.WEIGHT_SEED)
+    cnt = oracle.neighbours(s.coords, s.box, m.rc, 1)[0]
+    if name != "water96_small_box":
+        assert np.sum(cnt > m.nmax) > 0          # truncation is active
+    else:
+        nj = oracle.neighbours(s.coords, s.box, m.rc, 4 * m.nmax)[1]
+        assert any(len(set(nj[i, :cnt[i]].tolist())) < cnt[i] for i in range(s.n))
+    rng = np.random.default_rng(5)
+    sample = np.unique(np.concatenate([rng.choice(s.n, 9, replace=False),
+                                       [int(np.argmax(cnt)), 0]])).astype(np.int32)
+    F_sub = oracle.af_forces_subset(m, w, s.types, s.coords, s.box, sample)
+    E, ae, F, V = oracle.af_compute(m, w, s.types, s.coords, s.box)
+    fr = np.sqrt(np.mean(F ** 2))
+    assert np.max(np.abs(F_sub - F[sample])) <= 1e-12 * fr
+    # the sampled atomic energies come from the same per-centre routine
+    ae_sub = oracle.af_atoms(m, w, s.types, s.coords, s.box, sample)["atom_e"]
+    assert np.max(np.abs(ae_sub - ae[sample])) <= 1e-12 * np.max(np.abs(ae))
