@@ -307,7 +307,11 @@ int dp_selftest_timeout(long long max_polls);
  *   n_in_rc [n_atoms]            device pointer, neighbours within rcut
  *   cuda_stream                  stream to run on (NULL: legacy default stream)
  * Limits: n_atoms <= 1024 and at most 384 neighbours within rcut per atom
- * (DP_ERR_ARG / DP_ERR_NLIST_OVERFLOW beyond).  Its scratch memory is a static
+ * (DP_ERR_ARG / DP_ERR_NLIST_OVERFLOW beyond).  A box whose own periodic
+ * images of one atom already exceed 384 within rcut is refused before any
+ * launch.  After DP_ERR_NLIST_OVERFLOW from the kernel, n_in_rc of every atom
+ * that overflowed is 385 (more than the limit) and its rows of nbr_j /
+ * nbr_img are empty (-1 / 0); the other atoms' rows are complete.  Its scratch memory is a static
  * array of the library (about 6.3 MB on every GPU that loads it, held until
  * the process exits), shared by all calls: calls that overlap on the GPU race
  * and must be serialised by the caller.  The first call on a device looks up

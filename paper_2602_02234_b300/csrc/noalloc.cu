@@ -10,8 +10,12 @@
 //
 // Limits: at most kNoallocMaxAtoms atoms and kNoallocMaxCand candidates
 // within rc per atom (images included); larger requests are rejected with
-// DP_ERR_ARG / DP_ERR_NLIST_OVERFLOW.  Every GPU that loads the library holds
-// the array (about 6.3 MB) until the process exits.
+// DP_ERR_ARG / DP_ERR_NLIST_OVERFLOW.  A box so small that an atom's own
+// periodic images alone exceed the candidate limit is refused on the host
+// before any launch, and the kernel stops scanning an atom's candidates as
+// soon as they exceed the limit, so an overflowing call returns quickly.
+// Every GPU that loads the library holds the array (about 6.3 MB) until the
+// process exits.
 //
 // The array is shared by every call in the process: calls whose kernels
 // overlap on the GPU (different streams, or different host threads) race on
@@ -20,6 +24,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <mutex>
 #include <string>
 
 #include "common.cuh"
@@ -101,10 +106,20 @@ __global__ void k_neighbours_noalloc(int n, const double* __restrict__ x, double
       mine[pos].img = pack_img(nn[0], nn[1], nn[2]);
     }
     cnt += __popc(b);
+    if (cnt > kNoallocMaxCand) break;   // cnt is the same in every lane
   }
   if (cnt > kNoallocMaxCand) {
-    if (lane == 0) atomicOr(&scr->status, 1);
-    cnt = kNoallocMaxCand;
+    // overflow: flag it, report "more than the limit" and leave empty rows
+    if (lane == 0) {
+      atomicOr(&scr->status, 1);
+      n_in_rc[i] = kNoallocMaxCand + 1;
+    }
+    for (int p = lane; p < nmax; p += 32) {
+      size_t o = (size_t)i * nmax + p;
+      nbr_j[o] = -1;
+      for (int a = 0; a < 3; ++a) nbr_img[3 * o + a] = 0;
+    }
+    return;
   }
   __syncwarp();
   if (lane == 0) n_in_rc[i] = cnt;
@@ -134,8 +149,34 @@ __global__ void k_neighbours_noalloc(int n, const double* __restrict__ x, double
 
 // Device address of the scratch array, looked up once per device with that
 // device current (the host-side name of a __device__ variable is not a
-// device address).
+// device address).  The lookup is serialised by a mutex, so host threads
+// that make their first calls at the same time do not race on the table.
 static NoallocScratch* g_scratch_ptr[64] = {nullptr};
+static std::mutex g_scratch_mutex;
+
+// Periodic images n != 0 of one atom with |n L| < rc, counted from the
+// centre outwards (0, 1, -1, 2, -2, ...) and given up once above `limit`:
+// the loop stays short whether the count is small or large.
+static int own_images_within(const double* L, double rc, const int* nimg, int limit) {
+  auto at = [](int k) { return (k & 1) ? (k + 1) / 2 : -(k / 2); };
+  int count = 0;
+  const double rc2 = rc * rc;
+  for (int ka = 0; ka < 2 * nimg[0] + 1; ++ka) {
+    const double xa = at(ka) * L[0];
+    if (xa * xa >= rc2) break;
+    for (int kb = 0; kb < 2 * nimg[1] + 1; ++kb) {
+      const double yb = at(kb) * L[1];
+      if (xa * xa + yb * yb >= rc2) break;
+      for (int kc = 0; kc < 2 * nimg[2] + 1; ++kc) {
+        const double zc = at(kc) * L[2];
+        const double d2 = xa * xa + yb * yb + zc * zc;
+        if (d2 >= rc2) break;
+        if (d2 > 0.0 && ++count > limit) return count;
+      }
+    }
+  }
+  return count;
+}
 
 static thread_local std::string g_noalloc_error;
 
@@ -170,33 +211,42 @@ extern "C" int dp_neighbour_list_noalloc(const double* coords, int n_atoms, cons
       g_noalloc_error = "box lengths must be positive";
       return DP_ERR_ARG;
     }
+  int img[3];
+  for (int a = 0; a < 3; ++a) img[a] = (int)ceil(rcut / box[a]) + 1;
+  if (img[0] > 500 || img[1] > 500 || img[2] > 500) {
+    g_noalloc_error = "box too small for the cutoff";
+    return DP_ERR_ARG;
+  }
+  if (own_images_within(box, rcut, img, kNoallocMaxCand) > kNoallocMaxCand) {
+    g_noalloc_error = "more than " + std::to_string(kNoallocMaxCand) +
+                      " periodic images of one atom lie within rcut";
+    return DP_ERR_NLIST_OVERFLOW;
+  }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= 64) {
     g_noalloc_error = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
     return DP_ERR_CUDA;
   }
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      g_noalloc_error = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
-      return DP_ERR_CUDA;
+  NoallocScratch* scr = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_ptr[dev]) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p) {
+        g_noalloc_error = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+        return DP_ERR_CUDA;
+      }
+      g_scratch_ptr[dev] = (NoallocScratch*)p;
     }
-    g_scratch_ptr[dev] = (NoallocScratch*)p;
+    scr = g_scratch_ptr[dev];
   }
-  NoallocScratch* scr = g_scratch_ptr[dev];
   cudaStream_t st = (cudaStream_t)cuda_stream;
   e = cudaMemsetAsync(&scr->status, 0, sizeof(int), st);
   if (e != cudaSuccess) {
     g_noalloc_error = std::string("clearing the status word: ") + cudaGetErrorString(e);
     return DP_ERR_CUDA;
-  }
-  int img[3];
-  for (int a = 0; a < 3; ++a) img[a] = (int)ceil(rcut / box[a]) + 1;
-  if (img[0] > 500 || img[1] > 500 || img[2] > 500) {
-    g_noalloc_error = "box too small for the cutoff";
-    return DP_ERR_ARG;
   }
   const int warps = 4;
   k_neighbours_noalloc<<<(n_atoms + warps - 1) / warps, 32 * warps, 0, st>>>(
