@@ -8,9 +8,10 @@
 //              neighbour slots are the 128 rows of every tile.  Environment
 //              and softmax in FP32 registers (several threads per row, each
 //              owning 32-column chunks of it), every matrix
-//              product a tcgen05.mma from shared-memory BF16 tiles into
-//              FP32 tensor memory.  Writes the descriptor D (BF16), T (FP32),
-//              the layer inputs G_l (BF16 tiles) and LayerNorm 1/sigma.
+//              product a tcgen05.mma from shared-memory 16-bit tiles (FP16
+//              by default, BF16 when built with DP_FUSED_BF16) into FP32
+//              tensor memory.  Writes the descriptor D (16-bit), T (FP32),
+//              the layer inputs G_l (16-bit tiles) and LayerNorm 1/sigma.
 //   k_fit      tiles of 128 atoms of one species: fitting MLP forward, atomic
 //              energies (FP64 sum of FP32 products) and the input-gradient
 //              chain down to dE/dD, all products on the tensor cores.
@@ -111,6 +112,8 @@ static_assert(kSmemAtom <= 227 * 1024, "per-atom shared memory");
 
 struct Params {
   int n, nmax, e1, e2, m2, n_layers, heads, dh;
+  int m1;                                 // real embedding width; columns [m1, 128) are padding
+  float inv_m1;
   int atom0;                              // atoms [atom0, n) are evaluated
   float rs, rc, inv_nmax, inv_sqrt_d;
   const int* sel_j;
@@ -736,7 +739,9 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
       sum += (s4[0] + s4[1]) + (s4[2] + s4[3]);
     }
     sum = row_sum(m, make_float4(sum, 0.f, 0.f, 0.f)).x;
-    const float mu = sum * (1.f / kW);
+    // real columns: every column with message passing (it needs m1 = 128)
+    const int m1 = MP ? kW : p.m1;
+    const float mu = sum * (MP ? 1.f / kW : p.inv_m1);
     for (int c = 32 * pt; c < kW; c += kStride) {
       float g[32], y[32];
       tc::tmem_ld32(tb + lo + R2 + c, g);
@@ -744,19 +749,19 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
       float s4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
-        const float z = g[q] + y[q] + bo[c + q] - mu;
+        const float z = c + q < m1 ? g[q] + y[q] + bo[c + q] - mu : 0.f;   // padding: none
         s4[q & 3] += z * z;
       }
       sq += (s4[0] + s4[1]) + (s4[2] + s4[3]);
     }
     sq = row_sum(m, make_float4(sq, 0.f, 0.f, 0.f)).x;
-    const float rs = valid ? rsqrtf(sq * (1.f / kW) + 1e-5f) : 0.f;
+    const float rs = valid ? rsqrtf(sq * (MP ? 1.f / kW : p.inv_m1) + 1e-5f) : 0.f;
     for (int c = 32 * pt; c < kW; c += kStride) {
       float g[32], y[32];
       tc::tmem_ld32(tb + lo + R2 + c, g);
       tc::tmem_ld32(tb + lo + R1 + c, y);
 #pragma unroll
-      for (int q = 0; q < 32; ++q) g[q] = (g[q] + y[q] + bo[c + q] - mu) * rs;
+      for (int q = 0; q < 32; ++q) g[q] = c + q < m1 ? (g[q] + y[q] + bo[c + q] - mu) * rs : 0.f;
       tc::tmem_st32(tb + lo + R2 + c, g);
       store32(sm + SM_G, r, c, kW, kW, g);
     }
@@ -1068,15 +1073,17 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
         s2 += (b4[0] + b4[1]) + (b4[2] + b4[3]);
       }
       const float4 o = row_sum(m, make_float4(s1, s2, 0.f, 0.f));
-      s1 = o.x * (1.f / kW);
-      s2 = o.y * (1.f / kW);
+      const int m1 = MP ? kW : p.m1;   // message passing needs m1 = 128
+      s1 = o.x * (MP ? 1.f / kW : p.inv_m1);
+      s2 = o.y * (MP ? 1.f / kW : p.inv_m1);
       for (int c = 32 * pt; c < kW; c += kStride) {
         float dg[32], go[32];
         tc::tmem_ld32(tb + lo + R2 + c, dg);
 #pragma unroll
         for (int q = 0; q < 32; q += 8) load8(sm + SM_V, r, c + q, kW, go + q);
 #pragma unroll
-        for (int q = 0; q < 32; ++q) dg[q] = valid ? rs * (dg[q] - s1 - go[q] * s2) : 0.f;
+        for (int q = 0; q < 32; ++q)
+          dg[q] = valid && c + q < m1 ? rs * (dg[q] - s1 - go[q] * s2) : 0.f;
         tc::tmem_st32(tb + lo + R2 + c, dg);
         store32(sm + SM_P, r, c, kW, kW, dg);
       }
@@ -1775,29 +1782,35 @@ class FusedAf : public Model {
 bool FusedAf::init(const AfDims& m, const double* w, int n_atoms, const int* types, std::string* err) {
   m_ = m;
   n_ = n_atoms;
-  const int S = m.n_species, L = m.n_layers, E1 = m.e1, E2 = m.e2, H = m.hidden;
-  const int KD = kW * m.m2;
+  const int S = m.n_species, L = m.n_layers, H = m.hidden;
+  // Real widths (blob layout) and the widths the kernels run at: the embedding
+  // widths are padded to multiples of 16 and m1 to 128 with zero weights and
+  // biases, so every padded unit is tanh(0) = 0 and feeds nothing; the
+  // LayerNorm takes its statistics over the m1 real columns only.
+  const int E1r = m.e1, E2r = m.e2, M1 = m.m1;
+  const int E1 = (E1r + 15) / 16 * 16, E2 = (E2r + 15) / 16 * 16;
+  const int KD = kW * m.m2, KDr = M1 * m.m2;
   // ---- walk the blob
   size_t off = 0;
   auto at = [&](size_t o) { return w[o]; };
   std::vector<size_t> oW1(S), ob1(S), oW2(S), ob2(S), oW3(S), ob3(S);
   for (int t = 0; t < S; ++t) {
-    oW1[t] = off; off += E1;
-    ob1[t] = off; off += E1;
-    oW2[t] = off; off += (size_t)E1 * E2;
-    ob2[t] = off; off += E2;
-    oW3[t] = off; off += (size_t)E2 * kW;
-    ob3[t] = off; off += kW;
+    oW1[t] = off; off += E1r;
+    ob1[t] = off; off += E1r;
+    oW2[t] = off; off += (size_t)E1r * E2r;
+    ob2[t] = off; off += E2r;
+    oW3[t] = off; off += (size_t)E2r * M1;
+    ob3[t] = off; off += M1;
   }
   size_t oWt = 0;
   if (m.mp) { oWt = off; off += (size_t)S * kW; }
   std::vector<size_t> oq(L), ok(L), ov(L), oo(L), obo(L), oWm(L), obm(L);
   for (int l = 0; l < L; ++l) {
-    oq[l] = off; off += (size_t)kW * H;
-    ok[l] = off; off += (size_t)kW * H;
-    ov[l] = off; off += (size_t)kW * H;
-    oo[l] = off; off += (size_t)H * kW;
-    obo[l] = off; off += kW;
+    oq[l] = off; off += (size_t)M1 * H;
+    ok[l] = off; off += (size_t)M1 * H;
+    ov[l] = off; off += (size_t)M1 * H;
+    oo[l] = off; off += (size_t)H * M1;
+    obo[l] = off; off += M1;
     if (m.mp) {
       oWm[l] = off; off += (size_t)kW * kW;
       obm[l] = off; off += kW;
@@ -1805,7 +1818,7 @@ bool FusedAf::init(const AfDims& m, const double* w, int n_atoms, const int* typ
   }
   std::vector<size_t> oF1(S), oc1(S), oF2(S), oc2(S), oF3(S), oc3(S), oF4(S), oc4(S);
   for (int t = 0; t < S; ++t) {
-    oF1[t] = off; off += (size_t)KD * m.f1;
+    oF1[t] = off; off += (size_t)KDr * m.f1;
     oc1[t] = off; off += m.f1;
     oF2[t] = off; off += (size_t)m.f1 * m.f2;
     oc2[t] = off; off += m.f2;
@@ -1817,28 +1830,32 @@ bool FusedAf::init(const AfDims& m, const double* w, int n_atoms, const int* typ
   // ---- pack tiles
   std::vector<uint16_t> W2T, W3T, W2R, W3R, WqT, WkT, WvT, WoT, WqR, WkR, WvR, WoR;
   std::vector<float> W1, b1, b2, b3, bo;
+  // weight (row, col) of a row-major (rows x cols) block at o, zero outside
+  auto wz = [&](size_t o, int row, int col, int rows, int cols) {
+    return row < rows && col < cols ? at(o + (size_t)row * cols + col) : 0.0;
+  };
   for (int t = 0; t < S; ++t) {
-    pack(W2T, E2, E1, E1, [&](int r, int k) { return at(oW2[t] + (size_t)k * E2 + r); });
-    pack(W3T, kW, E2, E2, [&](int r, int k) { return at(oW3[t] + (size_t)k * kW + r); });
-    pack(W2R, E1, E2, E2, [&](int r, int k) { return at(oW2[t] + (size_t)r * E2 + k); });
-    pack(W3R, E2, kW, kW, [&](int r, int k) { return at(oW3[t] + (size_t)r * kW + k); });
+    pack(W2T, E2, E1, E1, [&](int r, int k) { return wz(oW2[t], k, r, E1r, E2r); });
+    pack(W3T, kW, E2, E2, [&](int r, int k) { return wz(oW3[t], k, r, E2r, M1); });
+    pack(W2R, E1, E2, E2, [&](int r, int k) { return wz(oW2[t], r, k, E1r, E2r); });
+    pack(W3R, E2, kW, kW, [&](int r, int k) { return wz(oW3[t], r, k, E2r, M1); });
     for (int k = 0; k < E1; ++k) {
-      W1.push_back((float)at(oW1[t] + k));
-      b1.push_back((float)at(ob1[t] + k));
+      W1.push_back(k < E1r ? (float)at(oW1[t] + k) : 0.f);
+      b1.push_back(k < E1r ? (float)at(ob1[t] + k) : 0.f);
     }
-    for (int k = 0; k < E2; ++k) b2.push_back((float)at(ob2[t] + k));
-    for (int k = 0; k < kW; ++k) b3.push_back((float)at(ob3[t] + k));
+    for (int k = 0; k < E2; ++k) b2.push_back(k < E2r ? (float)at(ob2[t] + k) : 0.f);
+    for (int k = 0; k < kW; ++k) b3.push_back(k < M1 ? (float)at(ob3[t] + k) : 0.f);
   }
   for (int l = 0; l < L; ++l) {
-    pack(WqT, H, kW, kW, [&](int r, int k) { return at(oq[l] + (size_t)k * H + r); });
-    pack(WkT, H, kW, kW, [&](int r, int k) { return at(ok[l] + (size_t)k * H + r); });
-    pack(WvT, H, kW, kW, [&](int r, int k) { return at(ov[l] + (size_t)k * H + r); });
-    pack(WoT, kW, H, H, [&](int r, int k) { return at(oo[l] + (size_t)k * kW + r); });
-    pack(WqR, kW, H, H, [&](int r, int k) { return at(oq[l] + (size_t)r * H + k); });
-    pack(WkR, kW, H, H, [&](int r, int k) { return at(ok[l] + (size_t)r * H + k); });
-    pack(WvR, kW, H, H, [&](int r, int k) { return at(ov[l] + (size_t)r * H + k); });
-    pack(WoR, H, kW, kW, [&](int r, int k) { return at(oo[l] + (size_t)r * kW + k); });
-    for (int k = 0; k < kW; ++k) bo.push_back((float)at(obo[l] + k));
+    pack(WqT, H, kW, kW, [&](int r, int k) { return wz(oq[l], k, r, M1, H); });
+    pack(WkT, H, kW, kW, [&](int r, int k) { return wz(ok[l], k, r, M1, H); });
+    pack(WvT, H, kW, kW, [&](int r, int k) { return wz(ov[l], k, r, M1, H); });
+    pack(WoT, kW, H, H, [&](int r, int k) { return wz(oo[l], k, r, H, M1); });
+    pack(WqR, kW, H, H, [&](int r, int k) { return wz(oq[l], r, k, M1, H); });
+    pack(WkR, kW, H, H, [&](int r, int k) { return wz(ok[l], r, k, M1, H); });
+    pack(WvR, kW, H, H, [&](int r, int k) { return wz(ov[l], r, k, M1, H); });
+    pack(WoR, H, kW, kW, [&](int r, int k) { return wz(oo[l], r, k, H, M1); });
+    for (int k = 0; k < kW; ++k) bo.push_back(k < M1 ? (float)at(obo[l] + k) : 0.f);
   }
   // fitting: chunk widths kc1 for K = KD, kc2 for K = f
   const int kc1 = 32;
@@ -1846,14 +1863,14 @@ bool FusedAf::init(const AfDims& m, const double* w, int n_atoms, const int* typ
   std::vector<uint16_t> F1T, F2T, F3T, F3R, F2R, F1R;
   std::vector<float> c1, c2, c3, F4, c4;
   for (int t = 0; t < S; ++t) {
-    pack(F1T, m.f1, KD, kc1, [&](int r, int k) { return at(oF1[t] + (size_t)k * m.f1 + r); });
+    pack(F1T, m.f1, KD, kc1, [&](int r, int k) { return wz(oF1[t], k, r, KDr, m.f1); });
     pack(F2T, m.f2, m.f1, kc2, [&](int r, int k) { return at(oF2[t] + (size_t)k * m.f2 + r); });
     pack(F3T, m.f3, m.f2, kc2, [&](int r, int k) { return at(oF3[t] + (size_t)k * m.f3 + r); });
     pack(F3R, m.f2, m.f3, kc2, [&](int r, int k) { return at(oF3[t] + (size_t)r * m.f3 + k); });
     pack(F2R, m.f1, m.f2, kc2, [&](int r, int k) { return at(oF2[t] + (size_t)r * m.f2 + k); });
     for (int nb = 0; nb < KD / 256; ++nb)
       pack(F1R, 256, m.f1, kc2,
-           [&](int r, int k) { return at(oF1[t] + (size_t)(nb * 256 + r) * m.f1 + k); });
+           [&](int r, int k) { return wz(oF1[t], nb * 256 + r, k, KDr, m.f1); });
     for (int k = 0; k < m.f1; ++k) c1.push_back((float)at(oc1[t] + k));
     for (int k = 0; k < m.f2; ++k) c2.push_back((float)at(oc2[t] + k));
     for (int k = 0; k < m.f3; ++k) {
@@ -1874,7 +1891,7 @@ bool FusedAf::init(const AfDims& m, const double* w, int n_atoms, const int* typ
     HeadTiles& X = extra[h - 1];
     const size_t sh = (size_t)h * fit_len;
     for (int t = 0; t < S; ++t) {
-      pack(X.F1T, m.f1, KD, kc1, [&](int r, int k) { return at(sh + oF1[t] + (size_t)k * m.f1 + r); });
+      pack(X.F1T, m.f1, KD, kc1, [&](int r, int k) { return wz(sh + oF1[t], k, r, KDr, m.f1); });
       pack(X.F2T, m.f2, m.f1, kc2, [&](int r, int k) { return at(sh + oF2[t] + (size_t)k * m.f2 + r); });
       pack(X.F3T, m.f3, m.f2, kc2, [&](int r, int k) { return at(sh + oF3[t] + (size_t)k * m.f3 + r); });
       for (int k = 0; k < m.f1; ++k) X.c1.push_back((float)at(sh + oc1[t] + k));
@@ -1888,6 +1905,7 @@ bool FusedAf::init(const AfDims& m, const double* w, int n_atoms, const int* typ
   }
   Params& p = base_;
   p.n = n_atoms; p.nmax = m.nmax; p.e1 = E1; p.e2 = E2; p.m2 = m.m2; p.n_layers = L;
+  p.m1 = M1; p.inv_m1 = 1.f / M1;
   p.heads = m.heads; p.dh = H / m.heads;
   p.rs = (float)m.rs; p.rc = (float)m.rc; p.inv_nmax = 1.f / m.nmax;
   p.inv_sqrt_d = 1.f / sqrtf((float)p.dh);
@@ -1927,7 +1945,7 @@ bool FusedAf::init(const AfDims& m, const double* w, int n_atoms, const int* typ
     *err = "fused message passing supports at most 500,000 atoms";
     return false;
   }
-  if (m.mp) {   // message passing: FP32 weights of the atom channel and the between-launch state
+  if (m.mp) {   // message passing (m1 = 128): FP32 atom-channel weights and between-launch state
     std::vector<float> Wt(w + oWt, w + oWt + (size_t)S * kW);
     if (!upload(&mp_Wt_, Wt, err)) return false;
     mp_Wm_.resize(L);
@@ -2014,9 +2032,10 @@ bool FusedAf::init(const AfDims& m, const double* w, int n_atoms, const int* typ
 }  // namespace fz
 
 bool fused_af_supported(const AfDims& m, std::string* why) {
-  if (m.m1 != 128 || m.hidden != 128) { *why = "fused path needs m1 = hidden = 128"; return false; }
+  if (m.m1 < 1 || m.m1 > 128 || m.hidden != 128) { *why = "fused path needs m1 <= 128 and hidden = 128"; return false; }
+  if (m.mp && m.m1 != 128) { *why = "fused message passing needs m1 = 128"; return false; }
   if (m.heads != 4) { *why = "fused path needs 4 heads of width 32"; return false; }
-  if (m.e1 % 16 || m.e2 % 16 || m.e1 > 64 || m.e2 > 128) { *why = "fused path needs e1 (<= 64) and e2 (<= 128) multiples of 16"; return false; }
+  if (m.e1 < 1 || m.e2 < 1 || m.e1 > 64 || m.e2 > 128) { *why = "fused path needs e1 <= 64 and e2 <= 128"; return false; }
   if (m.nmax > 128) { *why = "fused path needs nmax <= 128"; return false; }
   if ((128 * m.m2) % 256) { *why = "fused path needs 128 * m2 to be a multiple of 256"; return false; }
   if (m.f1 % 16 || m.f2 % 16 || m.f3 % 16 || m.f1 > 256 || m.f2 > 256 || m.f3 > 256) { *why = "fused path needs fitting widths multiples of 16 and <= 256"; return false; }

@@ -57,8 +57,11 @@ def test_neighbour_lists_exact(name):
 
 
 # ------------------------------------------------------------------ energies / forces
-@pytest.mark.parametrize("prec", [dp.PREC_PLAIN_F64, dp.PREC_PLAIN_F32])
+@pytest.mark.parametrize("prec", [dp.PREC_PLAIN_F64, dp.PREC_PLAIN_F32, dp.PREC_FUSED])
 def test_water64_energy_forces_virial(prec):
+    """The 64-water model (embedding 1-25-50-100, one attention layer, nmax 46):
+    the fused form runs it with the embedding widths padded to 32, 64 and 128
+    (zero weights; LayerNorm statistics over the 100 real columns)."""
     m, s = C.WATER64_MODEL, C.water64()
     pot, w = make(m, s, prec)
     E, F, V = pot.compute(s.coords)
@@ -298,11 +301,27 @@ def test_fused_vs_plain_full_size():
     assert np.max(np.abs(F - Fp)) <= TOL_F[dp.PREC_FUSED] * frms(Fp)
 
 
-def test_fused_unsupported_sizes_are_refused():
-    m, s = C.WATER64_MODEL, C.water64()      # m1 = 100: not a fused shape
+@pytest.mark.parametrize("change", [dict(hidden=96), dict(heads=2), dict(m1=160),
+                                    dict(m1=100, message_passing=1), dict(nmax=130)])
+def test_fused_unsupported_sizes_are_refused(change):
+    m, s = replace(C.WATER64_MODEL, **change), C.water64()
     with pytest.raises(dp.DPError) as e:
         make(m, s, dp.PREC_FUSED)
     assert e.value.code == dp.DP_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("shape", [dict(m1=72, e1=20, e2=36, n_layers=2),
+                                   dict(m1=120, e1=8, e2=100, n_layers=1, m2=8)])
+def test_fused_padded_widths_vs_oracle(shape):
+    """Embedding and attention widths below the tile width (padded inside the
+    packed tiles) on the 300-atom water box, every atom against the oracle."""
+    m, s = replace(C.ATTN_MODEL, **shape), serving_system(300, 4)
+    pot, w = make(m, s, dp.PREC_FUSED)
+    E, F, V = pot.compute(s.coords)
+    Eo, aeo, Fo, Vo = oracle.af_compute(m, w, s.types, s.coords, s.box)
+    assert abs(E - Eo) <= TOL_E[dp.PREC_FUSED] * abs(Eo)
+    assert np.max(np.abs(F - Fo)) <= TOL_F[dp.PREC_FUSED] * frms(Fo)
+    assert np.max(np.abs(V - Vo)) <= TOL_F[dp.PREC_FUSED] * np.linalg.norm(Vo)
 
 
 def test_fused_md_tracks_plain():
