@@ -1,7 +1,8 @@
 """Continuous batching (dp_server): a system's trajectory is the same alone and
 in a mix (bitwise: per-atom work and per-system reductions do not depend on the
 batch), equals the single-system dp_step path, admission respects the memory
-capacity, and requests that arrive while others run are admitted at once."""
+capacity, requests that arrive while others run are admitted at once, and the
+served energies, forces and trajectories agree with the FP64 oracle."""
 from dataclasses import replace
 
 import numpy as np
@@ -117,3 +118,55 @@ def test_late_arrival_overlaps_running_work():
     srv.close()
     assert out["b"][3]["tick_admitted"] < out["a"][3]["tick_done"]
     assert out["b"][3]["tick_done"] < out["a"][3]["tick_done"]
+
+
+def test_served_systems_match_the_oracle():
+    """Served results against the FP64 oracle, not only against other GPU runs.
+
+    Four uneven systems (96 to 1,200 atoms; the 96-atom box is smaller than
+    2 rc) share the batch, admitted at different ticks.  The integration is
+    FP64, so a one-step request returns the forces it used: the first drift
+    gives F(x0) = (x1 - x0 - dt v0) 2 m / (dt^2 kappa) and the closing kick
+    F(x1) = 2 m (v1 - v0) / (dt kappa) - F(x0).  Both are held to the fused
+    bound (2e-2 of the oracle's force RMS) and the energy of the step to 1e-3.
+    Four-step requests are compared with the oracle's own velocity-Verlet
+    run: per-step energies within 1e-3, and positions within the drift that a
+    force error at the bound can cause, n^2 dt^2 kappa / m_min times it."""
+    m, w, ms = M, weights(), masses()
+    kappa = oracle.KAPPA
+    dt = C.DT_FS
+    systems = [serving_system(96, 41), serving_system(320, 42), serving_system(700, 43),
+               serving_system(1200, 44)]
+    steps = [1, 4, 1, 4]
+    v0 = [vel(s, 50 + k) for k, s in enumerate(systems)]
+    srv = server(max_slots=8)
+    ids = {}
+    for k in (0, 3):
+        ids[k] = srv.submit(systems[k].types, systems[k].box, systems[k].coords, v0[k], steps[k])
+    srv.tick()
+    for k in (1, 2):
+        ids[k] = srv.submit(systems[k].types, systems[k].box, systems[k].coords, v0[k], steps[k])
+    out = run_to_end(srv, ids)
+    srv.close()
+    for k, s in enumerate(systems):
+        x, v, e, _ = out[k]
+        mass = ms[s.types][:, None]
+        _, _, F0o, _ = oracle.af_compute(m, w, s.types, s.coords, s.box)
+        fr = frms(F0o)
+        if steps[k] == 1:
+            F0 = (x - s.coords - dt * v0[k]) * 2.0 * mass / (dt * dt * kappa)
+            assert np.max(np.abs(F0 - F0o)) <= 2e-2 * fr, k
+            E1o, _, F1o, _ = oracle.af_compute(m, w, s.types, x, s.box)
+            F1 = 2.0 * mass * (v - v0[k]) / (dt * kappa) - F0
+            assert np.max(np.abs(F1 - F1o)) <= 2e-2 * frms(F1o), k
+            assert abs(e[0, 0] - E1o) <= 1e-3 * abs(E1o), k
+        else:
+            n = steps[k]
+            xo, vo, epo, eko = oracle.af_md(m, w, s.types, ms, s.coords, v0[k], s.box, n, dt)
+            assert np.all(np.abs(e[:, 0] - epo) <= 1e-3 * np.abs(epo)), k
+            bound = n * n * dt * dt * kappa / np.min(ms[s.types]) * 2e-2 * fr
+            assert np.max(np.abs(x - xo)) <= bound, (k, np.max(np.abs(x - xo)), bound)
+
+
+def frms(F):
+    return float(np.sqrt(np.mean(F ** 2)))
