@@ -42,11 +42,44 @@ GRAPH_WORKLOAD = ("protein-in-water 24,000 atoms (same system), graph family: no
                   "rc 6 A, nmax 120; NVE dt 0.5 fs, rebuild every 10")
 METRIC = "energy+force atom-steps/s"
 FP32_ALU_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # 148 SMs x 128 FP32 lanes x FMA x 2.032 GHz
-# DRAM bytes (read + write) per atom of one launch, from the ncu captures of the
-# 4,800-atom case (profiles/k_af_*_small_ncu.md); traffic grows with the atoms
-# processed (per-atom tiles, lists, gradients), so a launch over N atoms moves N x this
+# DRAM bytes (read + write) per atom of one launch, from an ncu capture of the
+# 4,800-atom case (`--system small`); traffic grows with the atoms processed
+# (per-atom tiles, lists, gradients), so a launch over N atoms moves N x this.
+# These are not measured by this program: they hold for the kernel source whose
+# SHA-256 prefix is recorded beside them, and the line reports null otherwise.
 NCU_TRAFFIC_PER_ATOM = {"k_af_bwd": (545.673728e6 + 9.578496e6) / 4800,
                         "k_af_fwd": (13.900800e6 + 452.975104e6) / 4800}
+NCU_TRAFFIC_SOURCE = ("paper_2602_02234_b300/csrc/fused_af.cu", "e855c4b2149e3a3f")
+
+
+def _source_sha(rel):
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            return hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+
+
+def traffic_per_atom(kernel):
+    """The captured DRAM bytes per atom of `kernel`, or None when the kernel's
+    source has changed since the capture."""
+    rel, sha = NCU_TRAFFIC_SOURCE
+    if kernel not in NCU_TRAFFIC_PER_ATOM or not sha or _source_sha(rel) != sha:
+        return None
+    return NCU_TRAFFIC_PER_ATOM[kernel]
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or "unknown"
 
 
 def peaks():
@@ -181,30 +214,41 @@ def run_reference(args, rank, world):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_atoms": s.n},
             "cpu_baseline": {"value": value, "unit": "atom-steps/s", "cores": threads,
-                             "kind": "oracle", "sample": sample},
+                             "kind": "oracle", "sample": sample, "nproc": os.cpu_count(),
+                             "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": "atom-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def cpu_baseline(seconds=12.0):
-    """The oracle as it stands, timed on this host over a bounded random sample."""
+def cpu_baseline(seconds=12.0, seconds_1thread=6.0):
+    """The oracle as it stands, timed on this host over a bounded random
+    sample: OpenMP over every host core, then on one thread."""
     import oracle
     s, model, _, _ = setup_system()
     w = normal_blob(oracle.af_weight_count(model), CF.WEIGHT_SEED)
     rng = np.random.default_rng(1)
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    batch = max(8, threads * 4)
-    done = 0
-    t0 = time.perf_counter()
-    while time.perf_counter() - t0 < seconds:
-        oracle.af_atoms(model, w, s.types, s.coords, s.box, rng.choice(s.n, batch, replace=False))
-        done += batch
-    dt = time.perf_counter() - t0
+
+    def rate(nthreads, batch, budget):
+        done = 0
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < budget:
+            oracle.af_atoms(model, w, s.types, s.coords, s.box,
+                            rng.choice(s.n, batch, replace=False), nthreads)
+            done += batch
+        dt = time.perf_counter() - t0
+        return done, dt
+
+    done, dt = rate(threads, max(8, threads * 4), seconds)
+    done1, dt1 = rate(1, 2, seconds_1thread)
     return {"value": done / dt, "unit": "atom-steps/s", "cores": threads, "kind": "oracle",
             "sample": f"{done} random centre atoms of the 24,000-atom system in {dt:.1f} s "
-                      f"(energy + pair gradients per atom, FP64, OpenMP)"}
+                      f"(energy + pair gradients per atom, FP64, OpenMP)",
+            "value_1thread": done1 / dt1,
+            "sample_1thread": f"{done1} random centre atoms on one thread in {dt1:.1f} s",
+            "nproc": os.cpu_count(), "cpu_model": cpu_model()}
 
 
 # ------------------------------------------------------------------ serving
@@ -353,10 +397,12 @@ def run_ours(args, rank, world, local_rank):
         dominant = max(kernel_ms, key=kernel_ms.get)
         flops = float(parts[{"k_af_fwd": 0, "k_fit": 1, "k_af_bwd": 2}[dominant]])
         net_ms = kernel_ms[dominant]
-        peak = pk.get("bf16_tflops_sustained", 1400.0)
+        # each kernel is timed alone (a few back-to-back launches, well under a
+        # second), so the burst peak is the one that applies
+        peak = pk.get("bf16_tflops", 1800.0)
         bound = "tensor"
-        peak_note = (f"dense 16-bit tensor peak sustained ({pk_kind}; the FP16 rate equals the "
-                     "measured BF16 rate, nominal ratio 1)")
+        peak_note = (f"dense 16-bit tensor peak, burst ({pk_kind}; the kernel is timed alone; "
+                     "the FP16 rate equals the measured BF16 rate, nominal ratio 1)")
         kernel_name = dominant
     else:
         net_ms = time_network(0)
@@ -369,11 +415,13 @@ def run_ours(args, rank, world, local_rank):
         achieved = flops / (net_ms / 1e3) / 1e12
         if args.message_passing:   # every network part is several launches plus cross-atom steps
             kernel_name += " (message passing: one launch per layer)"
-        traffic = NCU_TRAFFIC_PER_ATOM.get(kernel_name)
+        traffic = traffic_per_atom(kernel_name)
         roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak,
-                    "traffic": traffic * s.n if traffic and args.system == "protein24k" else None,
-                    "traffic_note": "DRAM bytes per launch, scaled from the 4,800-atom ncu capture",
+                    "traffic": traffic * s.n if traffic else None,
+                    "traffic_note": "not measured by this run: DRAM bytes per atom from an ncu "
+                                    "capture of the same kernel source on 4,800 atoms, times "
+                                    "the atoms of one launch (null when the source differs)",
                     "kernel": kernel_name,
                     "peak_kind": peak_note, "algorithmic_flop_per_launch": flops,
                     "launch_ms": net_ms, "kernel_ms": kernel_ms}
@@ -415,6 +463,28 @@ def run_ours(args, rank, world, local_rank):
                       "ms_per_step": results[name]["ms"] / K}
     if fused_name in results and "plain_f32" in results:
         line["fused_vs_plain"] = results["plain_f32"]["ms"] / results[fused_name]["ms"]
+        if not graph:
+            # the comparison arm's own roofline: its network phase (all plain
+            # kernels of one evaluation) against the derived FP32 FFMA peak
+            ppot = results["plain_f32"]["pot"]
+            ppot.enqueue_network(1, 0)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                ppot.enqueue_network(2, 0)
+                e1.record(stream)
+            e1.synchronize()
+            pms = e0.elapsed_time(e1) / 2
+            pflops = float(parts.sum())
+            line["plain_f32"]["roofline"] = {
+                "bound": "alu", "achieved": pflops / (pms / 1e3) / 1e12,
+                "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": pflops / (pms / 1e3) / 1e12 / FP32_ALU_PEAK_TFLOPS,
+                "kernel": "plain network phase (all kernels of one evaluation)",
+                "peak_kind": "FP32 FFMA: 148 SMs x 128 lanes x 2 x 2.032 GHz (derived)",
+                "algorithmic_flop_per_launch": pflops, "launch_ms": pms}
     plain_model = not args.message_passing and not graph
     if rank == 0 and args.serving > 0 and args.system == "protein24k" and plain_model:
         line["serving"] = serving_bench(args.serving)
@@ -469,7 +539,7 @@ def report_config(which):
     import paper_2602_02234_b300 as dp
     stream = torch.cuda.Stream()
     out = {"config": which}
-    if which == 1:      # 64 waters, plain FP64 / FP32 against the oracle, 100 NVE steps
+    if which == 1:      # 64 waters, FP64 / FP32 / fused against the oracle, 100 NVE steps
         m, s = CF.WATER64_MODEL, CF.water64()
         w = normal_blob(oracle.af_weight_count(m), CF.WEIGHT_SEED)
         masses = s.masses
@@ -479,7 +549,8 @@ def report_config(which):
         xo, vo, epo, eko = oracle.af_md(m, w, s.types, masses, s.coords, v0, s.box, 100, CF.DT_FS)
         out["oracle_md_atom_steps_per_s"] = s.n * 100 / (time.perf_counter() - t0)
         out["oracle_drift"] = _drift(np.stack([epo, eko], 1), s.n, CF.DT_FS)
-        for name, prec in (("plain_f64", dp.PREC_PLAIN_F64), ("plain_f32", dp.PREC_PLAIN_F32)):
+        for name, prec in (("plain_f64", dp.PREC_PLAIN_F64), ("plain_f32", dp.PREC_PLAIN_F32),
+                           ("fused_f16", dp.PREC_FUSED)):
             pot = dp.DeepPotential(dp.model_desc(m, prec), s.types, s.box, w, masses=masses,
                                    stream=stream)
             E, F, V = pot.compute(s.coords)
@@ -661,7 +732,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=48)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serving", type=int, default=48,
+    ap.add_argument("--serving", type=int, default=256,
                     help="requests in the continuous-batching measurement (0: skip)")
     ap.add_argument("--system", choices=["protein24k", "small"], default="protein24k",
                     help="small: 4,800-atom box of the same recipe, for profiler captures")
