@@ -658,12 +658,12 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
   const bool valid = m->tj[r] >= 0;
   const float2 rj[3] = {make_float2(m->cl[1][r], m->cl[1][r]), make_float2(m->cl[2][r], m->cl[2][r]),
                         make_float2(m->cl[3][r], m->cl[3][r])};
-  const int jr = MP && r < p.nmax ? p.sel_j[(size_t)atom * p.nmax + r] : -1;
   const int l_end = MP ? p.le : p.n_layers;
   for (int l = MP ? p.lb : 0; l < l_end; ++l) {
     if constexpr (MP) {
       // message: G' = G + U of the slot's neighbour, into R2 (FP32) and the G
       // tile (16-bit, also kept for the backward's recomputation)
+      const int jr = r < p.nmax ? p.sel_j[(size_t)atom * p.nmax + r] : -1;
       const float* u = p.U + ((size_t)l * p.cap + (jr >= 0 ? jr : 0)) * kW;
       for (int c = 32 * pt; c < kW; c += kStride) {
         float g[32];
@@ -1023,9 +1023,13 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
       issue_copy(xb, sm + SM_K, p.WkT + (size_t)l * kTile, kTile, 0);
     }
     // the layer's softmax normalisers (one per head), needed by the heads below
+    // (with message passing read per head, which keeps the variant's live
+    // state within its registers)
     float beta4[4];
+    if constexpr (!MP) {
 #pragma unroll
-    for (int h = 0; h < 4; ++h) beta4[h] = p.smx[(((size_t)atom * L + l) * 4 + h) * kW + r];
+      for (int h = 0; h < 4; ++h) beta4[h] = p.smx[(((size_t)atom * L + l) * 4 + h) * kW + r];
+    }
     if (ngroups > 0 && !gb.wait(p.status)) return false;
     if (MP && l + 1 < L) {
       // adjoint of h^{l+1} = h^l + (1/Nmax) sum_r sw_r G_{l+1}[r]: dG_{l+1}[r] +=
@@ -1127,7 +1131,8 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
               mma_issue(tb + R3, kop(sm + SM_Q, kW), kop(sm + SM_K, kW), kW, DH, false));
     for (int h = 0; h < p.heads; ++h) {
       const int c0 = h * DH;
-      const float st = h == 0 ? beta4[0] : h == 1 ? beta4[1] : h == 2 ? beta4[2] : beta4[3];
+      const float st = MP ? p.smx[(((size_t)atom * L + l) * 4 + h) * kW + r]
+                          : h == 0 ? beta4[0] : h == 1 ? beta4[1] : h == 2 ? beta4[2] : beta4[3];
       // w (kept in R3 for the adjoint below) and A = w * gate -> G tile
       for (int c = 32 * pt; c < kW; c += kStride) {
         float v[32];
