@@ -288,6 +288,15 @@ const char* dp_server_last_error(const dp_server* srv);
 int dp_selftest_mma(int n, int k, int a_mn, int b_mn, int swap, const float* A, const float* B,
                     float* D);
 
+/* Diagnostics (no paper counterpart): SM cycles per tensor-core product of
+ * 128 x n x 16 (16-bit operands from shared memory, FP32 accumulation in
+ * tensor memory), measured on one CTA over `reps` groups of 64 products issued
+ * by `issuers` threads (1..8) and waited for after each group.  16 <= n <=
+ * 128, a multiple of 16; 1 <= reps <= 100000.  Allocates its own buffers.
+ * Returns DP_ERR_ARG for other sizes, DP_ERR_TIMEOUT if a group never
+ * completed (bounded wait). */
+int dp_selftest_mma_rate(int n, int issuers, int reps, double* cycles_per_mma);
+
 /* Diagnostics (no paper counterpart): the bounded device-side wait of the
  * fused kernels, on an mbarrier that is never completed, polled at most
  * max_polls (1..2^20) times.  Returns DP_ERR_TIMEOUT when the wait ran out and

@@ -126,6 +126,7 @@ def lib():
         L.dp_noalloc_last_error.restype = C.c_char_p
         L.dp_selftest_mma.argtypes = [i, i, i, i, i, vp, vp, vp]
         L.dp_selftest_timeout.argtypes = [C.c_longlong]
+        L.dp_selftest_mma_rate.argtypes = [i, i, i, C.POINTER(C.c_double)]
         L.dp_server_create.argtypes = [C.POINTER(vp), C.POINTER(ModelDesc), vp, vp, C.c_size_t, i,
                                        C.c_longlong, C.c_size_t, d, vp]
         L.dp_server_capacity.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -445,6 +446,15 @@ def selftest_mma(A, B, a_mn=0, b_mn=0, swap=0):
     if rc:
         raise DPError(rc, "selftest_mma")
     return D
+
+
+def selftest_mma_rate(n, issuers=1, reps=200):
+    """``dp_selftest_mma_rate``: SM cycles per 128 x n x 16 tensor-core product."""
+    out = C.c_double()
+    rc = lib().dp_selftest_mma_rate(int(n), int(issuers), int(reps), C.byref(out))
+    if rc:
+        raise DPError(rc, "selftest_mma_rate")
+    return out.value
 
 
 def _dpenergy_class():

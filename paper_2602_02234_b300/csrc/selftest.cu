@@ -160,3 +160,94 @@ extern "C" int dp_selftest_timeout(long long max_polls) {
   if (e != cudaSuccess) return DP_ERR_CUDA;
   return (st & dp::kFlagTimeout) ? DP_ERR_TIMEOUT : DP_OK;
 }
+
+// Issue-to-completion cost of 128 x N x 16 tensor-core products from shared
+// memory: `reps` groups of 64 products (8 chains of K = 128 into four
+// 128-column accumulators), issued by `issuers` threads (lane 0 of warps
+// 0 .. issuers-1, each committing its own share), each group waited for.
+// Thread 0's clock64 over all groups, divided by the products.
+constexpr int kRateTile = 128 * 128 * 2;
+
+__global__ void __launch_bounds__(512) k_selftest_mma_rate(int N, int issuers, int reps,
+                                                           unsigned long long* cycles,
+                                                           int* status) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ uint32_t tptr;
+  __shared__ __align__(8) uint64_t bar;
+  const int t = threadIdx.x, warp = t >> 5;
+  for (int i = t; i < 2 * kRateTile / 16; i += blockDim.x)
+    reinterpret_cast<int4*>(sm)[i] = make_int4(0, 0, 0, 0);
+  if (t == 0) {
+    dp::tc::mbar_init(&bar, (uint32_t)issuers);
+    dp::tc::fence_mbar_init();
+  }
+  if (warp == 0) {
+    dp::tc::tmem_alloc(&tptr, 512);
+    dp::tc::tmem_relinquish();
+  }
+  dp::tc::fence_async_smem();
+  dp::tc::fence_before_sync();
+  __syncthreads();
+  dp::tc::fence_after_sync();
+  const uint32_t tb = tptr;
+  const uint32_t a = dp::tc::smem_u32(sm), b = dp::tc::smem_u32(sm + kRateTile);
+  const uint32_t idesc = dp::tc::idesc_bf16(128, N, 0, 0);
+  // K-major 128 x 128 tiles: a K step of 16 is two core matrices (256 bytes)
+  const uint64_t da0 = dp::tc::make_desc(a, 128u, 16u * 128u);
+  const uint64_t db0 = dp::tc::make_desc(b, 128u, 16u * 128u);
+  bool ok = true;
+  uint32_t phase = 0;
+  const unsigned long long t0 = clock64();
+  for (int r = 0; r < reps; ++r) {
+    if ((t & 31) == 0 && warp < issuers) {
+      for (int g = warp; g < 8; g += issuers)
+        for (int ks = 0; ks < 8; ++ks)
+          dp::tc::mma_bf16(tb + (uint32_t)((g & 3) * 128), da0 + 16u * ks, db0 + 16u * ks, idesc,
+                           ks > 0 ? 1u : 0u);
+      dp::tc::mma_commit(&bar);
+    }
+    if (t == 0) ok = ok && dp::tc::mbar_wait(&bar, phase & 1u, 1LL << 22);
+    phase ^= 1u;
+    ok = __syncthreads_and(ok) != 0;
+    dp::tc::fence_after_sync();
+    if (!ok) break;
+  }
+  if (t == 0) {
+    *cycles = clock64() - t0;
+    if (!ok) atomicOr(status, dp::kFlagTimeout);
+  }
+  dp::tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) dp::tc::tmem_dealloc(tb, 512);
+}
+
+extern "C" int dp_selftest_mma_rate(int n, int issuers, int reps, double* cycles_per_mma) {
+  if (n < 16 || n > 128 || n % 16 || issuers < 1 || issuers > 8 || reps < 1 || reps > 100000 ||
+      !cycles_per_mma)
+    return DP_ERR_ARG;
+  unsigned long long* dc = nullptr;
+  int* ds = nullptr;
+  if (cudaMalloc(&dc, sizeof(unsigned long long)) != cudaSuccess) return DP_ERR_OOM;
+  if (cudaMalloc(&ds, sizeof(int)) != cudaSuccess) {
+    cudaFree(dc);
+    return DP_ERR_OOM;
+  }
+  cudaMemset(ds, 0, sizeof(int));
+  cudaFuncSetAttribute(k_selftest_mma_rate, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       2 * kRateTile);
+  unsigned long long c = 0;
+  int st = 0;
+  cudaError_t e = cudaSuccess;
+  for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {   // the first pass warms up
+    k_selftest_mma_rate<<<1, 512, 2 * kRateTile>>>(n, issuers, reps, dc, ds);
+    e = cudaDeviceSynchronize();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(&c, dc, sizeof(c), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&st, ds, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(dc);
+  cudaFree(ds);
+  if (e != cudaSuccess) return DP_ERR_CUDA;
+  if (st & dp::kFlagTimeout) return DP_ERR_TIMEOUT;
+  *cycles_per_mma = (double)c / ((double)reps * 64.0);
+  return DP_OK;
+}

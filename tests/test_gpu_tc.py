@@ -41,3 +41,20 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     A = bf16(np.ones((128, 16)))
     B = bf16(np.ones((16, 16)))
     assert np.allclose(dp.selftest_mma(A, B), 16.0)
+
+
+def test_product_rate_self_test():
+    """dp_selftest_mma_rate: a 128 x n x 16 product costs at least the
+    tensor-core time of its n columns, and wider products never cost less
+    than narrower ones (one or four issuing threads)."""
+    r16 = dp.selftest_mma_rate(16)
+    r32 = dp.selftest_mma_rate(32)
+    r128 = dp.selftest_mma_rate(128)
+    r32x4 = dp.selftest_mma_rate(32, issuers=4)
+    for r in (r16, r32, r128, r32x4):
+        assert np.isfinite(r) and r > 0
+    assert r128 >= r16
+    # 128 x 128 x 16 is 2^18 multiply-adds; no SM does more than 8,192 per cycle
+    assert r128 >= 32.0
+    with pytest.raises(dp.DPError):
+        dp.selftest_mma_rate(24)
