@@ -168,5 +168,33 @@ def test_served_systems_match_the_oracle():
             assert np.max(np.abs(x - xo)) <= bound, (k, np.max(np.abs(x - xo)), bound)
 
 
+def test_served_message_passing_forces_match_the_oracle():
+    """The model with cross-atom messages in a mixed batch: one-step requests
+    return the forces they used (FP64 integration), held to the fused bound
+    against the whole-system message-passing oracle; the step's energy to the
+    2e-3 that the extra 16-bit rounding of the messages allows."""
+    m, w, ms = M_MP, weights(M_MP), masses()
+    kappa, dt = oracle.KAPPA, C.DT_FS
+    systems = [serving_system(96, 61), serving_system(700, 62), serving_system(320, 63)]
+    v0 = [vel(s, 70 + k) for k, s in enumerate(systems)]
+    srv = server(M_MP, max_slots=4)
+    ids = {0: srv.submit(systems[0].types, systems[0].box, systems[0].coords, v0[0], 1)}
+    srv.tick()
+    for k in (1, 2):
+        ids[k] = srv.submit(systems[k].types, systems[k].box, systems[k].coords, v0[k], 1)
+    out = run_to_end(srv, ids)
+    srv.close()
+    for k, s in enumerate(systems):
+        x, v, e, _ = out[k]
+        mass = ms[s.types][:, None]
+        _, _, F0o, _ = oracle.af_compute(m, w, s.types, s.coords, s.box)
+        F0 = (x - s.coords - dt * v0[k]) * 2.0 * mass / (dt * dt * kappa)
+        assert np.max(np.abs(F0 - F0o)) <= 2e-2 * frms(F0o), k
+        E1o, _, F1o, _ = oracle.af_compute(m, w, s.types, x, s.box)
+        F1 = 2.0 * mass * (v - v0[k]) / (dt * kappa) - F0
+        assert np.max(np.abs(F1 - F1o)) <= 2e-2 * frms(F1o), k
+        assert abs(e[0, 0] - E1o) <= 2e-3 * abs(E1o), k
+
+
 def frms(F):
     return float(np.sqrt(np.mean(F ** 2)))
