@@ -166,3 +166,21 @@ def test_gf_pair_beyond_cutoff():
     d = [abs(oracle.gf_compute(m, w, t, np.array([[20.0, 20, 20], [26.0 - h, 20, 20]]), box)[0] - alone)
          for h in (0.4, 0.2)]
     assert d[0] > 0 and d[1] / d[0] < 0.15
+
+
+def test_stored_24k_result_is_current_and_consistent():
+    """The stored whole-system oracle result at 24,000 atoms (the expected
+    value of the full-size graph-family GPU test) belongs to the current
+    generators and weights (input digest), and obeys the model's invariants:
+    zero net force and a symmetric virial."""
+    import json
+    from tests.golden import make_gf_protein24k as g
+    m, s, w = g.inputs()
+    with open(g.OUT) as f:
+        ref = json.load(f)
+    assert ref["inputs_sha256"] == g.digest(s, w)
+    assert len(ref["sample"]) >= 200 and len(ref["forces"]) == len(ref["sample"])
+    V = np.array(ref["virial"])
+    assert np.max(np.abs(V - V.T)) <= 1e-9 * np.linalg.norm(V)
+    assert np.max(np.abs(ref["net_force"])) <= 1e-9 * ref["force_rms"] * np.sqrt(s.n)
+    assert np.array_equal(np.array(ref["sample"]), g.sample(s, m))
