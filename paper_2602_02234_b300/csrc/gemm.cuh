@@ -1,6 +1,10 @@
 // Generic batched SIMT GEMM used by the plain (unfused) FP32 / FP64 paths.
 #pragma once
 
+#include <stdint.h>
+
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace dp {
@@ -110,9 +114,137 @@ __global__ void __launch_bounds__(256) k_gemm(Gemm<T> g, long long batch) {
   }
 }
 
+// =========================================================================
+// FP32 fast path for one (unbatched) product with row-major A (unit column
+// stride), row-major B (K x N, unit column stride) and row-major C: 128 x 128
+// tiles, 8-deep K slices, 8 x 8 outputs per thread from two 4-wide fragments
+// in each direction, the next slice's float4 loads in registers while the
+// current one is multiplied out of the other shared buffer.  Same result
+// definition as k_gemm (sums in increasing k per output), same epilogues.
+// =========================================================================
+constexpr int kSgBM = 128, kSgBN = 128, kSgBK = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sgemm128(Gemm<T> g) {
+  static_assert(std::is_same<T, float>::value, "FP32 only");
+  __shared__ __align__(16) float As[2][kSgBK][kSgBM];
+  __shared__ __align__(16) float Bs[2][kSgBK][kSgBN];
+  const int tiles_n = (g.N + kSgBN - 1) / kSgBN;
+  const int tm = blockIdx.x / tiles_n, tn = blockIdx.x - tm * tiles_n;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  // loads: A slice 128 x 8 (thread: row tid >> 1, columns 4 (tid & 1) .. +3),
+  // B slice 8 x 128 (thread: row tid >> 5, columns 4 (tid & 31) .. +3)
+  const int am = tid >> 1, ak = (tid & 1) << 2;
+  const int bk = tid >> 5, bn = (tid & 31) << 2;
+  const long long m_ld = (long long)tm * kSgBM + am;
+  const long long arow = m_ld < g.M ? (g.a_rows ? (long long)g.a_rows[m_ld] : m_ld) : -1;
+  const float* Ap = arow >= 0 ? g.A + arow * g.a_rm : nullptr;
+  const int n_ld = tn * kSgBN + bn;
+  auto load_a = [&](int k0) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int k = k0 + ak;
+    if (Ap) {
+      if (k + 3 < g.K) {
+        v = *reinterpret_cast<const float4*>(Ap + k);
+      } else {
+        if (k < g.K) v.x = Ap[k];
+        if (k + 1 < g.K) v.y = Ap[k + 1];
+        if (k + 2 < g.K) v.z = Ap[k + 2];
+      }
+    }
+    return v;
+  };
+  auto load_b = [&](int k0) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int k = k0 + bk;
+    if (k < g.K && n_ld < g.N) v = *reinterpret_cast<const float4*>(g.B + (long long)k * g.b_rk + n_ld);
+    return v;
+  };
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  float4 ra = load_a(0), rb = load_b(0);
+  int buf = 0;
+  As[0][ak][am] = ra.x; As[0][ak + 1][am] = ra.y; As[0][ak + 2][am] = ra.z; As[0][ak + 3][am] = ra.w;
+  *reinterpret_cast<float4*>(&Bs[0][bk][bn]) = rb;
+  __syncthreads();
+  for (int k0 = 0; k0 < g.K; k0 += kSgBK) {
+    const bool more = k0 + kSgBK < g.K;
+    if (more) {
+      ra = load_a(k0 + kSgBK);
+      rb = load_b(k0 + kSgBK);
+    }
+#pragma unroll
+    for (int kk = 0; kk < kSgBK; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][4 * ty]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][4 * ty + 64]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][4 * tx]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][4 * tx + 64]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    if (more) {
+      buf ^= 1;
+      As[buf][ak][am] = ra.x; As[buf][ak + 1][am] = ra.y; As[buf][ak + 2][am] = ra.z;
+      As[buf][ak + 3][am] = ra.w;
+      *reinterpret_cast<float4*>(&Bs[buf][bk][bn]) = rb;
+      __syncthreads();
+    }
+  }
+  // outputs: rows 4 ty + i (i < 4) and 64 + 4 ty + i - 4, columns likewise
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const long long m = (long long)tm * kSgBM + (i < 4 ? 4 * ty + i : 64 + 4 * ty + i - 4);
+    if (m >= g.M) continue;
+    const long long row = g.c_rows ? (long long)g.c_rows[m] : m;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int n = tn * kSgBN + (j < 4 ? 4 * tx + j : 64 + 4 * tx + j - 4);
+      if (n >= g.N) continue;
+      const long long o = row * g.c_rm + n;
+      float v = g.alpha * acc[i][j];
+      if (g.bias) v += g.bias[n];
+      if (g.beta != 0.f) v += g.beta * g.C[o];
+      if (g.epi == 1) v = tanhf(v);
+      else if (g.epi == 2) {
+        const float y = g.aux[o];
+        v *= 1.f - y * y;
+      }
+      g.C[o] = v;
+    }
+  }
+}
+
+template <typename T>
+inline bool sgemm128_ok(const Gemm<T>& g, long long batch) {
+  if constexpr (!std::is_same<T, float>::value) {
+    return false;
+  } else {
+    auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+    return batch == 1 && g.a_rk == 1 && g.b_rn == 1 && g.c_rn == 1 && g.a_rm % 4 == 0 &&
+           g.b_rk % 4 == 0 && g.N % 4 == 0 && al16(g.A) && al16(g.B) && g.M >= kSgBM &&
+           g.K >= kSgBK && g.N >= 96;   // narrower products keep the 64 x 64 tiles
+  }
+}
+
 template <typename T>
 inline void gemm(const Gemm<T>& g, long long batch, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0 || batch <= 0) return;
+  if constexpr (std::is_same<T, float>::value) {
+    if (sgemm128_ok(g, batch)) {
+      const long long tiles = ((long long)(g.M + kSgBM - 1) / kSgBM) * ((g.N + kSgBN - 1) / kSgBN);
+      if (tiles <= 0x7fffffffLL) {
+        k_sgemm128<float><<<(unsigned)tiles, 256, 0, st>>>(g);
+        return;
+      }
+    }
+  }
   int tiles = ((g.M + 63) / 64) * ((g.N + 63) / 64);
   long long by = batch < 65535 ? batch : 65535;
   long long bz = (batch + by - 1) / by;
