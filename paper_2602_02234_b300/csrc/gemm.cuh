@@ -3,6 +3,7 @@
 
 #include <stdint.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "common.cuh"
@@ -221,6 +222,102 @@ __global__ void __launch_bounds__(256) k_sgemm128(Gemm<T> g) {
   }
 }
 
+// =========================================================================
+// FP32 batched small products (M, N <= 128, any K, any element strides, no
+// row gather): one CTA of 256 threads per batch item (persistent over items),
+// 32-deep K slices staged in shared memory in k-major order (each operand
+// read along whichever of its strides is 1), and a register tile of 8 rows x
+// TN columns per thread (rows 4 ty .. + 3 and 64 + 4 ty .. + 3; columns
+// likewise for TN = 8, 2 tx .. + 1 for TN = 2).  Sums in increasing k.
+// =========================================================================
+constexpr int kBgK = 32, kBgLd = 132;
+
+template <int TN>
+__global__ void __launch_bounds__(256, 2) k_bgemm_small(Gemm<float> g, long long batch) {
+  __shared__ __align__(16) float As[kBgK][kBgLd];
+  __shared__ __align__(16) float Bs[kBgK][kBgLd];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (long long b = blockIdx.x; b < batch; b += gridDim.x) {
+    const long long b1 = b / g.nb2, b2 = b - b1 * g.nb2;
+    const float* A = g.A + b1 * g.a_b1 + b2 * g.a_b2;
+    const float* B = g.B + b1 * g.b_b1 + b2 * g.b_b2;
+    float* C = g.C + b1 * g.c_b1 + b2 * g.c_b2;
+    float acc[8][TN];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+    for (int k0 = 0; k0 < g.K; k0 += kBgK) {
+      __syncthreads();   // the previous slice (or item) has been read
+      // A(m, k) -> As[k - k0][m]; rows beyond M and k beyond K are zero
+      if (g.a_rk == 1) {
+        for (int i = tid; i < 128 * kBgK; i += 256) {
+          const int m = i >> 5, kk = i & 31, k = k0 + kk;
+          As[kk][m] = (m < g.M && k < g.K) ? A[(long long)m * g.a_rm + k] : 0.f;
+        }
+      } else {
+        for (int i = tid; i < 128 * kBgK; i += 256) {
+          const int kk = i >> 7, m = i & 127, k = k0 + kk;
+          As[kk][m] = (m < g.M && k < g.K) ? A[(long long)m * g.a_rm + (long long)k * g.a_rk] : 0.f;
+        }
+      }
+      // B(k, n) -> Bs[k - k0][n]
+      if (g.b_rk == 1) {
+        for (int i = tid; i < 128 * kBgK; i += 256) {
+          const int n = i >> 5, kk = i & 31, k = k0 + kk;
+          Bs[kk][n] = (n < g.N && k < g.K) ? B[(long long)n * g.b_rn + k] : 0.f;
+        }
+      } else {
+        for (int i = tid; i < 128 * kBgK; i += 256) {
+          const int kk = i >> 7, n = i & 127, k = k0 + kk;
+          Bs[kk][n] = (n < g.N && k < g.K) ? B[(long long)k * g.b_rk + (long long)n * g.b_rn] : 0.f;
+        }
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int kk = 0; kk < kBgK; ++kk) {
+        const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][4 * ty]);
+        const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][64 + 4 * ty]);
+        const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        float bv[TN];
+        if constexpr (TN == 8) {
+          const float4 c0 = *reinterpret_cast<const float4*>(&Bs[kk][4 * tx]);
+          const float4 c1 = *reinterpret_cast<const float4*>(&Bs[kk][64 + 4 * tx]);
+          bv[0] = c0.x; bv[1] = c0.y; bv[2] = c0.z; bv[3] = c0.w;
+          bv[4] = c1.x; bv[5] = c1.y; bv[6] = c1.z; bv[7] = c1.w;
+        } else {
+          const float2 c0 = *reinterpret_cast<const float2*>(&Bs[kk][2 * tx]);
+          bv[0] = c0.x; bv[1] = c0.y;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], bv[j], acc[i][j]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int m = i < 4 ? 4 * ty + i : 64 + 4 * ty + i - 4;
+      if (m >= g.M) continue;
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const int n = TN == 8 ? (j < 4 ? 4 * tx + j : 64 + 4 * tx + j - 4) : 2 * tx + j;
+        if (n >= g.N) continue;
+        const long long o = (long long)m * g.c_rm + (long long)n * g.c_rn;
+        float v = g.alpha * acc[i][j];
+        if (g.bias) v += g.bias[n];
+        if (g.beta != 0.f) v += g.beta * C[o];
+        if (g.epi == 1) v = tanhf(v);
+        else if (g.epi == 2) {
+          const float y = g.aux[b1 * g.c_b1 + b2 * g.c_b2 + o];
+          v *= 1.f - y * y;
+        }
+        C[o] = v;
+      }
+    }
+  }
+}
+
 template <typename T>
 inline bool sgemm128_ok(const Gemm<T>& g, long long batch) {
   if constexpr (!std::is_same<T, float>::value) {
@@ -237,6 +334,19 @@ template <typename T>
 inline void gemm(const Gemm<T>& g, long long batch, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0 || batch <= 0) return;
   if constexpr (std::is_same<T, float>::value) {
+    if (batch > 1 && g.M <= 128 && g.N <= 128 && !g.a_rows && !g.c_rows) {
+      static int sms = 0;
+      if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 148;
+      }
+      const long long grid = std::min<long long>(batch, (long long)sms * 8);
+      if (g.N <= 32) k_bgemm_small<2><<<(unsigned)grid, 256, 0, st>>>(g, batch);
+      else k_bgemm_small<8><<<(unsigned)grid, 256, 0, st>>>(g, batch);
+      return;
+    }
     if (sgemm128_ok(g, batch)) {
       const long long tiles = ((long long)(g.M + kSgBM - 1) / kSgBM) * ((g.N + kSgBN - 1) / kSgBN);
       if (tiles <= 0x7fffffffLL) {
