@@ -232,6 +232,56 @@ __global__ void __launch_bounds__(256) k_sgemm128(Gemm<T> g) {
 // =========================================================================
 constexpr int kBgK = 32, kBgLd = 132;
 
+// X(r, k) = X[r s_r + k s_k] for r < R, k0 <= k < k0 + 32, into S[k - k0][r]
+// (zero outside R x K), read along whichever stride is 1, four elements at a
+// time where the rows are 16-byte aligned
+__device__ __forceinline__ void stage_slice(const float* X, long long s_r, long long s_k, int R, int K,
+                                            int k0, float (*S)[kBgLd]) {
+  const int tid = threadIdx.x;
+  const bool al = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+  if (s_k == 1 && al && s_r % 4 == 0) {          // rows contiguous in k
+    for (int i = tid; i < 128 * (kBgK / 4); i += 256) {
+      const int r = i >> 3, kk = (i & 7) << 2, k = k0 + kk;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r < R) {
+        const float* x = X + (long long)r * s_r + k;
+        if (k + 3 < K) {
+          v = *reinterpret_cast<const float4*>(x);
+        } else {
+          if (k < K) v.x = x[0];
+          if (k + 1 < K) v.y = x[1];
+          if (k + 2 < K) v.z = x[2];
+        }
+      }
+      S[kk][r] = v.x;
+      S[kk + 1][r] = v.y;
+      S[kk + 2][r] = v.z;
+      S[kk + 3][r] = v.w;
+    }
+  } else if (s_r == 1 && al && s_k % 4 == 0) {   // columns contiguous in r
+    for (int i = tid; i < kBgK * 32; i += 256) {
+      const int kk = i >> 5, r = (i & 31) << 2, k = k0 + kk;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (k < K) {
+        const float* x = X + (long long)k * s_k + r;
+        if (r + 3 < R) {
+          v = *reinterpret_cast<const float4*>(x);
+        } else {
+          if (r < R) v.x = x[0];
+          if (r + 1 < R) v.y = x[1];
+          if (r + 2 < R) v.z = x[2];
+        }
+      }
+      *reinterpret_cast<float4*>(&S[kk][r]) = v;
+    }
+  } else {
+    for (int i = tid; i < 128 * kBgK; i += 256) {
+      const int kk = i >> 7, r = i & 127, k = k0 + kk;
+      S[kk][r] = (r < R && k < K) ? X[(long long)r * s_r + (long long)k * s_k] : 0.f;
+    }
+  }
+}
+
 template <int TN>
 __global__ void __launch_bounds__(256, 2) k_bgemm_small(Gemm<float> g, long long batch) {
   __shared__ __align__(16) float As[kBgK][kBgLd];
@@ -249,30 +299,10 @@ __global__ void __launch_bounds__(256, 2) k_bgemm_small(Gemm<float> g, long long
       for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
     for (int k0 = 0; k0 < g.K; k0 += kBgK) {
       __syncthreads();   // the previous slice (or item) has been read
-      // A(m, k) -> As[k - k0][m]; rows beyond M and k beyond K are zero
-      if (g.a_rk == 1) {
-        for (int i = tid; i < 128 * kBgK; i += 256) {
-          const int m = i >> 5, kk = i & 31, k = k0 + kk;
-          As[kk][m] = (m < g.M && k < g.K) ? A[(long long)m * g.a_rm + k] : 0.f;
-        }
-      } else {
-        for (int i = tid; i < 128 * kBgK; i += 256) {
-          const int kk = i >> 7, m = i & 127, k = k0 + kk;
-          As[kk][m] = (m < g.M && k < g.K) ? A[(long long)m * g.a_rm + (long long)k * g.a_rk] : 0.f;
-        }
-      }
-      // B(k, n) -> Bs[k - k0][n]
-      if (g.b_rk == 1) {
-        for (int i = tid; i < 128 * kBgK; i += 256) {
-          const int n = i >> 5, kk = i & 31, k = k0 + kk;
-          Bs[kk][n] = (n < g.N && k < g.K) ? B[(long long)n * g.b_rn + k] : 0.f;
-        }
-      } else {
-        for (int i = tid; i < 128 * kBgK; i += 256) {
-          const int kk = i >> 7, n = i & 127, k = k0 + kk;
-          Bs[kk][n] = (n < g.N && k < g.K) ? B[(long long)k * g.b_rk + (long long)n * g.b_rn] : 0.f;
-        }
-      }
+      // A(m, k) -> As[k - k0][m] and B(k, n) -> Bs[k - k0][n]; rows beyond
+      // M (N) and k beyond K are zero
+      stage_slice(A, g.a_rm, g.a_rk, g.M, g.K, k0, As);
+      stage_slice(B, g.b_rn, g.b_rk, g.N, g.K, k0, Bs);
       __syncthreads();
 #pragma unroll 4
       for (int kk = 0; kk < kBgK; ++kk) {
