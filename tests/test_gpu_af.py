@@ -311,10 +311,13 @@ def test_fused_unsupported_sizes_are_refused(change):
 
 
 @pytest.mark.parametrize("shape", [dict(m1=72, e1=20, e2=36, n_layers=2),
-                                   dict(m1=120, e1=8, e2=100, n_layers=1, m2=8)])
+                                   dict(m1=120, e1=8, e2=100, n_layers=1, m2=8),
+                                   dict(nmax=12, m2=2, n_layers=1)])
 def test_fused_padded_widths_vs_oracle(shape):
     """Embedding and attention widths below the tile width (padded inside the
-    packed tiles) on the 300-atom water box, every atom against the oracle."""
+    packed tiles) on the 300-atom water box, every atom against the oracle;
+    and a neighbour limit of 12 (every list truncated, two row groups of the
+    128-row tiles real) with an axis of 2."""
     m, s = replace(C.ATTN_MODEL, **shape), serving_system(300, 4)
     pot, w = make(m, s, dp.PREC_FUSED)
     E, F, V = pot.compute(s.coords)
