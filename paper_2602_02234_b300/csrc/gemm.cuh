@@ -117,7 +117,8 @@ __global__ void __launch_bounds__(256) k_gemm(Gemm<T> g, long long batch) {
 
 // =========================================================================
 // FP32 fast path for one (unbatched) product with row-major A (unit column
-// stride), row-major B (K x N, unit column stride) and row-major C: 128 x 128
+// stride), B row-major (K x N, unit column stride) or stored transposed (unit
+// row stride) and row-major C: 128 x 128
 // tiles, 8-deep K slices, 8 x 8 outputs per thread from two 4-wide fragments
 // in each direction, the next slice's float4 loads in registers while the
 // current one is multiplied out of the other shared buffer.  Same result
@@ -155,11 +156,34 @@ __global__ void __launch_bounds__(256) k_sgemm128(Gemm<T> g) {
     }
     return v;
   };
+  // B (K x N) with unit column stride: four columns of one row; B stored
+  // transposed (unit row stride, b_rk == 1): four rows of one column, like A
+  const bool bt = g.b_rn != 1;
+  const int tn_ld = tn * kSgBN + am;   // transposed B: column of this thread
   auto load_b = [&](int k0) {
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    const int k = k0 + bk;
-    if (k < g.K && n_ld < g.N) v = *reinterpret_cast<const float4*>(g.B + (long long)k * g.b_rk + n_ld);
+    if (!bt) {
+      const int k = k0 + bk;
+      if (k < g.K && n_ld < g.N) v = *reinterpret_cast<const float4*>(g.B + (long long)k * g.b_rk + n_ld);
+    } else if (tn_ld < g.N) {
+      const int k = k0 + ak;
+      const float* Bp = g.B + (long long)tn_ld * g.b_rn;
+      if (k + 3 < g.K) {
+        v = *reinterpret_cast<const float4*>(Bp + k);
+      } else {
+        if (k < g.K) v.x = Bp[k];
+        if (k + 1 < g.K) v.y = Bp[k + 1];
+        if (k + 2 < g.K) v.z = Bp[k + 2];
+      }
+    }
     return v;
+  };
+  auto store_b = [&](int bf, float4 v) {
+    if (!bt) {
+      *reinterpret_cast<float4*>(&Bs[bf][bk][bn]) = v;
+    } else {
+      Bs[bf][ak][am] = v.x; Bs[bf][ak + 1][am] = v.y; Bs[bf][ak + 2][am] = v.z; Bs[bf][ak + 3][am] = v.w;
+    }
   };
   float acc[8][8];
 #pragma unroll
@@ -169,7 +193,7 @@ __global__ void __launch_bounds__(256) k_sgemm128(Gemm<T> g) {
   float4 ra = load_a(0), rb = load_b(0);
   int buf = 0;
   As[0][ak][am] = ra.x; As[0][ak + 1][am] = ra.y; As[0][ak + 2][am] = ra.z; As[0][ak + 3][am] = ra.w;
-  *reinterpret_cast<float4*>(&Bs[0][bk][bn]) = rb;
+  store_b(0, rb);
   __syncthreads();
   for (int k0 = 0; k0 < g.K; k0 += kSgBK) {
     const bool more = k0 + kSgBK < g.K;
@@ -194,7 +218,7 @@ __global__ void __launch_bounds__(256) k_sgemm128(Gemm<T> g) {
       buf ^= 1;
       As[buf][ak][am] = ra.x; As[buf][ak + 1][am] = ra.y; As[buf][ak + 2][am] = ra.z;
       As[buf][ak + 3][am] = ra.w;
-      *reinterpret_cast<float4*>(&Bs[buf][bk][bn]) = rb;
+      store_b(buf, rb);
       __syncthreads();
     }
   }
@@ -354,8 +378,10 @@ inline bool sgemm128_ok(const Gemm<T>& g, long long batch) {
     return false;
   } else {
     auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
-    return batch == 1 && g.a_rk == 1 && g.b_rn == 1 && g.c_rn == 1 && g.a_rm % 4 == 0 &&
-           g.b_rk % 4 == 0 && g.N % 4 == 0 && al16(g.A) && al16(g.B) && g.M >= kSgBM &&
+    const bool b_rows = g.b_rn == 1 && g.b_rk % 4 == 0 && g.N % 4 == 0;   // B row-major
+    const bool b_cols = g.b_rk == 1 && g.b_rn % 4 == 0;                   // B stored transposed
+    return batch == 1 && g.a_rk == 1 && (b_rows || b_cols) && g.c_rn == 1 && g.a_rm % 4 == 0 &&
+           al16(g.A) && al16(g.B) && g.M >= kSgBM &&
            g.K >= kSgBK && g.N >= 96;   // narrower products keep the 64 x 64 tiles
   }
 }
