@@ -307,7 +307,7 @@ __device__ __forceinline__ void stage_slice(const float* X, long long s_r, long 
 }
 
 template <int TN>
-__global__ void __launch_bounds__(256, 2) k_bgemm_small(Gemm<float> g, long long batch) {
+__global__ void __launch_bounds__(256, TN == 2 ? 4 : 2) k_bgemm_small(Gemm<float> g, long long batch) {
   __shared__ __align__(16) float As[kBgK][kBgLd];
   __shared__ __align__(16) float Bs[kBgK][kBgLd];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
