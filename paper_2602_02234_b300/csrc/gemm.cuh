@@ -390,14 +390,14 @@ template <typename T>
 inline void gemm(const Gemm<T>& g, long long batch, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0 || batch <= 0) return;
   if constexpr (std::is_same<T, float>::value) {
+    static int sms = 0;
+    if (sms == 0) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (sms <= 0) sms = 148;
+    }
     if (batch > 1 && g.M <= 128 && g.N <= 128 && !g.a_rows && !g.c_rows) {
-      static int sms = 0;
-      if (sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 148;
-      }
       const long long grid = std::min<long long>(batch, (long long)sms * 8);
       if (g.N <= 32) k_bgemm_small<2><<<(unsigned)grid, 256, 0, st>>>(g, batch);
       else k_bgemm_small<8><<<(unsigned)grid, 256, 0, st>>>(g, batch);
@@ -405,7 +405,8 @@ inline void gemm(const Gemm<T>& g, long long batch, cudaStream_t st) {
     }
     if (sgemm128_ok(g, batch)) {
       const long long tiles = ((long long)(g.M + kSgBM - 1) / kSgBM) * ((g.N + kSgBN - 1) / kSgBN);
-      if (tiles <= 0x7fffffffLL) {
+      // small products keep the 64 x 64 tiles, which give the GPU more CTAs
+      if (tiles >= 2LL * sms && tiles <= 0x7fffffffLL) {
         k_sgemm128<float><<<(unsigned)tiles, 256, 0, st>>>(g);
         return;
       }
