@@ -1427,6 +1427,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_af_bwd(Params p) {
 // ================================================================== fitting
 struct FitParams {
   int n_tiles, kd, f1, f2, f3, kc1, kc2;
+  int kcw;                // one chunk over K = f1 (F2T, F1R), staged in the free Y2 + Y3 space
   const int4* tiles;      // {species, start, count, 0}
   const int* order;       // atoms grouped by species
   const op_t* D;          // [n][kd]
@@ -1448,13 +1449,14 @@ constexpr int FT_CB = FT_CA + 128 * 32 * 2;
 constexpr int FT_MISC = FT_CB + 256 * 48 * 2;
 constexpr int kSmemFit = FT_MISC + 64;
 
-// acc(128 x N, tmem col0) = A(tile, Kx = K) * B(chunks of kc columns, N rows)
-__device__ bool fit_product(uint8_t* sm, const uint8_t* A, int K, const uint8_t* Bchunks, int N,
+// acc(128 x N, tmem col0) = A(tile, Kx = K) * B(chunks of kc columns, N rows),
+// each chunk staged in bbuf
+__device__ bool fit_product(uint8_t* bbuf, const uint8_t* A, int K, const uint8_t* Bchunks, int N,
                             int kc, uint32_t tcol, Bar& mb, Bar& wb, int* status) {
   for (int k0 = 0; k0 < K; k0 += kc) {
-    bulk_load(wb, sm + FT_CB, Bchunks + (size_t)(k0 / kc) * N * kc * 2, N * kc * 2);
+    bulk_load(wb, bbuf, Bchunks + (size_t)(k0 / kc) * N * kc * 2, N * kc * 2);
     if (!wb.wait(status)) return false;
-    MMA_GROUP(mb, status, mma_issue(tcol, kop(A, K, k0), kop(sm + FT_CB, kc), N, kc, k0 > 0));
+    MMA_GROUP(mb, status, mma_issue(tcol, kop(A, K, k0), kop(bbuf, kc), N, kc, k0 > 0));
   }
   return true;
 }
@@ -1487,21 +1489,24 @@ __global__ void __launch_bounds__(kFitThreads, 1) k_fit(FitParams p) {
   const uint32_t tb = *tptr;
   Bar mb{bar, 0u}, wb{wbar, 0u};
   bool ok = true;
-  uint8_t *Y1 = sm + FT_Y1, *Y2 = sm + FT_Y2, *Y3 = sm + FT_Y3, *CA = sm + FT_CA;
+  uint8_t *Y1 = sm + FT_Y1, *Y2 = sm + FT_Y2, *Y3 = sm + FT_Y3;
   for (int tile = blockIdx.x; tile < p.n_tiles && ok; tile += gridDim.x) {
     const int4 td = p.tiles[tile];
     const int sp = td.x;
     const int atom = t < td.z ? p.order[td.y + t] : -1;
-    // ---- layer 1: D (gathered rows, K = kd in chunks of kc1) x F1
+    // ---- layer 1: D (gathered rows, K = kd in chunks of kc1) x F1; the
+    // chunks' A and B tiles use the Y2 and Y3 space, free until layer 2
+    uint8_t* CA1 = sm + FT_Y2;
+    uint8_t* CB1 = CA1 + 128 * p.kc1 * 2;
     for (int k0 = 0; k0 < p.kd && ok; k0 += p.kc1) {
       for (int c = 0; c < p.kc1; c += 8) {
         uint4 u = make_uint4(0, 0, 0, 0);
         if (atom >= 0) u = *reinterpret_cast<const uint4*>(p.D + (size_t)atom * p.kd + k0 + c);
-        *reinterpret_cast<uint4*>(CA + tc::kmajor_off(t, c, p.kc1)) = u;
+        *reinterpret_cast<uint4*>(CA1 + tc::kmajor_off(t, c, p.kc1)) = u;
       }
-      bulk_load(wb, sm + FT_CB, p.F1T + sp * p.sF1T + (size_t)(k0 / p.kc1) * p.f1 * p.kc1 * 2,
+      bulk_load(wb, CB1, p.F1T + sp * p.sF1T + (size_t)(k0 / p.kc1) * p.f1 * p.kc1 * 2,
                 p.f1 * p.kc1 * 2);
-      ok = wb.wait(p.status) && fit_layer1(CA, sm + FT_CB, p.kc1, p.f1, k0 > 0, tb, mb, p.status);
+      ok = wb.wait(p.status) && fit_layer1(CA1, CB1, p.kc1, p.f1, k0 > 0, tb, mb, p.status);
     }
     if (!ok) break;
     // epilogue: y = tanh(acc + c) into a K-major tile
@@ -1515,11 +1520,13 @@ __global__ void __launch_bounds__(kFitThreads, 1) k_fit(FitParams p) {
     };
     epi_tanh(p.f1, p.c1, Y1);
     tc::fence_before_sync();
-    ok = fit_product(sm, Y1, p.f1, p.F2T + sp * p.sF2T, p.f2, p.kc2, tb, mb, wb, p.status);
+    // layer 2 in one chunk: its weights fill the Y2 + Y3 space, free until
+    // the epilogue writes y2
+    ok = fit_product(Y2, Y1, p.f1, p.F2T + sp * p.sF2T, p.f2, p.kcw, tb, mb, wb, p.status);
     if (!ok) break;
     epi_tanh(p.f2, p.c2, Y2);
     tc::fence_before_sync();
-    ok = fit_product(sm, Y2, p.f2, p.F3T + sp * p.sF3T, p.f3, p.kc2, tb, mb, wb, p.status);
+    ok = fit_product(sm + FT_CB, Y2, p.f2, p.F3T + sp * p.sF3T, p.f3, p.kc2, tb, mb, wb, p.status);
     if (!ok) break;
     // y3, energy (FP64 sum) and delta3 = seed F4 (1 - y3^2) into Y3
     {
@@ -1553,17 +1560,18 @@ __global__ void __launch_bounds__(kFitThreads, 1) k_fit(FitParams p) {
         }
       }
     };
-    ok = fit_product(sm, Y3, p.f3, p.F3R + sp * p.sF3R, p.f2, p.kc2, tb, mb, wb, p.status);
+    ok = fit_product(sm + FT_CB, Y3, p.f3, p.F3R + sp * p.sF3R, p.f2, p.kc2, tb, mb, wb, p.status);
     if (!ok) break;
     epi_dtanh(p.f2, Y2);
     tc::fence_before_sync();
-    ok = fit_product(sm, Y2, p.f2, p.F2R + sp * p.sF2R, p.f1, p.kc2, tb, mb, wb, p.status);
+    ok = fit_product(sm + FT_CB, Y2, p.f2, p.F2R + sp * p.sF2R, p.f1, p.kc2, tb, mb, wb, p.status);
     if (!ok) break;
     epi_dtanh(p.f1, Y1);
     tc::fence_before_sync();
-    // dE/dD = delta1 F1^T, 256 columns at a time
+    // dE/dD = delta1 F1^T, 256 columns at a time, each in one chunk staged
+    // in the Y2 + Y3 space (delta2 has been used)
     for (int nb = 0; nb < p.kd / 256 && ok; ++nb) {
-      ok = fit_product(sm, Y1, p.f1, p.F1R + sp * p.sF1R + (size_t)nb * 256 * p.f1 * 2, 256, p.kc2,
+      ok = fit_product(Y2, Y1, p.f1, p.F1R + sp * p.sF1R + (size_t)nb * 256 * p.f1 * 2, 256, p.kcw,
                        tb, mb, wb, p.status);
       if (!ok) break;
       for (int c = 0; c < 256; c += 32) {
@@ -1862,19 +1870,21 @@ bool FusedAf::init(const AfDims& m, const double* w, int n_atoms, const int* typ
     pack(WoR, H, kW, kW, [&](int r, int k) { return wz(oo[l], r, k, H, M1); });
     for (int k = 0; k < kW; ++k) bo.push_back(k < M1 ? (float)at(obo[l] + k) : 0.f);
   }
-  // fitting: chunk widths kc1 for K = KD, kc2 for K = f
-  const int kc1 = 32;
+  // fitting: chunk widths kc1 for K = KD (the A and B chunks of 128 x kc1
+  // and f1 x kc1 fill the 128 KB of the Y2 and Y3 tiles at most), kc2 for K = f
+  const int kc1 = 128;
   const int kc2 = (m.f1 % 48 == 0 && m.f2 % 48 == 0 && m.f3 % 48 == 0) ? 48 : 16;
+  const int kcw = m.f1;   // f2 x f1 or 256 x f1 16-bit: at most 128 KB, the Y2 + Y3 space
   std::vector<uint16_t> F1T, F2T, F3T, F3R, F2R, F1R;
   std::vector<float> c1, c2, c3, F4, c4;
   for (int t = 0; t < S; ++t) {
     pack(F1T, m.f1, KD, kc1, [&](int r, int k) { return wz(oF1[t], k, r, KDr, m.f1); });
-    pack(F2T, m.f2, m.f1, kc2, [&](int r, int k) { return at(oF2[t] + (size_t)k * m.f2 + r); });
+    pack(F2T, m.f2, m.f1, kcw, [&](int r, int k) { return at(oF2[t] + (size_t)k * m.f2 + r); });
     pack(F3T, m.f3, m.f2, kc2, [&](int r, int k) { return at(oF3[t] + (size_t)k * m.f3 + r); });
     pack(F3R, m.f2, m.f3, kc2, [&](int r, int k) { return at(oF3[t] + (size_t)r * m.f3 + k); });
     pack(F2R, m.f1, m.f2, kc2, [&](int r, int k) { return at(oF2[t] + (size_t)r * m.f2 + k); });
     for (int nb = 0; nb < KD / 256; ++nb)
-      pack(F1R, 256, m.f1, kc2,
+      pack(F1R, 256, m.f1, kcw,
            [&](int r, int k) { return wz(oF1[t], nb * 256 + r, k, KDr, m.f1); });
     for (int k = 0; k < m.f1; ++k) c1.push_back((float)at(oc1[t] + k));
     for (int k = 0; k < m.f2; ++k) c2.push_back((float)at(oc2[t] + k));
@@ -1897,7 +1907,7 @@ bool FusedAf::init(const AfDims& m, const double* w, int n_atoms, const int* typ
     const size_t sh = (size_t)h * fit_len;
     for (int t = 0; t < S; ++t) {
       pack(X.F1T, m.f1, KD, kc1, [&](int r, int k) { return wz(sh + oF1[t], k, r, KDr, m.f1); });
-      pack(X.F2T, m.f2, m.f1, kc2, [&](int r, int k) { return at(sh + oF2[t] + (size_t)k * m.f2 + r); });
+      pack(X.F2T, m.f2, m.f1, kcw, [&](int r, int k) { return at(sh + oF2[t] + (size_t)k * m.f2 + r); });
       pack(X.F3T, m.f3, m.f2, kc2, [&](int r, int k) { return at(sh + oF3[t] + (size_t)k * m.f3 + r); });
       for (int k = 0; k < m.f1; ++k) X.c1.push_back((float)at(sh + oc1[t] + k));
       for (int k = 0; k < m.f2; ++k) X.c2.push_back((float)at(sh + oc2[t] + k));
@@ -1975,7 +1985,7 @@ bool FusedAf::init(const AfDims& m, const double* w, int n_atoms, const int* typ
   // fitting tiles (capacity for any atom set up to n_atoms): see set_atoms
   FitParams& f = fit_;
   f.kd = KD; f.f1 = m.f1; f.f2 = m.f2; f.f3 = m.f3;
-  f.kc1 = kc1; f.kc2 = kc2;
+  f.kc1 = kc1; f.kc2 = kc2; f.kcw = kcw;
   cap_ = n_atoms;
   if (!dalloc(&dtiles_, (size_t)n_atoms / 128 + S + 1, err) || !dalloc(&dorder_, (size_t)n_atoms, err))
     return false;
