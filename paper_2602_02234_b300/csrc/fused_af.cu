@@ -397,8 +397,34 @@ __device__ bool species_loop(unsigned mask, const uint8_t* base, size_t stride, 
   return true;
 }
 
+// Species loop in pairs: the set bits of `mask` in increasing order, two at a
+// time; both species' weight blocks arrive together (tiles t0, t1 on k0, k1)
+// and body(sa, t0, sb, t1) issues both products in one group (sb = -1 when
+// the count is odd).  Most atoms see two species, so one product group does
+// the work of two.
+template <typename F>
+__device__ bool species_pairs(unsigned mask, const uint8_t* base, size_t stride, uint32_t bytes,
+                              uint8_t* t0, uint8_t* t1, Bar& k0, Bar& k1, int* status, F&& body) {
+  while (mask) {
+    const int sa = __ffs(mask) - 1;
+    mask &= mask - 1u;
+    const int sb = mask ? __ffs(mask) - 1 : -1;
+    if (sb >= 0) mask &= mask - 1u;
+    tc::fence_async_smem();
+    __syncthreads();   // every earlier access to t0 and t1 is done
+    if (threadIdx.x == 0) {
+      issue_copy(k0, t0, base + (size_t)sa * stride, bytes, bytes);
+      if (sb >= 0) issue_copy(k1, t1, base + (size_t)sb * stride, bytes, bytes);
+    }
+    if (!k0.wait(status)) return false;
+    if (sb >= 0 && !k1.wait(status)) return false;
+    if (!body(sa, t0, sb, t1)) return false;
+  }
+  return true;
+}
+
 // Layer 1 on the SIMT cores into the K-major tile H1, layer 2 on the tensor
-// cores species by species into H2 (16-bit); weights through tiles w0, w1.
+// cores two species at a time into H2 (16-bit); weights through tiles w0, w1.
 __device__ bool embed_h2(const Params& p, uint8_t* sm, Misc* m, uint32_t tb, Bar& mb, Bar& k0,
                          Bar& k1, uint8_t* H1, uint8_t* H2, uint8_t* w0, uint8_t* w1) {
   const int r = row_id(), pt = part_id();
@@ -417,17 +443,29 @@ __device__ bool embed_h2(const Params& p, uint8_t* sm, Misc* m, uint32_t tb, Bar
     store8(H2, r, c, p.e2, z);
   }
   const uint32_t bytes = p.e2 * p.e1 * 2;
-  return species_loop((unsigned)m->mask, p.W2T, bytes, bytes, w0, w1, k0, k1, p.status,
-                      [&](int sp, uint8_t* Wt) -> bool {
-    MMA_GROUP(mb, p.status, mma_issue(tb + R0, kop(H1, p.e1), kop(Wt, p.e1), p.e2, p.e1, false));
-    const bool mine = tj == sp;
+  const uint32_t rb = p.e2 <= 64 ? R0 + 64 : R1;   // the second species' accumulator
+  return species_pairs((unsigned)m->mask, p.W2T, bytes, bytes, w0, w1, k0, k1, p.status,
+                       [&](int sa, uint8_t* Wa, int sb, uint8_t* Wb) -> bool {
+    MMA_GROUP(mb, p.status,
+              mma_issue(tb + R0, kop(H1, p.e1), kop(Wa, p.e1), p.e2, p.e1, false);
+              if (sb >= 0) mma_issue(tb + rb, kop(H1, p.e1), kop(Wb, p.e1), p.e2, p.e1, false));
+    const bool mine = tj >= 0 && (tj == sa || tj == sb);
     if (__any_sync(0xffffffffu, mine)) {
       for (int c = 16 * pt; c < p.e2; c += 16 * kSplit) {
         float v[16];
-        tc::tmem_ld16(tb + lo + R0 + c, v);
+        if (sb >= 0) {
+          float u[16];
+          tc::tmem_ld16x2(tb + lo + R0 + c, v, tb + lo + rb + c, u);
+          if (tj == sb) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) v[q] = u[q];
+          }
+        } else {
+          tc::tmem_ld16(tb + lo + R0 + c, v);
+        }
         if (mine) {
 #pragma unroll
-          for (int q = 0; q < 16; ++q) v[q] = tanh_hw(v[q] + p.b2[sp * p.e2 + c + q]);
+          for (int q = 0; q < 16; ++q) v[q] = tanh_hw(v[q] + p.b2[tj * p.e2 + c + q]);
           store8(H2, r, c, p.e2, v);
           store8(H2, r, c + 8, p.e2, v + 8);
         }
@@ -456,19 +494,31 @@ __device__ bool embed_forward(const Params& p, uint8_t* sm, Misc* m, uint32_t tb
     for (int c = 32 * pt; c < kW; c += kStride) tc::tmem_st32(tb + lo + R2 + c, z);
   }
   const uint32_t bytes = kW * p.e2 * 2;
-  return species_loop((unsigned)m->mask, p.W3T, bytes, bytes, sm + SM_W, sm + SM_P, wb, xb,
-                      p.status, [&](int sp, uint8_t* Wt) -> bool {
-    MMA_GROUP(mb, p.status, mma_issue(tb + R1, kop(H2, p.e2), kop(Wt, p.e2), kW, p.e2, false));
-    const bool mine = tj == sp;
+  // two species per product group: the first into R1, the second into R3
+  return species_pairs((unsigned)m->mask, p.W3T, bytes, bytes, sm + SM_W, sm + SM_P, wb, xb,
+                       p.status, [&](int sa, uint8_t* Wa, int sb, uint8_t* Wb) -> bool {
+    MMA_GROUP(mb, p.status,
+              mma_issue(tb + R1, kop(H2, p.e2), kop(Wa, p.e2), kW, p.e2, false);
+              if (sb >= 0) mma_issue(tb + R3, kop(H2, p.e2), kop(Wb, p.e2), kW, p.e2, false));
+    const bool mine = tj >= 0 && (tj == sa || tj == sb);
+    const uint32_t racc = sb >= 0 && tj == sb ? R3 : R1;
     if (__any_sync(0xffffffffu, mine)) {
       for (int c = 32 * pt; c < kW; c += kStride) {
 #pragma unroll
         for (int c16 = 0; c16 < 32; c16 += 16) {
           float v[16], g[16];
           tc::tmem_ld16x2(tb + lo + R1 + c + c16, v, tb + lo + R2 + c + c16, g);
+          if (sb >= 0) {
+            float u[16];
+            tc::tmem_ld16(tb + lo + R3 + c + c16, u);
+            if (racc == R3) {
+#pragma unroll
+              for (int q = 0; q < 16; ++q) v[q] = u[q];
+            }
+          }
           if (mine) {
 #pragma unroll
-            for (int q = 0; q < 16; ++q) g[q] = tanhf(v[q] + p.b3[sp * kW + c + c16 + q]);   // G0 enters the FP32 residual stream
+            for (int q = 0; q < 16; ++q) g[q] = tanhf(v[q] + p.b3[tj * kW + c + c16 + q]);   // G0 enters the FP32 residual stream
             store8(Gt, r, c + c16, kW, g);
             store8(Gt, r, c + c16 + 8, kW, g + 8);
           }
