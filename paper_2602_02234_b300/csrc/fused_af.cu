@@ -776,36 +776,36 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
     MMA_GROUP(mb, p.status, mma_issue(tb + R1, kop(sm + SM_Q, kW), kop(sm + SM_W, kW), kW, kW, false));
     // next layer's projections land in the free Q, K, V tiles during the LayerNorm
     if (l + 1 < l_end) load_qkv_weights(p, l + 1, sm, xb);
-    // residual + LayerNorm over the row's 128 columns: mean, variance, scale
+    // residual + LayerNorm over the row's real columns: the sum and the sum of
+    // squares of z = G + Y + bo in one pass and one row exchange (z is 0 in
+    // the padding columns), variance = mean(z^2) - mean(z)^2
     const float* bo = p.bo + l * kW;
+    // real columns: every column with message passing (it needs m1 = 128)
+    const int m1 = MP ? kW : p.m1;
+    const float inv_m1 = MP ? 1.f / kW : p.inv_m1;
     float sum = 0.f, sq = 0.f;
     for (int c = 32 * pt; c < kW; c += kStride) {
       float g[32], y[32];
       tc::tmem_ld32(tb + lo + R2 + c, g);
       tc::tmem_ld32(tb + lo + R1 + c, y);
-      float s4[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-      for (int q = 0; q < 32; ++q) s4[q & 3] += g[q] + y[q] + bo[c + q];
-      sum += (s4[0] + s4[1]) + (s4[2] + s4[3]);
-    }
-    sum = row_sum(m, make_float4(sum, 0.f, 0.f, 0.f)).x;
-    // real columns: every column with message passing (it needs m1 = 128)
-    const int m1 = MP ? kW : p.m1;
-    const float mu = sum * (MP ? 1.f / kW : p.inv_m1);
-    for (int c = 32 * pt; c < kW; c += kStride) {
-      float g[32], y[32];
-      tc::tmem_ld32(tb + lo + R2 + c, g);
-      tc::tmem_ld32(tb + lo + R1 + c, y);
-      float s4[4] = {0.f, 0.f, 0.f, 0.f};
+      float s4[4] = {0.f, 0.f, 0.f, 0.f}, q4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
-        const float z = c + q < m1 ? g[q] + y[q] + bo[c + q] - mu : 0.f;   // padding: none
-        s4[q & 3] += z * z;
+        const float z = g[q] + y[q] + bo[c + q];
+        s4[q & 3] += z;
+        q4[q & 3] += z * z;
       }
-      sq += (s4[0] + s4[1]) + (s4[2] + s4[3]);
+      sum += (s4[0] + s4[1]) + (s4[2] + s4[3]);
+      sq += (q4[0] + q4[1]) + (q4[2] + q4[3]);
     }
-    sq = row_sum(m, make_float4(sq, 0.f, 0.f, 0.f)).x;
-    const float rs = valid ? rsqrtf(sq * (MP ? 1.f / kW : p.inv_m1) + 1e-5f) : 0.f;
+    {
+      const float4 o = row_sum(m, make_float4(sum, sq, 0.f, 0.f));
+      sum = o.x;
+      sq = o.y;
+    }
+    const float mu = sum * inv_m1;
+    const float var = fmaxf(sq * inv_m1 - mu * mu, 0.f);
+    const float rs = valid ? rsqrtf(var + 1e-5f) : 0.f;
     for (int c = 32 * pt; c < kW; c += kStride) {
       float g[32], y[32];
       tc::tmem_ld32(tb + lo + R2 + c, g);
