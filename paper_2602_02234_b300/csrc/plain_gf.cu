@@ -222,60 +222,135 @@ __global__ void k_edge(long long P, int nmax, int ed, int ed_shift, const int* _
   e1[idx] = e_in[idx] + y;
 }
 
-__device__ __forceinline__ void legendre4(float c, float* P, float* dP) {
-  P[0] = 1.f; P[1] = c; P[2] = 0.5f * (3.f * c * c - 1.f); P[3] = 0.5f * (5.f * c * c * c - 3.f * c);
-  dP[0] = 0.f; dP[1] = 1.f; dP[2] = 3.f * c; dP[3] = 0.5f * (15.f * c * c - 3.f);
-}
-__device__ __forceinline__ void legendre4(double c, double* P, double* dP) {
-  P[0] = 1.0; P[1] = c; P[2] = 0.5 * (3.0 * c * c - 1.0); P[3] = 0.5 * (5.0 * c * c * c - 3.0 * c);
-  dP[0] = 0.0; dP[1] = 1.0; dP[2] = 3.0 * c; dP[3] = 0.5 * (15.0 * c * c - 3.0);
-}
-
 constexpr int kMaxNa = 64;
 
-// acc[l] += c[l] * x for l < 4; FP32 as two packed pair instructions
-__device__ __forceinline__ void fma4(double* acc, const double* c, double x) {
+// acc[i] += c[i] * x for i < N (N even); FP32 as packed pair instructions
+template <int N>
+__device__ __forceinline__ void fma_n(double* acc, const double* c, double x) {
 #pragma unroll
-  for (int l = 0; l < 4; ++l) acc[l] += c[l] * x;
+  for (int i = 0; i < N; ++i) acc[i] += c[i] * x;
 }
-__device__ __forceinline__ void fma4(float* acc, const float* c, float x) {
+template <int N>
+__device__ __forceinline__ void fma_n(float* acc, const float* c, float x) {
 #pragma unroll
-  for (int h = 0; h < 4; h += 2)
+  for (int h = 0; h < N; h += 2)
     asm("{\n\t.reg .b64 ra, rb, rc;\n\t"
         "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %4};\n\tmov.b64 rc, {%0, %1};\n\t"
         "fma.rn.f32x2 rc, ra, rb, rc;\n\tmov.b64 {%0, %1}, rc;\n\t}"
         : "+f"(acc[h]), "+f"(acc[h + 1])
         : "f"(c[h]), "f"(c[h + 1]), "f"(x));
 }
-
-// Angle-channel blocks: kAngThreads threads per atom.  The products over the
-// angle slots are register-tiled: a thread owns a 4 x 4 block of outputs
-// (4 slot rows x the columns cg + 16 j, j < 4, of a 64-column block, cg =
-// thread mod 16) and keeps the four Legendre orders' partial sums of each in
-// registers, so one pass over the summed index reads 4 row values and 4
-// coefficient quadruples per 64 multiply-adds.  Rows beyond the atom's angle
-// count are computed from clamped (valid) rows and never stored.
-constexpr int kAngThreads = 128;
-
-// coef[(p na + k) 4 + l] = w_pk P_l(c_pk) for p, k < nang, 0 elsewhere (also
-// for p == k and for the padding rows up to ra = na rounded up to 4), from
-// the slots' switches gsa and unit vectors grh staged in shared memory
-template <typename T>
-__device__ void angle_coef(T* coef, int na, int ra, int nang, const T* gsa, const T* grh,
-                           T inv_na) {
-  for (int pk = threadIdx.x; pk < ra * na; pk += blockDim.x) {
-    const int p = pk / na, k = pk - p * na;
-    T P[4] = {T(0), T(0), T(0), T(0)}, dP[4];
-    T w = T(0);
-    if (p < nang && k < nang && p != k) {
-      const T* rp = grh + 3 * p;
-      const T* rk = grh + 3 * k;
-      legendre4(rp[0] * rk[0] + rp[1] * rk[1] + rp[2] * rk[2], P, dP);
-      w = inv_na * gsa[p] * gsa[k];
-    }
+// sum_i a[i] b[i] for i < N (N even), as two interleaved partial sums
+template <int N, typename T>
+__device__ __forceinline__ T dot_n(const T* a, const T* b) {
+  T s0 = T(0), s1 = T(0);
 #pragma unroll
-    for (int l = 0; l < 4; ++l) coef[(size_t)pk * 4 + l] = w * P[l];
+  for (int i = 0; i < N; i += 2) {
+    s0 += a[i] * b[i];
+    s1 += a[i + 1] * b[i + 1];
   }
+  return s0 + s1;
+}
+
+// Angle channel by monomial sums.  The angle sums weight q_k by
+// sum_l Wphi[l][c] P_l(u_p . u_k) for l <= 3 (unit vectors u).  In the power
+// basis P_l(x) = sum_n A_ln x^n (P2 = 1.5 x^2 - 0.5, P3 = 2.5 x^3 - 1.5 x),
+// so the weight is sum_n beta_n[c] x^n with beta_n[c] = sum_l Wphi[l][c] A_ln,
+// and (u . v)^n = sum_{|m| = n} mult(m) u^m v^m over the monomials
+// u^m = ux^mx uy^my uz^mz of degree n (multinomial weights mult(m) = n! /
+// (mx! my! mz!)).  Hence, for an atom with angle slots k < nang,
+//   sum_{k != p} sa_k q_k[c] sum_n beta_n[c] (u_p . u_k)^n
+//     = sum_m u_p^m YB_m[c] - sa_p q_p[c] sum_n beta_n[c] (u_p . u_p)^n,
+//   YB_m[c] = mult(m) beta_|m|[c] Y_m[c],   Y_m[c] = sum_k sa_k u_k^m q_k[c]
+// (the k = p term is taken out of the full sum).  This is an identity between
+// polynomials in the unit-vector components, so its derivatives are those of
+// the pairwise form as well; it costs two passes of 20 multiply-adds per
+// (slot, column) instead of four per (slot, partner, column).
+constexpr int kMono = 20;
+// the 20 monomials of degree <= 3 in this order: 1 | x y z | xx yy zz xy xz yz |
+// xxx yyy zzz xxy xxz xyy yyz xzz yzz xyz
+__host__ __device__ constexpr int mono_deg(int m) { return m == 0 ? 0 : m < 4 ? 1 : m < 10 ? 2 : 3; }
+__host__ __device__ constexpr int mono_mult(int m) {
+  return m == 19 ? 6 : (m >= 13 ? 3 : (m >= 7 && m < 10 ? 2 : 1));
+}
+template <typename T>
+__device__ __forceinline__ void monomials(T x, T y, T z, T* m) {
+  m[0] = T(1); m[1] = x; m[2] = y; m[3] = z;
+  m[4] = x * x; m[5] = y * y; m[6] = z * z; m[7] = x * y; m[8] = x * z; m[9] = y * z;
+  m[10] = m[4] * x; m[11] = m[5] * y; m[12] = m[6] * z; m[13] = m[4] * y; m[14] = m[4] * z;
+  m[15] = x * m[5]; m[16] = m[5] * z; m[17] = x * m[6]; m[18] = y * m[6]; m[19] = m[7] * z;
+}
+// d/du of sum_m g[m] u^m
+template <typename T>
+__device__ __forceinline__ void monomial_grad(T x, T y, T z, const T* g, T* d) {
+  d[0] = g[1] + T(2) * x * g[4] + y * g[7] + z * g[8] + T(3) * x * x * g[10] + T(2) * x * y * g[13] +
+         T(2) * x * z * g[14] + y * y * g[15] + z * z * g[17] + y * z * g[19];
+  d[1] = g[2] + T(2) * y * g[5] + x * g[7] + z * g[9] + T(3) * y * y * g[11] + x * x * g[13] +
+         T(2) * x * y * g[15] + T(2) * y * z * g[16] + z * z * g[18] + x * z * g[19];
+  d[2] = g[3] + T(2) * z * g[6] + x * g[8] + y * g[9] + T(3) * z * z * g[12] + x * x * g[14] +
+         y * y * g[16] + T(2) * x * z * g[17] + T(2) * y * z * g[18] + x * y * g[19];
+}
+template <typename T>
+__device__ __forceinline__ void ld20(const T* p, T* v) {
+#pragma unroll
+  for (int i = 0; i < kMono; i += 4) ld4(p + i, v + i);
+}
+
+// Angle-channel blocks: kAngThreads threads per atom.  Column phases give
+// each column of a 64-column block two threads (kAngCols = kAngThreads / 2).
+constexpr int kAngThreads = 128, kAngCols = kAngThreads / 2;
+
+// beta[4 c + n] = sum_l Wphi[l][c] A_ln (Wphi stored [4][ed])
+template <typename T>
+__device__ void angle_beta(T* beta, const T* Wphi, int ed) {
+  for (int c = threadIdx.x; c < ed; c += blockDim.x) {
+    const T w0 = Wphi[c], w1 = Wphi[ed + c], w2 = Wphi[2 * ed + c], w3 = Wphi[3 * ed + c];
+    beta[4 * c] = w0 - T(0.5) * w2;
+    beta[4 * c + 1] = w1 - T(1.5) * w3;
+    beta[4 * c + 2] = T(1.5) * w2;
+    beta[4 * c + 3] = T(2.5) * w3;
+  }
+}
+// per angle slot s < nang: mono[s] = u_s^m, monosa[s] = sa_s u_s^m, and
+// xpow[s] = (u_s . u_s)^n, n < 4
+template <typename T>
+__device__ void angle_mono(T* mono, T* monosa, T* xpow, int nang, const T* gsa, const T* grh) {
+  for (int s = threadIdx.x; s < nang; s += blockDim.x) {
+    T m[kMono];
+    const T x = grh[3 * s], y = grh[3 * s + 1], z = grh[3 * s + 2], sp = gsa[s];
+    monomials(x, y, z, m);
+    const T xx = m[4] + m[5] + m[6];
+#pragma unroll
+    for (int i = 0; i < kMono; ++i) {
+      mono[s * kMono + i] = m[i];
+      monosa[s * kMono + i] = sp * m[i];
+    }
+    xpow[4 * s] = T(1);
+    xpow[4 * s + 1] = xx;
+    xpow[4 * s + 2] = xx * xx;
+    xpow[4 * s + 3] = xx * xx * xx;
+  }
+}
+// One half (monomials 10 H .. 10 H + 9) of the weighted sums of column c over
+// the angle slots: out[c][m] = scale mult(m) beta_|m|[c] sum_k monosa[k][m] x_k[c]
+template <int H, typename T>
+__device__ __forceinline__ void angle_ysum(T* out, const T* beta, const T* monosa, int nang, const T* xs,
+                                           int ld, int c, T scale) {
+  T acc[10];
+#pragma unroll
+  for (int j = 0; j < 10; ++j) acc[j] = T(0);
+  for (int k = 0; k < nang; ++k) {
+    const T xv = xs[k * ld + c];
+    T w[10];
+#pragma unroll
+    for (int j = 0; j < 10; j += 2) ld2(monosa + k * kMono + 10 * H + j, w + j);
+    fma_n<10>(acc, w, xv);
+  }
+  T b[4];
+  ld4(beta + 4 * c, b);
+#pragma unroll
+  for (int j = 0; j < 10; ++j)
+    out[c * kMono + 10 * H + j] = scale * T(mono_mult(10 * H + j)) * b[mono_deg(10 * H + j)] * acc[j];
 }
 
 // Asynchronous element copies global -> shared (cp.async, completion per
@@ -354,12 +429,13 @@ __device__ __forceinline__ int angle_next(const AngleBuf<T>& cur, const AngleBuf
   return __syncthreads_count(threadIdx.x < ca && cur.sa[threadIdx.x] > T(0));
 }
 
-// (c) forward: a_p[c] = sum_l Wphi[l][c] sum_k coef_pkl q_k[c] for the angle
-// slots p of each atom.  q and a hold the angle rows only: slot p < ca of atom
-// i at row i ca + p (ca = min(na, nmax)); rows from the atom's angle count up
-// to ca get a = 0.  Shared memory: the coefficients (ra x na x 4), Wphi by
-// column (ed x 4, Wphi[l][c] at W4[4 c + l]), then two slot-data buffers
-// (q rows staged when `staged`).
+// (c) forward: a_p[c] = (1/na) sa_p sum_{k != p} sa_k q_k[c] sum_l Wphi[l][c] P_l(u_p . u_k)
+// for the angle slots p of each atom, by the monomial sums above.  q and a
+// hold the angle rows only: slot p < ca of atom i at row i ca + p (ca =
+// min(na, nmax)); rows from the atom's angle count up to ca get a = 0.
+// Shared memory: beta (ed x 4), the slots' monomials, sa-weighted monomials
+// and (u . u)^n (na x 20, na x 20, na x 4), YB (ed x 20), then two slot-data
+// buffers (q rows staged when `staged`).
 template <typename T>
 __global__ void __launch_bounds__(kAngThreads) k_angle(int n, int nmax, int na, int ca, int ed, T inv_na,
                                                        const T* __restrict__ sa,
@@ -368,14 +444,17 @@ __global__ void __launch_bounds__(kAngThreads) k_angle(int n, int nmax, int na, 
                                                        const T* __restrict__ Wphi,
                                                        T* __restrict__ a, int staged) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  const int ra = (na + 3) & ~3;
-  T* coef = reinterpret_cast<T*>(sm_raw);
-  T* W4 = coef + (size_t)ra * na * 4;
-  T* bufs = W4 + (size_t)ed * 4;
-  for (int idx = threadIdx.x; idx < 4 * ed; idx += blockDim.x) W4[idx] = Wphi[(idx & 3) * ed + (idx >> 2)];
+  T* beta = reinterpret_cast<T*>(sm_raw);
+  T* mono = beta + (size_t)ed * 4;
+  T* monosa = mono + (size_t)na * kMono;
+  T* xpow = monosa + (size_t)na * kMono;
+  T* YB = xpow + (size_t)na * 4;
+  T* bufs = YB + (size_t)ed * kMono;
+  angle_beta(beta, Wphi, ed);
   const int nrows = staged ? 1 : 0;
   int i = blockIdx.x;
   if (i < n) angle_fetch(angle_buf(bufs, na, ed, nrows, 0), ca, ed, (long long)i * nmax, (long long)i * ca, sa, rh, q, q);
+  const int cl = threadIdx.x % kAngCols, half = threadIdx.x / kAngCols;
   for (int it = 0; i < n; ++it, i += gridDim.x) {
     const AngleBuf<T> cur = angle_buf(bufs, na, ed, nrows, it & 1);
     const int nang = angle_next(cur, angle_buf(bufs, na, ed, nrows, (it + 1) & 1), i, n, nmax, ca, ed, sa,
@@ -383,52 +462,29 @@ __global__ void __launch_bounds__(kAngThreads) k_angle(int n, int nmax, int na, 
     const long long abase = (long long)i * ca;
     const T* qs = staged ? cur.r0 : q + abase * ed;
     const int ld = staged ? ed + 1 : ed;
-    angle_coef(coef, na, ra, nang, cur.sa, cur.rh, inv_na);
+    angle_mono(mono, monosa, xpow, nang, cur.sa, cur.rh);
     __syncthreads();
-    const int cg = threadIdx.x & 15;
-    const int ntile = (nang + 3) >> 2;
-    for (int cb = 0; cb < ed; cb += 64)
-      for (int rt = threadIdx.x >> 4; rt < ntile; rt += kAngThreads / 16) {
-        const int p0 = 4 * rt;
-        int cc[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) cc[j] = min(cb + cg + 16 * j, ed - 1);
-        T acc[4][4][4];
-#pragma unroll
-        for (int x = 0; x < 4; ++x)
-#pragma unroll
-          for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int l = 0; l < 4; ++l) acc[x][j][l] = T(0);
-        for (int k = 0; k < nang; ++k) {
-          T qv[4];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) qv[j] = qs[k * ld + cc[j]];
-#pragma unroll
-          for (int x = 0; x < 4; ++x) {
-            T cf[4];
-            ld4(coef + ((size_t)(p0 + x) * na + k) * 4, cf);
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-              fma4(acc[x][j], cf, qv[j]);
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int c = cb + cg + 16 * j;
-          if (c >= ed) continue;
-          T w[4];
-          ld4(W4 + 4 * c, w);
-#pragma unroll
-          for (int x = 0; x < 4; ++x)
-            if (p0 + x < nang)
-              a[(abase + p0 + x) * ed + c] =
-                  w[0] * acc[x][j][0] + w[1] * acc[x][j][1] + w[2] * acc[x][j][2] + w[3] * acc[x][j][3];
-        }
+    for (int c = cl; c < ed; c += kAngCols) {   // YB: half of the monomials per thread
+      if (half == 0) angle_ysum<0>(YB, beta, monosa, nang, qs, ld, c, T(1));
+      else angle_ysum<1>(YB, beta, monosa, nang, qs, ld, c, T(1));
+    }
+    __syncthreads();
+    for (int c = cl; c < ed; c += kAngCols) {   // a: every second slot per thread
+      T yb[kMono], b[4];
+      ld20(YB + c * kMono, yb);
+      ld4(beta + 4 * c, b);
+      for (int p = half; p < nang; p += 2) {
+        T m[kMono], xp[4];
+        ld20(mono + p * kMono, m);
+        ld4(xpow + 4 * p, xp);
+        const T z = b[0] + b[1] * xp[1] + b[2] * xp[2] + b[3] * xp[3];
+        const T sp = cur.sa[p];
+        a[(abase + p) * ed + c] = inv_na * sp * (dot_n<kMono>(m, yb) - sp * qs[p * ld + c] * z);
       }
+    }
     for (int idx = threadIdx.x; idx < (ca - nang) * ed; idx += blockDim.x)
       a[(abase + nang) * ed + idx] = T(0);
-    __syncthreads();   // the coefficients and this buffer are rewritten next
+    __syncthreads();   // the monomials, YB and this buffer are rewritten next
   }
 }
 
@@ -517,11 +573,21 @@ __global__ void k_angle_out_bwd4(long long PA, int ed, int nmax, int ca, const T
   if (l16 == 0 && s > T(0)) dsa_e[e] += acc;
 }
 
-// (c) adjoint of a_p for each atom: dq, then the switch and unit-vector
-// terms through dcoef_pkl = sum_c da_p[c] Wphi[l][c] q_k[c].  q, da and dq
-// hold the angle rows only (row i ca + p).  Shared memory: the coefficients
-// (ra x na x 4; overwritten by dcoef once dq is done), Wphi by column (ed x
-// 4), then two slot-data buffers (da and q rows staged when `staged`).
+// (c) adjoint of a_p for each atom, with g_p[c] = dE/da_p[c] (da) and the
+// forward's YB recomputed:
+//   dY_m[c] = (1/na) mult(m) beta_|m|[c] sum_p sa_p u_p^m g_p[c]            (dYB)
+//   dq_k[c] = sa_k (sum_m u_k^m dY_m[c] - (1/na) sa_k g_k[c] Z_k[c]),
+//             Z_k[c] = sum_n beta_n[c] (u_k . u_k)^n
+// and per slot s, from H_m(s) = sum_c g_s[c] YB_m[c], K_m(s) = sum_c q_s[c] dY_m[c]
+// and D_n(s) = sum_c g_s[c] q_s[c] beta_n[c]:
+//   dE/dsa_s  = (1/na) (sum_m u_s^m H_m - 2 sa_s sum_n D_n x^n) + sum_m u_s^m K_m
+//   dE/du_s^m = sa_s ((1/na) H_m + K_m)
+//   dE/dx     = -(1/na) sa_s^2 (D_1 + 2 D_2 x + 3 D_3 x^2),   x = u_s . u_s
+// dE/du_s then follows by differentiating the monomials (plus 2 u_s dE/dx).
+// q, da and dq hold the angle rows only (row i ca + p).  Shared memory: beta,
+// the monomials (as in the forward), YB and dYB (ed x 20 each), the per-slot
+// sums H, K, D (na x 44), then two slot-data buffers (da and q rows staged
+// when `staged`).
 template <typename T>
 __global__ void __launch_bounds__(kAngThreads) k_angle_bwd(int n, int nmax, int na, int ca, int ed, T inv_na,
                                                            const T* __restrict__ sa,
@@ -532,16 +598,22 @@ __global__ void __launch_bounds__(kAngThreads) k_angle_bwd(int n, int nmax, int 
                                                            T* __restrict__ dq, T* __restrict__ dsa_e,
                                                            T* __restrict__ drh, int staged) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  const int ra = (na + 3) & ~3;
-  T* coef = reinterpret_cast<T*>(sm_raw);   // later dcoef
-  T* W4 = coef + (size_t)ra * na * 4;
-  T* bufs = W4 + (size_t)ed * 4;
-  for (int idx = threadIdx.x; idx < 4 * ed; idx += blockDim.x) W4[idx] = Wphi[(idx & 3) * ed + (idx >> 2)];
+  constexpr int kHKD = 2 * kMono + 4;
+  T* beta = reinterpret_cast<T*>(sm_raw);
+  T* mono = beta + (size_t)ed * 4;
+  T* monosa = mono + (size_t)na * kMono;
+  T* xpow = monosa + (size_t)na * kMono;
+  T* YB = xpow + (size_t)na * 4;
+  T* dYB = YB + (size_t)ed * kMono;
+  T* hkd = dYB + (size_t)ed * kMono;
+  T* bufs = hkd + (size_t)na * kHKD;
+  angle_beta(beta, Wphi, ed);
   const int nrows = staged ? 2 : 0;
   int i = blockIdx.x;
   if (i < n)
     angle_fetch(angle_buf(bufs, na, ed, nrows, 0), ca, ed, (long long)i * nmax, (long long)i * ca, sa, rh,
                 da, q);
+  const int cl = threadIdx.x % kAngCols, half = threadIdx.x / kAngCols;
   for (int it = 0; i < n; ++it, i += gridDim.x) {
     const AngleBuf<T> cur = angle_buf(bufs, na, ed, nrows, it & 1);
     const int nang = angle_next(cur, angle_buf(bufs, na, ed, nrows, (it + 1) & 1), i, n, nmax, ca, ed, sa,
@@ -550,135 +622,100 @@ __global__ void __launch_bounds__(kAngThreads) k_angle_bwd(int n, int nmax, int 
     const T* das = staged ? cur.r0 : da + abase * ed;
     const T* qs = staged ? cur.r1 : q + abase * ed;
     const int ld = staged ? ed + 1 : ed;
-    const T* gsa = cur.sa;
-    const T* grh = cur.rh;
-    angle_coef(coef, na, ra, nang, gsa, grh, inv_na);
+    angle_mono(mono, monosa, xpow, nang, cur.sa, cur.rh);
     __syncthreads();
-    const int ntile = (nang + 3) >> 2;
-    // dq_k[c] = sum_l Wphi[l][c] sum_p coef_pkl da_p[c]: a 4 x 4 block (slots
-    // k0.., columns cg + 16 j) per thread, summed over p
-    {
-      const int cg = threadIdx.x & 15;
-      for (int cb = 0; cb < ed; cb += 64)
-        for (int rt = threadIdx.x >> 4; rt < ntile; rt += kAngThreads / 16) {
-          const int k0 = 4 * rt;
-          int cc[4];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) cc[j] = min(cb + cg + 16 * j, ed - 1);
-          T acc[4][4][4];
-#pragma unroll
-          for (int x = 0; x < 4; ++x)
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-#pragma unroll
-              for (int l = 0; l < 4; ++l) acc[x][j][l] = T(0);
-          for (int p = 0; p < nang; ++p) {
-            T dv[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) dv[j] = das[p * ld + cc[j]];
-#pragma unroll
-            for (int x = 0; x < 4; ++x) {
-              T cf[4];
-              ld4(coef + ((size_t)p * na + k0 + x) * 4, cf);
-#pragma unroll
-              for (int j = 0; j < 4; ++j)
-                fma4(acc[x][j], cf, dv[j]);
-            }
-          }
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int c = cb + cg + 16 * j;
-            if (c >= ed) continue;
-            T w[4];
-            ld4(W4 + 4 * c, w);
-#pragma unroll
-            for (int x = 0; x < 4; ++x)
-              if (k0 + x < nang)
-                dq[(abase + k0 + x) * ed + c] =
-                    w[0] * acc[x][j][0] + w[1] * acc[x][j][1] + w[2] * acc[x][j][2] + w[3] * acc[x][j][3];
-          }
-        }
-      for (int idx = threadIdx.x; idx < (ca - nang) * ed; idx += blockDim.x)
-        dq[(abase + nang) * ed + idx] = T(0);
+    for (int c = cl; c < ed; c += kAngCols) {   // YB and dYB, half of the monomials per thread
+      if (half == 0) {
+        angle_ysum<0>(YB, beta, monosa, nang, qs, ld, c, T(1));
+        angle_ysum<0>(dYB, beta, monosa, nang, das, ld, c, inv_na);
+      } else {
+        angle_ysum<1>(YB, beta, monosa, nang, qs, ld, c, T(1));
+        angle_ysum<1>(dYB, beta, monosa, nang, das, ld, c, inv_na);
+      }
     }
-    __syncthreads();   // the coefficients are read for the last time above
-    // dcoef_pkl = sum_c da_p[c] Wphi[l][c] q_k[c]: a 2 x 4 block of (p, k) per
-    // thread (enough blocks to occupy the whole CTA), summed over the columns
-    // in order; written over the coefficients
-    T* dcoef = coef;
-    const int nkt = ntile, npt = (nang + 1) >> 1;
-    for (int tile = threadIdx.x; tile < npt * nkt; tile += blockDim.x) {
-      const int p0 = 2 * (tile / nkt), k0 = 4 * (tile % nkt);
-      int pr[2], kr[4];
-#pragma unroll
-      for (int x = 0; x < 2; ++x) pr[x] = min(p0 + x, nang - 1) * ld;
-#pragma unroll
-      for (int y = 0; y < 4; ++y) kr[y] = min(k0 + y, nang - 1) * ld;
-      T acc[2][4][4];
+    __syncthreads();
+    for (int c = cl; c < ed; c += kAngCols) {   // dq: every second slot per thread
+      T dyb[kMono], b[4];
+      ld20(dYB + c * kMono, dyb);
+      ld4(beta + 4 * c, b);
+      for (int p = half; p < nang; p += 2) {
+        T m[kMono], xp[4];
+        ld20(mono + p * kMono, m);
+        ld4(xpow + 4 * p, xp);
+        const T z = b[0] + b[1] * xp[1] + b[2] * xp[2] + b[3] * xp[3];
+        const T sp = cur.sa[p];
+        dq[(abase + p) * ed + c] = sp * (dot_n<kMono>(m, dyb) - inv_na * sp * das[p * ld + c] * z);
+      }
+    }
+    for (int idx = threadIdx.x; idx < (ca - nang) * ed; idx += blockDim.x)
+      dq[(abase + nang) * ed + idx] = T(0);
+    // H, K (and D) of two slots and four monomials per thread, summed over the
+    // columns in order
+    const int npair = (nang + 1) >> 1;
+    for (int tile = threadIdx.x; tile < npair * 5; tile += blockDim.x) {
+      const int p0 = 2 * (tile / 5), mb = 4 * (tile % 5);
+      const int p1 = min(p0 + 1, nang - 1);
+      T h[2][4], k[2][4], d[2][4];
 #pragma unroll
       for (int x = 0; x < 2; ++x)
 #pragma unroll
-        for (int y = 0; y < 4; ++y)
-#pragma unroll
-          for (int l = 0; l < 4; ++l) acc[x][y][l] = T(0);
-#pragma unroll 2
+        for (int j = 0; j < 4; ++j) h[x][j] = k[x][j] = d[x][j] = T(0);
       for (int c = 0; c < ed; ++c) {
-        T dv[2], qv[4], w[4];
+        const T g[2] = {das[p0 * ld + c], das[p1 * ld + c]};
+        const T qv[2] = {qs[p0 * ld + c], qs[p1 * ld + c]};
+        T yb[4], dy[4];
+        ld4(YB + c * kMono + mb, yb);
+        ld4(dYB + c * kMono + mb, dy);
 #pragma unroll
-        for (int x = 0; x < 2; ++x) dv[x] = das[pr[x] + c];
+        for (int x = 0; x < 2; ++x) {
+          fma_n<4>(h[x], yb, g[x]);
+          fma_n<4>(k[x], dy, qv[x]);
+        }
+        if (mb == 0) {
+          T b[4];
+          ld4(beta + 4 * c, b);
 #pragma unroll
-        for (int y = 0; y < 4; ++y) qv[y] = qs[kr[y] + c];
-        ld4(W4 + 4 * c, w);
-#pragma unroll
-        for (int x = 0; x < 2; ++x)
-#pragma unroll
-          for (int y = 0; y < 4; ++y) {
-            const T xy = dv[x] * qv[y];
-            fma4(acc[x][y], w, xy);
-          }
+          for (int x = 0; x < 2; ++x) fma_n<4>(d[x], b, g[x] * qv[x]);
+        }
       }
 #pragma unroll
-      for (int x = 0; x < 2; ++x)
+      for (int x = 0; x < 2; ++x) {
+        const int p = p0 + x;
+        if (p >= nang) continue;
 #pragma unroll
-        for (int y = 0; y < 4; ++y) {
-          const int p = p0 + x, k = k0 + y;
-          if (p >= nang || k >= nang) continue;
-#pragma unroll
-          for (int l = 0; l < 4; ++l) dcoef[((size_t)p * na + k) * 4 + l] = p == k ? T(0) : acc[x][y][l];
+        for (int j = 0; j < 4; ++j) {
+          hkd[p * kHKD + mb + j] = h[x][j];
+          hkd[p * kHKD + kMono + mb + j] = k[x][j];
+          if (mb == 0) hkd[p * kHKD + 2 * kMono + j] = d[x][j];
         }
+      }
     }
     __syncthreads();
-    // switch and unit-vector terms: one warp per angle slot p, lanes over the
-    // partners k, then a fixed-order warp reduction
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int p = warp; p < nang; p += nw) {
-      const T* rp = grh + 3 * p;
-      const T sp = gsa[p];
-      T dsp = T(0), dr[3] = {T(0), T(0), T(0)};
-      for (int k = lane; k < nang; k += 32) {
-        if (k == p) continue;
-        const T* rk = grh + 3 * k;
-        T P[4], dP[4];
-        legendre4(rp[0] * rk[0] + rp[1] * rk[1] + rp[2] * rk[2], P, dP);
-        // p as the first index (dcoef_pk) and as the second (dcoef_kp)
-        const T* d1 = dcoef + ((size_t)p * na + k) * 4;
-        const T* d2 = dcoef + ((size_t)k * na + p) * 4;
-        const T sk = gsa[k];
-        T dc = T(0);
-        for (int l = 0; l < 4; ++l) {
-          dsp += (d1[l] + d2[l]) * inv_na * sk * P[l];
-          dc += (d1[l] + d2[l]) * inv_na * sp * sk * dP[l];
-        }
-        for (int a = 0; a < 3; ++a) dr[a] += dc * rk[a];
-      }
-      dsp = warp_sum(dsp);
-      for (int a = 0; a < 3; ++a) dr[a] = warp_sum(dr[a]);
-      if (lane == 0) {
-        dsa_e[base + p] += dsp;
-        for (int a = 0; a < 3; ++a) drh[3 * (base + p) + a] += dr[a];
-      }
+    // switch and unit-vector terms: one thread per angle slot
+    for (int s = threadIdx.x; s < nang; s += blockDim.x) {
+      T m[kMono], hh[kMono], kk[kMono], dd[4], xp[4];
+      ld20(mono + s * kMono, m);
+      ld20(hkd + s * kHKD, hh);
+      ld20(hkd + s * kHKD + kMono, kk);
+      ld4(hkd + s * kHKD + 2 * kMono, dd);
+      ld4(xpow + 4 * s, xp);
+      const T sp = cur.sa[s];
+      const T dsp = inv_na * (dot_n<kMono>(m, hh) -
+                              T(2) * sp * (dd[0] + dd[1] * xp[1] + dd[2] * xp[2] + dd[3] * xp[3])) +
+                    dot_n<kMono>(m, kk);
+      T dm[kMono];
+#pragma unroll
+      for (int j = 0; j < kMono; ++j) dm[j] = sp * (inv_na * hh[j] + kk[j]);
+      const T dx = -inv_na * sp * sp * (dd[1] + T(2) * dd[2] * xp[1] + T(3) * dd[3] * xp[2]);
+      const T ux = cur.rh[3 * s], uy = cur.rh[3 * s + 1], uz = cur.rh[3 * s + 2];
+      T dr[3];
+      monomial_grad(ux, uy, uz, dm, dr);
+      dsa_e[base + s] += dsp;
+      drh[3 * (base + s)] += dr[0] + T(2) * dx * ux;
+      drh[3 * (base + s) + 1] += dr[1] + T(2) * dx * uy;
+      drh[3 * (base + s) + 2] += dr[2] + T(2) * dx * uz;
     }
-    __syncthreads();   // dcoef and this buffer are rewritten next
+    __syncthreads();   // the monomials, the sums and this buffer are rewritten next
   }
 }
 
@@ -1200,20 +1237,23 @@ bool PlainGf<T>::init(const GfDims& m, const double* w, int n_atoms, const int* 
     ok = dalloc(&hh_[l], N * Nd, err) && dalloc(&uu_[l], N * Ed, err) &&
          dalloc(&mm_[l], N * Ed, err) && dalloc(&vv_[l], P * Ed, err) && dalloc(&qq_[l], PA * Ed, err) &&
          dalloc(&tt_[l], PA * Ed, err);
-  // the angle kernels hold the coefficients and Wphi in shared memory, with
-  // two slot-data buffers (switches and unit vectors, plus the slots' rows
-  // when they fit in 227 KB)
-  const size_t kMaxSmem = 232448, ra = (size_t)((m.na + 3) & ~3),
-               fixed = (ra * m.na * 4 + (size_t)m.ed * 4) * sizeof(T),
-               geo = 2 * (size_t)m.na * 4 * sizeof(T), arows = 2 * (size_t)m.na * (m.ed + 1) * sizeof(T);
-  if (fixed + geo > kMaxSmem) {
-    *err = "graph model: the angle coefficients do not fit in shared memory";
+  // the angle kernels hold their monomial sums in shared memory, with two
+  // slot-data buffers (switches and unit vectors, plus the slots' rows when
+  // they fit in 227 KB); fixed parts: beta (ed x 4), the slots' monomials
+  // (na x 44) and YB (ed x 20), and in the adjoint also dYB (ed x 20) and the
+  // per-slot sums (na x 44)
+  const size_t kMaxSmem = 232448, na_ = (size_t)m.na, ed_ = (size_t)m.ed,
+               fixed = (4 * ed_ + (2 * kMono + 4) * na_ + kMono * ed_) * sizeof(T),
+               fixed_bwd = fixed + (kMono * ed_ + (2 * kMono + 4) * na_) * sizeof(T),
+               geo = 2 * na_ * 4 * sizeof(T), arows = 2 * na_ * (ed_ + 1) * sizeof(T);
+  if (fixed_bwd + geo > kMaxSmem) {
+    *err = "graph model: the angle channel's sums do not fit in shared memory";
     return false;
   }
   angle_staged_ = fixed + geo + arows <= kMaxSmem ? 1 : 0;
   angle_smem_ = fixed + geo + (angle_staged_ ? arows : 0);
-  angle_bwd_staged_ = fixed + geo + 2 * arows <= kMaxSmem ? 1 : 0;
-  angle_bwd_smem_ = fixed + geo + (angle_bwd_staged_ ? 2 * arows : 0);
+  angle_bwd_staged_ = fixed_bwd + geo + 2 * arows <= kMaxSmem ? 1 : 0;
+  angle_bwd_smem_ = fixed_bwd + geo + (angle_bwd_staged_ ? 2 * arows : 0);
   const int angle_smem = (int)angle_smem_, angle_bwd_smem = (int)angle_bwd_smem_;
   if (cudaFuncSetAttribute(k_angle<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, angle_smem) !=
           cudaSuccess ||

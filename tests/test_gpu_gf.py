@@ -177,13 +177,14 @@ def test_gf_mixed_md_tracks_fp32():
 
 @pytest.mark.parametrize("na,ed,mode", [(40, 64, "rows staged in both kernels"),
                                         (64, 16, "rows staged in both kernels, 64 slots"),
-                                        (64, 64, "the adjoint reads its rows from global memory"),
-                                        (64, 128, "both kernels read their rows from global memory")])
+                                        (64, 64, "rows staged in both kernels, 64 slots, width 64"),
+                                        (64, 128, "the adjoint reads its rows from global memory"),
+                                        (64, 192, "both kernels read their rows from global memory")])
 def test_gf_angle_channel_shared_memory_variants_fp64(na, ed, mode):
-    """The angle kernels hold the coefficients in shared memory with two
+    """The angle kernels hold their monomial sums in shared memory with two
     buffers of slot data, the slots' q and da rows included when they fit:
     with FP64 and 64 angle slots the adjoint's rows stop fitting at edge width
-    64 and the forward's at 128.  Every variant must give the oracle's result."""
+    128 and the forward's at 192.  Every variant must give the oracle's result."""
     m = replace(C.GRAPH_MODEL, node=32, edge=ed, n_layers=2, f1=32, f2=32, f3=16, nmax=96, na=na)
     s = serving_system(96, 7)
     w = weights(m, 5, 0.2)
