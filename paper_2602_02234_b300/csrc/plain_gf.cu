@@ -267,6 +267,10 @@ __device__ __forceinline__ T dot_n(const T* a, const T* b) {
 // the pairwise form as well; it costs two passes of 20 multiply-adds per
 // (slot, column) instead of four per (slot, partner, column).
 constexpr int kMono = 20;
+// sa-weighted monomials are stored in two halves of 10 at offsets 0 and 12 of
+// a 24-wide row, so that each half starts on a 16-byte boundary
+constexpr int kMonoSa = 24;
+__host__ __device__ constexpr int monosa_at(int m) { return m < 10 ? m : m + 2; }
 // the 20 monomials of degree <= 3 in this order: 1 | x y z | xx yy zz xy xz yz |
 // xxx yyy zzz xxy xxz xyy yyz xzz yzz xyz
 __host__ __device__ constexpr int mono_deg(int m) { return m == 0 ? 0 : m < 4 ? 1 : m < 10 ? 2 : 3; }
@@ -311,8 +315,8 @@ __device__ void angle_beta(T* beta, const T* Wphi, int ed) {
     beta[4 * c + 3] = T(2.5) * w3;
   }
 }
-// per angle slot s < nang: mono[s] = u_s^m, monosa[s] = sa_s u_s^m, and
-// xpow[s] = (u_s . u_s)^n, n < 4
+// per angle slot s < nang: mono[s] = u_s^m, monosa[s] = sa_s u_s^m (24-wide
+// rows), and xpow[s] = (u_s . u_s)^n, n < 4
 template <typename T>
 __device__ void angle_mono(T* mono, T* monosa, T* xpow, int nang, const T* gsa, const T* grh) {
   for (int s = threadIdx.x; s < nang; s += blockDim.x) {
@@ -323,7 +327,7 @@ __device__ void angle_mono(T* mono, T* monosa, T* xpow, int nang, const T* gsa, 
 #pragma unroll
     for (int i = 0; i < kMono; ++i) {
       mono[s * kMono + i] = m[i];
-      monosa[s * kMono + i] = sp * m[i];
+      monosa[s * kMonoSa + monosa_at(i)] = sp * m[i];
     }
     xpow[4 * s] = T(1);
     xpow[4 * s + 1] = xx;
@@ -333,24 +337,31 @@ __device__ void angle_mono(T* mono, T* monosa, T* xpow, int nang, const T* gsa, 
 }
 // One half (monomials 10 H .. 10 H + 9) of the weighted sums of column c over
 // the angle slots: out[c][m] = scale mult(m) beta_|m|[c] sum_k monosa[k][m] x_k[c]
-template <int H, typename T>
-__device__ __forceinline__ void angle_ysum(T* out, const T* beta, const T* monosa, int nang, const T* xs,
-                                           int ld, int c, T scale) {
-  T acc[10];
+// for NX arrays x at once (the monomials are read once for all of them)
+template <int H, int NX, typename T>
+__device__ __forceinline__ void angle_ysum(T* const* out, const T* beta, const T* monosa, int nang,
+                                           const T* const* xs, int ld, int c, const T* scale) {
+  T acc[NX][10];
 #pragma unroll
-  for (int j = 0; j < 10; ++j) acc[j] = T(0);
+  for (int x = 0; x < NX; ++x)
+#pragma unroll
+    for (int j = 0; j < 10; ++j) acc[x][j] = T(0);
   for (int k = 0; k < nang; ++k) {
-    const T xv = xs[k * ld + c];
     T w[10];
+    const T* row = monosa + k * kMonoSa + 12 * H;
+    ld4(row, w);
+    ld4(row + 4, w + 4);
+    ld2(row + 8, w + 8);
 #pragma unroll
-    for (int j = 0; j < 10; j += 2) ld2(monosa + k * kMono + 10 * H + j, w + j);
-    fma_n<10>(acc, w, xv);
+    for (int x = 0; x < NX; ++x) fma_n<10>(acc[x], w, xs[x][k * ld + c]);
   }
   T b[4];
   ld4(beta + 4 * c, b);
 #pragma unroll
-  for (int j = 0; j < 10; ++j)
-    out[c * kMono + 10 * H + j] = scale * T(mono_mult(10 * H + j)) * b[mono_deg(10 * H + j)] * acc[j];
+  for (int x = 0; x < NX; ++x)
+#pragma unroll
+    for (int j = 0; j < 10; ++j)
+      out[x][c * kMono + 10 * H + j] = scale[x] * T(mono_mult(10 * H + j)) * b[mono_deg(10 * H + j)] * acc[x][j];
 }
 
 // Asynchronous element copies global -> shared (cp.async, completion per
@@ -372,43 +383,28 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // The angle kernels are persistent: a block loops over atoms i = blockIdx.x,
 // + gridDim.x, ... and, while it works on one atom, copies the next atom's
-// slot data into the other of two buffers.  A buffer holds the slots'
-// switches (na), unit vectors (3 na) and, when staged, rows of up to two
-// (rows x ed) arrays with stride ed + 1 (the rows of one column then fall in
-// different banks).
+// slot switches (na) and unit vectors (3 na) into the other of two buffers.
+// The slots' q and da rows are read from global memory where they are used
+// (through L1): staging them in shared memory as well cost resident blocks
+// and made both kernels slower.
 template <typename T>
 struct AngleBuf {
-  T *sa, *rh, *r0, *r1;
+  T *sa, *rh;
 };
 template <typename T>
-__device__ __forceinline__ AngleBuf<T> angle_buf(T* start, int na, int ed, int nrows, int b) {
-  const size_t one = 4 * (size_t)na + (size_t)nrows * na * (ed + 1);
-  T* p = start + (size_t)b * one;
+__device__ __forceinline__ AngleBuf<T> angle_buf(T* start, int na, int b) {
+  T* p = start + (size_t)b * 4 * na;
   AngleBuf<T> u;
   u.sa = p;
   u.rh = p + na;
-  u.r0 = nrows > 0 ? p + 4 * (size_t)na : nullptr;
-  u.r1 = nrows > 1 ? u.r0 + (size_t)na * (ed + 1) : nullptr;
   return u;
 }
 // start the copies of atom i's slot data into u (one commit group per thread)
 template <typename T>
-__device__ __forceinline__ void angle_fetch(const AngleBuf<T>& u, int ca, int ed, long long base,
-                                            long long abase, const T* sa, const T* rh, const T* x0,
-                                            const T* x1) {
+__device__ __forceinline__ void angle_fetch(const AngleBuf<T>& u, int ca, long long base, const T* sa,
+                                            const T* rh) {
   if (threadIdx.x < ca) cp_async_elem(u.sa + threadIdx.x, sa + base + threadIdx.x);
   for (int idx = threadIdx.x; idx < 3 * ca; idx += blockDim.x) cp_async_elem(u.rh + idx, rh + 3 * base + idx);
-  const int total = ca * ed;
-  if (u.r0)
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-      const int p = idx / ed;
-      cp_async_elem(u.r0 + p * (ed + 1) + (idx - p * ed), x0 + abase * ed + idx);
-    }
-  if (u.r1)
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-      const int p = idx / ed;
-      cp_async_elem(u.r1 + p * (ed + 1) + (idx - p * ed), x1 + abase * ed + idx);
-    }
   cp_async_commit();
 }
 // Next atom's copies started, this atom's awaited; returns the angle count
@@ -417,11 +413,10 @@ __device__ __forceinline__ void angle_fetch(const AngleBuf<T>& u, int ca, int ed
 // switch t itself, so it may read it before the barrier.
 template <typename T>
 __device__ __forceinline__ int angle_next(const AngleBuf<T>& cur, const AngleBuf<T>& nxt, int i, int n,
-                                          int nmax, int ca, int ed, const T* sa, const T* rh,
-                                          const T* x0, const T* x1) {
+                                          int nmax, int ca, const T* sa, const T* rh) {
   const int nx = i + gridDim.x;
   if (nx < n) {
-    angle_fetch(nxt, ca, ed, (long long)nx * nmax, (long long)nx * ca, sa, rh, x0, x1);
+    angle_fetch(nxt, ca, (long long)nx * nmax, sa, rh);
     cp_async_wait<1>();
   } else {
     cp_async_wait<0>();
@@ -434,39 +429,40 @@ __device__ __forceinline__ int angle_next(const AngleBuf<T>& cur, const AngleBuf
 // hold the angle rows only: slot p < ca of atom i at row i ca + p (ca =
 // min(na, nmax)); rows from the atom's angle count up to ca get a = 0.
 // Shared memory: beta (ed x 4), the slots' monomials, sa-weighted monomials
-// and (u . u)^n (na x 20, na x 20, na x 4), YB (ed x 20), then two slot-data
-// buffers (q rows staged when `staged`).
+// and (u . u)^n (na x 20, na x 24, na x 4), YB (ed x 20), then two slot-data
+// buffers.
 template <typename T>
 __global__ void __launch_bounds__(kAngThreads) k_angle(int n, int nmax, int na, int ca, int ed, T inv_na,
                                                        const T* __restrict__ sa,
                                                        const T* __restrict__ rh,
                                                        const T* __restrict__ q,
                                                        const T* __restrict__ Wphi,
-                                                       T* __restrict__ a, int staged) {
+                                                       T* __restrict__ a) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* beta = reinterpret_cast<T*>(sm_raw);
   T* mono = beta + (size_t)ed * 4;
   T* monosa = mono + (size_t)na * kMono;
-  T* xpow = monosa + (size_t)na * kMono;
+  T* xpow = monosa + (size_t)na * kMonoSa;
   T* YB = xpow + (size_t)na * 4;
   T* bufs = YB + (size_t)ed * kMono;
   angle_beta(beta, Wphi, ed);
-  const int nrows = staged ? 1 : 0;
   int i = blockIdx.x;
-  if (i < n) angle_fetch(angle_buf(bufs, na, ed, nrows, 0), ca, ed, (long long)i * nmax, (long long)i * ca, sa, rh, q, q);
+  if (i < n) angle_fetch(angle_buf(bufs, na, 0), ca, (long long)i * nmax, sa, rh);
   const int cl = threadIdx.x % kAngCols, half = threadIdx.x / kAngCols;
   for (int it = 0; i < n; ++it, i += gridDim.x) {
-    const AngleBuf<T> cur = angle_buf(bufs, na, ed, nrows, it & 1);
-    const int nang = angle_next(cur, angle_buf(bufs, na, ed, nrows, (it + 1) & 1), i, n, nmax, ca, ed, sa,
-                                rh, q, q);
+    const AngleBuf<T> cur = angle_buf(bufs, na, it & 1);
+    const int nang = angle_next(cur, angle_buf(bufs, na, (it + 1) & 1), i, n, nmax, ca, sa, rh);
     const long long abase = (long long)i * ca;
-    const T* qs = staged ? cur.r0 : q + abase * ed;
-    const int ld = staged ? ed + 1 : ed;
+    const T* qs = q + abase * ed;
+    const int ld = ed;
     angle_mono(mono, monosa, xpow, nang, cur.sa, cur.rh);
     __syncthreads();
     for (int c = cl; c < ed; c += kAngCols) {   // YB: half of the monomials per thread
-      if (half == 0) angle_ysum<0>(YB, beta, monosa, nang, qs, ld, c, T(1));
-      else angle_ysum<1>(YB, beta, monosa, nang, qs, ld, c, T(1));
+      T* const out[1] = {YB};
+      const T* const xs[1] = {qs};
+      const T one[1] = {T(1)};
+      if (half == 0) angle_ysum<0, 1>(out, beta, monosa, nang, xs, ld, c, one);
+      else angle_ysum<1, 1>(out, beta, monosa, nang, xs, ld, c, one);
     }
     __syncthreads();
     for (int c = cl; c < ed; c += kAngCols) {   // a: every second slot per thread
@@ -586,8 +582,7 @@ __global__ void k_angle_out_bwd4(long long PA, int ed, int nmax, int ca, const T
 // dE/du_s then follows by differentiating the monomials (plus 2 u_s dE/dx).
 // q, da and dq hold the angle rows only (row i ca + p).  Shared memory: beta,
 // the monomials (as in the forward), YB and dYB (ed x 20 each), the per-slot
-// sums H, K, D (na x 44), then two slot-data buffers (da and q rows staged
-// when `staged`).
+// sums H, K, D (na x 44), then two slot-data buffers.
 template <typename T>
 __global__ void __launch_bounds__(kAngThreads) k_angle_bwd(int n, int nmax, int na, int ca, int ed, T inv_na,
                                                            const T* __restrict__ sa,
@@ -596,42 +591,36 @@ __global__ void __launch_bounds__(kAngThreads) k_angle_bwd(int n, int nmax, int 
                                                            const T* __restrict__ Wphi,
                                                            const T* __restrict__ da,
                                                            T* __restrict__ dq, T* __restrict__ dsa_e,
-                                                           T* __restrict__ drh, int staged) {
+                                                           T* __restrict__ drh) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   constexpr int kHKD = 2 * kMono + 4;
   T* beta = reinterpret_cast<T*>(sm_raw);
   T* mono = beta + (size_t)ed * 4;
   T* monosa = mono + (size_t)na * kMono;
-  T* xpow = monosa + (size_t)na * kMono;
+  T* xpow = monosa + (size_t)na * kMonoSa;
   T* YB = xpow + (size_t)na * 4;
   T* dYB = YB + (size_t)ed * kMono;
   T* hkd = dYB + (size_t)ed * kMono;
   T* bufs = hkd + (size_t)na * kHKD;
   angle_beta(beta, Wphi, ed);
-  const int nrows = staged ? 2 : 0;
   int i = blockIdx.x;
-  if (i < n)
-    angle_fetch(angle_buf(bufs, na, ed, nrows, 0), ca, ed, (long long)i * nmax, (long long)i * ca, sa, rh,
-                da, q);
+  if (i < n) angle_fetch(angle_buf(bufs, na, 0), ca, (long long)i * nmax, sa, rh);
   const int cl = threadIdx.x % kAngCols, half = threadIdx.x / kAngCols;
   for (int it = 0; i < n; ++it, i += gridDim.x) {
-    const AngleBuf<T> cur = angle_buf(bufs, na, ed, nrows, it & 1);
-    const int nang = angle_next(cur, angle_buf(bufs, na, ed, nrows, (it + 1) & 1), i, n, nmax, ca, ed, sa,
-                                rh, da, q);
+    const AngleBuf<T> cur = angle_buf(bufs, na, it & 1);
+    const int nang = angle_next(cur, angle_buf(bufs, na, (it + 1) & 1), i, n, nmax, ca, sa, rh);
     const long long base = (long long)i * nmax, abase = (long long)i * ca;
-    const T* das = staged ? cur.r0 : da + abase * ed;
-    const T* qs = staged ? cur.r1 : q + abase * ed;
-    const int ld = staged ? ed + 1 : ed;
+    const T* das = da + abase * ed;
+    const T* qs = q + abase * ed;
+    const int ld = ed;
     angle_mono(mono, monosa, xpow, nang, cur.sa, cur.rh);
     __syncthreads();
     for (int c = cl; c < ed; c += kAngCols) {   // YB and dYB, half of the monomials per thread
-      if (half == 0) {
-        angle_ysum<0>(YB, beta, monosa, nang, qs, ld, c, T(1));
-        angle_ysum<0>(dYB, beta, monosa, nang, das, ld, c, inv_na);
-      } else {
-        angle_ysum<1>(YB, beta, monosa, nang, qs, ld, c, T(1));
-        angle_ysum<1>(dYB, beta, monosa, nang, das, ld, c, inv_na);
-      }
+      T* const out[2] = {YB, dYB};
+      const T* const xs[2] = {qs, das};
+      const T sc[2] = {T(1), inv_na};
+      if (half == 0) angle_ysum<0, 2>(out, beta, monosa, nang, xs, ld, c, sc);
+      else angle_ysum<1, 2>(out, beta, monosa, nang, xs, ld, c, sc);
     }
     __syncthreads();
     for (int c = cl; c < ed; c += kAngCols) {   // dq: every second slot per thread
@@ -1088,8 +1077,7 @@ class PlainGf : public Model {
   int* flags_ = nullptr;
   const unsigned char* seed_ = nullptr;   // energy seed (device, optional)
   // shared-memory variants of the angle kernels (see k_angle, k_angle_bwd):
-  // the slots' rows staged in shared memory when they fit
-  int angle_staged_ = 0, angle_bwd_staged_ = 0, angle_grid_ = 1, angle_bwd_grid_ = 1;
+  int angle_grid_ = 1, angle_bwd_grid_ = 1;
   size_t angle_smem_ = 0, angle_bwd_smem_ = 0;
 
   template <typename U>
@@ -1238,22 +1226,19 @@ bool PlainGf<T>::init(const GfDims& m, const double* w, int n_atoms, const int* 
          dalloc(&mm_[l], N * Ed, err) && dalloc(&vv_[l], P * Ed, err) && dalloc(&qq_[l], PA * Ed, err) &&
          dalloc(&tt_[l], PA * Ed, err);
   // the angle kernels hold their monomial sums in shared memory, with two
-  // slot-data buffers (switches and unit vectors, plus the slots' rows when
-  // they fit in 227 KB); fixed parts: beta (ed x 4), the slots' monomials
-  // (na x 44) and YB (ed x 20), and in the adjoint also dYB (ed x 20) and the
-  // per-slot sums (na x 44)
+  // slot-data buffers (switches and unit vectors): beta (ed x 4), the slots'
+  // monomials (na x 48) and YB (ed x 20), and in the adjoint also dYB (ed x
+  // 20) and the per-slot sums (na x 44)
   const size_t kMaxSmem = 232448, na_ = (size_t)m.na, ed_ = (size_t)m.ed,
-               fixed = (4 * ed_ + (2 * kMono + 4) * na_ + kMono * ed_) * sizeof(T),
+               fixed = (4 * ed_ + (kMono + kMonoSa + 4) * na_ + kMono * ed_) * sizeof(T),
                fixed_bwd = fixed + (kMono * ed_ + (2 * kMono + 4) * na_) * sizeof(T),
-               geo = 2 * na_ * 4 * sizeof(T), arows = 2 * na_ * (ed_ + 1) * sizeof(T);
+               geo = 2 * na_ * 4 * sizeof(T);
   if (fixed_bwd + geo > kMaxSmem) {
     *err = "graph model: the angle channel's sums do not fit in shared memory";
     return false;
   }
-  angle_staged_ = fixed + geo + arows <= kMaxSmem ? 1 : 0;
-  angle_smem_ = fixed + geo + (angle_staged_ ? arows : 0);
-  angle_bwd_staged_ = fixed_bwd + geo + 2 * arows <= kMaxSmem ? 1 : 0;
-  angle_bwd_smem_ = fixed_bwd + geo + (angle_bwd_staged_ ? 2 * arows : 0);
+  angle_smem_ = fixed + geo;
+  angle_bwd_smem_ = fixed_bwd + geo;
   const int angle_smem = (int)angle_smem_, angle_bwd_smem = (int)angle_bwd_smem_;
   if (cudaFuncSetAttribute(k_angle<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, angle_smem) !=
           cudaSuccess ||
@@ -1339,7 +1324,7 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
       mm(g, st);
     }
     k_angle<T><<<angle_grid_, kAngThreads, angle_smem, st>>>(n, NM, NA, CA, Ed, inv_na, sa_, rh_, qq_[l],
-                                                             Wphi_[l], aa_, angle_staged_);
+                                                             Wphi_[l], aa_);
     if (angle_out_fused(l, st)) {
       --k;   // one launch instead of two
     } else {
@@ -1415,7 +1400,7 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
       mm(g, st);
     }
     k_angle_bwd<T><<<angle_bwd_grid_, kAngThreads, angle_bwd_smem, st>>>(
-        n, NM, NA, CA, Ed, inv_na, sa_, rh_, qq_[l], Wphi_[l], da_, dq_, dsa_e_, drh_, angle_bwd_staged_);
+        n, NM, NA, CA, Ed, inv_na, sa_, rh_, qq_[l], Wphi_[l], da_, dq_, dsa_e_, drh_);
     {  // de1 = de + dq Wp^T, in place on the angle rows' slots (dq is 0 elsewhere)
       Gemm<T> g{};
       g.M = (int)PA; g.N = Ed; g.K = Ed;

@@ -175,16 +175,12 @@ def test_gf_mixed_md_tracks_fp32():
     assert np.all(np.isfinite(et)) and np.max(np.abs(et - et[0])) < 1e-3 * abs(et[0])
 
 
-@pytest.mark.parametrize("na,ed,mode", [(40, 64, "rows staged in both kernels"),
-                                        (64, 16, "rows staged in both kernels, 64 slots"),
-                                        (64, 64, "rows staged in both kernels, 64 slots, width 64"),
-                                        (64, 128, "the adjoint reads its rows from global memory"),
-                                        (64, 192, "both kernels read their rows from global memory")])
-def test_gf_angle_channel_shared_memory_variants_fp64(na, ed, mode):
-    """The angle kernels hold their monomial sums in shared memory with two
-    buffers of slot data, the slots' q and da rows included when they fit:
-    with FP64 and 64 angle slots the adjoint's rows stop fitting at edge width
-    128 and the forward's at 192.  Every variant must give the oracle's result."""
+@pytest.mark.parametrize("na,ed", [(40, 64), (64, 16), (64, 64), (64, 128), (64, 192)])
+def test_gf_angle_channel_shapes_fp64(na, ed):
+    """The angle kernels hold their monomial sums (per slot and per column) in
+    shared memory, sized by the angle-slot count and the edge width, and read
+    the slots' rows from global memory.  Up to 64 angle slots and widths from
+    16 to 192 must give the oracle's result (which sums over the slot pairs)."""
     m = replace(C.GRAPH_MODEL, node=32, edge=ed, n_layers=2, f1=32, f2=32, f3=16, nmax=96, na=na)
     s = serving_system(96, 7)
     w = weights(m, 5, 0.2)
