@@ -315,24 +315,11 @@ __device__ __forceinline__ void issue_copy(Bar& b, uint8_t* dst, const void* src
   tc::bulk_g2s(dst, src, bytes, reinterpret_cast<uint64_t*>(b.bar));
 }
 
-// Thread 0: L2 prefetch of the whole 16-byte units within [off, off + len)
-// bytes after `base`, in pieces of at most 32 KB.  A hint only: it never
-// reaches outside the range and nothing waits for it.
-__device__ __forceinline__ void prefetch_l2(const void* base, size_t off, size_t len) {
-  const uintptr_t a = reinterpret_cast<uintptr_t>(base) + off;
-  uintptr_t b = (a + 15) & ~static_cast<uintptr_t>(15);
-  const uintptr_t e = (a + len) & ~static_cast<uintptr_t>(15);
-  for (; b < e; b += 32768) {
-    const uintptr_t n = e - b < 32768 ? e - b : 32768;
-    tc::bulk_prefetch_l2(reinterpret_cast<const void*>(b), static_cast<uint32_t>(n));
-  }
-}
-
 // Thread 0: the selected neighbours of the atom this CTA takes next, into L2
 // while the current one runs (the environment set-up reads them first).
 __device__ __forceinline__ void prefetch_env(const Params& p, int next) {
-  prefetch_l2(p.sel_j, (size_t)next * p.nmax * sizeof(int), (size_t)p.nmax * sizeof(int));
-  prefetch_l2(p.sel_r, (size_t)next * p.nmax * 3 * sizeof(double), (size_t)p.nmax * 3 * sizeof(double));
+  tc::prefetch_l2(p.sel_j, (size_t)next * p.nmax * sizeof(int), (size_t)p.nmax * sizeof(int));
+  tc::prefetch_l2(p.sel_r, (size_t)next * p.nmax * 3 * sizeof(double), (size_t)p.nmax * 3 * sizeof(double));
 }
 
 // One product group: barrier, issue by thread 0, commit to `mb`, wait.
@@ -699,7 +686,7 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
   if (t == 0 && atom + (int)gridDim.x < p.n) {
     const int next = atom + (int)gridDim.x;
     prefetch_env(p, next);
-    if (MP && p.lb > 0) prefetch_l2(p.Gf32, (size_t)next * 32 * kW * 16, (size_t)32 * kW * 16);
+    if (MP && p.lb > 0) tc::prefetch_l2(p.Gf32, (size_t)next * 32 * kW * 16, (size_t)32 * kW * 16);
   }
   atom_setup(p, atom, m);
   const int ngroups = (m->nvalid + 7) >> 3;

@@ -102,6 +102,18 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 __device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
+// L2 prefetch of the whole 16-byte units within [off, off + len) bytes after
+// `base`, in pieces of at most 32 KB.  A hint only: it never reaches outside
+// the range and nothing waits for it.
+__device__ __forceinline__ void prefetch_l2(const void* base, size_t off, size_t len) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(base) + off;
+  uintptr_t b = (a + 15) & ~static_cast<uintptr_t>(15);
+  const uintptr_t e = (a + len) & ~static_cast<uintptr_t>(15);
+  for (; b < e; b += 32768) {
+    const uintptr_t n = e - b < 32768 ? e - b : 32768;
+    bulk_prefetch_l2(reinterpret_cast<const void*>(b), static_cast<uint32_t>(n));
+  }
+}
 
 // ------------------------------------------------------------------ fences
 __device__ __forceinline__ void fence_async_smem() {
