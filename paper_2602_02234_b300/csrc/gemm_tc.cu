@@ -31,6 +31,12 @@ __device__ __forceinline__ uint64_t desc_mn(uint32_t base, int Kx, int k0) {
                        128u);
 }
 
+// four values rounded to the 16-bit operand type, as one 8-byte store
+__device__ __forceinline__ uint2 pack4(int fp16, float a, float b, float c, float d) {
+  return fp16 ? make_uint2(tc::pack_f16(a, b), tc::pack_f16(c, d))
+              : make_uint2(tc::pack_bf16(a, b), tc::pack_bf16(c, d));
+}
+
 __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
   extern __shared__ __align__(1024) uint8_t sm[];
   const int t = threadIdx.x, warp = t >> 5;
@@ -113,11 +119,40 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
   uint32_t phase = 0;
   for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const long long m0 = (long long)tile * kRows;
+    if (g.a16) {
+      // A rows stored in 16 bits (the operand type): 16-byte chunks straight
+      // into the core-matrix layout, eight reads in flight per thread
+      constexpr int kLoads16 = 8;
+      const int k8 = g.K >> 3, total16 = kRows * k8;
+      for (int base = 0; base < total16; base += kRows * kLoads16) {
+        uint4 v[kLoads16];
+#pragma unroll
+        for (int u = 0; u < kLoads16; ++u) {
+          const int i = base + u * kRows + t;
+          v[u] = make_uint4(0u, 0u, 0u, 0u);
+          if (i < total16) {
+            const int r = i / k8, c = (i - r * k8) << 3;
+            const long long m = m0 + r;
+            if (m < g.M) {
+              const long long row = g.a_rows ? (long long)g.a_rows[m] : m;
+              v[u] = *reinterpret_cast<const uint4*>(g.a16 + row * g.lda + c);
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kLoads16; ++u) {
+          const int i = base + u * kRows + t;
+          if (i >= total16) break;
+          const int r = i / k8, c = (i - r * k8) << 3;
+          *reinterpret_cast<uint4*>(As + tc::kmajor_off(r, c, g.K)) = v[u];
+        }
+      }
+    }
     // A tile: 128 rows x K, coalesced float4 reads -> 16-bit core-matrix layout;
     // each thread issues kLoads reads before converting any, so that enough
     // bytes are in flight to keep HBM busy
     constexpr int kLoads = 16;
-    const int total = kRows * k4;
+    const int total = g.a16 ? 0 : kRows * k4;
     for (int base = 0; base < total; base += kRows * kLoads) {
       float4 v[kLoads];
 #pragma unroll
@@ -243,16 +278,19 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
               xo[q] = f * gq[q] * eq[q];
               dacc[u] += gq[q] * eq[q] * uq[q];
             }
-            *reinterpret_cast<float4*>(g.x_out + row * g.ldc + col) = make_float4(xo[0], xo[1], xo[2], xo[3]);
+            if (g.x16)
+              *reinterpret_cast<uint2*>(g.x16 + row * g.ldc + col) = pack4(g.fp16, xo[0], xo[1], xo[2], xo[3]);
+            else
+              *reinterpret_cast<float4*>(g.x_out + row * g.ldc + col) = make_float4(xo[0], xo[1], xo[2], xo[3]);
           }
           *Cp = make_float4(y[0], y[1], y[2], y[3]);
           continue;
         }
         if (g.epi == 3) {   // edge update: v = tanh(Ai + Bj + acc + b), e1 = e_in + v
-          float4* Vp = reinterpret_cast<float4*>(g.v_out + row * g.ldc + col);
           const int jn = g.sel_j[row];
           if (jn < 0) {
-            *Vp = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (g.v16) *reinterpret_cast<uint2*>(g.v16 + row * g.ldc + col) = make_uint2(0u, 0u);
+            else *reinterpret_cast<float4*>(g.v_out + row * g.ldc + col) = make_float4(0.f, 0.f, 0.f, 0.f);
             *Cp = make_float4(0.f, 0.f, 0.f, 0.f);
             continue;
           }
@@ -263,7 +301,8 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
           const float y1 = tanhf(av.y + bj.y + x[1] + b[1]);
           const float y2 = tanhf(av.z + bj.z + x[2] + b[2]);
           const float y3 = tanhf(av.w + bj.w + x[3] + b[3]);
-          *Vp = make_float4(y0, y1, y2, y3);
+          if (g.v16) *reinterpret_cast<uint2*>(g.v16 + row * g.ldc + col) = pack4(g.fp16, y0, y1, y2, y3);
+          else *reinterpret_cast<float4*>(g.v_out + row * g.ldc + col) = make_float4(y0, y1, y2, y3);
           *Cp = make_float4(e.x + y0, e.y + y1, e.z + y2, e.w + y3);
           continue;
         }
@@ -357,6 +396,7 @@ void gemm_tc(const GemmTc& g0, cudaStream_t st) {
   if (g0.M <= 0) return;
   GemmTc g = g0;
   if (g.split && smem_of(g) > g_max_dyn) g.split = 0;
+  if (g.a16) g.split = 0;   // a 16-bit A has no remainder to carry
   int cols = 32;
   while (cols < g.N) cols <<= 1;
   // at most 512 / cols CTAs may share an SM's tensor memory: pad the shared

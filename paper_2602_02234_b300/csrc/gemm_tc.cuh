@@ -2,6 +2,8 @@
 // FP32 accumulation), used by the graph family's mixed-precision form.
 #pragma once
 
+#include <stdint.h>
+
 #include <string>
 
 #include <cuda_runtime.h>
@@ -59,6 +61,12 @@ struct GemmTc {
   long long lddm;
   float *x_out, *dsw;
   float inv_nmax;
+  // 16-bit storage in the operand type (FP16, or BF16 when fp16 = 0) instead
+  // of FP32, where set: A (a16, lda in elements, a multiple of 8, 16-byte
+  // aligned rows; no split), epi 3's v_out (v16) and epi 5's x_out (x16),
+  // both laid out like C
+  const uint16_t* a16;
+  uint16_t *v16, *x16;
 };
 
 bool gemm_tc_shape_ok(int N, int K);

@@ -4,9 +4,18 @@
 // gather.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 
 namespace dp {
+
+// a stored per-slot value as the accumulation type
+__device__ __forceinline__ float mp_val(float x) { return x; }
+__device__ __forceinline__ double mp_val(double x) { return x; }
+__device__ __forceinline__ float mp_val(__half x) { return __half2float(x); }
+__device__ __forceinline__ float mp_val(__nv_bfloat16 x) { return __bfloat162float(x); }
 
 // h_i = Wt[t_i]
 template <typename T>
@@ -22,11 +31,12 @@ __global__ void k_mp_init(int n, int m1, const int* __restrict__ types, const T*
 // (i, p) being row i * row_stride + p of dG (U null: the plain sum).  The
 // slots are found through j's skin list and summed in increasing i * nmax + p,
 // so the result does not depend on the order the skin list holds them in.
+// dG may be stored in 16 bits (S = __half or __nv_bfloat16 with T = float).
 // One warp per atom; shared memory: 2 x cap ints per warp.
-template <typename T>
+template <typename T, typename S = T>
 __global__ void k_mp_gather(int n, int nmax, int row_stride, int m1, int cap,
                             const SkinEntry* __restrict__ skin, const int* __restrict__ skin_cnt, const int* __restrict__ mirror,
-                            const short* __restrict__ selpos, const T* __restrict__ dG,
+                            const short* __restrict__ selpos, const S* __restrict__ dG,
                             const T* __restrict__ U, T* __restrict__ dq) {
   extern __shared__ int mp_smem[];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -73,9 +83,9 @@ __global__ void k_mp_gather(int n, int nmax, int row_stride, int m1, int cap,
         T x0[4], x1[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const T* r = dG + (long long)ord[t + q] * m1 + f;
-          x0[q] = r[0];
-          x1[q] = r[1];
+          const S* r = dG + (long long)ord[t + q] * m1 + f;
+          x0[q] = mp_val(r[0]);
+          x1[q] = mp_val(r[1]);
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -84,9 +94,9 @@ __global__ void k_mp_gather(int n, int nmax, int row_stride, int m1, int cap,
         }
       }
       for (; t < k; ++t) {
-        const T* r = dG + (long long)ord[t] * m1 + f;
-        a0 += r[0];
-        a1 += r[1];
+        const S* r = dG + (long long)ord[t] * m1 + f;
+        a0 += mp_val(r[0]);
+        a1 += mp_val(r[1]);
       }
       if (U) {
         const T u0 = U[(long long)j * m1 + f], u1 = U[(long long)j * m1 + f + 1];
@@ -100,7 +110,7 @@ __global__ void k_mp_gather(int n, int nmax, int row_stride, int m1, int cap,
   }
   for (int f = lane; f < m1; f += 32) {
     T acc = T(0);
-    for (int t = 0; t < k; ++t) acc += dG[(long long)ord[t] * m1 + f];
+    for (int t = 0; t < k; ++t) acc += mp_val(dG[(long long)ord[t] * m1 + f]);
     if (U) {
       const T u = U[(long long)j * m1 + f];
       acc *= T(1) - u * u;

@@ -62,6 +62,34 @@ __device__ __forceinline__ void st4(double* p, const double* v) {
   reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
   reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
 }
+// the mixed form keeps some per-slot arrays in 16 bits, in the type of its
+// tensor-core operands (FP16; BF16 when built with DP_GF_BF16)
+#ifdef DP_GF_BF16
+using gf16_t = __nv_bfloat16;
+#else
+using gf16_t = __half;
+#endif
+// four consecutive 16-bit values (8-byte aligned) as FP32, and back (rounded)
+__device__ __forceinline__ void ld4(const __half* p, float* v) {
+  const uint2 u = *reinterpret_cast<const uint2*>(p);
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void ld4(const __nv_bfloat16* p, float* v) {
+  const uint2 u = *reinterpret_cast<const uint2*>(p);
+  const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+  const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void st4(__half* p, const float* v) {
+  const __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
+  *reinterpret_cast<uint2*>(p) = make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
+}
+__device__ __forceinline__ void st4(__nv_bfloat16* p, const float* v) {
+  const __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]), b = __floats2bfloat162_rn(v[2], v[3]);
+  *reinterpret_cast<uint2*>(p) = make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
+}
 
 
 // ------------------------------------------------------------------ kernels
@@ -732,10 +760,12 @@ __global__ void k_dtanh4(long long n4, const T* __restrict__ g, const T* __restr
 // (b) fused per atom: dy = de1 (1 - v^2) on every slot row and the atom's sum
 // of those rows (block per atom; ed a multiple of 4, at most 4 x blockDim).
 // Thread t owns the column quad t mod (ed / 4) and the rows congruent to
-// t / (ed / 4); the row groups' partial sums are added in group order.
-template <typename T>
-__global__ void k_dtanh_rowsum(int nmax, int ed, const T* __restrict__ g, const T* __restrict__ y,
-                               T* __restrict__ dy, T* __restrict__ out) {
+// t / (ed / 4); the row groups' partial sums are added in group order.  v and
+// dy are stored as V and Y (16 bits in the mixed form); the sums add the
+// products before dy is rounded to Y.
+template <typename T, typename V = T, typename Y = T>
+__global__ void k_dtanh_rowsum(int nmax, int ed, const T* __restrict__ g, const V* __restrict__ y,
+                               Y* __restrict__ dy, T* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* part = reinterpret_cast<T*>(sm_raw);   // [row group][ed]
   const int cqn = ed >> 2, nrg = blockDim.x / cqn;
@@ -980,10 +1010,11 @@ class PlainGf : public Model {
   }
   // per atom j: the sum of x over every kept slot (i, p) whose neighbour is j,
   // in increasing (i, p) order whatever the skin list's order
-  void gather_in(const NbrView& nv, const T* x, T* out, cudaStream_t st) {
+  template <typename S>
+  void gather_in(const NbrView& nv, const S* x, T* out, cudaStream_t st) {
     int warps = 4;
     while (warps > 1 && sizeof(int) * 2 * nv.cap * warps > 48 * 1024) --warps;
-    k_mp_gather<T><<<ceil_div(n_, warps), warps * 32, sizeof(int) * 2 * nv.cap * warps, st>>>(
+    k_mp_gather<T, S><<<ceil_div(n_, warps), warps * 32, sizeof(int) * 2 * nv.cap * warps, st>>>(
         n_, m_.nmax, m_.nmax, m_.ed, nv.cap, nv.skin, nv.skin_cnt, nv.mirror, nv.selpos, x,
         nullptr, out);
   }
@@ -1000,6 +1031,7 @@ class PlainGf : public Model {
       t.C = ee_[l + 1]; t.ldc = Ed;   // e1; the angle channel then updates its rows in place
       t.bias = be_[l]; t.epi = 3;
       t.sel_j = nv.sel_j; t.nmax = m_.nmax; t.Ai = Ai_; t.Bj = Bj_; t.e_in = ee_[l]; t.v_out = vv_[l];
+      if (s16_) t.v16 = reinterpret_cast<uint16_t*>(vv16_[l]);
       t.status = flags_;
 #ifdef DP_GF_BF16
       t.fp16 = 0;
@@ -1057,10 +1089,12 @@ class PlainGf : public Model {
       GemmTc t{};
       t.M = (int)((long long)n_ * m_.nmax); t.N = Ed; t.K = Ed;
       t.A = dy_; t.lda = Ed;
+      if (s16_) t.a16 = reinterpret_cast<const uint16_t*>(dy16_);
       t.B = Wc_[l]; t.ldb = Ed; t.b_nk = 1;
       t.C = de_; t.ldc = Ed; t.beta = 1.f; t.epi = 5;
       t.sel_j = nv.sel_j; t.nmax = m_.nmax; t.sw = sw_; t.dm = dnm_ + Nd; t.lddm = Nd + Ed;
       t.u = uu_[l]; t.e_in = ee_[l]; t.x_out = X_; t.dsw = dsw_e_; t.inv_nmax = 1.f / (float)m_.nmax;
+      if (s16_) t.x16 = reinterpret_cast<uint16_t*>(X16_);
       t.status = flags_;
 #ifdef DP_GF_BF16
       t.fp16 = 0;
@@ -1074,6 +1108,13 @@ class PlainGf : public Model {
     }
   }
   bool tc_ = false;
+  // mixed form: v (the edge update's tanh, kept for the adjoint), dy (the
+  // A operand of de += dy Wc^T) and X (the message adjoint's per-slot rows)
+  // stored in 16 bits, the operand type (S16; T itself outside the mixed form)
+  using S16 = typename std::conditional<std::is_same<T, float>::value, gf16_t, T>::type;
+  bool s16_ = false;
+  std::vector<S16*> vv16_;
+  S16 *dy16_ = nullptr, *X16_ = nullptr;
   int* flags_ = nullptr;
   const unsigned char* seed_ = nullptr;   // energy seed (device, optional)
   // shared-memory variants of the angle kernels (see k_angle, k_angle_bwd):
@@ -1220,10 +1261,15 @@ bool PlainGf<T>::init(const GfDims& m, const double* w, int n_atoms, const int* 
        dalloc(&rh_, 3 * P, err);
   nn_.resize(L + 1); ee_.resize(L + 1);
   hh_.resize(L); uu_.resize(L); mm_.resize(L); vv_.resize(L); qq_.resize(L); tt_.resize(L);
+  // the mixed form's products and epilogues take the 16-bit rows (every
+  // width it accepts has ed a multiple of 16 and nd of 16)
+  s16_ = tc_ && std::is_same<T, float>::value && Ed % 16 == 0 && Ed <= 256 && Nd % 4 == 0;
+  vv16_.assign(L, nullptr);
+  dy_ = X_ = nullptr;
   for (int l = 0; l <= L && ok; ++l) ok = dalloc(&nn_[l], N * Nd, err) && dalloc(&ee_[l], P * Ed, err);
   for (int l = 0; l < L && ok; ++l)
     ok = dalloc(&hh_[l], N * Nd, err) && dalloc(&uu_[l], N * Ed, err) &&
-         dalloc(&mm_[l], N * Ed, err) && dalloc(&vv_[l], P * Ed, err) && dalloc(&qq_[l], PA * Ed, err) &&
+         dalloc(&mm_[l], N * Ed, err) && (s16_ ? dalloc(&vv16_[l], P * Ed, err) : dalloc(&vv_[l], P * Ed, err)) && dalloc(&qq_[l], PA * Ed, err) &&
          dalloc(&tt_[l], PA * Ed, err);
   // the angle kernels hold their monomial sums in shared memory, with two
   // slot-data buffers (switches and unit vectors): beta (ed x 4), the slots'
@@ -1264,10 +1310,10 @@ bool PlainGf<T>::init(const GfDims& m, const double* w, int n_atoms, const int* 
        dalloc(&aa_, PA * Ed, err) && dalloc(&y1_, N * m.f1, err) && dalloc(&y2_, N * m.f2, err) &&
        dalloc(&y3_, N * m.f3, err) && dalloc(&d1_, N * m.f1, err) && dalloc(&d2_, N * m.f2, err) &&
        dalloc(&d3_, N * m.f3, err) && dalloc(&dn_, N * Nd, err) && dalloc(&dn1_, N * Nd, err) &&
-       dalloc(&de_, P * Ed, err) && dalloc(&dy_, P * Ed, err) &&
+       dalloc(&de_, P * Ed, err) && (s16_ ? dalloc(&dy16_, P * Ed, err) : dalloc(&dy_, P * Ed, err)) &&
        dalloc(&dz_, PA * Ed, err) && dalloc(&da_, PA * Ed, err) && dalloc(&dq_, PA * Ed, err) &&
        dalloc(&du_, N * Ed, err) && dalloc(&dx_, N * Nd, err) && dalloc(&dnm_, N * (Nd + Ed), err) &&
-       dalloc(&X_, P * Ed, err) && dalloc(&sdy_, N * Ed, err) && dalloc(&gat_, N * Ed, err) &&
+       (s16_ ? dalloc(&X16_, P * Ed, err) : dalloc(&X_, P * Ed, err)) && dalloc(&sdy_, N * Ed, err) && dalloc(&gat_, N * Ed, err) &&
        dalloc(&dsw_e_, P, err) && dalloc(&dsa_e_, P, err) && dalloc(&drh_, 3 * P, err) &&
        dalloc(&g_, 3 * P, err);
   return ok;
@@ -1413,7 +1459,11 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
     // (b): de now holds dE/de1; it becomes dE/de_l (e1 = e_l + tanh(...))
     const bool fused_rowsum = Ed % 4 == 0 && Ed <= 1024;
     if (fused_rowsum)   // dy and its per-atom row sum sdy in one pass
-      k_dtanh_rowsum<T><<<n, 256, 256 / (Ed / 4) * Ed * sizeof(T), st>>>(NM, Ed, de_, vv_[l], dy_, sdy_);
+      if (s16_)
+        k_dtanh_rowsum<T, S16, S16><<<n, 256, 256 / (Ed / 4) * Ed * sizeof(T), st>>>(NM, Ed, de_, vv16_[l],
+                                                                                     dy16_, sdy_);
+      else
+        k_dtanh_rowsum<T><<<n, 256, 256 / (Ed / 4) * Ed * sizeof(T), st>>>(NM, Ed, de_, vv_[l], dy_, sdy_);
     else if (PE % 4 == 0)
       k_dtanh4<T><<<grid(PE / 4), 256, 0, st>>>(PE / 4, de_, vv_[l], dy_);
     else
@@ -1428,7 +1478,8 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
       mm(g, st);
     }
     if (!fused_rowsum) k_rowsum<T><<<n, 64, 0, st>>>(NM, Ed, dy_, sdy_);
-    gather_in(nv, dy_, gat_, st);
+    if (s16_) gather_in(nv, dy16_, gat_, st);
+    else gather_in(nv, dy_, gat_, st);
     k_copy<T><<<grid((long long)n * Nd), 256, 0, st>>>((long long)n * Nd, dn_, dn1_);
     {  // dn1 += sdy Wa^T + gat Wb^T
       Gemm<T> g{};
@@ -1459,7 +1510,8 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
     else
       k_msg_bwd<T><<<grid(P * 32), 256, 0, st>>>(P, NM, Ed, Nd + Ed, inv_nmax, nv.sel_j, sw_, ee_[l],
                                                  uu_[l], dnm_ + Nd, de_, X_, dsw_e_);
-    gather_in(nv, X_, du_, st);
+    if (s16_) gather_in(nv, X16_, du_, st);
+    else gather_in(nv, X_, du_, st);
     {  // dn += du Wm^T
       Gemm<T> g{};
       g.M = n; g.N = Nd; g.K = Ed;
