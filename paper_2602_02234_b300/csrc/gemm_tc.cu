@@ -37,6 +37,9 @@ __device__ __forceinline__ uint2 pack4(int fp16, float a, float b, float c, floa
               : make_uint2(tc::pack_bf16(a, b), tc::pack_bf16(c, d));
 }
 
+// EPI: 3, 4 or 5 for those epilogues, 0 for the others (none, tanh, the
+// 1 - aux^2 factor), so that each variant carries only its own epilogue
+template <int EPI>
 __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
   extern __shared__ __align__(1024) uint8_t sm[];
   const int t = threadIdx.x, warp = t >> 5;
@@ -248,7 +251,7 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
         const float4 bv = g.bias ? *reinterpret_cast<const float4*>(g.bias + col)
                                  : make_float4(0.f, 0.f, 0.f, 0.f);
         const float b[4] = {bv.x, bv.y, bv.z, bv.w};
-        if (g.epi == 4) {   // angle output: t = tanh(acc + b), e_out = e_in + sa t
+        if constexpr (EPI == 4) {   // angle output: t = tanh(acc + b), e_out = e_in + sa t
           const long long xr = g.x_rows ? (long long)g.x_rows[m] : row;
           const float4 e = *reinterpret_cast<const float4*>(g.e_in + xr * g.ldc + col);
           const float sw = g.sa[xr];
@@ -260,7 +263,7 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
               make_float4(e.x + sw * y[0], e.y + sw * y[1], e.z + sw * y[2], e.w + sw * y[3]);
           continue;
         }
-        if (g.epi == 5) {   // edge adjoint and the message's adjoint on kept slots
+        if constexpr (EPI == 5) {   // edge adjoint and the message's adjoint on kept slots
           const float4 dv = *Cp;
           float y[4] = {dv.x + x[0], dv.y + x[1], dv.z + x[2], dv.w + x[3]};
           const int jn = g.sel_j[row];
@@ -286,7 +289,7 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
           *Cp = make_float4(y[0], y[1], y[2], y[3]);
           continue;
         }
-        if (g.epi == 3) {   // edge update: v = tanh(Ai + Bj + acc + b), e1 = e_in + v
+        if constexpr (EPI == 3) {   // edge update: v = tanh(Ai + Bj + acc + b), e1 = e_in + v
           const int jn = g.sel_j[row];
           if (jn < 0) {
             if (g.v16) *reinterpret_cast<uint2*>(g.v16 + row * g.ldc + col) = make_uint2(0u, 0u);
@@ -331,7 +334,7 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
       }
       __syncwarp();   // the stage is rewritten by the next column block
     }
-    if (g.epi == 5) {   // each row's dsw sum over its four threads (lanes 4r .. 4r + 3), in a fixed order
+    if constexpr (EPI == 5) {   // each row's dsw sum over its four threads (lanes 4r .. 4r + 3), in a fixed order
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         float v = dacc[u];
@@ -378,17 +381,22 @@ bool gemm_tc_prepare(std::string* err) {
   }
   // up to the per-block limit less the static part (a split A that would not
   // fit falls back to one product)
-  cudaFuncAttributes fa{};
-  if (cudaFuncGetAttributes(&fa, k_gemm_tc) != cudaSuccess) {
-    *err = "tensor-core GEMM: cannot query the kernel";
-    return false;
+  void (*const kernels[4])(GemmTc, int) = {k_gemm_tc<0>, k_gemm_tc<3>, k_gemm_tc<4>, k_gemm_tc<5>};
+  size_t stat = 0;
+  for (auto k : kernels) {
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) {
+      *err = "tensor-core GEMM: cannot query the kernel";
+      return false;
+    }
+    stat = std::max(stat, fa.sharedSizeBytes);
   }
-  g_max_dyn = kMaxSmemBlock - fa.sharedSizeBytes;
-  if (cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g_max_dyn) !=
-      cudaSuccess) {
-    *err = "tensor-core GEMM cannot get its shared memory";
-    return false;
-  }
+  g_max_dyn = kMaxSmemBlock - stat;
+  for (auto k : kernels)
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g_max_dyn) != cudaSuccess) {
+      *err = "tensor-core GEMM cannot get its shared memory";
+      return false;
+    }
   return true;
 }
 
@@ -406,7 +414,12 @@ void gemm_tc(const GemmTc& g0, cudaStream_t st) {
   const size_t smem = std::max(smem_of(g), floor_smem);
   const int tiles = (g.M + kRows - 1) / kRows;
   const int grid = std::min(tiles, std::max(1, g_sms) * per_sm);
-  k_gemm_tc<<<grid, kRows, smem, st>>>(g, cols);
+  switch (g.epi) {
+    case 3: k_gemm_tc<3><<<grid, kRows, smem, st>>>(g, cols); break;
+    case 4: k_gemm_tc<4><<<grid, kRows, smem, st>>>(g, cols); break;
+    case 5: k_gemm_tc<5><<<grid, kRows, smem, st>>>(g, cols); break;
+    default: k_gemm_tc<0><<<grid, kRows, smem, st>>>(g, cols); break;
+  }
 }
 
 }  // namespace dp

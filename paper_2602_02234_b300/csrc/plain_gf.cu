@@ -677,9 +677,7 @@ __global__ void __launch_bounds__(kAngThreads) k_angle_bwd(int n, int nmax, int 
       for (int x = 0; x < 2; ++x)
 #pragma unroll
         for (int j = 0; j < 4; ++j) h[x][j] = k[x][j] = d[x][j] = T(0);
-      for (int c = 0; c < ed; ++c) {
-        const T g[2] = {das[p0 * ld + c], das[p1 * ld + c]};
-        const T qv[2] = {qs[p0 * ld + c], qs[p1 * ld + c]};
+      auto column = [&](int c, const T* g, const T* qv) {
         T yb[4], dy[4];
         ld4(YB + c * kMono + mb, yb);
         ld4(dYB + c * kMono + mb, dy);
@@ -693,6 +691,26 @@ __global__ void __launch_bounds__(kAngThreads) k_angle_bwd(int n, int nmax, int 
           ld4(beta + 4 * c, b);
 #pragma unroll
           for (int x = 0; x < 2; ++x) fma_n<4>(d[x], b, g[x] * qv[x]);
+        }
+      };
+      if ((ed & 3) == 0) {   // the two slots' rows four columns per load
+        for (int c = 0; c < ed; c += 4) {
+          T g4[2][4], q4[2][4];
+          ld4(das + p0 * ld + c, g4[0]);
+          ld4(das + p1 * ld + c, g4[1]);
+          ld4(qs + p0 * ld + c, q4[0]);
+          ld4(qs + p1 * ld + c, q4[1]);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const T g[2] = {g4[0][u], g4[1][u]}, qv[2] = {q4[0][u], q4[1][u]};
+            column(c + u, g, qv);
+          }
+        }
+      } else {
+        for (int c = 0; c < ed; ++c) {
+          const T g[2] = {das[p0 * ld + c], das[p1 * ld + c]};
+          const T qv[2] = {qs[p0 * ld + c], qs[p1 * ld + c]};
+          column(c, g, qv);
         }
       }
 #pragma unroll
