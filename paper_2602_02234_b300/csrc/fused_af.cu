@@ -266,6 +266,7 @@ __device__ __forceinline__ float4 row_sum(Misc* m, float4 v) {
 struct Bar {
   unsigned long long* bar;
   uint32_t phase;
+  uint32_t commits = 1;   // arrivals the barrier takes per phase (product groups)
   __device__ bool wait(int* status) {
     bool ok = tc::mbar_wait(reinterpret_cast<uint64_t*>(bar), phase & 1u, kPolls);
     phase ^= 1u;
@@ -322,12 +323,32 @@ __device__ __forceinline__ void prefetch_env(const Params& p, int next) {
   tc::prefetch_l2(p.sel_r, (size_t)next * p.nmax * 3 * sizeof(double), (size_t)p.nmax * 3 * sizeof(double));
 }
 
-// One product group: barrier, issue by thread 0, commit to `mb`, wait.
+// One product group: barrier, issue by thread 0, commit to `mb` (as many
+// times as the barrier takes arrivals), wait.
 #define MMA_GROUP(mb, status, ...)                                   \
   do {                                                               \
     before_mma();                                                    \
     if (threadIdx.x == 0) {                                          \
       __VA_ARGS__;                                                   \
+      for (uint32_t c_ = 0; c_ < (mb).commits; ++c_)                 \
+        tc::mma_commit(reinterpret_cast<uint64_t*>((mb).bar));       \
+    }                                                                \
+    if (!(mb).wait_mma(status)) return false;                        \
+  } while (0)
+// The same with four issuing threads (lane 0 of warps 0-3), each issuing its
+// own products (those that accumulate into one region stay with one thread)
+// and committing once; `mb` takes four arrivals per phase.  A single thread
+// issues one 128 x n x 16 product about every 72 cycles; four of them reach
+// the rate the shared-memory operand reads allow (about 46 cycles for n <= 32).
+#define MMA_GROUP4(mb, status, P0, P1, P2, P3)                       \
+  do {                                                               \
+    before_mma();                                                    \
+    if ((threadIdx.x & 31) == 0 && threadIdx.x < 128) {              \
+      const int w_ = threadIdx.x >> 5;                               \
+      if (w_ == 0) { P0; }                                           \
+      else if (w_ == 1) { P1; }                                      \
+      else if (w_ == 2) { P2; }                                      \
+      else { P3; }                                                   \
       tc::mma_commit(reinterpret_cast<uint64_t*>((mb).bar));         \
     }                                                                \
     if (!(mb).wait_mma(status)) return false;                        \
@@ -906,10 +927,10 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
   return true;
 }
 
-__device__ void kernel_prologue(Misc* m) {
+__device__ void kernel_prologue(Misc* m, uint32_t product_arrivals) {
   const int t = threadIdx.x, warp = t >> 5;
   if (t == 0) {
-    tc::mbar_init(reinterpret_cast<uint64_t*>(&m->bar), 1);
+    tc::mbar_init(reinterpret_cast<uint64_t*>(&m->bar), product_arrivals);
     tc::mbar_init(reinterpret_cast<uint64_t*>(&m->wbar), 1);
     tc::mbar_init(reinterpret_cast<uint64_t*>(&m->pbar), 1);
     tc::mbar_init(reinterpret_cast<uint64_t*>(&m->xbar), 1);
@@ -934,7 +955,7 @@ template <bool MP>
 __global__ void __launch_bounds__(kThreads, 1) k_af_fwd(Params p) {
   extern __shared__ __align__(1024) uint8_t sm[];
   Misc* m = reinterpret_cast<Misc*>(sm + SM_MISC);
-  kernel_prologue(m);
+  kernel_prologue(m, 1);
   Bar mb{&m->bar, 0u}, wb{&m->wbar, 0u}, xb{&m->xbar, 0u};
   for (int atom = p.atom0 + blockIdx.x; atom < p.n; atom += gridDim.x)
     if (!fwd_atom<MP>(p, atom, sm, m, m->tptr, mb, wb, xb)) break;
@@ -1171,10 +1192,10 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
       const bool ok = xb.wait(p.status);
       if (!(wb.wait(p.status) && ok)) return false;
     }
-    MMA_GROUP(mb, p.status,
-              mma_issue(tb + R0, kop(sm + SM_G, kW), kop(sm + SM_Q, kW), kW, kW, false);
-              mma_issue(tb + R1, kop(sm + SM_G, kW), kop(sm + SM_K, kW), kW, kW, false);
-              mma_issue(tb + R3, kop(sm + SM_G, kW), kop(sm + SM_W, kW), kW, kW, false));
+    MMA_GROUP4(mb, p.status,
+               mma_issue(tb + R0, kop(sm + SM_G, kW), kop(sm + SM_Q, kW), kW, kW, false),
+               mma_issue(tb + R1, kop(sm + SM_G, kW), kop(sm + SM_K, kW), kW, kW, false),
+               mma_issue(tb + R3, kop(sm + SM_G, kW), kop(sm + SM_W, kW), kW, kW, false), (void)0);
     {
       const uint32_t src[3] = {R0, R1, R3};
       uint8_t* tiles[3] = {sm + SM_Q, sm + SM_K, sm + SM_V};
@@ -1217,11 +1238,11 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
       tc::fence_before_sync();
       // dA = dO_h V_h^T (R1), dV_h = A^T dO_h (R0 + 2d), O_h = A V_h (R0, consumed
       // below before dQ_h overwrites it)
-      MMA_GROUP(mb, p.status,
-                mma_issue(tb + R1, kop(sm + SM_P, kW, c0), kop(sm + SM_V, kW, c0), kW, DH, false);
-                mma_issue(tb + R0 + 2 * DH, mnop(sm + SM_G, kW, 0), mnop(sm + SM_P, kW, c0), DH, kW,
-                          false);
-                mma_issue(tb + R0, kop(sm + SM_G, kW), mnop(sm + SM_V, kW, c0), DH, kW, false));
+      MMA_GROUP4(mb, p.status,
+                 mma_issue(tb + R1, kop(sm + SM_P, kW, c0), kop(sm + SM_V, kW, c0), kW, DH, false),
+                 mma_issue(tb + R0 + 2 * DH, mnop(sm + SM_G, kW, 0), mnop(sm + SM_P, kW, c0), DH, kW,
+                           false),
+                 mma_issue(tb + R0, kop(sm + SM_G, kW), mnop(sm + SM_V, kW, c0), DH, kW, false), (void)0);
       // sum_k w_jk dw_jk = sum_k A_jk dA_jk = dO_j . O_j over this head's
       // columns; every part forms it whole (same order, same value)
       float wdw = 0.f;
@@ -1277,15 +1298,15 @@ __device__ bool bwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
       // (ones) and of the gate adjoint weighted by rh_j (accumulated over
       // heads); row sums of the gate adjoint weighted by rh_k (R1, free once
       // dA has been read); the next head's scores (R3, w has been read)
-      MMA_GROUP(mb, p.status,
-                mma_issue(tb + R0, kop(sm + SM_W, kW), mnop(sm + SM_K, kW, c0), DH, kW, false);
-                mma_issue(tb + R0 + DH, mnop(sm + SM_W, kW, 0), mnop(sm + SM_Q, kW, c0), DH, kW, false);
-                mma_issue(tb + R0 + 112, mnop(sm + SM_W, kW, 0), kop(m->ones, kW), 16, kW, h > 0);
-                mma_issue(tb + R0 + 96, mnop(sm + SM_G, kW, 0), kop(m->rhb, kW), 16, kW, h > 0);
-                mma_issue(tb + R1, kop(sm + SM_G, kW), kop(m->rhb, kW), 16, kW, false);
-                if (h + 1 < p.heads)
-                  mma_issue(tb + R3, kop(sm + SM_Q, kW, c0 + DH), kop(sm + SM_K, kW, c0 + DH), kW, DH,
-                            false));
+      MMA_GROUP4(mb, p.status,
+                 mma_issue(tb + R0, kop(sm + SM_W, kW), mnop(sm + SM_K, kW, c0), DH, kW, false),
+                 mma_issue(tb + R0 + DH, mnop(sm + SM_W, kW, 0), mnop(sm + SM_Q, kW, c0), DH, kW, false),
+                 mma_issue(tb + R0 + 112, mnop(sm + SM_W, kW, 0), kop(m->ones, kW), 16, kW, h > 0);
+                 mma_issue(tb + R0 + 96, mnop(sm + SM_G, kW, 0), kop(m->rhb, kW), 16, kW, h > 0),
+                 mma_issue(tb + R1, kop(sm + SM_G, kW), kop(m->rhb, kW), 16, kW, false);
+                 if (h + 1 < p.heads)
+                   mma_issue(tb + R3, kop(sm + SM_Q, kW, c0 + DH), kop(sm + SM_K, kW, c0 + DH), kW, DH,
+                             false));
       // the gate adjoint's row part, sum_k dc_jk rh_k, joins the column part in drc
       if (pt == 0) {
         float v[8];
@@ -1472,7 +1493,7 @@ template <bool MP>
 __global__ void __launch_bounds__(kThreads, 1) k_af_bwd(Params p) {
   extern __shared__ __align__(1024) uint8_t sm[];
   Misc* m = reinterpret_cast<Misc*>(sm + SM_MISC);
-  kernel_prologue(m);
+  kernel_prologue(m, 4);   // product groups with four issuers
   // constant operand: a ones row (column sums) and zero rows 3..15 of rhb
   zero_smem(m->ones, 16 * kW * 2);
   zero_smem(m->rhb, 16 * kW * 2);
@@ -1480,7 +1501,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_af_bwd(Params p) {
   if (threadIdx.x < kW)
     *reinterpret_cast<op_t*>(m->ones + tc::kmajor_off(0, threadIdx.x, kW)) = f2op(1.f);
   __syncthreads();
-  Bar mb{&m->bar, 0u}, wb{&m->wbar, 0u}, gb{&m->pbar, 0u}, xb{&m->xbar, 0u};
+  Bar mb{&m->bar, 0u, 4u}, wb{&m->wbar, 0u}, gb{&m->pbar, 0u}, xb{&m->xbar, 0u};
   for (int atom = p.atom0 + blockIdx.x; atom < p.n; atom += gridDim.x)
     if (!bwd_atom<MP>(p, atom, sm, m, m->tptr, mb, wb, gb, xb)) break;
   kernel_epilogue(m);
