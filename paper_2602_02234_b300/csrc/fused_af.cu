@@ -474,9 +474,9 @@ __device__ bool embed_h2(const Params& p, uint8_t* sm, Misc* m, uint32_t tb, Bar
   const uint32_t rb = p.e2 <= 64 ? R0 + 64 : R1;   // the second species' accumulator
   return species_pairs((unsigned)m->mask, p.W2T, bytes, bytes, w0, w1, k0, k1, p.status,
                        [&](int sa, uint8_t* Wa, int sb, uint8_t* Wb) -> bool {
-    MMA_GROUP(mb, p.status,
-              mma_issue(tb + R0, kop(H1, p.e1), kop(Wa, p.e1), p.e2, p.e1, false);
-              if (sb >= 0) mma_issue(tb + rb, kop(H1, p.e1), kop(Wb, p.e1), p.e2, p.e1, false));
+    MMA_GROUP4(mb, p.status, mma_issue(tb + R0, kop(H1, p.e1), kop(Wa, p.e1), p.e2, p.e1, false),
+               if (sb >= 0) mma_issue(tb + rb, kop(H1, p.e1), kop(Wb, p.e1), p.e2, p.e1, false), (void)0,
+               (void)0);
     const bool mine = tj >= 0 && (tj == sa || tj == sb);
     if (__any_sync(0xffffffffu, mine)) {
       for (int c = 16 * pt; c < p.e2; c += 16 * kSplit) {
@@ -525,9 +525,9 @@ __device__ bool embed_forward(const Params& p, uint8_t* sm, Misc* m, uint32_t tb
   // two species per product group: the first into R1, the second into R3
   return species_pairs((unsigned)m->mask, p.W3T, bytes, bytes, sm + SM_W, sm + SM_P, wb, xb,
                        p.status, [&](int sa, uint8_t* Wa, int sb, uint8_t* Wb) -> bool {
-    MMA_GROUP(mb, p.status,
-              mma_issue(tb + R1, kop(H2, p.e2), kop(Wa, p.e2), kW, p.e2, false);
-              if (sb >= 0) mma_issue(tb + R3, kop(H2, p.e2), kop(Wb, p.e2), kW, p.e2, false));
+    MMA_GROUP4(mb, p.status, mma_issue(tb + R1, kop(H2, p.e2), kop(Wa, p.e2), kW, p.e2, false),
+               if (sb >= 0) mma_issue(tb + R3, kop(H2, p.e2), kop(Wb, p.e2), kW, p.e2, false), (void)0,
+               (void)0);
     const bool mine = tj >= 0 && (tj == sa || tj == sb);
     const uint32_t racc = sb >= 0 && tj == sb ? R3 : R1;
     if (__any_sync(0xffffffffu, mine)) {
@@ -577,10 +577,9 @@ __device__ bool qkv(const Params& p, uint8_t* sm, uint32_t tb, Bar& mb, Bar& xb)
   const int r = row_id(), pt = part_id();
   const uint32_t lo = lane_base();
   if (!xb.wait(p.status)) return false;
-  MMA_GROUP(mb, p.status,
-            mma_issue(tb + R0, kop(sm + SM_G, kW), kop(sm + SM_Q, kW), kW, kW, false);
-            mma_issue(tb + R1, kop(sm + SM_G, kW), kop(sm + SM_K, kW), kW, kW, false);
-            mma_issue(tb + R3, kop(sm + SM_G, kW), kop(sm + SM_V, kW), kW, kW, false));
+  MMA_GROUP4(mb, p.status, mma_issue(tb + R0, kop(sm + SM_G, kW), kop(sm + SM_Q, kW), kW, kW, false),
+             mma_issue(tb + R1, kop(sm + SM_G, kW), kop(sm + SM_K, kW), kW, kW, false),
+             mma_issue(tb + R3, kop(sm + SM_G, kW), kop(sm + SM_V, kW), kW, kW, false), (void)0);
   const uint32_t src[3] = {R0, R1, R3};
   uint8_t* dst[3] = {sm + SM_Q, sm + SM_K, sm + SM_V};
 #pragma unroll
@@ -791,17 +790,25 @@ __device__ bool fwd_atom(const Params& p, int atom, uint8_t* sm, Misc* m, uint32
         store32(sm + SM_P, r, c, kW, kW, v);
       }
       tc::fence_before_sync();
-      // O_h = A V_h, and the next head's scores (R3 has been read)
-      MMA_GROUP(mb, p.status,
-                mma_issue(tb + R0 + h * kDH, kop(sm + SM_P, kW), mnop(sm + SM_V, kW, h * kDH), kDH,
-                          kW, false);
-                if (h + 1 < p.heads)
-                  mma_issue(tb + R3, kop(sm + SM_Q, kW, (h + 1) * kDH),
-                            kop(sm + SM_K, kW, (h + 1) * kDH), kW, kDH, false));
+      // O_h = A V_h as two halves of the neighbour sum (R0 and R1, added at
+      // the drain) and the next head's scores (R3 has been read), from three
+      // issuing threads
+      MMA_GROUP4(mb, p.status,
+                 mma_issue(tb + R0 + h * kDH, kop(sm + SM_P, kW), mnop(sm + SM_V, kW, h * kDH), kDH,
+                           kW / 2, false),
+                 mma_issue(tb + R1 + h * kDH, kop(sm + SM_P, kW, kW / 2),
+                           mnop(sm + SM_V, kW, h * kDH, kW / 2), kDH, kW / 2, false),
+                 if (h + 1 < p.heads)
+                   mma_issue(tb + R3, kop(sm + SM_Q, kW, (h + 1) * kDH),
+                             kop(sm + SM_K, kW, (h + 1) * kDH), kW, kDH, false),
+                 (void)0);
     }
     for (int c = 32 * pt; c < kW; c += kStride) {
-      float v[32];
+      float v[32], u[32];
       tc::tmem_ld32(tb + lo + R0 + c, v);
+      tc::tmem_ld32(tb + lo + R1 + c, u);
+#pragma unroll
+      for (int q = 0; q < 32; ++q) v[q] += u[q];
       store32(sm + SM_Q, r, c, kW, kW, v);
     }
     tc::fence_before_sync();
@@ -955,8 +962,8 @@ template <bool MP>
 __global__ void __launch_bounds__(kThreads, 1) k_af_fwd(Params p) {
   extern __shared__ __align__(1024) uint8_t sm[];
   Misc* m = reinterpret_cast<Misc*>(sm + SM_MISC);
-  kernel_prologue(m, 1);
-  Bar mb{&m->bar, 0u}, wb{&m->wbar, 0u}, xb{&m->xbar, 0u};
+  kernel_prologue(m, 4);   // product groups with up to four issuers
+  Bar mb{&m->bar, 0u, 4u}, wb{&m->wbar, 0u}, xb{&m->xbar, 0u};
   for (int atom = p.atom0 + blockIdx.x; atom < p.n; atom += gridDim.x)
     if (!fwd_atom<MP>(p, atom, sm, m, m->tptr, mb, wb, xb)) break;
   kernel_epilogue(m);
