@@ -47,9 +47,9 @@ FP32_ALU_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # 148 SMs x 128 FP32 lan
 # (per-atom tiles, lists, gradients), so a launch over N atoms moves N x this.
 # These are not measured by this program: they hold for the kernel source whose
 # SHA-256 prefix is recorded beside them, and the line reports null otherwise.
-NCU_TRAFFIC_PER_ATOM = {"k_af_bwd": (545.588480e6 + 9.186304e6) / 4800,
-                        "k_af_fwd": (16.658688e6 + 452.925184e6) / 4800}
-NCU_TRAFFIC_SOURCE = ("paper_2602_02234_b300/csrc/fused_af.cu", "e253d692c0610fd6")
+NCU_TRAFFIC_PER_ATOM = {"k_af_bwd": (545.724672e6 + 9.589760e6) / 4800,
+                        "k_af_fwd": (16.883712e6 + 452.838144e6) / 4800}
+NCU_TRAFFIC_SOURCE = ("paper_2602_02234_b300/csrc/fused_af.cu", "313160fdb172cd7c")
 
 
 def _source_sha(rel):
