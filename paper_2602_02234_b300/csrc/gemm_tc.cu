@@ -215,6 +215,36 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
       }
       tc::mma_commit(bar);
     }
+    // The epilogue's row indices, read while the products run.  Thread
+    // (warp w, lane) owns rows 32 w + lane / 4 + 8 u (u = 0..3) and, in every
+    // 16-column block, the four columns from (lane mod 4) x 4.
+    const int c4 = (lane & 3) << 2;
+    long long rowu[4];   // row'(m) of each owned row, -1 beyond M
+    long long xru[4];    // epi 4: row of e_in, v_out and sa
+    int jnu[4];          // epi 3, 5: the slot's neighbour (-1: empty slot or beyond M)
+    float fu[4];         // epi 5: inv_nmax sw of a kept slot; epi 4: sa of the row
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long m = m0 + 32 * warp + (lane >> 2) + 8 * u;
+      rowu[u] = m < g.M ? (g.c_rows ? (long long)g.c_rows[m] : m) : -1;
+      xru[u] = -1;
+      if constexpr (EPI == 4)
+        if (m < g.M) xru[u] = g.x_rows ? (long long)g.x_rows[m] : rowu[u];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      jnu[u] = -1;
+      fu[u] = 0.f;
+      if constexpr (EPI == 3 || EPI == 5)
+        if (rowu[u] >= 0) jnu[u] = g.sel_j[rowu[u]];
+      if constexpr (EPI == 4)
+        if (xru[u] >= 0) fu[u] = g.sa[xru[u]];
+    }
+    if constexpr (EPI == 5) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (jnu[u] >= 0) fu[u] = g.inv_nmax * g.sw[rowu[u]];
+    }
     bool ok = true;
     if (t == 0) ok = tc::mbar_wait(bar, phase & 1u, kPollsTc);
     phase ^= 1u;
@@ -227,10 +257,41 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
     // epilogue, 16 columns at a time: each warp reads its 32 accumulator rows
     // (thread = row) and turns them around through its shared-memory stage,
     // so that four neighbouring threads own one row's 16 columns and every
-    // global access of the warp covers 8 rows x 64 contiguous bytes
+    // global access of the warp covers 8 rows x 64 contiguous bytes.  A
+    // block's global operands of all four owned rows are requested before any
+    // of them is used, so that their latencies overlap.
     float* st = stage + warp * 32 * kStageLd;
     float dacc[4] = {0.f, 0.f, 0.f, 0.f};   // epi 5: this thread's part of each row's dsw sum
     for (int c = 0; c < g.N; c += 16) {
+      const int col = c + c4;
+      const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      float4 o0[4], o1[4], o2[4], o3[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        o0[u] = o1[u] = o2[u] = o3[u] = z4;
+        const long long row = rowu[u];
+        if constexpr (EPI == 3) {        // Ai of the slot's atom, Bj of its neighbour, e_in
+          if (jnu[u] >= 0) {
+            o0[u] = *reinterpret_cast<const float4*>(g.Ai + (long long)((int)row / g.nmax) * g.ldc + col);
+            o1[u] = *reinterpret_cast<const float4*>(g.Bj + (long long)jnu[u] * g.ldc + col);
+            o2[u] = *reinterpret_cast<const float4*>(g.e_in + row * g.ldc + col);
+          }
+        } else if constexpr (EPI == 5) { // de, and on kept slots g_i, u_j, e_in
+          if (row >= 0) o0[u] = *reinterpret_cast<const float4*>(g.C + row * g.ldc + col);
+          if (jnu[u] >= 0) {
+            o1[u] = *reinterpret_cast<const float4*>(g.dm + (long long)((int)row / g.nmax) * g.lddm + col);
+            o2[u] = *reinterpret_cast<const float4*>(g.u + (long long)jnu[u] * g.ldc + col);
+            o3[u] = *reinterpret_cast<const float4*>(g.e_in + row * g.ldc + col);
+          }
+        } else if constexpr (EPI == 4) { // e_in of the output row
+          if (xru[u] >= 0) o0[u] = *reinterpret_cast<const float4*>(g.e_in + xru[u] * g.ldc + col);
+        } else {                         // C (beta != 0), aux (epi 2)
+          if (row >= 0) {
+            if (g.beta != 0.f) o0[u] = *reinterpret_cast<const float4*>(g.C + row * g.ldc + col);
+            if (g.epi == 2) o1[u] = *reinterpret_cast<const float4*>(g.aux + row * g.ldc + col);
+          }
+        }
+      }
       float v[16];
       tc::tmem_ld16(tb + lane_off + (uint32_t)c, v);
 #pragma unroll
@@ -238,23 +299,20 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
         *reinterpret_cast<float4*>(st + lane * kStageLd + 4 * q) =
             make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
       __syncwarp();
+      const float4 bv = g.bias ? *reinterpret_cast<const float4*>(g.bias + col) : z4;
+      const float b[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int f = lane + 32 * u, rl = f >> 2, c4 = (f & 3) << 2;
-        const long long m = m0 + 32 * warp + rl;
-        if (m >= g.M) continue;
+        const long long row = rowu[u];
+        if (row < 0) continue;
+        const int rl = (lane >> 2) + 8 * u;
         const float4 acc = *reinterpret_cast<const float4*>(st + rl * kStageLd + c4);
         const float x[4] = {acc.x, acc.y, acc.z, acc.w};
-        const int col = c + c4;
-        const long long row = g.c_rows ? (long long)g.c_rows[m] : m;
         float4* Cp = reinterpret_cast<float4*>(g.C + row * g.ldc + col);
-        const float4 bv = g.bias ? *reinterpret_cast<const float4*>(g.bias + col)
-                                 : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float b[4] = {bv.x, bv.y, bv.z, bv.w};
         if constexpr (EPI == 4) {   // angle output: t = tanh(acc + b), e_out = e_in + sa t
-          const long long xr = g.x_rows ? (long long)g.x_rows[m] : row;
-          const float4 e = *reinterpret_cast<const float4*>(g.e_in + xr * g.ldc + col);
-          const float sw = g.sa[xr];
+          const long long xr = xru[u];
+          const float4 e = o0[u];
+          const float sw = fu[u];
           float y[4];
 #pragma unroll
           for (int q = 0; q < 4; ++q) y[q] = tanhf(x[q] + b[q]);
@@ -264,14 +322,11 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
           continue;
         }
         if constexpr (EPI == 5) {   // edge adjoint and the message's adjoint on kept slots
-          const float4 dv = *Cp;
+          const float4 dv = o0[u];
           float y[4] = {dv.x + x[0], dv.y + x[1], dv.z + x[2], dv.w + x[3]};
-          const int jn = g.sel_j[row];
-          if (jn >= 0) {
-            const float f = g.inv_nmax * g.sw[row];
-            const float4 gv = *reinterpret_cast<const float4*>(g.dm + (long long)((int)row / g.nmax) * g.lddm + col);
-            const float4 uv = *reinterpret_cast<const float4*>(g.u + (long long)jn * g.ldc + col);
-            const float4 ev = *reinterpret_cast<const float4*>(g.e_in + row * g.ldc + col);
+          if (jnu[u] >= 0) {
+            const float f = fu[u];
+            const float4 gv = o1[u], uv = o2[u], ev = o3[u];
             const float gq[4] = {gv.x, gv.y, gv.z, gv.w}, uq[4] = {uv.x, uv.y, uv.z, uv.w},
                         eq[4] = {ev.x, ev.y, ev.z, ev.w};
             float xo[4];
@@ -290,16 +345,13 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
           continue;
         }
         if constexpr (EPI == 3) {   // edge update: v = tanh(Ai + Bj + acc + b), e1 = e_in + v
-          const int jn = g.sel_j[row];
-          if (jn < 0) {
+          if (jnu[u] < 0) {
             if (g.v16) *reinterpret_cast<uint2*>(g.v16 + row * g.ldc + col) = make_uint2(0u, 0u);
             else *reinterpret_cast<float4*>(g.v_out + row * g.ldc + col) = make_float4(0.f, 0.f, 0.f, 0.f);
             *Cp = make_float4(0.f, 0.f, 0.f, 0.f);
             continue;
           }
-          const float4 av = *reinterpret_cast<const float4*>(g.Ai + (long long)((int)row / g.nmax) * g.ldc + col);
-          const float4 bj = *reinterpret_cast<const float4*>(g.Bj + (long long)jn * g.ldc + col);
-          const float4 e = *reinterpret_cast<const float4*>(g.e_in + row * g.ldc + col);
+          const float4 av = o0[u], bj = o1[u], e = o2[u];
           const float y0 = tanhf(av.x + bj.x + x[0] + b[0]);
           const float y1 = tanhf(av.y + bj.y + x[1] + b[1]);
           const float y2 = tanhf(av.z + bj.z + x[2] + b[2]);
@@ -309,15 +361,8 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
           *Cp = make_float4(e.x + y0, e.y + y1, e.z + y2, e.w + y3);
           continue;
         }
-        float cin[4] = {0.f, 0.f, 0.f, 0.f}, ax[4] = {0.f, 0.f, 0.f, 0.f};
-        if (g.beta != 0.f) {
-          const float4 w = *Cp;
-          cin[0] = w.x; cin[1] = w.y; cin[2] = w.z; cin[3] = w.w;
-        }
-        if (g.epi == 2) {
-          const float4 w = *reinterpret_cast<const float4*>(g.aux + row * g.ldc + col);
-          ax[0] = w.x; ax[1] = w.y; ax[2] = w.z; ax[3] = w.w;
-        }
+        const float cin[4] = {o0[u].x, o0[u].y, o0[u].z, o0[u].w};
+        const float ax[4] = {o1[u].x, o1[u].y, o1[u].z, o1[u].w};
         float y[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -340,11 +385,7 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
         float v = dacc[u];
         v += __shfl_xor_sync(0xffffffffu, v, 1);
         v += __shfl_xor_sync(0xffffffffu, v, 2);
-        const long long m = m0 + 32 * warp + (lane >> 2) + 8 * u;
-        if ((lane & 3) == 0 && m < g.M) {
-          const long long row = g.c_rows ? (long long)g.c_rows[m] : m;
-          if (g.sel_j[row] >= 0) g.dsw[row] += g.inv_nmax * v;
-        }
+        if ((lane & 3) == 0 && jnu[u] >= 0) g.dsw[rowu[u]] += g.inv_nmax * v;
       }
     }
     tc::fence_before_sync();
