@@ -135,6 +135,37 @@ __device__ __forceinline__ __int128 to_fixed(double v, bool* bad) {
   return v < 0 ? -(__int128)u : (__int128)u;
 }
 
+// The same conversions from the bit patterns, in integer arithmetic only
+// (this part's FP64 pipe retires about two lanes per clock per SM): for a
+// binary floating-point value m 2^(e - bias - mbits), v 2^80 truncated toward
+// zero is m shifted by e - bias - mbits + 80.  Same results as to_fixed.
+__device__ __forceinline__ __int128 shift_fixed(unsigned long long m, int sh, bool neg) {
+  unsigned __int128 u;
+  if (sh >= 0) u = (unsigned __int128)m << sh;
+  else u = sh > -64 ? (unsigned __int128)(m >> -sh) : 0;
+  return neg ? -(__int128)u : (__int128)u;
+}
+__device__ __forceinline__ __int128 to_fixed_f32(float v, bool* bad) {
+  const unsigned b = __float_as_uint(v);
+  const int e = (int)((b >> 23) & 0xffu);
+  if (e >= 127 + 46) {   // |v| >= 2^46, infinite or NaN
+    *bad = true;
+    return 0;
+  }
+  const unsigned long long m = (b & 0x7fffffu) | (e ? 0x800000u : 0u);
+  return shift_fixed(m, (e ? e : 1) - 127 - 23 + 80, (b >> 31) != 0);
+}
+__device__ __forceinline__ __int128 to_fixed_f64(double v, bool* bad) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7ffu);
+  if (e >= 1023 + 46) {
+    *bad = true;
+    return 0;
+  }
+  const unsigned long long m = (b & 0xfffffffffffffull) | (e ? (1ull << 52) : 0ull);
+  return shift_fixed(m, (e ? e : 1) - 1023 - 52 + 80, (b >> 63) != 0);
+}
+
 __device__ __forceinline__ __int128 warp_sum_fixed(__int128 v) {
   for (int o = 16; o > 0; o >>= 1) {
     const unsigned long long lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)v, o);

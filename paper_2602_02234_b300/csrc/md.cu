@@ -6,11 +6,15 @@
 // g = dE/dr_ij for r_ij = x_j - x_i.  The second sum is gathered, not
 // scattered: each skin entry (i -> j) knows the index of its mirror entry
 // (j -> i) in j's skin list, and selpos says which kept slot that is.  The
-// first sum runs over the kept slots in their (canonical) order.  The second
-// runs in skin-list order, which depends on when the list was last rebuilt,
-// so it is accumulated exactly in 128-bit fixed point (2^-80 resolution) and
-// rounded once: no atomics, and the force does not depend on the rebuild
-// schedule or on which other systems share the batch (bitwise reproducible).
+// second sum runs in skin-list order, which depends on when the list was last
+// rebuilt, so it is accumulated exactly in 128-bit fixed point (2^-80
+// resolution) and rounded once: no atomics, and the force does not depend on
+// the rebuild schedule or on which other systems share the batch (bitwise
+// reproducible).  With FP32 pair gradients the first sum and the per-atom
+// virial are accumulated the same way, in integer arithmetic; with FP64 ones
+// (the FP64 path) they are FP64 sums over the kept slots in their order.
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -26,6 +30,50 @@ __global__ void k_force_gather(int atom0, int n, int nmax, int cap, const int* _
   int i = atom0 + (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   int lane = threadIdx.x & 31;
   if (i >= n) return;
+  if constexpr (std::is_same<G, float>::value) {
+    // FP32 pair gradients: both force sums and the virial's FP32 products
+    // r_a g_b are accumulated exactly in 128-bit fixed point with integer
+    // arithmetic (no FP64 pipe work per slot), and each total is rounded
+    // once to FP64, by a lane of its own.
+    __int128 acc[12];   // F (3), then the virial -sum r_a g_b (9)
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = 0;
+    bool bad = false;
+    for (int p = lane; p < nmax; p += 32) {
+      const size_t o = (size_t)i * nmax + p;
+      if (sel_j[o] < 0) continue;
+      const float gg[3] = {g[3 * o], g[3 * o + 1], g[3 * o + 2]};
+      const float r[3] = {(float)sel_r[3 * o], (float)sel_r[3 * o + 1], (float)sel_r[3 * o + 2]};
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        acc[a] += to_fixed_f32(gg[a], &bad);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) acc[3 + 3 * a + b] -= to_fixed_f32(r[a] * gg[b], &bad);
+      }
+    }
+    const int cnt = skin_cnt[i];
+    for (int c = lane; c < cnt; c += 32) {
+      const size_t o = (size_t)i * cap + c;
+      const int mc = mirror[o];
+      if (mc < 0) continue;
+      const int j = skin[o].j;
+      const int p = selpos[(size_t)j * cap + mc];
+      if (p < 0) continue;
+      const size_t q = (size_t)j * nmax + p;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) acc[a] -= to_fixed_f32(g[3 * q + a], &bad);
+    }
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = warp_sum_fixed(acc[k]);
+    bad = __any_sync(0xffffffffu, bad);
+    __int128 mine = acc[0];
+#pragma unroll
+    for (int k = 1; k < 12; ++k)
+      if (lane == k) mine = acc[k];
+    if (lane < 3) F[3 * i + lane] = bad ? quiet_nan() : from_fixed(mine);
+    else if (lane < 12) atom_vir[9 * i + lane - 3] = from_fixed(mine);
+    return;
+  }
   double f[3] = {0, 0, 0};
   double vir[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   for (int p = lane; p < nmax; p += 32) {
@@ -74,42 +122,61 @@ void launch_force_gather(const ForceArgs& a, cudaStream_t st) {
                                                   a.atom_vir);
 }
 
-// one block per system: E and virial in FP64, fixed summation order
-// With a DP group, atoms outside it contribute nothing (their energy is set
-// to 0; they have no kept pairs, so no virial or force either).
-__global__ void k_reduce(const int* __restrict__ sys_atom0, double* __restrict__ atom_e,
-                         const double* __restrict__ atom_vir, const double* __restrict__ F,
-                         double* __restrict__ sys_e, double* __restrict__ sys_vir,
-                         int* __restrict__ flags, const unsigned char* __restrict__ grp) {
-  int s = blockIdx.x;
-  int a0 = sys_atom0[s], a1 = sys_atom0[s + 1];
-  __shared__ double sh[10][256];
-  double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+// One block per system: E and the virial summed exactly in 128-bit fixed
+// point (integer arithmetic, 2^-80 resolution) and rounded once to FP64, so
+// the totals do not depend on the summation order.  A value that is not
+// finite, or beyond the fixed-point range (|v| >= 2^46), raises the
+// non-finite flag, as a non-finite force does.  With a DP group, atoms
+// outside it contribute nothing (their energy is set to 0; they have no kept
+// pairs, so no virial or force either).
+constexpr int kReduceThreads = 1024;
+__global__ void __launch_bounds__(kReduceThreads) k_reduce(
+    const int* __restrict__ sys_atom0, double* __restrict__ atom_e, const double* __restrict__ atom_vir,
+    const double* __restrict__ F, double* __restrict__ sys_e, double* __restrict__ sys_vir,
+    int* __restrict__ flags, const unsigned char* __restrict__ grp) {
+  const int s = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int a0 = sys_atom0[s], a1 = sys_atom0[s + 1];
+  __shared__ unsigned long long sh[kReduceThreads / 32][10][2];
+  __int128 acc[10];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) acc[q] = 0;
   bool bad = false;
   for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
     if (grp && !grp[i]) atom_e[i] = 0.0;
-    acc[0] += atom_e[i];
-    for (int q = 0; q < 9; ++q) acc[1 + q] += atom_vir[9 * i + q];
-    for (int q = 0; q < 3; ++q) bad |= !isfinite(F[3 * i + q]);
-    bad |= !isfinite(atom_e[i]);
+    acc[0] += to_fixed_f64(atom_e[i], &bad);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) acc[1 + q] += to_fixed_f64(atom_vir[9 * (size_t)i + q], &bad);
+#pragma unroll
+    for (int q = 0; q < 3; ++q)   // exponent all ones: infinite or NaN
+      bad |= ((__double_as_longlong(F[3 * (size_t)i + q]) >> 52) & 0x7ff) == 0x7ff;
   }
-  if (bad) atomicOr(flags, kFlagNonFinite);
-  for (int q = 0; q < 10; ++q) sh[q][threadIdx.x] = acc[q];
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, kFlagNonFinite);
+#pragma unroll
+  for (int q = 0; q < 10; ++q) {
+    const __int128 v = warp_sum_fixed(acc[q]);
+    if (lane == 0) {
+      sh[warp][q][0] = (unsigned long long)v;
+      sh[warp][q][1] = (unsigned long long)(v >> 64);
+    }
+  }
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o)
-      for (int q = 0; q < 10; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + o];
-    __syncthreads();
+  if (warp != 0) return;
+  const int nw = blockDim.x >> 5;
+  __int128 mine = 0;
+#pragma unroll
+  for (int q = 0; q < 10; ++q) {
+    __int128 v = 0;
+    if (lane < nw) v = (__int128)(((unsigned __int128)sh[lane][q][1] << 64) | sh[lane][q][0]);
+    v = warp_sum_fixed(v);
+    if (lane == q) mine = v;
   }
-  if (threadIdx.x == 0) {
-    sys_e[s] = sh[0][0];
-    for (int q = 0; q < 9; ++q) sys_vir[9 * s + q] = sh[1 + q][0];
-  }
+  if (lane == 0) sys_e[s] = from_fixed(mine);
+  else if (lane < 10) sys_vir[9 * s + lane - 1] = from_fixed(mine);
 }
 
 void launch_reduce(const ReduceArgs& a, cudaStream_t st) {
-  k_reduce<<<a.n_sys, 256, 0, st>>>(a.sys_atom0, a.atom_e_out, a.atom_vir, a.F, a.sys_e,
-                                    a.sys_vir, a.flags, a.grp);
+  k_reduce<<<a.n_sys, kReduceThreads, 0, st>>>(a.sys_atom0, a.atom_e_out, a.atom_vir, a.F, a.sys_e,
+                                               a.sys_vir, a.flags, a.grp);
 }
 
 // v += dt/2 F/m; x += dt v; request a neighbour rebuild when an atom moved
@@ -203,22 +270,30 @@ void launch_compare(long long count, const double* a, const double* b, int* diff
 }
 
 // one block per (system, extra fitting head), fixed summation order
-__global__ void k_head_reduce(int heads, int n, const int* __restrict__ sys_atom0,
-                              const double* __restrict__ head_e, const unsigned char* __restrict__ grp,
-                              double* __restrict__ out) {
-  const int s = blockIdx.x, h = blockIdx.y;
+__global__ void __launch_bounds__(256) k_head_reduce(int heads, int n, const int* __restrict__ sys_atom0,
+                                                     const double* __restrict__ head_e,
+                                                     const unsigned char* __restrict__ grp,
+                                                     double* __restrict__ out) {
+  // the exact fixed-point sum of k_reduce, so that head 0's total equals E
+  const int s = blockIdx.x, h = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int a0 = sys_atom0[s], a1 = sys_atom0[s + 1];
-  __shared__ double sh[256];
-  double acc = 0.0;
+  __shared__ unsigned long long sh[8][2];
+  __int128 acc = 0;
+  bool bad = false;
   for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x)
-    if (!grp || grp[i]) acc += head_e[(size_t)h * n + i];
-  sh[threadIdx.x] = acc;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-    __syncthreads();
+    if (!grp || grp[i]) acc += to_fixed_f64(head_e[(size_t)h * n + i], &bad);
+  bad = __syncthreads_or(bad) != 0;
+  acc = warp_sum_fixed(acc);
+  if (lane == 0) {
+    sh[warp][0] = (unsigned long long)acc;
+    sh[warp][1] = (unsigned long long)(acc >> 64);
   }
-  if (threadIdx.x == 0) out[(size_t)s * heads + h] = sh[0];
+  __syncthreads();
+  if (warp != 0) return;
+  __int128 v = 0;
+  if (lane < (int)(blockDim.x >> 5)) v = (__int128)(((unsigned __int128)sh[lane][1] << 64) | sh[lane][0]);
+  v = warp_sum_fixed(v);
+  if (lane == 0) out[(size_t)s * heads + h] = bad ? quiet_nan() : from_fixed(v);
 }
 
 void launch_head_reduce(int n_sys, int heads, int n, const int* sys_atom0, const double* head_e,

@@ -464,6 +464,11 @@ void launch_select(const NlistArgs& a, cudaStream_t st) {
 void launch_flag_set(int* flags, int bits, cudaStream_t st) { k_flag_set<<<1, 32, 0, st>>>(flags, bits); }
 
 cudaError_t nlist_configure() {
+  // the largest shared-memory carve-out: each warp holds its atom's candidates
+  // there, and more resident warps hide the latency of the FP64 distances
+  cudaError_t e = cudaFuncSetAttribute(k_select, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       (int)cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)kSelectSmemMax);
 }
