@@ -50,7 +50,8 @@ enum {
   DP_ERR_OOM = -2,             /* device memory (or the set budget) exceeded */
   DP_ERR_NLIST_OVERFLOW = -3,  /* more candidates than the list capacity     */
   DP_ERR_TIMEOUT = -4,         /* a device-side wait gave up                 */
-  DP_ERR_NONFINITE = -5,       /* energy or forces not finite                */
+  DP_ERR_NONFINITE = -5,       /* energy, forces or virial not finite, or    */
+                               /* beyond +-2^46 (the exact sums' range)      */
   DP_ERR_CUDA = -6,            /* a CUDA runtime call failed                 */
   DP_ERR_UNSUPPORTED = -7      /* valid request the library does not support */
 };
