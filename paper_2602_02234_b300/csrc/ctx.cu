@@ -72,6 +72,7 @@ struct dp_ctx {
   int *sel_j = nullptr, *sel_img = nullptr, *n_in_rc = nullptr;
   double* sel_r = nullptr;
   double *atom_e = nullptr, *atom_vir = nullptr, *sys_e = nullptr, *sys_vir = nullptr;
+  double* atom_ke = nullptr;   // kinetic energy per atom (final kick -> record)
   int* flags = nullptr;
   long long* step = nullptr;   // [0] step counter, [1] trace base
   // dp_step's checkpoint for a retry after a neighbour-capacity overflow
@@ -259,7 +260,7 @@ static MdArgs md_args(dp_ctx* c, double dt) {
   m.n = c->n; m.dt = dt; m.x = c->x; m.v = c->v; m.F = c->F; m.minv = c->minv; m.mass = c->mass;
   m.xref = c->xref; m.half_skin2 = 0.25 * c->skin * c->skin; m.rebuild_every = c->rebuild_every;
   m.step = c->step; m.flags = c->flags; m.n_sys = c->n_sys; m.sys_atom0 = c->sys_atom0;
-  m.sys_of = c->sys_of;
+  m.sys_of = c->sys_of; m.atom_ke = c->atom_ke;
   return m;
 }
 
@@ -450,6 +451,7 @@ static int ctx_create(dp_ctx** out, const dp_model_desc* desc, const double* mas
   TRY(dalloc(c, &c->n_in_rc, N), "sel");
   TRY(dalloc(c, &c->atom_e, N), "energies");
   TRY(dalloc(c, &c->atom_vir, 9 * N), "virials");
+  TRY(dalloc(c, &c->atom_ke, N), "kinetic energies");
   TRY(dalloc(c, &c->sys_e, S), "energies");
   if (c->af.fit_heads > 1) TRY(dalloc(c, &c->head_sys_e, S * (c->af.fit_heads - 1)), "energies");
   TRY(dalloc(c, &c->sys_vir, 9 * S), "virials");

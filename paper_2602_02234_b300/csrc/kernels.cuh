@@ -84,7 +84,7 @@ struct MdArgs {
   int rebuild_every;
   long long* step;       // device step counter
   int* flags;
-  double* sys_ekin;      // n_sys
+  double* atom_ke;       // n: kinetic energy per atom, written by the final kick
   int n_sys;
   const int* sys_atom0;
   const int* sys_of;

@@ -205,11 +205,21 @@ __global__ void k_kick_drift(int n, double dt, double* __restrict__ x, double* _
   if (d2 > half_skin2) atomicOr(flags, kFlagRebuild);
 }
 
+// v += dt/2 F/m, and the atom's kinetic energy sum_a (m/2) v_a^2 (FP64,
+// spread over the whole grid) for the step's record
 __global__ void k_kick(int n, double dt, double* __restrict__ v, const double* __restrict__ F,
-                       const double* __restrict__ minv) {
+                       const double* __restrict__ minv, const double* __restrict__ mass,
+                       double* __restrict__ ke) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  for (int a = 0; a < 3; ++a) v[3 * i + a] += 0.5 * dt * F[3 * i + a] * minv[i];
+  const double hm = 0.5 * mass[i];
+  double k = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    const double vv = v[3 * i + a] + 0.5 * dt * F[3 * i + a] * minv[i];
+    v[3 * i + a] = vv;
+    k += hm * vv * vv;
+  }
+  ke[i] = k;
 }
 
 void launch_kick_drift(const MdArgs& a, cudaStream_t st) {
@@ -218,31 +228,39 @@ void launch_kick_drift(const MdArgs& a, cudaStream_t st) {
 }
 
 void launch_kick_final(const MdArgs& a, cudaStream_t st) {
-  k_kick<<<ceil_div(a.n, 256), 256, 0, st>>>(a.n, a.dt, a.v, a.F, a.minv);
+  k_kick<<<ceil_div(a.n, 256), 256, 0, st>>>(a.n, a.dt, a.v, a.F, a.minv, a.mass, a.atom_ke);
 }
 
-// per system: {E_pot, E_kin} of the step just finished into trace[step - base - 1]
-__global__ void k_record(const int* __restrict__ sys_atom0, const double* __restrict__ v,
-                         const double* __restrict__ mass, double inv_kappa,
-                         const double* __restrict__ sys_e, const long long* __restrict__ step,
-                         double* __restrict__ trace, int n_sys, int trace_len) {
-  int s = blockIdx.x;
-  int a0 = sys_atom0[s], a1 = sys_atom0[s + 1];
-  __shared__ double sh[256];
-  double acc = 0;
-  for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x)
-    for (int a = 0; a < 3; ++a) acc += 0.5 * mass[i] * v[3 * i + a] * v[3 * i + a];
-  sh[threadIdx.x] = acc;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-    __syncthreads();
+// per system: {E_pot, E_kin} of the step just finished into trace[step - base - 1];
+// E_kin is the exact fixed-point sum of the atoms' kinetic energies (from the
+// final kick), rounded once
+__global__ void __launch_bounds__(256) k_record(const int* __restrict__ sys_atom0,
+                                                const double* __restrict__ ke, double inv_kappa,
+                                                const double* __restrict__ sys_e,
+                                                const long long* __restrict__ step,
+                                                double* __restrict__ trace, int n_sys, int trace_len) {
+  const int s = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int a0 = sys_atom0[s], a1 = sys_atom0[s + 1];
+  __shared__ unsigned long long sh[8][2];
+  __int128 acc = 0;
+  bool bad = false;
+  for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) acc += to_fixed_f64(ke[i], &bad);
+  bad = __syncthreads_or(bad) != 0;
+  acc = warp_sum_fixed(acc);
+  if (lane == 0) {
+    sh[warp][0] = (unsigned long long)acc;
+    sh[warp][1] = (unsigned long long)(acc >> 64);
   }
-  if (threadIdx.x == 0) {
+  __syncthreads();
+  if (warp != 0) return;
+  __int128 v = 0;
+  if (lane < (int)(blockDim.x >> 5)) v = (__int128)(((unsigned __int128)sh[lane][1] << 64) | sh[lane][0]);
+  v = warp_sum_fixed(v);
+  if (lane == 0) {
     long long slot = step[0] - step[1] - 1;   // step[1] holds the base
     if (slot >= 0 && slot < trace_len) {
       trace[(slot * n_sys + s) * 2 + 0] = sys_e[s];
-      trace[(slot * n_sys + s) * 2 + 1] = sh[0] * inv_kappa;
+      trace[(slot * n_sys + s) * 2 + 1] = bad ? quiet_nan() : from_fixed(v) * inv_kappa;
     }
   }
 }
@@ -250,7 +268,7 @@ __global__ void k_record(const int* __restrict__ sys_atom0, const double* __rest
 void launch_record(const MdArgs& a, const double* sys_e, double* trace, int trace_len,
                    cudaStream_t st) {
   const double kappa = 1.602176634e-19 / (1.66053906660e-27 * 1e10);
-  k_record<<<a.n_sys, 256, 0, st>>>(a.sys_atom0, a.v, a.mass, 1.0 / kappa, sys_e, a.step, trace,
+  k_record<<<a.n_sys, 256, 0, st>>>(a.sys_atom0, a.atom_ke, 1.0 / kappa, sys_e, a.step, trace,
                                     a.n_sys, trace_len);
 }
 
