@@ -37,6 +37,21 @@ __device__ __forceinline__ uint2 pack4(int fp16, float a, float b, float c, floa
               : make_uint2(tc::pack_bf16(a, b), tc::pack_bf16(c, d));
 }
 
+// four 16-bit values, loaded as raw bits, as FP32 (the conversion is kept
+// apart from the load: the epilogue issues all of a block's loads first, and
+// a conversion next to its load would make the warp wait for that load)
+__device__ __forceinline__ float4 unpack4(int fp16, uint2 u) {
+  float2 a, b;
+  if (fp16) {
+    a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+    b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+  } else {
+    a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+    b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+  }
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+
 // EPI: 3, 4 or 5 for those epilogues, 0 for the others (none, tanh, the
 // 1 - aux^2 factor), so that each variant carries only its own epilogue
 template <int EPI>
@@ -266,25 +281,32 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
       const int col = c + c4;
       const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
       float4 o0[4], o1[4], o2[4], o3[4];
+      uint2 e16r[4];   // 16-bit edge rows (g.e16), converted where used
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         o0[u] = o1[u] = o2[u] = o3[u] = z4;
+        e16r[u] = make_uint2(0u, 0u);
         const long long row = rowu[u];
         if constexpr (EPI == 3) {        // Ai of the slot's atom, Bj of its neighbour, e_in
           if (jnu[u] >= 0) {
             o0[u] = *reinterpret_cast<const float4*>(g.Ai + (long long)((int)row / g.nmax) * g.ldc + col);
             o1[u] = *reinterpret_cast<const float4*>(g.Bj + (long long)jnu[u] * g.ldc + col);
-            o2[u] = *reinterpret_cast<const float4*>(g.e_in + row * g.ldc + col);
+            if (g.e16) e16r[u] = *reinterpret_cast<const uint2*>(g.e16 + row * g.ldc + col);
+            else o2[u] = *reinterpret_cast<const float4*>(g.e_in + row * g.ldc + col);
           }
         } else if constexpr (EPI == 5) { // de, and on kept slots g_i, u_j, e_in
           if (row >= 0) o0[u] = *reinterpret_cast<const float4*>(g.C + row * g.ldc + col);
           if (jnu[u] >= 0) {
             o1[u] = *reinterpret_cast<const float4*>(g.dm + (long long)((int)row / g.nmax) * g.lddm + col);
             o2[u] = *reinterpret_cast<const float4*>(g.u + (long long)jnu[u] * g.ldc + col);
-            o3[u] = *reinterpret_cast<const float4*>(g.e_in + row * g.ldc + col);
+            if (g.e16) e16r[u] = *reinterpret_cast<const uint2*>(g.e16 + row * g.ldc + col);
+            else o3[u] = *reinterpret_cast<const float4*>(g.e_in + row * g.ldc + col);
           }
         } else if constexpr (EPI == 4) { // e_in of the output row
-          if (xru[u] >= 0) o0[u] = *reinterpret_cast<const float4*>(g.e_in + xru[u] * g.ldc + col);
+          if (xru[u] >= 0) {
+            if (g.e16) e16r[u] = *reinterpret_cast<const uint2*>(g.e16 + xru[u] * g.ldc + col);
+            else o0[u] = *reinterpret_cast<const float4*>(g.e_in + xru[u] * g.ldc + col);
+          }
         } else {                         // C (beta != 0), aux (epi 2)
           if (row >= 0) {
             if (g.beta != 0.f) o0[u] = *reinterpret_cast<const float4*>(g.C + row * g.ldc + col);
@@ -311,14 +333,18 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
         float4* Cp = reinterpret_cast<float4*>(g.C + row * g.ldc + col);
         if constexpr (EPI == 4) {   // angle output: t = tanh(acc + b), e_out = e_in + sa t
           const long long xr = xru[u];
-          const float4 e = o0[u];
+          const float4 e = g.e16 ? unpack4(g.fp16, e16r[u]) : o0[u];
           const float sw = fu[u];
           float y[4];
 #pragma unroll
           for (int q = 0; q < 4; ++q) y[q] = tanhf(x[q] + b[q]);
           *Cp = make_float4(y[0], y[1], y[2], y[3]);
-          *reinterpret_cast<float4*>(g.v_out + xr * g.ldc + col) =
-              make_float4(e.x + sw * y[0], e.y + sw * y[1], e.z + sw * y[2], e.w + sw * y[3]);
+          if (g.o16)
+            *reinterpret_cast<uint2*>(g.o16 + xr * g.ldc + col) =
+                pack4(g.fp16, e.x + sw * y[0], e.y + sw * y[1], e.z + sw * y[2], e.w + sw * y[3]);
+          else
+            *reinterpret_cast<float4*>(g.v_out + xr * g.ldc + col) =
+                make_float4(e.x + sw * y[0], e.y + sw * y[1], e.z + sw * y[2], e.w + sw * y[3]);
           continue;
         }
         if constexpr (EPI == 5) {   // edge adjoint and the message's adjoint on kept slots
@@ -326,7 +352,7 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
           float y[4] = {dv.x + x[0], dv.y + x[1], dv.z + x[2], dv.w + x[3]};
           if (jnu[u] >= 0) {
             const float f = fu[u];
-            const float4 gv = o1[u], uv = o2[u], ev = o3[u];
+            const float4 gv = o1[u], uv = o2[u], ev = g.e16 ? unpack4(g.fp16, e16r[u]) : o3[u];
             const float gq[4] = {gv.x, gv.y, gv.z, gv.w}, uq[4] = {uv.x, uv.y, uv.z, uv.w},
                         eq[4] = {ev.x, ev.y, ev.z, ev.w};
             float xo[4];
@@ -348,17 +374,19 @@ __global__ void __launch_bounds__(kRows) k_gemm_tc(GemmTc g, int tmem_cols) {
           if (jnu[u] < 0) {
             if (g.v16) *reinterpret_cast<uint2*>(g.v16 + row * g.ldc + col) = make_uint2(0u, 0u);
             else *reinterpret_cast<float4*>(g.v_out + row * g.ldc + col) = make_float4(0.f, 0.f, 0.f, 0.f);
-            *Cp = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (g.o16) *reinterpret_cast<uint2*>(g.o16 + row * g.ldc + col) = make_uint2(0u, 0u);
+            else *Cp = make_float4(0.f, 0.f, 0.f, 0.f);
             continue;
           }
-          const float4 av = o0[u], bj = o1[u], e = o2[u];
+          const float4 av = o0[u], bj = o1[u], e = g.e16 ? unpack4(g.fp16, e16r[u]) : o2[u];
           const float y0 = tanhf(av.x + bj.x + x[0] + b[0]);
           const float y1 = tanhf(av.y + bj.y + x[1] + b[1]);
           const float y2 = tanhf(av.z + bj.z + x[2] + b[2]);
           const float y3 = tanhf(av.w + bj.w + x[3] + b[3]);
           if (g.v16) *reinterpret_cast<uint2*>(g.v16 + row * g.ldc + col) = pack4(g.fp16, y0, y1, y2, y3);
           else *reinterpret_cast<float4*>(g.v_out + row * g.ldc + col) = make_float4(y0, y1, y2, y3);
-          *Cp = make_float4(e.x + y0, e.y + y1, e.z + y2, e.w + y3);
+          if (g.o16) *reinterpret_cast<uint2*>(g.o16 + row * g.ldc + col) = pack4(g.fp16, e.x + y0, e.y + y1, e.z + y2, e.w + y3);
+          else *Cp = make_float4(e.x + y0, e.y + y1, e.z + y2, e.w + y3);
           continue;
         }
         const float cin[4] = {o0[u].x, o0[u].y, o0[u].z, o0[u].w};

@@ -67,6 +67,11 @@ struct GemmTc {
   // both laid out like C
   const uint16_t* a16;
   uint16_t *v16, *x16;
+  // the edge state in 16 bits (the operand type), where set: e16 replaces
+  // e_in (epi 3, 4, 5), and o16 receives epi 3's C (e1, C itself unused) or
+  // epi 4's v_out (e_{l+1}; o16 may equal e16), all laid out like C
+  const uint16_t* e16;
+  uint16_t* o16;
 };
 
 bool gemm_tc_shape_ok(int N, int K);

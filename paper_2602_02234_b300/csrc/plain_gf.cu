@@ -82,6 +82,19 @@ __device__ __forceinline__ void ld4(const __nv_bfloat16* p, float* v) {
   const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
   v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
 }
+// two 16-bit values as raw bits, and their FP32 values (a batch of loads is
+// issued before any conversion: in-order issue would otherwise make the warp
+// wait for each load at its conversion)
+__device__ __forceinline__ uint32_t ld2raw(const __half* p) { return *reinterpret_cast<const uint32_t*>(p); }
+__device__ __forceinline__ uint32_t ld2raw(const __nv_bfloat16* p) {
+  return *reinterpret_cast<const uint32_t*>(p);
+}
+__device__ __forceinline__ float2 raw2f(uint32_t u, const __half*) {
+  return __half22float2(*reinterpret_cast<const __half2*>(&u));
+}
+__device__ __forceinline__ float2 raw2f(uint32_t u, const __nv_bfloat16*) {
+  return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u));
+}
 __device__ __forceinline__ void st4(__half* p, const float* v) {
   const __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
   *reinterpret_cast<uint2*>(p) = make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
@@ -122,11 +135,11 @@ __global__ void k_env(long long P, int nmax, int na, const int* __restrict__ sel
   }
 }
 
-template <typename T>
+template <typename T, typename E = T>   // E: storage of the edge state (T, or 16 bits)
 __global__ void k_init(int n, int nmax, int nd, int ed, const int* __restrict__ types,
                        const int* __restrict__ sel_j, const T* __restrict__ s,
                        const T* __restrict__ Wt, const T* __restrict__ we,
-                       const T* __restrict__ be0, T* __restrict__ node, T* __restrict__ edge) {
+                       const T* __restrict__ be0, T* __restrict__ node, E* __restrict__ edge) {
   int i = blockIdx.x;
   for (int c = threadIdx.x; c < nd; c += blockDim.x) node[(size_t)i * nd + c] = Wt[types[i] * nd + c];
   if ((ed & 3) == 0) {   // four columns per thread, one 16-byte store
@@ -147,7 +160,7 @@ __global__ void k_init(int n, int nmax, int nd, int ed, const int* __restrict__ 
   for (int idx = threadIdx.x; idx < nmax * ed; idx += blockDim.x) {
     int p = idx / ed, c = idx % ed;
     size_t e = (size_t)i * nmax + p;
-    edge[e * ed + c] = sel_j[e] >= 0 ? dtanh(s[e] * we[c] + be0[c]) : T(0);
+    edge[e * ed + c] = E(sel_j[e] >= 0 ? dtanh(s[e] * we[c] + be0[c]) : T(0));
   }
 }
 
@@ -170,13 +183,16 @@ __global__ void k_msg(int nmax, int ed, T inv_nmax, const int* __restrict__ sel_
 }
 
 // The same, one warp per atom: lane l owns columns 2l, 2l + 1 (+ 64 k), and
-// four slots' rows are read before any is summed; the sum runs over the
-// slots in order and stops at the first empty one, as above (the kept slots
-// are a prefix of the list).  ed even.
-template <typename T>
+// a batch of slots' rows is read before any is summed (four slots, or eight
+// when the edge rows are 16-bit, so that as many bytes are in flight); the
+// sum runs over the slots in order and stops at the first empty one, as above
+// (the kept slots are a prefix of the list).  ed even.
+template <typename T, typename E = T>   // E: storage of the edge state
 __global__ void k_msg_warp(int n, int nmax, int ed, T inv_nmax, const int* __restrict__ sel_j,
-                           const T* __restrict__ sw, const T* __restrict__ edge,
+                           const T* __restrict__ sw, const E* __restrict__ edge,
                            const T* __restrict__ u, T* __restrict__ m) {
+  constexpr bool k16 = sizeof(E) == 2;
+  constexpr int B = k16 ? 8 : 4;
   const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (i >= n) return;
@@ -184,27 +200,37 @@ __global__ void k_msg_warp(int n, int nmax, int ed, T inv_nmax, const int* __res
   for (int c = 2 * lane; c < ed; c += 64) {
     T a0 = T(0), a1 = T(0);
     bool done = false;
-    for (int p = 0; p < nmax && !done; p += 4) {
-      int jj[4];
-      T sv[4], e0[4], e1[4], u0[4], u1[4];
+    for (int p = 0; p < nmax && !done; p += B) {
+      int jj[B];
+      T sv[B], e0[B], e1[B], u0[B], u1[B];
+      uint32_t er[B];   // 16-bit edge rows, converted below
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < B; ++q) {
         jj[q] = p + q < nmax ? sel_j[base + p + q] : -1;
         if (jj[q] >= 0) {
           const size_t e = base + p + q;
-          T ev[2], uv[2];
+          T uv[2];
           sv[q] = sw[e];
-          ld2(edge + e * ed + c, ev);
+          if constexpr (k16) {
+            er[q] = ld2raw(edge + e * ed + c);
+          } else {
+            T ev[2];
+            ld2(edge + e * ed + c, ev);
+            e0[q] = ev[0]; e1[q] = ev[1];
+          }
           ld2(u + (size_t)jj[q] * ed + c, uv);
-          e0[q] = ev[0]; e1[q] = ev[1];
           u0[q] = uv[0]; u1[q] = uv[1];
         }
       }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < B; ++q) {
         if (jj[q] < 0) {
           done = true;
           break;
+        }
+        if constexpr (k16) {
+          const float2 ev = raw2f(er[q], edge);
+          e0[q] = ev.x; e1[q] = ev.y;
         }
         a0 += sv[q] * e0[q] * u0[q];
         a1 += sv[q] * e1[q] * u1[q];
@@ -936,11 +962,11 @@ __global__ void k_pair_grad(long long P, int nmax, int ed, int atom0, const int*
 }
 // The same with 16 threads per slot, four columns each (ed a multiple of 4);
 // the ds sum closes with a fixed-order reduction over the 16 lanes.
-template <typename T>
+template <typename T, typename E = T>   // E: storage of the edge state
 __global__ void k_pair_grad4(long long P, int ed, const int* __restrict__ sel_j, const T* __restrict__ d,
                              const T* __restrict__ sw, const T* __restrict__ dsw,
                              const T* __restrict__ dsa, const T* __restrict__ rh,
-                             const T* __restrict__ e0, const T* __restrict__ we,
+                             const E* __restrict__ e0, const T* __restrict__ we,
                              const T* __restrict__ de, const T* __restrict__ dsw_e,
                              const T* __restrict__ dsa_e, const T* __restrict__ drh, T* __restrict__ g) {
   const long long s = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 4;
@@ -954,9 +980,9 @@ __global__ void k_pair_grad4(long long P, int ed, const int* __restrict__ sel_j,
   T ds = T(0);
   for (int c = 4 * l16; c < ed; c += 64) {
     T ev[4], dv[4], wv[4];
-    ld4(e0 + s * ed + c, ev);
-    ld4(de + s * ed + c, dv);
+    ld4(de + s * ed + c, dv);   // e0 last: a 16-bit e0 is converted right after its load
     ld4(we + c, wv);
+    ld4(e0 + s * ed + c, ev);
 #pragma unroll
     for (int q = 0; q < 4; ++q) ds += dv[q] * (T(1) - ev[q] * ev[q]) * wv[q];
   }
@@ -1049,7 +1075,11 @@ class PlainGf : public Model {
       t.C = ee_[l + 1]; t.ldc = Ed;   // e1; the angle channel then updates its rows in place
       t.bias = be_[l]; t.epi = 3;
       t.sel_j = nv.sel_j; t.nmax = m_.nmax; t.Ai = Ai_; t.Bj = Bj_; t.e_in = ee_[l]; t.v_out = vv_[l];
-      if (s16_) t.v16 = reinterpret_cast<uint16_t*>(vv16_[l]);
+      if (s16_) {
+        t.v16 = reinterpret_cast<uint16_t*>(vv16_[l]);
+        t.a16 = t.e16 = reinterpret_cast<const uint16_t*>(ee16_[l]);
+        t.o16 = reinterpret_cast<uint16_t*>(ee16_[l + 1]);
+      }
       t.status = flags_;
 #ifdef DP_GF_BF16
       t.fp16 = 0;
@@ -1078,6 +1108,10 @@ class PlainGf : public Model {
       t.C = tt_[l]; t.ldc = Ed;
       t.bias = bq_[l]; t.epi = 4;
       t.sa = sa_; t.e_in = ee_[l + 1]; t.v_out = ee_[l + 1]; t.x_rows = ang_rows_;
+      if (s16_) {
+        t.e16 = reinterpret_cast<const uint16_t*>(ee16_[l + 1]);
+        t.o16 = reinterpret_cast<uint16_t*>(ee16_[l + 1]);
+      }
       t.status = flags_;
 #ifdef DP_GF_BF16
       t.fp16 = 0;
@@ -1112,7 +1146,10 @@ class PlainGf : public Model {
       t.C = de_; t.ldc = Ed; t.beta = 1.f; t.epi = 5;
       t.sel_j = nv.sel_j; t.nmax = m_.nmax; t.sw = sw_; t.dm = dnm_ + Nd; t.lddm = Nd + Ed;
       t.u = uu_[l]; t.e_in = ee_[l]; t.x_out = X_; t.dsw = dsw_e_; t.inv_nmax = 1.f / (float)m_.nmax;
-      if (s16_) t.x16 = reinterpret_cast<uint16_t*>(X16_);
+      if (s16_) {
+        t.x16 = reinterpret_cast<uint16_t*>(X16_);
+        t.e16 = reinterpret_cast<const uint16_t*>(ee16_[l]);
+      }
       t.status = flags_;
 #ifdef DP_GF_BF16
       t.fp16 = 0;
@@ -1125,6 +1162,31 @@ class PlainGf : public Model {
       (void)l; (void)nv; (void)st;
     }
   }
+  // the angle channel's q = e_{l+1} Wp over the angle rows (their slots'
+  // rows of e gathered); in the mixed form from the 16-bit edge state
+  void q_product(int l, cudaStream_t st) {
+    const int Ed = m_.ed;
+    if constexpr (std::is_same<T, float>::value) {
+      if (s16_) {
+        GemmTc t{};
+        t.M = (int)((long long)n_ * nac_); t.N = Ed; t.K = Ed;
+        t.a16 = reinterpret_cast<const uint16_t*>(ee16_[l + 1]); t.lda = Ed; t.a_rows = ang_rows_;
+        t.B = Wp_[l]; t.ldb = Ed; t.b_nk = 0;
+        t.C = qq_[l]; t.ldc = Ed;
+        t.status = flags_;
+#ifdef DP_GF_BF16
+        t.fp16 = 0;
+#else
+        t.fp16 = 1;
+#endif
+        gemm_tc(t, st);
+        return;
+      }
+    }
+    Gemm<T> g = gemm_rowmajor<T>((int)((long long)n_ * nac_), Ed, Ed, ee_[l + 1], Ed, Wp_[l], Ed, qq_[l], Ed);
+    g.a_rows = ang_rows_;
+    mm(g, st);
+  }
   bool tc_ = false;
   // mixed form: v (the edge update's tanh, kept for the adjoint), dy (the
   // A operand of de += dy Wc^T) and X (the message adjoint's per-slot rows)
@@ -1132,6 +1194,10 @@ class PlainGf : public Model {
   using S16 = typename std::conditional<std::is_same<T, float>::value, gf16_t, T>::type;
   bool s16_ = false;
   std::vector<S16*> vv16_;
+  // the edge state e_0 .. e_L in 16 bits as well (mixed form): the tensor-core
+  // products round it to 16 bits anyway, and its residual updates e1 = e + v,
+  // e_{l+1} = e1 + swa t are rounded once per layer
+  std::vector<S16*> ee16_;
   S16 *dy16_ = nullptr, *X16_ = nullptr;
   int* flags_ = nullptr;
   const unsigned char* seed_ = nullptr;   // energy seed (device, optional)
@@ -1284,7 +1350,10 @@ bool PlainGf<T>::init(const GfDims& m, const double* w, int n_atoms, const int* 
   s16_ = tc_ && std::is_same<T, float>::value && Ed % 16 == 0 && Ed <= 256 && Nd % 4 == 0;
   vv16_.assign(L, nullptr);
   dy_ = X_ = nullptr;
-  for (int l = 0; l <= L && ok; ++l) ok = dalloc(&nn_[l], N * Nd, err) && dalloc(&ee_[l], P * Ed, err);
+  ee16_.assign(L + 1, nullptr);
+  for (int l = 0; l <= L && ok; ++l)
+    ok = dalloc(&nn_[l], N * Nd, err) &&
+         (s16_ ? dalloc(&ee16_[l], P * Ed, err) : dalloc(&ee_[l], P * Ed, err));
   for (int l = 0; l < L && ok; ++l)
     ok = dalloc(&hh_[l], N * Nd, err) && dalloc(&uu_[l], N * Ed, err) &&
          dalloc(&mm_[l], N * Ed, err) && (s16_ ? dalloc(&vv16_[l], P * Ed, err) : dalloc(&vv_[l], P * Ed, err)) && dalloc(&qq_[l], PA * Ed, err) &&
@@ -1349,14 +1418,20 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
   auto grid = [](long long n_) { return ceil_div(n_, 256); };
   k_env<T><<<grid(P), 256, 0, st>>>(P, NM, NA, nv.sel_j, nv.sel_r, m.rs, m.rc, m.rsa, m.rca, d_, sw_,
                                      dsw_, sa_, dsa_, s_, rh_);
-  k_init<T><<<n, 128, 0, st>>>(n, NM, Nd, Ed, types, nv.sel_j, s_, Wt_, we_, be0_, nn_[0], ee_[0]);
+  if (s16_)
+    k_init<T, S16><<<n, 128, 0, st>>>(n, NM, Nd, Ed, types, nv.sel_j, s_, Wt_, we_, be0_, nn_[0], ee16_[0]);
+  else
+    k_init<T><<<n, 128, 0, st>>>(n, NM, Nd, Ed, types, nv.sel_j, s_, Wt_, we_, be0_, nn_[0], ee_[0]);
   k += 2;
   const size_t angle_smem = angle_smem_, angle_bwd_smem = angle_bwd_smem_;
   const int ed_shift = (Ed & (Ed - 1)) == 0 ? __builtin_ctz((unsigned)Ed) : -1;
   for (int l = 0; l < L; ++l) {
     // (a)
     mm(gemm_rowmajor<T>(n, Ed, Nd, nn_[l], Nd, Wm_[l], Ed, uu_[l], Ed), st);
-    if (Ed % 2 == 0)
+    if (s16_)
+      k_msg_warp<T, S16><<<ceil_div((long long)n * 32, 256), 256, 0, st>>>(n, NM, Ed, inv_nmax, nv.sel_j,
+                                                                            sw_, ee16_[l], uu_[l], mm_[l]);
+    else if (Ed % 2 == 0)
       k_msg_warp<T><<<ceil_div((long long)n * 32, 256), 256, 0, st>>>(n, NM, Ed, inv_nmax, nv.sel_j, sw_,
                                                                        ee_[l], uu_[l], mm_[l]);
     else
@@ -1382,11 +1457,7 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
                                           ee_[l], vv_[l], ee_[l + 1]);
     }
     // (c) on the angle rows; e_{l+1} holds e1 until the angle update below
-    {
-      Gemm<T> g = gemm_rowmajor<T>((int)PA, Ed, Ed, ee_[l + 1], Ed, Wp_[l], Ed, qq_[l], Ed);
-      g.a_rows = ang_rows_;
-      mm(g, st);
-    }
+    q_product(l, st);
     k_angle<T><<<angle_grid_, kAngThreads, angle_smem, st>>>(n, NM, NA, CA, Ed, inv_na, sa_, rh_, qq_[l],
                                                              Wphi_[l], aa_);
     if (angle_out_fused(l, st)) {
@@ -1540,7 +1611,10 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
     }
     k += 18 - (fused_rowsum ? 1 : 0) - (fused_msg ? 1 : 0);
   }
-  if (Ed % 4 == 0)
+  if (s16_)
+    k_pair_grad4<T, S16><<<grid(P * 16), 256, 0, st>>>(P, Ed, nv.sel_j, d_, sw_, dsw_, dsa_, rh_, ee16_[0],
+                                                       we_, de_, dsw_e_, dsa_e_, drh_, g_);
+  else if (Ed % 4 == 0)
     k_pair_grad4<T><<<grid(P * 16), 256, 0, st>>>(P, Ed, nv.sel_j, d_, sw_, dsw_, dsa_, rh_, ee_[0], we_, de_,
                                                   dsw_e_, dsa_e_, drh_, g_);
   else
