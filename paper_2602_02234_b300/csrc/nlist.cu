@@ -386,13 +386,34 @@ __global__ void k_select(int n, int cap, int nmax, double rc, const double* __re
   }
   __syncwarp();
   if (lane == 0) n_in_rc[i] = k;
+  // rank = the number of keys (d2, j, n) below the query's.  The count runs
+  // on d2 alone (64-bit integer compares of the bit patterns, four keys per
+  // step with their loads issued together); a query whose d2 equals another
+  // key's is recounted with the full key, so the ranks are those of key_less.
+  const long long* sbits = reinterpret_cast<const long long*>(sd2);
   for (int q = lane; q < k; q += 32) {
-    double dq = sd2[4 * q];
+    const long long dqb = sbits[4 * q];
     int jq = sint[5 * q];
     const int* nq = sint + 5 * q + 1;
-    int rank = 0;
-    for (int p = 0; p < k; ++p)
-      rank += key_less(sd2[4 * p], sint[5 * p], sint + 5 * p + 1, dq, jq, nq) ? 1 : 0;
+    int rank = 0, eq = 0;
+    int p = 0;
+    for (; p + 4 <= k; p += 4) {
+      const long long d0 = sbits[4 * p], d1 = sbits[4 * p + 4], d2b = sbits[4 * p + 8],
+                      d3 = sbits[4 * p + 12];
+      rank += (d0 < dqb) + (d1 < dqb) + (d2b < dqb) + (d3 < dqb);
+      eq += (d0 == dqb) + (d1 == dqb) + (d2b == dqb) + (d3 == dqb);
+    }
+    for (; p < k; ++p) {
+      const long long d0 = sbits[4 * p];
+      rank += d0 < dqb;
+      eq += d0 == dqb;
+    }
+    if (eq > 1) {   // a tie besides the query itself
+      const double dq = sd2[4 * q];
+      rank = 0;
+      for (int t = 0; t < k; ++t)
+        rank += key_less(sd2[4 * t], sint[5 * t], sint + 5 * t + 1, dq, jq, nq) ? 1 : 0;
+    }
     if (rank < nmax) {
       size_t o = (size_t)i * nmax + rank;
       sel_j[o] = jq;
