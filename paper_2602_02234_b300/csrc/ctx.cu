@@ -73,6 +73,8 @@ struct dp_ctx {
   double* sel_r = nullptr;
   double *atom_e = nullptr, *atom_vir = nullptr, *sys_e = nullptr, *sys_vir = nullptr;
   double* atom_ke = nullptr;   // kinetic energy per atom (final kick -> record)
+  unsigned long long* red_part = nullptr;   // per-chunk partial sums of the system reduction
+  int red_chunks = 1;
   int* flags = nullptr;
   long long* step = nullptr;   // [0] step counter, [1] trace base
   // dp_step's checkpoint for a retry after a neighbour-capacity overflow
@@ -293,10 +295,11 @@ static int enqueue_compute(dp_ctx* c, int atom0 = 0) {
   }
   ReduceArgs ra{};
   ra.n_sys = c->n_sys; ra.sys_atom0 = c->sys_atom0; ra.atom_e = c->atom_e; ra.atom_vir = c->atom_vir;
+  ra.n = c->n; ra.part = c->red_part; ra.part_chunks = c->red_chunks;
   ra.F = c->F; ra.sys_e = c->sys_e; ra.sys_vir = c->sys_vir; ra.flags = c->flags;
   ra.atom_e_out = c->atom_e;
   ra.grp = c->use_grp ? c->grp : nullptr;
-  launch_reduce(ra, c->st); ++k;
+  launch_reduce(ra, c->st); k += 2;
   return k;
 }
 
@@ -452,6 +455,8 @@ static int ctx_create(dp_ctx** out, const dp_model_desc* desc, const double* mas
   TRY(dalloc(c, &c->atom_e, N), "energies");
   TRY(dalloc(c, &c->atom_vir, 9 * N), "virials");
   TRY(dalloc(c, &c->atom_ke, N), "kinetic energies");
+  c->red_chunks = (int)((N + kReduceChunk - 1) / kReduceChunk);
+  TRY(dalloc(c, &c->red_part, S * (size_t)c->red_chunks * 20), "reductions");
   TRY(dalloc(c, &c->sys_e, S), "energies");
   if (c->af.fit_heads > 1) TRY(dalloc(c, &c->head_sys_e, S * (c->af.fit_heads - 1)), "energies");
   TRY(dalloc(c, &c->sys_vir, 9 * S), "virials");

@@ -57,8 +57,14 @@ struct ForceArgs {
 };
 void launch_force_gather(const ForceArgs& a, cudaStream_t st);
 
+// The per-system sums run in chunks of kReduceChunk atoms spread over the GPU,
+// then one small block per system adds its chunks' exact partial sums.
+constexpr int kReduceChunk = 512;
 struct ReduceArgs {
   int n_sys;
+  int n;                 // atoms of all systems (chunks = ceil(n / kReduceChunk) at most)
+  unsigned long long* part;   // [sys][part_chunks][10] 128-bit partial sums (2 words each)
+  int part_chunks;       // chunk capacity of `part` per system
   const int* sys_atom0;  // n_sys + 1 offsets
   const double* atom_e;  // n (unused by the kernel: atom_e_out is read and written)
   const double* atom_vir;// n x 9

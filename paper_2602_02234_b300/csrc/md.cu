@@ -13,6 +13,7 @@
 // reproducible).  With FP32 pair gradients the first sum and the per-atom
 // virial are accumulated the same way, in integer arithmetic; with FP64 ones
 // (the FP64 path) they are FP64 sums over the kept slots in their order.
+#include <algorithm>
 #include <type_traits>
 
 #include "common.cuh"
@@ -51,17 +52,37 @@ __global__ void k_force_gather(int atom0, int n, int nmax, int cap, const int* _
         for (int b = 0; b < 3; ++b) acc[3 + 3 * a + b] -= to_fixed_f32(r[a] * gg[b], &bad);
       }
     }
+    // the mirrored gradients: four skin entries per lane go through each level
+    // of the gather chain (mirror index and neighbour, its slot, its
+    // gradient) together, so that their loads overlap
     const int cnt = skin_cnt[i];
-    for (int c = lane; c < cnt; c += 32) {
-      const size_t o = (size_t)i * cap + c;
-      const int mc = mirror[o];
-      if (mc < 0) continue;
-      const int j = skin[o].j;
-      const int p = selpos[(size_t)j * cap + mc];
-      if (p < 0) continue;
-      const size_t q = (size_t)j * nmax + p;
+    for (int c0 = lane; c0 < cnt; c0 += 4 * 32) {
+      int mc[4], jn[4], ps[4];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) acc[a] -= to_fixed_f32(g[3 * q + a], &bad);
+      for (int u = 0; u < 4; ++u) {
+        const int c = c0 + 32 * u;
+        mc[u] = -1;
+        jn[u] = 0;
+        if (c < cnt) {
+          const size_t o = (size_t)i * cap + c;
+          mc[u] = mirror[o];
+          jn[u] = skin[o].j;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) ps[u] = mc[u] >= 0 ? selpos[(size_t)jn[u] * cap + mc[u]] : -1;
+      float gm[4][3];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const size_t q = (size_t)jn[u] * nmax + (ps[u] >= 0 ? ps[u] : 0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) gm[u][a] = ps[u] >= 0 ? g[3 * q + a] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (ps[u] >= 0)
+#pragma unroll
+          for (int a = 0; a < 3; ++a) acc[a] -= to_fixed_f32(gm[u][a], &bad);
     }
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[k] = warp_sum_fixed(acc[k]);
@@ -122,26 +143,31 @@ void launch_force_gather(const ForceArgs& a, cudaStream_t st) {
                                                   a.atom_vir);
 }
 
-// One block per system: E and the virial summed exactly in 128-bit fixed
-// point (integer arithmetic, 2^-80 resolution) and rounded once to FP64, so
-// the totals do not depend on the summation order.  A value that is not
-// finite, or beyond the fixed-point range (|v| >= 2^46), raises the
+// Per system: E and the virial summed exactly in 128-bit fixed point
+// (integer arithmetic, 2^-80 resolution) and rounded once to FP64, so the
+// totals do not depend on the summation order.  Blocks of k_reduce_part take
+// chunks of kReduceChunk atoms of one system and write the chunk's partial
+// sums; k_reduce_final adds a system's partials (still exact).  A value that
+// is not finite, or beyond the fixed-point range (|v| >= 2^46), raises the
 // non-finite flag, as a non-finite force does.  With a DP group, atoms
 // outside it contribute nothing (their energy is set to 0; they have no kept
 // pairs, so no virial or force either).
-constexpr int kReduceThreads = 1024;
-__global__ void __launch_bounds__(kReduceThreads) k_reduce(
+constexpr int kReduceThreads = 256;
+__global__ void __launch_bounds__(kReduceThreads) k_reduce_part(
     const int* __restrict__ sys_atom0, double* __restrict__ atom_e, const double* __restrict__ atom_vir,
-    const double* __restrict__ F, double* __restrict__ sys_e, double* __restrict__ sys_vir,
-    int* __restrict__ flags, const unsigned char* __restrict__ grp) {
-  const int s = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double* __restrict__ F, int* __restrict__ flags, const unsigned char* __restrict__ grp,
+    unsigned long long* __restrict__ part, int part_chunks) {
+  const int s = blockIdx.y, chunk = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int a0 = sys_atom0[s], a1 = sys_atom0[s + 1];
+  const long long lo = (long long)a0 + (long long)chunk * kReduceChunk;
+  if (lo >= a1) return;   // beyond this system's atoms: no partial
+  const int hi = lo + kReduceChunk < a1 ? (int)(lo + kReduceChunk) : a1;
   __shared__ unsigned long long sh[kReduceThreads / 32][10][2];
   __int128 acc[10];
 #pragma unroll
   for (int q = 0; q < 10; ++q) acc[q] = 0;
   bool bad = false;
-  for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
+  for (int i = (int)lo + threadIdx.x; i < hi; i += blockDim.x) {
     if (grp && !grp[i]) atom_e[i] = 0.0;
     acc[0] += to_fixed_f64(atom_e[i], &bad);
 #pragma unroll
@@ -162,21 +188,39 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(
   __syncthreads();
   if (warp != 0) return;
   const int nw = blockDim.x >> 5;
-  __int128 mine = 0;
+  unsigned long long* out = part + ((size_t)s * part_chunks + chunk) * 20;
 #pragma unroll
   for (int q = 0; q < 10; ++q) {
     __int128 v = 0;
     if (lane < nw) v = (__int128)(((unsigned __int128)sh[lane][q][1] << 64) | sh[lane][q][0]);
     v = warp_sum_fixed(v);
-    if (lane == q) mine = v;
+    if (lane == q) {
+      out[2 * q] = (unsigned long long)v;
+      out[2 * q + 1] = (unsigned long long)(v >> 64);
+    }
   }
-  if (lane == 0) sys_e[s] = from_fixed(mine);
-  else if (lane < 10) sys_vir[9 * s + lane - 1] = from_fixed(mine);
+}
+// one warp per system: lane q < 10 adds value q over the system's chunks
+__global__ void k_reduce_final(const int* __restrict__ sys_atom0,
+                               const unsigned long long* __restrict__ part, int part_chunks,
+                               double* __restrict__ sys_e, double* __restrict__ sys_vir) {
+  const int s = blockIdx.x, q = threadIdx.x;
+  if (q >= 10) return;
+  const int na = sys_atom0[s + 1] - sys_atom0[s];
+  const int nch = (na + kReduceChunk - 1) / kReduceChunk;
+  const unsigned long long* in = part + (size_t)s * part_chunks * 20;
+  __int128 v = 0;
+  for (int c = 0; c < nch; ++c)
+    v += (__int128)(((unsigned __int128)in[20 * c + 2 * q + 1] << 64) | in[20 * c + 2 * q]);
+  if (q == 0) sys_e[s] = from_fixed(v);
+  else sys_vir[9 * s + q - 1] = from_fixed(v);
 }
 
 void launch_reduce(const ReduceArgs& a, cudaStream_t st) {
-  k_reduce<<<a.n_sys, kReduceThreads, 0, st>>>(a.sys_atom0, a.atom_e_out, a.atom_vir, a.F, a.sys_e,
-                                               a.sys_vir, a.flags, a.grp);
+  const int chunks = std::max(1, (a.n + kReduceChunk - 1) / kReduceChunk);
+  k_reduce_part<<<dim3(chunks, a.n_sys), kReduceThreads, 0, st>>>(
+      a.sys_atom0, a.atom_e_out, a.atom_vir, a.F, a.flags, a.grp, a.part, a.part_chunks);
+  k_reduce_final<<<a.n_sys, 32, 0, st>>>(a.sys_atom0, a.part, a.part_chunks, a.sys_e, a.sys_vir);
 }
 
 // v += dt/2 F/m; x += dt v; request a neighbour rebuild when an atom moved

@@ -183,16 +183,16 @@ __global__ void k_msg(int nmax, int ed, T inv_nmax, const int* __restrict__ sel_
 }
 
 // The same, one warp per atom: lane l owns columns 2l, 2l + 1 (+ 64 k), and
-// a batch of slots' rows is read before any is summed (four slots, or eight
-// when the edge rows are 16-bit, so that as many bytes are in flight); the
-// sum runs over the slots in order and stops at the first empty one, as above
-// (the kept slots are a prefix of the list).  ed even.
+// four slots' rows are read before any is summed (a 16-bit edge row as raw
+// bits, converted at the sum); the sum runs over the slots in order and stops
+// at the first empty one, as above (the kept slots are a prefix of the
+// list).  ed even.  Eight slots per batch for 16-bit rows measured slower.
 template <typename T, typename E = T>   // E: storage of the edge state
 __global__ void k_msg_warp(int n, int nmax, int ed, T inv_nmax, const int* __restrict__ sel_j,
                            const T* __restrict__ sw, const E* __restrict__ edge,
                            const T* __restrict__ u, T* __restrict__ m) {
   constexpr bool k16 = sizeof(E) == 2;
-  constexpr int B = k16 ? 8 : 4;
+  constexpr int B = 4;
   const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (i >= n) return;
