@@ -51,7 +51,8 @@ enum {
   DP_ERR_NLIST_OVERFLOW = -3,  /* more candidates than the list capacity     */
   DP_ERR_TIMEOUT = -4,         /* a device-side wait gave up                 */
   DP_ERR_NONFINITE = -5,       /* energy, forces or virial not finite, or    */
-                               /* beyond +-2^46 (the exact sums' range)      */
+                               /* beyond the exact sums' range (a term of    */
+                               /* 2^46 or a sum of 2^47 in magnitude)        */
   DP_ERR_CUDA = -6,            /* a CUDA runtime call failed                 */
   DP_ERR_UNSUPPORTED = -7      /* valid request the library does not support */
 };

@@ -18,7 +18,7 @@ enum : int {
   kFlagOverflow = 1 << 1,  // a skin list exceeded its capacity
   kFlagMirror = 1 << 2,    // a skin entry had no mirror entry (internal error)
   kFlagTimeout = 1 << 3,   // a bounded device-side wait gave up
-  kFlagNonFinite = 1 << 4  // non-finite energy or force
+  kFlagNonFinite = 1 << 4  // non-finite energy or force, or beyond the exact sums' range
 };
 
 // One periodic system of a batch.  Atoms [atom0, atom0 + natom) belong to it.
@@ -166,11 +166,19 @@ __device__ __forceinline__ __int128 to_fixed_f64(double v, bool* bad) {
   return shift_fixed(m, (e ? e : 1) - 1023 - 52 + 80, (b >> 63) != 0);
 }
 
-__device__ __forceinline__ __int128 warp_sum_fixed(__int128 v) {
+// a + b in 128-bit fixed point; *bad is set when the sum leaves the signed
+// 128-bit range (|sum| >= 2^47 at 2^-80 resolution), where it would wrap
+__device__ __forceinline__ __int128 fixed_add(__int128 a, __int128 b, bool* bad) {
+  const __int128 r = (__int128)((unsigned __int128)a + (unsigned __int128)b);
+  *bad |= ((a ^ r) & (b ^ r)) < 0;
+  return r;
+}
+
+__device__ __forceinline__ __int128 warp_sum_fixed(__int128 v, bool* bad) {
   for (int o = 16; o > 0; o >>= 1) {
     const unsigned long long lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)v, o);
     const long long hi = __shfl_xor_sync(0xffffffffu, (long long)(v >> 64), o);
-    v += (__int128)(((unsigned __int128)(unsigned long long)hi << 64) | lo);
+    v = fixed_add(v, (__int128)(((unsigned __int128)(unsigned long long)hi << 64) | lo), bad);
   }
   return v;
 }

@@ -47,9 +47,10 @@ __global__ void k_force_gather(int atom0, int n, int nmax, int cap, const int* _
       const float r[3] = {(float)sel_r[3 * o], (float)sel_r[3 * o + 1], (float)sel_r[3 * o + 2]};
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        acc[a] += to_fixed_f32(gg[a], &bad);
+        acc[a] = fixed_add(acc[a], to_fixed_f32(gg[a], &bad), &bad);
 #pragma unroll
-        for (int b = 0; b < 3; ++b) acc[3 + 3 * a + b] -= to_fixed_f32(r[a] * gg[b], &bad);
+        for (int b = 0; b < 3; ++b)
+          acc[3 + 3 * a + b] = fixed_add(acc[3 + 3 * a + b], -to_fixed_f32(r[a] * gg[b], &bad), &bad);
       }
     }
     // the mirrored gradients: four skin entries per lane go through each level
@@ -82,10 +83,10 @@ __global__ void k_force_gather(int atom0, int n, int nmax, int cap, const int* _
       for (int u = 0; u < 4; ++u)
         if (ps[u] >= 0)
 #pragma unroll
-          for (int a = 0; a < 3; ++a) acc[a] -= to_fixed_f32(gm[u][a], &bad);
+          for (int a = 0; a < 3; ++a) acc[a] = fixed_add(acc[a], -to_fixed_f32(gm[u][a], &bad), &bad);
     }
 #pragma unroll
-    for (int k = 0; k < 12; ++k) acc[k] = warp_sum_fixed(acc[k]);
+    for (int k = 0; k < 12; ++k) acc[k] = warp_sum_fixed(acc[k], &bad);
     bad = __any_sync(0xffffffffu, bad);
     __int128 mine = acc[0];
 #pragma unroll
@@ -118,10 +119,10 @@ __global__ void k_force_gather(int atom0, int n, int nmax, int cap, const int* _
     int p = selpos[(size_t)j * cap + mc];
     if (p < 0) continue;
     size_t q = (size_t)j * nmax + p;
-    for (int a = 0; a < 3; ++a) fm[a] += to_fixed((double)g[3 * q + a], &bad);
+    for (int a = 0; a < 3; ++a) fm[a] = fixed_add(fm[a], to_fixed((double)g[3 * q + a], &bad), &bad);
   }
   for (int a = 0; a < 3; ++a) f[a] = warp_sum(f[a]);
-  for (int a = 0; a < 3; ++a) fm[a] = warp_sum_fixed(fm[a]);
+  for (int a = 0; a < 3; ++a) fm[a] = warp_sum_fixed(fm[a], &bad);
   for (int a = 0; a < 9; ++a) vir[a] = warp_sum(vir[a]);
   bad = __any_sync(0xffffffffu, bad);
   if (lane == 0) {
@@ -148,7 +149,8 @@ void launch_force_gather(const ForceArgs& a, cudaStream_t st) {
 // totals do not depend on the summation order.  Blocks of k_reduce_part take
 // chunks of kReduceChunk atoms of one system and write the chunk's partial
 // sums; k_reduce_final adds a system's partials (still exact).  A value that
-// is not finite, or beyond the fixed-point range (|v| >= 2^46), raises the
+// is not finite, or beyond the fixed-point range (|v| >= 2^46), and a sum
+// that would leave it (|sum| >= 2^47, checked at every addition) raise the
 // non-finite flag, as a non-finite force does.  With a DP group, atoms
 // outside it contribute nothing (their energy is set to 0; they have no kept
 // pairs, so no virial or force either).
@@ -169,58 +171,66 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce_part(
   bool bad = false;
   for (int i = (int)lo + threadIdx.x; i < hi; i += blockDim.x) {
     if (grp && !grp[i]) atom_e[i] = 0.0;
-    acc[0] += to_fixed_f64(atom_e[i], &bad);
+    acc[0] = fixed_add(acc[0], to_fixed_f64(atom_e[i], &bad), &bad);
 #pragma unroll
-    for (int q = 0; q < 9; ++q) acc[1 + q] += to_fixed_f64(atom_vir[9 * (size_t)i + q], &bad);
+    for (int q = 0; q < 9; ++q)
+      acc[1 + q] = fixed_add(acc[1 + q], to_fixed_f64(atom_vir[9 * (size_t)i + q], &bad), &bad);
 #pragma unroll
     for (int q = 0; q < 3; ++q)   // exponent all ones: infinite or NaN
       bad |= ((__double_as_longlong(F[3 * (size_t)i + q]) >> 52) & 0x7ff) == 0x7ff;
   }
-  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, kFlagNonFinite);
 #pragma unroll
   for (int q = 0; q < 10; ++q) {
-    const __int128 v = warp_sum_fixed(acc[q]);
+    const __int128 v = warp_sum_fixed(acc[q], &bad);
     if (lane == 0) {
       sh[warp][q][0] = (unsigned long long)v;
       sh[warp][q][1] = (unsigned long long)(v >> 64);
     }
   }
-  __syncthreads();
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, kFlagNonFinite);
   if (warp != 0) return;
   const int nw = blockDim.x >> 5;
   unsigned long long* out = part + ((size_t)s * part_chunks + chunk) * 20;
+  bool over = false;
 #pragma unroll
   for (int q = 0; q < 10; ++q) {
     __int128 v = 0;
     if (lane < nw) v = (__int128)(((unsigned __int128)sh[lane][q][1] << 64) | sh[lane][q][0]);
-    v = warp_sum_fixed(v);
+    v = warp_sum_fixed(v, &over);
     if (lane == q) {
       out[2 * q] = (unsigned long long)v;
       out[2 * q + 1] = (unsigned long long)(v >> 64);
     }
   }
+  if (__any_sync(0xffffffffu, over) && lane == 0) atomicOr(flags, kFlagNonFinite);
 }
 // one warp per system: lane q < 10 adds value q over the system's chunks
 __global__ void k_reduce_final(const int* __restrict__ sys_atom0,
                                const unsigned long long* __restrict__ part, int part_chunks,
-                               double* __restrict__ sys_e, double* __restrict__ sys_vir) {
+                               double* __restrict__ sys_e, double* __restrict__ sys_vir,
+                               int* __restrict__ flags) {
   const int s = blockIdx.x, q = threadIdx.x;
   if (q >= 10) return;
   const int na = sys_atom0[s + 1] - sys_atom0[s];
   const int nch = (na + kReduceChunk - 1) / kReduceChunk;
   const unsigned long long* in = part + (size_t)s * part_chunks * 20;
   __int128 v = 0;
+  bool over = false;
   for (int c = 0; c < nch; ++c)
-    v += (__int128)(((unsigned __int128)in[20 * c + 2 * q + 1] << 64) | in[20 * c + 2 * q]);
-  if (q == 0) sys_e[s] = from_fixed(v);
-  else sys_vir[9 * s + q - 1] = from_fixed(v);
+    v = fixed_add(v, (__int128)(((unsigned __int128)in[20 * c + 2 * q + 1] << 64) | in[20 * c + 2 * q]),
+                  &over);
+  if (over) atomicOr(flags, kFlagNonFinite);
+  const double r = over ? quiet_nan() : from_fixed(v);
+  if (q == 0) sys_e[s] = r;
+  else sys_vir[9 * s + q - 1] = r;
 }
 
 void launch_reduce(const ReduceArgs& a, cudaStream_t st) {
   const int chunks = std::max(1, (a.n + kReduceChunk - 1) / kReduceChunk);
   k_reduce_part<<<dim3(chunks, a.n_sys), kReduceThreads, 0, st>>>(
       a.sys_atom0, a.atom_e_out, a.atom_vir, a.F, a.flags, a.grp, a.part, a.part_chunks);
-  k_reduce_final<<<a.n_sys, 32, 0, st>>>(a.sys_atom0, a.part, a.part_chunks, a.sys_e, a.sys_vir);
+  k_reduce_final<<<a.n_sys, 32, 0, st>>>(a.sys_atom0, a.part, a.part_chunks, a.sys_e, a.sys_vir,
+                                          a.flags);
 }
 
 // v += dt/2 F/m; x += dt v; request a neighbour rebuild when an atom moved
@@ -288,9 +298,9 @@ __global__ void __launch_bounds__(256) k_record(const int* __restrict__ sys_atom
   __shared__ unsigned long long sh[8][2];
   __int128 acc = 0;
   bool bad = false;
-  for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) acc += to_fixed_f64(ke[i], &bad);
+  for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) acc = fixed_add(acc, to_fixed_f64(ke[i], &bad), &bad);
+  acc = warp_sum_fixed(acc, &bad);
   bad = __syncthreads_or(bad) != 0;
-  acc = warp_sum_fixed(acc);
   if (lane == 0) {
     sh[warp][0] = (unsigned long long)acc;
     sh[warp][1] = (unsigned long long)(acc >> 64);
@@ -299,7 +309,8 @@ __global__ void __launch_bounds__(256) k_record(const int* __restrict__ sys_atom
   if (warp != 0) return;
   __int128 v = 0;
   if (lane < (int)(blockDim.x >> 5)) v = (__int128)(((unsigned __int128)sh[lane][1] << 64) | sh[lane][0]);
-  v = warp_sum_fixed(v);
+  v = warp_sum_fixed(v, &bad);
+  bad = __any_sync(0xffffffffu, bad);
   if (lane == 0) {
     long long slot = step[0] - step[1] - 1;   // step[1] holds the base
     if (slot >= 0 && slot < trace_len) {
@@ -343,9 +354,9 @@ __global__ void __launch_bounds__(256) k_head_reduce(int heads, int n, const int
   __int128 acc = 0;
   bool bad = false;
   for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x)
-    if (!grp || grp[i]) acc += to_fixed_f64(head_e[(size_t)h * n + i], &bad);
+    if (!grp || grp[i]) acc = fixed_add(acc, to_fixed_f64(head_e[(size_t)h * n + i], &bad), &bad);
+  acc = warp_sum_fixed(acc, &bad);
   bad = __syncthreads_or(bad) != 0;
-  acc = warp_sum_fixed(acc);
   if (lane == 0) {
     sh[warp][0] = (unsigned long long)acc;
     sh[warp][1] = (unsigned long long)(acc >> 64);
@@ -354,7 +365,8 @@ __global__ void __launch_bounds__(256) k_head_reduce(int heads, int n, const int
   if (warp != 0) return;
   __int128 v = 0;
   if (lane < (int)(blockDim.x >> 5)) v = (__int128)(((unsigned __int128)sh[lane][1] << 64) | sh[lane][0]);
-  v = warp_sum_fixed(v);
+  v = warp_sum_fixed(v, &bad);
+  bad = __any_sync(0xffffffffu, bad);
   if (lane == 0) out[(size_t)s * heads + h] = bad ? quiet_nan() : from_fixed(v);
 }
 

@@ -397,6 +397,36 @@ def test_fitting_heads_share_one_descriptor(prec):
     assert np.max(np.abs(V - Vo)) <= TOL_F[prec] * np.linalg.norm(Vo)
 
 
+@pytest.mark.parametrize("prec", [dp.PREC_PLAIN_F64, dp.PREC_PLAIN_F32, dp.PREC_FUSED])
+def test_energy_beyond_the_exact_sums_range_is_reported(prec):
+    """Forces, virials and energies are summed exactly in 128-bit fixed point
+    (2^-80 resolution, so a sum must stay below 2^47 in magnitude).  A total
+    energy beyond that range, made of in-range atomic energies, is reported
+    as DP_ERR_NONFINITE instead of wrapping; one just inside it is summed."""
+    m, s = C.WATER64_MODEL, C.water64()
+    n = len(s.types)
+    base = weights(m)
+
+    def with_bias(b):
+        w = base.copy()
+        for a in range(m.n_species):
+            w[oracle.af_weight_slice(m, "fb4", a)] = b
+        return w
+
+    # 192 atoms x 1e12 eV = 1.9e14 eV > 2^47 = 1.4e14 eV (each atom < 2^46)
+    pot = dp.DeepPotential(dp.model_desc(m, prec), s.types, s.box, with_bias(1e12))
+    with pytest.raises(dp.DPError) as e:
+        pot.compute(s.coords)
+    assert e.value.code == dp.DP_ERR_NONFINITE
+    pot.close()
+    # 192 x 1e11 eV = 1.9e13 eV: in range; the bias dominates every atom
+    pot = dp.DeepPotential(dp.model_desc(m, prec), s.types, s.box, with_bias(1e11))
+    E, F, V = pot.compute(s.coords)
+    assert np.isfinite(E) and abs(E - n * 1e11) <= 1e-6 * n * 1e11
+    assert np.all(np.isfinite(F)) and np.all(np.isfinite(V))
+    pot.close()
+
+
 @pytest.mark.parametrize("prec", [dp.PREC_PLAIN_F32, dp.PREC_FUSED])
 def test_isolated_atoms_keep_their_energy(prec):
     """Atoms with no neighbour within rc (the fused kernels skip their
