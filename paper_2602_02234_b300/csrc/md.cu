@@ -288,17 +288,26 @@ void launch_kick_final(const MdArgs& a, cudaStream_t st) {
 // per system: {E_pot, E_kin} of the step just finished into trace[step - base - 1];
 // E_kin is the exact fixed-point sum of the atoms' kinetic energies (from the
 // final kick), rounded once
-__global__ void __launch_bounds__(256) k_record(const int* __restrict__ sys_atom0,
+constexpr int kRecordThreads = 1024;
+__global__ void __launch_bounds__(kRecordThreads) k_record(const int* __restrict__ sys_atom0,
                                                 const double* __restrict__ ke, double inv_kappa,
                                                 const double* __restrict__ sys_e,
                                                 const long long* __restrict__ step,
                                                 double* __restrict__ trace, int n_sys, int trace_len) {
   const int s = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int a0 = sys_atom0[s], a1 = sys_atom0[s + 1];
-  __shared__ unsigned long long sh[8][2];
+  __shared__ unsigned long long sh[kRecordThreads / 32][2];
   __int128 acc = 0;
   bool bad = false;
-  for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) acc = fixed_add(acc, to_fixed_f64(ke[i], &bad), &bad);
+  // four loads in flight per thread (one SM runs the whole system)
+  const int bd = blockDim.x;
+  for (int i0 = a0 + threadIdx.x; i0 < a1; i0 += 4 * bd) {
+    double k[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) k[u] = i0 + u * bd < a1 ? ke[i0 + u * bd] : 0.0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc = fixed_add(acc, to_fixed_f64(k[u], &bad), &bad);
+  }
   acc = warp_sum_fixed(acc, &bad);
   bad = __syncthreads_or(bad) != 0;
   if (lane == 0) {
@@ -323,8 +332,8 @@ __global__ void __launch_bounds__(256) k_record(const int* __restrict__ sys_atom
 void launch_record(const MdArgs& a, const double* sys_e, double* trace, int trace_len,
                    cudaStream_t st) {
   const double kappa = 1.602176634e-19 / (1.66053906660e-27 * 1e10);
-  k_record<<<a.n_sys, 256, 0, st>>>(a.sys_atom0, a.atom_ke, 1.0 / kappa, sys_e, a.step, trace,
-                                    a.n_sys, trace_len);
+  k_record<<<a.n_sys, kRecordThreads, 0, st>>>(a.sys_atom0, a.atom_ke, 1.0 / kappa, sys_e, a.step,
+                                               trace, a.n_sys, trace_len);
 }
 
 __global__ void k_compare(long long count, const double* __restrict__ a,

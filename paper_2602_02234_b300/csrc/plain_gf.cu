@@ -595,10 +595,10 @@ __global__ void k_angle_out_bwd(long long PA, int ed, int nmax, int ca, const T*
 }
 // The same with 16 threads per angle row, four columns each (ed a multiple
 // of 4); the dsa sum closes with a fixed-order reduction over the 16 lanes.
-template <typename T>
+template <typename T, typename Z = T>   // Z: storage of dz (T, or 16 bits)
 __global__ void k_angle_out_bwd4(long long PA, int ed, int nmax, int ca, const T* __restrict__ sa,
                                  const T* __restrict__ t, const T* __restrict__ de,
-                                 T* __restrict__ dz, T* __restrict__ dsa_e) {
+                                 Z* __restrict__ dz, T* __restrict__ dsa_e) {
   const long long m = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 4;
   const int l16 = threadIdx.x & 15;
   if (m >= PA) return;   // the whole 16-lane group leaves together
@@ -637,14 +637,14 @@ __global__ void k_angle_out_bwd4(long long PA, int ed, int nmax, int ca, const T
 // q, da and dq hold the angle rows only (row i ca + p).  Shared memory: beta,
 // the monomials (as in the forward), YB and dYB (ed x 20 each), the per-slot
 // sums H, K, D (na x 44), then two slot-data buffers.
-template <typename T>
+template <typename T, typename DQ = T>   // DQ: storage of dq (T, or 16 bits)
 __global__ void __launch_bounds__(kAngThreads) k_angle_bwd(int n, int nmax, int na, int ca, int ed, T inv_na,
                                                            const T* __restrict__ sa,
                                                            const T* __restrict__ rh,
                                                            const T* __restrict__ q,
                                                            const T* __restrict__ Wphi,
                                                            const T* __restrict__ da,
-                                                           T* __restrict__ dq, T* __restrict__ dsa_e,
+                                                           DQ* __restrict__ dq, T* __restrict__ dsa_e,
                                                            T* __restrict__ drh) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   constexpr int kHKD = 2 * kMono + 4;
@@ -687,11 +687,11 @@ __global__ void __launch_bounds__(kAngThreads) k_angle_bwd(int n, int nmax, int 
         ld4(xpow + 4 * p, xp);
         const T z = b[0] + b[1] * xp[1] + b[2] * xp[2] + b[3] * xp[3];
         const T sp = cur.sa[p];
-        dq[(abase + p) * ed + c] = sp * (dot_n<kMono>(m, dyb) - inv_na * sp * das[p * ld + c] * z);
+        dq[(abase + p) * ed + c] = DQ(sp * (dot_n<kMono>(m, dyb) - inv_na * sp * das[p * ld + c] * z));
       }
     }
     for (int idx = threadIdx.x; idx < (ca - nang) * ed; idx += blockDim.x)
-      dq[(abase + nang) * ed + idx] = T(0);
+      dq[(abase + nang) * ed + idx] = DQ(T(0));
     // H, K (and D) of two slots and four monomials per thread, summed over the
     // columns in order
     const int npair = (nang + 1) >> 1;
@@ -1162,6 +1162,28 @@ class PlainGf : public Model {
       (void)l; (void)nv; (void)st;
     }
   }
+  // one product whose A operand is stored in 16 bits (mixed form only); the
+  // rest of g as for mm()
+  template <typename A16>
+  void mm_a16(Gemm<T> g, const A16* a16, cudaStream_t st) {
+    if constexpr (std::is_same<T, float>::value) {
+      GemmTc t{};
+      t.M = g.M; t.N = g.N; t.K = g.K;
+      t.a16 = reinterpret_cast<const uint16_t*>(a16); t.lda = g.a_rm; t.a_rows = g.a_rows;
+      t.B = g.B; t.b_nk = g.b_rn == 1 ? 0 : 1; t.ldb = g.b_rn == 1 ? g.b_rk : g.b_rn;
+      t.C = g.C; t.ldc = g.c_rm; t.c_rows = g.c_rows;
+      t.bias = g.bias; t.beta = g.beta; t.epi = g.epi; t.aux = g.aux;
+      t.status = flags_;
+#ifdef DP_GF_BF16
+      t.fp16 = 0;
+#else
+      t.fp16 = 1;
+#endif
+      gemm_tc(t, st);
+    } else {
+      (void)g; (void)a16; (void)st;
+    }
+  }
   // the angle channel's q = e_{l+1} Wp over the angle rows (their slots'
   // rows of e gathered); in the mixed form from the 16-bit edge state
   void q_product(int l, cudaStream_t st) {
@@ -1198,6 +1220,9 @@ class PlainGf : public Model {
   // products round it to 16 bits anyway, and its residual updates e1 = e + v,
   // e_{l+1} = e1 + swa t are rounded once per layer
   std::vector<S16*> ee16_;
+  // and the angle channel's adjoints dz and dq, which only ever feed a
+  // product as its A operand (rounded to 16 bits there anyway)
+  S16 *dz16_ = nullptr, *dq16_ = nullptr;
   S16 *dy16_ = nullptr, *X16_ = nullptr;
   int* flags_ = nullptr;
   const unsigned char* seed_ = nullptr;   // energy seed (device, optional)
@@ -1376,6 +1401,8 @@ bool PlainGf<T>::init(const GfDims& m, const double* w, int n_atoms, const int* 
   if (cudaFuncSetAttribute(k_angle<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, angle_smem) !=
           cudaSuccess ||
       cudaFuncSetAttribute(k_angle_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, angle_bwd_smem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_angle_bwd<T, S16>, cudaFuncAttributeMaxDynamicSharedMemorySize, angle_bwd_smem) !=
           cudaSuccess) {
     *err = "graph model: angle kernels cannot get their shared memory";
     return false;
@@ -1398,7 +1425,8 @@ bool PlainGf<T>::init(const GfDims& m, const double* w, int n_atoms, const int* 
        dalloc(&y3_, N * m.f3, err) && dalloc(&d1_, N * m.f1, err) && dalloc(&d2_, N * m.f2, err) &&
        dalloc(&d3_, N * m.f3, err) && dalloc(&dn_, N * Nd, err) && dalloc(&dn1_, N * Nd, err) &&
        dalloc(&de_, P * Ed, err) && (s16_ ? dalloc(&dy16_, P * Ed, err) : dalloc(&dy_, P * Ed, err)) &&
-       dalloc(&dz_, PA * Ed, err) && dalloc(&da_, PA * Ed, err) && dalloc(&dq_, PA * Ed, err) &&
+       (s16_ ? dalloc(&dz16_, PA * Ed, err) : dalloc(&dz_, PA * Ed, err)) && dalloc(&da_, PA * Ed, err) &&
+       (s16_ ? dalloc(&dq16_, PA * Ed, err) : dalloc(&dq_, PA * Ed, err)) &&
        dalloc(&du_, N * Ed, err) && dalloc(&dx_, N * Nd, err) && dalloc(&dnm_, N * (Nd + Ed), err) &&
        (s16_ ? dalloc(&X16_, P * Ed, err) : dalloc(&X_, P * Ed, err)) && dalloc(&sdy_, N * Ed, err) && dalloc(&gat_, N * Ed, err) &&
        dalloc(&dsw_e_, P, err) && dalloc(&dsa_e_, P, err) && dalloc(&drh_, 3 * P, err) &&
@@ -1522,7 +1550,9 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
   k += 1;   // k_fit_out
   for (int l = L - 1; l >= 0; --l) {
     // (c): de holds dE/de_{l+1}; it becomes dE/de1 in place (e_{l+1} = e1 + swa t)
-    if (Ed % 4 == 0)
+    if (s16_)
+      k_angle_out_bwd4<T, S16><<<grid(PA * 16), 256, 0, st>>>(PA, Ed, NM, CA, sa_, tt_[l], de_, dz16_, dsa_e_);
+    else if (Ed % 4 == 0)
       k_angle_out_bwd4<T><<<grid(PA * 16), 256, 0, st>>>(PA, Ed, NM, CA, sa_, tt_[l], de_, dz_, dsa_e_);
     else
       k_angle_out_bwd<T><<<grid(PA * 32), 256, 0, st>>>(PA, Ed, NM, CA, sa_, tt_[l], de_, dz_, dsa_e_);
@@ -1532,10 +1562,15 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
       g.A = dz_; g.a_rm = Ed; g.a_rk = 1;
       g.B = Wq_[l]; g.b_rk = 1; g.b_rn = Ed;
       g.C = da_; g.c_rm = Ed; g.c_rn = 1; g.nb2 = 1; g.alpha = T(1);
-      mm(g, st);
+      if (s16_) mm_a16(g, dz16_, st);
+      else mm(g, st);
     }
-    k_angle_bwd<T><<<angle_bwd_grid_, kAngThreads, angle_bwd_smem, st>>>(
-        n, NM, NA, CA, Ed, inv_na, sa_, rh_, qq_[l], Wphi_[l], da_, dq_, dsa_e_, drh_);
+    if (s16_)
+      k_angle_bwd<T, S16><<<angle_bwd_grid_, kAngThreads, angle_bwd_smem, st>>>(
+          n, NM, NA, CA, Ed, inv_na, sa_, rh_, qq_[l], Wphi_[l], da_, dq16_, dsa_e_, drh_);
+    else
+      k_angle_bwd<T><<<angle_bwd_grid_, kAngThreads, angle_bwd_smem, st>>>(
+          n, NM, NA, CA, Ed, inv_na, sa_, rh_, qq_[l], Wphi_[l], da_, dq_, dsa_e_, drh_);
     {  // de1 = de + dq Wp^T, in place on the angle rows' slots (dq is 0 elsewhere)
       Gemm<T> g{};
       g.M = (int)PA; g.N = Ed; g.K = Ed;
@@ -1543,7 +1578,8 @@ int PlainGf<T>::run(const NbrView& nv, const int* types, double* atom_e, cudaStr
       g.B = Wp_[l]; g.b_rk = 1; g.b_rn = Ed;
       g.C = de_; g.c_rm = Ed; g.c_rn = 1; g.nb2 = 1; g.alpha = T(1); g.beta = T(1);
       g.c_rows = ang_rows_;
-      mm(g, st);
+      if (s16_) mm_a16(g, dq16_, st);
+      else mm(g, st);
     }
     // (b): de now holds dE/de1; it becomes dE/de_l (e1 = e_l + tanh(...))
     const bool fused_rowsum = Ed % 4 == 0 && Ed <= 1024;
